@@ -1,0 +1,521 @@
+"""Plain FP64 CPU oracle of RF-DDES (Kalantzis, Xi, Saad: "Beyond AMLS: Domain decomposition
+with rational filtering", arXiv:1711.09487).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` may import this module.  The product path (the CUDA library and its Python
+binding) never calls it and shares no code with it; both sides read the same seeded arrays
+produced by ``rfdd_inputs``.
+
+Every routine follows the paper's steps in its own order and notation, using numpy/scipy
+primitives (dense LU, triangular solves, symmetric eigensolves, matrix products) as steps.  No
+blocking, fusion or reordering beyond what the cited passage states.  Readings of passages that
+are silent or ambiguous are marked "Reading:".
+
+Pins (see tests/test_oracle_*.py): closed-form Q1 spectra, the Midpoint-filter closed form,
+Gauss-Legendre exactness, the (2,2)-block identity of Eq. (finalizing), the block inverse of
+Eq. (inv_dd2) against a dense inverse, Prop. (lowrank), Theorems (uuhat), (uuhat2), (all) at
+tiny n, Sylvester inertia counts, and brute-force dense generalized eigensolves.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+MASK64 = (1 << 64) - 1
+
+
+# ----------------------------------------------------------------------------------------
+# Counter-based random numbers (SplitMix64, S. Vigna's published finaliser)
+# ----------------------------------------------------------------------------------------
+
+def splitmix64(x: int) -> int:
+    """SplitMix64 output for state ``x`` (increment already applied by the caller)."""
+    z = x & MASK64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK64
+    return z ^ (z >> 31)
+
+
+def counter_uniform(seed: int, stream: int, count: int) -> np.ndarray:
+    """Values in [-1, 1): element i of ``stream`` is
+    splitmix64(seed + (stream * 2^32 + i + 1) * 0x9E3779B97F4A7C15) >> 11, scaled by 2^-52 - 1.
+    Reading: the paper leaves the start vector of Algorithm 2 unspecified; both sides draw it from
+    this generator so that runs are reproducible and comparable."""
+    golden = np.uint64(0x9E3779B97F4A7C15)
+    c = (np.uint64(stream) << np.uint64(32)) + np.arange(1, count + 1, dtype=np.uint64)
+    z = np.uint64(seed & MASK64) + c * golden
+    z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+    z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    z = z ^ (z >> np.uint64(31))
+    return (z >> np.uint64(11)).astype(np.float64) * (2.0 ** -52) - 1.0
+
+
+# ----------------------------------------------------------------------------------------
+# Section 2.1: rational filter, Eq. (contour), (contour2), (contour3)
+# ----------------------------------------------------------------------------------------
+
+def quadrature(alpha: float, beta: float, n_nodes: int, rule: str = "midpoint"):
+    """Poles zeta_l (Im > 0) and weights omega_l of the discretised Cauchy integral.
+
+    Eq. (contour): I(zeta) = -1/(2 pi i) * contour integral of dnu / (zeta - nu) over the circle
+    nu = c + r e^{i theta}, c = (alpha+beta)/2, r = (beta-alpha)/2, counter-clockwise.  With
+    dnu = i r e^{i theta} d theta the integrand in theta is -(1/(2 pi)) r e^{i theta}/(zeta - nu).
+
+    * ``midpoint``: the midpoint rule of order 2 Nc on [0, 2 pi] (Section 6), keeping the Nc
+      nodes with positive imaginary part: theta_l = (2l-1) pi / (2 Nc), weight pi/Nc, so
+      omega_l = -r e^{i theta_l} / (2 Nc).
+    * ``gauss_legendre``: Nc Gauss-Legendre points t_l, w_l on [-1, 1] mapped to the upper
+      half circle theta = (pi/2)(1 + t) (the lower half follows by conjugation, Eq. contour3):
+      omega_l = -(r/4) w_l e^{i theta_l}.
+    """
+    if not (beta > alpha) or n_nodes < 1:
+        raise ValueError("need alpha < beta and n_nodes >= 1")
+    c = 0.5 * (alpha + beta)
+    r = 0.5 * (beta - alpha)
+    if rule == "midpoint":
+        theta = (2.0 * np.arange(1, n_nodes + 1) - 1.0) * np.pi / (2.0 * n_nodes)
+        e = np.exp(1j * theta)
+        z = c + r * e
+        w = -r * e / (2.0 * n_nodes)
+    elif rule == "gauss_legendre":
+        t, wl = np.polynomial.legendre.leggauss(n_nodes)
+        theta = 0.5 * np.pi * (1.0 + t)
+        e = np.exp(1j * theta)
+        z = c + r * e
+        w = -0.25 * r * wl * e
+    else:
+        raise ValueError(f"unknown rule {rule!r}")
+    return z.astype(np.complex128), w.astype(np.complex128)
+
+
+def filter_value(x, z, w):
+    """rho(x) = 2 Re sum_l omega_l / (x - zeta_l) for real x (Eq. contour3)."""
+    x = np.asarray(x, dtype=np.float64)[..., None]
+    return 2.0 * np.real(np.sum(w / (x - z), axis=-1))
+
+
+# ----------------------------------------------------------------------------------------
+# Section 2.3: domain-decomposition ordering, Eq. (dd1), (eq1)
+# ----------------------------------------------------------------------------------------
+
+class Blocks:
+    """Interior-first reordering of (A, M) and its blocks (Eq. dd1).
+
+    Interior variables of subdomain j = 0..p-1 come first (in increasing original index), then
+    the interface (label -1).  ``E[j]`` is the d_j x s coupling of subdomain j with the whole
+    interface; ``sidx[j]`` lists the interface columns where E[j] or ME[j] has a nonzero
+    (Reading: with a vertex separator the contiguous pattern E_j = [0, E^_j, 0] of Section 2.3 does
+    not hold; E^_j is E_j restricted to the columns sidx[j]).
+    """
+
+    def __init__(self, A, M, part, p):
+        A = sp.csr_matrix(A)
+        M = sp.csr_matrix(M)
+        part = np.asarray(part)
+        n = A.shape[0]
+        self.n, self.p = n, p
+        groups = [np.flatnonzero(part == j) for j in range(p)]
+        iface = np.flatnonzero(part == -1)
+        self.d = np.array([len(g) for g in groups], dtype=np.int64)
+        self.s = len(iface)
+        self.perm = np.concatenate(groups + [iface]).astype(np.int64)   # new -> old
+        self.iperm = np.empty(n, dtype=np.int64)
+        self.iperm[self.perm] = np.arange(n)                            # old -> new
+        self.off = np.concatenate([[0], np.cumsum(self.d)])
+        dsum = int(self.off[-1])
+        Ap = A[self.perm][:, self.perm].tocsr()
+        Mp = M[self.perm][:, self.perm].tocsr()
+        self.Ap, self.Mp = Ap, Mp
+        self.B, self.MB, self.E, self.ME, self.sidx = [], [], [], [], []
+        for j in range(p):
+            lo, hi = self.off[j], self.off[j + 1]
+            self.B.append(Ap[lo:hi, lo:hi].toarray())
+            self.MB.append(Mp[lo:hi, lo:hi].toarray())
+            Ej = Ap[lo:hi, dsum:].toarray()
+            MEj = Mp[lo:hi, dsum:].toarray()
+            # Eq. dd1: no couplings between different subdomains' interiors
+            for k in range(p):
+                if k != j:
+                    klo, khi = self.off[k], self.off[k + 1]
+                    if Ap[lo:hi, klo:khi].nnz or Mp[lo:hi, klo:khi].nnz:
+                        raise ValueError("partition is not a vertex separator")
+            cols = np.flatnonzero((np.abs(Ej).sum(0) + np.abs(MEj).sum(0)) > 0)
+            self.E.append(Ej)
+            self.ME.append(MEj)
+            self.sidx.append(cols)
+        self.C = Ap[dsum:, dsum:].toarray()
+        self.MC = Mp[dsum:, dsum:].toarray()
+
+    def to_original(self, X):
+        """Permute rows back to the input ordering (Algorithm 3, step 8)."""
+        return X[self.iperm]
+
+
+# ----------------------------------------------------------------------------------------
+# Section 3.1: shifted blocks and the Schur complement, Eq. (inv_dd2)
+# ----------------------------------------------------------------------------------------
+
+def shifted(blk: Blocks, z):
+    """B_z = B - z M_B, E_z = E - z M_E, C_z = C - z M_C (Section 3.1)."""
+    Bz = [blk.B[j] - z * blk.MB[j] for j in range(blk.p)]
+    Ez = [blk.E[j] - z * blk.ME[j] for j in range(blk.p)]
+    Cz = blk.C - z * blk.MC
+    return Bz, Ez, Cz
+
+
+def schur(blk: Blocks, z):
+    """S_z = C_z - E_z^T B_z^{-1} E_z.
+
+    Reading: the paper writes E^H in Eq. (inv_dd2); A - zM is complex *symmetric*, so its block
+    inverse uses the plain transpose (consistent with Eq. schur_eigvec3).  Never conjugate.
+    """
+    Bz, Ez, Cz = shifted(blk, z)
+    S = Cz.astype(np.complex128).copy()
+    for j in range(blk.p):
+        S -= Ez[j].T @ np.linalg.solve(Bz[j], Ez[j])
+    return S
+
+
+class Factors:
+    """LU factorisations of every B_j(zeta_l) and S(zeta_l) (Algorithm 3 step 5 needs solves with
+    them; the paper uses PARDISO/MUMPS, the oracle uses dense LU with partial pivoting)."""
+
+    def __init__(self, blk: Blocks, z):
+        self.blk = blk
+        self.z = np.atleast_1d(np.asarray(z, dtype=np.complex128))
+        self.Blu, self.Slu, self.Ez = [], [], []
+        for zl in self.z:
+            Bz, Ez, Cz = shifted(blk, zl)
+            lus = [sla.lu_factor(Bz[j]) for j in range(blk.p)]
+            S = Cz.astype(np.complex128).copy()
+            for j in range(blk.p):
+                S -= Ez[j].T @ sla.lu_solve(lus[j], Ez[j])
+            self.Blu.append(lus)
+            self.Ez.append(Ez)
+            self.Slu.append(sla.lu_factor(S))
+
+    def solve_S(self, l, G):
+        return sla.lu_solve(self.Slu[l], G.astype(np.complex128))
+
+    def solve_B(self, l, F):
+        """Block-diagonal solve with B_{zeta_l} on the interior part (d rows)."""
+        blk = self.blk
+        out = np.empty(F.shape, dtype=np.complex128)
+        for j in range(blk.p):
+            lo, hi = blk.off[j], blk.off[j + 1]
+            out[lo:hi] = sla.lu_solve(self.Blu[l][j], F[lo:hi].astype(np.complex128))
+        return out
+
+    def resolvent(self, l, V):
+        """(A - zeta_l M)^{-1} V through the block inverse of Eq. (inv_dd2):
+        t = B^{-1} f, y = S^{-1} (g - E^T t), u = t - B^{-1} E y."""
+        blk = self.blk
+        dsum = int(blk.off[-1])
+        f, g = V[:dsum], V[dsum:]
+        t = self.solve_B(l, f)
+        Et = np.vstack([self.Ez[l][j] for j in range(blk.p)])          # d x s (= E_z)
+        y = self.solve_S(l, g - Et.T @ t)
+        u = t - self.solve_B(l, Et @ y)
+        return np.vstack([u, y])
+
+
+def filter_interface(fac: Factors, w, X):
+    """Re sum_l omega_l S(zeta_l)^{-1} X  (Algorithm 2, line 2, as printed: no factor 2)."""
+    acc = np.zeros(X.shape, dtype=np.complex128)
+    for l in range(len(fac.z)):
+        acc += w[l] * fac.solve_S(l, X)
+    return np.real(acc)
+
+
+def filter_full(fac: Factors, w, MX):
+    """2 Re sum_l omega_l (A - zeta_l M)^{-1} (M X)  (Eq. rhoAM), applied via Eq. (inv_dd2)."""
+    acc = np.zeros(MX.shape, dtype=np.complex128)
+    for l in range(len(fac.z)):
+        acc += w[l] * fac.resolvent(l, MX)
+    return 2.0 * np.real(acc)
+
+
+# ----------------------------------------------------------------------------------------
+# Section 3.2: Algorithm 2 (Krylov restricted to the interface variables)
+# ----------------------------------------------------------------------------------------
+
+def _orth_against(Qs, W, passes=2):
+    for _ in range(passes):
+        for Qk in Qs:
+            W = W - Qk @ (Qk.T @ W)
+    return W
+
+
+def lanczos_interface(apply_F, s, tol=1e-6, block=1, seed=1, check_every=10, max_steps=None):
+    """Algorithm 2 on F = Re sum omega_l S_l^{-1} with block size ``block`` (b = 1 is the printed
+    algorithm).  Returns dict(Q (s x mu), alphas (list of b x b), betas, traces, mu).
+
+    Readings:
+    * q^(1): a counter-based uniform block, orthonormalised (the paper leaves it open).
+    * lines 4-6 (one classical Gram-Schmidt pass) are run twice ("CGS2"); no effect in exact
+      arithmetic, keeps ||Q^T Q - I|| at rounding level.
+    * line 13: every ``check_every`` vectors (ceil(check_every / b) block steps) stop when
+      |tr T_mu - tr T_(mu - check_every)| <= tol * |tr T_mu|; also stop once mu = s.
+    * breakdown (line 8): ||w|| <= 1e-14 max|a| -> new random vectors orthogonal to Q.
+    """
+    b = block
+    start = counter_uniform(seed, 0, s * b).reshape(s, b)
+    Q1, _ = np.linalg.qr(start)
+    Qs = [Q1]
+    Qprev = np.zeros((s, b))
+    Bmu = np.zeros((b, b))
+    alphas, betas, traces = [], [], []
+    steps_per_check = max(1, -(-check_every // b))
+    max_steps = max_steps or -(-s // b)
+    trace = 0.0
+    history = [0.0]
+    extra = 1
+    for mu in range(1, max_steps + 1):
+        Qmu = Qs[-1]
+        W = apply_F(Qmu) - Qprev @ Bmu.T                       # line 2
+        Amu = Qmu.T @ W                                         # line 3
+        Amu = 0.5 * (Amu + Amu.T)
+        W = _orth_against(Qs, W)                                # lines 4-6 (twice)
+        alphas.append(Amu)
+        trace += float(np.trace(Amu))
+        traces.append(trace)
+        if mu * b >= s:
+            break
+        Qn, R = np.linalg.qr(W)                                 # lines 7-12
+        amax = max(np.max(np.abs(np.diag(A_))) for A_ in alphas)
+        dead = np.abs(np.diag(R)) <= 1e-14 * max(amax, 1e-300)
+        if np.any(dead):
+            fresh = counter_uniform(seed, extra, s * b).reshape(s, b)
+            extra += 1
+            fresh = _orth_against(Qs, fresh)
+            Qf, _ = np.linalg.qr(fresh)
+            Qn[:, dead] = Qf[:, dead]
+            Qn = _orth_against(Qs, Qn)
+            Qn, R2 = np.linalg.qr(Qn)
+            R[dead, :] = 0.0
+        # a vector that lost most of its norm in lines 4-6 is mostly rounding noise: one more
+        # pass after normalisation restores orthogonality (the "twice is enough" rule)
+        Qn = _orth_against(Qs, Qn, passes=1)
+        Qn, R2 = np.linalg.qr(Qn)
+        R = R2 @ R
+        betas.append(R)
+        Bmu = R
+        Qprev = Qmu
+        Qs.append(Qn)
+        if mu % steps_per_check == 0:                          # line 13
+            if abs(trace - history[-1]) <= tol * abs(trace):
+                break
+            history.append(trace)
+    Q = np.hstack(Qs[:len(alphas)])
+    return dict(Q=Q, alphas=alphas, betas=betas, traces=traces, mu=Q.shape[1])
+
+
+# ----------------------------------------------------------------------------------------
+# Section 4 and 5: interior approximation, Eq. (prol2), (yet1), (trabala), (trabala2), (z)
+# ----------------------------------------------------------------------------------------
+
+def interior_eigvecs(blk: Blocks, sigma, nev_b):
+    """V_j: eigenvectors of (B_sigma^(j), M_B^(j)) for the nev_B^(j) eigenvalues of smallest
+    magnitude (Algorithm 3, step 3), M_B-normalised.  Dense generalised symmetric eigensolve."""
+    V = []
+    for j in range(blk.p):
+        Bs = blk.B[j] - sigma * blk.MB[j]
+        dl, X = sla.eigh(Bs, blk.MB[j])
+        k = min(int(nev_b), blk.d[j])
+        order = np.argsort(np.abs(dl), kind="stable")[:k]
+        V.append(X[:, np.sort(order)])
+    return V
+
+
+def interface_rows(blk: Blocks, Q, j):
+    """Q_j: rows of Q at subdomain j's coupled interface nodes (Eq. q; Reading: s_j = |sidx_j|)."""
+    return Q[blk.sidx[j]]
+
+
+def resolvent_chains(blk: Blocks, sigma, Q, psi):
+    """Sigma_j^(psi) and Gamma_j^(psi) of Eq. (trabala2) with Phi_j, Psi_j of Eq. (trabala)."""
+    Sig, Gam = [], []
+    for j in range(blk.p):
+        Bs = blk.B[j] - sigma * blk.MB[j]
+        lu = sla.lu_factor(Bs)
+        Qj = interface_rows(blk, Q, j)
+        Ehat = blk.E[j][:, blk.sidx[j]]
+        MEhat = blk.ME[j][:, blk.sidx[j]]
+        Phi = (Ehat - sigma * MEhat) @ Qj
+        Psi = MEhat @ Qj
+        cs, cg = [], []
+        X = sla.lu_solve(lu, Phi)
+        Y = sla.lu_solve(lu, Psi)
+        for t in range(psi):
+            cs.append(X)
+            cg.append(Y)
+            if t + 1 < psi:
+                X = sla.lu_solve(lu, blk.MB[j] @ X)
+                Y = sla.lu_solve(lu, blk.MB[j] @ Y)
+        Sig.append(np.hstack(cs))
+        Gam.append(np.hstack(cg))
+    return Sig, Gam
+
+
+def build_Z(blk: Blocks, V, Sig, Gam, Q, psi, with_gamma=None):
+    """Projection matrix Z of Eq. (z), rows in the interior-first ordering.
+
+    Column blocks: [blockdiag(V_j) | -Sigma^(psi) | Gamma^(psi)]; the interface rows hold
+    [Q, 0_{s,(psi-1)mu}] under the Sigma block.  Gamma is dropped when M_E == 0 (Section 5.1).
+    """
+    n, s = blk.n, blk.s
+    mu = Q.shape[1]
+    kappa = sum(v.shape[1] for v in V)
+    if with_gamma is None:
+        with_gamma = any(np.any(me != 0) for me in blk.ME)
+    k = kappa + psi * mu * (2 if with_gamma else 1)
+    Z = np.zeros((n, k))
+    col = 0
+    for j in range(blk.p):
+        lo, hi = blk.off[j], blk.off[j + 1]
+        Z[lo:hi, col:col + V[j].shape[1]] = V[j]
+        col += V[j].shape[1]
+    for j in range(blk.p):
+        lo, hi = blk.off[j], blk.off[j + 1]
+        Z[lo:hi, col:col + psi * mu] = -Sig[j]
+        if with_gamma:
+            Z[lo:hi, col + psi * mu:col + 2 * psi * mu] = Gam[j]
+    dsum = int(blk.off[-1])
+    Z[dsum:, col:col + mu] = Q
+    return Z
+
+
+# ----------------------------------------------------------------------------------------
+# Rayleigh-Ritz (Algorithm 3, step 7) and residuals
+# ----------------------------------------------------------------------------------------
+
+def m_orthonormal_basis(Ap, Mp, Z, drop=1e-12):
+    """Basis W of range(Z) with W^T M W = I.  Reading: Z may be rank deficient (its column
+    blocks overlap), so the Gram matrix Z^T M Z is eigendecomposed and directions with
+    eigenvalue < drop * max are pruned (this is the plain definition of Rayleigh-Ritz on
+    range(Z))."""
+    nrm = np.sqrt(np.maximum(np.einsum("ij,ij->j", Z, Mp @ Z), 1e-300))
+    Zs = Z / nrm
+    G = Zs.T @ (Mp @ Zs)
+    G = 0.5 * (G + G.T)
+    g, U = np.linalg.eigh(G)
+    keep = g > drop * g.max()
+    return Zs @ (U[:, keep] / np.sqrt(g[keep]))
+
+
+def rayleigh_ritz(Ap, Mp, Z, drop=1e-12):
+    """Solve Z^T A Z G = Z^T M Z G Lambda on range(Z); returns sorted (theta, X) with
+    X^T M X = I."""
+    W = m_orthonormal_basis(Ap, Mp, Z, drop)
+    H = W.T @ (Ap @ W)
+    H = 0.5 * (H + H.T)
+    th, G = np.linalg.eigh(H)
+    return th, W @ G
+
+
+def residuals(A, M, lam, X):
+    """||A x - lambda M x||_2 / (|lambda| ||M x||_2) per column."""
+    AX = A @ X
+    MX = M @ X
+    R = AX - MX * lam
+    return np.linalg.norm(R, axis=0) / (np.abs(lam) * np.linalg.norm(MX, axis=0))
+
+
+# ----------------------------------------------------------------------------------------
+# Counting: Sylvester inertia through the DD blocks (Haynsworth additivity)
+# ----------------------------------------------------------------------------------------
+
+def inertia_count(blk: Blocks, sigma):
+    """Number of eigenvalues of (A, M) below sigma: nu(A - sigma M) = nu(B_sigma) + nu(S(sigma))
+    (Haynsworth inertia additivity applied to the block form of Eq. eq1)."""
+    neg = 0
+    for j in range(blk.p):
+        neg += int(np.count_nonzero(np.linalg.eigvalsh(blk.B[j] - sigma * blk.MB[j]) < 0))
+    S = np.real(schur(blk, sigma))
+    S = 0.5 * (S + S.T)
+    neg += int(np.count_nonzero(np.linalg.eigvalsh(S) < 0))
+    return neg
+
+
+# ----------------------------------------------------------------------------------------
+# Algorithm 3 (RF-DDES) + completion passes
+# ----------------------------------------------------------------------------------------
+
+def select_nearest(theta, alpha, beta, m):
+    """Indices of the m values closest to [alpha, beta] (distance 0 inside)."""
+    dist = np.maximum(np.maximum(alpha - theta, theta - beta), 0.0)
+    order = np.lexsort((np.abs(theta - 0.5 * (alpha + beta)), dist))
+    return np.sort(order[:m])
+
+
+def rfdd_solve(A, M, part, p, alpha, beta, n_nodes=4, rule="midpoint", sigma=None, nev_b=100,
+               psi=3, lanczos_tol=1e-6, block=1, seed=1, res_tol=1e-10, max_passes=8,
+               guard_frac=0.3, min_guard=8):
+    """RF-DDES (Algorithm 3) followed by completion passes.
+
+    Readings:
+    * sigma defaults to (alpha+beta)/2 (the paper's default is 0; the theory favours sigma
+      near the wanted eigenvalues).
+    * nev_B^(j) = min(nev_b, d_j).
+    * Completion (accuracy contract beyond the paper): X <- 2 Re sum omega (A - zeta M)^{-1} M X
+      through Eq. (inv_dd2) with the same factors, then M-orthonormalisation and Rayleigh-Ritz;
+      X starts from the m RF-DDES Ritz vectors nearest the interval, m = n_in + max(ceil(0.3 n_in),
+      8); stop when every Ritz pair inside [alpha, beta] has residual <= res_tol and the count
+      inside is unchanged from the previous pass.
+    Returns a dict with eigenvalues, eigenvectors (original ordering), residuals and diagnostics.
+    """
+    A = sp.csr_matrix(A)
+    M = sp.csr_matrix(M)
+    if sigma is None:
+        sigma = 0.5 * (alpha + beta)
+    blk = Blocks(A, M, part, p)                                   # step 1
+    z, w = quadrature(alpha, beta, n_nodes, rule)
+    fac = Factors(blk, z)
+    V = interior_eigvecs(blk, sigma, nev_b)                       # steps 2-4
+    lz = lanczos_interface(lambda X: filter_interface(fac, w, X), blk.s, lanczos_tol, block, seed)
+    Q = lz["Q"]                                                   # step 5
+    Sig, Gam = resolvent_chains(blk, sigma, Q, psi)
+    Z = build_Z(blk, V, Sig, Gam, Q, psi)                         # step 6
+    Ap, Mp = blk.Ap, blk.Mp
+    theta, X = rayleigh_ritz(Ap, Mp, Z)                           # step 7
+    inside = (theta >= alpha) & (theta <= beta)
+    pre = dict(theta=theta[inside].copy(), res=residuals(Ap, Mp, theta[inside], X[:, inside]),
+               k=Z.shape[1], mu=lz["mu"])
+    n_in = int(np.count_nonzero(inside))
+    m = min(n_in + max(int(math.ceil(guard_frac * n_in)), min_guard), Z.shape[1])
+    X = X[:, select_nearest(theta, alpha, beta, m)]
+    count_prev = n_in
+    passes = 0
+    converged = False
+    res_in = pre["res"]
+    th_in = pre["theta"]
+    X_in = X
+    for passes in range(1, max_passes + 1):
+        X = filter_full(fac, w, Mp @ X)                           # completion pass
+        theta, X = rayleigh_ritz(Ap, Mp, X)
+        inside = (theta >= alpha) & (theta <= beta)
+        th_in = theta[inside]
+        X_in = X[:, inside]
+        res_in = residuals(Ap, Mp, th_in, X_in)
+        cnt = int(np.count_nonzero(inside))
+        if cnt == count_prev and (cnt == 0 or res_in.max() <= res_tol):
+            converged = True
+            break
+        count_prev = cnt
+    return dict(evals=th_in, evecs=blk.to_original(X_in), resid=res_in, passes=passes,
+                converged=converged, mu=lz["mu"], k=Z.shape[1], pre=pre, blocks=blk,
+                z=z, w=w, sigma=sigma, lanczos=lz)
+
+
+def brute_force(A, M, alpha=None, beta=None):
+    """All eigenpairs of the pencil by a dense generalised symmetric eigensolve (small n)."""
+    A = sp.csr_matrix(A).toarray()
+    M = sp.csr_matrix(M).toarray()
+    lam, X = sla.eigh(A, M)
+    if alpha is not None:
+        sel = (lam >= alpha) & (lam <= beta)
+        lam, X = lam[sel], X[:, sel]
+    return lam, X
