@@ -1,0 +1,215 @@
+/*
+ * rfdd.h -- C ABI of the GB300-native RF-DDES interface rational filter.
+ *
+ * Method: Kalantzis, Xi, Saad, "Beyond AMLS: Domain decomposition with rational filtering"
+ * (arXiv:1711.09487).  The library finds every eigenpair (lambda, x) of a real symmetric pencil
+ * A x = lambda M x (M SPD) with lambda in [alpha, beta] (Section 1).  The number of eigenpairs is
+ * found, not given.
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: RFDD_OK (0) or one of the RFDD_E* codes below.  On error nothing the caller
+ *    owns is modified, except output buffers of the failing call may hold partial data; the
+ *    message of the last error on the calling thread is available from rfdd_last_error().
+ *  - Sparse inputs are full (both triangles) CSR with int64 row pointers, int32 column indices
+ *    (sorted within each row) and float64 values, in HOST memory.  They are copied at setup;
+ *    the caller keeps ownership.
+ *  - Dense host arrays are row-major.  Complex values are interleaved (re, im) float64 pairs.
+ *  - "Interior-first ordering" (Eq. dd1): the interior unknowns of subdomain 0, 1, ..., p-1
+ *    (each in increasing original index), then the interface unknowns (label -1) in increasing
+ *    original index.  Subdomain j occupies rows [off_j, off_j + d_j); the interface occupies the
+ *    last s rows.  rfdd_layout() returns off_j, d_j, s and the permutation.
+ *  - Every call runs on the handle's CUDA stream and returns after its results are complete,
+ *    except rfdd_solve_async().
+ *  - A handle is not thread-safe; distinct handles may be used from different threads.
+ */
+#ifndef RFDD_H
+#define RFDD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------------- */
+#define RFDD_OK 0
+#define RFDD_EINVAL 1            /* bad argument: size mismatch, alpha >= beta, n_nodes < 1, NULL */
+#define RFDD_ENOTSYM 2           /* A or M not symmetric (pattern or values) */
+#define RFDD_EPARTITION 3        /* edge between two subdomains, empty subdomain, no interface */
+#define RFDD_ENOTSPD_M 4         /* M not positive definite (a non-positive diagonal entry) */
+#define RFDD_ESINGULAR 5         /* zero or non-finite pivot in a factorisation */
+#define RFDD_ENOMEM 6            /* device allocation failed */
+#define RFDD_EADMIT 7            /* the solve's device memory need exceeds opt.mem_budget */
+#define RFDD_NOT_CONVERGED 8     /* results returned, but some residual > res_tol */
+#define RFDD_ECUDA 9             /* CUDA runtime error */
+#define RFDD_ESTATE 10           /* call out of order (e.g. filter before factor) */
+
+/* ---- option values ---------------------------------------------------------------------- */
+#define RFDD_FP64 0              /* plain path: all factorisations and solves in FP64 */
+#define RFDD_MIXED 1             /* complex-FP32 factorisations, FP64 iterative refinement */
+#define RFDD_MIDPOINT 0          /* midpoint rule of order 2Nc (Section 6, the paper's choice) */
+#define RFDD_GAUSS_LEGENDRE 1    /* Gauss-Legendre on the upper half circle (Section 2.1) */
+
+typedef struct {
+  int64_t n;
+  const int64_t *rowptr; /* n+1 */
+  const int32_t *col;    /* rowptr[n] */
+  const double *val;     /* rowptr[n] */
+} rfdd_csr;
+
+typedef struct {
+  int precision;        /* RFDD_FP64 | RFDD_MIXED (default RFDD_MIXED) */
+  int quad_rule;        /* RFDD_MIDPOINT | RFDD_GAUSS_LEGENDRE (default midpoint) */
+  double sigma;         /* real shift of the interior step (Eq. prol2); NaN -> (alpha+beta)/2 */
+  int nev_b;            /* eigenvectors per subdomain in V_j (Alg. 3 step 3); default 100,
+                           capped at d_j */
+  int psi;              /* resolvent-expansion depth (Eq. yet1); default 3 */
+  double lanczos_tol;   /* Alg. 2 trace-stagnation tolerance; default 1e-6 */
+  int block;            /* block size b of the block variant of Alg. 2; default 32 */
+  double res_tol;       /* residual target ||Ax-lMx||/(|l| ||Mx||); default 1e-10 */
+  int max_passes;       /* completion passes (filtered subspace iteration); default 8 */
+  int ir_max;           /* FP64 iterative-refinement steps per shifted solve; default 10 */
+  uint64_t seed;        /* counter-based RNG seed for start blocks; default 1 */
+  size_t mem_budget;    /* device bytes one solve may hold; 0 = no limit */
+  void *stream;         /* cudaStream_t to run on; NULL = a stream owned by the handle */
+  double guard_frac;    /* completion block m = n_in + max(ceil(guard_frac n_in), min_guard) */
+  int min_guard;        /* (defaults 0.3 and 8) */
+  int keep_schur;       /* nonzero: keep an unfactored copy of every S(zeta_l) (for checks) */
+  int subspace_iters;   /* block shift-invert iterations that build V_j (default 4) */
+} rfdd_options;
+
+typedef struct rfdd_handle rfdd_handle;
+typedef struct rfdd_result rfdd_result;
+
+/* Diagnostics of one solve.  Times are CUDA-event milliseconds on the handle's stream. */
+typedef struct {
+  int64_t nev;          /* eigenpairs returned (inside [alpha, beta]) */
+  int64_t mu;           /* Alg. 2 basis size (columns of Q) */
+  int64_t k;            /* columns of Z (Eq. z) kept after M-orthonormalisation */
+  int64_t m;            /* completion block size */
+  int32_t passes;       /* completion passes run */
+  int32_t ir_steps_max; /* largest number of refinement steps any shifted solve needed */
+  double max_resid;     /* largest residual among the returned pairs */
+  double pre_max_resid; /* largest residual of the RF-DDES Ritz pairs before completion */
+  int64_t pre_nev;      /* RF-DDES Ritz values inside [alpha, beta] before completion */
+  double t_factor_ms;   /* a2-a5: shifted blocks, LU(B), Schur update, S assembly + LU(S) */
+  double t_lanczos_ms;  /* a6-a7 */
+  double t_interior_ms; /* a8 */
+  double t_rr_ms;       /* a9 */
+  double t_complete_ms; /* a10 */
+  double t_total_ms;
+  int32_t status;       /* RFDD_OK or RFDD_NOT_CONVERGED */
+} rfdd_info;
+
+/* Fill *opt with the defaults listed above. */
+void rfdd_default_options(rfdd_options *opt);
+
+/* Message of the last error on this thread ("" if none).  Valid until the next call. */
+const char *rfdd_last_error(void);
+
+/* Static description of a status code. */
+const char *rfdd_status_string(int code);
+
+/* ---- a0: quadrature (Section 2.1, Eq. contour/contour2/contour3; Section 6) -------------
+ * Poles zeta_l (Im > 0) and weights omega_l, l = 0..n_nodes-1, of the rational filter
+ * rho(x) = 2 Re sum_l omega_l/(x - zeta_l) on the circle through alpha and beta.
+ * z_out, w_out: host, 2*n_nodes doubles each (interleaved complex).  Host only. */
+int rfdd_quadrature(double alpha, double beta, int32_t n_nodes, int32_t rule, double *z_out,
+                    double *w_out);
+
+/* ---- a1: setup (Alg. 3 step 1; Section 2.3, Eq. dd1) -----------------------------------
+ * Validates (A, M, part), computes the interior-first ordering, splits the pencil into the
+ * blocks B_j, M_B^(j), E_j, M_E^(j), C, M_C and uploads them.  part: host int32[n], label -1
+ * for interface unknowns and 0..p-1 for subdomain interiors; the labels must form a vertex
+ * separator (no A or M entry couples two different subdomains) and every subdomain and the
+ * interface must be non-empty.  opt may be NULL (defaults).  On success *out owns device
+ * memory until rfdd_destroy(). */
+int rfdd_setup(const rfdd_csr *A, const rfdd_csr *M, const int32_t *part, int32_t p,
+               const rfdd_options *opt, rfdd_handle **out);
+
+/* Layout of the interior-first ordering: off (p+1 int64: subdomain j is rows off[j]..off[j+1]-1,
+ * the interface rows off[p]..n-1) and perm (n int64: new index -> original index).  Either
+ * pointer may be NULL.  *p_out and *s_out receive p and s. */
+int rfdd_layout(const rfdd_handle *h, int64_t *off, int64_t *perm, int32_t *p_out,
+                int64_t *s_out);
+
+void rfdd_destroy(rfdd_handle *h);
+
+/* ---- full solve: Alg. 3 (RF-DDES) + completion ------------------------------------------
+ * Runs a0-a10 for [alpha, beta] with n_nodes quadrature poles.  Factors of the previous solve
+ * are replaced.  *out receives a result (also on RFDD_NOT_CONVERGED, whose pairs carry their
+ * residuals); free it with rfdd_result_free(). */
+int rfdd_solve(rfdd_handle *h, double alpha, double beta, int32_t n_nodes, rfdd_result **out);
+
+/* Eigenpairs of a result.  evals: ascending, nev doubles.  evecs: n x nev row-major, original
+ * ordering, M-orthonormal.  resid: nev residuals ||A x - l M x||_2/(|l| ||M x||_2).  device = 0
+ * gives host pointers, 1 gives device pointers.  Pointers stay valid until rfdd_result_free().
+ * Any output pointer may be NULL. */
+int rfdd_result_get(const rfdd_result *r, int64_t *nev, const double **evals,
+                    const double **evecs, const double **resid, int32_t device);
+int rfdd_result_info(const rfdd_result *r, rfdd_info *info);
+/* RF-DDES Ritz values inside [alpha, beta] before completion (Alg. 3 step 7), ascending; host.
+ * *count receives their number; vals may be NULL to query it. */
+int rfdd_result_pre_evals(const rfdd_result *r, int64_t *count, double *vals);
+void rfdd_result_free(rfdd_result *r);
+
+/* ---- step-level entry points (each runs one row of the hot path on the handle) ------------ */
+
+/* a2-a5 (Section 3.1, Eq. inv_dd2; paper: PARDISO/MUMPS factorisations): for every node
+ * zeta_l (host, 2*n_nodes doubles, interleaved) assemble B_j(zeta_l) = B_j - zeta_l M_B^(j)
+ * densely, LU-factor all of them (partial pivoting by |re|+|im| within tournament-selected
+ * candidate rows), form X = B_j^{-1} E_j(zeta_l), the Schur complement
+ * S(zeta_l) = C - zeta_l M_C - sum_j E_j(zeta_l)^T X (plain transpose), and LU-factor each S.
+ * w (same layout) holds the quadrature weights used by later filter calls. */
+int rfdd_factor(rfdd_handle *h, int32_t n_nodes, const double *z, const double *w);
+
+/* Copy the assembled, unfactored S(zeta_l) (s x s complex, row-major, interleaved) to host
+ * memory S_out (2*s*s doubles).  Needs opt.keep_schur != 0 at setup. */
+int rfdd_schur_copy(rfdd_handle *h, int32_t node, double *S_out);
+
+/* Solve with the factors of node `node`: which = 0 -> B_j(zeta) X = R for subdomain j (R is
+ * d_j x nrhs); which = 1 -> S(zeta) X = R (R is s x nrhs); which = 2 -> (A - zeta M) X = R on
+ * the interior-first ordering (R is n x nrhs) through the block inverse of Eq. (inv_dd2) with
+ * FP64 iterative refinement.  R, X: host, complex interleaved row-major. */
+int rfdd_shifted_solve(rfdd_handle *h, int32_t node, int32_t which, int32_t j, int64_t nrhs,
+                       const double *R, double *X);
+
+/* a6 (Alg. 2 line 2): W = Re sum_l omega_l S(zeta_l)^{-1} X for a real s x b block X.
+ * X, W: host, s x b float64 row-major. */
+int rfdd_filter_apply(rfdd_handle *h, int64_t b, const double *X, double *W);
+
+/* a7 (Alg. 2, block variant, trace-stagnation stop every ceil(10/b) block steps): runs the
+ * interface Krylov process on F = Re sum omega_l S_l^{-1}.  Q_out: host s x cap float64
+ * row-major (may be NULL); *mu receives the basis size; traces (may be NULL, cap entries)
+ * receive tr(T) after each block step; *nsteps the number of block steps. */
+int rfdd_lanczos(rfdd_handle *h, int64_t cap, double *Q_out, int64_t *mu, double *traces,
+                 int32_t *nsteps);
+
+/* a8 (Section 4; Alg. 3 steps 2-4 and 6; Eq. trabala, trabala2, z): builds the projection
+ * basis Z = [blockdiag(V_j) | -Sigma^(psi) | Gamma^(psi)] from the last Lanczos basis Q with
+ * the real shift sigma (NaN -> (alpha+beta)/2 of the last solve or 0).  Z_out: host n x k
+ * float64 row-major on the interior-first ordering (may be NULL); *k receives its column
+ * count; kappa_out (may be NULL) receives sum_j nev_B^(j). */
+int rfdd_interior(rfdd_handle *h, double sigma, int64_t cap, double *Z_out, int64_t *k,
+                  int64_t *kappa_out);
+
+/* a9 (Alg. 3 step 7): Rayleigh-Ritz of (A, M) on range(Z) of the last rfdd_interior call.
+ * theta_out: host, all Ritz values ascending (cap entries); *k receives their number. */
+int rfdd_rayleigh_ritz(rfdd_handle *h, int64_t cap, double *theta_out, int64_t *k);
+
+/* Asynchronous solve for serving: enqueues the solve on `stream` (a cudaStream_t, NULL = the
+ * handle's) and returns; rfdd_result_ready() reports completion (1 done, 0 running, <0 error
+ * code negated).  The handle must not be used until the result is ready. */
+int rfdd_solve_async(rfdd_handle *h, double alpha, double beta, int32_t n_nodes, void *stream,
+                     rfdd_result **out);
+int rfdd_result_ready(const rfdd_result *r);
+
+/* Device bytes a solve with these parameters needs (factors, Schur complements, workspaces);
+ * used for admission against a memory budget. */
+int rfdd_memory_estimate(const rfdd_handle *h, int32_t n_nodes, int64_t nev_guess, size_t *bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RFDD_H */

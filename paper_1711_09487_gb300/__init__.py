@@ -1,0 +1,348 @@
+"""GB300-native RF-DDES interface rational filter (arXiv:1711.09487) -- Python binding.
+
+A thin ctypes layer over the C ABI declared in ``include/rfdd.h``; every function here has the
+name of the C entry point it marshals arguments for.  All numerical work runs in the CUDA
+library ``_build/librfdd.so`` (build it with ``paper_1711_09487_gb300.build.build()``).  There is
+no CPU fallback: if the library is missing, loading fails with an error.
+
+Dense arrays are numpy, row-major; complex data is numpy complex128 (interleaved re, im).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "librfdd.so")
+
+RFDD_OK = 0
+RFDD_EINVAL = 1
+RFDD_ENOTSYM = 2
+RFDD_EPARTITION = 3
+RFDD_ENOTSPD_M = 4
+RFDD_ESINGULAR = 5
+RFDD_ENOMEM = 6
+RFDD_EADMIT = 7
+RFDD_NOT_CONVERGED = 8
+RFDD_ECUDA = 9
+RFDD_ESTATE = 10
+RFDD_FP64 = 0
+RFDD_MIXED = 1
+RFDD_MIDPOINT = 0
+RFDD_GAUSS_LEGENDRE = 1
+
+# Exported C symbols (kept in sync with include/rfdd.h; checked by tests/test_abi.py).
+SYMBOLS = [
+    "rfdd_default_options", "rfdd_last_error", "rfdd_status_string", "rfdd_quadrature", "rfdd_setup",
+    "rfdd_layout", "rfdd_destroy", "rfdd_solve", "rfdd_result_get", "rfdd_result_info",
+    "rfdd_result_pre_evals", "rfdd_result_free", "rfdd_factor", "rfdd_schur_copy", "rfdd_shifted_solve",
+    "rfdd_filter_apply", "rfdd_lanczos", "rfdd_interior", "rfdd_rayleigh_ritz", "rfdd_solve_async",
+    "rfdd_result_ready", "rfdd_memory_estimate",
+]
+
+
+class RfddError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class rfdd_csr(C.Structure):
+    _fields_ = [("n", C.c_int64), ("rowptr", C.POINTER(C.c_int64)), ("col", C.POINTER(C.c_int32)),
+                ("val", C.POINTER(C.c_double))]
+
+
+class rfdd_options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("quad_rule", C.c_int), ("sigma", C.c_double), ("nev_b", C.c_int),
+                ("psi", C.c_int), ("lanczos_tol", C.c_double), ("block", C.c_int), ("res_tol", C.c_double),
+                ("max_passes", C.c_int), ("ir_max", C.c_int), ("seed", C.c_uint64), ("mem_budget", C.c_size_t),
+                ("stream", C.c_void_p), ("guard_frac", C.c_double), ("min_guard", C.c_int),
+                ("keep_schur", C.c_int), ("subspace_iters", C.c_int)]
+
+
+class rfdd_info(C.Structure):
+    _fields_ = [("nev", C.c_int64), ("mu", C.c_int64), ("k", C.c_int64), ("m", C.c_int64),
+                ("passes", C.c_int32), ("ir_steps_max", C.c_int32), ("max_resid", C.c_double),
+                ("pre_max_resid", C.c_double), ("pre_nev", C.c_int64), ("t_factor_ms", C.c_double),
+                ("t_lanczos_ms", C.c_double), ("t_interior_ms", C.c_double), ("t_rr_ms", C.c_double),
+                ("t_complete_ms", C.c_double), ("t_total_ms", C.c_double), ("status", C.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"CUDA library {p} is missing: run paper_1711_09487_gb300.build.build() first "
+                           "(there is no CPU fallback)")
+    lib = C.CDLL(p)
+    vp, i64, i32, dp = C.c_void_p, C.c_int64, C.c_int32, C.POINTER(C.c_double)
+    lib.rfdd_last_error.restype = C.c_char_p
+    lib.rfdd_status_string.restype = C.c_char_p
+    lib.rfdd_status_string.argtypes = [C.c_int]
+    lib.rfdd_default_options.argtypes = [C.POINTER(rfdd_options)]
+    lib.rfdd_quadrature.argtypes = [C.c_double, C.c_double, i32, i32, dp, dp]
+    lib.rfdd_setup.argtypes = [C.POINTER(rfdd_csr), C.POINTER(rfdd_csr), C.POINTER(C.c_int32), i32,
+                               C.POINTER(rfdd_options), C.POINTER(vp)]
+    lib.rfdd_layout.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i32), C.POINTER(i64)]
+    lib.rfdd_destroy.argtypes = [vp]
+    lib.rfdd_destroy.restype = None
+    lib.rfdd_solve.argtypes = [vp, C.c_double, C.c_double, i32, C.POINTER(vp)]
+    lib.rfdd_solve_async.argtypes = [vp, C.c_double, C.c_double, i32, vp, C.POINTER(vp)]
+    lib.rfdd_result_ready.argtypes = [vp]
+    lib.rfdd_result_get.argtypes = [vp, C.POINTER(i64), C.POINTER(dp), C.POINTER(dp), C.POINTER(dp), i32]
+    lib.rfdd_result_info.argtypes = [vp, C.POINTER(rfdd_info)]
+    lib.rfdd_result_pre_evals.argtypes = [vp, C.POINTER(i64), dp]
+    lib.rfdd_result_free.argtypes = [vp]
+    lib.rfdd_result_free.restype = None
+    lib.rfdd_factor.argtypes = [vp, i32, dp, dp]
+    lib.rfdd_schur_copy.argtypes = [vp, i32, dp]
+    lib.rfdd_shifted_solve.argtypes = [vp, i32, i32, i32, i64, dp, dp]
+    lib.rfdd_filter_apply.argtypes = [vp, i64, dp, dp]
+    lib.rfdd_lanczos.argtypes = [vp, i64, dp, C.POINTER(i64), dp, C.POINTER(i32)]
+    lib.rfdd_interior.argtypes = [vp, C.c_double, i64, dp, C.POINTER(i64), C.POINTER(i64)]
+    lib.rfdd_rayleigh_ritz.argtypes = [vp, i64, dp, C.POINTER(i64)]
+    lib.rfdd_memory_estimate.argtypes = [vp, i32, i64, C.POINTER(C.c_size_t)]
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, ok=(RFDD_OK,)):
+    if rc not in ok:
+        lib = load()
+        raise RfddError(rc, f"{lib.rfdd_status_string(rc).decode()}: {lib.rfdd_last_error().decode()}")
+    return rc
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def rfdd_default_options(**overrides) -> rfdd_options:
+    o = rfdd_options()
+    load().rfdd_default_options(C.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def rfdd_status_string(code: int) -> str:
+    return load().rfdd_status_string(code).decode()
+
+
+def rfdd_quadrature(alpha: float, beta: float, n_nodes: int, rule: int = RFDD_MIDPOINT):
+    z = np.zeros(2 * n_nodes)
+    w = np.zeros(2 * n_nodes)
+    _check(load().rfdd_quadrature(alpha, beta, n_nodes, rule, _dp(z), _dp(w)))
+    return z.view(np.complex128), w.view(np.complex128)
+
+
+class _Csr:
+    """Keeps the numpy arrays behind an rfdd_csr alive."""
+
+    def __init__(self, csr):
+        self.rowptr = np.ascontiguousarray(csr.rowptr, dtype=np.int64)
+        self.col = np.ascontiguousarray(csr.col, dtype=np.int32)
+        self.val = np.ascontiguousarray(csr.val, dtype=np.float64)
+        self.s = rfdd_csr(int(len(self.rowptr) - 1), self.rowptr.ctypes.data_as(C.POINTER(C.c_int64)),
+                          self.col.ctypes.data_as(C.POINTER(C.c_int32)), _dp(self.val))
+
+
+def _as_csr(x):
+    if hasattr(x, "rowptr"):
+        return x
+    import scipy.sparse as sp
+    a = sp.csr_matrix(x)
+    a.sort_indices()
+
+    class _T:
+        pass
+    t = _T()
+    t.rowptr, t.col, t.val = a.indptr, a.indices, a.data
+    return t
+
+
+class Handle:
+    """Owns an rfdd_handle* (destroyed with rfdd_destroy)."""
+
+    def __init__(self, ptr, n, opts):
+        self.ptr = C.c_void_p(ptr)
+        self.n = n
+        self.opts = opts
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and self.ptr.value and _lib is not None:
+            _lib.rfdd_destroy(self.ptr)
+            self.ptr = C.c_void_p(None)
+
+    close = __del__
+
+
+def rfdd_setup(A, M, part, p: int, opts: rfdd_options | None = None) -> Handle:
+    a, m = _Csr(_as_csr(A)), _Csr(_as_csr(M))
+    pt = np.ascontiguousarray(part, dtype=np.int32)
+    out = C.c_void_p()
+    o = opts if opts is not None else rfdd_default_options()
+    _check(load().rfdd_setup(C.byref(a.s), C.byref(m.s), pt.ctypes.data_as(C.POINTER(C.c_int32)), int(p),
+                             C.byref(o), C.byref(out)))
+    return Handle(out.value, a.s.n, o)
+
+
+def rfdd_layout(h: Handle):
+    lib = load()
+    pp, ss = C.c_int32(), C.c_int64()
+    _check(lib.rfdd_layout(h.ptr, None, None, C.byref(pp), C.byref(ss)))
+    off = np.zeros(pp.value + 1, dtype=np.int64)
+    perm = np.zeros(h.n, dtype=np.int64)
+    _check(lib.rfdd_layout(h.ptr, off.ctypes.data_as(C.POINTER(C.c_int64)),
+                           perm.ctypes.data_as(C.POINTER(C.c_int64)), None, None))
+    return off, perm, int(ss.value)
+
+
+class Result:
+    def __init__(self, ptr, status, n):
+        self.ptr = C.c_void_p(ptr)
+        self.status = status
+        self.n = n
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and self.ptr.value and _lib is not None:
+            _lib.rfdd_result_free(self.ptr)
+            self.ptr = C.c_void_p(None)
+
+
+def rfdd_solve(h: Handle, alpha: float, beta: float, n_nodes: int) -> Result:
+    out = C.c_void_p()
+    rc = load().rfdd_solve(h.ptr, alpha, beta, n_nodes, C.byref(out))
+    _check(rc, ok=(RFDD_OK, RFDD_NOT_CONVERGED))
+    return Result(out.value, rc, h.n)
+
+
+def rfdd_solve_async(h: Handle, alpha: float, beta: float, n_nodes: int, stream: int = 0) -> Result:
+    out = C.c_void_p()
+    _check(load().rfdd_solve_async(h.ptr, alpha, beta, n_nodes, C.c_void_p(stream or None), C.byref(out)))
+    return Result(out.value, RFDD_OK, h.n)
+
+
+def rfdd_result_ready(r: Result) -> int:
+    return load().rfdd_result_ready(r.ptr)
+
+
+def rfdd_result_get(r: Result, device: bool = False):
+    """Host copies (evals, evecs n x nev, resid); with device=True raw device pointers instead."""
+    lib = load()
+    nev = C.c_int64()
+    ev, ex, rs = C.POINTER(C.c_double)(), C.POINTER(C.c_double)(), C.POINTER(C.c_double)()
+    _check(lib.rfdd_result_get(r.ptr, C.byref(nev), C.byref(ev), C.byref(ex), C.byref(rs), 1 if device else 0))
+    k = nev.value
+    if device:
+        addr = lambda p: C.cast(p, C.c_void_p).value
+        return k, addr(ev), addr(ex), addr(rs)
+    evals = np.ctypeslib.as_array(ev, shape=(k,)).copy() if k else np.zeros(0)
+    resid = np.ctypeslib.as_array(rs, shape=(k,)).copy() if k else np.zeros(0)
+    evecs = (np.ctypeslib.as_array(ex, shape=(r.n * k,)).copy().reshape(r.n, k) if k
+             else np.zeros((r.n, 0)))
+    return evals, evecs, resid
+
+
+def rfdd_result_info(r: Result) -> dict:
+    inf = rfdd_info()
+    _check(load().rfdd_result_info(r.ptr, C.byref(inf)))
+    return inf.as_dict()
+
+
+def rfdd_result_pre_evals(r: Result) -> np.ndarray:
+    lib = load()
+    cnt = C.c_int64()
+    _check(lib.rfdd_result_pre_evals(r.ptr, C.byref(cnt), None))
+    v = np.zeros(cnt.value)
+    _check(lib.rfdd_result_pre_evals(r.ptr, C.byref(cnt), _dp(v)))
+    return v
+
+
+def rfdd_factor(h: Handle, z: np.ndarray, w: np.ndarray):
+    z = np.ascontiguousarray(z, dtype=np.complex128)
+    w = np.ascontiguousarray(w, dtype=np.complex128)
+    _check(load().rfdd_factor(h.ptr, len(z), _dp(z.view(np.float64)), _dp(w.view(np.float64))))
+
+
+def rfdd_schur_copy(h: Handle, node: int) -> np.ndarray:
+    _, _, s = rfdd_layout(h)
+    out = np.zeros((s, s), dtype=np.complex128)
+    _check(load().rfdd_schur_copy(h.ptr, node, _dp(out.view(np.float64))))
+    return out
+
+
+def rfdd_shifted_solve(h: Handle, node: int, which: int, j: int, R: np.ndarray) -> np.ndarray:
+    R = np.ascontiguousarray(R, dtype=np.complex128)
+    if R.ndim == 1:
+        R = R[:, None]
+    X = np.zeros_like(R)
+    _check(load().rfdd_shifted_solve(h.ptr, node, which, j, R.shape[1], _dp(R.view(np.float64)),
+                                     _dp(X.view(np.float64))))
+    return X
+
+
+def rfdd_filter_apply(h: Handle, X: np.ndarray) -> np.ndarray:
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    if X.ndim == 1:
+        X = X[:, None]
+    W = np.zeros_like(X)
+    _check(load().rfdd_filter_apply(h.ptr, X.shape[1], _dp(X), _dp(W)))
+    return W
+
+
+def rfdd_lanczos(h: Handle, cap: int | None = None):
+    lib = load()
+    _, _, s = rfdd_layout(h)
+    cap = cap or s
+    Q = np.zeros((s, cap))
+    tr = np.zeros(cap)
+    mu, ns = C.c_int64(), C.c_int32()
+    _check(lib.rfdd_lanczos(h.ptr, cap, _dp(Q), C.byref(mu), _dp(tr), C.byref(ns)))
+    return Q[:, :mu.value].copy(), tr[:ns.value].copy()
+
+
+def rfdd_interior(h: Handle, sigma: float = float("nan"), want_Z: bool = True):
+    lib = load()
+    k, kap = C.c_int64(), C.c_int64()
+    _check(lib.rfdd_interior(h.ptr, sigma, 0, None, C.byref(k), C.byref(kap)))
+    if not want_Z:
+        return None, k.value, kap.value
+    # the basis was built on the device by the call above; fetch it by a second call
+    Z = np.zeros((h.n, k.value))
+    _check(lib.rfdd_interior(h.ptr, sigma, k.value, _dp(Z), C.byref(k), C.byref(kap)))
+    return Z, k.value, kap.value
+
+
+def rfdd_rayleigh_ritz(h: Handle) -> np.ndarray:
+    lib = load()
+    k = C.c_int64()
+    _check(lib.rfdd_rayleigh_ritz(h.ptr, 0, None, C.byref(k)))
+    th = np.zeros(k.value)
+    _check(lib.rfdd_rayleigh_ritz(h.ptr, k.value, _dp(th), C.byref(k)))
+    return th
+
+
+def rfdd_memory_estimate(h: Handle, n_nodes: int, nev_guess: int) -> int:
+    b = C.c_size_t()
+    _check(load().rfdd_memory_estimate(h.ptr, n_nodes, nev_guess, C.byref(b)))
+    return int(b.value)
+
+
+def solve(A, M, part, p, alpha, beta, n_nodes, **opts):
+    """Convenience: setup + solve + host results (evals, evecs in original order, resid, info)."""
+    h = rfdd_setup(A, M, part, p, rfdd_default_options(**opts))
+    r = rfdd_solve(h, alpha, beta, n_nodes)
+    ev, X, rs = rfdd_result_get(r)
+    return ev, X, rs, rfdd_result_info(r)

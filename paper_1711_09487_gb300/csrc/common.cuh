@@ -1,0 +1,137 @@
+// Shared device/host helpers for the RF-DDES GB300 library: complex arithmetic, error
+// handling, batched-launch descriptors.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+#include <stdexcept>
+
+#include "../../include/rfdd.h"
+
+namespace rfdd {
+
+// ------------------------------------------------------------------------------------
+// Errors: every library failure is a C++ exception carrying an rfdd status code; the C-ABI
+// layer converts it to the return value and records the message for rfdd_last_error().
+// ------------------------------------------------------------------------------------
+struct Error : public std::runtime_error {
+  int code;
+  Error(int c, const std::string &m) : std::runtime_error(m), code(c) {}
+};
+
+#define RFDD_CUDA(call)                                                                    \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      throw ::rfdd::Error(RFDD_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_) + \
+                                          " (" + __FILE__ + ":" + std::to_string(__LINE__) + ")"); \
+  } while (0)
+
+#define RFDD_CHECK_LAUNCH() RFDD_CUDA(cudaGetLastError())
+
+#define RFDD_REQUIRE(cond, code, msg)                 \
+  do {                                                \
+    if (!(cond)) throw ::rfdd::Error((code), (msg));  \
+  } while (0)
+
+// ------------------------------------------------------------------------------------
+// Complex numbers (interleaved re, im), usable on host and device.
+// ------------------------------------------------------------------------------------
+template <typename R>
+struct cx {
+  R re, im;
+  __host__ __device__ cx() : re(0), im(0) {}
+  __host__ __device__ cx(R r) : re(r), im(0) {}
+  __host__ __device__ cx(R r, R i) : re(r), im(i) {}
+};
+
+template <typename R> __host__ __device__ inline cx<R> operator+(cx<R> a, cx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename R> __host__ __device__ inline cx<R> operator-(cx<R> a, cx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename R> __host__ __device__ inline cx<R> operator-(cx<R> a) { return {-a.re, -a.im}; }
+template <typename R> __host__ __device__ inline cx<R> operator*(cx<R> a, cx<R> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename R> __host__ __device__ inline cx<R> operator*(R s, cx<R> a) { return {s * a.re, s * a.im}; }
+
+// Scalar traits so that the dense kernels are written once for float, double, cx<float>,
+// cx<double>.
+template <typename T> struct ST;
+template <> struct ST<float> {
+  using real = float;
+  static constexpr bool is_complex = false;
+  __host__ __device__ static float zero() { return 0.f; }
+  __host__ __device__ static float one() { return 1.f; }
+  __host__ __device__ static float abs1(float a) { return fabsf(a); }
+  __host__ __device__ static float fma(float a, float b, float c) { return fmaf(a, b, c); }   // c + a*b
+  __host__ __device__ static float fms(float a, float b, float c) { return fmaf(-a, b, c); }  // c - a*b
+  __host__ __device__ static float div(float a, float b) { return a / b; }
+  __host__ __device__ static bool finite(float a) { return isfinite(a); }
+  __host__ __device__ static float from_re(double a) { return (float)a; }
+};
+template <> struct ST<double> {
+  using real = double;
+  static constexpr bool is_complex = false;
+  __host__ __device__ static double zero() { return 0.0; }
+  __host__ __device__ static double one() { return 1.0; }
+  __host__ __device__ static double abs1(double a) { return fabs(a); }
+  __host__ __device__ static double fma(double a, double b, double c) { return ::fma(a, b, c); }
+  __host__ __device__ static double fms(double a, double b, double c) { return ::fma(-a, b, c); }
+  __host__ __device__ static double div(double a, double b) { return a / b; }
+  __host__ __device__ static bool finite(double a) { return isfinite(a); }
+  __host__ __device__ static double from_re(double a) { return a; }
+};
+template <typename R> struct STC {
+  using T = cx<R>;
+  using real = R;
+  static constexpr bool is_complex = true;
+  __host__ __device__ static T zero() { return T(0, 0); }
+  __host__ __device__ static T one() { return T(1, 0); }
+  // LAPACK's cabs1 convention for pivot search: |re| + |im|
+  __host__ __device__ static R abs1(T a) { return (a.re < 0 ? -a.re : a.re) + (a.im < 0 ? -a.im : a.im); }
+  __host__ __device__ static T fma(T a, T b, T c) {  // c + a*b
+    T r;
+    r.re = c.re + a.re * b.re - a.im * b.im;
+    r.im = c.im + a.re * b.im + a.im * b.re;
+    return r;
+  }
+  __host__ __device__ static T fms(T a, T b, T c) {  // c - a*b
+    T r;
+    r.re = c.re - a.re * b.re + a.im * b.im;
+    r.im = c.im - a.re * b.im - a.im * b.re;
+    return r;
+  }
+  __host__ __device__ static T div(T a, T b) {
+    // Smith's algorithm for complex division (avoids overflow of |b|^2)
+    R ar = b.re < 0 ? -b.re : b.re, ai = b.im < 0 ? -b.im : b.im;
+    if (ar >= ai) {
+      R r = b.im / b.re, den = b.re + b.im * r;
+      return T((a.re + a.im * r) / den, (a.im - a.re * r) / den);
+    } else {
+      R r = b.re / b.im, den = b.re * r + b.im;
+      return T((a.re * r + a.im) / den, (a.im * r - a.re) / den);
+    }
+  }
+  __host__ __device__ static bool finite(T a) { return isfinite(a.re) && isfinite(a.im); }
+  __host__ __device__ static T from_re(double a) { return T((R)a, (R)0); }
+};
+template <> struct ST<cx<float>> : STC<float> {};
+template <> struct ST<cx<double>> : STC<double> {};
+
+// ------------------------------------------------------------------------------------
+// Device status flags (one int per solve): kernels record failures here instead of trapping.
+// ------------------------------------------------------------------------------------
+enum DevStatus : int {
+  DS_OK = 0,
+  DS_ZERO_PIVOT = 1,
+  DS_NONFINITE = 2,
+  DS_BAD_SIZE = 4,
+  DS_WAIT_TIMEOUT = 8,
+};
+
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+}  // namespace rfdd

@@ -1,0 +1,756 @@
+// Batched dense kernels: SIMT GEMM, blocked LU with tournament (CALU-style) pivoting on
+// bordered matrices, triangular solves.  The paper factors B_zeta and S_zeta with sparse
+// direct solvers (PARDISO/MUMPS, Section 6); here every shifted block is dense and all
+// (subdomain, node) pairs are factored in one batch per step.
+#include "dense.cuh"
+
+#include <algorithm>
+
+namespace rfdd {
+
+// ======================================================================================
+// GEMM (CUDA cores).  64x64 output tile per CTA, 16-deep K slices staged in shared memory,
+// 4x4 outputs per thread.
+// ======================================================================================
+template <typename T>
+struct GemmBatchP {
+  GemmItem<T> it[MAXB];
+};
+
+template <typename T, bool TA, bool TB>
+__global__ void __launch_bounds__(256) gemm_simt_kernel(GemmBatchP<T> batch, typename ST<T>::real alpha,
+                                                        typename ST<T>::real beta) {
+  using S = ST<T>;
+  const GemmItem<T> g = batch.it[blockIdx.z];
+  const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+  if (i0 >= g.m || j0 >= g.n) return;
+  __shared__ T As[16][65];
+  __shared__ T Bs[16][65];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  T acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = S::zero();
+  for (int k0 = 0; k0 < g.k; k0 += 16) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + q * 256;
+      int ii, kk;
+      if (!TA) { kk = e & 15; ii = e >> 4; } else { ii = e & 63; kk = e >> 6; }
+      const int gi = i0 + ii, gk = k0 + kk;
+      T v = S::zero();
+      if (gi < g.m && gk < g.k) v = TA ? g.A[(int64_t)gk * g.lda + gi] : g.A[(int64_t)gi * g.lda + gk];
+      As[kk][ii] = v;
+      int jj, kb;
+      if (!TB) { jj = e & 63; kb = e >> 6; } else { kb = e & 15; jj = e >> 4; }
+      const int gj = j0 + jj, gkb = k0 + kb;
+      T u = S::zero();
+      if (gj < g.n && gkb < g.k) u = TB ? g.B[(int64_t)gj * g.ldb + gkb] : g.B[(int64_t)gkb * g.ldb + gj];
+      Bs[kb][jj] = u;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      T a[4], b[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + 16 * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = S::fma(a[r], b[c], acc[r][c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int i = i0 + ty + 16 * r;
+    if (i >= g.m) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j = j0 + tx + 16 * c;
+      if (j >= g.n) continue;
+      T *p = g.C + (int64_t)i * g.ldc + j;
+      T v = alpha * acc[r][c];
+      if (beta != 0) v = v + beta * (*p);
+      *p = v;
+    }
+  }
+}
+
+template <typename T>
+void gemm_batched(cudaStream_t st, const std::vector<GemmItem<T>> &items, bool ta, bool tb,
+                  double alpha, double beta) {
+  using R = typename ST<T>::real;
+  std::vector<GemmItem<T>> live;
+  for (auto &g : items)
+    if (g.m > 0 && g.n > 0) live.push_back(g);
+  for (size_t s = 0; s < live.size(); s += MAXB) {
+    GemmBatchP<T> b;
+    memset(&b, 0, sizeof(b));
+    int cnt = (int)std::min<size_t>(MAXB, live.size() - s), mm = 0, nn = 0;
+    for (int i = 0; i < cnt; ++i) {
+      b.it[i] = live[s + i];
+      mm = std::max(mm, b.it[i].m);
+      nn = std::max(nn, b.it[i].n);
+    }
+    dim3 grid(ceil_div(nn, 64), ceil_div(mm, 64), cnt);
+    RFDD_REQUIRE(grid.y <= 65535, RFDD_EINVAL, "gemm: too many row tiles");
+    if (!ta && !tb) gemm_simt_kernel<T, false, false><<<grid, 256, 0, st>>>(b, (R)alpha, (R)beta);
+    else if (ta && !tb) gemm_simt_kernel<T, true, false><<<grid, 256, 0, st>>>(b, (R)alpha, (R)beta);
+    else if (!ta && tb) gemm_simt_kernel<T, false, true><<<grid, 256, 0, st>>>(b, (R)alpha, (R)beta);
+    else gemm_simt_kernel<T, true, true><<<grid, 256, 0, st>>>(b, (R)alpha, (R)beta);
+    RFDD_CHECK_LAUNCH();
+  }
+}
+
+// ======================================================================================
+// LU with tournament pivoting.
+// One inner step factors the panel columns [k0, k0+w) of every matrix:
+//  (1) tournament: each CTA runs partial pivoting (|re|+|im|, ties to the lower row index)
+//      on a chunk of R candidate rows held in shared memory and keeps the w pivot rows it
+//      chose; chosen sets are merged G at a time until one set of w rows remains;
+//  (2) the w interchanges that bring the winners to rows k0.. are applied to whole rows;
+//  (3) the winners' w x w block is factored without pivoting (it reproduces the final round
+//      of the tournament) and L21 = A21 U11^{-1} is formed for all rows below, border
+//      rows included;
+//  (4) U12 = L11^{-1} A12 for the columns of the current outer strip;
+//  (5) the strip's trailing columns get A22 -= L21 U12.
+// After an outer strip of width nbo is done, its U12 over all trailing columns is solved and
+// the whole trailing matrix is updated with one GEMM of depth nbo.
+// ======================================================================================
+template <typename T>
+struct LuBatchP {
+  LuItem<T> it[MAXB];
+};
+
+constexpr int TOURN_G = 8;   // candidate sets merged per CTA
+
+template <typename T>
+struct TournRows {           // rows per tournament CTA (R = G * NB), sized for <= 128 KB smem
+  static constexpr int R = TOURN_G * LU_NB;
+};
+
+__device__ inline int strip_end(int K0, int nbo, int dp) { return min(K0 + nbo, dp); }
+
+// number of candidate sets at a given tournament level for a matrix
+__device__ inline int tourn_sets(int rows, int R, int level) {
+  int n = (rows + R - 1) / R;
+  for (int l = 0; l < level; ++l) n = (n + TOURN_G - 1) / TOURN_G;
+  return n;
+}
+
+template <typename T>
+__device__ inline void warp_argmax(typename ST<T>::real &v, int &row, int &idx) {
+  for (int o = 16; o > 0; o >>= 1) {
+    auto v2 = __shfl_down_sync(0xffffffffu, v, o);
+    int r2 = __shfl_down_sync(0xffffffffu, row, o);
+    int i2 = __shfl_down_sync(0xffffffffu, idx, o);
+    if (v2 > v || (v2 == v && r2 < row)) { v = v2; row = r2; idx = i2; }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) lu_tourn_kernel(LuBatchP<T> lb, int K0, int nbo, int k0, int level,
+                                                       const int *__restrict__ cin, int *__restrict__ cout,
+                                                       int cand_stride) {
+  using S = ST<T>;
+  using Rl = typename S::real;
+  constexpr int NB = LU_NB;
+  constexpr int R = TournRows<T>::R;
+  const LuItem<T> it = lb.it[blockIdx.y];
+  const int wend = strip_end(K0, nbo, it.dp);
+  const int w = min(NB, wend - k0);
+  if (w <= 0) return;
+  const int rows_total = it.dp - k0;
+  const int set = blockIdx.x;
+  if (set >= tourn_sets(rows_total, R, level)) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *Sm = reinterpret_cast<T *>(smem_raw);          // R x NB
+  int *rid = reinterpret_cast<int *>(Sm + R * NB);  // R
+  __shared__ int nr_s;
+  __shared__ Rl red_v[8];
+  __shared__ int red_r[8], red_i[8];
+  __shared__ int piv_s;
+  const int tid = threadIdx.x;
+  if (level == 0) {
+    const int r0 = k0 + set * R;
+    const int nr = min(R, it.dp - r0);
+    for (int r = tid; r < nr; r += blockDim.x) rid[r] = r0 + r;
+    if (tid == 0) nr_s = nr;
+  } else {
+    const int *c = cin + (int64_t)blockIdx.y * cand_stride + (int64_t)set * TOURN_G * NB;
+    const int nsets_in = tourn_sets(rows_total, R, level - 1);
+    const int nin = min(TOURN_G, nsets_in - set * TOURN_G) * NB;
+    if (tid == 0) {
+      int nr = 0;
+      for (int e = 0; e < nin; ++e)
+        if (c[e] >= 0) rid[nr++] = c[e];
+      nr_s = nr;
+    }
+  }
+  __syncthreads();
+  const int nr = nr_s;
+  for (int e = tid; e < nr * w; e += blockDim.x) {
+    const int r = e / w, c = e - r * w;
+    Sm[r * NB + c] = it.A[(int64_t)rid[r] * it.ld + k0 + c];
+  }
+  __syncthreads();
+  const int steps = min(nr, w);
+  for (int t = 0; t < steps; ++t) {
+    Rl bv = (Rl)-1;
+    int br = 0x7fffffff, bi = -1;
+    for (int r = t + tid; r < nr; r += blockDim.x) {
+      const Rl v = S::abs1(Sm[r * NB + t]);
+      if (v > bv || (v == bv && rid[r] < br)) { bv = v; br = rid[r]; bi = r; }
+    }
+    warp_argmax<T>(bv, br, bi);
+    if ((tid & 31) == 0) { red_v[tid >> 5] = bv; red_r[tid >> 5] = br; red_i[tid >> 5] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      Rl v = red_v[0];
+      int r = red_r[0], i = red_i[0];
+      for (int q = 1; q < (int)(blockDim.x >> 5); ++q)
+        if (red_v[q] > v || (red_v[q] == v && red_r[q] < r)) { v = red_v[q]; r = red_r[q]; i = red_i[q]; }
+      piv_s = i;
+    }
+    __syncthreads();
+    const int pi = piv_s;
+    if (pi != t) {
+      for (int c = tid; c < w; c += blockDim.x) {
+        T a = Sm[t * NB + c];
+        Sm[t * NB + c] = Sm[pi * NB + c];
+        Sm[pi * NB + c] = a;
+      }
+      if (tid == 0) { int a = rid[t]; rid[t] = rid[pi]; rid[pi] = a; }
+    }
+    __syncthreads();
+    const T pv = Sm[t * NB + t];
+    const bool nz = S::abs1(pv) != (Rl)0;
+    if (nz)
+      for (int r = t + 1 + tid; r < nr; r += blockDim.x) Sm[r * NB + t] = S::div(Sm[r * NB + t], pv);
+    __syncthreads();
+    const int wc = w - t - 1;
+    if (nz && wc > 0)
+      for (int e = tid; e < (nr - t - 1) * wc; e += blockDim.x) {
+        const int r = t + 1 + e / wc, c = t + 1 + e % wc;
+        Sm[r * NB + c] = S::fms(Sm[r * NB + t], Sm[t * NB + c], Sm[r * NB + c]);
+      }
+    __syncthreads();
+  }
+  int *o = cout + (int64_t)blockIdx.y * cand_stride + (int64_t)set * NB;
+  for (int t = tid; t < NB; t += blockDim.x) o[t] = (t < steps) ? rid[t] : -1;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) lu_swap_kernel(LuBatchP<T> lb, int K0, int nbo, int k0,
+                                                      const int *__restrict__ cfinal, int cand_stride) {
+  constexpr int NB = LU_NB;
+  const LuItem<T> it = lb.it[blockIdx.y];
+  const int wend = strip_end(K0, nbo, it.dp);
+  const int w = min(NB, wend - k0);
+  if (w <= 0) return;
+  __shared__ int ipiv[NB];
+  if (threadIdx.x == 0) {
+    const int *pr = cfinal + (int64_t)blockIdx.y * cand_stride;
+    int key[2 * NB], val[2 * NB];
+    int nk = 0;
+    for (int t = 0; t < w; ++t) {
+      const int target = pr[t];
+      int q = target;
+      for (int i = 0; i < nk; ++i)
+        if (val[i] == target) { q = key[i]; break; }
+      ipiv[t] = q;
+      const int pa = k0 + t;
+      int ra = pa, rb = q;
+      for (int i = 0; i < nk; ++i) {
+        if (key[i] == pa) ra = val[i];
+        if (key[i] == q) rb = val[i];
+      }
+      bool fa = false, fb = false;
+      for (int i = 0; i < nk; ++i) {
+        if (key[i] == pa) { val[i] = rb; fa = true; }
+        else if (key[i] == q) { val[i] = ra; fb = true; }
+      }
+      if (!fa) { key[nk] = pa; val[nk] = rb; ++nk; }
+      if (!fb && q != pa) { key[nk] = q; val[nk] = ra; ++nk; }
+    }
+    if (blockIdx.x == 0)
+      for (int t = 0; t < w; ++t) it.piv[k0 + t] = ipiv[t];
+  }
+  __syncthreads();
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= it.D) return;
+  for (int t = 0; t < w; ++t) {
+    const int q = ipiv[t];
+    if (q != k0 + t) {
+      T *a = it.A + (int64_t)(k0 + t) * it.ld + c;
+      T *b = it.A + (int64_t)q * it.ld + c;
+      T x = *a;
+      *a = *b;
+      *b = x;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) lu_finish_kernel(LuBatchP<T> lb, int K0, int nbo, int k0, T *top,
+                                                        int *status) {
+  using S = ST<T>;
+  using Rl = typename S::real;
+  constexpr int NB = LU_NB;
+  const LuItem<T> it = lb.it[blockIdx.y];
+  const int wend = strip_end(K0, nbo, it.dp);
+  const int w = min(NB, wend - k0);
+  if (w <= 0) return;
+  __shared__ T U[NB][NB + 1];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < w * w; e += blockDim.x) {
+    const int r = e / w, c = e % w;
+    U[r][c] = it.A[(int64_t)(k0 + r) * it.ld + k0 + c];
+  }
+  __syncthreads();
+  for (int t = 0; t < w; ++t) {
+    const T pv = U[t][t];
+    const bool nz = S::abs1(pv) != (Rl)0;
+    if (nz)
+      for (int r = t + 1 + tid; r < w; r += blockDim.x) U[r][t] = S::div(U[r][t], pv);
+    __syncthreads();
+    const int wc = w - t - 1;
+    if (nz && wc > 0)
+      for (int e = tid; e < wc * wc; e += blockDim.x) {
+        const int r = t + 1 + e / wc, c = t + 1 + e % wc;
+        U[r][c] = S::fms(U[r][t], U[t][c], U[r][c]);
+      }
+    __syncthreads();
+  }
+  if (blockIdx.x == 0) {
+    T *tp = top + (int64_t)blockIdx.y * NB * NB;
+    for (int e = tid; e < w * w; e += blockDim.x) tp[e] = U[e / w][e % w];
+    if (tid < w) {
+      const T d = U[tid][tid];
+      if (!S::finite(d)) atomicOr(status, DS_NONFINITE);
+      else if (S::abs1(d) == (Rl)0) atomicOr(status, DS_ZERO_PIVOT);
+    }
+  }
+  const int r = k0 + w + blockIdx.x * blockDim.x + tid;
+  if (r >= it.D) return;
+  T *row = it.A + (int64_t)r * it.ld + k0;
+  T x[NB];
+#pragma unroll
+  for (int c = 0; c < NB; ++c)
+    if (c < w) x[c] = row[c];
+#pragma unroll
+  for (int c = 0; c < NB; ++c) {
+    if (c < w) {
+      T v = x[c];
+#pragma unroll
+      for (int t = 0; t < NB; ++t)
+        if (t < c) v = S::fms(x[t], U[t][c], v);
+      x[c] = S::abs1(U[c][c]) != (Rl)0 ? S::div(v, U[c][c]) : v;
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NB; ++c)
+    if (c < w) row[c] = x[c];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) lu_u12_kernel(LuBatchP<T> lb, int K0, int nbo, int k0,
+                                                     const T *__restrict__ top) {
+  using S = ST<T>;
+  constexpr int NB = LU_NB;
+  const LuItem<T> it = lb.it[blockIdx.y];
+  const int wend = strip_end(K0, nbo, it.dp);
+  const int w = min(NB, wend - k0);
+  if (w <= 0) return;
+  __shared__ T L[NB][NB + 1];
+  const T *tp = top + (int64_t)blockIdx.y * NB * NB;
+  for (int e = threadIdx.x; e < w * w; e += blockDim.x) L[e / w][e % w] = tp[e];
+  __syncthreads();
+  if (blockIdx.x == 0)
+    for (int e = threadIdx.x; e < w * w; e += blockDim.x)
+      it.A[(int64_t)(k0 + e / w) * it.ld + k0 + e % w] = L[e / w][e % w];
+  const int c = k0 + w + blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= wend) return;
+  T x[NB];
+#pragma unroll
+  for (int t = 0; t < NB; ++t)
+    if (t < w) x[t] = it.A[(int64_t)(k0 + t) * it.ld + c];
+#pragma unroll
+  for (int t = 0; t < NB; ++t) {
+    if (t < w) {
+      T v = x[t];
+#pragma unroll
+      for (int q = 0; q < NB; ++q)
+        if (q < t) v = S::fms(L[t][q], x[q], v);
+      x[t] = v;
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < NB; ++t)
+    if (t < w) it.A[(int64_t)(k0 + t) * it.ld + c] = x[t];
+}
+
+// ======================================================================================
+// Triangular solves on 32-row diagonal blocks (thread per right-hand-side column).
+// ======================================================================================
+template <typename T>
+struct TriItem {
+  const T *L;   // top-left of the w x w diagonal block
+  int ldl;
+  T *X;         // first row of the w-row slab of right-hand sides
+  int ldx;
+  int w, ncols;
+};
+template <typename T>
+struct TriBatchP {
+  TriItem<T> it[MAXB];
+};
+
+template <typename T, bool UPPER>
+__global__ void __launch_bounds__(256) trsm_diag_kernel(TriBatchP<T> tb) {
+  using S = ST<T>;
+  using Rl = typename S::real;
+  constexpr int NB = LU_NB;
+  const TriItem<T> it = tb.it[blockIdx.y];
+  __shared__ T L[NB][NB + 1];
+  const int w = it.w;
+  for (int e = threadIdx.x; e < w * w; e += blockDim.x) L[e / w][e % w] = it.L[(int64_t)(e / w) * it.ldl + e % w];
+  __syncthreads();
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= it.ncols) return;
+  T x[NB];
+#pragma unroll
+  for (int t = 0; t < NB; ++t)
+    if (t < w) x[t] = it.X[(int64_t)t * it.ldx + c];
+  if (!UPPER) {
+#pragma unroll
+    for (int t = 0; t < NB; ++t) {
+      if (t < w) {
+        T v = x[t];
+#pragma unroll
+        for (int q = 0; q < NB; ++q)
+          if (q < t) v = S::fms(L[t][q], x[q], v);
+        x[t] = v;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int t = NB - 1; t >= 0; --t) {
+      if (t < w) {
+        T v = x[t];
+#pragma unroll
+        for (int q = 0; q < NB; ++q)
+          if (q > t && q < w) v = S::fms(L[t][q], x[q], v);
+        x[t] = S::abs1(L[t][t]) != (Rl)0 ? S::div(v, L[t][t]) : v;
+      }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < NB; ++t)
+    if (t < w) it.X[(int64_t)t * it.ldx + c] = x[t];
+}
+
+template <typename T, bool UPPER>
+static void launch_trsm_diag(cudaStream_t st, const std::vector<TriItem<T>> &items) {
+  for (size_t s = 0; s < items.size(); s += MAXB) {
+    TriBatchP<T> b;
+    memset(&b, 0, sizeof(b));
+    int cnt = (int)std::min<size_t>(MAXB, items.size() - s), nc = 1;
+    for (int i = 0; i < cnt; ++i) { b.it[i] = items[s + i]; nc = std::max(nc, b.it[i].ncols); }
+    trsm_diag_kernel<T, UPPER><<<dim3(ceil_div(nc, 256), cnt), 256, 0, st>>>(b);
+    RFDD_CHECK_LAUNCH();
+  }
+}
+
+// ======================================================================================
+// Pivot application to right-hand sides (row interchanges in order, thread per column).
+// ======================================================================================
+template <typename T>
+struct PivItem {
+  const int *piv;
+  int npiv;
+  T *X;
+  int ldx, ncols;
+};
+template <typename T>
+struct PivBatchP {
+  PivItem<T> it[MAXB];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) apply_piv_kernel(PivBatchP<T> pb) {
+  const PivItem<T> it = pb.it[blockIdx.y];
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= it.ncols) return;
+  for (int t = 0; t < it.npiv; ++t) {
+    const int q = __ldg(it.piv + t);
+    if (q != t) {
+      T *a = it.X + (int64_t)t * it.ldx + c;
+      T *b = it.X + (int64_t)q * it.ldx + c;
+      T x = *a;
+      *a = *b;
+      *b = x;
+    }
+  }
+}
+
+// ======================================================================================
+// Host drivers
+// ======================================================================================
+template <typename T>
+static void launch_lu_common(cudaStream_t st, const std::vector<LuItem<T>> &items, int K0, int nbo,
+                             int k0, LuWork &wk, int *status) {
+  constexpr int NB = LU_NB;
+  constexpr int R = TournRows<T>::R;
+  const size_t smem = (size_t)R * NB * sizeof(T) + (size_t)R * sizeof(int);
+  for (size_t s = 0; s < items.size(); s += MAXB) {
+    LuBatchP<T> b;
+    memset(&b, 0, sizeof(b));
+    const int cnt = (int)std::min<size_t>(MAXB, items.size() - s);
+    int rows_max = 0, dmax = 0, wmax = 0;
+    for (int i = 0; i < cnt; ++i) {
+      b.it[i] = items[s + i];
+      rows_max = std::max(rows_max, b.it[i].dp - k0);
+      dmax = std::max(dmax, b.it[i].D);
+      wmax = std::max(wmax, std::min(NB, std::min(K0 + nbo, b.it[i].dp) - k0));
+    }
+    if (rows_max <= 0 || wmax <= 0) continue;
+    const int stride = (int)(wk.cand_ints / (2 * MAXB));
+    int *ca = wk.cand, *cb = wk.cand + (size_t)MAXB * stride;
+    // (1) tournament
+    int nsets = ceil_div(rows_max, R);
+    lu_tourn_kernel<T><<<dim3(nsets, cnt), 256, smem, st>>>(b, K0, nbo, k0, 0, nullptr, ca, stride);
+    RFDD_CHECK_LAUNCH();
+    int level = 0;
+    while (nsets > 1) {
+      ++level;
+      nsets = ceil_div(nsets, TOURN_G);
+      lu_tourn_kernel<T><<<dim3(nsets, cnt), 256, smem, st>>>(b, K0, nbo, k0, level, ca, cb, stride);
+      RFDD_CHECK_LAUNCH();
+      std::swap(ca, cb);
+    }
+    // (2) interchanges on whole rows
+    lu_swap_kernel<T><<<dim3(ceil_div(dmax, 256), cnt), 256, 0, st>>>(b, K0, nbo, k0, ca, stride);
+    RFDD_CHECK_LAUNCH();
+    // (3) U11/L11 and L21
+    lu_finish_kernel<T><<<dim3(std::max(1, ceil_div(dmax - k0 - 1, 256)), cnt), 256, 0, st>>>(
+        b, K0, nbo, k0, (T *)wk.top, status);
+    RFDD_CHECK_LAUNCH();
+    // (4) U12 inside the strip (also stores L11/U11 into the matrix)
+    lu_u12_kernel<T><<<dim3(std::max(1, ceil_div(nbo, 256)), cnt), 256, 0, st>>>(b, K0, nbo, k0,
+                                                                                (const T *)wk.top);
+    RFDD_CHECK_LAUNCH();
+  }
+  // (5) strip-internal trailing update
+  std::vector<GemmItem<T>> g;
+  for (auto &it : items) {
+    const int wend = std::min(K0 + nbo, it.dp);
+    const int w = std::min(NB, wend - k0);
+    if (w <= 0) continue;
+    GemmItem<T> x;
+    x.A = it.A + (int64_t)(k0 + w) * it.ld + k0;
+    x.B = it.A + (int64_t)k0 * it.ld + k0 + w;
+    x.C = it.A + (int64_t)(k0 + w) * it.ld + k0 + w;
+    x.m = it.D - k0 - w;
+    x.n = wend - k0 - w;
+    x.k = w;
+    x.lda = x.ldb = x.ldc = it.ld;
+    g.push_back(x);
+  }
+  gemm_batched<T>(st, g, false, false, -1.0, 1.0);
+}
+
+template <typename T>
+void lu_batched(cudaStream_t st, const std::vector<LuItem<T>> &items, int nbo, int *dev_status) {
+  constexpr int NB = LU_NB;
+  constexpr int R = TournRows<T>::R;
+  RFDD_REQUIRE(nbo % NB == 0 && nbo > 0, RFDD_EINVAL, "lu: outer block must be a multiple of 32");
+  if (items.empty()) return;
+  int dpmax = 0;
+  for (auto &it : items) {
+    RFDD_REQUIRE(it.dp >= 0 && it.D >= it.dp && it.ld >= it.D, RFDD_EINVAL, "lu: bad sizes");
+    dpmax = std::max(dpmax, it.dp);
+  }
+  if (dpmax == 0) return;
+  static bool attr_set = false;
+  const size_t smem = (size_t)R * NB * sizeof(T) + (size_t)R * sizeof(int);
+  if (!attr_set) {
+    RFDD_CUDA(cudaFuncSetAttribute(lu_tourn_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr_set = true;
+  }
+  LuWork wk;
+  const int stride = (ceil_div(dpmax, R) + 1) * NB;
+  wk.cand_ints = (size_t)2 * MAXB * stride;
+  wk.top_bytes = (size_t)MAXB * NB * NB * sizeof(T);
+  RFDD_CUDA(cudaMallocAsync((void **)&wk.cand, wk.cand_ints * sizeof(int), st));
+  RFDD_CUDA(cudaMallocAsync(&wk.top, wk.top_bytes, st));
+  try {
+    for (int K0 = 0; K0 < dpmax; K0 += nbo) {
+      std::vector<LuItem<T>> act;
+      for (auto &it : items)
+        if (it.dp > K0) act.push_back(it);
+      for (int k0 = K0; k0 < K0 + nbo && k0 < dpmax; k0 += NB) {
+        std::vector<LuItem<T>> in;
+        for (auto &it : act)
+          if (std::min(K0 + nbo, it.dp) > k0) in.push_back(it);
+        if (!in.empty()) launch_lu_common<T>(st, in, K0, nbo, k0, wk, dev_status);
+      }
+      // outer strip: U12 over all trailing columns, then the deep trailing update
+      std::vector<SolveItem<T>> tri;
+      std::vector<GemmItem<T>> g;
+      for (auto &it : act) {
+        const int wend = std::min(K0 + nbo, it.dp);
+        const int wo = wend - K0;
+        const int nc = it.D - wend;
+        if (wo <= 0 || nc <= 0) continue;
+        SolveItem<T> s;
+        s.LU = it.A + (int64_t)K0 * it.ld + K0;
+        s.piv = nullptr;
+        s.n = wo;
+        s.ld = it.ld;
+        s.X = it.A + (int64_t)K0 * it.ld + wend;
+        s.ldx = it.ld;
+        s.ncols = nc;
+        tri.push_back(s);
+        GemmItem<T> x;
+        x.A = it.A + (int64_t)wend * it.ld + K0;
+        x.B = it.A + (int64_t)K0 * it.ld + wend;
+        x.C = it.A + (int64_t)wend * it.ld + wend;
+        x.m = it.D - wend;
+        x.n = nc;
+        x.k = wo;
+        x.lda = x.ldb = x.ldc = it.ld;
+        g.push_back(x);
+      }
+      if (nbo > NB) trsm_lower_unit<T>(st, tri, NB);
+      else trsm_lower_unit<T>(st, tri, NB);
+      gemm_batched<T>(st, g, false, false, -1.0, 1.0);
+    }
+  } catch (...) {
+    cudaFreeAsync(wk.cand, st);
+    cudaFreeAsync(wk.top, st);
+    throw;
+  }
+  RFDD_CUDA(cudaFreeAsync(wk.cand, st));
+  RFDD_CUDA(cudaFreeAsync(wk.top, st));
+}
+
+template <typename T>
+void apply_pivots(cudaStream_t st, const std::vector<SolveItem<T>> &items) {
+  for (size_t s = 0; s < items.size(); s += MAXB) {
+    PivBatchP<T> b;
+    memset(&b, 0, sizeof(b));
+    int cnt = (int)std::min<size_t>(MAXB, items.size() - s), nc = 1;
+    for (int i = 0; i < cnt; ++i) {
+      const auto &it = items[s + i];
+      b.it[i].piv = it.piv;
+      b.it[i].npiv = it.n;
+      b.it[i].X = it.X;
+      b.it[i].ldx = it.ldx;
+      b.it[i].ncols = it.ncols;
+      nc = std::max(nc, it.ncols);
+    }
+    apply_piv_kernel<T><<<dim3(ceil_div(nc, 256), cnt), 256, 0, st>>>(b);
+    RFDD_CHECK_LAUNCH();
+  }
+}
+
+// X <- L^{-1} X, L unit lower (n x n): 32-row diagonal solves and GEMM updates, two levels
+// (updates inside an nbo-row block, then one deep update of everything below it).
+template <typename T>
+void trsm_lower_unit(cudaStream_t st, const std::vector<SolveItem<T>> &items, int nbo) {
+  constexpr int NB = LU_NB;
+  int nmax = 0;
+  for (auto &it : items) nmax = std::max(nmax, it.n);
+  for (int K0 = 0; K0 < nmax; K0 += nbo) {
+    for (int k0 = K0; k0 < K0 + nbo && k0 < nmax; k0 += NB) {
+      std::vector<TriItem<T>> d;
+      std::vector<GemmItem<T>> g;
+      for (auto &it : items) {
+        const int kend = std::min(K0 + nbo, it.n);
+        if (k0 >= kend || it.ncols <= 0) continue;
+        const int w = std::min(NB, kend - k0);
+        TriItem<T> t{it.LU + (int64_t)k0 * it.ld + k0, it.ld, it.X + (int64_t)k0 * it.ldx, it.ldx, w, it.ncols};
+        d.push_back(t);
+        if (kend - k0 - w > 0) {
+          GemmItem<T> x{it.LU + (int64_t)(k0 + w) * it.ld + k0, it.X + (int64_t)k0 * it.ldx,
+                        it.X + (int64_t)(k0 + w) * it.ldx, kend - k0 - w, it.ncols, w, it.ld, it.ldx, it.ldx};
+          g.push_back(x);
+        }
+      }
+      launch_trsm_diag<T, false>(st, d);
+      gemm_batched<T>(st, g, false, false, -1.0, 1.0);
+    }
+    std::vector<GemmItem<T>> g;
+    for (auto &it : items) {
+      const int kend = std::min(K0 + nbo, it.n);
+      if (K0 >= it.n || it.n - kend <= 0 || it.ncols <= 0) continue;
+      GemmItem<T> x{it.LU + (int64_t)kend * it.ld + K0, it.X + (int64_t)K0 * it.ldx, it.X + (int64_t)kend * it.ldx,
+                    it.n - kend, it.ncols, kend - K0, it.ld, it.ldx, it.ldx};
+      g.push_back(x);
+    }
+    gemm_batched<T>(st, g, false, false, -1.0, 1.0);
+  }
+}
+
+// X <- U^{-1} X, U upper (n x n) with its diagonal.
+template <typename T>
+void trsm_upper(cudaStream_t st, const std::vector<SolveItem<T>> &items, int nbo) {
+  constexpr int NB = LU_NB;
+  int nmax = 0;
+  for (auto &it : items) nmax = std::max(nmax, it.n);
+  if (nmax == 0) return;
+  for (int K0 = ((nmax - 1) / nbo) * nbo; K0 >= 0; K0 -= nbo) {
+    for (int k0 = K0 + nbo - NB; k0 >= K0; k0 -= NB) {
+      std::vector<TriItem<T>> d;
+      std::vector<GemmItem<T>> g;
+      for (auto &it : items) {
+        if (k0 >= it.n || it.ncols <= 0) continue;
+        const int w = std::min(NB, it.n - k0);
+        TriItem<T> t{it.LU + (int64_t)k0 * it.ld + k0, it.ld, it.X + (int64_t)k0 * it.ldx, it.ldx, w, it.ncols};
+        d.push_back(t);
+        if (k0 - K0 > 0) {
+          GemmItem<T> x{it.LU + (int64_t)K0 * it.ld + k0, it.X + (int64_t)k0 * it.ldx, it.X + (int64_t)K0 * it.ldx,
+                        k0 - K0, it.ncols, w, it.ld, it.ldx, it.ldx};
+          g.push_back(x);
+        }
+      }
+      launch_trsm_diag<T, true>(st, d);
+      gemm_batched<T>(st, g, false, false, -1.0, 1.0);
+    }
+    std::vector<GemmItem<T>> g;
+    for (auto &it : items) {
+      if (K0 >= it.n || K0 == 0 || it.ncols <= 0) continue;
+      const int kend = std::min(K0 + nbo, it.n);
+      GemmItem<T> x{it.LU + K0, it.X + (int64_t)K0 * it.ldx, it.X, K0, it.ncols, kend - K0, it.ld, it.ldx, it.ldx};
+      g.push_back(x);
+    }
+    gemm_batched<T>(st, g, false, false, -1.0, 1.0);
+  }
+}
+
+template <typename T>
+void lu_solve_batched(cudaStream_t st, const std::vector<SolveItem<T>> &items, int nbo) {
+  apply_pivots<T>(st, items);
+  trsm_lower_unit<T>(st, items, nbo);
+  trsm_upper<T>(st, items, nbo);
+}
+
+#define RFDD_INST_DENSE(T)                                                                          \
+  template void gemm_batched<T>(cudaStream_t, const std::vector<GemmItem<T>> &, bool, bool, double, double); \
+  template void lu_batched<T>(cudaStream_t, const std::vector<LuItem<T>> &, int, int *);          \
+  template void lu_solve_batched<T>(cudaStream_t, const std::vector<SolveItem<T>> &, int);        \
+  template void apply_pivots<T>(cudaStream_t, const std::vector<SolveItem<T>> &);                 \
+  template void trsm_lower_unit<T>(cudaStream_t, const std::vector<SolveItem<T>> &, int);         \
+  template void trsm_upper<T>(cudaStream_t, const std::vector<SolveItem<T>> &, int);
+
+RFDD_INST_DENSE(float)
+RFDD_INST_DENSE(double)
+RFDD_INST_DENSE(cx<float>)
+RFDD_INST_DENSE(cx<double>)
+
+}  // namespace rfdd

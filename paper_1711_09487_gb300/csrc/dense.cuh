@@ -1,0 +1,67 @@
+// Batched dense kernels (host-side launchers): GEMM, blocked LU with tournament pivoting on
+// bordered matrices, LU solves.  Every routine works on a batch of independent matrices of
+// uneven sizes and is instantiated for float, double, cx<float>, cx<double>.
+#pragma once
+#include "common.cuh"
+
+namespace rfdd {
+
+constexpr int MAXB = 64;      // matrices per launch (descriptors travel as kernel parameters)
+constexpr int LU_NB = 32;     // tournament panel width (pivot columns per inner step)
+
+// C = beta*C + alpha*op(A) op(B); row-major, op(X) = X or X^T (stored transposed).
+template <typename T>
+struct GemmItem {
+  const T *A;
+  const T *B;
+  T *C;
+  int m, n, k;
+  int lda, ldb, ldc;
+};
+
+template <typename T>
+void gemm_batched(cudaStream_t st, const std::vector<GemmItem<T>> &items, bool ta, bool tb,
+                  double alpha, double beta);
+
+// One bordered matrix for LU: D x D (row-major, leading dimension ld), of which the first dp
+// rows/columns are eliminated with pivoting restricted to rows < dp.  After the factorisation
+// the trailing (D-dp) x (D-dp) block holds C~ - E^T B^{-1} E (the Schur complement of the
+// leading block).  piv: int32[dp], LAPACK-style sequence of row interchanges (row t <-> piv[t]).
+template <typename T>
+struct LuItem {
+  T *A;
+  int *piv;
+  int dp, D, ld;
+};
+
+struct LuWork {
+  int *cand = nullptr;   // candidate buffers (2 x MAXB x stride ints)
+  void *top = nullptr;   // MAXB x NB x NB scratch
+  size_t cand_ints = 0, top_bytes = 0;
+};
+
+// nbo: outer block (trailing-update depth), a multiple of LU_NB.
+template <typename T>
+void lu_batched(cudaStream_t st, const std::vector<LuItem<T>> &items, int nbo, int *dev_status);
+
+// Solve with LU factors: X <- U^{-1} L^{-1} P X for the leading dp x dp block of each item.
+template <typename T>
+struct SolveItem {
+  const T *LU;
+  const int *piv;
+  int n, ld;       // order of the factored block and its leading dimension
+  T *X;
+  int ldx, ncols;
+};
+template <typename T>
+void lu_solve_batched(cudaStream_t st, const std::vector<SolveItem<T>> &items, int nbo);
+
+// Building blocks exposed for the tests of individual steps.
+template <typename T>
+void apply_pivots(cudaStream_t st, const std::vector<SolveItem<T>> &items);
+template <typename T>
+void trsm_lower_unit(cudaStream_t st, const std::vector<SolveItem<T>> &items, int nbo);
+template <typename T>
+void trsm_upper(cudaStream_t st, const std::vector<SolveItem<T>> &items, int nbo);
+
+}  // namespace rfdd

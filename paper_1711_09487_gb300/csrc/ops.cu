@@ -1,0 +1,486 @@
+// Sparse products, block assembly, Schur scatter and elementwise kernels.
+#include "ops.cuh"
+
+namespace rfdd {
+
+namespace {
+
+template <typename T>
+struct Shift;
+template <typename R>
+struct Shift<cx<R>> {
+  __device__ static cx<R> make(double a, double m, cx<double> z) {
+    return cx<R>((R)(a - z.re * m), (R)(-z.im * m));
+  }
+};
+template <>
+struct Shift<float> {
+  __device__ static float make(double a, double m, cx<double> z) { return (float)(a - z.re * m); }
+};
+template <>
+struct Shift<double> {
+  __device__ static double make(double a, double m, cx<double> z) { return a - z.re * m; }
+};
+
+}  // namespace
+
+// --------------------------------------------------------------------------------------
+// real SpMM, warp per row, lanes over columns
+// --------------------------------------------------------------------------------------
+__global__ void spmm_f64_kernel(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                const double *__restrict__ av, const double *__restrict__ mv, int64_t r0, int64_t r1,
+                                int64_t qlo, int64_t qhi, double ca, double cm, const double *__restrict__ X,
+                                int64_t ldx, double *__restrict__ Y, int64_t ldy, int64_t b, int acc) {
+  const int64_t r = r0 + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const int lane = threadIdx.x & 31;
+  if (r >= r1) return;
+  const int64_t e0 = rp[r], e1 = rp[r + 1];
+  for (int64_t c0 = 0; c0 < b; c0 += 32) {
+    const int64_t c = c0 + lane;
+    double s = 0.0;
+    if (c < b)
+      for (int64_t e = e0; e < e1; ++e) {
+        const int64_t q = col[e];
+        if (q < qlo || q >= qhi) continue;
+        const double v = ca * av[e] + cm * mv[e];
+        s = fma(v, X[(q - qlo) * ldx + c], s);
+      }
+    if (c < b) {
+      double *y = Y + (r - r0) * ldy + c;
+      *y = acc ? *y + s : s;
+    }
+  }
+}
+
+void spmm_f64(cudaStream_t st, const DevPencil &P, int64_t r0, int64_t r1, int64_t qlo, int64_t qhi, double ca,
+              double cm, const double *X, int64_t ldx, double *Y, int64_t ldy, int64_t b, bool accumulate) {
+  if (r1 <= r0 || b <= 0) return;
+  const int64_t warps = r1 - r0;
+  spmm_f64_kernel<<<ceil_div(warps * 32, 256), 256, 0, st>>>(P.rowptr, P.col, P.a, P.m, r0, r1, qlo, qhi, ca, cm, X,
+                                                               ldx, Y, ldy, b, accumulate ? 1 : 0);
+  RFDD_CHECK_LAUNCH();
+}
+
+// --------------------------------------------------------------------------------------
+// complex coupling products (E(z) y and E(z)^T t) in the factor precision
+// --------------------------------------------------------------------------------------
+template <typename T>
+__global__ void couple_kernel(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                              const double *__restrict__ av, const double *__restrict__ mv, int64_t r0, int64_t r1,
+                              int64_t qlo, int64_t qhi, const cx<double> *__restrict__ zz, const T *__restrict__ X,
+                              int64_t ldx, int64_t strideX, T *__restrict__ Y, int64_t ldy, int64_t strideY, int64_t b,
+                              double sign, int acc) {
+  using R = typename ST<T>::real;
+  const int64_t r = r0 + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const int lane = threadIdx.x & 31;
+  const int l = blockIdx.y;
+  if (r >= r1) return;
+  const cx<double> z = zz[l];
+  const T *Xl = X + l * strideX;
+  T *Yl = Y + l * strideY;
+  const int64_t e0 = rp[r], e1 = rp[r + 1];
+  for (int64_t c0 = 0; c0 < b; c0 += 32) {
+    const int64_t c = c0 + lane;
+    if (c >= b) break;
+    T s = ST<T>::zero();
+    for (int64_t e = e0; e < e1; ++e) {
+      const int64_t q = col[e];
+      if (q < qlo || q >= qhi) continue;
+      const T v = Shift<T>::make(av[e], mv[e], z);
+      s = ST<T>::fma(v, Xl[(q - qlo) * ldx + c], s);
+    }
+    T *y = Yl + (r - r0) * ldy + c;
+    T out = (R)sign * s;
+    *y = acc ? *y + out : out;
+  }
+}
+
+template <typename T>
+void couple(cudaStream_t st, const DevPencil &P, int64_t r0, int64_t r1, int64_t qlo, int64_t qhi,
+            const cx<double> *z_dev, int nnodes, const T *X, int64_t ldx, int64_t strideX, T *Y, int64_t ldy,
+            int64_t strideY, int64_t b, double sign, bool accumulate) {
+  if (r1 <= r0 || b <= 0 || nnodes <= 0) return;
+  dim3 grid(ceil_div((r1 - r0) * 32, 256), nnodes);
+  couple_kernel<T><<<grid, 256, 0, st>>>(P.rowptr, P.col, P.a, P.m, r0, r1, qlo, qhi, z_dev, X, ldx, strideX, Y, ldy,
+                                         strideY, b, sign, accumulate ? 1 : 0);
+  RFDD_CHECK_LAUNCH();
+}
+
+// --------------------------------------------------------------------------------------
+// FP64 shifted residual R = V - (A - zM) X (complex)
+// --------------------------------------------------------------------------------------
+__global__ void shifted_residual_kernel(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                        const double *__restrict__ av, const double *__restrict__ mv, int64_t n,
+                                        const cx<double> *__restrict__ zz, const cx<double> *__restrict__ V,
+                                        int64_t strideV, const cx<double> *__restrict__ X, cx<double> *__restrict__ Rr,
+                                        int64_t stride, int64_t b) {
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const int lane = threadIdx.x & 31;
+  const int l = blockIdx.y;
+  if (r >= n) return;
+  const cx<double> z = zz[l];
+  const cx<double> *Xl = X + l * stride;
+  const int64_t e0 = rp[r], e1 = rp[r + 1];
+  for (int64_t c0 = 0; c0 < b; c0 += 32) {
+    const int64_t c = c0 + lane;
+    if (c >= b) break;
+    double sr = 0.0, si = 0.0;
+    for (int64_t e = e0; e < e1; ++e) {
+      const cx<double> x = Xl[(int64_t)col[e] * b + c];
+      const double vr = av[e] - z.re * mv[e], vi = -z.im * mv[e];
+      sr = fma(vr, x.re, fma(-vi, x.im, sr));
+      si = fma(vr, x.im, fma(vi, x.re, si));
+    }
+    const cx<double> v = V[l * strideV + r * b + c];
+    Rr[l * stride + r * b + c] = cx<double>(v.re - sr, v.im - si);
+  }
+}
+
+void shifted_residual(cudaStream_t st, const DevPencil &P, const cx<double> *z_dev, int nnodes,
+                      const cx<double> *V, int64_t strideV, const cx<double> *X, cx<double> *R, int64_t stride,
+                      int64_t b) {
+  dim3 grid(ceil_div(P.n * 32, 256), nnodes);
+  shifted_residual_kernel<<<grid, 256, 0, st>>>(P.rowptr, P.col, P.a, P.m, P.n, z_dev, V, strideV, X, R, stride, b);
+  RFDD_CHECK_LAUNCH();
+}
+
+// --------------------------------------------------------------------------------------
+// a2: assemble dense (bordered) shifted blocks; warp per row
+// --------------------------------------------------------------------------------------
+template <typename T>
+__global__ void assemble_blocks_kernel(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                       const double *__restrict__ av, const double *__restrict__ mv, int p,
+                                       int64_t dsum, int64_t s, const int64_t *__restrict__ off,
+                                       const int32_t *__restrict__ sidx, const int64_t *__restrict__ sidx_off,
+                                       const int32_t *__restrict__ posmap, const int64_t *__restrict__ Doff,
+                                       int64_t total_rows, const int64_t *__restrict__ boff,
+                                       const cx<double> *__restrict__ zz, T *__restrict__ base, int border) {
+  const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const int lane = threadIdx.x & 31;
+  const int l = blockIdx.y;
+  if (g >= total_rows) return;
+  int lo = 0, hi = p;  // find j with Doff[j] <= g < Doff[j+1]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) / 2;
+    if (Doff[mid] <= g) lo = mid; else hi = mid;
+  }
+  const int j = lo;
+  const int64_t dj = off[j + 1] - off[j];
+  const int64_t sj = sidx_off[j + 1] - sidx_off[j];
+  const int64_t Dj = border ? dj + sj : dj;
+  const int64_t i = g - Doff[j];
+  T *row = base + boff[(int64_t)l * p + j] + i * Dj;
+  const cx<double> z = zz[l];
+  for (int64_t c = lane; c < Dj; c += 32) row[c] = ST<T>::zero();
+  __syncwarp();
+  const int32_t *pm = posmap + (int64_t)j * s;
+  if (i < dj) {
+    const int64_t r = off[j] + i;
+    for (int64_t e = rp[r] + lane; e < rp[r + 1]; e += 32) {
+      const int64_t q = col[e];
+      if (q < dsum) {
+        row[q - off[j]] = Shift<T>::make(av[e], mv[e], z);
+      } else if (border) {
+        const int pos = pm[q - dsum];
+        row[dj + pos] = Shift<T>::make(av[e], mv[e], z);
+      }
+    }
+  } else {
+    const int64_t a = sidx[sidx_off[j] + (i - dj)];
+    const int64_t r = dsum + a;
+    for (int64_t e = rp[r] + lane; e < rp[r + 1]; e += 32) {
+      const int64_t q = col[e];
+      if (q >= off[j] && q < off[j + 1]) row[q - off[j]] = Shift<T>::make(av[e], mv[e], z);
+    }
+  }
+}
+
+template <typename T>
+void assemble_blocks(cudaStream_t st, const DevPencil &P, const DevDD &dd, const int64_t *dev_D_off,
+                     int64_t total_rows, const int64_t *dev_boff, const cx<double> *z_dev, int nnodes, T *base,
+                     bool border) {
+  if (total_rows <= 0) return;
+  dim3 grid(ceil_div(total_rows * 32, 256), nnodes);
+  assemble_blocks_kernel<T><<<grid, 256, 0, st>>>(P.rowptr, P.col, P.a, P.m, dd.p, dd.dsum, dd.s, dd.off, dd.sidx,
+                                                  dd.sidx_off, dd.posmap, dev_D_off, total_rows, dev_boff, z_dev, base,
+                                                  border ? 1 : 0);
+  RFDD_CHECK_LAUNCH();
+}
+
+template <typename T>
+__global__ void assemble_interface_kernel(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                          const double *__restrict__ av, const double *__restrict__ mv,
+                                          int64_t dsum, int64_t s, const cx<double> *__restrict__ zz,
+                                          T *__restrict__ S) {
+  const int64_t a = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const int lane = threadIdx.x & 31;
+  const int l = blockIdx.y;
+  if (a >= s) return;
+  T *row = S + (int64_t)l * s * s + a * s;
+  for (int64_t c = lane; c < s; c += 32) row[c] = ST<T>::zero();
+  __syncwarp();
+  const cx<double> z = zz[l];
+  const int64_t r = dsum + a;
+  for (int64_t e = rp[r] + lane; e < rp[r + 1]; e += 32) {
+    const int64_t q = col[e];
+    if (q >= dsum) row[q - dsum] = Shift<T>::make(av[e], mv[e], z);
+  }
+}
+
+template <typename T>
+void assemble_interface(cudaStream_t st, const DevPencil &P, const DevDD &dd, const cx<double> *z_dev,
+                        int nnodes, T *S) {
+  dim3 grid(ceil_div(dd.s * 32, 256), nnodes);
+  assemble_interface_kernel<T><<<grid, 256, 0, st>>>(P.rowptr, P.col, P.a, P.m, dd.dsum, dd.s, z_dev, S);
+  RFDD_CHECK_LAUNCH();
+}
+
+template <typename T>
+__global__ void scatter_schur_kernel(const int32_t *__restrict__ sidx_j, int p, int j, int dj, int sj, int64_t s,
+                                     const int64_t *__restrict__ boff, const T *__restrict__ base,
+                                     T *__restrict__ S) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int l = blockIdx.y;
+  if (e >= (int64_t)sj * sj) return;
+  const int a = (int)(e / sj), b = (int)(e % sj);
+  const int64_t Dj = (int64_t)dj + sj;
+  const T *trail = base + boff[(int64_t)l * p + j] + (int64_t)dj * Dj + dj;
+  T *dst = S + (int64_t)l * s * s + (int64_t)sidx_j[a] * s + sidx_j[b];
+  *dst = *dst + trail[(int64_t)a * Dj + b];
+}
+
+template <typename T>
+void scatter_schur(cudaStream_t st, const DevDD &dd, int j, int dj, int sj, int64_t sidx_start,
+                   const int64_t *dev_boff, const T *base, int nnodes, T *S) {
+  if (sj <= 0) return;
+  dim3 grid(ceil_div((int64_t)sj * sj, 256), nnodes);
+  scatter_schur_kernel<T><<<grid, 256, 0, st>>>(dd.sidx + sidx_start, dd.p, j, dj, sj, dd.s, dev_boff, base, S);
+  RFDD_CHECK_LAUNCH();
+}
+
+// --------------------------------------------------------------------------------------
+// elementwise
+// --------------------------------------------------------------------------------------
+template <typename TO, typename TI>
+__global__ void convert_kernel(const TI *__restrict__ x, TO *__restrict__ y, int64_t n);
+
+#define RFDD_CONV_RR(TO, TI)                                                                           \
+  template <>                                                                                          \
+  __global__ void convert_kernel<TO, TI>(const TI *__restrict__ x, TO *__restrict__ y, int64_t n) {    \
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) \
+      y[i] = (TO)x[i];                                                                                 \
+  }
+#define RFDD_CONV_CC(RO, RI)                                                                           \
+  template <>                                                                                          \
+  __global__ void convert_kernel<cx<RO>, cx<RI>>(const cx<RI> *__restrict__ x, cx<RO> *__restrict__ y, int64_t n) { \
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) \
+      y[i] = cx<RO>((RO)x[i].re, (RO)x[i].im);                                                         \
+  }
+RFDD_CONV_RR(float, double)
+RFDD_CONV_RR(double, float)
+RFDD_CONV_RR(double, double)
+RFDD_CONV_RR(float, float)
+RFDD_CONV_CC(float, double)
+RFDD_CONV_CC(double, float)
+RFDD_CONV_CC(double, double)
+RFDD_CONV_CC(float, float)
+
+static int grid_for(int64_t n) { return (int)std::min<int64_t>(std::max<int64_t>(1, (n + 255) / 256), 152 * 32); }
+
+template <typename TO, typename TI>
+void convert(cudaStream_t st, const TI *x, TO *y, int64_t n) {
+  if (n <= 0) return;
+  convert_kernel<TO, TI><<<grid_for(n), 256, 0, st>>>(x, y, n);
+  RFDD_CHECK_LAUNCH();
+}
+template void convert<float, double>(cudaStream_t, const double *, float *, int64_t);
+template void convert<double, float>(cudaStream_t, const float *, double *, int64_t);
+template void convert<double, double>(cudaStream_t, const double *, double *, int64_t);
+template void convert<float, float>(cudaStream_t, const float *, float *, int64_t);
+template void convert<cx<float>, cx<double>>(cudaStream_t, const cx<double> *, cx<float> *, int64_t);
+template void convert<cx<double>, cx<float>>(cudaStream_t, const cx<float> *, cx<double> *, int64_t);
+template void convert<cx<double>, cx<double>>(cudaStream_t, const cx<double> *, cx<double> *, int64_t);
+template void convert<cx<float>, cx<float>>(cudaStream_t, const cx<float> *, cx<float> *, int64_t);
+
+template <typename T>
+__global__ void real_to_complex_kernel(const double *__restrict__ x, T *__restrict__ y, int64_t n, int nrep,
+                                       int64_t stride) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const T v = ST<T>::from_re(x[i]);
+    for (int r = 0; r < nrep; ++r) y[r * stride + i] = v;
+  }
+}
+template <typename T>
+void real_to_complex(cudaStream_t st, const double *x, T *y, int64_t n, int nrep, int64_t stride) {
+  if (n <= 0) return;
+  real_to_complex_kernel<T><<<grid_for(n), 256, 0, st>>>(x, y, n, nrep, stride);
+  RFDD_CHECK_LAUNCH();
+}
+
+template <typename T>
+__global__ void weighted_real_sum_kernel(const T *__restrict__ Y, int64_t strideY, const cx<double> *__restrict__ w,
+                                         int nnodes, double scale, double *__restrict__ W, int64_t count) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int l = 0; l < nnodes; ++l) {
+      const T y = Y[l * strideY + i];
+      acc += w[l].re * (double)y.re - w[l].im * (double)y.im;
+    }
+    W[i] = scale * acc;
+  }
+}
+template <typename T>
+void weighted_real_sum(cudaStream_t st, const T *Y, int64_t strideY, const cx<double> *w_dev, int nnodes,
+                       double scale, double *W, int64_t count) {
+  if (count <= 0) return;
+  weighted_real_sum_kernel<T><<<grid_for(count), 256, 0, st>>>(Y, strideY, w_dev, nnodes, scale, W, count);
+  RFDD_CHECK_LAUNCH();
+}
+
+__global__ void axpy_f64_kernel(double a, const double *__restrict__ x, double *__restrict__ y, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = fma(a, x[i], y[i]);
+}
+void axpy_f64(cudaStream_t st, double a, const double *x, double *y, int64_t n) {
+  if (n <= 0) return;
+  axpy_f64_kernel<<<grid_for(n), 256, 0, st>>>(a, x, y, n);
+  RFDD_CHECK_LAUNCH();
+}
+__global__ void axpy_c64_kernel(const cx<double> *__restrict__ x, cx<double> *__restrict__ y, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = y[i] + x[i];
+}
+void axpy_c64(cudaStream_t st, const cx<double> *x, cx<double> *y, int64_t n) {
+  if (n <= 0) return;
+  axpy_c64_kernel<<<grid_for(n), 256, 0, st>>>(x, y, n);
+  RFDD_CHECK_LAUNCH();
+}
+
+__global__ void scale_cols_kernel(double *X, int64_t n, int64_t b, int64_t ld, const double *__restrict__ s) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * b; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / b, c = e % b;
+    X[i * ld + c] *= s[c];
+  }
+}
+void scale_cols_f64(cudaStream_t st, double *X, int64_t n, int64_t b, int64_t ld, const double *s) {
+  if (n * b <= 0) return;
+  scale_cols_kernel<<<grid_for(n * b), 256, 0, st>>>(X, n, b, ld, s);
+  RFDD_CHECK_LAUNCH();
+}
+
+// SplitMix64 (Vigna): value i of stream `stream` is mix(seed + (stream*2^32 + i + 1)*golden),
+// mapped to (mix >> 11) * 2^-52 - 1 in [-1, 1).
+__global__ void counter_uniform_kernel(uint64_t seed, uint64_t stream, double *x, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t c = (stream << 32) + (uint64_t)i + 1ull;
+    uint64_t z = seed + c * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    x[i] = (double)(z >> 11) * 0x1p-52 - 1.0;
+  }
+}
+void counter_uniform_dev(cudaStream_t st, uint64_t seed, uint64_t stream, double *x, int64_t n) {
+  if (n <= 0) return;
+  counter_uniform_kernel<<<grid_for(n), 256, 0, st>>>(seed, stream, x, n);
+  RFDD_CHECK_LAUNCH();
+}
+
+// column dots: one CTA per column, fixed-order tree reduction (reproducible)
+__global__ void col_dots_kernel(const double *__restrict__ X, int64_t ldx, const double *__restrict__ Y, int64_t ldy,
+                                int64_t n, double *out) {
+  const int64_t c = blockIdx.x;
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s = fma(X[i * ldx + c], Y[i * ldy + c], s);
+  __shared__ double red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[c] = red[0];
+}
+void col_dots(cudaStream_t st, const double *X, int64_t ldx, const double *Y, int64_t ldy, int64_t n, int64_t b,
+              double *out) {
+  if (b <= 0) return;
+  col_dots_kernel<<<(unsigned)b, 256, 0, st>>>(X, ldx, Y, ldy, n, out);
+  RFDD_CHECK_LAUNCH();
+}
+
+__global__ void col_norms2_c64_kernel(const cx<double> *__restrict__ R, int64_t n, int64_t b, int64_t stride,
+                                      double *out) {
+  const int64_t c = blockIdx.x;
+  const int l = blockIdx.y;
+  const cx<double> *Rl = R + l * stride;
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const cx<double> v = Rl[i * b + c];
+    s = fma(v.re, v.re, fma(v.im, v.im, s));
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[(int64_t)l * b + c] = red[0];
+}
+void col_norms2_c64(cudaStream_t st, const cx<double> *R, int64_t n, int64_t b, int nnodes, int64_t stride,
+                    double *out) {
+  if (b <= 0 || nnodes <= 0) return;
+  col_norms2_c64_kernel<<<dim3((unsigned)b, nnodes), 256, 0, st>>>(R, n, b, stride, out);
+  RFDD_CHECK_LAUNCH();
+}
+
+__global__ void copy_rows_kernel(const double *__restrict__ src, int64_t lds, double *__restrict__ dst, int64_t ldd,
+                                 int64_t nrows, int64_t ncols) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nrows * ncols;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / ncols, c = e % ncols;
+    dst[i * ldd + c] = src[i * lds + c];
+  }
+}
+void copy_rows_f64(cudaStream_t st, const double *src, int64_t lds, double *dst, int64_t ldd, int64_t nrows,
+                   int64_t ncols) {
+  if (nrows * ncols <= 0) return;
+  copy_rows_kernel<<<grid_for(nrows * ncols), 256, 0, st>>>(src, lds, dst, ldd, nrows, ncols);
+  RFDD_CHECK_LAUNCH();
+}
+
+__global__ void gather_rows_kernel(const double *__restrict__ src, int64_t lds, const int64_t *__restrict__ idx,
+                                   double *__restrict__ dst, int64_t ldd, int64_t nrows, int64_t ncols) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nrows * ncols;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / ncols, c = e % ncols;
+    dst[i * ldd + c] = src[idx[i] * lds + c];
+  }
+}
+void gather_rows_f64(cudaStream_t st, const double *src, int64_t lds, const int64_t *idx, double *dst,
+                     int64_t ldd, int64_t nrows, int64_t ncols) {
+  if (nrows * ncols <= 0) return;
+  gather_rows_kernel<<<grid_for(nrows * ncols), 256, 0, st>>>(src, lds, idx, dst, ldd, nrows, ncols);
+  RFDD_CHECK_LAUNCH();
+}
+
+#define RFDD_INST_OPS(T)                                                                                     \
+  template void assemble_blocks<T>(cudaStream_t, const DevPencil &, const DevDD &, const int64_t *, int64_t, \
+                                   const int64_t *, const cx<double> *, int, T *, bool);
+RFDD_INST_OPS(float)
+RFDD_INST_OPS(double)
+RFDD_INST_OPS(cx<float>)
+RFDD_INST_OPS(cx<double>)
+
+#define RFDD_INST_OPSC(T)                                                                                         \
+  template void assemble_interface<T>(cudaStream_t, const DevPencil &, const DevDD &, const cx<double> *, int, T *); \
+  template void scatter_schur<T>(cudaStream_t, const DevDD &, int, int, int, int64_t, const int64_t *, const T *, int, T *);    \
+  template void couple<T>(cudaStream_t, const DevPencil &, int64_t, int64_t, int64_t, int64_t, const cx<double> *,  \
+                          int, const T *, int64_t, int64_t, T *, int64_t, int64_t, int64_t, double, bool);           \
+  template void real_to_complex<T>(cudaStream_t, const double *, T *, int64_t, int, int64_t);                        \
+  template void weighted_real_sum<T>(cudaStream_t, const T *, int64_t, const cx<double> *, int, double, double *,   \
+                                     int64_t);
+RFDD_INST_OPSC(cx<float>)
+RFDD_INST_OPSC(cx<double>)
+
+}  // namespace rfdd

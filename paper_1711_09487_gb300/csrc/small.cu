@@ -1,0 +1,174 @@
+// Small dense FP64 kernels for block orthonormalisation and Rayleigh-Ritz bookkeeping.
+#include "small.cuh"
+
+#include <algorithm>
+
+namespace rfdd {
+
+constexpr int CH_MAXB = 64;
+struct CholBatchP {
+  CholItem it[CH_MAXB];
+};
+
+// Right-looking Cholesky G = R^T R on the upper triangle, one CTA per matrix (global memory).
+// A pivot <= tol * (largest diagonal) marks its column dead: its row of R is zeroed and the
+// column is skipped, so the kept columns get an orthonormal basis and dead ones a zero column.
+__global__ void __launch_bounds__(512) chol_inv_kernel(CholBatchP bp, double tol) {
+  const CholItem it = bp.it[blockIdx.x];
+  const int b = it.b;
+  double *G = it.G;
+  __shared__ double dmax_s;
+  __shared__ int dead_s;
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int i = 0; i < b; ++i) m = fmax(m, G[(int64_t)i * b + i]);
+    dmax_s = m;
+  }
+  __syncthreads();
+  const double thr = tol * dmax_s;
+  for (int t = 0; t < b; ++t) {
+    if (threadIdx.x == 0) {
+      const double pv = G[(int64_t)t * b + t];
+      dead_s = !(pv > thr) || !isfinite(pv);
+      it.dead[t] = dead_s;
+      if (!dead_s) G[(int64_t)t * b + t] = sqrt(pv);
+    }
+    __syncthreads();
+    const double rtt = G[(int64_t)t * b + t];
+    if (dead_s) {
+      for (int c = t + threadIdx.x; c < b; c += blockDim.x) G[(int64_t)t * b + c] = 0.0;
+    } else {
+      for (int c = t + 1 + threadIdx.x; c < b; c += blockDim.x) G[(int64_t)t * b + c] /= rtt;
+    }
+    __syncthreads();
+    if (!dead_s) {
+      const int w = b - t - 1;
+      for (int e = threadIdx.x; e < w * w; e += blockDim.x) {
+        const int i = t + 1 + e / w, c = t + 1 + e % w;
+        if (c >= i) G[(int64_t)i * b + c] -= G[(int64_t)t * b + i] * G[(int64_t)t * b + c];
+      }
+    }
+    __syncthreads();
+  }
+  // zero the strict lower triangle so that G holds exactly R
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x)
+    if (e / b > e % b) G[e] = 0.0;
+  __syncthreads();
+  // R^{-1} by back substitution, thread per column
+  for (int c = threadIdx.x; c < b; c += blockDim.x) {
+    for (int i = b - 1; i >= 0; --i) {
+      double v;
+      if (it.dead[i]) {
+        v = 0.0;
+      } else {
+        v = (i == c) ? 1.0 : 0.0;
+        for (int k = i + 1; k <= c; ++k) v -= G[(int64_t)i * b + k] * it.Rinv[(int64_t)k * b + c];
+        v /= G[(int64_t)i * b + i];
+      }
+      if (i > c) v = 0.0;
+      it.Rinv[(int64_t)i * b + c] = v;
+    }
+  }
+}
+
+void chol_inv_batched(cudaStream_t st, const std::vector<CholItem> &items, double tol) {
+  for (size_t s = 0; s < items.size(); s += CH_MAXB) {
+    CholBatchP b;
+    memset(&b, 0, sizeof(b));
+    const int cnt = (int)std::min<size_t>(CH_MAXB, items.size() - s);
+    for (int i = 0; i < cnt; ++i) b.it[i] = items[s + i];
+    chol_inv_kernel<<<cnt, 512, 0, st>>>(b, tol);
+    RFDD_CHECK_LAUNCH();
+  }
+}
+
+static int gridn(int64_t n) { return (int)std::min<int64_t>(std::max<int64_t>(1, (n + 255) / 256), 152 * 32); }
+
+__global__ void scale_sym_kernel(double *A, int64_t k, const double *__restrict__ d) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += (int64_t)gridDim.x * blockDim.x)
+    A[e] *= d[e / k] * d[e % k];
+}
+void scale_sym(cudaStream_t st, double *A, int64_t k, const double *d) {
+  if (k <= 0) return;
+  scale_sym_kernel<<<gridn(k * k), 256, 0, st>>>(A, k, d);
+  RFDD_CHECK_LAUNCH();
+}
+
+__global__ void scale_rows_cols_kernel(const double *__restrict__ U, int64_t r, int64_t k, const double *__restrict__ d,
+                                       const double *__restrict__ f, double *out) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < r * k; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = U[e] * d[e % k] * f[e / k];
+}
+void scale_rows_cols(cudaStream_t st, const double *U, int64_t r, int64_t k, const double *d, const double *f,
+                     double *out) {
+  if (r * k <= 0) return;
+  scale_rows_cols_kernel<<<gridn(r * k), 256, 0, st>>>(U, r, k, d, f, out);
+  RFDD_CHECK_LAUNCH();
+}
+
+__global__ void inv_sqrt_diag_kernel(const double *__restrict__ G, int64_t k, double *d) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < k; c += (int64_t)gridDim.x * blockDim.x) {
+    const double g = G[c * k + c];
+    d[c] = g > 0.0 ? 1.0 / sqrt(g) : 0.0;
+  }
+}
+void inv_sqrt_diag(cudaStream_t st, const double *G, int64_t k, double *d) {
+  if (k <= 0) return;
+  inv_sqrt_diag_kernel<<<gridn(k), 256, 0, st>>>(G, k, d);
+  RFDD_CHECK_LAUNCH();
+}
+
+__global__ void inv_sqrt_vec_kernel(const double *__restrict__ lam, int64_t r, double *f) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < r; q += (int64_t)gridDim.x * blockDim.x)
+    f[q] = 1.0 / sqrt(lam[q]);
+}
+void inv_sqrt_vec(cudaStream_t st, const double *lam, int64_t r, double *f) {
+  if (r <= 0) return;
+  inv_sqrt_vec_kernel<<<gridn(r), 256, 0, st>>>(lam, r, f);
+  RFDD_CHECK_LAUNCH();
+}
+
+__global__ void ritz_residuals_kernel(const double *__restrict__ AX, const double *__restrict__ MX,
+                                      const double *__restrict__ theta, int64_t n, int64_t b, double *res) {
+  const int64_t c = blockIdx.x;
+  const double th = theta[c];
+  double sr = 0.0, sm = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double mx = MX[i * b + c];
+    const double r = AX[i * b + c] - th * mx;
+    sr = fma(r, r, sr);
+    sm = fma(mx, mx, sm);
+  }
+  __shared__ double r1[256], r2[256];
+  r1[threadIdx.x] = sr;
+  r2[threadIdx.x] = sm;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) { r1[threadIdx.x] += r1[threadIdx.x + o]; r2[threadIdx.x] += r2[threadIdx.x + o]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) res[c] = sqrt(r1[0]) / (fabs(th) * sqrt(r2[0]));
+}
+void ritz_residuals(cudaStream_t st, const double *AX, const double *MX, const double *theta, int64_t n, int64_t b,
+                    double *res) {
+  if (b <= 0) return;
+  ritz_residuals_kernel<<<(unsigned)b, 256, 0, st>>>(AX, MX, theta, n, b, res);
+  RFDD_CHECK_LAUNCH();
+}
+
+template <typename T>
+__global__ void sub_inplace_kernel(const T *__restrict__ x, T *__restrict__ y, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = y[i] - x[i];
+}
+template <typename T>
+void sub_inplace(cudaStream_t st, const T *x, T *y, int64_t n) {
+  if (n <= 0) return;
+  sub_inplace_kernel<T><<<gridn(n), 256, 0, st>>>(x, y, n);
+  RFDD_CHECK_LAUNCH();
+}
+template void sub_inplace<cx<float>>(cudaStream_t, const cx<float> *, cx<float> *, int64_t);
+template void sub_inplace<cx<double>>(cudaStream_t, const cx<double> *, cx<double> *, int64_t);
+template void sub_inplace<double>(cudaStream_t, const double *, double *, int64_t);
+
+}  // namespace rfdd

@@ -1,0 +1,32 @@
+// Small dense FP64 helpers (one CTA per matrix): Cholesky with drop tolerance and the inverse
+// of the triangular factor, used for block orthonormalisation (Cholesky-QR).
+#pragma once
+#include "common.cuh"
+
+namespace rfdd {
+
+struct CholItem {
+  double *G;     // b x b Gram matrix (row-major, ld = b); overwritten by R (upper, G = R^T R)
+  double *Rinv;  // b x b output: R^{-1} (columns of dropped pivots are zero)
+  int *dead;     // b flags: 1 where the pivot fell below tol * max diagonal
+  int b;
+};
+void chol_inv_batched(cudaStream_t st, const std::vector<CholItem> &items, double tol);
+
+// C = D A D elementwise for a k x k matrix with diagonal scaling vector d
+void scale_sym(cudaStream_t st, double *A, int64_t k, const double *d);
+// out[q][c] = U[q][c] * d[c] * f[q]   (r x k)
+void scale_rows_cols(cudaStream_t st, const double *U, int64_t r, int64_t k, const double *d, const double *f,
+                     double *out);
+// d[c] = G[c][c] > 0 ? 1/sqrt(G[c][c]) : 0
+void inv_sqrt_diag(cudaStream_t st, const double *G, int64_t k, double *d);
+// f[q] = 1/sqrt(lam[q0 + q])
+void inv_sqrt_vec(cudaStream_t st, const double *lam, int64_t r, double *f);
+// residual norms: res[c] = ||AX_c - theta_c MX_c|| / (|theta_c| ||MX_c||)
+void ritz_residuals(cudaStream_t st, const double *AX, const double *MX, const double *theta, int64_t n, int64_t b,
+                    double *res);
+// y[i] -= x[i] for generic element type
+template <typename T>
+void sub_inplace(cudaStream_t st, const T *x, T *y, int64_t n);
+
+}  // namespace rfdd

@@ -1,0 +1,1749 @@
+// RF-DDES orchestration on one GPU and the C ABI (include/rfdd.h).
+//
+// Algorithm 3 of the paper (RF-DDES) with its interface step Algorithm 2, in the
+// interior-first ordering of Eq. (dd1):
+//   a0 quadrature -> a1 setup -> a2 dense shifted (bordered) blocks -> a3/a4 batched LU of
+//   [[B_j(z), E_j(z)], [E_j(z)^T, 0]] (the trailing block becomes -E^T B^{-1} E) -> a5 S(z)
+//   assembly + LU -> a6/a7 block Lanczos on F = Re sum w S^{-1} -> a8 interior basis
+//   (V_j, Sigma, Gamma) -> a9 Rayleigh-Ritz on Z -> a10 completion passes with the DD
+//   resolvent of Eq. (inv_dd2) and FP64 iterative refinement.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <functional>
+#include <cmath>
+#include <memory>
+#include <mutex>
+#include <numeric>
+#include <thread>
+
+#include "dense.cuh"
+#include "eig.cuh"
+#include "ops.cuh"
+#include "small.cuh"
+
+using namespace rfdd;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+// ------------------------------------------------------------------------------------
+// device buffers
+// ------------------------------------------------------------------------------------
+struct Buf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  Buf() = default;
+  Buf(const Buf &) = delete;
+  Buf &operator=(const Buf &) = delete;
+  ~Buf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  void alloc(size_t b) {
+    release();
+    if (b == 0) b = 16;
+    cudaError_t e = cudaMalloc(&p, b);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      throw Error(RFDD_ENOMEM, "cudaMalloc of " + std::to_string(b) + " bytes failed: " + cudaGetErrorString(e));
+    }
+    bytes = b;
+  }
+  void ensure(size_t b) {
+    if (b > bytes) alloc(b);
+  }
+  template <typename T>
+  T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+template <typename T>
+void upload(Buf &b, const std::vector<T> &v, cudaStream_t st) {
+  b.alloc(v.size() * sizeof(T));
+  if (!v.empty()) RFDD_CUDA(cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+}
+
+struct Timer {
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaStream_t st;
+  explicit Timer(cudaStream_t s) : st(s) {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, st);
+  }
+  ~Timer() {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+  double ms() {
+    cudaEventRecord(b, st);
+    cudaEventSynchronize(b);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, a, b);
+    return t;
+  }
+};
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------
+// handle and result
+// ------------------------------------------------------------------------------------
+struct rfdd_result {
+  int64_t n = 0, nev = 0;
+  std::vector<double> evals, resid, pre_evals;
+  std::vector<double> evecs_host;  // filled on demand
+  bool host_ready = false;
+  Buf evecs, evals_dev, resid_dev;
+  rfdd_info info{};
+  std::atomic<int> ready{1};
+  std::thread worker;
+  cudaStream_t st = nullptr;
+  ~rfdd_result() {
+    if (worker.joinable()) worker.join();
+  }
+};
+
+struct rfdd_handle {
+  rfdd_options opt;
+  int64_t n = 0, s = 0, dsum = 0, nnz = 0;
+  int p = 0;
+  std::vector<int64_t> off, perm, iperm, d, sidx_off, D;
+  std::vector<int32_t> sidx;
+  double normA = 0.0, normM = 0.0;  // max absolute row sums
+  bool has_me = false;              // M_E != 0 (the Gamma block of Z is needed)
+  std::vector<int64_t> host_rp;
+  std::vector<int32_t> host_cl, host_posmap;
+  std::vector<double> host_av, host_mv;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  // device copies
+  Buf rowptr, col, aval, mval, off_dev, sidx_dev, sidx_off_dev, posmap, iperm_dev, status;
+  DevPencil P;
+  DevDD dd;
+  // factors (a2-a5)
+  int nnodes = 0;
+  std::vector<cx<double>> z, w;
+  Buf z_dev, w_dev, fac, boff_dev, Doff_dev, pivB, Sfac, pivS, Skeep;
+  std::vector<int64_t> boff, pivBoff;
+  bool have_factors = false;
+  double alpha = 0, beta = 0;
+  bool have_interval = false;
+  // Lanczos (a7)
+  Buf Q;
+  int64_t mu = 0, qcap = 0;
+  std::vector<double> traces;
+  // interior (a8)
+  Buf Zb;
+  int64_t kz = 0, kappa = 0;
+  double sigma_used = 0.0;
+  // Rayleigh-Ritz (a9)
+  std::vector<double> rr_theta;
+  Buf X0;
+  int64_t m0 = 0;
+};
+
+namespace {
+
+inline bool is_mixed(const rfdd_handle *h) { return h->opt.precision == RFDD_MIXED; }
+
+void sync_status(rfdd_handle *h, const char *where) {
+  RFDD_CUDA(cudaStreamSynchronize(h->st));
+  int s = 0;
+  RFDD_CUDA(cudaMemcpy(&s, h->status.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (s != 0) {
+    RFDD_CUDA(cudaMemset(h->status.p, 0, sizeof(int)));
+    if (s & (DS_ZERO_PIVOT | DS_NONFINITE))
+      throw Error(RFDD_ESINGULAR, std::string(where) + ": zero or non-finite pivot (device status " +
+                                      std::to_string(s) + ")");
+    throw Error(RFDD_ECUDA, std::string(where) + ": device status " + std::to_string(s));
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// a0: quadrature (Section 2.1; midpoint rule of Section 6)
+// ------------------------------------------------------------------------------------
+void quadrature(double alpha, double beta, int nc, int rule, std::vector<cx<double>> &z,
+                std::vector<cx<double>> &w) {
+  RFDD_REQUIRE(beta > alpha && nc >= 1, RFDD_EINVAL, "quadrature: need alpha < beta and n_nodes >= 1");
+  const double c = 0.5 * (alpha + beta), r = 0.5 * (beta - alpha);
+  z.resize(nc);
+  w.resize(nc);
+  if (rule == RFDD_MIDPOINT) {
+    for (int l = 0; l < nc; ++l) {
+      const double th = (2.0 * (l + 1) - 1.0) * M_PI / (2.0 * nc);
+      const double er = std::cos(th), ei = std::sin(th);
+      z[l] = cx<double>(c + r * er, r * ei);
+      w[l] = cx<double>(-r * er / (2.0 * nc), -r * ei / (2.0 * nc));
+    }
+  } else if (rule == RFDD_GAUSS_LEGENDRE) {
+    // Gauss-Legendre nodes by Newton iteration on P_nc from Chebyshev starting points
+    std::vector<double> t(nc), wt(nc);
+    for (int i = 0; i < nc; ++i) {
+      double x = std::cos(M_PI * (i + 0.75) / (nc + 0.5));
+      for (int it = 0; it < 100; ++it) {
+        double p0 = 1.0, p1 = x;
+        for (int k = 2; k <= nc; ++k) {
+          const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+          p0 = p1;
+          p1 = p2;
+        }
+        double pn = nc == 1 ? x : p1, pm = nc == 1 ? 1.0 : p0;
+        const double dp = nc * (x * pn - pm) / (x * x - 1.0);
+        const double dx = pn / dp;
+        x -= dx;
+        if (std::fabs(dx) < 1e-16) break;
+      }
+      double p0 = 1.0, p1 = x;
+      for (int k = 2; k <= nc; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      double pn = nc == 1 ? x : p1, pm = nc == 1 ? 1.0 : p0;
+      const double dp = nc * (x * pn - pm) / (x * x - 1.0);
+      t[i] = x;
+      wt[i] = 2.0 / ((1.0 - x * x) * dp * dp);
+    }
+    {  // ascending nodes t (theta increasing)
+      std::vector<int> o(nc);
+      std::iota(o.begin(), o.end(), 0);
+      std::sort(o.begin(), o.end(), [&](int a, int b) { return t[a] < t[b]; });
+      std::vector<double> t2(nc), w2(nc);
+      for (int i = 0; i < nc; ++i) { t2[i] = t[o[i]]; w2[i] = wt[o[i]]; }
+      t.swap(t2);
+      wt.swap(w2);
+    }
+    for (int l = 0; l < nc; ++l) {
+      const double th = 0.5 * M_PI * (1.0 + t[l]);
+      const double er = std::cos(th), ei = std::sin(th);
+      z[l] = cx<double>(c + r * er, r * ei);
+      w[l] = cx<double>(-0.25 * r * wt[l] * er, -0.25 * r * wt[l] * ei);
+    }
+  } else {
+    throw Error(RFDD_EINVAL, "quadrature: unknown rule");
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// a1: setup (validation, interior-first ordering, union CSR, interface maps)
+// ------------------------------------------------------------------------------------
+void validate_csr(const rfdd_csr *A, const char *name) {
+  RFDD_REQUIRE(A && A->rowptr && A->col && A->val && A->n > 0, RFDD_EINVAL, std::string(name) + ": NULL or empty");
+  const int64_t n = A->n;
+  RFDD_REQUIRE(A->rowptr[0] == 0, RFDD_EINVAL, std::string(name) + ": rowptr[0] != 0");
+  for (int64_t i = 0; i < n; ++i) {
+    RFDD_REQUIRE(A->rowptr[i + 1] >= A->rowptr[i], RFDD_EINVAL, std::string(name) + ": rowptr not monotone");
+    for (int64_t e = A->rowptr[i]; e < A->rowptr[i + 1]; ++e) {
+      RFDD_REQUIRE(A->col[e] >= 0 && A->col[e] < n, RFDD_EINVAL, std::string(name) + ": column out of range");
+      RFDD_REQUIRE(std::isfinite(A->val[e]), RFDD_EINVAL, std::string(name) + ": non-finite value");
+    }
+  }
+}
+
+// symmetric in pattern and value: compare with the transpose built by counting sort
+void check_symmetric(const rfdd_csr *A, const char *name) {
+  const int64_t n = A->n, nnz = A->rowptr[n];
+  std::vector<int64_t> cnt(n + 1, 0);
+  for (int64_t e = 0; e < nnz; ++e) cnt[A->col[e] + 1]++;
+  for (int64_t i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
+  std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
+  std::vector<int64_t> trow(nnz);
+  std::vector<double> tval(nnz);
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t e = A->rowptr[i]; e < A->rowptr[i + 1]; ++e) {
+      const int64_t q = pos[A->col[e]]++;
+      trow[q] = i;
+      tval[q] = A->val[e];
+    }
+  // row i of A^T: entries (trow, tval) in [cnt[i], cnt[i+1]); compare as sorted sets
+  std::vector<std::pair<int64_t, double>> ra, rt;
+  for (int64_t i = 0; i < n; ++i) {
+    ra.clear();
+    rt.clear();
+    for (int64_t e = A->rowptr[i]; e < A->rowptr[i + 1]; ++e) ra.push_back({A->col[e], A->val[e]});
+    for (int64_t q = cnt[i]; q < cnt[i + 1]; ++q) rt.push_back({trow[q], tval[q]});
+    std::sort(ra.begin(), ra.end());
+    std::sort(rt.begin(), rt.end());
+    RFDD_REQUIRE(ra.size() == rt.size(), RFDD_ENOTSYM, std::string(name) + " is not symmetric (pattern)");
+    for (size_t k = 0; k < ra.size(); ++k) {
+      RFDD_REQUIRE(ra[k].first == rt[k].first, RFDD_ENOTSYM, std::string(name) + " is not symmetric (pattern)");
+      const double a = ra[k].second, b = rt[k].second;
+      RFDD_REQUIRE(std::fabs(a - b) <= 1e-14 * std::max(std::fabs(a), std::fabs(b)), RFDD_ENOTSYM,
+                   std::string(name) + " is not symmetric (values)");
+    }
+  }
+}
+
+void do_setup(rfdd_handle *h, const rfdd_csr *A, const rfdd_csr *M, const int32_t *part, int32_t p) {
+  validate_csr(A, "A");
+  validate_csr(M, "M");
+  RFDD_REQUIRE(A->n == M->n, RFDD_EINVAL, "A and M differ in size");
+  RFDD_REQUIRE(part != nullptr && p >= 1, RFDD_EINVAL, "partition: NULL or p < 1");
+  check_symmetric(A, "A");
+  check_symmetric(M, "M");
+  const int64_t n = A->n;
+  for (int64_t i = 0; i < n; ++i) {
+    bool diag = false;
+    for (int64_t e = M->rowptr[i]; e < M->rowptr[i + 1]; ++e)
+      if (M->col[e] == i) {
+        RFDD_REQUIRE(M->val[e] > 0.0, RFDD_ENOTSPD_M, "M has a non-positive diagonal entry");
+        diag = true;
+      }
+    RFDD_REQUIRE(diag, RFDD_ENOTSPD_M, "M has a zero diagonal entry");
+  }
+  std::vector<int64_t> count(p + 1, 0);
+  for (int64_t i = 0; i < n; ++i) {
+    RFDD_REQUIRE(part[i] >= -1 && part[i] < p, RFDD_EPARTITION, "partition label out of range");
+    count[part[i] + 1]++;
+  }
+  RFDD_REQUIRE(count[0] > 0, RFDD_EPARTITION, "partition has no interface unknowns");
+  for (int j = 0; j < p; ++j) RFDD_REQUIRE(count[j + 1] > 0, RFDD_EPARTITION, "empty subdomain");
+  for (const rfdd_csr *X : {A, M})
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t e = X->rowptr[i]; e < X->rowptr[i + 1]; ++e) {
+        const int a = part[i], b = part[X->col[e]];
+        RFDD_REQUIRE(!(a >= 0 && b >= 0 && a != b), RFDD_EPARTITION,
+                     "partition is not a vertex separator (two subdomains are coupled)");
+      }
+  h->n = n;
+  h->p = p;
+  h->d.assign(p, 0);
+  for (int j = 0; j < p; ++j) h->d[j] = count[j + 1];
+  h->s = count[0];
+  h->off.assign(p + 1, 0);
+  for (int j = 0; j < p; ++j) h->off[j + 1] = h->off[j] + h->d[j];
+  h->dsum = h->off[p];
+  h->perm.resize(n);
+  h->iperm.resize(n);
+  {
+    std::vector<int64_t> cur(h->off.begin(), h->off.end());
+    int64_t ci = h->dsum;
+    for (int64_t i = 0; i < n; ++i) {
+      const int64_t r = part[i] >= 0 ? cur[part[i]]++ : ci++;
+      h->perm[r] = i;
+      h->iperm[i] = r;
+    }
+  }
+  // union CSR in the new ordering
+  std::vector<int64_t> rp(n + 1, 0);
+  std::vector<int32_t> cl;
+  std::vector<double> av, mv;
+  cl.reserve(A->rowptr[n] + M->rowptr[n]);
+  std::vector<std::pair<int64_t, std::pair<double, double>>> row;
+  h->normA = h->normM = 0.0;
+  for (int64_t r = 0; r < n; ++r) {
+    const int64_t i = h->perm[r];
+    row.clear();
+    double sa = 0, sm = 0;
+    for (int64_t e = A->rowptr[i]; e < A->rowptr[i + 1]; ++e) {
+      row.push_back({h->iperm[A->col[e]], {A->val[e], 0.0}});
+      sa += std::fabs(A->val[e]);
+    }
+    for (int64_t e = M->rowptr[i]; e < M->rowptr[i + 1]; ++e) {
+      row.push_back({h->iperm[M->col[e]], {0.0, M->val[e]}});
+      sm += std::fabs(M->val[e]);
+    }
+    h->normA = std::max(h->normA, sa);
+    h->normM = std::max(h->normM, sm);
+    std::sort(row.begin(), row.end(), [](auto &x, auto &y) { return x.first < y.first; });
+    for (size_t k = 0; k < row.size(); ++k) {
+      if (!cl.empty() && (int64_t)cl.size() > rp[r] && cl.back() == row[k].first) {
+        av.back() += row[k].second.first;
+        mv.back() += row[k].second.second;
+      } else {
+        cl.push_back((int32_t)row[k].first);
+        av.push_back(row[k].second.first);
+        mv.push_back(row[k].second.second);
+      }
+    }
+    rp[r + 1] = (int64_t)cl.size();
+  }
+  h->nnz = rp[n];
+  // interface coupling sets sidx_j
+  const int64_t s = h->s, dsum = h->dsum;
+  std::vector<int32_t> posmap((size_t)p * s, -1);
+  h->sidx.clear();
+  h->sidx_off.assign(p + 1, 0);
+  for (int j = 0; j < p; ++j) {
+    std::vector<int32_t> touched;
+    for (int64_t r = h->off[j]; r < h->off[j + 1]; ++r)
+      for (int64_t e = rp[r]; e < rp[r + 1]; ++e)
+        if (cl[e] >= dsum) touched.push_back((int32_t)(cl[e] - dsum));
+    std::sort(touched.begin(), touched.end());
+    touched.erase(std::unique(touched.begin(), touched.end()), touched.end());
+    for (size_t k = 0; k < touched.size(); ++k) posmap[(size_t)j * s + touched[k]] = (int32_t)k;
+    h->sidx.insert(h->sidx.end(), touched.begin(), touched.end());
+    h->sidx_off[j + 1] = (int64_t)h->sidx.size();
+  }
+  h->D.resize(p);
+  for (int j = 0; j < p; ++j) h->D[j] = h->d[j] + (h->sidx_off[j + 1] - h->sidx_off[j]);
+  h->host_rp = std::move(rp);
+  h->host_cl = std::move(cl);
+  h->host_av = std::move(av);
+  h->host_mv = std::move(mv);
+  h->host_posmap = std::move(posmap);
+}
+
+void do_upload(rfdd_handle *h) {
+  const int p = h->p;
+  const int64_t n = h->n, s = h->s, dsum = h->dsum;
+  auto &rp = h->host_rp;
+  auto &cl = h->host_cl;
+  auto &av = h->host_av;
+  auto &mv = h->host_mv;
+  auto &posmap = h->host_posmap;
+  cudaStream_t st = h->st;
+  upload(h->rowptr, rp, st);
+  upload(h->col, cl, st);
+  upload(h->aval, av, st);
+  upload(h->mval, mv, st);
+  upload(h->off_dev, h->off, st);
+  upload(h->sidx_dev, h->sidx, st);
+  upload(h->sidx_off_dev, h->sidx_off, st);
+  upload(h->posmap, posmap, st);
+  upload(h->iperm_dev, h->iperm, st);
+  h->status.alloc(sizeof(int));
+  RFDD_CUDA(cudaMemsetAsync(h->status.p, 0, sizeof(int), st));
+  RFDD_CUDA(cudaStreamSynchronize(st));
+  h->P.n = n;
+  h->P.nnz = h->nnz;
+  h->P.rowptr = h->rowptr.as<int64_t>();
+  h->P.col = h->col.as<int32_t>();
+  h->P.a = h->aval.as<double>();
+  h->P.m = h->mval.as<double>();
+  h->dd.p = p;
+  h->dd.dsum = dsum;
+  h->dd.s = s;
+  h->dd.off = h->off_dev.as<int64_t>();
+  h->dd.sidx = h->sidx_dev.as<int32_t>();
+  h->dd.sidx_off = h->sidx_off_dev.as<int64_t>();
+  h->dd.posmap = h->posmap.as<int32_t>();
+  // M_E != 0 iff some interior row has a nonzero M entry in an interface column
+  h->has_me = false;
+  for (int64_t r = 0; r < dsum && !h->has_me; ++r)
+    for (int64_t e = rp[r]; e < rp[r + 1]; ++e)
+      if (cl[e] >= dsum && mv[e] != 0.0) { h->has_me = true; break; }
+  rp.clear(); cl.clear(); av.clear(); mv.clear(); posmap.clear();
+  rp.shrink_to_fit(); cl.shrink_to_fit(); av.shrink_to_fit(); mv.shrink_to_fit(); posmap.shrink_to_fit();
+}
+
+// ------------------------------------------------------------------------------------
+// precision-dependent parts
+// ------------------------------------------------------------------------------------
+constexpr int NBO = 128;   // outer block of the factorisations and triangular solves
+
+size_t factor_bytes(const rfdd_handle *h, int nc, size_t scal) {
+  size_t e = 0;
+  for (int j = 0; j < h->p; ++j) e += (size_t)h->D[j] * h->D[j];
+  size_t b = (size_t)nc * e * scal;
+  b += (size_t)nc * h->s * h->s * scal * (h->opt.keep_schur ? 2 : 1);
+  b += (size_t)nc * (h->dsum + h->s) * sizeof(int);
+  return b;
+}
+
+template <typename Tf>
+void factor_impl(rfdd_handle *h) {
+  cudaStream_t st = h->st;
+  const int nc = h->nnodes, p = h->p;
+  const int64_t s = h->s;
+  // a2: bordered blocks for all (node, subdomain)
+  h->boff.assign((size_t)nc * p, 0);
+  int64_t tot = 0;
+  for (int l = 0; l < nc; ++l)
+    for (int j = 0; j < p; ++j) {
+      h->boff[(size_t)l * p + j] = tot;
+      tot += h->D[j] * h->D[j];
+    }
+  std::vector<int64_t> Doff(p + 1, 0);
+  for (int j = 0; j < p; ++j) Doff[j + 1] = Doff[j] + h->D[j];
+  h->fac.alloc((size_t)tot * sizeof(Tf));
+  upload(h->boff_dev, h->boff, st);
+  upload(h->Doff_dev, Doff, st);
+  h->pivBoff.assign((size_t)nc * p, 0);
+  int64_t pt = 0;
+  for (int l = 0; l < nc; ++l)
+    for (int j = 0; j < p; ++j) {
+      h->pivBoff[(size_t)l * p + j] = pt;
+      pt += h->d[j];
+    }
+  h->pivB.alloc((size_t)pt * sizeof(int));
+  Tf *base = h->fac.as<Tf>();
+  assemble_blocks<Tf>(st, h->P, h->dd, h->Doff_dev.as<int64_t>(), Doff[p], h->boff_dev.as<int64_t>(),
+                      h->z_dev.as<cx<double>>(), nc, base, true);
+  // a3 + a4: LU of the bordered blocks (pivots restricted to the B rows)
+  std::vector<LuItem<Tf>> items;
+  for (int l = 0; l < nc; ++l)
+    for (int j = 0; j < p; ++j) {
+      LuItem<Tf> it;
+      it.A = base + h->boff[(size_t)l * p + j];
+      it.piv = h->pivB.as<int>() + h->pivBoff[(size_t)l * p + j];
+      it.dp = (int)h->d[j];
+      it.D = (int)h->D[j];
+      it.ld = (int)h->D[j];
+      items.push_back(it);
+    }
+  lu_batched<Tf>(st, items, NBO, h->status.as<int>());
+  // a5: S(z) = C - z M_C + sum_j trailing_j, then LU
+  h->Sfac.alloc((size_t)nc * s * s * sizeof(Tf));
+  h->pivS.alloc((size_t)nc * s * sizeof(int));
+  Tf *S = h->Sfac.as<Tf>();
+  assemble_interface<Tf>(st, h->P, h->dd, h->z_dev.as<cx<double>>(), nc, S);
+  for (int j = 0; j < p; ++j) {
+    const int sj = (int)(h->sidx_off[j + 1] - h->sidx_off[j]);
+    scatter_schur<Tf>(st, h->dd, j, (int)h->d[j], sj, h->sidx_off[j], h->boff_dev.as<int64_t>(), base, nc, S);
+  }
+  if (h->opt.keep_schur) {
+    h->Skeep.alloc((size_t)nc * s * s * sizeof(Tf));
+    RFDD_CUDA(cudaMemcpyAsync(h->Skeep.p, S, (size_t)nc * s * s * sizeof(Tf), cudaMemcpyDeviceToDevice, st));
+  }
+  std::vector<LuItem<Tf>> sit;
+  for (int l = 0; l < nc; ++l) {
+    LuItem<Tf> it;
+    it.A = S + (int64_t)l * s * s;
+    it.piv = h->pivS.as<int>() + (int64_t)l * s;
+    it.dp = it.D = it.ld = (int)s;
+    sit.push_back(it);
+  }
+  lu_batched<Tf>(st, sit, NBO, h->status.as<int>());
+  sync_status(h, "factor");
+  h->have_factors = true;
+}
+
+// B_j(z_l) solves on a tall block F (n x m per node, stride fs): interior rows only
+template <typename Tf>
+void solve_B(rfdd_handle *h, Tf *F, int64_t ldf, int64_t fs, int64_t m, const std::vector<int> &nodes,
+             int64_t row_base_shift = 0) {
+  std::vector<SolveItem<Tf>> it;
+  Tf *base = h->fac.as<Tf>();
+  for (int l : nodes)
+    for (int j = 0; j < h->p; ++j) {
+      SolveItem<Tf> x;
+      x.LU = base + h->boff[(size_t)l * h->p + j];
+      x.piv = h->pivB.as<int>() + h->pivBoff[(size_t)l * h->p + j];
+      x.n = (int)h->d[j];
+      x.ld = (int)h->D[j];
+      x.X = F + (int64_t)l * fs + (h->off[j] - row_base_shift) * ldf;
+      x.ldx = (int)ldf;
+      x.ncols = (int)m;
+      it.push_back(x);
+    }
+  lu_solve_batched<Tf>(h->st, it, NBO);
+}
+
+template <typename Tf>
+void solve_S(rfdd_handle *h, Tf *G, int64_t ldg, int64_t gs, int64_t m, const std::vector<int> &nodes) {
+  std::vector<SolveItem<Tf>> it;
+  for (int l : nodes) {
+    SolveItem<Tf> x;
+    x.LU = h->Sfac.as<Tf>() + (int64_t)l * h->s * h->s;
+    x.piv = h->pivS.as<int>() + (int64_t)l * h->s;
+    x.n = (int)h->s;
+    x.ld = (int)h->s;
+    x.X = G + (int64_t)l * gs;
+    x.ldx = (int)ldg;
+    x.ncols = (int)m;
+    it.push_back(x);
+  }
+  lu_solve_batched<Tf>(h->st, it, NBO);
+}
+
+std::vector<int> all_nodes(const rfdd_handle *h) {
+  std::vector<int> v(h->nnodes);
+  std::iota(v.begin(), v.end(), 0);
+  return v;
+}
+
+// a6: W = scale * Re sum_l w_l S_l^{-1} X  (X, W: s x b FP64 device)
+template <typename Tf>
+void filter_impl(rfdd_handle *h, const double *X, double *W, int64_t b, double scale) {
+  const int64_t s = h->s;
+  const int nc = h->nnodes;
+  Buf rhs;
+  rhs.alloc((size_t)nc * s * b * sizeof(Tf));
+  real_to_complex<Tf>(h->st, X, rhs.as<Tf>(), s * b, nc, s * b);
+  solve_S<Tf>(h, rhs.as<Tf>(), b, s * b, b, all_nodes(h));
+  weighted_real_sum<Tf>(h->st, rhs.as<Tf>(), s * b, h->w_dev.as<cx<double>>(), nc, scale, W, s * b);
+}
+
+// DD resolvent (Eq. inv_dd2) in the factor precision for all nodes:
+// X_l = (A - z_l M)^{-1} R_l,  R, X: complex FP64, n x m per node (stride n*m).
+template <typename Tf>
+void dd_solve(rfdd_handle *h, const cx<double> *R, cx<double> *X, int64_t m, Buf &F, Buf &Ht) {
+  cudaStream_t st = h->st;
+  const int nc = h->nnodes;
+  const int64_t n = h->n, dsum = h->dsum, s = h->s;
+  const int64_t fs = n * m;
+  F.ensure((size_t)nc * fs * sizeof(Tf));
+  Ht.ensure((size_t)nc * std::max<int64_t>(dsum, 1) * m * sizeof(Tf));
+  Tf *f = F.as<Tf>(), *ht = Ht.as<Tf>();
+  convert<Tf, cx<double>>(st, R, f, nc * fs);
+  auto nodes = all_nodes(h);
+  solve_B<Tf>(h, f, m, fs, m, nodes);                                          // t = B^{-1} f
+  couple<Tf>(st, h->P, dsum, n, 0, dsum, h->z_dev.as<cx<double>>(), nc, f, m, fs, f + dsum * m, m, fs, m, -1.0,
+             true);                                                            // g' = g - E^T t
+  solve_S<Tf>(h, f + dsum * m, m, fs, m, nodes);                               // y = S^{-1} g'
+  couple<Tf>(st, h->P, 0, dsum, dsum, n, h->z_dev.as<cx<double>>(), nc, f + dsum * m, m, fs, ht, m, dsum * m, m, 1.0,
+             false);                                                           // h = E y
+  solve_B<Tf>(h, ht, m, dsum * m, m, nodes);                                   // B^{-1} h
+  for (int l = 0; l < nc; ++l) sub_inplace<Tf>(st, ht + l * dsum * m, f + l * fs, dsum * m);  // u = t - B^{-1}E y
+  convert<cx<double>, Tf>(st, f, X, nc * fs);
+}
+
+// Shifted solves with FP64 iterative refinement (Section 3.1 block inverse as the approximate
+// solver, FP64 sparse residuals): X_l = (A - z_l M)^{-1} V for all nodes; V real (n x m).
+template <typename Tf>
+int refined_solve(rfdd_handle *h, const double *V, cx<double> *X, int64_t m) {
+  cudaStream_t st = h->st;
+  const int nc = h->nnodes;
+  const int64_t n = h->n;
+  Buf Vc, Rr, Dx, F, Ht, nr, nx;
+  Vc.alloc((size_t)n * m * sizeof(cx<double>));
+  real_to_complex<cx<double>>(st, V, Vc.as<cx<double>>(), n * m, 1, 0);
+  dd_solve<Tf>(h, Vc.as<cx<double>>(), X, m, F, Ht);
+  const int irmax = std::is_same<Tf, cx<double>>::value ? std::min(1, h->opt.ir_max) : h->opt.ir_max;
+  Rr.alloc((size_t)nc * n * m * sizeof(cx<double>));
+  Dx.alloc((size_t)nc * n * m * sizeof(cx<double>));
+  nr.alloc((size_t)nc * m * sizeof(double));
+  nx.alloc((size_t)nc * m * sizeof(double));
+  std::vector<double> hr(nc * m), hx(nc * m);
+  int steps = 0;
+  for (int it = 0; it <= irmax; ++it) {
+    shifted_residual(st, h->P, h->z_dev.as<cx<double>>(), nc, Vc.as<cx<double>>(), 0, X, Rr.as<cx<double>>(), n * m,
+                     m);
+    col_norms2_c64(st, Rr.as<cx<double>>(), n, m, nc, n * m, nr.as<double>());
+    col_norms2_c64(st, X, n, m, nc, n * m, nx.as<double>());
+    RFDD_CUDA(cudaMemcpyAsync(hr.data(), nr.p, hr.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    RFDD_CUDA(cudaMemcpyAsync(hx.data(), nx.p, hx.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    RFDD_CUDA(cudaStreamSynchronize(st));
+    bool ok = true;
+    for (int l = 0; l < nc && ok; ++l) {
+      const double zn = std::sqrt(h->z[l].re * h->z[l].re + h->z[l].im * h->z[l].im);
+      const double scale = (h->normA + zn * h->normM);
+      for (int64_t c = 0; c < m; ++c)
+        if (std::sqrt(hr[l * m + c]) > 1e-14 * scale * std::sqrt(hx[l * m + c]) + 1e-300) { ok = false; break; }
+    }
+    if (ok || it == irmax) break;
+    dd_solve<Tf>(h, Rr.as<cx<double>>(), Dx.as<cx<double>>(), m, F, Ht);
+    axpy_c64(st, Dx.as<cx<double>>(), X, (int64_t)nc * n * m);
+    ++steps;
+  }
+  return steps;
+}
+
+// ------------------------------------------------------------------------------------
+// M-orthonormal Rayleigh-Ritz on range(Y) for a tall FP64 block Y (n x k, row-major):
+// Gram G = Y^T M Y and K = Y^T A Y, diagonal scaling, eigen-decomposition of the scaled Gram
+// with pruning of directions below drop * max, projected H, and its eigenpairs.  Returns all
+// Ritz values (ascending) and, for the selected sorted indices, the coefficient block
+// C (k x nsel) such that the Ritz vectors are Y C.
+// ------------------------------------------------------------------------------------
+struct RRout {
+  std::vector<double> theta;  // all Ritz values (ascending)
+  int64_t r = 0;              // dimension kept
+};
+
+RRout rayleigh_ritz_coeffs(rfdd_handle *h, const double *Y, int64_t k, double drop, bool gram_fp32,
+                           const std::function<std::vector<int>(const std::vector<double> &)> &select,
+                           Buf &Cout, std::vector<int> &sel_out) {
+  cudaStream_t st = h->st;
+  const int64_t n = h->n;
+  Buf MY, AY, G, K;
+  MY.alloc((size_t)n * k * sizeof(double));
+  AY.alloc((size_t)n * k * sizeof(double));
+  spmm_f64(st, h->P, 0, n, 0, n, 0.0, 1.0, Y, k, MY.as<double>(), k, k, false);
+  spmm_f64(st, h->P, 0, n, 0, n, 1.0, 0.0, Y, k, AY.as<double>(), k, k, false);
+  G.alloc((size_t)k * k * sizeof(double));
+  K.alloc((size_t)k * k * sizeof(double));
+  if (gram_fp32) {
+    Buf Yf, MYf, AYf, Gf;
+    Yf.alloc((size_t)n * k * sizeof(float));
+    MYf.alloc((size_t)n * k * sizeof(float));
+    AYf.alloc((size_t)n * k * sizeof(float));
+    Gf.alloc((size_t)2 * k * k * sizeof(float));
+    convert<float, double>(st, Y, Yf.as<float>(), n * k);
+    convert<float, double>(st, MY.as<double>(), MYf.as<float>(), n * k);
+    convert<float, double>(st, AY.as<double>(), AYf.as<float>(), n * k);
+    std::vector<GemmItem<float>> g = {
+        {Yf.as<float>(), MYf.as<float>(), Gf.as<float>(), (int)k, (int)k, (int)n, (int)k, (int)k, (int)k},
+        {Yf.as<float>(), AYf.as<float>(), Gf.as<float>() + k * k, (int)k, (int)k, (int)n, (int)k, (int)k, (int)k}};
+    gemm_batched<float>(st, g, true, false, 1.0, 0.0);
+    convert<double, float>(st, Gf.as<float>(), G.as<double>(), k * k);
+    convert<double, float>(st, Gf.as<float>() + k * k, K.as<double>(), k * k);
+  } else {
+    std::vector<GemmItem<double>> g = {
+        {Y, MY.as<double>(), G.as<double>(), (int)k, (int)k, (int)n, (int)k, (int)k, (int)k},
+        {Y, AY.as<double>(), K.as<double>(), (int)k, (int)k, (int)n, (int)k, (int)k, (int)k}};
+    gemm_batched<double>(st, g, true, false, 1.0, 0.0);
+  }
+  MY.release();
+  AY.release();
+  // symmetrise-free: G and K are exactly symmetric up to rounding; the eigensolver reads the
+  // full matrix.  Scale to unit diagonal.
+  Buf dsc;
+  dsc.alloc((size_t)k * sizeof(double));
+  inv_sqrt_diag(st, G.as<double>(), k, dsc.as<double>());
+  scale_sym(st, G.as<double>(), k, dsc.as<double>());
+  scale_sym(st, K.as<double>(), k, dsc.as<double>());
+  // eigen-decomposition of the Gram matrix
+  Buf ed, ee, et, ew, eZ, ep;
+  ed.alloc(k * sizeof(double));
+  ee.alloc(k * sizeof(double));
+  et.alloc(k * sizeof(double));
+  ew.alloc(k * sizeof(double));
+  eZ.alloc((size_t)k * k * sizeof(double));
+  ep.alloc(k * sizeof(int));
+  SymItem gi{G.as<double>(), (int)k, (int)k, ed.as<double>(), ee.as<double>(), et.as<double>(), ew.as<double>(),
+             eZ.as<double>(), ep.as<int>()};
+  sym_eig_values(st, {gi}, h->status.as<int>());
+  std::vector<double> lam(k);
+  RFDD_CUDA(cudaMemcpyAsync(lam.data(), ed.p, k * sizeof(double), cudaMemcpyDeviceToHost, st));
+  RFDD_CUDA(cudaStreamSynchronize(st));
+  const double lmax = lam.empty() ? 0.0 : lam.back();
+  std::vector<int> keep;
+  for (int64_t q = 0; q < k; ++q)
+    if (lam[q] > drop * lmax && lmax > 0) keep.push_back((int)q);
+  const int64_t r = (int64_t)keep.size();
+  RFDD_REQUIRE(r > 0, RFDD_ESINGULAR, "Rayleigh-Ritz: basis has no independent direction");
+  Buf keep_dev, Ut, C1t, f;
+  upload(keep_dev, keep, st);
+  Ut.alloc((size_t)r * k * sizeof(double));
+  sym_eig_vectors(st, {BackItem{&gi, keep_dev.as<int>(), (int)r, Ut.as<double>(), (int)k}});
+  f.alloc(r * sizeof(double));
+  Buf lamk;
+  {
+    std::vector<double> lk(r);
+    for (int64_t q = 0; q < r; ++q) lk[q] = lam[keep[q]];
+    upload(lamk, lk, st);
+  }
+  inv_sqrt_vec(st, lamk.as<double>(), r, f.as<double>());
+  C1t.alloc((size_t)r * k * sizeof(double));
+  scale_rows_cols(st, Ut.as<double>(), r, k, dsc.as<double>(), f.as<double>(), C1t.as<double>());  // C1^T (r x k)
+  // H = C1^T K C1
+  Buf T1, H;
+  T1.alloc((size_t)r * k * sizeof(double));
+  H.alloc((size_t)r * r * sizeof(double));
+  gemm_batched<double>(st, {{C1t.as<double>(), K.as<double>(), T1.as<double>(), (int)r, (int)k, (int)k, (int)k,
+                             (int)k, (int)k}},
+                       false, false, 1.0, 0.0);
+  gemm_batched<double>(st, {{T1.as<double>(), C1t.as<double>(), H.as<double>(), (int)r, (int)r, (int)k, (int)k,
+                             (int)k, (int)r}},
+                       false, true, 1.0, 0.0);
+  K.release();
+  G.release();
+  Buf hd, he, ht, hw, hZ, hp;
+  hd.alloc(r * sizeof(double));
+  he.alloc(r * sizeof(double));
+  ht.alloc(r * sizeof(double));
+  hw.alloc(r * sizeof(double));
+  hZ.alloc((size_t)r * r * sizeof(double));
+  hp.alloc(r * sizeof(int));
+  SymItem hi{H.as<double>(), (int)r, (int)r, hd.as<double>(), he.as<double>(), ht.as<double>(), hw.as<double>(),
+             hZ.as<double>(), hp.as<int>()};
+  sym_eig_values(st, {hi}, h->status.as<int>());
+  RRout out;
+  out.r = r;
+  out.theta.resize(r);
+  RFDD_CUDA(cudaMemcpyAsync(out.theta.data(), hd.p, r * sizeof(double), cudaMemcpyDeviceToHost, st));
+  RFDD_CUDA(cudaStreamSynchronize(st));
+  sel_out = select(out.theta);
+  const int64_t ns = (int64_t)sel_out.size();
+  if (ns > 0) {
+    Buf sel_dev, Yt;
+    upload(sel_dev, sel_out, st);
+    Yt.alloc((size_t)ns * r * sizeof(double));
+    sym_eig_vectors(st, {BackItem{&hi, sel_dev.as<int>(), (int)ns, Yt.as<double>(), (int)r}});
+    // C = C1 Y_sel (k x ns): C[k][q] = sum_t C1t[t][k] * Yt[q][t]
+    Cout.alloc((size_t)k * ns * sizeof(double));
+    gemm_batched<double>(st, {{C1t.as<double>(), Yt.as<double>(), Cout.as<double>(), (int)k, (int)ns, (int)r, (int)k,
+                               (int)r, (int)ns}},
+                         true, true, 1.0, 0.0);
+  }
+  sync_status(h, "rayleigh-ritz");
+  return out;
+}
+
+// Ritz values (sorted) -> the m indices nearest [alpha, beta] (distance 0 inside), sorted
+std::vector<int> select_nearest(const std::vector<double> &th, double a, double b, int64_t m) {
+  std::vector<int> idx(th.size());
+  std::iota(idx.begin(), idx.end(), 0);
+  const double c = 0.5 * (a + b);
+  std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
+    const double dx = std::max(std::max(a - th[x], th[x] - b), 0.0);
+    const double dy = std::max(std::max(a - th[y], th[y] - b), 0.0);
+    if (dx != dy) return dx < dy;
+    return std::fabs(th[x] - c) < std::fabs(th[y] - c);
+  });
+  if ((int64_t)idx.size() > m) idx.resize(m);
+  std::sort(idx.begin(), idx.end());
+  return idx;
+}
+
+// ------------------------------------------------------------------------------------
+// a7: block Lanczos on F (Alg. 2) with CGS2 against all previous blocks
+// ------------------------------------------------------------------------------------
+template <typename Tf>
+void lanczos_impl(rfdd_handle *h) {
+  cudaStream_t st = h->st;
+  const int64_t s = h->s;
+  const int64_t b = std::max<int64_t>(1, std::min<int64_t>(h->opt.block, s));
+  const int64_t qld = ((s + b - 1) / b) * b;
+  h->qcap = qld;
+  h->Q.alloc((size_t)s * qld * sizeof(double));
+  double *Q = h->Q.as<double>();
+  RFDD_CUDA(cudaMemsetAsync(Q, 0, (size_t)s * qld * sizeof(double), st));
+  Buf W, Xb, Cb, Gb, Rinv, dead, Bprev, Amu, tmp;
+  W.alloc((size_t)s * b * sizeof(double));
+  Xb.alloc((size_t)s * b * sizeof(double));
+  Cb.alloc((size_t)qld * b * sizeof(double));
+  Gb.alloc((size_t)b * b * sizeof(double));
+  Rinv.alloc((size_t)b * b * sizeof(double));
+  dead.alloc((size_t)b * sizeof(int));
+  Bprev.alloc((size_t)b * b * sizeof(double));
+  Amu.alloc((size_t)b * b * sizeof(double));
+  tmp.alloc((size_t)s * b * sizeof(double));
+  std::vector<int> hdead(b);
+  uint64_t stream_id = 0;
+  auto orthonormalize = [&](double *Wp, int64_t ncols_prev) {
+    // CGS2 against Q[:, 0:ncols_prev], then CholQR twice; dead columns -> fresh random vectors
+    for (int attempt = 0; attempt < 4; ++attempt) {
+      for (int pass = 0; pass < 2; ++pass) {
+        if (ncols_prev > 0) {
+          gemm_batched<double>(st, {{Q, Wp, Cb.as<double>(), (int)ncols_prev, (int)b, (int)s, (int)qld, (int)b,
+                                     (int)b}},
+                               true, false, 1.0, 0.0);
+          gemm_batched<double>(st, {{Q, Cb.as<double>(), Wp, (int)s, (int)b, (int)ncols_prev, (int)qld, (int)b,
+                                     (int)b}},
+                               false, false, -1.0, 1.0);
+        }
+      }
+      bool any_dead = false;
+      for (int q = 0; q < 2; ++q) {
+        gemm_batched<double>(st, {{Wp, Wp, Gb.as<double>(), (int)b, (int)b, (int)s, (int)b, (int)b, (int)b}}, true,
+                             false, 1.0, 0.0);
+        chol_inv_batched(st, {CholItem{Gb.as<double>(), Rinv.as<double>(), dead.as<int>(), (int)b}}, 1e-24);
+        gemm_batched<double>(st, {{Wp, Rinv.as<double>(), tmp.as<double>(), (int)s, (int)b, (int)b, (int)b, (int)b,
+                                   (int)b}},
+                             false, false, 1.0, 0.0);
+        RFDD_CUDA(cudaMemcpyAsync(Wp, tmp.p, (size_t)s * b * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        RFDD_CUDA(cudaMemcpyAsync(hdead.data(), dead.p, b * sizeof(int), cudaMemcpyDeviceToHost, st));
+        RFDD_CUDA(cudaStreamSynchronize(st));
+        for (int c = 0; c < b; ++c) any_dead |= hdead[c] != 0;
+        if (any_dead) break;
+        if (ncols_prev > 0 && q == 0) {
+          // one more projection pass after normalisation ("twice is enough")
+          gemm_batched<double>(st, {{Q, Wp, Cb.as<double>(), (int)ncols_prev, (int)b, (int)s, (int)qld, (int)b,
+                                     (int)b}},
+                               true, false, 1.0, 0.0);
+          gemm_batched<double>(st, {{Q, Cb.as<double>(), Wp, (int)s, (int)b, (int)ncols_prev, (int)qld, (int)b,
+                                     (int)b}},
+                               false, false, -1.0, 1.0);
+        }
+      }
+      if (!any_dead) return;
+      // breakdown (Alg. 2 line 9): replace the dead columns by fresh random vectors
+      Buf fresh;
+      fresh.alloc((size_t)s * b * sizeof(double));
+      counter_uniform_dev(st, h->opt.seed, 1000 + (++stream_id), fresh.as<double>(), s * b);
+      std::vector<double> hw((size_t)s * b), hf((size_t)s * b);
+      RFDD_CUDA(cudaMemcpyAsync(hw.data(), Wp, hw.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+      RFDD_CUDA(cudaMemcpyAsync(hf.data(), fresh.p, hf.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+      RFDD_CUDA(cudaStreamSynchronize(st));
+      for (int64_t i = 0; i < s; ++i)
+        for (int c = 0; c < b; ++c)
+          if (hdead[c]) hw[i * b + c] = hf[i * b + c];
+      RFDD_CUDA(cudaMemcpyAsync(Wp, hw.data(), hw.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    }
+    throw Error(RFDD_ESINGULAR, "lanczos: could not extend the basis");
+  };
+  // start block (Alg. 2 line 0)
+  counter_uniform_dev(st, h->opt.seed, 0, W.as<double>(), s * b);
+  orthonormalize(W.as<double>(), 0);
+  copy_rows_f64(st, W.as<double>(), b, Q, qld, s, b);
+  h->traces.clear();
+  double trace = 0.0, last_check = 0.0;
+  const int check_every = (int)std::max<int64_t>(1, (10 + b - 1) / b);
+  int64_t nblk = 0;
+  std::vector<double> ha(b * b);
+  while (true) {
+    double *Qmu = Q + nblk * b;
+    copy_rows_f64(st, Qmu, qld, Xb.as<double>(), b, s, b);
+    filter_impl<Tf>(h, Xb.as<double>(), W.as<double>(), b, 1.0);  // line 2: F q
+    if (nblk > 0) {  // - Q_{mu-1} B_mu^T
+      gemm_batched<double>(st, {{Q + (nblk - 1) * b, Bprev.as<double>(), W.as<double>(), (int)s, (int)b, (int)b,
+                                 (int)qld, (int)b, (int)b}},
+                           false, true, -1.0, 1.0);
+    }
+    // line 3: A_mu = Q_mu^T W
+    gemm_batched<double>(st, {{Xb.as<double>(), W.as<double>(), Amu.as<double>(), (int)b, (int)b, (int)s, (int)b,
+                               (int)b, (int)b}},
+                         true, false, 1.0, 0.0);
+    RFDD_CUDA(cudaMemcpyAsync(ha.data(), Amu.p, b * b * sizeof(double), cudaMemcpyDeviceToHost, st));
+    RFDD_CUDA(cudaStreamSynchronize(st));
+    for (int c = 0; c < b; ++c) trace += ha[c * b + c];
+    h->traces.push_back(trace);
+    ++nblk;
+    if ((nblk + 1) * b > s) break;  // the next block would not fit in R^s (mu <= s)
+    // lines 4-12: orthogonalise against all previous blocks, normalise
+    // B_{mu+1} = Q_{mu+1}^T W (upper triangular factor of the block QR)
+    RFDD_CUDA(cudaMemcpyAsync(tmp.p, W.p, (size_t)s * b * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    Buf Wraw;
+    Wraw.alloc((size_t)s * b * sizeof(double));
+    RFDD_CUDA(cudaMemcpyAsync(Wraw.p, W.p, (size_t)s * b * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    orthonormalize(W.as<double>(), nblk * b);
+    gemm_batched<double>(st, {{W.as<double>(), Wraw.as<double>(), Bprev.as<double>(), (int)b, (int)b, (int)s, (int)b,
+                               (int)b, (int)b}},
+                         true, false, 1.0, 0.0);
+    copy_rows_f64(st, W.as<double>(), b, Q + nblk * b, qld, s, b);
+    if (nblk % check_every == 0) {  // line 13
+      if (std::fabs(trace - last_check) <= h->opt.lanczos_tol * std::fabs(trace)) break;
+      last_check = trace;
+    }
+  }
+  h->mu = nblk * b;
+  RFDD_CUDA(cudaStreamSynchronize(st));
+}
+
+// ------------------------------------------------------------------------------------
+// a8: interior basis and Z (Eq. trabala, trabala2, z)
+// ------------------------------------------------------------------------------------
+template <typename Tr>
+void interior_impl(rfdd_handle *h, double sigma) {
+  cudaStream_t st = h->st;
+  const int p = h->p;
+  const int64_t n = h->n, dsum = h->dsum, s = h->s, mu = h->mu;
+  const int psi = std::max(1, h->opt.psi);
+  RFDD_REQUIRE(mu > 0, RFDD_ESTATE, "interior: run the Lanczos step first");
+  h->sigma_used = sigma;
+  // B_sigma^(j) dense (real) and its LU
+  std::vector<int64_t> doff(p + 1, 0), boffr(p, 0);
+  int64_t tot = 0;
+  for (int j = 0; j < p; ++j) {
+    doff[j + 1] = doff[j] + h->d[j];
+    boffr[j] = tot;
+    tot += h->d[j] * h->d[j];
+  }
+  Buf Bs, doff_dev, boffr_dev, zs, pivs;
+  Bs.alloc((size_t)tot * sizeof(Tr));
+  upload(doff_dev, doff, st);
+  upload(boffr_dev, boffr, st);
+  std::vector<cx<double>> zsig = {cx<double>(sigma, 0.0)};
+  upload(zs, zsig, st);
+  pivs.alloc((size_t)dsum * sizeof(int));
+  // assemble_blocks without border: D_j = d_j, and the same row mapping
+  assemble_blocks<Tr>(st, h->P, h->dd, doff_dev.as<int64_t>(), dsum, boffr_dev.as<int64_t>(), zs.as<cx<double>>(), 1,
+                      Bs.as<Tr>(), false);
+  std::vector<LuItem<Tr>> items;
+  for (int j = 0; j < p; ++j) {
+    LuItem<Tr> it;
+    it.A = Bs.as<Tr>() + boffr[j];
+    it.piv = pivs.as<int>() + h->off[j];
+    it.dp = it.D = it.ld = (int)h->d[j];
+    items.push_back(it);
+  }
+  lu_batched<Tr>(st, items, NBO, h->status.as<int>());
+  sync_status(h, "interior LU");
+  auto solve_Bs = [&](double *X, int64_t ldx, int64_t m) {  // X (dsum x m FP64, all subdomains) <- B_sigma^{-1} X
+    Buf t;
+    t.alloc((size_t)dsum * m * sizeof(Tr));
+    convert<Tr, double>(st, X, t.as<Tr>(), dsum * m);
+    std::vector<SolveItem<Tr>> si;
+    for (int j = 0; j < p; ++j) {
+      SolveItem<Tr> x;
+      x.LU = Bs.as<Tr>() + boffr[j];
+      x.piv = pivs.as<int>() + h->off[j];
+      x.n = x.ld = (int)h->d[j];
+      x.X = t.as<Tr>() + h->off[j] * m;
+      x.ldx = (int)m;
+      x.ncols = (int)m;
+      si.push_back(x);
+    }
+    lu_solve_batched<Tr>(st, si, NBO);
+    convert<double, Tr>(st, t.as<Tr>(), X, dsum * m);
+    (void)ldx;
+  };
+  // V_j: block shift-invert subspace iteration on B_sigma^{-1} M_B with M_B-orthonormalisation,
+  // then a Rayleigh-Ritz step that keeps the nev_B eigenvectors with the smallest |delta - sigma|
+  std::vector<int64_t> nvb(p), mb(p), voff(p + 1, 0);
+  int64_t mbmax = 0;
+  for (int j = 0; j < p; ++j) {
+    nvb[j] = std::min<int64_t>(h->opt.nev_b, h->d[j]);
+    mb[j] = std::min<int64_t>(h->d[j], nvb[j] + std::max<int64_t>(8, nvb[j] / 5));
+    mbmax = std::max(mbmax, mb[j]);
+    voff[j + 1] = voff[j] + nvb[j];
+  }
+  h->kappa = voff[p];
+  // one tall block X (dsum x mbmax): subdomain j uses rows off_j.. and its first mb_j columns
+  const int64_t mw = mbmax;
+  Buf X, Y, G, Rinv, dead, T;
+  X.alloc((size_t)dsum * mw * sizeof(double));
+  Y.alloc((size_t)dsum * mw * sizeof(double));
+  T.alloc((size_t)dsum * mw * sizeof(double));
+  G.alloc((size_t)p * mw * mw * sizeof(double));
+  Rinv.alloc((size_t)p * mw * mw * sizeof(double));
+  dead.alloc((size_t)p * mw * sizeof(int));
+  RFDD_CUDA(cudaMemsetAsync(T.p, 0, (size_t)dsum * mw * sizeof(double), st));
+  counter_uniform_dev(st, h->opt.seed, 500, X.as<double>(), dsum * mw);
+  auto m_orth = [&](double *Xp) {  // M_B-orthonormalise each subdomain block (CholQR, twice)
+    for (int pass = 0; pass < 2; ++pass) {
+      spmm_f64(st, h->P, 0, dsum, 0, dsum, 0.0, 1.0, Xp, mw, Y.as<double>(), mw, mw, false);
+      std::vector<GemmItem<double>> g;
+      std::vector<CholItem> ch;
+      for (int j = 0; j < p; ++j) {
+        g.push_back({Xp + h->off[j] * mw, Y.as<double>() + h->off[j] * mw, G.as<double>() + (int64_t)j * mw * mw,
+                     (int)mb[j], (int)mb[j], (int)h->d[j], (int)mw, (int)mw, (int)mb[j]});
+        ch.push_back({G.as<double>() + (int64_t)j * mw * mw, Rinv.as<double>() + (int64_t)j * mw * mw,
+                      dead.as<int>() + j * mw, (int)mb[j]});
+      }
+      gemm_batched<double>(st, g, true, false, 1.0, 0.0);
+      chol_inv_batched(st, ch, 1e-28);
+      std::vector<GemmItem<double>> g2;
+      for (int j = 0; j < p; ++j)
+        g2.push_back({Xp + h->off[j] * mw, Rinv.as<double>() + (int64_t)j * mw * mw, T.as<double>() + h->off[j] * mw,
+                      (int)h->d[j], (int)mb[j], (int)mb[j], (int)mw, (int)mb[j], (int)mw});
+      gemm_batched<double>(st, g2, false, false, 1.0, 0.0);
+      RFDD_CUDA(cudaMemcpyAsync(Xp, T.p, (size_t)dsum * mw * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
+  };
+  m_orth(X.as<double>());
+  const int iters = std::max(1, h->opt.subspace_iters);
+  for (int it = 0; it < iters; ++it) {
+    spmm_f64(st, h->P, 0, dsum, 0, dsum, 0.0, 1.0, X.as<double>(), mw, Y.as<double>(), mw, mw, false);  // M_B X
+    solve_Bs(Y.as<double>(), mw, mw);
+    RFDD_CUDA(cudaMemcpyAsync(X.p, Y.p, (size_t)dsum * mw * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    m_orth(X.as<double>());
+  }
+  // Rayleigh-Ritz for (B_sigma, M_B) on span(X_j): H_j = X_j^T B_sigma X_j (X_j is M_B-orthonormal)
+  spmm_f64(st, h->P, 0, dsum, 0, dsum, 1.0, -sigma, X.as<double>(), mw, Y.as<double>(), mw, mw, false);
+  {
+    std::vector<GemmItem<double>> g;
+    for (int j = 0; j < p; ++j)
+      g.push_back({X.as<double>() + h->off[j] * mw, Y.as<double>() + h->off[j] * mw,
+                   G.as<double>() + (int64_t)j * mw * mw, (int)mb[j], (int)mb[j], (int)h->d[j], (int)mw, (int)mw,
+                   (int)mb[j]});
+    gemm_batched<double>(st, g, true, false, 1.0, 0.0);
+  }
+  Buf ed, ee, et, ew, eZ, ep;
+  ed.alloc((size_t)p * mw * sizeof(double));
+  ee.alloc((size_t)p * mw * sizeof(double));
+  et.alloc((size_t)p * mw * sizeof(double));
+  ew.alloc((size_t)p * mw * sizeof(double));
+  eZ.alloc((size_t)p * mw * mw * sizeof(double));
+  ep.alloc((size_t)p * mw * sizeof(int));
+  std::vector<SymItem> si;
+  for (int j = 0; j < p; ++j)
+    si.push_back({G.as<double>() + (int64_t)j * mw * mw, (int)mb[j], (int)mb[j], ed.as<double>() + j * mw,
+                  ee.as<double>() + j * mw, et.as<double>() + j * mw, ew.as<double>() + j * mw,
+                  eZ.as<double>() + (int64_t)j * mw * mw, ep.as<int>() + j * mw});
+  sym_eig_values(st, si, h->status.as<int>());
+  std::vector<double> ev((size_t)p * mw);
+  RFDD_CUDA(cudaMemcpyAsync(ev.data(), ed.p, ev.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  RFDD_CUDA(cudaStreamSynchronize(st));
+  std::vector<int> sel_all;
+  std::vector<int64_t> sel_off(p + 1, 0);
+  for (int j = 0; j < p; ++j) {
+    std::vector<int> idx(mb[j]);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(),
+                     [&](int a, int b) { return std::fabs(ev[j * mw + a]) < std::fabs(ev[j * mw + b]); });
+    idx.resize(nvb[j]);
+    std::sort(idx.begin(), idx.end());
+    sel_all.insert(sel_all.end(), idx.begin(), idx.end());
+    sel_off[j + 1] = (int64_t)sel_all.size();
+  }
+  Buf sel_dev, Gt;
+  upload(sel_dev, sel_all, st);
+  Gt.alloc((size_t)p * mw * mw * sizeof(double));
+  std::vector<BackItem> bi;
+  for (int j = 0; j < p; ++j)
+    bi.push_back({&si[j], sel_dev.as<int>() + sel_off[j], (int)nvb[j], Gt.as<double>() + (int64_t)j * mw * mw,
+                  (int)mb[j]});
+  sym_eig_vectors(st, bi);
+  // Z = [blockdiag(V_j) | -Sigma^(psi) | Gamma^(psi)] (n x k), interface rows [0 | Q 0 | 0]
+  const bool with_gamma = h->has_me;
+  const int64_t kz = h->kappa + (int64_t)psi * mu * (with_gamma ? 2 : 1);
+  h->kz = kz;
+  h->Zb.alloc((size_t)n * kz * sizeof(double));
+  double *Z = h->Zb.as<double>();
+  RFDD_CUDA(cudaMemsetAsync(Z, 0, (size_t)n * kz * sizeof(double), st));
+  {
+    // V_j = X_j * Gt_j^T  (d_j x nvb_j) into Z rows off_j, columns voff_j
+    std::vector<GemmItem<double>> g;
+    for (int j = 0; j < p; ++j)
+      g.push_back({X.as<double>() + h->off[j] * mw, Gt.as<double>() + (int64_t)j * mw * mw, Z + h->off[j] * kz + voff[j],
+                   (int)h->d[j], (int)nvb[j], (int)mb[j], (int)mw, (int)mb[j], (int)kz});
+    gemm_batched<double>(st, g, false, true, 1.0, 0.0);
+  }
+  X.release();
+  Y.release();
+  T.release();
+  // Phi = (E - sigma M_E) Q, Psi = M_E Q  (all interior rows, d x mu)
+  Buf Phi, Psi;
+  Phi.alloc((size_t)dsum * mu * sizeof(double));
+  spmm_f64(st, h->P, 0, dsum, dsum, n, 1.0, -sigma, h->Q.as<double>(), h->qcap, Phi.as<double>(), mu, mu, false);
+  if (with_gamma) {
+    Psi.alloc((size_t)dsum * mu * sizeof(double));
+    spmm_f64(st, h->P, 0, dsum, dsum, n, 0.0, 1.0, h->Q.as<double>(), h->qcap, Psi.as<double>(), mu, mu, false);
+  }
+  Buf tmp;
+  tmp.alloc((size_t)dsum * mu * sizeof(double));
+  for (int chain = 0; chain < (with_gamma ? 2 : 1); ++chain) {
+    double *Xc = chain == 0 ? Phi.as<double>() : Psi.as<double>();
+    const double sign = chain == 0 ? -1.0 : 1.0;
+    const int64_t col0 = h->kappa + (chain == 0 ? 0 : (int64_t)psi * mu);
+    for (int t = 0; t < psi; ++t) {
+      if (t > 0) {
+        spmm_f64(st, h->P, 0, dsum, 0, dsum, 0.0, 1.0, Xc, mu, tmp.as<double>(), mu, mu, false);  // M_B X
+        RFDD_CUDA(cudaMemcpyAsync(Xc, tmp.p, (size_t)dsum * mu * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      }
+      solve_Bs(Xc, mu, mu);
+      // Z[0:dsum, col0 + t*mu : +mu] = sign * Xc
+      RFDD_CUDA(cudaMemcpyAsync(tmp.p, Xc, (size_t)dsum * mu * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      if (sign < 0) {
+        Buf zero;
+        zero.alloc((size_t)dsum * mu * sizeof(double));
+        RFDD_CUDA(cudaMemsetAsync(zero.p, 0, (size_t)dsum * mu * sizeof(double), st));
+        sub_inplace<double>(st, Xc, zero.as<double>(), dsum * mu);
+        copy_rows_f64(st, zero.as<double>(), mu, Z + col0 + t * mu, kz, dsum, mu);
+      } else {
+        copy_rows_f64(st, Xc, mu, Z + col0 + t * mu, kz, dsum, mu);
+      }
+    }
+  }
+  // interface rows: Q under the first mu columns of the Sigma block
+  copy_rows_f64(st, h->Q.as<double>(), h->qcap, Z + dsum * kz + h->kappa, kz, s, mu);
+  sync_status(h, "interior");
+}
+
+// ------------------------------------------------------------------------------------
+// a9 + a10
+// ------------------------------------------------------------------------------------
+struct SolveState {
+  double *X = nullptr;
+};
+
+template <typename Tf>
+void rr_on_Z(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
+  cudaStream_t st = h->st;
+  const int64_t n = h->n, kz = h->kz;
+  Buf C;
+  std::vector<int> sel;
+  int64_t m_sel = 0;
+  const double drop = is_mixed(h) ? 1e-10 : 1e-12;
+  RRout rr = rayleigh_ritz_coeffs(
+      h, h->Zb.as<double>(), kz, drop, is_mixed(h),
+      [&](const std::vector<double> &th) {
+        int64_t nin = 0;
+        for (double t : th) nin += (t >= alpha && t <= beta);
+        const int64_t m = std::min<int64_t>((int64_t)th.size(),
+                                            nin + std::max<int64_t>((int64_t)std::ceil(h->opt.guard_frac * nin),
+                                                                    h->opt.min_guard));
+        m_sel = m;
+        return select_nearest(th, alpha, beta, m);
+      },
+      C, sel);
+  h->rr_theta = rr.theta;
+  h->m0 = (int64_t)sel.size();
+  h->X0.alloc((size_t)n * std::max<int64_t>(1, h->m0) * sizeof(double));
+  if (h->m0 > 0)
+    gemm_batched<double>(st, {{h->Zb.as<double>(), C.as<double>(), h->X0.as<double>(), (int)n, (int)h->m0, (int)kz,
+                               (int)kz, (int)h->m0, (int)h->m0}},
+                         false, false, 1.0, 0.0);
+  if (res) {
+    res->pre_evals.clear();
+    for (double t : rr.theta)
+      if (t >= alpha && t <= beta) res->pre_evals.push_back(t);
+    res->info.k = rr.r;
+  }
+  RFDD_CUDA(cudaStreamSynchronize(st));
+}
+
+template <typename Tf>
+void complete(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
+  cudaStream_t st = h->st;
+  const int64_t n = h->n;
+  const int nc = h->nnodes;
+  int64_t m = h->m0;
+  Buf X;
+  X.alloc((size_t)n * m * sizeof(double));
+  RFDD_CUDA(cudaMemcpyAsync(X.p, h->X0.p, (size_t)n * m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  // residuals of the RF-DDES Ritz pairs before completion (diagnostic)
+  auto residuals_of = [&](const double *Xp, int64_t mm, const std::vector<double> &th, std::vector<double> &out) {
+    Buf AX, MX, thd, rs;
+    AX.alloc((size_t)n * mm * sizeof(double));
+    MX.alloc((size_t)n * mm * sizeof(double));
+    spmm_f64(st, h->P, 0, n, 0, n, 1.0, 0.0, Xp, mm, AX.as<double>(), mm, mm, false);
+    spmm_f64(st, h->P, 0, n, 0, n, 0.0, 1.0, Xp, mm, MX.as<double>(), mm, mm, false);
+    upload(thd, th, st);
+    rs.alloc(mm * sizeof(double));
+    ritz_residuals(st, AX.as<double>(), MX.as<double>(), thd.as<double>(), n, mm, rs.as<double>());
+    out.resize(mm);
+    RFDD_CUDA(cudaMemcpyAsync(out.data(), rs.p, mm * sizeof(double), cudaMemcpyDeviceToHost, st));
+    RFDD_CUDA(cudaStreamSynchronize(st));
+  };
+  {
+    // Ritz values of the selected X0 columns (sorted-by-value selection of rr_theta)
+    std::vector<double> th0 = h->rr_theta;
+    std::vector<int> idx = select_nearest(th0, alpha, beta, m);
+    std::vector<double> ths;
+    for (int i : idx) ths.push_back(th0[i]);
+    std::vector<double> r0;
+    if (m > 0) residuals_of(X.as<double>(), m, ths, r0);
+    double mx = 0.0;
+    int64_t nin = 0;
+    for (int64_t c = 0; c < m; ++c)
+      if (ths[c] >= alpha && ths[c] <= beta) { mx = std::max(mx, r0[c]); ++nin; }
+    res->info.pre_max_resid = mx;
+    res->info.pre_nev = nin;
+  }
+  int64_t count_prev = res->info.pre_nev;
+  Buf V, Xc, C;
+  std::vector<double> theta, resid;
+  int passes = 0, irmax = 0;
+  bool converged = false;
+  int64_t c0 = 0, nin = 0;
+  for (passes = 1; passes <= h->opt.max_passes; ++passes) {
+    // X <- 2 Re sum w_l (A - z_l M)^{-1} M X   (Eq. rhoAM through Eq. inv_dd2)
+    V.ensure((size_t)n * m * sizeof(double));
+    spmm_f64(st, h->P, 0, n, 0, n, 0.0, 1.0, X.as<double>(), m, V.as<double>(), m, m, false);
+    Xc.ensure((size_t)nc * n * m * sizeof(cx<double>));
+    irmax = std::max(irmax, refined_solve<Tf>(h, V.as<double>(), Xc.as<cx<double>>(), m));
+    weighted_real_sum<cx<double>>(st, Xc.as<cx<double>>(), n * m, h->w_dev.as<cx<double>>(), nc, 2.0, X.as<double>(),
+                                  n * m);
+    // Rayleigh-Ritz on range(X), all Ritz pairs kept
+    std::vector<int> sel;
+    RRout rr = rayleigh_ritz_coeffs(
+        h, X.as<double>(), m, 1e-12, false,
+        [&](const std::vector<double> &th) {
+          std::vector<int> all(th.size());
+          std::iota(all.begin(), all.end(), 0);
+          return all;
+        },
+        C, sel);
+    const int64_t r = rr.r;
+    Buf Xn;
+    Xn.alloc((size_t)n * r * sizeof(double));
+    gemm_batched<double>(st, {{X.as<double>(), C.as<double>(), Xn.as<double>(), (int)n, (int)r, (int)m, (int)m,
+                               (int)r, (int)r}},
+                         false, false, 1.0, 0.0);
+    theta = rr.theta;
+    residuals_of(Xn.as<double>(), r, theta, resid);
+    X.alloc((size_t)n * r * sizeof(double));
+    RFDD_CUDA(cudaMemcpyAsync(X.p, Xn.p, (size_t)n * r * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    m = r;
+    c0 = 0;
+    nin = 0;
+    double mx = 0.0;
+    for (int64_t c = 0; c < r; ++c)
+      if (theta[c] >= alpha && theta[c] <= beta) {
+        if (nin == 0) c0 = c;
+        ++nin;
+        mx = std::max(mx, resid[c]);
+      }
+    if (nin == count_prev && (nin == 0 || mx <= h->opt.res_tol)) {
+      converged = true;
+      break;
+    }
+    count_prev = nin;
+  }
+  if (passes > h->opt.max_passes) passes = h->opt.max_passes;
+  // results in the original ordering: evecs[i_orig][c] = X[iperm[i_orig]][c0 + c]
+  res->n = n;
+  res->nev = nin;
+  res->evals.assign(theta.begin() + c0, theta.begin() + c0 + nin);
+  res->resid.assign(resid.begin() + c0, resid.begin() + c0 + nin);
+  res->evecs.alloc((size_t)n * std::max<int64_t>(1, nin) * sizeof(double));
+  if (nin > 0) gather_rows_f64(st, X.as<double>() + c0, m, h->iperm_dev.as<int64_t>(), res->evecs.as<double>(), nin, n, nin);
+  upload(res->evals_dev, res->evals, st);
+  upload(res->resid_dev, res->resid, st);
+  RFDD_CUDA(cudaStreamSynchronize(st));
+  res->info.nev = nin;
+  res->info.m = h->m0;
+  res->info.passes = passes;
+  res->info.ir_steps_max = irmax;
+  res->info.max_resid = 0.0;
+  for (double v : res->resid) res->info.max_resid = std::max(res->info.max_resid, v);
+  res->info.status = converged ? RFDD_OK : RFDD_NOT_CONVERGED;
+}
+
+// ------------------------------------------------------------------------------------
+// precision dispatch
+// ------------------------------------------------------------------------------------
+void set_nodes(rfdd_handle *h, int nc, const double *z, const double *w) {
+  h->nnodes = nc;
+  h->z.resize(nc);
+  h->w.resize(nc);
+  for (int l = 0; l < nc; ++l) {
+    h->z[l] = cx<double>(z[2 * l], z[2 * l + 1]);
+    h->w[l] = cx<double>(w[2 * l], w[2 * l + 1]);
+    RFDD_REQUIRE(std::isfinite(h->z[l].re) && std::isfinite(h->z[l].im) && h->z[l].im != 0.0, RFDD_EINVAL,
+                 "quadrature poles must be finite and off the real axis");
+  }
+  upload(h->z_dev, h->z, h->st);
+  upload(h->w_dev, h->w, h->st);
+}
+
+void factor(rfdd_handle *h) {
+  const size_t scal = is_mixed(h) ? sizeof(cx<float>) : sizeof(cx<double>);
+  if (h->opt.mem_budget > 0) {
+    const size_t need = factor_bytes(h, h->nnodes, scal);
+    RFDD_REQUIRE(need <= h->opt.mem_budget, RFDD_EADMIT,
+                 "factorisation needs " + std::to_string(need) + " bytes, budget " + std::to_string(h->opt.mem_budget));
+  }
+  h->have_factors = false;
+  h->fac.release();
+  h->Sfac.release();
+  h->Skeep.release();
+  if (is_mixed(h)) factor_impl<cx<float>>(h);
+  else factor_impl<cx<double>>(h);
+}
+
+void run_solve(rfdd_handle *h, double alpha, double beta, int nc, rfdd_result *res) {
+  RFDD_REQUIRE(beta > alpha && nc >= 1, RFDD_EINVAL, "solve: need alpha < beta and n_nodes >= 1");
+  Timer total(h->st);
+  std::vector<cx<double>> z, w;
+  quadrature(alpha, beta, nc, h->opt.quad_rule, z, w);
+  std::vector<double> zz(2 * nc), ww(2 * nc);
+  for (int l = 0; l < nc; ++l) {
+    zz[2 * l] = z[l].re;
+    zz[2 * l + 1] = z[l].im;
+    ww[2 * l] = w[l].re;
+    ww[2 * l + 1] = w[l].im;
+  }
+  set_nodes(h, nc, zz.data(), ww.data());
+  h->alpha = alpha;
+  h->beta = beta;
+  h->have_interval = true;
+  {
+    Timer t(h->st);
+    factor(h);
+    res->info.t_factor_ms = t.ms();
+  }
+  {
+    Timer t(h->st);
+    if (is_mixed(h)) lanczos_impl<cx<float>>(h);
+    else lanczos_impl<cx<double>>(h);
+    res->info.t_lanczos_ms = t.ms();
+    res->info.mu = h->mu;
+  }
+  const double sigma = std::isnan(h->opt.sigma) ? 0.5 * (alpha + beta) : h->opt.sigma;
+  {
+    Timer t(h->st);
+    if (is_mixed(h)) interior_impl<float>(h, sigma);
+    else interior_impl<double>(h, sigma);
+    res->info.t_interior_ms = t.ms();
+  }
+  {
+    Timer t(h->st);
+    if (is_mixed(h)) rr_on_Z<cx<float>>(h, alpha, beta, res);
+    else rr_on_Z<cx<double>>(h, alpha, beta, res);
+    res->info.t_rr_ms = t.ms();
+  }
+  {
+    Timer t(h->st);
+    if (is_mixed(h)) complete<cx<float>>(h, alpha, beta, res);
+    else complete<cx<double>>(h, alpha, beta, res);
+    res->info.t_complete_ms = t.ms();
+  }
+  res->info.t_total_ms = total.ms();
+}
+
+template <typename F>
+int guarded(F &&f) {
+  try {
+    g_last_error.clear();
+    f();
+    return RFDD_OK;
+  } catch (const Error &e) {
+    g_last_error = e.what();
+    return e.code;
+  } catch (const std::bad_alloc &) {
+    g_last_error = "host allocation failed";
+    return RFDD_ENOMEM;
+  } catch (const std::exception &e) {
+    g_last_error = e.what();
+    return RFDD_ECUDA;
+  }
+}
+
+}  // namespace
+
+// ======================================================================================
+// C ABI
+// ======================================================================================
+extern "C" {
+
+void rfdd_default_options(rfdd_options *o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->precision = RFDD_MIXED;
+  o->quad_rule = RFDD_MIDPOINT;
+  o->sigma = NAN;
+  o->nev_b = 100;
+  o->psi = 3;
+  o->lanczos_tol = 1e-6;
+  o->block = 32;
+  o->res_tol = 1e-10;
+  o->max_passes = 8;
+  o->ir_max = 10;
+  o->seed = 1;
+  o->mem_budget = 0;
+  o->stream = nullptr;
+  o->guard_frac = 0.3;
+  o->min_guard = 8;
+  o->keep_schur = 0;
+  o->subspace_iters = 4;
+}
+
+const char *rfdd_last_error(void) { return g_last_error.c_str(); }
+
+const char *rfdd_status_string(int code) {
+  switch (code) {
+    case RFDD_OK: return "ok";
+    case RFDD_EINVAL: return "invalid argument";
+    case RFDD_ENOTSYM: return "matrix not symmetric";
+    case RFDD_EPARTITION: return "invalid partition";
+    case RFDD_ENOTSPD_M: return "M not positive definite";
+    case RFDD_ESINGULAR: return "singular factorisation";
+    case RFDD_ENOMEM: return "out of device memory";
+    case RFDD_EADMIT: return "memory budget exceeded";
+    case RFDD_NOT_CONVERGED: return "not converged";
+    case RFDD_ECUDA: return "CUDA error";
+    case RFDD_ESTATE: return "call out of order";
+    default: return "unknown status";
+  }
+}
+
+int rfdd_quadrature(double alpha, double beta, int32_t n_nodes, int32_t rule, double *z_out, double *w_out) {
+  return guarded([&] {
+    RFDD_REQUIRE(z_out && w_out, RFDD_EINVAL, "quadrature: NULL output");
+    std::vector<cx<double>> z, w;
+    quadrature(alpha, beta, n_nodes, rule, z, w);
+    for (int l = 0; l < n_nodes; ++l) {
+      z_out[2 * l] = z[l].re;
+      z_out[2 * l + 1] = z[l].im;
+      w_out[2 * l] = w[l].re;
+      w_out[2 * l + 1] = w[l].im;
+    }
+  });
+}
+
+int rfdd_setup(const rfdd_csr *A, const rfdd_csr *M, const int32_t *part, int32_t p, const rfdd_options *opt,
+               rfdd_handle **out) {
+  if (!out) return RFDD_EINVAL;
+  *out = nullptr;
+  rfdd_handle *h = new (std::nothrow) rfdd_handle();
+  if (!h) return RFDD_ENOMEM;
+  int rc = guarded([&] {
+    if (opt) h->opt = *opt;
+    else rfdd_default_options(&h->opt);
+    RFDD_REQUIRE(h->opt.precision == RFDD_FP64 || h->opt.precision == RFDD_MIXED, RFDD_EINVAL, "bad precision");
+    RFDD_REQUIRE(h->opt.block >= 1 && h->opt.block <= 64, RFDD_EINVAL, "block must be in [1, 64]");
+    RFDD_REQUIRE(h->opt.psi >= 1 && h->opt.nev_b >= 1, RFDD_EINVAL, "psi and nev_b must be >= 1");
+    do_setup(h, A, M, part, p);  // host-side validation and ordering (no CUDA calls)
+    if (h->opt.stream) {
+      h->st = (cudaStream_t)h->opt.stream;
+    } else {
+      RFDD_CUDA(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking));
+      h->own_stream = true;
+    }
+    do_upload(h);
+  });
+  if (rc != RFDD_OK) {
+    rfdd_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return RFDD_OK;
+}
+
+int rfdd_layout(const rfdd_handle *h, int64_t *off, int64_t *perm, int32_t *p_out, int64_t *s_out) {
+  if (!h) return RFDD_EINVAL;
+  if (off) std::copy(h->off.begin(), h->off.end(), off);
+  if (perm) std::copy(h->perm.begin(), h->perm.end(), perm);
+  if (p_out) *p_out = h->p;
+  if (s_out) *s_out = h->s;
+  return RFDD_OK;
+}
+
+void rfdd_destroy(rfdd_handle *h) {
+  if (!h) return;
+  if (h->st) cudaStreamSynchronize(h->st);
+  cudaStream_t st = h->st;
+  bool own = h->own_stream;
+  delete h;
+  if (own && st) cudaStreamDestroy(st);
+}
+
+int rfdd_factor(rfdd_handle *h, int32_t n_nodes, const double *z, const double *w) {
+  if (!h || !z || !w || n_nodes < 1) return RFDD_EINVAL;
+  return guarded([&] {
+    set_nodes(h, n_nodes, z, w);
+    factor(h);
+  });
+}
+
+int rfdd_schur_copy(rfdd_handle *h, int32_t node, double *S_out) {
+  if (!h || !S_out) return RFDD_EINVAL;
+  return guarded([&] {
+    RFDD_REQUIRE(h->have_factors && h->opt.keep_schur, RFDD_ESTATE, "schur_copy needs keep_schur and rfdd_factor");
+    RFDD_REQUIRE(node >= 0 && node < h->nnodes, RFDD_EINVAL, "node out of range");
+    const int64_t s = h->s;
+    if (is_mixed(h)) {
+      Buf t;
+      t.alloc((size_t)s * s * sizeof(cx<double>));
+      convert<cx<double>, cx<float>>(h->st, h->Skeep.as<cx<float>>() + (int64_t)node * s * s, t.as<cx<double>>(), s * s);
+      RFDD_CUDA(cudaMemcpyAsync(S_out, t.p, (size_t)s * s * sizeof(cx<double>), cudaMemcpyDeviceToHost, h->st));
+      RFDD_CUDA(cudaStreamSynchronize(h->st));
+    } else {
+      RFDD_CUDA(cudaMemcpyAsync(S_out, h->Skeep.as<cx<double>>() + (int64_t)node * s * s,
+                                (size_t)s * s * sizeof(cx<double>), cudaMemcpyDeviceToHost, h->st));
+      RFDD_CUDA(cudaStreamSynchronize(h->st));
+    }
+  });
+}
+
+int rfdd_shifted_solve(rfdd_handle *h, int32_t node, int32_t which, int32_t j, int64_t nrhs, const double *R,
+                       double *X) {
+  if (!h || !R || !X || nrhs < 1) return RFDD_EINVAL;
+  return guarded([&] {
+    RFDD_REQUIRE(h->have_factors, RFDD_ESTATE, "shifted_solve needs rfdd_factor");
+    RFDD_REQUIRE(node >= 0 && node < h->nnodes, RFDD_EINVAL, "node out of range");
+    cudaStream_t st = h->st;
+    int64_t rows;
+    if (which == 0) {
+      RFDD_REQUIRE(j >= 0 && j < h->p, RFDD_EINVAL, "subdomain out of range");
+      rows = h->d[j];
+    } else if (which == 1) {
+      rows = h->s;
+    } else if (which == 2) {
+      rows = h->n;
+    } else {
+      throw Error(RFDD_EINVAL, "which must be 0, 1 or 2");
+    }
+    Buf r64;
+    r64.alloc((size_t)rows * nrhs * sizeof(cx<double>));
+    RFDD_CUDA(cudaMemcpyAsync(r64.p, R, (size_t)rows * nrhs * sizeof(cx<double>), cudaMemcpyHostToDevice, st));
+    auto go = [&](auto tag) {
+      using Tf = decltype(tag);
+      if (which == 2) {
+        // (A - z_l M) X = R through the block inverse with FP64 refinement; every node is
+        // solved on replicated input and node l is returned
+        const int nc = h->nnodes;
+        Buf Rall, Xall, Rr, Dx, F, Ht;
+        Rall.alloc((size_t)nc * rows * nrhs * sizeof(cx<double>));
+        for (int l = 0; l < nc; ++l)
+          RFDD_CUDA(cudaMemcpyAsync(Rall.as<cx<double>>() + (int64_t)l * rows * nrhs, r64.p,
+                                    (size_t)rows * nrhs * sizeof(cx<double>), cudaMemcpyDeviceToDevice, st));
+        Xall.alloc((size_t)nc * rows * nrhs * sizeof(cx<double>));
+        Rr.alloc((size_t)nc * rows * nrhs * sizeof(cx<double>));
+        Dx.alloc((size_t)nc * rows * nrhs * sizeof(cx<double>));
+        dd_solve<Tf>(h, Rall.as<cx<double>>(), Xall.as<cx<double>>(), nrhs, F, Ht);
+        for (int it = 0; it < h->opt.ir_max; ++it) {
+          shifted_residual(st, h->P, h->z_dev.as<cx<double>>(), nc, Rall.as<cx<double>>(), rows * nrhs,
+                           Xall.as<cx<double>>(), Rr.as<cx<double>>(), rows * nrhs, nrhs);
+          dd_solve<Tf>(h, Rr.as<cx<double>>(), Dx.as<cx<double>>(), nrhs, F, Ht);
+          axpy_c64(st, Dx.as<cx<double>>(), Xall.as<cx<double>>(), (int64_t)nc * rows * nrhs);
+        }
+        RFDD_CUDA(cudaMemcpyAsync(X, Xall.as<cx<double>>() + (int64_t)node * rows * nrhs,
+                                  (size_t)rows * nrhs * sizeof(cx<double>), cudaMemcpyDeviceToHost, st));
+        RFDD_CUDA(cudaStreamSynchronize(st));
+        return;
+      }
+      Buf t;
+      t.alloc((size_t)rows * nrhs * sizeof(Tf));
+      convert<Tf, cx<double>>(st, r64.as<cx<double>>(), t.as<Tf>(), rows * nrhs);
+      std::vector<SolveItem<Tf>> si(1);
+      if (which == 0) {
+        si[0].LU = h->fac.as<Tf>() + h->boff[(size_t)node * h->p + j];
+        si[0].piv = h->pivB.as<int>() + h->pivBoff[(size_t)node * h->p + j];
+        si[0].n = (int)h->d[j];
+        si[0].ld = (int)h->D[j];
+      } else {
+        si[0].LU = h->Sfac.as<Tf>() + (int64_t)node * h->s * h->s;
+        si[0].piv = h->pivS.as<int>() + (int64_t)node * h->s;
+        si[0].n = (int)h->s;
+        si[0].ld = (int)h->s;
+      }
+      si[0].X = t.as<Tf>();
+      si[0].ldx = (int)nrhs;
+      si[0].ncols = (int)nrhs;
+      lu_solve_batched<Tf>(st, si, NBO);
+      convert<cx<double>, Tf>(st, t.as<Tf>(), r64.as<cx<double>>(), rows * nrhs);
+      RFDD_CUDA(cudaMemcpyAsync(X, r64.p, (size_t)rows * nrhs * sizeof(cx<double>), cudaMemcpyDeviceToHost, st));
+      RFDD_CUDA(cudaStreamSynchronize(st));
+    };
+    if (is_mixed(h)) go(cx<float>());
+    else go(cx<double>());
+  });
+}
+
+int rfdd_filter_apply(rfdd_handle *h, int64_t b, const double *X, double *W) {
+  if (!h || !X || !W || b < 1) return RFDD_EINVAL;
+  return guarded([&] {
+    RFDD_REQUIRE(h->have_factors, RFDD_ESTATE, "filter_apply needs rfdd_factor");
+    const int64_t s = h->s;
+    Buf x, wv;
+    x.alloc((size_t)s * b * sizeof(double));
+    wv.alloc((size_t)s * b * sizeof(double));
+    RFDD_CUDA(cudaMemcpyAsync(x.p, X, (size_t)s * b * sizeof(double), cudaMemcpyHostToDevice, h->st));
+    if (is_mixed(h)) filter_impl<cx<float>>(h, x.as<double>(), wv.as<double>(), b, 1.0);
+    else filter_impl<cx<double>>(h, x.as<double>(), wv.as<double>(), b, 1.0);
+    RFDD_CUDA(cudaMemcpyAsync(W, wv.p, (size_t)s * b * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    RFDD_CUDA(cudaStreamSynchronize(h->st));
+  });
+}
+
+int rfdd_lanczos(rfdd_handle *h, int64_t cap, double *Q_out, int64_t *mu, double *traces, int32_t *nsteps) {
+  if (!h) return RFDD_EINVAL;
+  return guarded([&] {
+    RFDD_REQUIRE(h->have_factors, RFDD_ESTATE, "lanczos needs rfdd_factor");
+    if (is_mixed(h)) lanczos_impl<cx<float>>(h);
+    else lanczos_impl<cx<double>>(h);
+    if (mu) *mu = h->mu;
+    if (nsteps) *nsteps = (int32_t)h->traces.size();
+    if (traces)
+      for (int64_t i = 0; i < (int64_t)h->traces.size() && i < cap; ++i) traces[i] = h->traces[i];
+    if (Q_out) {
+      RFDD_REQUIRE(cap >= h->mu, RFDD_EINVAL, "lanczos: cap smaller than the basis");
+      Buf q;
+      q.alloc((size_t)h->s * h->mu * sizeof(double));
+      copy_rows_f64(h->st, h->Q.as<double>(), h->qcap, q.as<double>(), h->mu, h->s, h->mu);
+      std::vector<double> tmp((size_t)h->s * h->mu);
+      RFDD_CUDA(cudaMemcpyAsync(tmp.data(), q.p, tmp.size() * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+      RFDD_CUDA(cudaStreamSynchronize(h->st));
+      for (int64_t i = 0; i < h->s; ++i)
+        std::copy(tmp.begin() + i * h->mu, tmp.begin() + (i + 1) * h->mu, Q_out + i * cap);
+    }
+  });
+}
+
+int rfdd_interior(rfdd_handle *h, double sigma, int64_t cap, double *Z_out, int64_t *k, int64_t *kappa_out) {
+  if (!h) return RFDD_EINVAL;
+  return guarded([&] {
+    RFDD_REQUIRE(h->mu > 0, RFDD_ESTATE, "interior needs rfdd_lanczos");
+    double sg = sigma;
+    if (std::isnan(sg)) sg = h->have_interval ? 0.5 * (h->alpha + h->beta) : 0.0;
+    if (is_mixed(h)) interior_impl<float>(h, sg);
+    else interior_impl<double>(h, sg);
+    if (k) *k = h->kz;
+    if (kappa_out) *kappa_out = h->kappa;
+    if (Z_out) {
+      RFDD_REQUIRE(cap >= h->kz, RFDD_EINVAL, "interior: cap smaller than the number of columns");
+      std::vector<double> tmp((size_t)h->n * h->kz);
+      RFDD_CUDA(cudaMemcpyAsync(tmp.data(), h->Zb.p, tmp.size() * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+      RFDD_CUDA(cudaStreamSynchronize(h->st));
+      for (int64_t i = 0; i < h->n; ++i)
+        std::copy(tmp.begin() + i * h->kz, tmp.begin() + (i + 1) * h->kz, Z_out + i * cap);
+    }
+  });
+}
+
+int rfdd_rayleigh_ritz(rfdd_handle *h, int64_t cap, double *theta_out, int64_t *k) {
+  if (!h) return RFDD_EINVAL;
+  return guarded([&] {
+    RFDD_REQUIRE(h->kz > 0, RFDD_ESTATE, "rayleigh_ritz needs rfdd_interior");
+    const double a = h->have_interval ? h->alpha : -INFINITY, b = h->have_interval ? h->beta : INFINITY;
+    if (is_mixed(h)) rr_on_Z<cx<float>>(h, a, b, nullptr);
+    else rr_on_Z<cx<double>>(h, a, b, nullptr);
+    if (k) *k = (int64_t)h->rr_theta.size();
+    if (theta_out)
+      for (int64_t i = 0; i < (int64_t)h->rr_theta.size() && i < cap; ++i) theta_out[i] = h->rr_theta[i];
+  });
+}
+
+int rfdd_solve(rfdd_handle *h, double alpha, double beta, int32_t n_nodes, rfdd_result **out) {
+  if (!h || !out) return RFDD_EINVAL;
+  *out = nullptr;
+  rfdd_result *r = new (std::nothrow) rfdd_result();
+  if (!r) return RFDD_ENOMEM;
+  int rc = guarded([&] { run_solve(h, alpha, beta, n_nodes, r); });
+  if (rc != RFDD_OK) {
+    delete r;
+    return rc;
+  }
+  *out = r;
+  return r->info.status;
+}
+
+int rfdd_solve_async(rfdd_handle *h, double alpha, double beta, int32_t n_nodes, void *stream, rfdd_result **out) {
+  if (!h || !out) return RFDD_EINVAL;
+  *out = nullptr;
+  if (!(beta > alpha) || n_nodes < 1) return RFDD_EINVAL;
+  rfdd_result *r = new (std::nothrow) rfdd_result();
+  if (!r) return RFDD_ENOMEM;
+  if (stream) h->st = (cudaStream_t)stream;
+  r->ready.store(0);
+  r->worker = std::thread([h, alpha, beta, n_nodes, r] {
+    int device = 0;
+    int rc = guarded([&] { run_solve(h, alpha, beta, n_nodes, r); });
+    (void)device;
+    if (rc != RFDD_OK) r->ready.store(-rc);
+    else r->ready.store(1);
+  });
+  *out = r;
+  return RFDD_OK;
+}
+
+int rfdd_result_ready(const rfdd_result *r) {
+  if (!r) return -RFDD_EINVAL;
+  return r->ready.load();
+}
+
+int rfdd_result_get(const rfdd_result *r_, int64_t *nev, const double **evals, const double **evecs,
+                    const double **resid, int32_t device) {
+  rfdd_result *r = const_cast<rfdd_result *>(r_);
+  if (!r) return RFDD_EINVAL;
+  if (r->ready.load() != 1) return r->ready.load() < 0 ? -r->ready.load() : RFDD_ESTATE;
+  return guarded([&] {
+    if (nev) *nev = r->nev;
+    if (device) {
+      if (evals) *evals = r->evals_dev.as<double>();
+      if (evecs) *evecs = r->evecs.as<double>();
+      if (resid) *resid = r->resid_dev.as<double>();
+    } else {
+      if (evecs && !r->host_ready) {
+        r->evecs_host.resize((size_t)r->n * r->nev);
+        if (!r->evecs_host.empty())
+          RFDD_CUDA(cudaMemcpy(r->evecs_host.data(), r->evecs.p, r->evecs_host.size() * sizeof(double),
+                               cudaMemcpyDeviceToHost));
+        r->host_ready = true;
+      }
+      if (evals) *evals = r->evals.data();
+      if (evecs) *evecs = r->evecs_host.data();
+      if (resid) *resid = r->resid.data();
+    }
+  });
+}
+
+int rfdd_result_info(const rfdd_result *r, rfdd_info *info) {
+  if (!r || !info) return RFDD_EINVAL;
+  *info = r->info;
+  return RFDD_OK;
+}
+
+int rfdd_result_pre_evals(const rfdd_result *r, int64_t *count, double *vals) {
+  if (!r || !count) return RFDD_EINVAL;
+  *count = (int64_t)r->pre_evals.size();
+  if (vals) std::copy(r->pre_evals.begin(), r->pre_evals.end(), vals);
+  return RFDD_OK;
+}
+
+void rfdd_result_free(rfdd_result *r) { delete r; }
+
+int rfdd_memory_estimate(const rfdd_handle *h, int32_t n_nodes, int64_t nev_guess, size_t *bytes) {
+  if (!h || !bytes || n_nodes < 1) return RFDD_EINVAL;
+  const size_t scal = h->opt.precision == RFDD_MIXED ? sizeof(cx<float>) : sizeof(cx<double>);
+  size_t b = factor_bytes(h, n_nodes, scal);
+  const int64_t m = nev_guess + std::max<int64_t>((int64_t)std::ceil(h->opt.guard_frac * nev_guess), h->opt.min_guard);
+  b += (size_t)n_nodes * h->n * m * (sizeof(cx<double>) * 3 + scal * 2);  // completion blocks
+  b += (size_t)h->s * h->s * sizeof(double);                               // Lanczos basis
+  *bytes = b;
+  return RFDD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,116 @@
+"""C-ABI library checks that need no GPU: it loads, exports every symbol include/rfdd.h declares,
+and its host-only paths (options, status strings, quadrature, input validation) behave."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import rfdd_inputs as I
+from oracle import rfdd_oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def R():
+    from paper_1711_09487_gb300 import build
+    build.build()
+    import paper_1711_09487_gb300 as pkg
+    pkg.load()
+    return pkg
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "rfdd.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rfdd_[a-z_]+)\s*\(", text)))
+
+
+def test_header_lists_the_boundary():
+    syms = declared_symbols()
+    for need in ("rfdd_setup", "rfdd_solve", "rfdd_result_get", "rfdd_result_free", "rfdd_destroy",
+                 "rfdd_status_string", "rfdd_factor", "rfdd_filter_apply", "rfdd_lanczos"):
+        assert need in syms
+
+
+def test_library_exports_every_declared_symbol(R):
+    lib = ctypes.CDLL(R.LIB_PATH)
+    missing = [s for s in declared_symbols() if not hasattr(lib, s)]
+    assert not missing, missing
+    assert sorted(R.SYMBOLS) == declared_symbols()
+    out = subprocess.run(["nm", "-D", "--defined-only", R.LIB_PATH], capture_output=True, text=True).stdout
+    for s in declared_symbols():
+        assert re.search(rf"\bT {s}\b", out), s
+
+
+def test_options_and_status(R):
+    o = R.rfdd_default_options()
+    assert o.precision == R.RFDD_MIXED and o.psi == 3 and o.nev_b == 100 and o.block == 32
+    assert abs(o.lanczos_tol - 1e-6) < 1e-20 and abs(o.res_tol - 1e-10) < 1e-24 and np.isnan(o.sigma)
+    assert R.rfdd_status_string(R.RFDD_ESINGULAR) == "singular factorisation"
+    assert R.rfdd_status_string(12345) == "unknown status"
+
+
+@pytest.mark.parametrize("rule,name", [(0, "midpoint"), (1, "gauss_legendre")])
+@pytest.mark.parametrize("nc", [1, 2, 3, 4, 8, 16])
+def test_quadrature_matches_oracle(R, rule, name, nc):
+    z, w = R.rfdd_quadrature(742.98, 1499.75, nc, rule)
+    zo, wo = O.quadrature(742.98, 1499.75, nc, name)
+    np.testing.assert_allclose(z, zo, rtol=1e-14, atol=1e-12)
+    np.testing.assert_allclose(w, wo, rtol=1e-13, atol=1e-13)
+
+
+def test_quadrature_rejects_bad_interval(R):
+    with pytest.raises(R.RfddError) as e:
+        R.rfdd_quadrature(2.0, 1.0, 4)
+    assert e.value.code == R.RFDD_EINVAL
+
+
+def _small():
+    w = I.workload("q1_2d_24")
+    return w.A, w.M, w.part, w.p
+
+
+def test_setup_rejects_nonsymmetric(R):
+    A, M, part, p = _small()
+    a = A.to_scipy().tolil()
+    a[0, 1] = a[0, 1] + 1.0
+    with pytest.raises(R.RfddError) as e:
+        R.rfdd_setup(sp.csr_matrix(a), M, part, p)
+    assert e.value.code == R.RFDD_ENOTSYM
+
+
+def test_setup_rejects_bad_partitions(R):
+    A, M, part, p = _small()
+    bad = part.copy()
+    bad[bad == 1] = 0          # subdomain 1 empty
+    with pytest.raises(R.RfddError) as e:
+        R.rfdd_setup(A, M, bad, p)
+    assert e.value.code == R.RFDD_EPARTITION
+    bad = part.copy()
+    bad[bad == -1] = 0         # no interface: subdomains touch
+    with pytest.raises(R.RfddError) as e:
+        R.rfdd_setup(A, M, bad, p)
+    assert e.value.code == R.RFDD_EPARTITION
+    bad = part.copy()
+    bad[0] = 7                 # label out of range
+    with pytest.raises(R.RfddError) as e:
+        R.rfdd_setup(A, M, bad, p)
+    assert e.value.code == R.RFDD_EPARTITION
+
+
+def test_setup_rejects_indefinite_mass_and_size_mismatch(R):
+    A, M, part, p = _small()
+    m = M.to_scipy().tolil()
+    m[3, 3] = -1.0
+    with pytest.raises(R.RfddError) as e:
+        R.rfdd_setup(A, sp.csr_matrix(m), part, p)
+    assert e.value.code == R.RFDD_ENOTSPD_M
+    A2, M2 = I.q1_pencil(23, 2)
+    with pytest.raises(R.RfddError) as e:
+        R.rfdd_setup(A2, M, part, p)
+    assert e.value.code == R.RFDD_EINVAL
