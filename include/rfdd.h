@@ -198,6 +198,23 @@ int rfdd_interior(rfdd_handle *h, double sigma, int64_t cap, double *Z_out, int6
  * theta_out: host, all Ritz values ascending (cap entries); *k receives their number. */
 int rfdd_rayleigh_ritz(rfdd_handle *h, int64_t cap, double *theta_out, int64_t *k);
 
+/* a9 building block (Alg. 3 step 7 solves its projected problem with a dense symmetric
+ * eigensolver): eigen-decomposition of a dense symmetric n x n FP64 matrix H on the GPU by
+ * Householder tridiagonalisation, implicit-shift QL and back-transformation.  H, evals, evecs
+ * are host arrays; evals (n) ascending; evecs (n x n row-major) holds eigenvector j in ROW j.
+ * Needs no handle (runs on the default stream of the current device). */
+int rfdd_sym_eig(int64_t n, const double *H, double *evals, double *evecs);
+
+/* ---- measurement hooks (no counterpart in the paper) -------------------------------------
+ * rfdd_kernel_launches: number of kernels this library has launched in this process.
+ * rfdd_profile(1): clear the records and time every launch of the dense contraction kernels
+ * (kind 0: CUDA-core GEMM, kind 1: tensor-core GEMM) with CUDA events on their stream;
+ * rfdd_profile(0) stops recording.  rfdd_profile_get sums, for one kind, the launches, their
+ * event-measured milliseconds and their algorithmic flops (a complex multiply-add counts 8). */
+long long rfdd_kernel_launches(void);
+int rfdd_profile(int32_t enable);
+int rfdd_profile_get(int32_t kind, int64_t *launches, double *ms, double *flops);
+
 /* Asynchronous solve for serving: enqueues the solve on `stream` (a cudaStream_t, NULL = the
  * handle's) and returns; rfdd_result_ready() reports completion (1 done, 0 running, <0 error
  * code negated).  The handle must not be used until the result is ready. */

@@ -39,7 +39,8 @@ SYMBOLS = [
     "rfdd_layout", "rfdd_destroy", "rfdd_solve", "rfdd_result_get", "rfdd_result_info",
     "rfdd_result_pre_evals", "rfdd_result_free", "rfdd_factor", "rfdd_schur_copy", "rfdd_shifted_solve",
     "rfdd_filter_apply", "rfdd_lanczos", "rfdd_interior", "rfdd_rayleigh_ritz", "rfdd_solve_async",
-    "rfdd_result_ready", "rfdd_memory_estimate",
+    "rfdd_result_ready", "rfdd_memory_estimate", "rfdd_sym_eig", "rfdd_kernel_launches", "rfdd_profile",
+    "rfdd_profile_get",
 ]
 
 
@@ -113,6 +114,10 @@ def load(path: str | None = None):
     lib.rfdd_interior.argtypes = [vp, C.c_double, i64, dp, C.POINTER(i64), C.POINTER(i64)]
     lib.rfdd_rayleigh_ritz.argtypes = [vp, i64, dp, C.POINTER(i64)]
     lib.rfdd_memory_estimate.argtypes = [vp, i32, i64, C.POINTER(C.c_size_t)]
+    lib.rfdd_sym_eig.argtypes = [i64, dp, dp, dp]
+    lib.rfdd_kernel_launches.restype = C.c_longlong
+    lib.rfdd_profile.argtypes = [i32]
+    lib.rfdd_profile_get.argtypes = [i32, C.POINTER(i64), dp, dp]
     _lib = lib
     return lib
 
@@ -238,18 +243,22 @@ def rfdd_result_ready(r: Result) -> int:
     return load().rfdd_result_ready(r.ptr)
 
 
-def rfdd_result_get(r: Result, device: bool = False):
-    """Host copies (evals, evecs n x nev, resid); with device=True raw device pointers instead."""
+def rfdd_result_get(r: Result, device: bool = False, vectors: bool = True):
+    """Host copies (evals, evecs n x nev, resid); with device=True raw device pointers instead.
+    vectors=False skips the eigenvector copy (evecs is then None)."""
     lib = load()
     nev = C.c_int64()
     ev, ex, rs = C.POINTER(C.c_double)(), C.POINTER(C.c_double)(), C.POINTER(C.c_double)()
-    _check(lib.rfdd_result_get(r.ptr, C.byref(nev), C.byref(ev), C.byref(ex), C.byref(rs), 1 if device else 0))
+    _check(lib.rfdd_result_get(r.ptr, C.byref(nev), C.byref(ev), C.byref(ex) if vectors else None, C.byref(rs),
+                               1 if device else 0))
     k = nev.value
     if device:
         addr = lambda p: C.cast(p, C.c_void_p).value
         return k, addr(ev), addr(ex), addr(rs)
     evals = np.ctypeslib.as_array(ev, shape=(k,)).copy() if k else np.zeros(0)
     resid = np.ctypeslib.as_array(rs, shape=(k,)).copy() if k else np.zeros(0)
+    if not vectors:
+        return evals, None, resid
     evecs = (np.ctypeslib.as_array(ex, shape=(r.n * k,)).copy().reshape(r.n, k) if k
              else np.zeros((r.n, 0)))
     return evals, evecs, resid
@@ -338,6 +347,31 @@ def rfdd_memory_estimate(h: Handle, n_nodes: int, nev_guess: int) -> int:
     b = C.c_size_t()
     _check(load().rfdd_memory_estimate(h.ptr, n_nodes, nev_guess, C.byref(b)))
     return int(b.value)
+
+
+def rfdd_sym_eig(H: np.ndarray):
+    """(evals ascending, evecs with eigenvector j in row j) of a dense symmetric FP64 matrix."""
+    H = np.ascontiguousarray(H, dtype=np.float64)
+    n = H.shape[0]
+    ev = np.zeros(n)
+    V = np.zeros((n, n))
+    _check(load().rfdd_sym_eig(n, _dp(H), _dp(ev), _dp(V)))
+    return ev, V
+
+
+def rfdd_kernel_launches() -> int:
+    return int(load().rfdd_kernel_launches())
+
+
+def rfdd_profile(enable: bool):
+    _check(load().rfdd_profile(1 if enable else 0))
+
+
+def rfdd_profile_get(kind: int):
+    """(launches, milliseconds, algorithmic flops) recorded for one kernel kind."""
+    n, ms, fl = C.c_int64(), C.c_double(), C.c_double()
+    _check(load().rfdd_profile_get(kind, C.byref(n), C.byref(ms), C.byref(fl)))
+    return n.value, ms.value, fl.value
 
 
 def solve(A, M, part, p, alpha, beta, n_nodes, **opts):

@@ -9,6 +9,7 @@
 #include <string>
 #include <vector>
 #include <stdexcept>
+#include <atomic>
 
 #include "../../include/rfdd.h"
 
@@ -31,7 +32,24 @@ struct Error : public std::runtime_error {
                                           " (" + __FILE__ + ":" + std::to_string(__LINE__) + ")"); \
   } while (0)
 
-#define RFDD_CHECK_LAUNCH() RFDD_CUDA(cudaGetLastError())
+// Every kernel launch of the library goes through RFDD_CHECK_LAUNCH, which also counts it.
+extern std::atomic<long long> g_kernel_launches;
+#define RFDD_CHECK_LAUNCH()                                           \
+  do {                                                                \
+    ::rfdd::g_kernel_launches.fetch_add(1, std::memory_order_relaxed); \
+    RFDD_CUDA(cudaGetLastError());                                    \
+  } while (0)
+
+// Optional CUDA-event timing of the dense contraction kernels (the dominant work of the
+// factorisations and triangular solves), enabled through rfdd_profile().
+struct ProfileRec {
+  cudaEvent_t a, b;
+  double flops;   // algorithmic flops of the launch (complex multiply-add = 8 real flops)
+  int kind;       // 0: SIMT GEMM, 1: tensor-core GEMM
+};
+bool profiling_enabled();
+void profile_push(cudaEvent_t a, cudaEvent_t b, double flops, int kind);
+cudaEvent_t profile_event();
 
 #define RFDD_REQUIRE(cond, code, msg)                 \
   do {                                                \

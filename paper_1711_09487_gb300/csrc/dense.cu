@@ -98,11 +98,23 @@ void gemm_batched(cudaStream_t st, const std::vector<GemmItem<T>> &items, bool t
     }
     dim3 grid(ceil_div(nn, 64), ceil_div(mm, 64), cnt);
     RFDD_REQUIRE(grid.y <= 65535, RFDD_EINVAL, "gemm: too many row tiles");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    double flops = 0.0;
+    if (profiling_enabled()) {
+      for (int i = 0; i < cnt; ++i) flops += (ST<T>::is_complex ? 8.0 : 2.0) * b.it[i].m * (double)b.it[i].n * b.it[i].k;
+      e0 = profile_event();
+      e1 = profile_event();
+      cudaEventRecord(e0, st);
+    }
     if (!ta && !tb) gemm_simt_kernel<T, false, false><<<grid, 256, 0, st>>>(b, (R)alpha, (R)beta);
     else if (ta && !tb) gemm_simt_kernel<T, true, false><<<grid, 256, 0, st>>>(b, (R)alpha, (R)beta);
     else if (!ta && tb) gemm_simt_kernel<T, false, true><<<grid, 256, 0, st>>>(b, (R)alpha, (R)beta);
     else gemm_simt_kernel<T, true, true><<<grid, 256, 0, st>>>(b, (R)alpha, (R)beta);
     RFDD_CHECK_LAUNCH();
+    if (e0) {
+      cudaEventRecord(e1, st);
+      profile_push(e0, e1, flops, 0);
+    }
   }
 }
 

@@ -4,6 +4,8 @@
 #include "eig.cuh"
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 
 namespace rfdd {
 
@@ -105,91 +107,98 @@ __global__ void rank2_kernel(SymBatchP b, int i) {
   }
 }
 
-// Implicit QL on the tridiagonal matrix (one CTA per matrix): thread 0 runs the scalar
-// recurrence of one QL sweep and records its rotations; all threads then apply them to their
-// components of the eigenvector rows Zt.  Ends with a rank sort of the eigenvalues.
-__global__ void __launch_bounds__(1024) tql_kernel(SymBatchP b, int *status) {
+// Implicit QL on the tridiagonal matrix.  The scalar recurrence is sequential; it runs on one
+// thread per matrix and logs every QL sweep's rotations (first index m, count, then the (c, s)
+// pairs).  A second kernel applies the logged rotations to the eigenvector matrix: every row of
+// Z (one component of all eigenvectors) evolves independently under the same rotation sequence,
+// so rows are spread over many CTAs and kept in shared memory.
+struct RotLog {
+  double *cs;       // cap pairs (c, s) per matrix
+  int *sweeps;      // cap_sw pairs (m, nrot) per matrix
+  int *nsweeps;     // one counter per matrix
+  int64_t cap, cap_sw;
+};
+
+__global__ void tql_scalar_kernel(SymBatchP b, RotLog lg, int *status) {
   SymItem it = b.it[blockIdx.x];
   const int n = it.n;
-  double *d = it.d, *e = it.e, *Z = it.Zt;
-  extern __shared__ double sh[];
-  double *cs = sh;          // n rotations: c
-  double *sn = sh + n;      // s
-  __shared__ int lo_s, hi_s, nrot_s, done_s;
-  for (int64_t q = threadIdx.x; q < (int64_t)n * n; q += blockDim.x) Z[q] = ((q / n) == (q % n)) ? 1.0 : 0.0;
-  if (threadIdx.x == 0 && n > 0) e[n - 1] = 0.0;
-  __syncthreads();
-  const double eps = 2.220446049250313e-16;
-  for (int l = 0; l < n; ++l) {
-    int iter = 0;
-    while (true) {
-      if (threadIdx.x == 0) {
+  double *d = it.d, *e = it.e;
+  double *cs = lg.cs + (int64_t)blockIdx.x * lg.cap * 2;
+  int *sw = lg.sweeps + (int64_t)blockIdx.x * lg.cap_sw * 2;
+  if (threadIdx.x == 0) {
+    if (n > 0) e[n - 1] = 0.0;
+    const double eps = 2.220446049250313e-16;
+    // global scale for the splitting test: an off-diagonal at the rounding level of the whole
+    // matrix also splits (otherwise clusters of near-zero eigenvalues never deflate)
+    double tnorm = 0.0;
+    for (int i = 0; i < n; ++i) tnorm = fmax(tnorm, fabs(d[i]) + fabs(e[i]));
+    int64_t used = 0, nsw = 0;
+    bool overflow = false;
+    for (int l = 0; l < n; ++l) {
+      for (int iter = 0;; ++iter) {
         int m = l;
         for (; m < n - 1; ++m) {
           const double dd = fabs(d[m]) + fabs(d[m + 1]);
-          if (fabs(e[m]) <= eps * dd) break;
+          if (fabs(e[m]) <= eps * dd || fabs(e[m]) <= 0.5 * eps * tnorm) break;
         }
-        done_s = (m == l) || (iter >= 60);
-        if (iter >= 60 && m != l) atomicOr(status, DS_NONFINITE);
-        nrot_s = 0;
-        if (!done_s) {
-          double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-          double r = hypot(g, 1.0);
-          g = d[m] - d[l] + e[l] / (g + (g >= 0 ? fabs(r) : -fabs(r)));
-          double s = 1.0, c = 1.0, p = 0.0;
-          int i = m - 1;
-          bool early = false;
-          for (; i >= l; --i) {
-            double f = s * e[i];
-            const double bb = c * e[i];
-            r = hypot(f, g);
-            e[i + 1] = r;
-            if (r == 0.0) {
-              d[i + 1] -= p;
-              e[m] = 0.0;
-              early = true;
-              break;
-            }
-            s = f / r;
-            c = g / r;
-            g = d[i + 1] - p;
-            r = (d[i] - g) * s + 2.0 * c * bb;
-            p = s * r;
-            d[i + 1] = g + p;
-            g = c * r - bb;
-            cs[m - 1 - i] = c;
-            sn[m - 1 - i] = s;
-            nrot_s = m - i;
-          }
-          if (!early) {
-            d[l] -= p;
-            e[l] = g;
+        if (m == l) break;
+        if (iter >= 100) {
+          atomicOr(status, DS_NONFINITE);
+          break;
+        }
+        double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+        double r = hypot(g, 1.0);
+        g = d[m] - d[l] + e[l] / (g + (g >= 0 ? fabs(r) : -fabs(r)));
+        double s = 1.0, c = 1.0, p = 0.0;
+        bool early = false;
+        int nrot = 0;
+        const int64_t base = used;
+        for (int i = m - 1; i >= l; --i) {
+          const double f = s * e[i];
+          const double bb = c * e[i];
+          r = hypot(f, g);
+          e[i + 1] = r;
+          if (r == 0.0) {
+            d[i + 1] -= p;
             e[m] = 0.0;
+            early = true;
+            break;
           }
-          lo_s = l;
-          hi_s = m;
+          s = f / r;
+          c = g / r;
+          g = d[i + 1] - p;
+          r = (d[i] - g) * s + 2.0 * c * bb;
+          p = s * r;
+          d[i + 1] = g + p;
+          g = c * r - bb;
+          if (!overflow && base + nrot < lg.cap) {
+            cs[2 * (base + nrot)] = c;
+            cs[2 * (base + nrot) + 1] = s;
+          }
+          ++nrot;
+        }
+        if (!early) {
+          d[l] -= p;
+          e[l] = g;
+          e[m] = 0.0;
+        }
+        if (nrot > 0 && !overflow) {
+          if (base + nrot > lg.cap || nsw >= lg.cap_sw) {
+            overflow = true;
+            atomicOr(status, DS_BAD_SIZE);
+          } else {
+            sw[2 * nsw] = m;
+            sw[2 * nsw + 1] = nrot;
+            ++nsw;
+            used += nrot;
+          }
         }
       }
-      __syncthreads();
-      if (done_s) break;
-      const int nrot = nrot_s, m = hi_s;
-      for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        for (int q = 0; q < nrot; ++q) {
-          const int i = m - 1 - q;
-          const double c = cs[q], s = sn[q];
-          double *zi = Z + (int64_t)i * n + k;
-          double *zi1 = Z + (int64_t)(i + 1) * n + k;
-          const double f = *zi1;
-          *zi1 = s * (*zi) + c * f;
-          *zi = c * (*zi) - s * f;
-        }
-      }
-      ++iter;
-      __syncthreads();
     }
-    __syncthreads();
+    lg.nsweeps[blockIdx.x] = (int)nsw;
   }
-  // rank sort (ties by index): perm[rank] = k, eigenvalues into work then back to d
+  __syncthreads();
+  // rank sort (ties by index): perm[rank] = k, eigenvalues ascending into d
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     const double v = d[k];
     int rank = 0;
@@ -204,6 +213,41 @@ __global__ void __launch_bounds__(1024) tql_kernel(SymBatchP b, int *status) {
   for (int k = threadIdx.x; k < n; k += blockDim.x) d[k] = it.work[k];
 }
 
+// rows [row0, row0 + blockDim.x) of Z (Z = I initially) under the logged rotations; the
+// result is written transposed: Zt[i][k] = Z[k][i] (row i of Zt = eigenvector i)
+__global__ void tql_apply_kernel(SymBatchP b, RotLog lg, int rows_per_cta) {
+  const SymItem it = b.it[blockIdx.y];
+  const int n = it.n;
+  const int k = blockIdx.x * rows_per_cta + threadIdx.x;
+  if (blockIdx.x * rows_per_cta >= n) return;
+  extern __shared__ double zs[];
+  const int pitch = n | 1;
+  double *z = zs + (int64_t)threadIdx.x * pitch;
+  const bool live = k < n && threadIdx.x < rows_per_cta;
+  if (live)
+    for (int i = 0; i < n; ++i) z[i] = (i == k) ? 1.0 : 0.0;
+  const double *cs = lg.cs + (int64_t)blockIdx.y * lg.cap * 2;
+  const int *sw = lg.sweeps + (int64_t)blockIdx.y * lg.cap_sw * 2;
+  const int nsw = lg.nsweeps[blockIdx.y];
+  if (live) {
+    int64_t off = 0;
+    for (int q = 0; q < nsw; ++q) {
+      const int m = sw[2 * q], nrot = sw[2 * q + 1];
+      double carry = z[m];
+      for (int t = 0; t < nrot; ++t) {
+        const int i = m - 1 - t;
+        const double c = __ldg(cs + 2 * (off + t)), s = __ldg(cs + 2 * (off + t) + 1);
+        const double zi = z[i];
+        z[i + 1] = s * zi + c * carry;
+        carry = c * zi - s * carry;
+      }
+      z[m - nrot] = carry;
+      off += nrot;
+    }
+    for (int i = 0; i < n; ++i) it.Zt[(int64_t)i * n + k] = z[i];
+  }
+}
+
 void sym_eig_values(cudaStream_t st, const std::vector<SymItem> &items, int *status) {
   for (size_t s0 = 0; s0 < items.size(); s0 += EIG_MAXB) {
     SymBatchP b;
@@ -212,6 +256,14 @@ void sym_eig_values(cudaStream_t st, const std::vector<SymItem> &items, int *sta
     int nmax = 0;
     for (int i = 0; i < cnt; ++i) { b.it[i] = items[s0 + i]; nmax = std::max(nmax, b.it[i].n); }
     if (nmax == 0) continue;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
+    const bool timing = getenv("RFDD_LOG") && getenv("RFDD_LOG")[0] && getenv("RFDD_LOG")[0] != '0';
+    if (timing) {
+      cudaEventCreate(&ev0);
+      cudaEventCreate(&ev1);
+      cudaEventCreate(&ev2);
+      cudaEventRecord(ev0, st);
+    }
     for (int i = 0; i < nmax; ++i) {
       house_kernel<<<cnt, 256, 0, st>>>(b, i);
       RFDD_CHECK_LAUNCH();
@@ -224,11 +276,42 @@ void sym_eig_values(cudaStream_t st, const std::vector<SymItem> &items, int *sta
         RFDD_CHECK_LAUNCH();
       }
     }
-    const size_t smem = (size_t)2 * nmax * sizeof(double);
-    RFDD_REQUIRE(smem <= 200 * 1024, RFDD_EINVAL, "sym_eig: order too large");
-    RFDD_CUDA(cudaFuncSetAttribute(tql_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    tql_kernel<<<cnt, 1024, smem, st>>>(b, status);
+    RotLog lg;
+    lg.cap = 2 * (int64_t)nmax * nmax + 64;
+    lg.cap_sw = 40 * (int64_t)nmax + 64;
+    RFDD_CUDA(cudaMallocAsync((void **)&lg.cs, (size_t)cnt * lg.cap * 2 * sizeof(double), st));
+    RFDD_CUDA(cudaMallocAsync((void **)&lg.sweeps, (size_t)cnt * lg.cap_sw * 2 * sizeof(int), st));
+    RFDD_CUDA(cudaMallocAsync((void **)&lg.nsweeps, (size_t)cnt * sizeof(int), st));
+    if (timing) cudaEventRecord(ev1, st);
+    tql_scalar_kernel<<<cnt, 256, 0, st>>>(b, lg, status);
     RFDD_CHECK_LAUNCH();
+    if (timing) cudaEventRecord(ev2, st);
+    const int pitch = nmax | 1;
+    int rows = (int)std::min<int64_t>(64, (200 * 1024) / ((int64_t)pitch * sizeof(double)));
+    RFDD_REQUIRE(rows >= 1, RFDD_EINVAL, "sym_eig: order too large");
+    const size_t smem = (size_t)rows * pitch * sizeof(double);
+    RFDD_CUDA(cudaFuncSetAttribute(tql_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    tql_apply_kernel<<<dim3(ceil_div(nmax, rows), cnt), rows, smem, st>>>(b, lg, rows);
+    RFDD_CHECK_LAUNCH();
+    if (timing) {
+      cudaEvent_t ev3;
+      cudaEventCreate(&ev3);
+      cudaEventRecord(ev3, st);
+      cudaEventSynchronize(ev3);
+      float a = 0, bb = 0, c = 0;
+      cudaEventElapsedTime(&a, ev0, ev1);
+      cudaEventElapsedTime(&bb, ev1, ev2);
+      cudaEventElapsedTime(&c, ev2, ev3);
+      fprintf(stderr, "[rfdd]     sym_eig n=%d x%d: tridiag %.2f ms, QL scalar %.2f ms, QL apply %.2f ms\n", nmax, cnt,
+              a, bb, c);
+      cudaEventDestroy(ev0);
+      cudaEventDestroy(ev1);
+      cudaEventDestroy(ev2);
+      cudaEventDestroy(ev3);
+    }
+    RFDD_CUDA(cudaFreeAsync(lg.cs, st));
+    RFDD_CUDA(cudaFreeAsync(lg.sweeps, st));
+    RFDD_CUDA(cudaFreeAsync(lg.nsweeps, st));
   }
 }
 

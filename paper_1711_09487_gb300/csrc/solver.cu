@@ -24,9 +24,51 @@
 
 using namespace rfdd;
 
+namespace rfdd {
+std::atomic<long long> g_kernel_launches{0};
+namespace {
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfileRec> g_prof;
+std::vector<cudaEvent_t> g_prof_pool;
+}  // namespace
+bool profiling_enabled() { return g_prof_on; }
+cudaEvent_t profile_event() {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (!g_prof_pool.empty()) {
+    cudaEvent_t e = g_prof_pool.back();
+    g_prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+void profile_push(cudaEvent_t a, cudaEvent_t b, double flops, int kind) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_prof.push_back({a, b, flops, kind});
+}
+}  // namespace rfdd
+
 namespace {
 
 thread_local std::string g_last_error;
+
+// Diagnostics on stderr when the environment variable RFDD_LOG is set to a nonzero value.
+bool log_on() {
+  static int on = [] {
+    const char *v = getenv("RFDD_LOG");
+    return (v && v[0] && v[0] != '0') ? 1 : 0;
+  }();
+  return on != 0;
+}
+#define RFDD_LOGF(...)                    \
+  do {                                    \
+    if (log_on()) {                       \
+      fprintf(stderr, "[rfdd] " __VA_ARGS__); \
+      fputc('\n', stderr);                \
+    }                                     \
+  } while (0)
 
 // ------------------------------------------------------------------------------------
 // device buffers
@@ -66,6 +108,34 @@ void upload(Buf &b, const std::vector<T> &v, cudaStream_t st) {
   b.alloc(v.size() * sizeof(T));
   if (!v.empty()) RFDD_CUDA(cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
 }
+
+// CUDA-event lap timer for the diagnostics log (no-op unless RFDD_LOG is set)
+struct Lap {
+  cudaStream_t st;
+  cudaEvent_t e0 = nullptr;
+  const char *what;
+  Lap(cudaStream_t s, const char *w) : st(s), what(w) {
+    if (log_on()) {
+      cudaEventCreate(&e0);
+      cudaEventRecord(e0, st);
+    }
+  }
+  void mark(const char *label) {
+    if (!log_on()) return;
+    cudaEvent_t e1;
+    cudaEventCreate(&e1);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    fprintf(stderr, "[rfdd]   %s/%s: %.3f ms\n", what, label, ms);
+    cudaEventDestroy(e0);
+    e0 = e1;
+  }
+  ~Lap() {
+    if (e0) cudaEventDestroy(e0);
+  }
+};
 
 struct Timer {
   cudaEvent_t a = nullptr, b = nullptr;
@@ -572,16 +642,17 @@ void filter_impl(rfdd_handle *h, const double *X, double *W, int64_t b, double s
 
 // DD resolvent (Eq. inv_dd2) in the factor precision for all nodes:
 // X_l = (A - z_l M)^{-1} R_l,  R, X: complex FP64, n x m per node (stride n*m).
+// R_l = R + l * strideR (strideR = 0: one right-hand side shared by all nodes).
 template <typename Tf>
-void dd_solve(rfdd_handle *h, const cx<double> *R, cx<double> *X, int64_t m, Buf &F, Buf &Ht) {
+void dd_solve(rfdd_handle *h, const cx<double> *R, int64_t strideR, cx<double> *X, int64_t m, Buf &F, Buf &Ht) {
   cudaStream_t st = h->st;
   const int nc = h->nnodes;
-  const int64_t n = h->n, dsum = h->dsum, s = h->s;
+  const int64_t n = h->n, dsum = h->dsum;
   const int64_t fs = n * m;
   F.ensure((size_t)nc * fs * sizeof(Tf));
   Ht.ensure((size_t)nc * std::max<int64_t>(dsum, 1) * m * sizeof(Tf));
   Tf *f = F.as<Tf>(), *ht = Ht.as<Tf>();
-  convert<Tf, cx<double>>(st, R, f, nc * fs);
+  for (int l = 0; l < nc; ++l) convert<Tf, cx<double>>(st, R + l * strideR, f + l * fs, fs);
   auto nodes = all_nodes(h);
   solve_B<Tf>(h, f, m, fs, m, nodes);                                          // t = B^{-1} f
   couple<Tf>(st, h->P, dsum, n, 0, dsum, h->z_dev.as<cx<double>>(), nc, f, m, fs, f + dsum * m, m, fs, m, -1.0,
@@ -604,7 +675,7 @@ int refined_solve(rfdd_handle *h, const double *V, cx<double> *X, int64_t m) {
   Buf Vc, Rr, Dx, F, Ht, nr, nx;
   Vc.alloc((size_t)n * m * sizeof(cx<double>));
   real_to_complex<cx<double>>(st, V, Vc.as<cx<double>>(), n * m, 1, 0);
-  dd_solve<Tf>(h, Vc.as<cx<double>>(), X, m, F, Ht);
+  dd_solve<Tf>(h, Vc.as<cx<double>>(), 0, X, m, F, Ht);
   const int irmax = std::is_same<Tf, cx<double>>::value ? std::min(1, h->opt.ir_max) : h->opt.ir_max;
   Rr.alloc((size_t)nc * n * m * sizeof(cx<double>));
   Dx.alloc((size_t)nc * n * m * sizeof(cx<double>));
@@ -627,8 +698,18 @@ int refined_solve(rfdd_handle *h, const double *V, cx<double> *X, int64_t m) {
       for (int64_t c = 0; c < m; ++c)
         if (std::sqrt(hr[l * m + c]) > 1e-14 * scale * std::sqrt(hx[l * m + c]) + 1e-300) { ok = false; break; }
     }
+    if (log_on()) {
+      double worst = 0.0;
+      for (int l = 0; l < nc; ++l) {
+        const double zn = std::sqrt(h->z[l].re * h->z[l].re + h->z[l].im * h->z[l].im);
+        for (int64_t c = 0; c < m; ++c)
+          worst = std::max(worst, std::sqrt(hr[l * m + c]) / ((h->normA + zn * h->normM) *
+                                                               std::sqrt(hx[l * m + c]) + 1e-300));
+      }
+      RFDD_LOGF("  refinement step %d: worst scaled residual %.3e", it, worst);
+    }
     if (ok || it == irmax) break;
-    dd_solve<Tf>(h, Rr.as<cx<double>>(), Dx.as<cx<double>>(), m, F, Ht);
+    dd_solve<Tf>(h, Rr.as<cx<double>>(), n * m, Dx.as<cx<double>>(), m, F, Ht);
     axpy_c64(st, Dx.as<cx<double>>(), X, (int64_t)nc * n * m);
     ++steps;
   }
@@ -652,6 +733,7 @@ RRout rayleigh_ritz_coeffs(rfdd_handle *h, const double *Y, int64_t k, double dr
                            Buf &Cout, std::vector<int> &sel_out) {
   cudaStream_t st = h->st;
   const int64_t n = h->n;
+  Lap lap(st, "rr");
   Buf MY, AY, G, K;
   MY.alloc((size_t)n * k * sizeof(double));
   AY.alloc((size_t)n * k * sizeof(double));
@@ -682,13 +764,13 @@ RRout rayleigh_ritz_coeffs(rfdd_handle *h, const double *Y, int64_t k, double dr
   }
   MY.release();
   AY.release();
+  lap.mark("spmm+gram");
   // symmetrise-free: G and K are exactly symmetric up to rounding; the eigensolver reads the
   // full matrix.  Scale to unit diagonal.
   Buf dsc;
   dsc.alloc((size_t)k * sizeof(double));
   inv_sqrt_diag(st, G.as<double>(), k, dsc.as<double>());
-  scale_sym(st, G.as<double>(), k, dsc.as<double>());
-  scale_sym(st, K.as<double>(), k, dsc.as<double>());
+  scale_sym(st, G.as<double>(), k, dsc.as<double>());   // K stays unscaled: C1 below carries D
   // eigen-decomposition of the Gram matrix
   Buf ed, ee, et, ew, eZ, ep;
   ed.alloc(k * sizeof(double));
@@ -700,6 +782,7 @@ RRout rayleigh_ritz_coeffs(rfdd_handle *h, const double *Y, int64_t k, double dr
   SymItem gi{G.as<double>(), (int)k, (int)k, ed.as<double>(), ee.as<double>(), et.as<double>(), ew.as<double>(),
              eZ.as<double>(), ep.as<int>()};
   sym_eig_values(st, {gi}, h->status.as<int>());
+  lap.mark("gram eig values");
   std::vector<double> lam(k);
   RFDD_CUDA(cudaMemcpyAsync(lam.data(), ed.p, k * sizeof(double), cudaMemcpyDeviceToHost, st));
   RFDD_CUDA(cudaStreamSynchronize(st));
@@ -713,6 +796,7 @@ RRout rayleigh_ritz_coeffs(rfdd_handle *h, const double *Y, int64_t k, double dr
   upload(keep_dev, keep, st);
   Ut.alloc((size_t)r * k * sizeof(double));
   sym_eig_vectors(st, {BackItem{&gi, keep_dev.as<int>(), (int)r, Ut.as<double>(), (int)k}});
+  lap.mark("gram eig vectors");
   f.alloc(r * sizeof(double));
   Buf lamk;
   {
@@ -735,6 +819,7 @@ RRout rayleigh_ritz_coeffs(rfdd_handle *h, const double *Y, int64_t k, double dr
                        false, true, 1.0, 0.0);
   K.release();
   G.release();
+  lap.mark("projected H");
   Buf hd, he, ht, hw, hZ, hp;
   hd.alloc(r * sizeof(double));
   he.alloc(r * sizeof(double));
@@ -745,6 +830,7 @@ RRout rayleigh_ritz_coeffs(rfdd_handle *h, const double *Y, int64_t k, double dr
   SymItem hi{H.as<double>(), (int)r, (int)r, hd.as<double>(), he.as<double>(), ht.as<double>(), hw.as<double>(),
              hZ.as<double>(), hp.as<int>()};
   sym_eig_values(st, {hi}, h->status.as<int>());
+  lap.mark("H eig values");
   RRout out;
   out.r = r;
   out.theta.resize(r);
@@ -763,6 +849,7 @@ RRout rayleigh_ritz_coeffs(rfdd_handle *h, const double *Y, int64_t k, double dr
                                (int)r, (int)ns}},
                          true, true, 1.0, 0.0);
   }
+  lap.mark("H eig vectors + coefficients");
   sync_status(h, "rayleigh-ritz");
   return out;
 }
@@ -791,13 +878,14 @@ void lanczos_impl(rfdd_handle *h) {
   cudaStream_t st = h->st;
   const int64_t s = h->s;
   const int64_t b = std::max<int64_t>(1, std::min<int64_t>(h->opt.block, s));
-  const int64_t qld = ((s + b - 1) / b) * b;
+  const int64_t qld = s;  // mu <= s columns
   h->qcap = qld;
   h->Q.alloc((size_t)s * qld * sizeof(double));
   double *Q = h->Q.as<double>();
   RFDD_CUDA(cudaMemsetAsync(Q, 0, (size_t)s * qld * sizeof(double), st));
-  Buf W, Xb, Cb, Gb, Rinv, dead, Bprev, Amu, tmp;
+  Buf W, Wraw, Xb, Cb, Gb, Rinv, dead, Bprev, Amu, tmp;
   W.alloc((size_t)s * b * sizeof(double));
+  Wraw.alloc((size_t)s * b * sizeof(double));
   Xb.alloc((size_t)s * b * sizeof(double));
   Cb.alloc((size_t)qld * b * sizeof(double));
   Gb.alloc((size_t)b * b * sizeof(double));
@@ -808,103 +896,102 @@ void lanczos_impl(rfdd_handle *h) {
   tmp.alloc((size_t)s * b * sizeof(double));
   std::vector<int> hdead(b);
   uint64_t stream_id = 0;
-  auto orthonormalize = [&](double *Wp, int64_t ncols_prev) {
-    // CGS2 against Q[:, 0:ncols_prev], then CholQR twice; dead columns -> fresh random vectors
+  auto project_out = [&](double *Wp, int64_t bw, int64_t ncols_prev) {  // W -= Q (Q^T W)
+    if (ncols_prev <= 0) return;
+    gemm_batched<double>(st, {{Q, Wp, Cb.as<double>(), (int)ncols_prev, (int)bw, (int)s, (int)qld, (int)bw, (int)bw}},
+                         true, false, 1.0, 0.0);
+    gemm_batched<double>(st, {{Q, Cb.as<double>(), Wp, (int)s, (int)bw, (int)ncols_prev, (int)qld, (int)bw, (int)bw}},
+                         false, false, -1.0, 1.0);
+  };
+  // Lines 4-12 of Alg. 2 for a block of bw columns (row stride bw): two classical Gram-Schmidt
+  // passes against Q[:, 0:ncols_prev], Cholesky-QR, one more projection and Cholesky-QR; columns
+  // that vanish (breakdown, line 8) are replaced by fresh random vectors (line 9).
+  auto orthonormalize = [&](double *Wp, int64_t bw, int64_t ncols_prev) {
     for (int attempt = 0; attempt < 4; ++attempt) {
-      for (int pass = 0; pass < 2; ++pass) {
-        if (ncols_prev > 0) {
-          gemm_batched<double>(st, {{Q, Wp, Cb.as<double>(), (int)ncols_prev, (int)b, (int)s, (int)qld, (int)b,
-                                     (int)b}},
-                               true, false, 1.0, 0.0);
-          gemm_batched<double>(st, {{Q, Cb.as<double>(), Wp, (int)s, (int)b, (int)ncols_prev, (int)qld, (int)b,
-                                     (int)b}},
-                               false, false, -1.0, 1.0);
-        }
-      }
+      project_out(Wp, bw, ncols_prev);
+      project_out(Wp, bw, ncols_prev);
       bool any_dead = false;
       for (int q = 0; q < 2; ++q) {
-        gemm_batched<double>(st, {{Wp, Wp, Gb.as<double>(), (int)b, (int)b, (int)s, (int)b, (int)b, (int)b}}, true,
+        gemm_batched<double>(st, {{Wp, Wp, Gb.as<double>(), (int)bw, (int)bw, (int)s, (int)bw, (int)bw, (int)bw}}, true,
                              false, 1.0, 0.0);
-        chol_inv_batched(st, {CholItem{Gb.as<double>(), Rinv.as<double>(), dead.as<int>(), (int)b}}, 1e-24);
-        gemm_batched<double>(st, {{Wp, Rinv.as<double>(), tmp.as<double>(), (int)s, (int)b, (int)b, (int)b, (int)b,
-                                   (int)b}},
+        chol_inv_batched(st, {CholItem{Gb.as<double>(), Rinv.as<double>(), dead.as<int>(), (int)bw}}, 1e-24);
+        gemm_batched<double>(st, {{Wp, Rinv.as<double>(), tmp.as<double>(), (int)s, (int)bw, (int)bw, (int)bw, (int)bw,
+                                   (int)bw}},
                              false, false, 1.0, 0.0);
-        RFDD_CUDA(cudaMemcpyAsync(Wp, tmp.p, (size_t)s * b * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        RFDD_CUDA(cudaMemcpyAsync(hdead.data(), dead.p, b * sizeof(int), cudaMemcpyDeviceToHost, st));
+        RFDD_CUDA(cudaMemcpyAsync(Wp, tmp.p, (size_t)s * bw * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        RFDD_CUDA(cudaMemcpyAsync(hdead.data(), dead.p, bw * sizeof(int), cudaMemcpyDeviceToHost, st));
         RFDD_CUDA(cudaStreamSynchronize(st));
-        for (int c = 0; c < b; ++c) any_dead |= hdead[c] != 0;
+        for (int c = 0; c < bw; ++c) any_dead |= hdead[c] != 0;
         if (any_dead) break;
-        if (ncols_prev > 0 && q == 0) {
-          // one more projection pass after normalisation ("twice is enough")
-          gemm_batched<double>(st, {{Q, Wp, Cb.as<double>(), (int)ncols_prev, (int)b, (int)s, (int)qld, (int)b,
-                                     (int)b}},
-                               true, false, 1.0, 0.0);
-          gemm_batched<double>(st, {{Q, Cb.as<double>(), Wp, (int)s, (int)b, (int)ncols_prev, (int)qld, (int)b,
-                                     (int)b}},
-                               false, false, -1.0, 1.0);
-        }
+        if (q == 0) project_out(Wp, bw, ncols_prev);  // "twice is enough" after normalisation
       }
       if (!any_dead) return;
-      // breakdown (Alg. 2 line 9): replace the dead columns by fresh random vectors
       Buf fresh;
-      fresh.alloc((size_t)s * b * sizeof(double));
-      counter_uniform_dev(st, h->opt.seed, 1000 + (++stream_id), fresh.as<double>(), s * b);
-      std::vector<double> hw((size_t)s * b), hf((size_t)s * b);
+      fresh.alloc((size_t)s * bw * sizeof(double));
+      counter_uniform_dev(st, h->opt.seed, 1000 + (++stream_id), fresh.as<double>(), s * bw);
+      std::vector<double> hw((size_t)s * bw), hf((size_t)s * bw);
       RFDD_CUDA(cudaMemcpyAsync(hw.data(), Wp, hw.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
       RFDD_CUDA(cudaMemcpyAsync(hf.data(), fresh.p, hf.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
       RFDD_CUDA(cudaStreamSynchronize(st));
       for (int64_t i = 0; i < s; ++i)
-        for (int c = 0; c < b; ++c)
-          if (hdead[c]) hw[i * b + c] = hf[i * b + c];
+        for (int c = 0; c < bw; ++c)
+          if (hdead[c]) hw[i * bw + c] = hf[i * bw + c];
       RFDD_CUDA(cudaMemcpyAsync(Wp, hw.data(), hw.size() * sizeof(double), cudaMemcpyHostToDevice, st));
     }
     throw Error(RFDD_ESINGULAR, "lanczos: could not extend the basis");
   };
-  // start block (Alg. 2 line 0)
-  counter_uniform_dev(st, h->opt.seed, 0, W.as<double>(), s * b);
-  orthonormalize(W.as<double>(), 0);
-  copy_rows_f64(st, W.as<double>(), b, Q, qld, s, b);
+  // line 0: start block
+  int64_t bc = b, bprev = 0, col = 0;  // current block width, previous width, first column
+  counter_uniform_dev(st, h->opt.seed, 0, W.as<double>(), s * bc);
+  orthonormalize(W.as<double>(), bc, 0);
+  copy_rows_f64(st, W.as<double>(), bc, Q, qld, s, bc);
   h->traces.clear();
   double trace = 0.0, last_check = 0.0;
   const int check_every = (int)std::max<int64_t>(1, (10 + b - 1) / b);
   int64_t nblk = 0;
   std::vector<double> ha(b * b);
   while (true) {
-    double *Qmu = Q + nblk * b;
-    copy_rows_f64(st, Qmu, qld, Xb.as<double>(), b, s, b);
-    filter_impl<Tf>(h, Xb.as<double>(), W.as<double>(), b, 1.0);  // line 2: F q
-    if (nblk > 0) {  // - Q_{mu-1} B_mu^T
-      gemm_batched<double>(st, {{Q + (nblk - 1) * b, Bprev.as<double>(), W.as<double>(), (int)s, (int)b, (int)b,
-                                 (int)qld, (int)b, (int)b}},
+    double *Qmu = Q + col;
+    copy_rows_f64(st, Qmu, qld, Xb.as<double>(), bc, s, bc);
+    filter_impl<Tf>(h, Xb.as<double>(), W.as<double>(), bc, 1.0);  // line 2: F q
+    if (nblk > 0)  // ... - Q_{mu-1} B_mu^T
+      gemm_batched<double>(st, {{Q + col - bprev, Bprev.as<double>(), W.as<double>(), (int)s, (int)bc, (int)bprev,
+                                 (int)qld, (int)bprev, (int)bc}},
                            false, true, -1.0, 1.0);
-    }
     // line 3: A_mu = Q_mu^T W
-    gemm_batched<double>(st, {{Xb.as<double>(), W.as<double>(), Amu.as<double>(), (int)b, (int)b, (int)s, (int)b,
-                               (int)b, (int)b}},
+    gemm_batched<double>(st, {{Xb.as<double>(), W.as<double>(), Amu.as<double>(), (int)bc, (int)bc, (int)s, (int)bc,
+                               (int)bc, (int)bc}},
                          true, false, 1.0, 0.0);
-    RFDD_CUDA(cudaMemcpyAsync(ha.data(), Amu.p, b * b * sizeof(double), cudaMemcpyDeviceToHost, st));
+    RFDD_CUDA(cudaMemcpyAsync(ha.data(), Amu.p, bc * bc * sizeof(double), cudaMemcpyDeviceToHost, st));
     RFDD_CUDA(cudaStreamSynchronize(st));
-    for (int c = 0; c < b; ++c) trace += ha[c * b + c];
+    for (int c = 0; c < bc; ++c) trace += ha[c * bc + c];
     h->traces.push_back(trace);
     ++nblk;
-    if ((nblk + 1) * b > s) break;  // the next block would not fit in R^s (mu <= s)
-    // lines 4-12: orthogonalise against all previous blocks, normalise
-    // B_{mu+1} = Q_{mu+1}^T W (upper triangular factor of the block QR)
-    RFDD_CUDA(cudaMemcpyAsync(tmp.p, W.p, (size_t)s * b * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    Buf Wraw;
-    Wraw.alloc((size_t)s * b * sizeof(double));
-    RFDD_CUDA(cudaMemcpyAsync(Wraw.p, W.p, (size_t)s * b * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    orthonormalize(W.as<double>(), nblk * b);
-    gemm_batched<double>(st, {{W.as<double>(), Wraw.as<double>(), Bprev.as<double>(), (int)b, (int)b, (int)s, (int)b,
-                               (int)b, (int)b}},
-                         true, false, 1.0, 0.0);
-    copy_rows_f64(st, W.as<double>(), b, Q + nblk * b, qld, s, b);
+    const int64_t mu_now = col + bc;
+    if (mu_now >= s) break;  // the space is exhausted (mu = s)
     if (nblk % check_every == 0) {  // line 13
       if (std::fabs(trace - last_check) <= h->opt.lanczos_tol * std::fabs(trace)) break;
       last_check = trace;
     }
+    // lines 4-12 for the next block (width bn), B_{mu+1} = Q_{mu+1}^T W
+    const int64_t bn = std::min<int64_t>(b, s - mu_now);
+    if (bn < bc)  // keep the leading bn columns of W (row stride bc -> bn)
+      copy_rows_f64(st, W.as<double>(), bc, tmp.as<double>(), bn, s, bn);
+    else
+      RFDD_CUDA(cudaMemcpyAsync(tmp.p, W.p, (size_t)s * bc * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    RFDD_CUDA(cudaMemcpyAsync(Wraw.p, W.p, (size_t)s * bc * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    RFDD_CUDA(cudaMemcpyAsync(W.p, tmp.p, (size_t)s * bn * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    orthonormalize(W.as<double>(), bn, mu_now);
+    // B (bn x bc) = Q_next^T W_raw
+    gemm_batched<double>(st, {{W.as<double>(), Wraw.as<double>(), Bprev.as<double>(), (int)bn, (int)bc, (int)s, (int)bn,
+                               (int)bc, (int)bc}},
+                         true, false, 1.0, 0.0);
+    copy_rows_f64(st, W.as<double>(), bn, Q + mu_now, qld, s, bn);
+    bprev = bc;
+    col = mu_now;
+    bc = bn;
   }
-  h->mu = nblk * b;
+  h->mu = col + bc;
   RFDD_CUDA(cudaStreamSynchronize(st));
 }
 
@@ -1133,9 +1220,10 @@ void rr_on_Z(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
   Buf C;
   std::vector<int> sel;
   int64_t m_sel = 0;
-  const double drop = is_mixed(h) ? 1e-10 : 1e-12;
+  // directions below the Gram matrix's rounding level are pruned
+  const double drop = 1e-12;
   RRout rr = rayleigh_ritz_coeffs(
-      h, h->Zb.as<double>(), kz, drop, is_mixed(h),
+      h, h->Zb.as<double>(), kz, drop, false,
       [&](const std::vector<double> &th) {
         int64_t nin = 0;
         for (double t : th) nin += (t >= alpha && t <= beta);
@@ -1199,6 +1287,8 @@ void complete(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
       if (ths[c] >= alpha && ths[c] <= beta) { mx = std::max(mx, r0[c]); ++nin; }
     res->info.pre_max_resid = mx;
     res->info.pre_nev = nin;
+    RFDD_LOGF("rf-ddes: mu=%lld kz=%lld r=%zu m0=%lld inside=%lld max_res_inside=%.3e", (long long)h->mu,
+              (long long)h->kz, h->rr_theta.size(), (long long)m, (long long)nin, mx);
   }
   int64_t count_prev = res->info.pre_nev;
   Buf V, Xc, C;
@@ -1244,6 +1334,8 @@ void complete(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
         ++nin;
         mx = std::max(mx, resid[c]);
       }
+    RFDD_LOGF("pass %d: m=%lld r=%lld inside=%lld (prev %lld) max_res_inside=%.3e ir_steps=%d", passes,
+              (long long)m, (long long)r, (long long)nin, (long long)count_prev, mx, irmax);
     if (nin == count_prev && (nin == 0 || mx <= h->opt.res_tol)) {
       converged = true;
       break;
@@ -1542,11 +1634,11 @@ int rfdd_shifted_solve(rfdd_handle *h, int32_t node, int32_t which, int32_t j, i
         Xall.alloc((size_t)nc * rows * nrhs * sizeof(cx<double>));
         Rr.alloc((size_t)nc * rows * nrhs * sizeof(cx<double>));
         Dx.alloc((size_t)nc * rows * nrhs * sizeof(cx<double>));
-        dd_solve<Tf>(h, Rall.as<cx<double>>(), Xall.as<cx<double>>(), nrhs, F, Ht);
+        dd_solve<Tf>(h, Rall.as<cx<double>>(), rows * nrhs, Xall.as<cx<double>>(), nrhs, F, Ht);
         for (int it = 0; it < h->opt.ir_max; ++it) {
           shifted_residual(st, h->P, h->z_dev.as<cx<double>>(), nc, Rall.as<cx<double>>(), rows * nrhs,
                            Xall.as<cx<double>>(), Rr.as<cx<double>>(), rows * nrhs, nrhs);
-          dd_solve<Tf>(h, Rr.as<cx<double>>(), Dx.as<cx<double>>(), nrhs, F, Ht);
+          dd_solve<Tf>(h, Rr.as<cx<double>>(), rows * nrhs, Dx.as<cx<double>>(), nrhs, F, Ht);
           axpy_c64(st, Dx.as<cx<double>>(), Xall.as<cx<double>>(), (int64_t)nc * rows * nrhs);
         }
         RFDD_CUDA(cudaMemcpyAsync(X, Xall.as<cx<double>>() + (int64_t)node * rows * nrhs,
@@ -1734,6 +1826,70 @@ int rfdd_result_pre_evals(const rfdd_result *r, int64_t *count, double *vals) {
 }
 
 void rfdd_result_free(rfdd_result *r) { delete r; }
+
+int rfdd_sym_eig(int64_t n, const double *H, double *evals, double *evecs) {
+  if (n < 1 || !H || !evals || !evecs) return RFDD_EINVAL;
+  return guarded([&] {
+    cudaStream_t st = 0;
+    Buf Hd, d, e, t, w, Z, perm, sel, out, status;
+    Hd.alloc((size_t)n * n * sizeof(double));
+    RFDD_CUDA(cudaMemcpy(Hd.p, H, (size_t)n * n * sizeof(double), cudaMemcpyHostToDevice));
+    d.alloc(n * sizeof(double));
+    e.alloc(n * sizeof(double));
+    t.alloc(n * sizeof(double));
+    w.alloc(n * sizeof(double));
+    Z.alloc((size_t)n * n * sizeof(double));
+    perm.alloc(n * sizeof(int));
+    status.alloc(sizeof(int));
+    RFDD_CUDA(cudaMemset(status.p, 0, sizeof(int)));
+    SymItem si{Hd.as<double>(), (int)n, (int)n, d.as<double>(), e.as<double>(), t.as<double>(), w.as<double>(),
+               Z.as<double>(), perm.as<int>()};
+    sym_eig_values(st, {si}, status.as<int>());
+    std::vector<int> all(n);
+    std::iota(all.begin(), all.end(), 0);
+    upload(sel, all, st);
+    out.alloc((size_t)n * n * sizeof(double));
+    sym_eig_vectors(st, {BackItem{&si, sel.as<int>(), (int)n, out.as<double>(), (int)n}});
+    RFDD_CUDA(cudaStreamSynchronize(st));
+    int stt = 0;
+    RFDD_CUDA(cudaMemcpy(&stt, status.p, sizeof(int), cudaMemcpyDeviceToHost));
+    RFDD_REQUIRE(stt == 0, RFDD_ESINGULAR, "sym_eig: QL iteration did not converge");
+    RFDD_CUDA(cudaMemcpy(evals, d.p, n * sizeof(double), cudaMemcpyDeviceToHost));
+    RFDD_CUDA(cudaMemcpy(evecs, out.p, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToHost));
+  });
+}
+
+long long rfdd_kernel_launches(void) { return g_kernel_launches.load(); }
+
+int rfdd_profile(int32_t enable) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (auto &r : g_prof) {
+    g_prof_pool.push_back(r.a);
+    g_prof_pool.push_back(r.b);
+  }
+  g_prof.clear();
+  g_prof_on = enable != 0;
+  return RFDD_OK;
+}
+
+int rfdd_profile_get(int32_t kind, int64_t *launches, double *ms, double *flops) {
+  if (!launches || !ms || !flops) return RFDD_EINVAL;
+  return guarded([&] {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    *launches = 0;
+    *ms = 0.0;
+    *flops = 0.0;
+    for (auto &r : g_prof) {
+      if (r.kind != kind) continue;
+      RFDD_CUDA(cudaEventSynchronize(r.b));
+      float t = 0.f;
+      RFDD_CUDA(cudaEventElapsedTime(&t, r.a, r.b));
+      *launches += 1;
+      *ms += t;
+      *flops += r.flops;
+    }
+  });
+}
 
 int rfdd_memory_estimate(const rfdd_handle *h, int32_t n_nodes, int64_t nev_guess, size_t *bytes) {
   if (!h || !bytes || n_nodes < 1) return RFDD_EINVAL;

@@ -34,7 +34,7 @@ import scipy.sparse as sp
 __all__ = [
     "Csr", "Pencil", "q1_1d", "q1_pencil", "q1_eigenvalues", "varkappa7_pencil",
     "separator_planes", "geometric_partition", "interval_from_sorted", "workload",
-    "WORKLOADS", "random_rhs",
+    "WORKLOADS", "random_rhs", "snap_to_gaps",
 ]
 
 
@@ -234,10 +234,21 @@ def interval_from_sorted(ev: np.ndarray, first: int, last: int) -> tuple[float, 
 # Named workloads
 # ----------------------------------------------------------------------------------------
 
+def snap_to_gaps(ev: np.ndarray, first: int, last: int, rtol: float = 1e-10) -> tuple[int, int]:
+    """Widen the 1-based window first..last so that it does not cut through a cluster of equal
+    eigenvalues (multiplicities of tensor-product spectra)."""
+    while first > 1 and ev[first - 1] - ev[first - 2] <= rtol * abs(ev[first - 1]):
+        first -= 1
+    while last < len(ev) and ev[last] - ev[last - 1] <= rtol * abs(ev[last - 1]):
+        last += 1
+    return first, last
+
+
 def _q1_workload(name, N, dim, splits, first, last, n_nodes, rule):
     A, M = q1_pencil(N, dim)
     part, p = geometric_partition(N, dim, splits)
     ev = q1_eigenvalues(N, dim)
+    first, last = snap_to_gaps(ev, first, last)
     alpha, beta = interval_from_sorted(ev, first, last)
     nev = int(np.count_nonzero((ev > alpha) & (ev < beta)))
     return Pencil(name, A, M, part, p, alpha, beta, n_nodes, rule, ev, nev,
