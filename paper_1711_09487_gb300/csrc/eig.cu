@@ -1,6 +1,7 @@
 // Dense symmetric eigensolver used by the Rayleigh-Ritz steps (Alg. 3 step 7 and the
-// completion passes).  Textbook algorithms: Householder reduction to tridiagonal form, implicit
-// QL iteration with Wilkinson-type shifts on the tridiagonal matrix, back-transformation.
+// completion passes).  Textbook algorithms: Householder reduction to tridiagonal form,
+// bisection on Sturm counts for the eigenvalues of the tridiagonal matrix, inverse iteration
+// with Gram-Schmidt inside clusters of close eigenvalues, back-transformation.
 #include "eig.cuh"
 
 #include <algorithm>
@@ -107,148 +108,52 @@ __global__ void rank2_kernel(SymBatchP b, int i) {
   }
 }
 
-// Implicit QL on the tridiagonal matrix.  The scalar recurrence is sequential; it runs on one
-// thread per matrix and logs every QL sweep's rotations (first index m, count, then the (c, s)
-// pairs).  A second kernel applies the logged rotations to the eigenvector matrix: every row of
-// Z (one component of all eigenvectors) evolves independently under the same rotation sequence,
-// so rows are spread over many CTAs and kept in shared memory.
-struct RotLog {
-  double *cs;       // cap pairs (c, s) per matrix
-  int *sweeps;      // cap_sw pairs (m, nrot) per matrix
-  int *nsweeps;     // one counter per matrix
-  int64_t cap, cap_sw;
-};
-
-__global__ void tql_scalar_kernel(SymBatchP b, RotLog lg, int *status) {
-  SymItem it = b.it[blockIdx.x];
-  const int n = it.n;
-  double *d = it.d, *e = it.e;
-  double *cs = lg.cs + (int64_t)blockIdx.x * lg.cap * 2;
-  int *sw = lg.sweeps + (int64_t)blockIdx.x * lg.cap_sw * 2;
-  if (threadIdx.x == 0) {
-    if (n > 0) e[n - 1] = 0.0;
-    const double eps = 2.220446049250313e-16;
-    // global scale for the splitting test: an off-diagonal at the rounding level of the whole
-    // matrix also splits (otherwise clusters of near-zero eigenvalues never deflate)
-    double tnorm = 0.0;
-    for (int i = 0; i < n; ++i) tnorm = fmax(tnorm, fabs(d[i]) + fabs(e[i]));
-    int64_t used = 0, nsw = 0;
-    bool overflow = false;
-    for (int l = 0; l < n; ++l) {
-      for (int iter = 0;; ++iter) {
-        int m = l;
-        for (; m < n - 1; ++m) {
-          const double dd = fabs(d[m]) + fabs(d[m + 1]);
-          if (fabs(e[m]) <= eps * dd || fabs(e[m]) <= 0.5 * eps * tnorm) break;
-        }
-        if (m == l) break;
-        if (iter >= 100) {
-          atomicOr(status, DS_NONFINITE);
-          break;
-        }
-        double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-        double r = hypot(g, 1.0);
-        g = d[m] - d[l] + e[l] / (g + (g >= 0 ? fabs(r) : -fabs(r)));
-        double s = 1.0, c = 1.0, p = 0.0;
-        bool early = false;
-        int nrot = 0;
-        const int64_t base = used;
-        for (int i = m - 1; i >= l; --i) {
-          const double f = s * e[i];
-          const double bb = c * e[i];
-          r = hypot(f, g);
-          e[i + 1] = r;
-          if (r == 0.0) {
-            d[i + 1] -= p;
-            e[m] = 0.0;
-            early = true;
-            break;
-          }
-          s = f / r;
-          c = g / r;
-          g = d[i + 1] - p;
-          r = (d[i] - g) * s + 2.0 * c * bb;
-          p = s * r;
-          d[i + 1] = g + p;
-          g = c * r - bb;
-          if (!overflow && base + nrot < lg.cap) {
-            cs[2 * (base + nrot)] = c;
-            cs[2 * (base + nrot) + 1] = s;
-          }
-          ++nrot;
-        }
-        if (!early) {
-          d[l] -= p;
-          e[l] = g;
-          e[m] = 0.0;
-        }
-        if (nrot > 0 && !overflow) {
-          if (base + nrot > lg.cap || nsw >= lg.cap_sw) {
-            overflow = true;
-            atomicOr(status, DS_BAD_SIZE);
-          } else {
-            sw[2 * nsw] = m;
-            sw[2 * nsw + 1] = nrot;
-            ++nsw;
-            used += nrot;
-          }
-        }
-      }
-    }
-    lg.nsweeps[blockIdx.x] = (int)nsw;
+// --------------------------------------------------------------------------------------
+// Eigenvalues of the tridiagonal matrix by bisection: thread per eigenvalue index.  The Sturm
+// count of x is the number of negative pivots of the LDL^T factorisation of T - x I.
+// --------------------------------------------------------------------------------------
+__device__ inline int sturm_count(const double *d, const double *e, int n, double x, double pivmin) {
+  int cnt = 0;
+  double q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  cnt += q < 0.0;
+  for (int k = 1; k < n; ++k) {
+    q = d[k] - x - e[k - 1] * e[k - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    cnt += q < 0.0;
   }
-  __syncthreads();
-  // rank sort (ties by index): perm[rank] = k, eigenvalues ascending into d
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
-    const double v = d[k];
-    int rank = 0;
-    for (int j = 0; j < n; ++j) {
-      const double u = d[j];
-      rank += (u < v) || (u == v && j < k);
-    }
-    it.perm[rank] = k;
-    it.work[rank] = v;
-  }
-  __syncthreads();
-  for (int k = threadIdx.x; k < n; k += blockDim.x) d[k] = it.work[k];
+  return cnt;
 }
 
-// rows [row0, row0 + blockDim.x) of Z (Z = I initially) under the logged rotations; the
-// result is written transposed: Zt[i][k] = Z[k][i] (row i of Zt = eigenvector i)
-__global__ void tql_apply_kernel(SymBatchP b, RotLog lg, int rows_per_cta) {
+__global__ void bisect_kernel(SymBatchP b) {
   const SymItem it = b.it[blockIdx.y];
   const int n = it.n;
-  const int k = blockIdx.x * rows_per_cta + threadIdx.x;
-  if (blockIdx.x * rows_per_cta >= n) return;
-  extern __shared__ double zs[];
-  const int pitch = n | 1;
-  double *z = zs + (int64_t)threadIdx.x * pitch;
-  const bool live = k < n && threadIdx.x < rows_per_cta;
-  if (live)
-    for (int i = 0; i < n; ++i) z[i] = (i == k) ? 1.0 : 0.0;
-  const double *cs = lg.cs + (int64_t)blockIdx.y * lg.cap * 2;
-  const int *sw = lg.sweeps + (int64_t)blockIdx.y * lg.cap_sw * 2;
-  const int nsw = lg.nsweeps[blockIdx.y];
-  if (live) {
-    int64_t off = 0;
-    for (int q = 0; q < nsw; ++q) {
-      const int m = sw[2 * q], nrot = sw[2 * q + 1];
-      double carry = z[m];
-      for (int t = 0; t < nrot; ++t) {
-        const int i = m - 1 - t;
-        const double c = __ldg(cs + 2 * (off + t)), s = __ldg(cs + 2 * (off + t) + 1);
-        const double zi = z[i];
-        z[i + 1] = s * zi + c * carry;
-        carry = c * zi - s * carry;
-      }
-      z[m - nrot] = carry;
-      off += nrot;
-    }
-    for (int i = 0; i < n; ++i) it.Zt[(int64_t)i * n + k] = z[i];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double *d = it.d, *e = it.e;
+  double gl = d[0], gu = d[0], emax2 = 0.0;
+  for (int k = 0; k < n; ++k) {
+    const double r = (k > 0 ? fabs(e[k - 1]) : 0.0) + (k < n - 1 ? fabs(e[k]) : 0.0);
+    gl = fmin(gl, d[k] - r);
+    gu = fmax(gu, d[k] + r);
+    if (k < n - 1) emax2 = fmax(emax2, e[k] * e[k]);
   }
+  const double eps = 2.220446049250313e-16;
+  const double pivmin = 2.2250738585072014e-308 * fmax(1.0, emax2);
+  const double span = fmax(fabs(gl), fabs(gu));
+  double lo = gl - 2.0 * eps * span * n - pivmin, hi = gu + 2.0 * eps * span * n + pivmin;
+  for (int iter = 0; iter < 200; ++iter) {
+    if (hi - lo <= 2.0 * eps * fmax(fabs(lo), fabs(hi)) + 4.0 * pivmin) break;
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (sturm_count(d, e, n, mid, pivmin) > i) hi = mid;
+    else lo = mid;
+  }
+  it.lam[i] = 0.5 * (lo + hi);
 }
 
 void sym_eig_values(cudaStream_t st, const std::vector<SymItem> &items, int *status) {
+  (void)status;
   for (size_t s0 = 0; s0 < items.size(); s0 += EIG_MAXB) {
     SymBatchP b;
     memset(&b, 0, sizeof(b));
@@ -256,14 +161,6 @@ void sym_eig_values(cudaStream_t st, const std::vector<SymItem> &items, int *sta
     int nmax = 0;
     for (int i = 0; i < cnt; ++i) { b.it[i] = items[s0 + i]; nmax = std::max(nmax, b.it[i].n); }
     if (nmax == 0) continue;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
-    const bool timing = getenv("RFDD_LOG") && getenv("RFDD_LOG")[0] && getenv("RFDD_LOG")[0] != '0';
-    if (timing) {
-      cudaEventCreate(&ev0);
-      cudaEventCreate(&ev1);
-      cudaEventCreate(&ev2);
-      cudaEventRecord(ev0, st);
-    }
     for (int i = 0; i < nmax; ++i) {
       house_kernel<<<cnt, 256, 0, st>>>(b, i);
       RFDD_CHECK_LAUNCH();
@@ -276,50 +173,149 @@ void sym_eig_values(cudaStream_t st, const std::vector<SymItem> &items, int *sta
         RFDD_CHECK_LAUNCH();
       }
     }
-    RotLog lg;
-    lg.cap = 2 * (int64_t)nmax * nmax + 64;
-    lg.cap_sw = 40 * (int64_t)nmax + 64;
-    RFDD_CUDA(cudaMallocAsync((void **)&lg.cs, (size_t)cnt * lg.cap * 2 * sizeof(double), st));
-    RFDD_CUDA(cudaMallocAsync((void **)&lg.sweeps, (size_t)cnt * lg.cap_sw * 2 * sizeof(int), st));
-    RFDD_CUDA(cudaMallocAsync((void **)&lg.nsweeps, (size_t)cnt * sizeof(int), st));
-    if (timing) cudaEventRecord(ev1, st);
-    tql_scalar_kernel<<<cnt, 256, 0, st>>>(b, lg, status);
+    // e[n-1] = 0 for every item (house_kernel leaves it undefined)
+    bisect_kernel<<<dim3(ceil_div(nmax, 128), cnt), 128, 0, st>>>(b);
     RFDD_CHECK_LAUNCH();
-    if (timing) cudaEventRecord(ev2, st);
-    const int pitch = nmax | 1;
-    int rows = (int)std::min<int64_t>(64, (200 * 1024) / ((int64_t)pitch * sizeof(double)));
-    RFDD_REQUIRE(rows >= 1, RFDD_EINVAL, "sym_eig: order too large");
-    const size_t smem = (size_t)rows * pitch * sizeof(double);
-    RFDD_CUDA(cudaFuncSetAttribute(tql_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    tql_apply_kernel<<<dim3(ceil_div(nmax, rows), cnt), rows, smem, st>>>(b, lg, rows);
-    RFDD_CHECK_LAUNCH();
-    if (timing) {
-      cudaEvent_t ev3;
-      cudaEventCreate(&ev3);
-      cudaEventRecord(ev3, st);
-      cudaEventSynchronize(ev3);
-      float a = 0, bb = 0, c = 0;
-      cudaEventElapsedTime(&a, ev0, ev1);
-      cudaEventElapsedTime(&bb, ev1, ev2);
-      cudaEventElapsedTime(&c, ev2, ev3);
-      fprintf(stderr, "[rfdd]     sym_eig n=%d x%d: tridiag %.2f ms, QL scalar %.2f ms, QL apply %.2f ms\n", nmax, cnt,
-              a, bb, c);
-      cudaEventDestroy(ev0);
-      cudaEventDestroy(ev1);
-      cudaEventDestroy(ev2);
-      cudaEventDestroy(ev3);
-    }
-    RFDD_CUDA(cudaFreeAsync(lg.cs, st));
-    RFDD_CUDA(cudaFreeAsync(lg.sweeps, st));
-    RFDD_CUDA(cudaFreeAsync(lg.nsweeps, st));
   }
 }
 
-// x = H_0 H_1 ... H_{n-3} z for the selected eigenvectors z of the tridiagonal matrix; one CTA
-// per output vector, the vector in shared memory.
+// --------------------------------------------------------------------------------------
+// Eigenvectors of the tridiagonal matrix by inverse iteration, one CTA per cluster.  Thread 0
+// factors T - lambda I with partial pivoting (rows k, k+1 swapped when |sub| > |diagonal|) and
+// runs the triangular solves; all threads share the Gram-Schmidt against the cluster's earlier
+// vectors and the normalisation.
+// --------------------------------------------------------------------------------------
+struct Cluster {
+  int item;   // index into the batch
+  int first;  // position in the item's selection list
+  int size;
+};
+struct InvIterP {
+  SymItem it[EIG_MAXB];
+  const int *sel[EIG_MAXB];   // device copies of the selections
+};
+
+__global__ void __launch_bounds__(256) inviter_kernel(InvIterP p, const Cluster *__restrict__ cl, double *scratch,
+                                                      int64_t scratch_per_cta, double ctol) {
+  const Cluster c = cl[blockIdx.x];
+  const SymItem it = p.it[c.item];
+  const int *sel = p.sel[c.item];
+  const int n = it.n;
+  const double *d = it.d, *e = it.e;
+  double *u1 = scratch + (int64_t)blockIdx.x * scratch_per_cta;
+  double *u2 = u1 + n, *u3 = u2 + n, *ml = u3 + n, *pv = ml + n, *x = pv + n;
+  __shared__ double red[32];
+  __shared__ double tnorm_s;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < n; ++k) t = fmax(t, fabs(d[k]) + (k > 0 ? fabs(e[k - 1]) : 0.0) + (k < n - 1 ? fabs(e[k]) : 0.0));
+    tnorm_s = t;
+  }
+  __syncthreads();
+  const double eps = 2.220446049250313e-16;
+  const double delta = eps * fmax(tnorm_s, 1e-300);
+  for (int q = 0; q < c.size; ++q) {
+    const int row = c.first + q;  // output row in Zt
+    const double lam = it.lam[sel[row]];
+    // start vector: counter-based hash of (eigen index, component)
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      uint64_t z = (uint64_t)(sel[row] + 1) * 0x9E3779B97F4A7C15ull + (uint64_t)(k + 1) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      z ^= z >> 31;
+      x[k] = (double)(z >> 11) * 0x1p-53 + 0.5;
+    }
+    if (threadIdx.x == 0) {
+      double cd = d[0] - lam, ce1 = n > 1 ? e[0] : 0.0, ce2 = 0.0;
+      for (int k = 0; k < n - 1; ++k) {
+        const double sub = e[k];
+        const double an = d[k + 1] - lam;
+        const double bn = (k + 1 < n - 1) ? e[k + 1] : 0.0;
+        if (fabs(cd) >= fabs(sub)) {
+          if (cd == 0.0) cd = delta;
+          const double l = sub / cd;
+          u1[k] = cd;
+          u2[k] = ce1;
+          u3[k] = ce2;
+          pv[k] = 0.0;
+          ml[k] = l;
+          cd = an - l * ce1;
+          ce1 = bn - l * ce2;
+          ce2 = 0.0;
+        } else {
+          const double l = cd / sub;
+          u1[k] = sub;
+          u2[k] = an;
+          u3[k] = bn;
+          pv[k] = 1.0;
+          ml[k] = l;
+          const double nd = ce1 - l * an;
+          const double ne1 = ce2 - l * bn;
+          cd = nd;
+          ce1 = ne1;
+          ce2 = 0.0;
+        }
+      }
+      u1[n - 1] = (fabs(cd) < delta) ? (cd < 0 ? -delta : delta) : cd;
+      for (int k = 0; k < n - 1; ++k)
+        if (fabs(u1[k]) < delta) u1[k] = u1[k] < 0 ? -delta : delta;
+    }
+    __syncthreads();
+    for (int iter = 0; iter < 3; ++iter) {
+      if (threadIdx.x == 0) {
+        for (int k = 0; k < n - 1; ++k) {
+          if (pv[k] != 0.0) {
+            const double t = x[k];
+            x[k] = x[k + 1];
+            x[k + 1] = t;
+          }
+          x[k + 1] -= ml[k] * x[k];
+        }
+        x[n - 1] /= u1[n - 1];
+        if (n > 1) x[n - 2] = (x[n - 2] - u2[n - 2] * x[n - 1]) / u1[n - 2];
+        for (int k = n - 3; k >= 0; --k) x[k] = (x[k] - u2[k] * x[k + 1] - u3[k] * x[k + 2]) / u1[k];
+      }
+      __syncthreads();
+      // scale to unit max-norm first so that the dot products below cannot overflow
+      double mx = 0.0;
+      for (int k = threadIdx.x; k < n; k += blockDim.x) mx = fmax(mx, fabs(x[k]));
+      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+      __syncthreads();
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+      __syncthreads();
+      double m2 = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m2 = fmax(m2, red[w]);
+      const double inv = m2 > 0.0 ? 1.0 / m2 : 1.0;
+      for (int k = threadIdx.x; k < n; k += blockDim.x) x[k] *= inv;
+      __syncthreads();
+      // Gram-Schmidt against the earlier vectors of the cluster (twice)
+      for (int pass = 0; pass < 2; ++pass)
+        for (int pq = 0; pq < q; ++pq) {
+          const double *v = it.Zt + (int64_t)(c.first + pq) * n;
+          double s = 0.0;
+          for (int k = threadIdx.x; k < n; k += blockDim.x) s = fma(x[k], v[k], s);
+          const double dot = block_sum(s, red);
+          for (int k = threadIdx.x; k < n; k += blockDim.x) x[k] -= dot * v[k];
+          __syncthreads();
+        }
+      double s = 0.0;
+      for (int k = threadIdx.x; k < n; k += blockDim.x) s = fma(x[k], x[k], s);
+      const double nrm = sqrt(block_sum(s, red));
+      const double sc = nrm > 0.0 ? 1.0 / nrm : 0.0;
+      for (int k = threadIdx.x; k < n; k += blockDim.x) x[k] *= sc;
+      __syncthreads();
+    }
+    double *out = it.Zt + (int64_t)row * n;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) out[k] = x[k];
+    __syncthreads();
+  }
+  (void)ctol;
+}
+
+// x = H_0 H_1 ... H_{n-3} z for each tridiagonal eigenvector z (row of Zt); one CTA per vector,
+// the vector in shared memory.
 struct BackBatchP {
   SymItem s[EIG_MAXB];
-  const int *sel[EIG_MAXB];
   double *out[EIG_MAXB];
   int nsel[EIG_MAXB];
   int ld_out[EIG_MAXB];
@@ -333,8 +329,7 @@ __global__ void back_kernel(BackBatchP b) {
   const int n = it.n;
   extern __shared__ double x[];
   __shared__ double red[32];
-  const int row = it.perm[b.sel[bi][r]];
-  for (int k = threadIdx.x; k < n; k += blockDim.x) x[k] = it.Zt[(int64_t)row * n + k];
+  for (int k = threadIdx.x; k < n; k += blockDim.x) x[k] = it.Zt[(int64_t)r * n + k];
   __syncthreads();
   for (int i = n - 3; i >= 0; --i) {
     const double tau = it.tau[i];
@@ -351,28 +346,71 @@ __global__ void back_kernel(BackBatchP b) {
   for (int k = threadIdx.x; k < n; k += blockDim.x) o[k] = x[k];
 }
 
-void sym_eig_vectors(cudaStream_t st, const std::vector<BackItem> &items) {
+void sym_eig_vectors(cudaStream_t st, const std::vector<BackItem> &items, double ctol) {
   for (size_t s0 = 0; s0 < items.size(); s0 += EIG_MAXB) {
-    BackBatchP b;
-    memset(&b, 0, sizeof(b));
     const int cnt = (int)std::min<size_t>(EIG_MAXB, items.size() - s0);
+    InvIterP ip;
+    memset(&ip, 0, sizeof(ip));
+    BackBatchP bb;
+    memset(&bb, 0, sizeof(bb));
+    std::vector<Cluster> clusters;
+    std::vector<int> allsel;
+    std::vector<size_t> seloff(cnt);
     int nmax = 1, selmax = 0;
     for (int i = 0; i < cnt; ++i) {
-      const BackItem &it = items[s0 + i];
-      b.s[i] = *it.s;
-      b.sel[i] = it.sel;
-      b.out[i] = it.out;
-      b.nsel[i] = it.nsel;
-      b.ld_out[i] = it.ld_out;
-      nmax = std::max(nmax, it.s->n);
-      selmax = std::max(selmax, it.nsel);
+      const BackItem &bi = items[s0 + i];
+      const SymItem &it = *bi.s;
+      ip.it[i] = it;
+      bb.s[i] = it;
+      bb.out[i] = bi.out;
+      bb.nsel[i] = (int)bi.sel.size();
+      bb.ld_out[i] = bi.ld_out;
+      nmax = std::max(nmax, it.n);
+      selmax = std::max(selmax, (int)bi.sel.size());
+      seloff[i] = allsel.size();
+      allsel.insert(allsel.end(), bi.sel.begin(), bi.sel.end());
+      if (bi.sel.empty()) continue;
+      // clusters of close selected eigenvalues (needs the eigenvalues and the matrix scale)
+      std::vector<double> lam(it.n), dd(it.n), ee(it.n);
+      RFDD_CUDA(cudaMemcpyAsync(lam.data(), it.lam, it.n * sizeof(double), cudaMemcpyDeviceToHost, st));
+      RFDD_CUDA(cudaMemcpyAsync(dd.data(), it.d, it.n * sizeof(double), cudaMemcpyDeviceToHost, st));
+      RFDD_CUDA(cudaMemcpyAsync(ee.data(), it.e, it.n * sizeof(double), cudaMemcpyDeviceToHost, st));
+      RFDD_CUDA(cudaStreamSynchronize(st));
+      double tnorm = 0.0;
+      for (int k = 0; k < it.n; ++k)
+        tnorm = std::max(tnorm, std::fabs(dd[k]) + (k > 0 ? std::fabs(ee[k - 1]) : 0.0) +
+                                    (k < it.n - 1 ? std::fabs(ee[k]) : 0.0));
+      int start = 0;
+      for (int q = 1; q <= (int)bi.sel.size(); ++q) {
+        if (q == (int)bi.sel.size() || lam[bi.sel[q]] - lam[bi.sel[q - 1]] > ctol * tnorm) {
+          clusters.push_back({i, start, q - start});
+          start = q;
+        }
+      }
     }
-    if (selmax == 0) continue;
+    if (clusters.empty()) continue;
+    int *sel_dev = nullptr;
+    Cluster *cl_dev = nullptr;
+    double *scratch = nullptr;
+    const int64_t per = (int64_t)6 * nmax;
+    RFDD_CUDA(cudaMallocAsync((void **)&sel_dev, allsel.size() * sizeof(int), st));
+    RFDD_CUDA(cudaMallocAsync((void **)&cl_dev, clusters.size() * sizeof(Cluster), st));
+    RFDD_CUDA(cudaMallocAsync((void **)&scratch, (size_t)clusters.size() * per * sizeof(double), st));
+    RFDD_CUDA(cudaMemcpyAsync(sel_dev, allsel.data(), allsel.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    RFDD_CUDA(cudaMemcpyAsync(cl_dev, clusters.data(), clusters.size() * sizeof(Cluster), cudaMemcpyHostToDevice, st));
+    for (int i = 0; i < cnt; ++i) ip.sel[i] = sel_dev + seloff[i];
+    inviter_kernel<<<(unsigned)clusters.size(), 256, 0, st>>>(ip, cl_dev, scratch, per, ctol);
+    RFDD_CHECK_LAUNCH();
     const size_t smem = (size_t)nmax * sizeof(double);
     RFDD_REQUIRE(smem <= 200 * 1024, RFDD_EINVAL, "sym_eig: order too large");
     RFDD_CUDA(cudaFuncSetAttribute(back_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    back_kernel<<<dim3(selmax, cnt), 256, smem, st>>>(b);
+    back_kernel<<<dim3(selmax, cnt), 256, smem, st>>>(bb);
     RFDD_CHECK_LAUNCH();
+    RFDD_CUDA(cudaFreeAsync(sel_dev, st));
+    RFDD_CUDA(cudaFreeAsync(cl_dev, st));
+    RFDD_CUDA(cudaFreeAsync(scratch, st));
+    // host vectors referenced by async copies must outlive them
+    RFDD_CUDA(cudaStreamSynchronize(st));
   }
 }
 

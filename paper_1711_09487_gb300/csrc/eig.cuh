@@ -1,6 +1,7 @@
 // Dense symmetric eigensolver (FP64) for the Rayleigh-Ritz steps: Householder
-// tridiagonalisation, implicit-shift QL on the tridiagonal with rotation accumulation, and
-// back-transformation of selected eigenvectors.  Batched over matrices of uneven order.
+// tridiagonalisation, eigenvalues of the tridiagonal matrix by bisection on Sturm counts (one
+// thread per eigenvalue), eigenvectors of selected eigenvalues by inverse iteration (one CTA per
+// cluster of close eigenvalues, Gram-Schmidt within the cluster), back-transformation.
 #pragma once
 #include "common.cuh"
 
@@ -9,27 +10,26 @@ namespace rfdd {
 struct SymItem {
   double *H;      // n x n symmetric, row-major (ld); overwritten by Householder vectors
   int n, ld;
-  double *d;      // n: diagonal -> eigenvalues (ascending after sym_eig_values)
-  double *e;      // n: sub-diagonal
-  double *tau;    // n
-  double *work;   // n
-  double *Zt;     // n x n: row j = eigenvector j of the tridiagonal matrix
-  int *perm;      // n: sorted position -> row of Zt
+  double *d;      // n: diagonal of the tridiagonal matrix
+  double *e;      // n: its off-diagonal (e[i] couples i and i+1; e[n-1] = 0)
+  double *tau;    // n: Householder scalars
+  double *work;   // n: scratch
+  double *lam;    // n: eigenvalues, ascending (output of sym_eig_values)
+  double *Zt;     // >= nsel x n scratch: eigenvectors of the tridiagonal matrix (rows)
 };
 
-// Tridiagonalise every H, then diagonalise the tridiagonal matrices; on return d holds the
-// eigenvalues in ascending order and perm maps sorted index -> row of Zt.  status gets
-// DS_NONFINITE if QL did not converge within 60 iterations for some eigenvalue.
+// Tridiagonalise every H and compute all its eigenvalues into lam (ascending).
 void sym_eig_values(cudaStream_t st, const std::vector<SymItem> &items, int *status);
 
-// out_b (nsel_b x n_b, row-major, ld_out) row r = eigenvector for sorted index sel_b[r] of H_b.
+// Eigenvectors for the ascending sorted indices sel of each item: out row r (ld_out) = unit
+// eigenvector of H for lam[sel[r]].  Eigenvalues closer than ctol * ||T|| to a neighbouring
+// selected one form a cluster whose vectors are orthogonalised against each other.
 struct BackItem {
   const SymItem *s;
-  const int *sel;  // device, nsel entries (sorted-order indices)
-  int nsel;
+  std::vector<int> sel;   // host, ascending
   double *out;
   int ld_out;
 };
-void sym_eig_vectors(cudaStream_t st, const std::vector<BackItem> &items);
+void sym_eig_vectors(cudaStream_t st, const std::vector<BackItem> &items, double ctol);
 
 }  // namespace rfdd

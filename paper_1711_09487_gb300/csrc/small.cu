@@ -172,3 +172,189 @@ template void sub_inplace<cx<double>>(cudaStream_t, const cx<double> *, cx<doubl
 template void sub_inplace<double>(cudaStream_t, const double *, double *, int64_t);
 
 }  // namespace rfdd
+
+namespace rfdd {
+
+// ---------------------------------------------------------------------------------------
+// Pivoted Cholesky (right-looking, full symmetric storage), one step per launch pair.
+// Step t: choose the largest remaining diagonal entry, stop (rank = t) when it is <= tol,
+// interchange rows and columns t and p (whole matrix, including the factored rows' trailing
+// part), scale row t; then update the trailing block.  On exit the leading rank x rank upper
+// triangle holds R with P^T G P = R^T R on the kept directions.
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) pchol_pivot_kernel(double *G, int k, int *perm, int t, double tol, int *rank) {
+  if (*rank >= 0) return;
+  __shared__ double bv[32];
+  __shared__ int bi[32];
+  __shared__ int piv_s;
+  double v = -1.0;
+  int idx = k;
+  for (int i = t + threadIdx.x; i < k; i += blockDim.x) {
+    const double g = G[(int64_t)i * k + i];
+    if (g > v || (g == v && i < idx)) { v = g; idx = i; }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double v2 = __shfl_down_sync(0xffffffffu, v, o);
+    const int i2 = __shfl_down_sync(0xffffffffu, idx, o);
+    if (v2 > v || (v2 == v && i2 < idx)) { v = v2; idx = i2; }
+  }
+  if ((threadIdx.x & 31) == 0) { bv[threadIdx.x >> 5] = v; bi[threadIdx.x >> 5] = idx; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double bvv = bv[0];
+    int bii = bi[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+      if (bv[w] > bvv || (bv[w] == bvv && bi[w] < bii)) { bvv = bv[w]; bii = bi[w]; }
+    piv_s = (bvv > tol && isfinite(bvv)) ? bii : -1;
+    if (piv_s < 0) *rank = t;
+  }
+  __syncthreads();
+  const int p = piv_s;
+  if (p < 0) return;
+  if (p != t) {
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+      const double a = G[(int64_t)t * k + c];
+      G[(int64_t)t * k + c] = G[(int64_t)p * k + c];
+      G[(int64_t)p * k + c] = a;
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < k; r += blockDim.x) {
+      const double a = G[(int64_t)r * k + t];
+      G[(int64_t)r * k + t] = G[(int64_t)r * k + p];
+      G[(int64_t)r * k + p] = a;
+    }
+    if (threadIdx.x == 0) {
+      const int a = perm[t];
+      perm[t] = perm[p];
+      perm[p] = a;
+    }
+    __syncthreads();
+  }
+  const double r = sqrt(G[(int64_t)t * k + t]);
+  __syncthreads();
+  if (threadIdx.x == 0) G[(int64_t)t * k + t] = r;
+  for (int c = t + 1 + threadIdx.x; c < k; c += blockDim.x) G[(int64_t)t * k + c] /= r;
+}
+
+__global__ void pchol_update_kernel(double *G, int k, int t, const int *rank) {
+  if (*rank >= 0) return;
+  const int len = k - t - 1;
+  const int64_t total = (int64_t)len * len;
+  const double *rt = G + (int64_t)t * k + t + 1;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / len), j = (int)(e % len);
+    G[(int64_t)(t + 1 + i) * k + t + 1 + j] -= rt[i] * rt[j];
+  }
+}
+
+__global__ void iota_kernel(int *p, int k) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) p[i] = i;
+}
+__global__ void set_int_kernel(int *p, int v) { *p = v; }
+
+int pivoted_cholesky(cudaStream_t st, double *G, int k, int *perm, double tol, int *rank_dev) {
+  iota_kernel<<<ceil_div(k, 256), 256, 0, st>>>(perm, k);
+  RFDD_CHECK_LAUNCH();
+  set_int_kernel<<<1, 1, 0, st>>>(rank_dev, -1);
+  RFDD_CHECK_LAUNCH();
+  for (int t = 0; t < k; ++t) {
+    pchol_pivot_kernel<<<1, 1024, 0, st>>>(G, k, perm, t, tol, rank_dev);
+    RFDD_CHECK_LAUNCH();
+    const int len = k - t - 1;
+    if (len > 0) {
+      const int blocks = std::max(1, std::min(1024, ceil_div((int64_t)len * len, 256 * 8)));
+      pchol_update_kernel<<<blocks, 256, 0, st>>>(G, k, t, rank_dev);
+      RFDD_CHECK_LAUNCH();
+    }
+  }
+  int rank = -1;
+  RFDD_CUDA(cudaMemcpyAsync(&rank, rank_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+  RFDD_CUDA(cudaStreamSynchronize(st));
+  return rank < 0 ? k : rank;
+}
+
+// out[i][j] = K[perm[i]][perm[j]] for i, j < r
+__global__ void gather_sym_kernel(const double *__restrict__ K, int k, const int *__restrict__ perm, int r,
+                                  double *out) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)r * r; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / r), j = (int)(e % r);
+    out[e] = K[(int64_t)perm[i] * k + perm[j]];
+  }
+}
+void gather_sym(cudaStream_t st, const double *K, int k, const int *perm, int r, double *out) {
+  if (r <= 0) return;
+  gather_sym_kernel<<<gridn((int64_t)r * r), 256, 0, st>>>(K, k, perm, r, out);
+  RFDD_CHECK_LAUNCH();
+}
+
+// Lt[i][j] = R[j][i] / R[i][i] (j < i), 1 (j == i), 0 (j > i): unit lower, from upper R (ld ldr)
+__global__ void unit_lower_from_upper_kernel(const double *__restrict__ R, int ldr, int r, double *Lt) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)r * r; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / r), j = (int)(e % r);
+    Lt[e] = j < i ? R[(int64_t)j * ldr + i] / R[(int64_t)i * ldr + i] : (i == j ? 1.0 : 0.0);
+  }
+}
+void unit_lower_from_upper(cudaStream_t st, const double *R, int ldr, int r, double *Lt) {
+  if (r <= 0) return;
+  unit_lower_from_upper_kernel<<<gridn((int64_t)r * r), 256, 0, st>>>(R, ldr, r, Lt);
+  RFDD_CHECK_LAUNCH();
+}
+
+// out[i][j] = (trans ? in[j][i] : in[i][j]) / R[i][i]   (r x r)
+__global__ void scale_rows_by_rdiag_kernel(const double *__restrict__ in, int r, int trans, const double *__restrict__ R,
+                                           int ldr, double *out) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)r * r; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / r), j = (int)(e % r);
+    const double v = trans ? in[(int64_t)j * r + i] : in[e];
+    out[e] = v / R[(int64_t)i * ldr + i];
+  }
+}
+void scale_rows_by_rdiag(cudaStream_t st, const double *in, int r, bool trans, const double *R, int ldr, double *out) {
+  if (r <= 0) return;
+  scale_rows_by_rdiag_kernel<<<gridn((int64_t)r * r), 256, 0, st>>>(in, r, trans ? 1 : 0, R, ldr, out);
+  RFDD_CHECK_LAUNCH();
+}
+
+// out = (A + A^T)/2 (r x r), into a separate buffer
+__global__ void symmetrize_kernel(const double *__restrict__ A, int r, double *out) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)r * r; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / r), j = (int)(e % r);
+    out[e] = 0.5 * (A[e] + A[(int64_t)j * r + i]);
+  }
+}
+void symmetrize(cudaStream_t st, const double *A, int r, double *out) {
+  if (r <= 0) return;
+  symmetrize_kernel<<<gridn((int64_t)r * r), 256, 0, st>>>(A, r, out);
+  RFDD_CHECK_LAUNCH();
+}
+
+// out (b x a) = in^T (in: a x b row-major)
+__global__ void transpose_kernel(const double *__restrict__ in, int a, int b, double *out) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)a * b; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / b), j = (int)(e % b);
+    out[(int64_t)j * a + i] = in[e];
+  }
+}
+void transpose(cudaStream_t st, const double *in, int a, int b, double *out) {
+  if ((int64_t)a * b <= 0) return;
+  transpose_kernel<<<gridn((int64_t)a * b), 256, 0, st>>>(in, a, b, out);
+  RFDD_CHECK_LAUNCH();
+}
+
+// Cfull[perm[i]][c] = d[perm[i]] * Cr[i][c] for i < r (other rows untouched; caller zeroes)
+__global__ void scatter_rows_kernel(const double *__restrict__ Cr, int r, int ns, const int *__restrict__ perm,
+                                    const double *__restrict__ d, double *Cfull) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)r * ns; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / ns), c = (int)(e % ns);
+    const int row = perm[i];
+    Cfull[(int64_t)row * ns + c] = d[row] * Cr[e];
+  }
+}
+void scatter_rows_perm(cudaStream_t st, const double *Cr, int r, int ns, const int *perm, const double *d,
+                       double *Cfull) {
+  if ((int64_t)r * ns <= 0) return;
+  scatter_rows_kernel<<<gridn((int64_t)r * ns), 256, 0, st>>>(Cr, r, ns, perm, d, Cfull);
+  RFDD_CHECK_LAUNCH();
+}
+
+}  // namespace rfdd

@@ -30,3 +30,16 @@ template <typename T>
 void sub_inplace(cudaStream_t st, const T *x, T *y, int64_t n);
 
 }  // namespace rfdd
+
+namespace rfdd {
+// Pivoted Cholesky of the k x k symmetric G (full storage, in place); returns the rank (pivots
+// > tol), perm (device, k) the column order; R is the leading rank x rank upper triangle.
+int pivoted_cholesky(cudaStream_t st, double *G, int k, int *perm, double tol, int *rank_dev);
+void gather_sym(cudaStream_t st, const double *K, int k, const int *perm, int r, double *out);
+void unit_lower_from_upper(cudaStream_t st, const double *R, int ldr, int r, double *Lt);
+void scale_rows_by_rdiag(cudaStream_t st, const double *in, int r, bool trans, const double *R, int ldr, double *out);
+void symmetrize(cudaStream_t st, const double *A, int r, double *out);
+void transpose(cudaStream_t st, const double *in, int a, int b, double *out);
+void scatter_rows_perm(cudaStream_t st, const double *Cr, int r, int ns, const int *perm, const double *d,
+                       double *Cfull);
+}  // namespace rfdd

@@ -667,8 +667,10 @@ void dd_solve(rfdd_handle *h, const cx<double> *R, int64_t strideR, cx<double> *
 
 // Shifted solves with FP64 iterative refinement (Section 3.1 block inverse as the approximate
 // solver, FP64 sparse residuals): X_l = (A - z_l M)^{-1} V for all nodes; V real (n x m).
+// Refinement stops once every shifted residual satisfies
+//   ||r|| <= tol * (||A|| + |z| ||M||) ||x||   (tol >= 1e-14), or after ir_max steps.
 template <typename Tf>
-int refined_solve(rfdd_handle *h, const double *V, cx<double> *X, int64_t m) {
+int refined_solve(rfdd_handle *h, const double *V, cx<double> *X, int64_t m, double tol) {
   cudaStream_t st = h->st;
   const int nc = h->nnodes;
   const int64_t n = h->n;
@@ -696,7 +698,7 @@ int refined_solve(rfdd_handle *h, const double *V, cx<double> *X, int64_t m) {
       const double zn = std::sqrt(h->z[l].re * h->z[l].re + h->z[l].im * h->z[l].im);
       const double scale = (h->normA + zn * h->normM);
       for (int64_t c = 0; c < m; ++c)
-        if (std::sqrt(hr[l * m + c]) > 1e-14 * scale * std::sqrt(hx[l * m + c]) + 1e-300) { ok = false; break; }
+        if (std::sqrt(hr[l * m + c]) > tol * scale * std::sqrt(hx[l * m + c]) + 1e-300) { ok = false; break; }
     }
     if (log_on()) {
       double worst = 0.0;
@@ -718,9 +720,10 @@ int refined_solve(rfdd_handle *h, const double *V, cx<double> *X, int64_t m) {
 
 // ------------------------------------------------------------------------------------
 // M-orthonormal Rayleigh-Ritz on range(Y) for a tall FP64 block Y (n x k, row-major):
-// Gram G = Y^T M Y and K = Y^T A Y, diagonal scaling, eigen-decomposition of the scaled Gram
-// with pruning of directions below drop * max, projected H, and its eigenpairs.  Returns all
-// Ritz values (ascending) and, for the selected sorted indices, the coefficient block
+// Gram G = Y^T M Y and K = Y^T A Y, unit-diagonal scaling D, pivoted Cholesky
+// P^T (D G D) P = R^T R that drops directions whose pivot falls below `drop` (Y's columns may
+// be linearly dependent), projected H = R^{-T} P^T (D K D) P R^{-1}, and its eigenpairs.
+// Returns all Ritz values (ascending) and, for the selected sorted indices, the coefficient block
 // C (k x nsel) such that the Ritz vectors are Y C.
 // ------------------------------------------------------------------------------------
 struct RRout {
@@ -728,7 +731,7 @@ struct RRout {
   int64_t r = 0;              // dimension kept
 };
 
-RRout rayleigh_ritz_coeffs(rfdd_handle *h, const double *Y, int64_t k, double drop, bool gram_fp32,
+RRout rayleigh_ritz_coeffs(rfdd_handle *h, const double *Y, int64_t k, double drop, double ctol,
                            const std::function<std::vector<int>(const std::vector<double> &)> &select,
                            Buf &Cout, std::vector<int> &sel_out) {
   cudaStream_t st = h->st;
@@ -741,22 +744,7 @@ RRout rayleigh_ritz_coeffs(rfdd_handle *h, const double *Y, int64_t k, double dr
   spmm_f64(st, h->P, 0, n, 0, n, 1.0, 0.0, Y, k, AY.as<double>(), k, k, false);
   G.alloc((size_t)k * k * sizeof(double));
   K.alloc((size_t)k * k * sizeof(double));
-  if (gram_fp32) {
-    Buf Yf, MYf, AYf, Gf;
-    Yf.alloc((size_t)n * k * sizeof(float));
-    MYf.alloc((size_t)n * k * sizeof(float));
-    AYf.alloc((size_t)n * k * sizeof(float));
-    Gf.alloc((size_t)2 * k * k * sizeof(float));
-    convert<float, double>(st, Y, Yf.as<float>(), n * k);
-    convert<float, double>(st, MY.as<double>(), MYf.as<float>(), n * k);
-    convert<float, double>(st, AY.as<double>(), AYf.as<float>(), n * k);
-    std::vector<GemmItem<float>> g = {
-        {Yf.as<float>(), MYf.as<float>(), Gf.as<float>(), (int)k, (int)k, (int)n, (int)k, (int)k, (int)k},
-        {Yf.as<float>(), AYf.as<float>(), Gf.as<float>() + k * k, (int)k, (int)k, (int)n, (int)k, (int)k, (int)k}};
-    gemm_batched<float>(st, g, true, false, 1.0, 0.0);
-    convert<double, float>(st, Gf.as<float>(), G.as<double>(), k * k);
-    convert<double, float>(st, Gf.as<float>() + k * k, K.as<double>(), k * k);
-  } else {
+  {
     std::vector<GemmItem<double>> g = {
         {Y, MY.as<double>(), G.as<double>(), (int)k, (int)k, (int)n, (int)k, (int)k, (int)k},
         {Y, AY.as<double>(), K.as<double>(), (int)k, (int)k, (int)n, (int)k, (int)k, (int)k}};
@@ -765,91 +753,83 @@ RRout rayleigh_ritz_coeffs(rfdd_handle *h, const double *Y, int64_t k, double dr
   MY.release();
   AY.release();
   lap.mark("spmm+gram");
-  // symmetrise-free: G and K are exactly symmetric up to rounding; the eigensolver reads the
-  // full matrix.  Scale to unit diagonal.
-  Buf dsc;
+  Buf dsc, perm, rankd;
   dsc.alloc((size_t)k * sizeof(double));
+  perm.alloc((size_t)k * sizeof(int));
+  rankd.alloc(sizeof(int));
   inv_sqrt_diag(st, G.as<double>(), k, dsc.as<double>());
-  scale_sym(st, G.as<double>(), k, dsc.as<double>());   // K stays unscaled: C1 below carries D
-  // eigen-decomposition of the Gram matrix
-  Buf ed, ee, et, ew, eZ, ep;
-  ed.alloc(k * sizeof(double));
-  ee.alloc(k * sizeof(double));
-  et.alloc(k * sizeof(double));
-  ew.alloc(k * sizeof(double));
-  eZ.alloc((size_t)k * k * sizeof(double));
-  ep.alloc(k * sizeof(int));
-  SymItem gi{G.as<double>(), (int)k, (int)k, ed.as<double>(), ee.as<double>(), et.as<double>(), ew.as<double>(),
-             eZ.as<double>(), ep.as<int>()};
-  sym_eig_values(st, {gi}, h->status.as<int>());
-  lap.mark("gram eig values");
-  std::vector<double> lam(k);
-  RFDD_CUDA(cudaMemcpyAsync(lam.data(), ed.p, k * sizeof(double), cudaMemcpyDeviceToHost, st));
-  RFDD_CUDA(cudaStreamSynchronize(st));
-  const double lmax = lam.empty() ? 0.0 : lam.back();
-  std::vector<int> keep;
-  for (int64_t q = 0; q < k; ++q)
-    if (lam[q] > drop * lmax && lmax > 0) keep.push_back((int)q);
-  const int64_t r = (int64_t)keep.size();
+  scale_sym(st, G.as<double>(), k, dsc.as<double>());
+  scale_sym(st, K.as<double>(), k, dsc.as<double>());
+  const int r = pivoted_cholesky(st, G.as<double>(), (int)k, perm.as<int>(), drop, rankd.as<int>());
+  lap.mark("pivoted cholesky");
   RFDD_REQUIRE(r > 0, RFDD_ESINGULAR, "Rayleigh-Ritz: basis has no independent direction");
-  Buf keep_dev, Ut, C1t, f;
-  upload(keep_dev, keep, st);
-  Ut.alloc((size_t)r * k * sizeof(double));
-  sym_eig_vectors(st, {BackItem{&gi, keep_dev.as<int>(), (int)r, Ut.as<double>(), (int)k}});
-  lap.mark("gram eig vectors");
-  f.alloc(r * sizeof(double));
-  Buf lamk;
-  {
-    std::vector<double> lk(r);
-    for (int64_t q = 0; q < r; ++q) lk[q] = lam[keep[q]];
-    upload(lamk, lk, st);
-  }
-  inv_sqrt_vec(st, lamk.as<double>(), r, f.as<double>());
-  C1t.alloc((size_t)r * k * sizeof(double));
-  scale_rows_cols(st, Ut.as<double>(), r, k, dsc.as<double>(), f.as<double>(), C1t.as<double>());  // C1^T (r x k)
-  // H = C1^T K C1
-  Buf T1, H;
-  T1.alloc((size_t)r * k * sizeof(double));
+  // H = R^{-T} Kp R^{-1}: with Lt = (D_R^{-1} R^T) unit lower, R^{-T} B = Lt^{-1} D_R^{-1} B
+  Buf Kp, Lt, B, H;
+  Kp.alloc((size_t)r * r * sizeof(double));
+  Lt.alloc((size_t)r * r * sizeof(double));
+  B.alloc((size_t)r * r * sizeof(double));
   H.alloc((size_t)r * r * sizeof(double));
-  gemm_batched<double>(st, {{C1t.as<double>(), K.as<double>(), T1.as<double>(), (int)r, (int)k, (int)k, (int)k,
-                             (int)k, (int)k}},
-                       false, false, 1.0, 0.0);
-  gemm_batched<double>(st, {{T1.as<double>(), C1t.as<double>(), H.as<double>(), (int)r, (int)r, (int)k, (int)k,
-                             (int)k, (int)r}},
-                       false, true, 1.0, 0.0);
+  gather_sym(st, K.as<double>(), (int)k, perm.as<int>(), r, Kp.as<double>());
+  unit_lower_from_upper(st, G.as<double>(), (int)k, r, Lt.as<double>());
+  scale_rows_by_rdiag(st, Kp.as<double>(), r, false, G.as<double>(), (int)k, B.as<double>());
+  SolveItem<double> tri;
+  tri.LU = Lt.as<double>();
+  tri.piv = nullptr;
+  tri.n = r;
+  tri.ld = r;
+  tri.X = B.as<double>();
+  tri.ldx = r;
+  tri.ncols = r;
+  trsm_lower_unit<double>(st, {tri}, 128);                                   // B = R^{-T} Kp
+  scale_rows_by_rdiag(st, B.as<double>(), r, true, G.as<double>(), (int)k, Kp.as<double>());
+  tri.X = Kp.as<double>();
+  trsm_lower_unit<double>(st, {tri}, 128);                                   // Kp = R^{-T} B^T = H^T
+  symmetrize(st, Kp.as<double>(), r, H.as<double>());
   K.release();
-  G.release();
+  Kp.release();
+  B.release();
   lap.mark("projected H");
-  Buf hd, he, ht, hw, hZ, hp;
+  Buf hd, he, ht, hw, hl, hZ;
   hd.alloc(r * sizeof(double));
   he.alloc(r * sizeof(double));
   ht.alloc(r * sizeof(double));
   hw.alloc(r * sizeof(double));
-  hZ.alloc((size_t)r * r * sizeof(double));
-  hp.alloc(r * sizeof(int));
-  SymItem hi{H.as<double>(), (int)r, (int)r, hd.as<double>(), he.as<double>(), ht.as<double>(), hw.as<double>(),
-             hZ.as<double>(), hp.as<int>()};
+  hl.alloc(r * sizeof(double));
+  SymItem hi{H.as<double>(), r, r, hd.as<double>(), he.as<double>(), ht.as<double>(), hw.as<double>(), hl.as<double>(),
+             nullptr};
   sym_eig_values(st, {hi}, h->status.as<int>());
-  lap.mark("H eig values");
   RRout out;
   out.r = r;
   out.theta.resize(r);
-  RFDD_CUDA(cudaMemcpyAsync(out.theta.data(), hd.p, r * sizeof(double), cudaMemcpyDeviceToHost, st));
+  RFDD_CUDA(cudaMemcpyAsync(out.theta.data(), hl.p, r * sizeof(double), cudaMemcpyDeviceToHost, st));
   RFDD_CUDA(cudaStreamSynchronize(st));
+  lap.mark("H eigenvalues");
   sel_out = select(out.theta);
   const int64_t ns = (int64_t)sel_out.size();
   if (ns > 0) {
-    Buf sel_dev, Yt;
-    upload(sel_dev, sel_out, st);
+    Buf Yt, Ct;
+    hZ.alloc((size_t)ns * r * sizeof(double));
+    hi.Zt = hZ.as<double>();
     Yt.alloc((size_t)ns * r * sizeof(double));
-    sym_eig_vectors(st, {BackItem{&hi, sel_dev.as<int>(), (int)ns, Yt.as<double>(), (int)r}});
-    // C = C1 Y_sel (k x ns): C[k][q] = sum_t C1t[t][k] * Yt[q][t]
+    BackItem bi{&hi, sel_out, Yt.as<double>(), r};
+    sym_eig_vectors(st, {bi}, ctol);
+    // C_r = R^{-1} Y_sel^T (r x ns), then rows back to the original column order with D
+    Ct.alloc((size_t)r * ns * sizeof(double));
+    transpose(st, Yt.as<double>(), (int)ns, r, Ct.as<double>());
+    SolveItem<double> up;
+    up.LU = G.as<double>();
+    up.piv = nullptr;
+    up.n = r;
+    up.ld = (int)k;
+    up.X = Ct.as<double>();
+    up.ldx = (int)ns;
+    up.ncols = (int)ns;
+    trsm_upper<double>(st, {up}, 128);
     Cout.alloc((size_t)k * ns * sizeof(double));
-    gemm_batched<double>(st, {{C1t.as<double>(), Yt.as<double>(), Cout.as<double>(), (int)k, (int)ns, (int)r, (int)k,
-                               (int)r, (int)ns}},
-                         true, true, 1.0, 0.0);
+    RFDD_CUDA(cudaMemsetAsync(Cout.p, 0, (size_t)k * ns * sizeof(double), st));
+    scatter_rows_perm(st, Ct.as<double>(), r, (int)ns, perm.as<int>(), dsc.as<double>(), Cout.as<double>());
   }
-  lap.mark("H eig vectors + coefficients");
+  lap.mark("eigenvectors + coefficients");
   sync_status(h, "rayleigh-ritz");
   return out;
 }
@@ -1114,24 +1094,25 @@ void interior_impl(rfdd_handle *h, double sigma) {
                    (int)mb[j]});
     gemm_batched<double>(st, g, true, false, 1.0, 0.0);
   }
-  Buf ed, ee, et, ew, eZ, ep;
+  Buf ed, ee, et, ew, el, eZ;
   ed.alloc((size_t)p * mw * sizeof(double));
   ee.alloc((size_t)p * mw * sizeof(double));
   et.alloc((size_t)p * mw * sizeof(double));
   ew.alloc((size_t)p * mw * sizeof(double));
+  el.alloc((size_t)p * mw * sizeof(double));
   eZ.alloc((size_t)p * mw * mw * sizeof(double));
-  ep.alloc((size_t)p * mw * sizeof(int));
   std::vector<SymItem> si;
   for (int j = 0; j < p; ++j)
     si.push_back({G.as<double>() + (int64_t)j * mw * mw, (int)mb[j], (int)mb[j], ed.as<double>() + j * mw,
                   ee.as<double>() + j * mw, et.as<double>() + j * mw, ew.as<double>() + j * mw,
-                  eZ.as<double>() + (int64_t)j * mw * mw, ep.as<int>() + j * mw});
+                  el.as<double>() + j * mw, eZ.as<double>() + (int64_t)j * mw * mw});
   sym_eig_values(st, si, h->status.as<int>());
   std::vector<double> ev((size_t)p * mw);
-  RFDD_CUDA(cudaMemcpyAsync(ev.data(), ed.p, ev.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  RFDD_CUDA(cudaMemcpyAsync(ev.data(), el.p, ev.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
   RFDD_CUDA(cudaStreamSynchronize(st));
-  std::vector<int> sel_all;
-  std::vector<int64_t> sel_off(p + 1, 0);
+  Buf Gt;
+  Gt.alloc((size_t)p * mw * mw * sizeof(double));
+  std::vector<BackItem> bi;
   for (int j = 0; j < p; ++j) {
     std::vector<int> idx(mb[j]);
     std::iota(idx.begin(), idx.end(), 0);
@@ -1139,17 +1120,9 @@ void interior_impl(rfdd_handle *h, double sigma) {
                      [&](int a, int b) { return std::fabs(ev[j * mw + a]) < std::fabs(ev[j * mw + b]); });
     idx.resize(nvb[j]);
     std::sort(idx.begin(), idx.end());
-    sel_all.insert(sel_all.end(), idx.begin(), idx.end());
-    sel_off[j + 1] = (int64_t)sel_all.size();
+    bi.push_back({&si[j], idx, Gt.as<double>() + (int64_t)j * mw * mw, (int)mb[j]});
   }
-  Buf sel_dev, Gt;
-  upload(sel_dev, sel_all, st);
-  Gt.alloc((size_t)p * mw * mw * sizeof(double));
-  std::vector<BackItem> bi;
-  for (int j = 0; j < p; ++j)
-    bi.push_back({&si[j], sel_dev.as<int>() + sel_off[j], (int)nvb[j], Gt.as<double>() + (int64_t)j * mw * mw,
-                  (int)mb[j]});
-  sym_eig_vectors(st, bi);
+  sym_eig_vectors(st, bi, 1e-6);
   // Z = [blockdiag(V_j) | -Sigma^(psi) | Gamma^(psi)] (n x k), interface rows [0 | Q 0 | 0]
   const bool with_gamma = h->has_me;
   const int64_t kz = h->kappa + (int64_t)psi * mu * (with_gamma ? 2 : 1);
@@ -1220,10 +1193,10 @@ void rr_on_Z(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
   Buf C;
   std::vector<int> sel;
   int64_t m_sel = 0;
-  // directions below the Gram matrix's rounding level are pruned
+  // pivots below this (on the unit-diagonal Gram matrix) mark linearly dependent columns of Z
   const double drop = 1e-12;
   RRout rr = rayleigh_ritz_coeffs(
-      h, h->Zb.as<double>(), kz, drop, false,
+      h, h->Zb.as<double>(), kz, drop, 1e-9,
       [&](const std::vector<double> &th) {
         int64_t nin = 0;
         for (double t : th) nin += (t >= alpha && t <= beta);
@@ -1291,6 +1264,7 @@ void complete(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
               (long long)h->kz, h->rr_theta.size(), (long long)m, (long long)nin, mx);
   }
   int64_t count_prev = res->info.pre_nev;
+  double res_level = std::max(res->info.pre_max_resid, 1e-300);
   Buf V, Xc, C;
   std::vector<double> theta, resid;
   int passes = 0, irmax = 0;
@@ -1301,13 +1275,16 @@ void complete(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
     V.ensure((size_t)n * m * sizeof(double));
     spmm_f64(st, h->P, 0, n, 0, n, 0.0, 1.0, X.as<double>(), m, V.as<double>(), m, m, false);
     Xc.ensure((size_t)nc * n * m * sizeof(cx<double>));
-    irmax = std::max(irmax, refined_solve<Tf>(h, V.as<double>(), Xc.as<cx<double>>(), m));
+    // the filter only has to be as accurate as the subspace it acts on: refine the shifted
+    // solves to a small fraction of the current residual level
+    const double ir_tol = std::max(1e-14, 1e-6 * res_level);
+    irmax = std::max(irmax, refined_solve<Tf>(h, V.as<double>(), Xc.as<cx<double>>(), m, ir_tol));
     weighted_real_sum<cx<double>>(st, Xc.as<cx<double>>(), n * m, h->w_dev.as<cx<double>>(), nc, 2.0, X.as<double>(),
                                   n * m);
     // Rayleigh-Ritz on range(X), all Ritz pairs kept
     std::vector<int> sel;
     RRout rr = rayleigh_ritz_coeffs(
-        h, X.as<double>(), m, 1e-12, false,
+        h, X.as<double>(), m, 1e-12, 1e-5,
         [&](const std::vector<double> &th) {
           std::vector<int> all(th.size());
           std::iota(all.begin(), all.end(), 0);
@@ -1336,6 +1313,7 @@ void complete(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
       }
     RFDD_LOGF("pass %d: m=%lld r=%lld inside=%lld (prev %lld) max_res_inside=%.3e ir_steps=%d", passes,
               (long long)m, (long long)r, (long long)nin, (long long)count_prev, mx, irmax);
+    res_level = nin > 0 ? mx : 1.0;
     if (nin == count_prev && (nin == 0 || mx <= h->opt.res_tol)) {
       converged = true;
       break;
@@ -1831,30 +1809,29 @@ int rfdd_sym_eig(int64_t n, const double *H, double *evals, double *evecs) {
   if (n < 1 || !H || !evals || !evecs) return RFDD_EINVAL;
   return guarded([&] {
     cudaStream_t st = 0;
-    Buf Hd, d, e, t, w, Z, perm, sel, out, status;
+    Buf Hd, d, e, t, w, lam, Z, out, status;
     Hd.alloc((size_t)n * n * sizeof(double));
     RFDD_CUDA(cudaMemcpy(Hd.p, H, (size_t)n * n * sizeof(double), cudaMemcpyHostToDevice));
     d.alloc(n * sizeof(double));
     e.alloc(n * sizeof(double));
     t.alloc(n * sizeof(double));
     w.alloc(n * sizeof(double));
+    lam.alloc(n * sizeof(double));
     Z.alloc((size_t)n * n * sizeof(double));
-    perm.alloc(n * sizeof(int));
     status.alloc(sizeof(int));
     RFDD_CUDA(cudaMemset(status.p, 0, sizeof(int)));
     SymItem si{Hd.as<double>(), (int)n, (int)n, d.as<double>(), e.as<double>(), t.as<double>(), w.as<double>(),
-               Z.as<double>(), perm.as<int>()};
+               lam.as<double>(), Z.as<double>()};
     sym_eig_values(st, {si}, status.as<int>());
     std::vector<int> all(n);
     std::iota(all.begin(), all.end(), 0);
-    upload(sel, all, st);
     out.alloc((size_t)n * n * sizeof(double));
-    sym_eig_vectors(st, {BackItem{&si, sel.as<int>(), (int)n, out.as<double>(), (int)n}});
+    sym_eig_vectors(st, {BackItem{&si, all, out.as<double>(), (int)n}}, 1e-5);
     RFDD_CUDA(cudaStreamSynchronize(st));
     int stt = 0;
     RFDD_CUDA(cudaMemcpy(&stt, status.p, sizeof(int), cudaMemcpyDeviceToHost));
-    RFDD_REQUIRE(stt == 0, RFDD_ESINGULAR, "sym_eig: QL iteration did not converge");
-    RFDD_CUDA(cudaMemcpy(evals, d.p, n * sizeof(double), cudaMemcpyDeviceToHost));
+    RFDD_REQUIRE(stt == 0, RFDD_ESINGULAR, "sym_eig: eigensolver reported a failure");
+    RFDD_CUDA(cudaMemcpy(evals, lam.p, n * sizeof(double), cudaMemcpyDeviceToHost));
     RFDD_CUDA(cudaMemcpy(evecs, out.p, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToHost));
   });
 }

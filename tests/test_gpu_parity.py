@@ -190,13 +190,22 @@ def test_interior_chains_and_rr(R, name, prec):
         # last three of the nev_B oracle directions must be captured
         sv = np.linalg.svd(Vg.T @ blk.MB[j] @ Vo[j], compute_uv=False)
         assert sv[:-3].min() >= 0.99, sv
-    # a9: Ritz values on range(Z) vs the oracle's Rayleigh-Ritz on the same Z
+    # a9: Ritz values on range(Z) vs the oracle's Rayleigh-Ritz on the same Z.  Z's columns are
+    # numerically dependent; the oracle prunes near-null directions of Z^T M Z by its
+    # eigendecomposition, the GPU by pivoted Cholesky (both at 1e-12), so the two Ritz sets agree
+    # to the RF-DDES approximation level (a few 1e-6 relative here), not to rounding.  Both must be
+    # equally close to the exact eigenvalues.
     th_g = R.rfdd_rayleigh_ritz(h)
     th_o, _ = O.rayleigh_ritz(blk.Ap, blk.Mp, Z)
     sel_o = th_o[(th_o > w.alpha) & (th_o < w.beta)]
     sel_g = th_g[(th_g > w.alpha) & (th_g < w.beta)]
     assert len(sel_g) == len(sel_o)
-    np.testing.assert_allclose(sel_g, sel_o, rtol=1e-8 if prec == 0 else 1e-5)
+    np.testing.assert_allclose(sel_g, sel_o, rtol=1e-5)
+    ex = w.exact[(w.exact > w.alpha) & (w.exact < w.beta)]
+    if len(ex) == len(sel_o):
+        err_o = np.max(np.abs(sel_o - ex) / ex)
+        err_g = np.max(np.abs(sel_g - ex) / ex)
+        assert err_g <= 3.0 * err_o + 1e-9, (err_g, err_o)
 
 
 def check_result(R, w, ev, X, rs, info, prec):
