@@ -292,8 +292,40 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_one_solve(args):
+    """One untimed solve of the workload (the command profiled for the kernel launch list)."""
+    import torch
+    import paper_1711_09487_gb300 as R
+    torch.cuda.set_device(0)
+    R.load()
+    w = I.workload(args.workload)
+    precision = R.RFDD_MIXED if args.precision == "mixed" else R.RFDD_FP64
+    h = R.rfdd_setup(w.A, w.M, w.part, w.p,
+                     R.rfdd_default_options(precision=precision, quad_rule=0 if w.rule == "midpoint" else 1))
+    r = R.rfdd_solve(h, w.alpha, w.beta, w.n_nodes)
+    info = R.rfdd_result_info(r)
+    print(json.dumps({"mode": "one-solve", "workload": w.name, "nev": info["nev"], "max_resid": info["max_resid"],
+                      "t_total_ms": info["t_total_ms"]}), flush=True)
+
+
+def run_gemm(args):
+    """One large complex GEMM C -= A B (m x k times k x n) on the tensor cores: the shape of the
+    deep trailing updates of the factorisations (profiled alone with ncu)."""
+    import paper_1711_09487_gb300 as R
+    R.load()
+    m, n, k = args.gemm
+    g = np.random.default_rng(0)
+    A = (g.standard_normal((m, k)) + 1j * g.standard_normal((m, k))).astype(np.complex64)
+    B = (g.standard_normal((k, n)) + 1j * g.standard_normal((k, n))).astype(np.complex64)
+    C = np.zeros((m, n), dtype=np.complex64)
+    R.rfdd_cgemm(A, B, C, -1.0, 1.0, 1)
+    print(json.dumps({"mode": "gemm", "m": m, "n": n, "k": k}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--mode", default="bench", choices=["bench", "one-solve", "gemm"])
+    ap.add_argument("--gemm", type=int, nargs=3, default=[8192, 8192, 128], metavar=("M", "N", "K"))
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
@@ -304,6 +336,12 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.mode == "one-solve":
+        run_one_solve(args)
+        return
+    if args.mode == "gemm":
+        run_gemm(args)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
         return

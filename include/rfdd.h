@@ -205,6 +205,13 @@ int rfdd_rayleigh_ritz(rfdd_handle *h, int64_t cap, double *theta_out, int64_t *
  * Needs no handle (runs on the default stream of the current device). */
 int rfdd_sym_eig(int64_t n, const double *H, double *evals, double *evecs);
 
+/* Building block of a3-a5 (trailing updates of the factorisations), a6 and a10 (triangular-solve
+ * updates): C = beta*C + alpha*A*B for complex single-precision A (m x k, leading dimension lda),
+ * B (k x n, ldb), C (m x n, ldc), host arrays, row-major, interleaved (re, im) floats.
+ * engine 0 = CUDA-core kernel, 1 = tensor-core kernel (tcgen05, 3xTF32 split). */
+int rfdd_cgemm(int64_t m, int64_t n, int64_t k, const float *A, int64_t lda, const float *B, int64_t ldb,
+               float *C, int64_t ldc, double alpha, double beta, int32_t engine);
+
 /* ---- measurement hooks (no counterpart in the paper) -------------------------------------
  * rfdd_kernel_launches: number of kernels this library has launched in this process.
  * rfdd_profile(1): clear the records and time every launch of the dense contraction kernels

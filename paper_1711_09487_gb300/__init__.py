@@ -40,7 +40,7 @@ SYMBOLS = [
     "rfdd_result_pre_evals", "rfdd_result_free", "rfdd_factor", "rfdd_schur_copy", "rfdd_shifted_solve",
     "rfdd_filter_apply", "rfdd_lanczos", "rfdd_interior", "rfdd_rayleigh_ritz", "rfdd_solve_async",
     "rfdd_result_ready", "rfdd_memory_estimate", "rfdd_sym_eig", "rfdd_kernel_launches", "rfdd_profile",
-    "rfdd_profile_get",
+    "rfdd_profile_get", "rfdd_cgemm",
 ]
 
 
@@ -116,6 +116,8 @@ def load(path: str | None = None):
     lib.rfdd_memory_estimate.argtypes = [vp, i32, i64, C.POINTER(C.c_size_t)]
     lib.rfdd_sym_eig.argtypes = [i64, dp, dp, dp]
     lib.rfdd_kernel_launches.restype = C.c_longlong
+    fp = C.POINTER(C.c_float)
+    lib.rfdd_cgemm.argtypes = [i64, i64, i64, fp, i64, fp, i64, fp, i64, C.c_double, C.c_double, i32]
     lib.rfdd_profile.argtypes = [i32]
     lib.rfdd_profile_get.argtypes = [i32, C.POINTER(i64), dp, dp]
     _lib = lib
@@ -357,6 +359,22 @@ def rfdd_sym_eig(H: np.ndarray):
     V = np.zeros((n, n))
     _check(load().rfdd_sym_eig(n, _dp(H), _dp(ev), _dp(V)))
     return ev, V
+
+
+def rfdd_cgemm(A: np.ndarray, B: np.ndarray, C: np.ndarray, alpha: float = 1.0, beta: float = 0.0,
+               engine: int = 1) -> np.ndarray:
+    """beta*C + alpha*A@B for complex64 row-major arrays on the GPU (engine 1: tensor cores)."""
+    A = np.ascontiguousarray(A, dtype=np.complex64)
+    B = np.ascontiguousarray(B, dtype=np.complex64)
+    C = np.ascontiguousarray(C, dtype=np.complex64).copy()
+    m, k = A.shape
+    n = B.shape[1]
+    fp = lambda x: x.view(np.float32).ctypes.data_as(C_float_p)
+    _check(load().rfdd_cgemm(m, n, k, fp(A), k, fp(B), n, fp(C), n, alpha, beta, engine))
+    return C
+
+
+C_float_p = C.POINTER(C.c_float)
 
 
 def rfdd_kernel_launches() -> int:

@@ -3,8 +3,10 @@
 // direct solvers (PARDISO/MUMPS, Section 6); here every shifted block is dense and all
 // (subdomain, node) pairs are factored in one batch per step.
 #include "dense.cuh"
+#include "tc_gemm.cuh"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace rfdd {
 
@@ -83,6 +85,27 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(GemmBatchP<T> batch, typ
 template <typename T>
 void gemm_batched(cudaStream_t st, const std::vector<GemmItem<T>> &items, bool ta, bool tb,
                   double alpha, double beta) {
+  if constexpr (std::is_same<T, cx<float>>::value) {
+    // complex FP32 products go to the tensor cores (3xTF32 split, FP32 accumulation)
+    if (!ta && !tb && tc_enabled()) {
+      std::vector<GemmItem<T>> live;
+      for (auto &g : items)
+        if (g.m > 0 && g.n > 0 && g.k > 0) live.push_back(g);
+      if (!live.empty()) tc_gemm_complex(st, live, alpha, beta);
+      // k == 0 items still need C = beta*C
+      std::vector<GemmItem<T>> k0;
+      for (auto &g : items)
+        if (g.m > 0 && g.n > 0 && g.k <= 0 && beta != 1.0) k0.push_back(g);
+      if (!k0.empty()) gemm_simt_batched<T>(st, k0, false, false, alpha, beta);
+      return;
+    }
+  }
+  gemm_simt_batched<T>(st, items, ta, tb, alpha, beta);
+}
+
+template <typename T>
+void gemm_simt_batched(cudaStream_t st, const std::vector<GemmItem<T>> &items, bool ta, bool tb,
+                       double alpha, double beta) {
   using R = typename ST<T>::real;
   std::vector<GemmItem<T>> live;
   for (auto &g : items)
@@ -754,6 +777,7 @@ void lu_solve_batched(cudaStream_t st, const std::vector<SolveItem<T>> &items, i
 
 #define RFDD_INST_DENSE(T)                                                                          \
   template void gemm_batched<T>(cudaStream_t, const std::vector<GemmItem<T>> &, bool, bool, double, double); \
+  template void gemm_simt_batched<T>(cudaStream_t, const std::vector<GemmItem<T>> &, bool, bool, double, double); \
   template void lu_batched<T>(cudaStream_t, const std::vector<LuItem<T>> &, int, int *);          \
   template void lu_solve_batched<T>(cudaStream_t, const std::vector<SolveItem<T>> &, int);        \
   template void apply_pivots<T>(cudaStream_t, const std::vector<SolveItem<T>> &);                 \

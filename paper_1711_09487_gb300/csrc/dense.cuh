@@ -22,6 +22,10 @@ struct GemmItem {
 template <typename T>
 void gemm_batched(cudaStream_t st, const std::vector<GemmItem<T>> &items, bool ta, bool tb,
                   double alpha, double beta);
+// the CUDA-core kernel only (no tensor-core dispatch)
+template <typename T>
+void gemm_simt_batched(cudaStream_t st, const std::vector<GemmItem<T>> &items, bool ta, bool tb,
+                       double alpha, double beta);
 
 // One bordered matrix for LU: D x D (row-major, leading dimension ld), of which the first dp
 // rows/columns are eliminated with pivoting restricted to rows < dp.  After the factorisation

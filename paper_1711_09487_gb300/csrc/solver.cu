@@ -21,6 +21,7 @@
 #include "eig.cuh"
 #include "ops.cuh"
 #include "small.cuh"
+#include "tc_gemm.cuh"
 
 using namespace rfdd;
 
@@ -225,6 +226,9 @@ void sync_status(rfdd_handle *h, const char *where) {
   RFDD_CUDA(cudaStreamSynchronize(h->st));
   int s = 0;
   RFDD_CUDA(cudaMemcpy(&s, h->status.p, sizeof(int), cudaMemcpyDeviceToHost));
+  const int tce = tc_take_error();
+  if (tce & DS_WAIT_TIMEOUT)
+    throw Error(RFDD_ECUDA, std::string(where) + ": a tensor-core GEMM timed out waiting for its operands");
   if (s != 0) {
     RFDD_CUDA(cudaMemset(h->status.p, 0, sizeof(int)));
     if (s & (DS_ZERO_PIVOT | DS_NONFINITE))
@@ -1833,6 +1837,28 @@ int rfdd_sym_eig(int64_t n, const double *H, double *evals, double *evecs) {
     RFDD_REQUIRE(stt == 0, RFDD_ESINGULAR, "sym_eig: eigensolver reported a failure");
     RFDD_CUDA(cudaMemcpy(evals, lam.p, n * sizeof(double), cudaMemcpyDeviceToHost));
     RFDD_CUDA(cudaMemcpy(evecs, out.p, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToHost));
+  });
+}
+
+int rfdd_cgemm(int64_t m, int64_t n, int64_t k, const float *A, int64_t lda, const float *B, int64_t ldb, float *C,
+               int64_t ldc, double alpha, double beta, int32_t engine) {
+  if (m < 1 || n < 1 || k < 1 || !A || !B || !C || lda < k || ldb < n || ldc < n) return RFDD_EINVAL;
+  return guarded([&] {
+    cudaStream_t st = 0;
+    Buf a, b, c;
+    a.alloc((size_t)m * lda * sizeof(cx<float>));
+    b.alloc((size_t)k * ldb * sizeof(cx<float>));
+    c.alloc((size_t)m * ldc * sizeof(cx<float>));
+    RFDD_CUDA(cudaMemcpy(a.p, A, (size_t)m * lda * sizeof(cx<float>), cudaMemcpyHostToDevice));
+    RFDD_CUDA(cudaMemcpy(b.p, B, (size_t)k * ldb * sizeof(cx<float>), cudaMemcpyHostToDevice));
+    RFDD_CUDA(cudaMemcpy(c.p, C, (size_t)m * ldc * sizeof(cx<float>), cudaMemcpyHostToDevice));
+    std::vector<GemmItem<cx<float>>> it = {{a.as<cx<float>>(), b.as<cx<float>>(), c.as<cx<float>>(), (int)m, (int)n,
+                                            (int)k, (int)lda, (int)ldb, (int)ldc}};
+    if (engine == 1) tc_gemm_complex(st, it, alpha, beta);
+    else gemm_simt_batched<cx<float>>(st, it, false, false, alpha, beta);
+    RFDD_CUDA(cudaStreamSynchronize(st));
+    RFDD_REQUIRE(tc_take_error() == 0, RFDD_ECUDA, "tensor-core GEMM reported a time-out");
+    RFDD_CUDA(cudaMemcpy(C, c.p, (size_t)m * ldc * sizeof(cx<float>), cudaMemcpyDeviceToHost));
   });
 }
 

@@ -1,0 +1,393 @@
+// Complex-FP32 GEMM on the 5th-generation tensor cores (tcgen05, kind::tf32) for sm_103a.
+//
+// C = beta*C + alpha*A*B with complex A (m x k), B (k x n), C (m x n), interleaved (re, im),
+// row-major.  The complex product is computed in real ("4M", realified) form:
+//   Cr (m x 2n) = Ar (m x 2k) * Br (2k x 2n),
+// where Ar and Cr are the interleaved storage read as real matrices and each complex B[p][j]
+// becomes the 2x2 real block [[re, im], [-im, re]] of Br.  FP32 accuracy comes from the 3xTF32
+// split x = hi + lo (hi = x rounded to TF32): A*B ~ Ahi*Bhi + Ahi*Blo + Alo*Bhi, accumulated
+// in FP32 in tensor memory.
+//
+// Operands are first packed (and split) into tiles already laid out in the UMMA K-major
+// 128-byte-swizzled shared-memory format: A tiles of 128 rows x 32 floats (16 KB), B tiles of
+// 256 rows x 32 floats (32 KB).  A CTA computes one 128 x 256 tile of Cr: one thread streams the
+// tiles into shared memory with 1-D bulk copies (cp.async.bulk, completion on an mbarrier), one
+// thread issues tcgen05.mma into a 256-column TMEM accumulator, and four warps read the
+// accumulator back with tcgen05.ld for the epilogue.  Every mbarrier wait is bounded; on time-out
+// the kernel records DS_WAIT_TIMEOUT and skips its output.
+#include "dense.cuh"
+#include "tc_gemm.cuh"
+
+#include <algorithm>
+#include <cstdlib>
+
+namespace rfdd {
+
+constexpr int TC_BM = 128;
+constexpr int TC_BN = 256;
+constexpr int TC_BK = 32;
+constexpr int TC_STAGES = 2;
+constexpr int A_TILE = TC_BM * TC_BK;  // floats
+constexpr int B_TILE = TC_BN * TC_BK;  // floats
+constexpr int STAGE_BYTES = (2 * A_TILE + 2 * B_TILE) * 4;  // 96 KB
+constexpr int TC_SMEM = TC_STAGES * STAGE_BYTES + 1024;
+constexpr long long WAIT_LIMIT = 1ll << 24;
+
+// error flags of the tensor-core kernels (DS_* bits), read and cleared by tc_take_error()
+__device__ int g_tc_error = 0;
+
+struct TcItem {
+  const float *Ahi, *Alo, *Bhi, *Blo;
+  float *C;
+  long long ldc;  // real leading dimension of C
+  int m, n2, nkt, mtc, ntc;
+};
+constexpr int TC_MAXB = 64;
+struct TcBatchP {
+  TcItem it[TC_MAXB];
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (long long i = 0; i < WAIT_LIMIT; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+  const uint64_t g = (uint64_t)__cvta_generic_to_global(src);
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(g), "r"(bytes), "r"(bar)
+               : "memory");
+}
+// UMMA shared-memory descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;              // leading byte offset (unused with 128B swizzle, K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset
+  d |= (uint64_t)1 << 46;              // descriptor version
+  d |= (uint64_t)2 << 61;              // SWIZZLE_128B
+  return d;
+}
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(da), "l"(db), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+#define TC_LD32(taddr, v)                                                                                      \
+  asm volatile(                                                                                                \
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17," \
+      "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                                       \
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),       \
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), \
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),            \
+        "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),            \
+        "=r"(v[30]), "=r"(v[31])                                                                              \
+      : "r"(taddr))
+
+__global__ void __launch_bounds__(128, 1) tc_gemm_kernel(TcBatchP b, float alpha, float beta) {
+  int *err = &g_tc_error;
+  const TcItem it = b.it[blockIdx.z];
+  const int mt = blockIdx.y, nt = blockIdx.x;
+  if (mt >= it.mtc || nt >= it.ntc) return;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t full_bar[TC_STAGES], empty_bar[TC_STAGES], done_bar;
+  __shared__ uint32_t tmem_s;
+  __shared__ int abort_s;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(smem_u32(&full_bar[s]), 1);
+      mbar_init(smem_u32(&empty_bar[s]), 1);
+    }
+    mbar_init(smem_u32(&done_bar), 1);
+    abort_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_s)),
+                 "r"(TC_BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_s;
+  const int nk = it.nkt;
+  const float *Ahi = it.Ahi + (long long)mt * nk * A_TILE;
+  const float *Alo = it.Alo + (long long)mt * nk * A_TILE;
+  const float *Bhi = it.Bhi + (long long)nt * nk * B_TILE;
+  const float *Blo = it.Blo + (long long)nt * nk * B_TILE;
+  auto stage_addr = [&](int s, int which) -> uint32_t {
+    // which: 0 Ahi, 1 Alo, 2 Bhi, 3 Blo
+    const uint32_t off = (uint32_t)s * STAGE_BYTES +
+                         (which == 0 ? 0u : which == 1 ? A_TILE * 4u : which == 2 ? 2u * A_TILE * 4u
+                                                                                  : 2u * A_TILE * 4u + B_TILE * 4u);
+    return smem_u32(base + off);
+  };
+  if (threadIdx.x == 0) {
+    // producer: stream k-tiles into the two-stage ring
+    int issued = 0;
+    for (int kt = 0; kt < nk; ++kt) {
+      const int s = kt & 1;
+      if (kt >= TC_STAGES && !mbar_wait(smem_u32(&empty_bar[s]), ((kt >> 1) - 1) & 1)) {
+        atomicOr(err, DS_WAIT_TIMEOUT);
+        abort_s = 1;
+        break;
+      }
+      const uint32_t fb = smem_u32(&full_bar[s]);
+      mbar_expect_tx(fb, STAGE_BYTES);
+      bulk_g2s(stage_addr(s, 0), Ahi + (long long)kt * A_TILE, A_TILE * 4, fb);
+      bulk_g2s(stage_addr(s, 1), Alo + (long long)kt * A_TILE, A_TILE * 4, fb);
+      bulk_g2s(stage_addr(s, 2), Bhi + (long long)kt * B_TILE, B_TILE * 4, fb);
+      bulk_g2s(stage_addr(s, 3), Blo + (long long)kt * B_TILE, B_TILE * 4, fb);
+      ++issued;
+    }
+    // make sure no copy is still in flight when the CTA could leave early
+    if (abort_s) {
+      for (int kt = max(0, issued - TC_STAGES); kt < issued; ++kt)
+        mbar_wait(smem_u32(&full_bar[kt & 1]), (kt >> 1) & 1);
+    }
+  } else if (threadIdx.x == 32) {
+    // MMA issuer
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
+                           ((uint32_t)(TC_BM >> 4) << 24);
+    bool ok = true;
+    for (int kt = 0; kt < nk; ++kt) {
+      const int s = kt & 1;
+      if (!mbar_wait(smem_u32(&full_bar[s]), (kt >> 1) & 1)) {
+        atomicOr(err, DS_WAIT_TIMEOUT);
+        abort_s = 1;
+        ok = false;
+        break;
+      }
+      fence_after();
+      const uint32_t ah = stage_addr(s, 0), al = stage_addr(s, 1), bh = stage_addr(s, 2), bl = stage_addr(s, 3);
+#pragma unroll
+      for (int kk = 0; kk < TC_BK / 8; ++kk) {
+        const uint32_t o = kk * 32;  // 8 TF32 values = 32 bytes along K inside the swizzle row
+        mma_tf32(tmem, sdesc(ah + o), sdesc(bh + o), idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+        mma_tf32(tmem, sdesc(ah + o), sdesc(bl + o), idesc, 1u);
+        mma_tf32(tmem, sdesc(al + o), sdesc(bh + o), idesc, 1u);
+      }
+      mma_commit(smem_u32(&empty_bar[s]));
+    }
+    if (ok) mma_commit(smem_u32(&done_bar));
+  }
+  __syncwarp();
+  // epilogue: warp w owns accumulator lanes (tile rows) 32w .. 32w+31
+  bool ready = true;
+  if (!abort_s) ready = mbar_wait(smem_u32(&done_bar), 0);
+  if (!ready) atomicOr(err, DS_WAIT_TIMEOUT);
+  __syncwarp();
+  fence_after();
+  if (ready && !abort_s) {
+    const int row = mt * TC_BM + warp * 32 + lane;
+    float *crow = it.C + (long long)row * it.ldc;
+#pragma unroll 1
+    for (int c = 0; c < TC_BN / 32; ++c) {
+      uint32_t v[32];
+      TC_LD32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      const int col0 = nt * TC_BN + c * 32;
+      if (row < it.m) {
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          const int col = col0 + q;
+          if (col < it.n2) {
+            const float acc = __uint_as_float(v[q]);
+            crow[col] = beta != 0.f ? fmaf(alpha, acc, beta * crow[col]) : alpha * acc;
+          }
+        }
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// packing: split into TF32 hi/lo and write swizzled tiles
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void split_tf32(float x, float &hi, float &lo) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  hi = __uint_as_float(r);
+  lo = x - hi;
+}
+
+struct PackItem {
+  const float *src;   // interleaved complex source (as floats)
+  long long ld;       // complex leading dimension
+  int m, n, k;        // A: m x k ; B: k x n (complex)
+  float *hi, *lo;     // tile buffers
+  int mtc, ntc, nkt;
+};
+struct PackBatchP {
+  PackItem it[TC_MAXB];
+};
+
+// A tiles: [mt][kt] 128 rows x 32 floats; float4 chunk c of row r stored at chunk c ^ (r & 7)
+__global__ void pack_a_kernel(PackBatchP pb) {
+  const PackItem it = pb.it[blockIdx.y];
+  const long long chunks = (long long)it.mtc * TC_BM * it.nkt * 8;
+  const int k2 = 2 * it.k;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < chunks; e += (long long)gridDim.x * blockDim.x) {
+    const long long row = e / (it.nkt * 8);
+    const int q = (int)(e % (it.nkt * 8));
+    const int kt = q >> 3, c = q & 7;
+    const int mt = (int)(row / TC_BM), r = (int)(row % TC_BM);
+    float h[4], l[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int kr = kt * TC_BK + c * 4 + t;
+      float x = 0.f;
+      if (row < it.m && kr < k2) x = it.src[row * 2 * it.ld + kr];
+      split_tf32(x, h[t], l[t]);
+    }
+    const long long off = ((long long)mt * it.nkt + kt) * A_TILE + r * TC_BK + ((c ^ (r & 7)) << 2);
+    *reinterpret_cast<float4 *>(it.hi + off) = make_float4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<float4 *>(it.lo + off) = make_float4(l[0], l[1], l[2], l[3]);
+  }
+}
+
+// B tiles: Br^T rows n' = 2j + t (t: 0 real part column, 1 imaginary), K index k' = 2p + u:
+//   Br^T[2j][2p] = re B[p][j], Br^T[2j][2p+1] = -im B[p][j], Br^T[2j+1][2p] = im, Br^T[2j+1][2p+1] = re
+__global__ void pack_b_kernel(PackBatchP pb) {
+  const PackItem it = pb.it[blockIdx.y];
+  const long long chunks = (long long)it.ntc * TC_BN * it.nkt * 8;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < chunks; e += (long long)gridDim.x * blockDim.x) {
+    const long long rowp = e / (it.nkt * 8);
+    const int q = (int)(e % (it.nkt * 8));
+    const int kt = q >> 3, c = q & 7;
+    const int nt = (int)(rowp / TC_BN), r = (int)(rowp % TC_BN);
+    const long long j = rowp >> 1;
+    const int tt = (int)(rowp & 1);
+    float h[4], l[4];
+#pragma unroll
+    for (int t2 = 0; t2 < 2; ++t2) {
+      const int p = (kt * TC_BK + c * 4) / 2 + t2;
+      float re = 0.f, im = 0.f;
+      if (j < it.n && p < it.k) {
+        const float *s = it.src + ((long long)p * it.ld + j) * 2;
+        re = s[0];
+        im = s[1];
+      }
+      const float x0 = tt == 0 ? re : im;    // coefficient of Re A
+      const float x1 = tt == 0 ? -im : re;   // coefficient of Im A
+      split_tf32(x0, h[2 * t2], l[2 * t2]);
+      split_tf32(x1, h[2 * t2 + 1], l[2 * t2 + 1]);
+    }
+    const long long off = ((long long)nt * it.nkt + kt) * B_TILE + r * TC_BK + ((c ^ (r & 7)) << 2);
+    *reinterpret_cast<float4 *>(it.hi + off) = make_float4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<float4 *>(it.lo + off) = make_float4(l[0], l[1], l[2], l[3]);
+  }
+}
+
+bool tc_enabled() {
+  static int on = [] {
+    const char *v = getenv("RFDD_TC");
+    return (v && v[0] == '0') ? 0 : 1;
+  }();
+  return on != 0;
+}
+
+static int g_tc_attr_done = 0;
+
+int tc_take_error() {
+  int v = 0, z = 0;
+  RFDD_CUDA(cudaMemcpyFromSymbol(&v, g_tc_error, sizeof(int)));
+  if (v) RFDD_CUDA(cudaMemcpyToSymbol(g_tc_error, &z, sizeof(int)));
+  return v;
+}
+
+void tc_gemm_complex(cudaStream_t st, const std::vector<GemmItem<cx<float>>> &items, double alpha, double beta) {
+  if (!g_tc_attr_done) {
+    RFDD_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+    g_tc_attr_done = 1;
+  }
+  for (size_t s0 = 0; s0 < items.size(); s0 += TC_MAXB) {
+    const int cnt = (int)std::min<size_t>(TC_MAXB, items.size() - s0);
+    PackBatchP pa, pbb;
+    TcBatchP tb;
+    memset(&pa, 0, sizeof(pa));
+    memset(&pbb, 0, sizeof(pbb));
+    memset(&tb, 0, sizeof(tb));
+    size_t total = 0;
+    std::vector<size_t> offA(cnt), offB(cnt);
+    int mtmax = 1, ntmax = 1;
+    long long achunks = 1, bchunks = 1;
+    double flops = 0.0;
+    for (int i = 0; i < cnt; ++i) {
+      const auto &g = items[s0 + i];
+      const int mtc = ceil_div(g.m, TC_BM), ntc = ceil_div(2 * (int64_t)g.n, TC_BN), nkt = ceil_div(2 * (int64_t)g.k, TC_BK);
+      offA[i] = total;
+      total += (size_t)mtc * nkt * A_TILE * 2;
+      offB[i] = total;
+      total += (size_t)ntc * nkt * B_TILE * 2;
+      mtmax = std::max(mtmax, mtc);
+      ntmax = std::max(ntmax, ntc);
+      achunks = std::max(achunks, (long long)mtc * TC_BM * nkt * 8);
+      bchunks = std::max(bchunks, (long long)ntc * TC_BN * nkt * 8);
+      flops += 8.0 * g.m * (double)g.n * g.k;
+    }
+    float *ws = nullptr;
+    RFDD_CUDA(cudaMallocAsync((void **)&ws, total * sizeof(float), st));
+    for (int i = 0; i < cnt; ++i) {
+      const auto &g = items[s0 + i];
+      const int mtc = ceil_div(g.m, TC_BM), ntc = ceil_div(2 * (int64_t)g.n, TC_BN), nkt = ceil_div(2 * (int64_t)g.k, TC_BK);
+      float *Ah = ws + offA[i], *Al = Ah + (size_t)mtc * nkt * A_TILE;
+      float *Bh = ws + offB[i], *Bl = Bh + (size_t)ntc * nkt * B_TILE;
+      pa.it[i] = {reinterpret_cast<const float *>(g.A), g.lda, g.m, g.n, g.k, Ah, Al, mtc, ntc, nkt};
+      pbb.it[i] = {reinterpret_cast<const float *>(g.B), g.ldb, g.m, g.n, g.k, Bh, Bl, mtc, ntc, nkt};
+      tb.it[i] = {Ah, Al, Bh, Bl, reinterpret_cast<float *>(g.C), 2ll * g.ldc, g.m, 2 * g.n, nkt, mtc, ntc};
+    }
+    pack_a_kernel<<<dim3((unsigned)std::min<long long>(ceil_div(achunks, 256), 4096), cnt), 256, 0, st>>>(pa);
+    RFDD_CHECK_LAUNCH();
+    pack_b_kernel<<<dim3((unsigned)std::min<long long>(ceil_div(bchunks, 256), 4096), cnt), 256, 0, st>>>(pbb);
+    RFDD_CHECK_LAUNCH();
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (profiling_enabled()) {
+      e0 = profile_event();
+      e1 = profile_event();
+      cudaEventRecord(e0, st);
+    }
+    tc_gemm_kernel<<<dim3(ntmax, mtmax, cnt), 128, TC_SMEM, st>>>(tb, (float)alpha, (float)beta);
+    RFDD_CHECK_LAUNCH();
+    if (e0) {
+      cudaEventRecord(e1, st);
+      profile_push(e0, e1, flops, 1);
+    }
+    RFDD_CUDA(cudaFreeAsync(ws, st));
+  }
+}
+
+}  // namespace rfdd

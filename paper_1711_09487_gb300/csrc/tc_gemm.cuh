@@ -1,0 +1,11 @@
+// Tensor-core (tcgen05, 3xTF32) complex-FP32 GEMM; host launcher.
+#pragma once
+#include "dense.cuh"
+
+namespace rfdd {
+bool tc_enabled();  // false when the environment variable RFDD_TC is "0"
+// C = beta*C + alpha*A*B for every item (complex, row-major, no transposes)
+void tc_gemm_complex(cudaStream_t st, const std::vector<GemmItem<cx<float>>> &items, double alpha, double beta);
+// returns and clears the device-side error flags of the tensor-core kernels (DS_* bits)
+int tc_take_error();
+}  // namespace rfdd
