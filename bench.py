@@ -318,8 +318,13 @@ def run_gemm(args):
     A = (g.standard_normal((m, k)) + 1j * g.standard_normal((m, k))).astype(np.complex64)
     B = (g.standard_normal((k, n)) + 1j * g.standard_normal((k, n))).astype(np.complex64)
     C = np.zeros((m, n), dtype=np.complex64)
+    R.rfdd_cgemm(A, B, C, -1.0, 1.0, 1)  # warm-up
+    R.rfdd_profile(True)
     R.rfdd_cgemm(A, B, C, -1.0, 1.0, 1)
-    print(json.dumps({"mode": "gemm", "m": m, "n": n, "k": k}), flush=True)
+    launches, ms, flops = R.rfdd_profile_get(1)
+    R.rfdd_profile(False)
+    print(json.dumps({"mode": "gemm", "m": m, "n": n, "k": k, "kernel_ms": ms,
+                      "tflops_4m": flops / (ms / 1e3) / 1e12 if ms > 0 else None}), flush=True)
 
 
 def main():

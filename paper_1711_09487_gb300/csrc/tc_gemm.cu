@@ -14,7 +14,9 @@
 // tiles into shared memory with 1-D bulk copies (cp.async.bulk, completion on an mbarrier), one
 // thread issues tcgen05.mma into a 256-column TMEM accumulator, and four warps read the
 // accumulator back with tcgen05.ld for the epilogue.  Every mbarrier wait is bounded; on time-out
-// the kernel records DS_WAIT_TIMEOUT and skips its output.
+// the kernel records DS_WAIT_TIMEOUT and skips its output.  The kernel is persistent: one CTA per
+// SM walks a static round-robin list of all output tiles of all batch items, with two TMEM
+// accumulators so that draining tile i overlaps the MMAs of tile i+1.
 #include "dense.cuh"
 #include "tc_gemm.cuh"
 
@@ -30,7 +32,11 @@ constexpr int TC_STAGES = 2;
 constexpr int A_TILE = TC_BM * TC_BK;  // floats
 constexpr int B_TILE = TC_BN * TC_BK;  // floats
 constexpr int STAGE_BYTES = (2 * A_TILE + 2 * B_TILE) * 4;  // 96 KB
-constexpr int TC_SMEM = TC_STAGES * STAGE_BYTES + 1024;
+constexpr int EPI_WARPS = 8;  // two per TMEM lane quarter, each drains half of the columns
+constexpr int EPI_PITCH = 33;
+constexpr int EPI_BYTES = EPI_WARPS * 32 * EPI_PITCH * 4;
+constexpr int TC_THREADS = 64 + 32 * EPI_WARPS;  // producer warp, MMA warp, epilogue warps
+constexpr int TC_SMEM = TC_STAGES * STAGE_BYTES + EPI_BYTES + 1024;
 constexpr long long WAIT_LIMIT = 1ll << 24;
 
 // error flags of the tensor-core kernels (DS_* bits), read and cleared by tc_take_error()
@@ -40,11 +46,12 @@ struct TcItem {
   const float *Ahi, *Alo, *Bhi, *Blo;
   float *C;
   long long ldc;  // real leading dimension of C
-  int m, n2, nkt, mtc, ntc;
+  int m, n2, nkt, mtc, ntc, tile0;  // tile0: first global tile index of this item
 };
 constexpr int TC_MAXB = 64;
 struct TcBatchP {
   TcItem it[TC_MAXB];
+  int count, total_tiles;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -55,7 +62,11 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// bounded wait; returns false on time-out or when another role aborted
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
   for (long long i = 0; i < WAIT_LIMIT; ++i) {
     uint32_t ok;
     asm volatile(
@@ -64,6 +75,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
         : "r"(bar), "r"(parity)
         : "memory");
     if (ok) return true;
+    if ((i & 1023) == 1023 && *abort_flag) return false;
   }
   return false;
 }
@@ -107,30 +119,43 @@ __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::aft
         "=r"(v[30]), "=r"(v[31])                                                                              \
       : "r"(taddr))
 
-__global__ void __launch_bounds__(128, 1) tc_gemm_kernel(TcBatchP b, float alpha, float beta) {
+__device__ __forceinline__ int find_item(const TcBatchP &b, int tile) {
+  int lo = 0, hi = b.count;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (b.it[mid].tile0 <= tile) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Persistent, warp-specialised: warp 0 streams operand tiles, warp 1 issues the MMAs into one of
+// two TMEM accumulators (256 columns each), warps 2..5 drain the other accumulator to C.
+__global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_constant__ TcBatchP b, float alpha,
+                                                                float beta) {
   int *err = &g_tc_error;
-  const TcItem it = b.it[blockIdx.z];
-  const int mt = blockIdx.y, nt = blockIdx.x;
-  if (mt >= it.mtc || nt >= it.ntc) return;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t full_bar[TC_STAGES], empty_bar[TC_STAGES], done_bar;
+  float *epi = reinterpret_cast<float *>(base + TC_STAGES * STAGE_BYTES);
+  __shared__ __align__(8) uint64_t full_bar[TC_STAGES], empty_bar[TC_STAGES], tfull_bar[2], tempty_bar[2];
   __shared__ uint32_t tmem_s;
-  __shared__ int abort_s;
+  __shared__ volatile int abort_s;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
       mbar_init(smem_u32(&full_bar[s]), 1);
       mbar_init(smem_u32(&empty_bar[s]), 1);
     }
-    mbar_init(smem_u32(&done_bar), 1);
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(smem_u32(&tfull_bar[a]), 1);
+      mbar_init(smem_u32(&tempty_bar[a]), 32 * EPI_WARPS);
+    }
     abort_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_s)),
-                 "r"(TC_BN)
+                 "r"(2 * TC_BN)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -138,99 +163,132 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(TcBatchP b, float alpha
   __syncthreads();
   fence_after();
   const uint32_t tmem = tmem_s;
-  const int nk = it.nkt;
-  const float *Ahi = it.Ahi + (long long)mt * nk * A_TILE;
-  const float *Alo = it.Alo + (long long)mt * nk * A_TILE;
-  const float *Bhi = it.Bhi + (long long)nt * nk * B_TILE;
-  const float *Blo = it.Blo + (long long)nt * nk * B_TILE;
-  auto stage_addr = [&](int s, int which) -> uint32_t {
-    // which: 0 Ahi, 1 Alo, 2 Bhi, 3 Blo
+  auto stage_addr = [&](int s, int which) -> uint32_t {  // which: 0 Ahi, 1 Alo, 2 Bhi, 3 Blo
     const uint32_t off = (uint32_t)s * STAGE_BYTES +
                          (which == 0 ? 0u : which == 1 ? A_TILE * 4u : which == 2 ? 2u * A_TILE * 4u
                                                                                   : 2u * A_TILE * 4u + B_TILE * 4u);
     return smem_u32(base + off);
   };
-  if (threadIdx.x == 0) {
-    // producer: stream k-tiles into the two-stage ring
-    int issued = 0;
-    for (int kt = 0; kt < nk; ++kt) {
-      const int s = kt & 1;
-      if (kt >= TC_STAGES && !mbar_wait(smem_u32(&empty_bar[s]), ((kt >> 1) - 1) & 1)) {
-        atomicOr(err, DS_WAIT_TIMEOUT);
-        abort_s = 1;
-        break;
+  if (warp == 0) {
+    if (lane == 0) {  // producer
+      long long g = 0;  // global k-tile counter (stage ring position)
+      for (int tile = blockIdx.x; tile < b.total_tiles && !abort_s; tile += gridDim.x) {
+        const TcItem &it = b.it[find_item(b, tile)];
+        const int local = tile - it.tile0, mt = local / it.ntc, nt = local % it.ntc;
+        const float *Ahi = it.Ahi + (long long)mt * it.nkt * A_TILE, *Alo = it.Alo + (long long)mt * it.nkt * A_TILE;
+        const float *Bhi = it.Bhi + (long long)nt * it.nkt * B_TILE, *Blo = it.Blo + (long long)nt * it.nkt * B_TILE;
+        for (int kt = 0; kt < it.nkt; ++kt, ++g) {
+          const int s = (int)(g % TC_STAGES);
+          const long long u = g / TC_STAGES;
+          if (u >= 1 && !mbar_wait(smem_u32(&empty_bar[s]), (uint32_t)((u - 1) & 1), &abort_s)) {
+            atomicOr(err, DS_WAIT_TIMEOUT);
+            abort_s = 1;
+            break;
+          }
+          const uint32_t fb = smem_u32(&full_bar[s]);
+          mbar_expect_tx(fb, STAGE_BYTES);
+          bulk_g2s(stage_addr(s, 0), Ahi + (long long)kt * A_TILE, A_TILE * 4, fb);
+          bulk_g2s(stage_addr(s, 1), Alo + (long long)kt * A_TILE, A_TILE * 4, fb);
+          bulk_g2s(stage_addr(s, 2), Bhi + (long long)kt * B_TILE, B_TILE * 4, fb);
+          bulk_g2s(stage_addr(s, 3), Blo + (long long)kt * B_TILE, B_TILE * 4, fb);
+        }
       }
-      const uint32_t fb = smem_u32(&full_bar[s]);
-      mbar_expect_tx(fb, STAGE_BYTES);
-      bulk_g2s(stage_addr(s, 0), Ahi + (long long)kt * A_TILE, A_TILE * 4, fb);
-      bulk_g2s(stage_addr(s, 1), Alo + (long long)kt * A_TILE, A_TILE * 4, fb);
-      bulk_g2s(stage_addr(s, 2), Bhi + (long long)kt * B_TILE, B_TILE * 4, fb);
-      bulk_g2s(stage_addr(s, 3), Blo + (long long)kt * B_TILE, B_TILE * 4, fb);
-      ++issued;
+      // drain: every issued copy must land before the CTA can exit
+      for (long long q = (g > TC_STAGES ? g - TC_STAGES : 0); q < g; ++q)
+        mbar_wait(smem_u32(&full_bar[q % TC_STAGES]), (uint32_t)((q / TC_STAGES) & 1), &abort_s);
     }
-    // make sure no copy is still in flight when the CTA could leave early
-    if (abort_s) {
-      for (int kt = max(0, issued - TC_STAGES); kt < issued; ++kt)
-        mbar_wait(smem_u32(&full_bar[kt & 1]), (kt >> 1) & 1);
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
+                             ((uint32_t)(TC_BM >> 4) << 24);
+      long long g = 0;
+      int lt = 0;
+      for (int tile = blockIdx.x; tile < b.total_tiles && !abort_s; tile += gridDim.x, ++lt) {
+        const TcItem &it = b.it[find_item(b, tile)];
+        const int acc = lt & 1;
+        if (lt >= 2 && !mbar_wait(smem_u32(&tempty_bar[acc]), (uint32_t)(((lt >> 1) - 1) & 1), &abort_s)) {
+          atomicOr(err, DS_WAIT_TIMEOUT);
+          abort_s = 1;
+          break;
+        }
+        fence_after();
+        const uint32_t dacc = tmem + (uint32_t)(acc * TC_BN);
+        bool ok = true;
+        for (int kt = 0; kt < it.nkt; ++kt, ++g) {
+          const int s = (int)(g % TC_STAGES);
+          if (!mbar_wait(smem_u32(&full_bar[s]), (uint32_t)((g / TC_STAGES) & 1), &abort_s)) {
+            atomicOr(err, DS_WAIT_TIMEOUT);
+            abort_s = 1;
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t ah = stage_addr(s, 0), al = stage_addr(s, 1), bh = stage_addr(s, 2), bl = stage_addr(s, 3);
+#pragma unroll
+          for (int kk = 0; kk < TC_BK / 8; ++kk) {
+            const uint32_t o = kk * 32;  // 8 TF32 values = 32 bytes along K inside the swizzle row
+            mma_tf32(dacc, sdesc(ah + o), sdesc(bh + o), idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+            mma_tf32(dacc, sdesc(ah + o), sdesc(bl + o), idesc, 1u);
+            mma_tf32(dacc, sdesc(al + o), sdesc(bh + o), idesc, 1u);
+          }
+          mma_commit(smem_u32(&empty_bar[s]));
+        }
+        if (!ok) break;
+        mma_commit(smem_u32(&tfull_bar[acc]));
+      }
     }
-  } else if (threadIdx.x == 32) {
-    // MMA issuer
-    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
-                           ((uint32_t)(TC_BM >> 4) << 24);
-    bool ok = true;
-    for (int kt = 0; kt < nk; ++kt) {
-      const int s = kt & 1;
-      if (!mbar_wait(smem_u32(&full_bar[s]), (kt >> 1) & 1)) {
-        atomicOr(err, DS_WAIT_TIMEOUT);
+  } else {
+    // epilogue warps: warp w reads accumulator lanes 32*(w % 4) .. +31 (its TMEM sub-partition);
+    // warps 2..5 take column chunks 0..3, warps 6..9 chunks 4..7
+    const int q = warp & 3;
+    const int half = (warp - 2) >> 2;
+    float *stg = epi + (warp - 2) * 32 * EPI_PITCH;
+    int lt = 0;
+    for (int tile = blockIdx.x; tile < b.total_tiles; tile += gridDim.x, ++lt) {
+      const TcItem &it = b.it[find_item(b, tile)];
+      const int local = tile - it.tile0, mt = local / it.ntc, nt = local % it.ntc;
+      const int acc = lt & 1;
+      const bool ready = mbar_wait(smem_u32(&tfull_bar[acc]), (uint32_t)((lt >> 1) & 1), &abort_s);
+      // the whole warp takes the same branch (tcgen05.ld below is a warp-collective)
+      if (!__all_sync(0xffffffffu, ready && !abort_s)) {
+        if (lane == 0) atomicOr(err, DS_WAIT_TIMEOUT);
         abort_s = 1;
-        ok = false;
         break;
       }
       fence_after();
-      const uint32_t ah = stage_addr(s, 0), al = stage_addr(s, 1), bh = stage_addr(s, 2), bl = stage_addr(s, 3);
-#pragma unroll
-      for (int kk = 0; kk < TC_BK / 8; ++kk) {
-        const uint32_t o = kk * 32;  // 8 TF32 values = 32 bytes along K inside the swizzle row
-        mma_tf32(tmem, sdesc(ah + o), sdesc(bh + o), idesc, (kt > 0 || kk > 0) ? 1u : 0u);
-        mma_tf32(tmem, sdesc(ah + o), sdesc(bl + o), idesc, 1u);
-        mma_tf32(tmem, sdesc(al + o), sdesc(bh + o), idesc, 1u);
-      }
-      mma_commit(smem_u32(&empty_bar[s]));
-    }
-    if (ok) mma_commit(smem_u32(&done_bar));
-  }
-  __syncwarp();
-  // epilogue: warp w owns accumulator lanes (tile rows) 32w .. 32w+31
-  bool ready = true;
-  if (!abort_s) ready = mbar_wait(smem_u32(&done_bar), 0);
-  if (!ready) atomicOr(err, DS_WAIT_TIMEOUT);
-  __syncwarp();
-  fence_after();
-  if (ready && !abort_s) {
-    const int row = mt * TC_BM + warp * 32 + lane;
-    float *crow = it.C + (long long)row * it.ldc;
+      const int row0 = mt * TC_BM + q * 32;
+      const int nrows = min(32, it.m - row0);
+      float *__restrict__ Cb = it.C;
 #pragma unroll 1
-    for (int c = 0; c < TC_BN / 32; ++c) {
-      uint32_t v[32];
-      TC_LD32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      const int col0 = nt * TC_BN + c * 32;
-      if (row < it.m) {
+      for (int c = half * (TC_BN / 64); c < (half + 1) * (TC_BN / 64); ++c) {
+        uint32_t v[32];
+        TC_LD32(tmem + (uint32_t)(acc * TC_BN) + ((uint32_t)(q * 32) << 16) + (uint32_t)(c * 32), v);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int q = 0; q < 32; ++q) {
-          const int col = col0 + q;
-          if (col < it.n2) {
-            const float acc = __uint_as_float(v[q]);
-            crow[col] = beta != 0.f ? fmaf(alpha, acc, beta * crow[col]) : alpha * acc;
-          }
+        for (int j = 0; j < 32; ++j) stg[lane * EPI_PITCH + j] = __uint_as_float(v[j]);
+        __syncwarp();
+        const int col = nt * TC_BN + c * 32 + lane;
+        if (col < it.n2 && nrows > 0) {
+          // all loads of C first (independent, in flight together), then the stores
+          float cv[32];
+#pragma unroll
+          for (int r = 0; r < 32; ++r)
+            cv[r] = (beta != 0.f && r < nrows) ? Cb[(long long)(row0 + r) * it.ldc + col] : 0.f;
+#pragma unroll
+          for (int r = 0; r < 32; ++r)
+            if (r < nrows) Cb[(long long)(row0 + r) * it.ldc + col] = fmaf(alpha, stg[r * EPI_PITCH + lane], beta * cv[r]);
         }
+        __syncwarp();
       }
+      fence_before();
+      mbar_arrive(smem_u32(&tempty_bar[acc]));
     }
   }
   fence_before();
   __syncthreads();
+  fence_after();
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_BN) : "memory");
   }
 }
 
@@ -361,6 +419,7 @@ void tc_gemm_complex(cudaStream_t st, const std::vector<GemmItem<cx<float>>> &it
     }
     float *ws = nullptr;
     RFDD_CUDA(cudaMallocAsync((void **)&ws, total * sizeof(float), st));
+    int tiles = 0;
     for (int i = 0; i < cnt; ++i) {
       const auto &g = items[s0 + i];
       const int mtc = ceil_div(g.m, TC_BM), ntc = ceil_div(2 * (int64_t)g.n, TC_BN), nkt = ceil_div(2 * (int64_t)g.k, TC_BK);
@@ -368,8 +427,11 @@ void tc_gemm_complex(cudaStream_t st, const std::vector<GemmItem<cx<float>>> &it
       float *Bh = ws + offB[i], *Bl = Bh + (size_t)ntc * nkt * B_TILE;
       pa.it[i] = {reinterpret_cast<const float *>(g.A), g.lda, g.m, g.n, g.k, Ah, Al, mtc, ntc, nkt};
       pbb.it[i] = {reinterpret_cast<const float *>(g.B), g.ldb, g.m, g.n, g.k, Bh, Bl, mtc, ntc, nkt};
-      tb.it[i] = {Ah, Al, Bh, Bl, reinterpret_cast<float *>(g.C), 2ll * g.ldc, g.m, 2 * g.n, nkt, mtc, ntc};
+      tb.it[i] = {Ah, Al, Bh, Bl, reinterpret_cast<float *>(g.C), 2ll * g.ldc, g.m, 2 * g.n, nkt, mtc, ntc, tiles};
+      tiles += mtc * ntc;
     }
+    tb.count = cnt;
+    tb.total_tiles = tiles;
     pack_a_kernel<<<dim3((unsigned)std::min<long long>(ceil_div(achunks, 256), 4096), cnt), 256, 0, st>>>(pa);
     RFDD_CHECK_LAUNCH();
     pack_b_kernel<<<dim3((unsigned)std::min<long long>(ceil_div(bchunks, 256), 4096), cnt), 256, 0, st>>>(pbb);
@@ -380,7 +442,10 @@ void tc_gemm_complex(cudaStream_t st, const std::vector<GemmItem<cx<float>>> &it
       e1 = profile_event();
       cudaEventRecord(e0, st);
     }
-    tc_gemm_kernel<<<dim3(ntmax, mtmax, cnt), 128, TC_SMEM, st>>>(tb, (float)alpha, (float)beta);
+    int nsm = 0;
+    RFDD_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, 0));
+    const int grid = std::max(1, std::min(tiles, nsm));
+    tc_gemm_kernel<<<grid, TC_THREADS, TC_SMEM, st>>>(tb, (float)alpha, (float)beta);
     RFDD_CHECK_LAUNCH();
     if (e0) {
       cudaEventRecord(e1, st);
