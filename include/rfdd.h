@@ -212,6 +212,22 @@ int rfdd_sym_eig(int64_t n, const double *H, double *evals, double *evecs);
 int rfdd_cgemm(int64_t m, int64_t n, int64_t k, const float *A, int64_t lda, const float *B, int64_t ldb,
                float *C, int64_t ldc, double alpha, double beta, int32_t engine);
 
+/* Allocation-free variant of rfdd_cgemm (no counterpart in the paper).  For callers that cannot
+ * allocate device memory -- a process whose device memory is capped or owned by another
+ * allocator, a real-time loop that must not enter the allocator, code that must not pay the
+ * implicit synchronisation an allocation can cause -- this computes C = beta*C + alpha*A*B on the
+ * tensor cores with A, B, C in DEVICE memory (complex single precision, row-major, interleaved,
+ * leading dimensions in complex elements) and stages the packed operands in a fixed static
+ * device array (6 MiB per device that has loaded the library, held until process exit) instead
+ * of a workspace.  Limits: 1 <= m, n <= 1024 and 1 <= k <= 128; larger sizes return RFDD_EINVAL.
+ * The first call on a device looks up that array's device address (make that first call before
+ * any stream capture).  Work runs on `stream` (a cudaStream_t, NULL = default stream); the call
+ * returns after the stream has finished it.  Every call shares the one array: calls that overlap
+ * on the GPU (from different host threads or streams) race and must be serialised by the caller.
+ * No memory is allocated or freed by this call. */
+int rfdd_cgemm_noalloc(int64_t m, int64_t n, int64_t k, const float *A, int64_t lda, const float *B,
+                       int64_t ldb, float *C, int64_t ldc, double alpha, double beta, void *stream);
+
 /* ---- measurement hooks (no counterpart in the paper) -------------------------------------
  * rfdd_kernel_launches: number of kernels this library has launched in this process.
  * rfdd_profile(1): clear the records and time every launch of the dense contraction kernels

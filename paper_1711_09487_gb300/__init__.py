@@ -40,7 +40,7 @@ SYMBOLS = [
     "rfdd_result_pre_evals", "rfdd_result_free", "rfdd_factor", "rfdd_schur_copy", "rfdd_shifted_solve",
     "rfdd_filter_apply", "rfdd_lanczos", "rfdd_interior", "rfdd_rayleigh_ritz", "rfdd_solve_async",
     "rfdd_result_ready", "rfdd_memory_estimate", "rfdd_sym_eig", "rfdd_kernel_launches", "rfdd_profile",
-    "rfdd_profile_get", "rfdd_cgemm",
+    "rfdd_profile_get", "rfdd_cgemm", "rfdd_cgemm_noalloc",
 ]
 
 
@@ -118,6 +118,7 @@ def load(path: str | None = None):
     lib.rfdd_kernel_launches.restype = C.c_longlong
     fp = C.POINTER(C.c_float)
     lib.rfdd_cgemm.argtypes = [i64, i64, i64, fp, i64, fp, i64, fp, i64, C.c_double, C.c_double, i32]
+    lib.rfdd_cgemm_noalloc.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, i64, C.c_double, C.c_double, vp]
     lib.rfdd_profile.argtypes = [i32]
     lib.rfdd_profile_get.argtypes = [i32, C.POINTER(i64), dp, dp]
     _lib = lib
@@ -375,6 +376,13 @@ def rfdd_cgemm(A: np.ndarray, B: np.ndarray, C: np.ndarray, alpha: float = 1.0, 
 
 
 C_float_p = C.POINTER(C.c_float)
+
+
+def rfdd_cgemm_noalloc(m: int, n: int, k: int, A_ptr: int, lda: int, B_ptr: int, ldb: int, C_ptr: int, ldc: int,
+                       alpha: float = 1.0, beta: float = 0.0, stream: int = 0):
+    """Allocation-free tensor-core GEMM on device pointers (complex64, row-major); see rfdd.h."""
+    _check(load().rfdd_cgemm_noalloc(m, n, k, C.c_void_p(A_ptr), lda, C.c_void_p(B_ptr), ldb, C.c_void_p(C_ptr), ldc,
+                                     alpha, beta, C.c_void_p(stream or None)))
 
 
 def rfdd_kernel_launches() -> int:

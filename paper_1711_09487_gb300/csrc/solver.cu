@@ -1862,6 +1862,19 @@ int rfdd_cgemm(int64_t m, int64_t n, int64_t k, const float *A, int64_t lda, con
   });
 }
 
+int rfdd_cgemm_noalloc(int64_t m, int64_t n, int64_t k, const float *A, int64_t lda, const float *B, int64_t ldb,
+                       float *C, int64_t ldc, double alpha, double beta, void *stream) {
+  if (!A || !B || !C || lda < k || ldb < n || ldc < n) return RFDD_EINVAL;
+  return guarded([&] {
+    cudaStream_t st = (cudaStream_t)stream;
+    tc_gemm_complex_noalloc(st, reinterpret_cast<const cx<float> *>(A), lda, reinterpret_cast<const cx<float> *>(B),
+                            ldb, reinterpret_cast<cx<float> *>(C), ldc, (int)std::min<int64_t>(m, INT32_MAX),
+                            (int)std::min<int64_t>(n, INT32_MAX), (int)std::min<int64_t>(k, INT32_MAX), alpha, beta);
+    RFDD_CUDA(cudaStreamSynchronize(st));
+    RFDD_REQUIRE(tc_take_error() == 0, RFDD_ECUDA, "tensor-core GEMM reported a time-out");
+  });
+}
+
 long long rfdd_kernel_launches(void) { return g_kernel_launches.load(); }
 
 int rfdd_profile(int32_t enable) {

@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <mutex>
 
 namespace rfdd {
 
@@ -453,6 +454,78 @@ void tc_gemm_complex(cudaStream_t st, const std::vector<GemmItem<cx<float>>> &it
     }
     RFDD_CUDA(cudaFreeAsync(ws, st));
   }
+}
+
+
+// =========================================================================================
+// Allocation-free variant of the tensor-core complex GEMM.
+//
+// Some callers cannot call cudaMalloc: code running inside a memory-capped process or allocator
+// arena, real-time loops that must not touch the allocator, or host code that must not
+// synchronise with other streams the way allocation can.  For them the packed operand tiles
+// live in the file-scope array below instead of a per-call workspace.  The array's host-side
+// name is only a stand-in: its device address is looked up with cudaGetSymbolAddress once per
+// device (on that device's first call, with the device current) and passed to the kernels.
+// =========================================================================================
+constexpr int NOALLOC_MAX_M = 1024;   // complex rows of A and C
+constexpr int NOALLOC_MAX_N = 1024;   // complex columns of B and C
+constexpr int NOALLOC_MAX_K = 128;    // complex inner dimension
+constexpr size_t NOALLOC_A_FLOATS =
+    (size_t)((NOALLOC_MAX_M + TC_BM - 1) / TC_BM) * ((2 * NOALLOC_MAX_K + TC_BK - 1) / TC_BK) * A_TILE * 2;
+constexpr size_t NOALLOC_B_FLOATS =
+    (size_t)((2 * NOALLOC_MAX_N + TC_BN - 1) / TC_BN) * ((2 * NOALLOC_MAX_K + TC_BK - 1) / TC_BK) * B_TILE * 2;
+constexpr size_t NOALLOC_FLOATS = NOALLOC_A_FLOATS + NOALLOC_B_FLOATS;  // 6 MiB of floats in total
+
+static __device__ __align__(256) float g_noalloc_scratch[NOALLOC_FLOATS];
+
+static float *noalloc_scratch_address(int dev) {
+  static std::mutex mu;
+  static std::vector<float *> addr(256, nullptr);
+  std::lock_guard<std::mutex> lk(mu);
+  RFDD_REQUIRE(dev >= 0 && dev < (int)addr.size(), RFDD_EINVAL, "device index out of range");
+  if (!addr[dev]) {
+    void *p = nullptr;
+    RFDD_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    addr[dev] = reinterpret_cast<float *>(p);
+  }
+  return addr[dev];
+}
+
+void tc_gemm_complex_noalloc(cudaStream_t st, const cx<float> *A, int64_t lda, const cx<float> *B, int64_t ldb,
+                             cx<float> *C, int64_t ldc, int m, int n, int k, double alpha, double beta) {
+  RFDD_REQUIRE(m >= 1 && n >= 1 && k >= 1, RFDD_EINVAL, "cgemm_noalloc: sizes must be positive");
+  RFDD_REQUIRE(m <= NOALLOC_MAX_M && n <= NOALLOC_MAX_N && k <= NOALLOC_MAX_K, RFDD_EINVAL,
+               "cgemm_noalloc: m, n must be <= 1024 and k <= 128 (size of the static scratch)");
+  int dev = 0;
+  RFDD_CUDA(cudaGetDevice(&dev));
+  float *ws = noalloc_scratch_address(dev);
+  if (!g_tc_attr_done) {
+    RFDD_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+    g_tc_attr_done = 1;
+  }
+  const int mtc = ceil_div(m, TC_BM), ntc = ceil_div(2 * (int64_t)n, TC_BN), nkt = ceil_div(2 * (int64_t)k, TC_BK);
+  float *Ah = ws, *Al = Ah + (size_t)mtc * nkt * A_TILE;
+  float *Bh = ws + NOALLOC_A_FLOATS, *Bl = Bh + (size_t)ntc * nkt * B_TILE;
+  PackBatchP pa, pbb;
+  TcBatchP tb;
+  memset(&pa, 0, sizeof(pa));
+  memset(&pbb, 0, sizeof(pbb));
+  memset(&tb, 0, sizeof(tb));
+  pa.it[0] = {reinterpret_cast<const float *>(A), lda, m, n, k, Ah, Al, mtc, ntc, nkt};
+  pbb.it[0] = {reinterpret_cast<const float *>(B), ldb, m, n, k, Bh, Bl, mtc, ntc, nkt};
+  tb.it[0] = {Ah, Al, Bh, Bl, reinterpret_cast<float *>(C), 2ll * ldc, m, 2 * n, nkt, mtc, ntc, 0};
+  tb.count = 1;
+  tb.total_tiles = mtc * ntc;
+  const long long achunks = (long long)mtc * TC_BM * nkt * 8, bchunks = (long long)ntc * TC_BN * nkt * 8;
+  pack_a_kernel<<<dim3((unsigned)std::min<long long>(ceil_div(achunks, 256), 4096), 1), 256, 0, st>>>(pa);
+  RFDD_CHECK_LAUNCH();
+  pack_b_kernel<<<dim3((unsigned)std::min<long long>(ceil_div(bchunks, 256), 4096), 1), 256, 0, st>>>(pbb);
+  RFDD_CHECK_LAUNCH();
+  int nsm = 0;
+  RFDD_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  tc_gemm_kernel<<<std::max(1, std::min(tb.total_tiles, nsm)), TC_THREADS, TC_SMEM, st>>>(tb, (float)alpha,
+                                                                                      (float)beta);
+  RFDD_CHECK_LAUNCH();
 }
 
 }  // namespace rfdd
