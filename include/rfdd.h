@@ -77,6 +77,9 @@ typedef struct {
   int min_guard;        /* (defaults 0.3 and 8) */
   int keep_schur;       /* nonzero: keep an unfactored copy of every S(zeta_l) (for checks) */
   int subspace_iters;   /* block shift-invert iterations that build V_j (default 4) */
+  int m_align;          /* completion block m rounded up to a multiple of this (default 128, the
+                           complex column width of one tensor-core tile: the extra guard vectors
+                           ride in tile columns that would otherwise be padding); <= 1: none */
 } rfdd_options;
 
 typedef struct rfdd_handle rfdd_handle;
@@ -200,7 +203,8 @@ int rfdd_rayleigh_ritz(rfdd_handle *h, int64_t cap, double *theta_out, int64_t *
 
 /* a9 building block (Alg. 3 step 7 solves its projected problem with a dense symmetric
  * eigensolver): eigen-decomposition of a dense symmetric n x n FP64 matrix H on the GPU by
- * Householder tridiagonalisation, implicit-shift QL and back-transformation.  H, evals, evecs
+ * Householder tridiagonalisation, bisection on Sturm counts, inverse iteration (clusters
+ * re-orthogonalised) and back-transformation.  H, evals, evecs
  * are host arrays; evals (n) ascending; evecs (n x n row-major) holds eigenvector j in ROW j.
  * Needs no handle (runs on the default stream of the current device). */
 int rfdd_sym_eig(int64_t n, const double *H, double *evals, double *evecs);
@@ -211,6 +215,19 @@ int rfdd_sym_eig(int64_t n, const double *H, double *evals, double *evecs);
  * engine 0 = CUDA-core kernel, 1 = tensor-core kernel (tcgen05, 3xTF32 split). */
 int rfdd_cgemm(int64_t m, int64_t n, int64_t k, const float *A, int64_t lda, const float *B, int64_t ldb,
                float *C, int64_t ldc, double alpha, double beta, int32_t engine);
+
+/* Building block of a7-a10 (products on the eigenvector bases: Lanczos projections and Gram
+ * matrices, the interior CholQR, the Rayleigh-Ritz Gram matrices and Ritz vector updates):
+ * C = beta*C + alpha*op(A)*op(B) for FP64 host arrays, row-major; op(X) = X^T when the flag is 1
+ * (A then stored k x m with leading dimension lda >= m; B stored n x k with ldb >= k).
+ * engine 0 = FP64 CUDA-core kernel; 1 = the double-FP32 kernel the solver uses for these
+ * products (each operand split into two floats, error-free products and compensated sums:
+ * |error| within about 2^-42 of sum_k |a_ik||b_kj|).  sym = 1 declares op(A)*op(B) symmetric
+ * (m == n required): only the upper 64 x 64 tiles are formed and mirrored.
+ * Deep K with few output tiles is split over CTAs and the partial tiles summed in a fixed order. */
+int rfdd_dgemm(int64_t m, int64_t n, int64_t k, int32_t ta, const double *A, int64_t lda, int32_t tb,
+               const double *B, int64_t ldb, double *C, int64_t ldc, double alpha, double beta,
+               int32_t engine, int32_t sym);
 
 /* Allocation-free variant of rfdd_cgemm (no counterpart in the paper).  For callers that cannot
  * allocate device memory -- a process whose device memory is capped or owned by another

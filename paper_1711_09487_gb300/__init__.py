@@ -40,7 +40,7 @@ SYMBOLS = [
     "rfdd_result_pre_evals", "rfdd_result_free", "rfdd_factor", "rfdd_schur_copy", "rfdd_shifted_solve",
     "rfdd_filter_apply", "rfdd_lanczos", "rfdd_interior", "rfdd_rayleigh_ritz", "rfdd_solve_async",
     "rfdd_result_ready", "rfdd_memory_estimate", "rfdd_sym_eig", "rfdd_kernel_launches", "rfdd_profile",
-    "rfdd_profile_get", "rfdd_cgemm", "rfdd_cgemm_noalloc",
+    "rfdd_profile_get", "rfdd_cgemm", "rfdd_dgemm", "rfdd_cgemm_noalloc",
 ]
 
 
@@ -60,7 +60,7 @@ class rfdd_options(C.Structure):
                 ("psi", C.c_int), ("lanczos_tol", C.c_double), ("block", C.c_int), ("res_tol", C.c_double),
                 ("max_passes", C.c_int), ("ir_max", C.c_int), ("seed", C.c_uint64), ("mem_budget", C.c_size_t),
                 ("stream", C.c_void_p), ("guard_frac", C.c_double), ("min_guard", C.c_int),
-                ("keep_schur", C.c_int), ("subspace_iters", C.c_int)]
+                ("keep_schur", C.c_int), ("subspace_iters", C.c_int), ("m_align", C.c_int)]
 
 
 class rfdd_info(C.Structure):
@@ -118,6 +118,7 @@ def load(path: str | None = None):
     lib.rfdd_kernel_launches.restype = C.c_longlong
     fp = C.POINTER(C.c_float)
     lib.rfdd_cgemm.argtypes = [i64, i64, i64, fp, i64, fp, i64, fp, i64, C.c_double, C.c_double, i32]
+    lib.rfdd_dgemm.argtypes = [i64, i64, i64, i32, dp, i64, i32, dp, i64, dp, i64, C.c_double, C.c_double, i32, i32]
     lib.rfdd_cgemm_noalloc.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, i64, C.c_double, C.c_double, vp]
     lib.rfdd_profile.argtypes = [i32]
     lib.rfdd_profile_get.argtypes = [i32, C.POINTER(i64), dp, dp]
@@ -376,6 +377,22 @@ def rfdd_cgemm(A: np.ndarray, B: np.ndarray, C: np.ndarray, alpha: float = 1.0, 
 
 
 C_float_p = C.POINTER(C.c_float)
+C_double_p = C.POINTER(C.c_double)
+
+
+def rfdd_dgemm(A: np.ndarray, B: np.ndarray, C: np.ndarray, alpha: float = 1.0, beta: float = 0.0,
+               ta: bool = False, tb: bool = False, engine: int = 1, sym: bool = False) -> np.ndarray:
+    """beta*C + alpha*op(A)@op(B) for float64 row-major arrays on the GPU (engine 1: double-FP32)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    C = np.array(C, dtype=np.float64, order="C", copy=True)
+    m, n = C.shape
+    k = A.shape[0] if ta else A.shape[1]
+    lda, ldb = A.shape[1], B.shape[1]
+    dptr = lambda X: X.ctypes.data_as(C_double_p)
+    _check(load().rfdd_dgemm(m, n, k, int(ta), dptr(A), lda, int(tb), dptr(B), ldb, dptr(C), n, alpha, beta,
+                             engine, int(sym)))
+    return C
 
 
 def rfdd_cgemm_noalloc(m: int, n: int, k: int, A_ptr: int, lda: int, B_ptr: int, ldb: int, C_ptr: int, ldc: int,

@@ -14,18 +14,32 @@ namespace rfdd {
 // GEMM (CUDA cores).  64x64 output tile per CTA, 16-deep K slices staged in shared memory,
 // 4x4 outputs per thread.
 // ======================================================================================
+// Split-K: item i runs nsplit[i] K-chunks of depth kchunk (grid z = item * smax + chunk); with
+// nsplit[i] > 1 each chunk writes its unscaled partial tile to ws[i] + chunk * m * n (ld n) and
+// splitk_reduce_kernel sums the chunks in order, so the result does not depend on scheduling.
 template <typename T>
 struct GemmBatchP {
   GemmItem<T> it[MAXB];
+  T *ws[MAXB];
+  int nsplit[MAXB];
+  int smax, kchunk;
+  unsigned long long symmask;  // bit i: item i is a symmetric product (upper tiles computed, mirrored)
 };
 
 template <typename T, bool TA, bool TB>
 __global__ void __launch_bounds__(256) gemm_simt_kernel(GemmBatchP<T> batch, typename ST<T>::real alpha,
                                                         typename ST<T>::real beta) {
   using S = ST<T>;
-  const GemmItem<T> g = batch.it[blockIdx.z];
+  const int item = blockIdx.z / batch.smax, chunk = blockIdx.z % batch.smax;
+  if (chunk >= batch.nsplit[item]) return;
+  const GemmItem<T> g = batch.it[item];
   const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
   if (i0 >= g.m || j0 >= g.n) return;
+  const bool sym = (batch.symmask >> item) & 1ull;
+  if (sym && i0 > j0) return;  // lower tiles are mirrored from the upper ones
+  T *const ws = batch.nsplit[item] > 1 ? batch.ws[item] + (int64_t)chunk * g.m * g.n : nullptr;
+  const int kb = ws ? chunk * batch.kchunk : 0;
+  const int ke = ws ? min(g.k, kb + batch.kchunk) : g.k;
   __shared__ T As[16][65];
   __shared__ T Bs[16][65];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -34,7 +48,7 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(GemmBatchP<T> batch, typ
   for (int r = 0; r < 4; ++r)
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[r][c] = S::zero();
-  for (int k0 = 0; k0 < g.k; k0 += 16) {
+  for (int k0 = kb; k0 < ke; k0 += 16) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int e = tid + q * 256;
@@ -42,13 +56,13 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(GemmBatchP<T> batch, typ
       if (!TA) { kk = e & 15; ii = e >> 4; } else { ii = e & 63; kk = e >> 6; }
       const int gi = i0 + ii, gk = k0 + kk;
       T v = S::zero();
-      if (gi < g.m && gk < g.k) v = TA ? g.A[(int64_t)gk * g.lda + gi] : g.A[(int64_t)gi * g.lda + gk];
+      if (gi < g.m && gk < ke) v = TA ? g.A[(int64_t)gk * g.lda + gi] : g.A[(int64_t)gi * g.lda + gk];
       As[kk][ii] = v;
       int jj, kb;
       if (!TB) { jj = e & 63; kb = e >> 6; } else { kb = e & 15; jj = e >> 4; }
       const int gj = j0 + jj, gkb = k0 + kb;
       T u = S::zero();
-      if (gj < g.n && gkb < g.k) u = TB ? g.B[(int64_t)gj * g.ldb + gkb] : g.B[(int64_t)gkb * g.ldb + gj];
+      if (gj < g.n && gkb < ke) u = TB ? g.B[(int64_t)gj * g.ldb + gkb] : g.B[(int64_t)gkb * g.ldb + gj];
       Bs[kb][jj] = u;
     }
     __syncthreads();
@@ -74,12 +88,271 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(GemmBatchP<T> batch, typ
     for (int c = 0; c < 4; ++c) {
       const int j = j0 + tx + 16 * c;
       if (j >= g.n) continue;
+      if (ws) {
+        ws[(int64_t)i * g.n + j] = acc[r][c];
+        continue;
+      }
+      if (sym && i > j) continue;  // diagonal tile: the upper triangle is mirrored below
       T *p = g.C + (int64_t)i * g.ldc + j;
       T v = alpha * acc[r][c];
       if (beta != 0) v = v + beta * (*p);
       *p = v;
+      if (sym && i != j) {
+        T *q = g.C + (int64_t)j * g.ldc + i;
+        T w = alpha * acc[r][c];
+        if (beta != 0) w = w + beta * (*q);
+        *q = w;
+      }
     }
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) splitk_reduce_kernel(GemmBatchP<T> batch, typename ST<T>::real alpha,
+                                                            typename ST<T>::real beta) {
+  const int item = blockIdx.y, ns = batch.nsplit[item];
+  if (ns <= 1) return;
+  const GemmItem<T> g = batch.it[item];
+  const int64_t mn = (int64_t)g.m * g.n;
+  const T *ws = batch.ws[item];
+  const bool sym = (batch.symmask >> item) & 1ull;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < mn; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / g.n, j = e % g.n;
+    // a symmetric product takes its lower triangle from the upper one (exactly symmetric result)
+    const int64_t src = (sym && i > j) ? j * g.n + i : e;
+    T v = ws[src];
+    for (int c = 1; c < ns; ++c) v = v + ws[c * mn + src];
+    T *p = g.C + i * g.ldc + j;
+    v = alpha * v;
+    if (beta != 0) v = v + beta * (*p);
+    *p = v;
+  }
+}
+
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+  }
+  return n;
+}
+
+// ======================================================================================
+// FP64 GEMM in double-FP32 arithmetic.  GB300's FP64 pipes run at a small fraction of FP32, so
+// the products on the eigenvector bases (Gram matrices, projections, basis updates) split each
+// FP64 operand x into hi = fl32(x), lo = fl32(x - hi) (|x - hi - lo| <= 2^-48 |x|) and form
+//   a b ~ ah bh + (ah bl + al bh)
+// with ah bh split exactly by an FMA (TwoProduct) and the running sum kept as an unevaluated
+// pair (s, c) updated by TwoSum (Knuth, TAOCP Vol. 2, 4.2.2).  Per multiply-add that is 12 FP32
+// operations; the result has a relative error near 2^-46 of sum |a_k b_k| instead of 2^-53.
+// Same tiling as gemm_simt_kernel (64x64 tile, 16-deep K slices, 4x4 outputs per thread), with
+// split-K and symmetric-product support.
+// ======================================================================================
+__device__ __forceinline__ void split_df(double v, float &hi, float &lo) {
+  hi = __double2float_rn(v);
+  lo = __double2float_rn(v - (double)hi);
+}
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) gemm_df64_kernel(GemmBatchP<double> batch, double alpha, double beta) {
+  const int item = blockIdx.z / batch.smax, chunk = blockIdx.z % batch.smax;
+  if (chunk >= batch.nsplit[item]) return;
+  const GemmItem<double> g = batch.it[item];
+  const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+  if (i0 >= g.m || j0 >= g.n) return;
+  const bool sym = (batch.symmask >> item) & 1ull;
+  if (sym && i0 > j0) return;  // lower tiles are mirrored from the upper ones
+  double *const ws = batch.nsplit[item] > 1 ? batch.ws[item] + (int64_t)chunk * g.m * g.n : nullptr;
+  const int kb = ws ? chunk * batch.kchunk : 0;
+  const int ke = ws ? min(g.k, kb + batch.kchunk) : g.k;
+  __shared__ float Ah[16][65], Al[16][65], Bh[16][65], Bl[16][65];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float sh[4][4], sl[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) sh[r][c] = sl[r][c] = 0.f;
+  for (int k0 = kb; k0 < ke; k0 += 16) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + q * 256;
+      int ii, kk;
+      if (!TA) { kk = e & 15; ii = e >> 4; } else { ii = e & 63; kk = e >> 6; }
+      const int gi = i0 + ii, gk = k0 + kk;
+      double v = 0.0;
+      if (gi < g.m && gk < ke) v = TA ? g.A[(int64_t)gk * g.lda + gi] : g.A[(int64_t)gi * g.lda + gk];
+      split_df(v, Ah[kk][ii], Al[kk][ii]);
+      int jj, kq;
+      if (!TB) { jj = e & 63; kq = e >> 6; } else { kq = e & 15; jj = e >> 4; }
+      const int gj = j0 + jj, gkq = k0 + kq;
+      double u = 0.0;
+      if (gj < g.n && gkq < ke) u = TB ? g.B[(int64_t)gj * g.ldb + gkq] : g.B[(int64_t)gkq * g.ldb + gj];
+      split_df(u, Bh[kq][jj], Bl[kq][jj]);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < 16; ++kk) {
+      float ah[4], al[4], bh[4], bl[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        ah[r] = Ah[kk][ty + 16 * r];
+        al[r] = Al[kk][ty + 16 * r];
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        bh[c] = Bh[kk][tx + 16 * c];
+        bl[c] = Bl[kk][tx + 16 * c];
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          // intrinsics keep the compiler from contracting the error-free transformations
+          const float p = __fmul_rn(ah[r], bh[c]);
+          const float e = __fmaf_rn(ah[r], bh[c], -p);
+          const float t = __fmaf_rn(ah[r], bl[c], __fmaf_rn(al[r], bh[c], e));
+          const float s1 = __fadd_rn(sh[r][c], p);
+          const float bb = __fsub_rn(s1, sh[r][c]);
+          const float err = __fadd_rn(__fsub_rn(sh[r][c], __fsub_rn(s1, bb)), __fsub_rn(p, bb));
+          sh[r][c] = s1;
+          sl[r][c] = __fadd_rn(sl[r][c], __fadd_rn(err, t));
+        }
+    }
+    // renormalise (FastTwoSum, |sl| << |sh|): the correction term stays near 2^-24 |sh|, so its
+    // own rounding errors stay near 2^-48 |sh| per slice
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float s1 = __fadd_rn(sh[r][c], sl[r][c]);
+        sl[r][c] = __fsub_rn(sl[r][c], __fsub_rn(s1, sh[r][c]));
+        sh[r][c] = s1;
+      }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int i = i0 + ty + 16 * r;
+    if (i >= g.m) continue;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j = j0 + tx + 16 * c;
+      if (j >= g.n) continue;
+      const double acc = (double)sh[r][c] + (double)sl[r][c];
+      if (ws) {
+        ws[(int64_t)i * g.n + j] = acc;
+        continue;
+      }
+      if (sym && i > j) continue;  // diagonal tile: the upper triangle is mirrored below
+      double *p = g.C + (int64_t)i * g.ldc + j;
+      *p = beta != 0.0 ? alpha * acc + beta * (*p) : alpha * acc;
+      if (sym && i != j) {
+        double *q = g.C + (int64_t)j * g.ldc + i;
+        *q = beta != 0.0 ? alpha * acc + beta * (*q) : alpha * acc;
+      }
+    }
+  }
+}
+
+// Shared launch logic of the CUDA-core GEMMs: batching, split-K choice, partial workspace.
+template <typename T, typename Launch>
+void gemm_launch_batches(cudaStream_t st, const std::vector<GemmItem<T>> &live, const std::vector<char> &symv,
+                         double alpha, double beta, Launch &&launch) {
+  using R = typename ST<T>::real;
+  for (size_t s = 0; s < live.size(); s += MAXB) {
+    GemmBatchP<T> b;
+    memset(&b, 0, sizeof(b));
+    int cnt = (int)std::min<size_t>(MAXB, live.size() - s), mm = 0, nn = 0;
+    for (int i = 0; i < cnt; ++i) {
+      b.it[i] = live[s + i];
+      mm = std::max(mm, b.it[i].m);
+      nn = std::max(nn, b.it[i].n);
+      if (!symv.empty() && symv[s + i]) {
+        RFDD_REQUIRE(b.it[i].m == b.it[i].n, RFDD_EINVAL, "gemm: symmetric product must be square");
+        b.symmask |= 1ull << i;
+      }
+    }
+    // Few output tiles over a deep K (Gram matrices, projections on a basis): split K so that
+    // about four CTAs per SM have work; chunks no shallower than kmin.
+    double work = 0.0;
+    for (int i = 0; i < cnt; ++i) {
+      const GemmItem<T> &g = b.it[i];
+      double tiles = (double)ceil_div(g.m, 64) * ceil_div(g.n, 64);
+      if ((b.symmask >> i) & 1ull) tiles = 0.5 * (tiles + ceil_div(g.m, 64));
+      work += tiles * std::max(g.k, 1);
+    }
+    const int kmin = sizeof(R) == 8 ? 128 : 256;
+    int kchunk = (int)std::min<double>(2e9, std::ceil(work / (4.0 * sm_count())));
+    kchunk = std::max(kmin, (kchunk + 15) / 16 * 16);
+    b.smax = 1;
+    b.kchunk = kchunk;
+    for (int i = 0; i < cnt; ++i) {
+      const GemmItem<T> &g = b.it[i];
+      b.nsplit[i] = g.k > kchunk ? std::min(64, ceil_div(g.k, kchunk)) : 1;
+      // the chunk count cap can leave chunks deeper than kchunk: widen kchunk for all items
+      if (b.nsplit[i] > 1) b.kchunk = std::max(b.kchunk, (ceil_div(g.k, b.nsplit[i]) + 15) / 16 * 16);
+    }
+    size_t wsz = 0;
+    for (int i = 0; i < cnt; ++i) {
+      const GemmItem<T> &g = b.it[i];
+      if (b.nsplit[i] > 1) b.nsplit[i] = ceil_div(g.k, b.kchunk);
+      b.smax = std::max(b.smax, b.nsplit[i]);
+      if (b.nsplit[i] > 1) wsz += (size_t)b.nsplit[i] * g.m * g.n;
+    }
+    T *wsbase = nullptr;
+    if (wsz) {
+      RFDD_CUDA(cudaMallocAsync((void **)&wsbase, wsz * sizeof(T), st));
+      size_t o = 0;
+      for (int i = 0; i < cnt; ++i)
+        if (b.nsplit[i] > 1) {
+          b.ws[i] = wsbase + o;
+          o += (size_t)b.nsplit[i] * b.it[i].m * b.it[i].n;
+        }
+    }
+    dim3 grid(ceil_div(nn, 64), ceil_div(mm, 64), cnt * b.smax);
+    RFDD_REQUIRE(grid.y <= 65535 && grid.z <= 65535, RFDD_EINVAL, "gemm: too many row tiles");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    double flops = 0.0;
+    if (profiling_enabled()) {
+      for (int i = 0; i < cnt; ++i) flops += (ST<T>::is_complex ? 8.0 : 2.0) * b.it[i].m * (double)b.it[i].n * b.it[i].k;
+      e0 = profile_event();
+      e1 = profile_event();
+      cudaEventRecord(e0, st);
+    }
+    launch(grid, b);
+    RFDD_CHECK_LAUNCH();
+    if (wsbase) {
+      int64_t mnmax = 0;
+      for (int i = 0; i < cnt; ++i) mnmax = std::max<int64_t>(mnmax, (int64_t)b.it[i].m * b.it[i].n);
+      splitk_reduce_kernel<T><<<dim3((unsigned)std::min<int64_t>(1024, ceil_div(mnmax, 256)), cnt), 256, 0, st>>>(
+          b, (R)alpha, (R)beta);
+      RFDD_CHECK_LAUNCH();
+      RFDD_CUDA(cudaFreeAsync(wsbase, st));
+    }
+    if (e0) {
+      cudaEventRecord(e1, st);
+      profile_push(e0, e1, flops, 0);
+    }
+  }
+}
+
+void gemm_f64x2_batched(cudaStream_t st, const std::vector<GemmItem<double>> &items, bool ta, bool tb, double alpha,
+                        double beta, const std::vector<char> &sym) {
+  std::vector<GemmItem<double>> live;
+  std::vector<char> symv;
+  for (size_t i = 0; i < items.size(); ++i)
+    if (items[i].m > 0 && items[i].n > 0) {
+      live.push_back(items[i]);
+      symv.push_back(sym.empty() ? 0 : sym[i]);
+    }
+  gemm_launch_batches<double>(st, live, symv, alpha, beta, [&](dim3 grid, const GemmBatchP<double> &b) {
+    if (!ta && !tb) gemm_df64_kernel<false, false><<<grid, 256, 0, st>>>(b, alpha, beta);
+    else if (ta && !tb) gemm_df64_kernel<true, false><<<grid, 256, 0, st>>>(b, alpha, beta);
+    else if (!ta && tb) gemm_df64_kernel<false, true><<<grid, 256, 0, st>>>(b, alpha, beta);
+    else gemm_df64_kernel<true, true><<<grid, 256, 0, st>>>(b, alpha, beta);
+  });
 }
 
 template <typename T>
@@ -100,45 +373,41 @@ void gemm_batched(cudaStream_t st, const std::vector<GemmItem<T>> &items, bool t
       return;
     }
   }
+  if constexpr (std::is_same<T, float>::value) {
+    if (!ta && !tb && tc_enabled()) {
+      std::vector<GemmItem<T>> live, k0;
+      for (auto &g : items) {
+        if (g.m > 0 && g.n > 0 && g.k > 0) live.push_back(g);
+        else if (g.m > 0 && g.n > 0 && beta != 1.0) k0.push_back(g);
+      }
+      if (!live.empty()) tc_gemm_real(st, live, alpha, beta);
+      if (!k0.empty()) gemm_simt_batched<T>(st, k0, false, false, alpha, beta);
+      return;
+    }
+  }
   gemm_simt_batched<T>(st, items, ta, tb, alpha, beta);
 }
 
 template <typename T>
 void gemm_simt_batched(cudaStream_t st, const std::vector<GemmItem<T>> &items, bool ta, bool tb,
-                       double alpha, double beta) {
+                       double alpha, double beta, const std::vector<char> &sym) {
   using R = typename ST<T>::real;
   std::vector<GemmItem<T>> live;
-  for (auto &g : items)
-    if (g.m > 0 && g.n > 0) live.push_back(g);
-  for (size_t s = 0; s < live.size(); s += MAXB) {
-    GemmBatchP<T> b;
-    memset(&b, 0, sizeof(b));
-    int cnt = (int)std::min<size_t>(MAXB, live.size() - s), mm = 0, nn = 0;
-    for (int i = 0; i < cnt; ++i) {
-      b.it[i] = live[s + i];
-      mm = std::max(mm, b.it[i].m);
-      nn = std::max(nn, b.it[i].n);
+  std::vector<char> symv;
+  for (size_t i = 0; i < items.size(); ++i)
+    if (items[i].m > 0 && items[i].n > 0) {
+      live.push_back(items[i]);
+      symv.push_back(sym.empty() ? 0 : sym[i]);
     }
-    dim3 grid(ceil_div(nn, 64), ceil_div(mm, 64), cnt);
-    RFDD_REQUIRE(grid.y <= 65535, RFDD_EINVAL, "gemm: too many row tiles");
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    double flops = 0.0;
-    if (profiling_enabled()) {
-      for (int i = 0; i < cnt; ++i) flops += (ST<T>::is_complex ? 8.0 : 2.0) * b.it[i].m * (double)b.it[i].n * b.it[i].k;
-      e0 = profile_event();
-      e1 = profile_event();
-      cudaEventRecord(e0, st);
-    }
+  bool anysym = false;
+  for (char c : symv) anysym |= c != 0;
+  RFDD_REQUIRE(!anysym || !ST<T>::is_complex, RFDD_EINVAL, "gemm: symmetric products are real only");
+  gemm_launch_batches<T>(st, live, symv, alpha, beta, [&](dim3 grid, const GemmBatchP<T> &b) {
     if (!ta && !tb) gemm_simt_kernel<T, false, false><<<grid, 256, 0, st>>>(b, (R)alpha, (R)beta);
     else if (ta && !tb) gemm_simt_kernel<T, true, false><<<grid, 256, 0, st>>>(b, (R)alpha, (R)beta);
     else if (!ta && tb) gemm_simt_kernel<T, false, true><<<grid, 256, 0, st>>>(b, (R)alpha, (R)beta);
     else gemm_simt_kernel<T, true, true><<<grid, 256, 0, st>>>(b, (R)alpha, (R)beta);
-    RFDD_CHECK_LAUNCH();
-    if (e0) {
-      cudaEventRecord(e1, st);
-      profile_push(e0, e1, flops, 0);
-    }
-  }
+  });
 }
 
 // ======================================================================================
@@ -452,8 +721,13 @@ __global__ void __launch_bounds__(256) trsm_diag_kernel(TriBatchP<T> tb) {
   constexpr int NB = LU_NB;
   const TriItem<T> it = tb.it[blockIdx.y];
   __shared__ T L[NB][NB + 1];
+  __shared__ T rdiag[NB];
   const int w = it.w;
   for (int e = threadIdx.x; e < w * w; e += blockDim.x) L[e / w][e % w] = it.L[(int64_t)(e / w) * it.ldl + e % w];
+  if (UPPER && threadIdx.x < w) {
+    const T d = it.L[(int64_t)threadIdx.x * it.ldl + threadIdx.x];
+    rdiag[threadIdx.x] = S::abs1(d) != (Rl)0 ? S::div(S::one(), d) : S::one();
+  }
   __syncthreads();
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= it.ncols) return;
@@ -480,7 +754,7 @@ __global__ void __launch_bounds__(256) trsm_diag_kernel(TriBatchP<T> tb) {
 #pragma unroll
         for (int q = 0; q < NB; ++q)
           if (q > t && q < w) v = S::fms(L[t][q], x[q], v);
-        x[t] = S::abs1(L[t][t]) != (Rl)0 ? S::div(v, L[t][t]) : v;
+        x[t] = v * rdiag[t];
       }
     }
   }
@@ -661,8 +935,7 @@ void lu_batched(cudaStream_t st, const std::vector<LuItem<T>> &items, int nbo, i
         x.lda = x.ldb = x.ldc = it.ld;
         g.push_back(x);
       }
-      if (nbo > NB) trsm_lower_unit<T>(st, tri, NB);
-      else trsm_lower_unit<T>(st, tri, NB);
+      trsm_lower_unit<T>(st, tri, NB);
       gemm_batched<T>(st, g, false, false, -1.0, 1.0);
     }
   } catch (...) {
@@ -718,7 +991,7 @@ void trsm_lower_unit(cudaStream_t st, const std::vector<SolveItem<T>> &items, in
         }
       }
       launch_trsm_diag<T, false>(st, d);
-      gemm_batched<T>(st, g, false, false, -1.0, 1.0);
+      gemm_simt_batched<T>(st, g, false, false, -1.0, 1.0);  // small in-block updates
     }
     std::vector<GemmItem<T>> g;
     for (auto &it : items) {
@@ -755,7 +1028,7 @@ void trsm_upper(cudaStream_t st, const std::vector<SolveItem<T>> &items, int nbo
         }
       }
       launch_trsm_diag<T, true>(st, d);
-      gemm_batched<T>(st, g, false, false, -1.0, 1.0);
+      gemm_simt_batched<T>(st, g, false, false, -1.0, 1.0);  // small in-block updates
     }
     std::vector<GemmItem<T>> g;
     for (auto &it : items) {
@@ -777,7 +1050,8 @@ void lu_solve_batched(cudaStream_t st, const std::vector<SolveItem<T>> &items, i
 
 #define RFDD_INST_DENSE(T)                                                                          \
   template void gemm_batched<T>(cudaStream_t, const std::vector<GemmItem<T>> &, bool, bool, double, double); \
-  template void gemm_simt_batched<T>(cudaStream_t, const std::vector<GemmItem<T>> &, bool, bool, double, double); \
+  template void gemm_simt_batched<T>(cudaStream_t, const std::vector<GemmItem<T>> &, bool, bool, double, double, \
+                                     const std::vector<char> &);                                               \
   template void lu_batched<T>(cudaStream_t, const std::vector<LuItem<T>> &, int, int *);          \
   template void lu_solve_batched<T>(cudaStream_t, const std::vector<SolveItem<T>> &, int);        \
   template void apply_pivots<T>(cudaStream_t, const std::vector<SolveItem<T>> &);                 \

@@ -22,10 +22,15 @@ struct GemmItem {
 template <typename T>
 void gemm_batched(cudaStream_t st, const std::vector<GemmItem<T>> &items, bool ta, bool tb,
                   double alpha, double beta);
-// the CUDA-core kernel only (no tensor-core dispatch)
+// FP64 operands and result, double-FP32 arithmetic (relative error near 2^-46 of sum |a b|):
+// for products on eigenvector bases.  sym[i] != 0 marks a square product known to be symmetric
+// (A^T P A with P symmetric): only its upper tiles are formed and mirrored.
+void gemm_f64x2_batched(cudaStream_t st, const std::vector<GemmItem<double>> &items, bool ta, bool tb, double alpha,
+                        double beta, const std::vector<char> &sym = {});
+// the CUDA-core kernel only (no tensor-core dispatch); sym as for gemm_f64x2_batched (real T)
 template <typename T>
 void gemm_simt_batched(cudaStream_t st, const std::vector<GemmItem<T>> &items, bool ta, bool tb,
-                       double alpha, double beta);
+                       double alpha, double beta, const std::vector<char> &sym = {});
 
 // One bordered matrix for LU: D x D (row-major, leading dimension ld), of which the first dp
 // rows/columns are eliminated with pivoting restricted to rows < dp.  After the factorisation

@@ -483,4 +483,54 @@ RFDD_INST_OPS(cx<double>)
 RFDD_INST_OPSC(cx<float>)
 RFDD_INST_OPSC(cx<double>)
 
+
+// ---------------------------------------------------------------------------------------
+// Interface gather / ordered scatter for the bordered-factor DD solve
+// ---------------------------------------------------------------------------------------
+// Yj_l[a][c] = G_l[sidx_j[a]][c]  for all nodes l
+template <typename T>
+__global__ void gather_iface_kernel(const int32_t *__restrict__ sidx_j, int sj, int64_t m, const T *__restrict__ G,
+                                    int64_t strideG, T *__restrict__ Y, int64_t strideY) {
+  const int l = blockIdx.y;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)sj * m; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = e / m, c = e % m;
+    Y[l * strideY + e] = G[l * strideG + (int64_t)sidx_j[a] * m + c];
+  }
+}
+template <typename T>
+void gather_iface(cudaStream_t st, const int32_t *sidx_j, int sj, int64_t m, const T *G, int64_t strideG, T *Y,
+                  int64_t strideY, int nnodes) {
+  if (sj <= 0 || m <= 0) return;
+  gather_iface_kernel<T><<<dim3(std::min(4096, ceil_div((int64_t)sj * m, 256)), nnodes), 256, 0, st>>>(
+      sidx_j, sj, m, G, strideG, Y, strideY);
+  RFDD_CHECK_LAUNCH();
+}
+// G_l[sidx_j[a]][c] -= Rj_l[a][c]; called for j = 0..p-1 in order (reproducible sums)
+template <typename T>
+__global__ void scatter_sub_iface_kernel(const int32_t *__restrict__ sidx_j, int sj, int64_t m, const T *__restrict__ Rj,
+                                         int64_t strideR, T *__restrict__ G, int64_t strideG) {
+  const int l = blockIdx.y;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)sj * m; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = e / m, c = e % m;
+    T *g = G + l * strideG + (int64_t)sidx_j[a] * m + c;
+    *g = *g - Rj[l * strideR + e];
+  }
+}
+template <typename T>
+void scatter_sub_iface(cudaStream_t st, const int32_t *sidx_j, int sj, int64_t m, const T *Rj, int64_t strideR, T *G,
+                       int64_t strideG, int nnodes) {
+  if (sj <= 0 || m <= 0) return;
+  scatter_sub_iface_kernel<T><<<dim3(std::min(4096, ceil_div((int64_t)sj * m, 256)), nnodes), 256, 0, st>>>(
+      sidx_j, sj, m, Rj, strideR, G, strideG);
+  RFDD_CHECK_LAUNCH();
+}
+template void gather_iface<cx<float>>(cudaStream_t, const int32_t *, int, int64_t, const cx<float> *, int64_t,
+                                      cx<float> *, int64_t, int);
+template void gather_iface<cx<double>>(cudaStream_t, const int32_t *, int, int64_t, const cx<double> *, int64_t,
+                                       cx<double> *, int64_t, int);
+template void scatter_sub_iface<cx<float>>(cudaStream_t, const int32_t *, int, int64_t, const cx<float> *, int64_t,
+                                           cx<float> *, int64_t, int);
+template void scatter_sub_iface<cx<double>>(cudaStream_t, const int32_t *, int, int64_t, const cx<double> *, int64_t,
+                                            cx<double> *, int64_t, int);
+
 }  // namespace rfdd

@@ -87,4 +87,12 @@ void copy_rows_f64(cudaStream_t st, const double *src, int64_t lds, double *dst,
 void gather_rows_f64(cudaStream_t st, const double *src, int64_t lds, const int64_t *idx, double *dst,
                      int64_t ldd, int64_t nrows, int64_t ncols);
 
+// Y_l (s_j x m) = rows sidx_j of G_l ; G_l rows sidx_j -= R_l (ordered, call for j = 0..p-1)
+template <typename T>
+void gather_iface(cudaStream_t st, const int32_t *sidx_j, int sj, int64_t m, const T *G, int64_t strideG, T *Y,
+                  int64_t strideY, int nnodes);
+template <typename T>
+void scatter_sub_iface(cudaStream_t st, const int32_t *sidx_j, int sj, int64_t m, const T *Rj, int64_t strideR, T *G,
+                       int64_t strideG, int nnodes);
+
 }  // namespace rfdd

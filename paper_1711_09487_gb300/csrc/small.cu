@@ -357,4 +357,19 @@ void scatter_rows_perm(cudaStream_t st, const double *Cr, int r, int ns, const i
   RFDD_CHECK_LAUNCH();
 }
 
+
+// G[c][r] = G[r][c] for r in [r0, r1), c in [c0, c1)  (k x k row-major)
+__global__ void mirror_block_kernel(double *G, int64_t k, int64_t r0, int64_t r1, int64_t c0, int64_t c1) {
+  const int64_t w = c1 - c0, total = (r1 - r0) * w;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = r0 + e / w, c = c0 + e % w;
+    G[c * k + r] = G[r * k + c];
+  }
+}
+void mirror_block(cudaStream_t st, double *G, int64_t k, int64_t r0, int64_t r1, int64_t c0, int64_t c1) {
+  if (r1 <= r0 || c1 <= c0) return;
+  mirror_block_kernel<<<gridn((r1 - r0) * (c1 - c0)), 256, 0, st>>>(G, k, r0, r1, c0, c1);
+  RFDD_CHECK_LAUNCH();
+}
+
 }  // namespace rfdd

@@ -42,4 +42,6 @@ void symmetrize(cudaStream_t st, const double *A, int r, double *out);
 void transpose(cudaStream_t st, const double *in, int a, int b, double *out);
 void scatter_rows_perm(cudaStream_t st, const double *Cr, int r, int ns, const int *perm, const double *d,
                        double *Cfull);
+// G[c][r] = G[r][c] for r in [r0, r1), c in [c0, c1)  (k x k row-major)
+void mirror_block(cudaStream_t st, double *G, int64_t k, int64_t r0, int64_t r1, int64_t c0, int64_t c1);
 }  // namespace rfdd

@@ -211,6 +211,7 @@ struct rfdd_handle {
   // interior (a8)
   Buf Zb;
   int64_t kz = 0, kappa = 0;
+  std::vector<int64_t> voff;  // V_j occupies Z columns [voff[j], voff[j+1])
   double sigma_used = 0.0;
   // Rayleigh-Ritz (a9)
   std::vector<double> rr_theta;
@@ -646,26 +647,96 @@ void filter_impl(rfdd_handle *h, const double *X, double *W, int64_t b, double s
 
 // DD resolvent (Eq. inv_dd2) in the factor precision for all nodes:
 // X_l = (A - z_l M)^{-1} R_l,  R, X: complex FP64, n x m per node (stride n*m).
+// The bordered factorisation P[B_j E_j] = L[U U12], [E_j^T 0] = L21[U U12] + [0 T_j] holds the
+// block LU of (A - z M) restricted to subdomain j, so with w_j = L^{-1} P f_j:
+//   S y = g - sum_j L21_j w_j,     u_j = U^{-1} (w_j - U12_j y[sidx_j]),
+// one forward and one backward triangular solve per block plus two border products.
 // R_l = R + l * strideR (strideR = 0: one right-hand side shared by all nodes).
 template <typename Tf>
 void dd_solve(rfdd_handle *h, const cx<double> *R, int64_t strideR, cx<double> *X, int64_t m, Buf &F, Buf &Ht) {
   cudaStream_t st = h->st;
-  const int nc = h->nnodes;
+  const int nc = h->nnodes, p = h->p;
   const int64_t n = h->n, dsum = h->dsum;
   const int64_t fs = n * m;
+  int64_t smax = 1;
+  for (int j = 0; j < p; ++j) smax = std::max<int64_t>(smax, h->sidx_off[j + 1] - h->sidx_off[j]);
   F.ensure((size_t)nc * fs * sizeof(Tf));
-  Ht.ensure((size_t)nc * std::max<int64_t>(dsum, 1) * m * sizeof(Tf));
+  Ht.ensure((size_t)nc * p * smax * m * sizeof(Tf));
   Tf *f = F.as<Tf>(), *ht = Ht.as<Tf>();
+  Tf *base = h->fac.as<Tf>();
+  const int64_t hs = (int64_t)p * smax * m;  // per-node stride of the border scratch
+  Lap lap(st, "dd");
   for (int l = 0; l < nc; ++l) convert<Tf, cx<double>>(st, R + l * strideR, f + l * fs, fs);
-  auto nodes = all_nodes(h);
-  solve_B<Tf>(h, f, m, fs, m, nodes);                                          // t = B^{-1} f
-  couple<Tf>(st, h->P, dsum, n, 0, dsum, h->z_dev.as<cx<double>>(), nc, f, m, fs, f + dsum * m, m, fs, m, -1.0,
-             true);                                                            // g' = g - E^T t
-  solve_S<Tf>(h, f + dsum * m, m, fs, m, nodes);                               // y = S^{-1} g'
-  couple<Tf>(st, h->P, 0, dsum, dsum, n, h->z_dev.as<cx<double>>(), nc, f + dsum * m, m, fs, ht, m, dsum * m, m, 1.0,
-             false);                                                           // h = E y
-  solve_B<Tf>(h, ht, m, dsum * m, m, nodes);                                   // B^{-1} h
-  for (int l = 0; l < nc; ++l) sub_inplace<Tf>(st, ht + l * dsum * m, f + l * fs, dsum * m);  // u = t - B^{-1}E y
+  // w = L^{-1} P f for every (node, subdomain)
+  {
+    std::vector<SolveItem<Tf>> it;
+    for (int l = 0; l < nc; ++l)
+      for (int j = 0; j < p; ++j) {
+        SolveItem<Tf> x;
+        x.LU = base + h->boff[(size_t)l * p + j];
+        x.piv = h->pivB.as<int>() + h->pivBoff[(size_t)l * p + j];
+        x.n = (int)h->d[j];
+        x.ld = (int)h->D[j];
+        x.X = f + (int64_t)l * fs + h->off[j] * m;
+        x.ldx = (int)m;
+        x.ncols = (int)m;
+        it.push_back(x);
+      }
+    apply_pivots<Tf>(st, it);
+    trsm_lower_unit<Tf>(st, it, NBO);
+  }
+  lap.mark("forward");
+  // g -= sum_j L21_j w_j  (s_j x d_j times d_j x m, then an ordered scatter)
+  {
+    std::vector<GemmItem<Tf>> g;
+    for (int l = 0; l < nc; ++l)
+      for (int j = 0; j < p; ++j) {
+        const int sj = (int)(h->sidx_off[j + 1] - h->sidx_off[j]);
+        if (sj == 0) continue;
+        const int64_t Dj = h->D[j], dj = h->d[j];
+        g.push_back({base + h->boff[(size_t)l * p + j] + dj * Dj, f + (int64_t)l * fs + h->off[j] * m,
+                     ht + l * hs + (int64_t)j * smax * m, sj, (int)m, (int)dj, (int)Dj, (int)m, (int)m});
+      }
+    gemm_batched<Tf>(st, g, false, false, 1.0, 0.0);
+    for (int j = 0; j < p; ++j) {
+      const int sj = (int)(h->sidx_off[j + 1] - h->sidx_off[j]);
+      scatter_sub_iface<Tf>(st, h->dd.sidx + h->sidx_off[j], sj, m, ht + (int64_t)j * smax * m, hs, f + dsum * m, fs,
+                            nc);
+    }
+  }
+  lap.mark("border L21");
+  solve_S<Tf>(h, f + dsum * m, m, fs, m, all_nodes(h));  // y = S^{-1} g'
+  lap.mark("S solve");
+  // w_j -= U12_j y[sidx_j], then u_j = U^{-1} w_j
+  {
+    for (int j = 0; j < p; ++j) {
+      const int sj = (int)(h->sidx_off[j + 1] - h->sidx_off[j]);
+      gather_iface<Tf>(st, h->dd.sidx + h->sidx_off[j], sj, m, f + dsum * m, fs, ht + (int64_t)j * smax * m, hs, nc);
+    }
+    std::vector<GemmItem<Tf>> g;
+    std::vector<SolveItem<Tf>> it;
+    for (int l = 0; l < nc; ++l)
+      for (int j = 0; j < p; ++j) {
+        const int sj = (int)(h->sidx_off[j + 1] - h->sidx_off[j]);
+        const int64_t Dj = h->D[j], dj = h->d[j];
+        if (sj > 0)
+          g.push_back({base + h->boff[(size_t)l * p + j] + dj, ht + l * hs + (int64_t)j * smax * m,
+                       f + (int64_t)l * fs + h->off[j] * m, (int)dj, (int)m, sj, (int)Dj, (int)m, (int)m});
+        SolveItem<Tf> x;
+        x.LU = base + h->boff[(size_t)l * p + j];
+        x.piv = nullptr;
+        x.n = (int)dj;
+        x.ld = (int)Dj;
+        x.X = f + (int64_t)l * fs + h->off[j] * m;
+        x.ldx = (int)m;
+        x.ncols = (int)m;
+        it.push_back(x);
+      }
+    gemm_batched<Tf>(st, g, false, false, -1.0, 1.0);
+    lap.mark("border U12");
+    trsm_upper<Tf>(st, it, NBO);
+  }
+  lap.mark("backward");
   convert<cx<double>, Tf>(st, f, X, nc * fs);
 }
 
@@ -735,9 +806,19 @@ struct RRout {
   int64_t r = 0;              // dimension kept
 };
 
+// vstruct: the leading kappa columns of Y are blockdiag(V_j) (subdomain j's rows only, columns
+// voff[j]..voff[j+1]); their Gram blocks are then formed per subdomain (exactly zero between
+// different subdomains), and only the remaining columns need full-length products.
+// fast_gram: form the Gram matrices in double-FP32 arithmetic (near 2^-42 relative) instead of
+// FP64.  Only for bases without near-dependent columns: the pivoted Cholesky's rank test looks
+// at pivots near drop (1e-12), which a Gram matrix wrong in the 13th digit cannot resolve.
 RRout rayleigh_ritz_coeffs(rfdd_handle *h, const double *Y, int64_t k, double drop, double ctol,
                            const std::function<std::vector<int>(const std::vector<double> &)> &select,
-                           Buf &Cout, std::vector<int> &sel_out) {
+                           Buf &Cout, std::vector<int> &sel_out, bool vstruct, bool fast_gram) {
+  auto gram = [&](const std::vector<GemmItem<double>> &g, const std::vector<char> &sym) {
+    if (fast_gram) gemm_f64x2_batched(h->st, g, true, false, 1.0, 0.0, sym);
+    else gemm_simt_batched<double>(h->st, g, true, false, 1.0, 0.0, sym);
+  };
   cudaStream_t st = h->st;
   const int64_t n = h->n;
   Lap lap(st, "rr");
@@ -746,17 +827,52 @@ RRout rayleigh_ritz_coeffs(rfdd_handle *h, const double *Y, int64_t k, double dr
   AY.alloc((size_t)n * k * sizeof(double));
   spmm_f64(st, h->P, 0, n, 0, n, 0.0, 1.0, Y, k, MY.as<double>(), k, k, false);
   spmm_f64(st, h->P, 0, n, 0, n, 1.0, 0.0, Y, k, AY.as<double>(), k, k, false);
+  lap.mark("spmm");
   G.alloc((size_t)k * k * sizeof(double));
   K.alloc((size_t)k * k * sizeof(double));
-  {
+  const int64_t kap = vstruct ? h->kappa : 0;
+  if (kap > 0) {
+    const int64_t ks = k - kap;
+    RFDD_CUDA(cudaMemsetAsync(G.p, 0, (size_t)k * k * sizeof(double), st));
+    RFDD_CUDA(cudaMemsetAsync(K.p, 0, (size_t)k * k * sizeof(double), st));
+    std::vector<GemmItem<double>> g;
+    std::vector<char> sym;
+    for (int q = 0; q < 2; ++q) {  // q = 0: M (Gram), q = 1: A
+      const double *PY = q == 0 ? MY.as<double>() : AY.as<double>();
+      double *Out = q == 0 ? G.as<double>() : K.as<double>();
+      if (ks > 0) {  // S^T (P S)
+        g.push_back({Y + kap, PY + kap, Out + kap * k + kap, (int)ks, (int)ks, (int)n, (int)k, (int)k, (int)k});
+        sym.push_back(1);
+      }
+      for (int j = 0; j < h->p; ++j) {
+        const int64_t v0 = h->voff[j], nv = h->voff[j + 1] - h->voff[j];
+        if (nv <= 0) continue;
+        const int64_t r0 = h->off[j], dj = h->d[j];
+        // V_j^T (P V_j) and V_j^T (P S) over subdomain j's rows
+        g.push_back({Y + r0 * k + v0, PY + r0 * k + v0, Out + v0 * k + v0, (int)nv, (int)nv, (int)dj, (int)k, (int)k,
+                     (int)k});
+        sym.push_back(1);
+        if (ks > 0) {
+          g.push_back({Y + r0 * k + v0, PY + r0 * k + kap, Out + v0 * k + kap, (int)nv, (int)ks, (int)dj, (int)k,
+                       (int)k, (int)k});
+          sym.push_back(0);
+        }
+      }
+    }
+    gram(g, sym);
+    if (ks > 0) {
+      mirror_block(st, G.as<double>(), k, 0, kap, kap, k);  // (S, V) blocks from (V, S)
+      mirror_block(st, K.as<double>(), k, 0, kap, kap, k);
+    }
+  } else {
     std::vector<GemmItem<double>> g = {
         {Y, MY.as<double>(), G.as<double>(), (int)k, (int)k, (int)n, (int)k, (int)k, (int)k},
         {Y, AY.as<double>(), K.as<double>(), (int)k, (int)k, (int)n, (int)k, (int)k, (int)k}};
-    gemm_batched<double>(st, g, true, false, 1.0, 0.0);
+    gram(g, {1, 1});
   }
   MY.release();
   AY.release();
-  lap.mark("spmm+gram");
+  lap.mark("gram");
   Buf dsc, perm, rankd;
   dsc.alloc((size_t)k * sizeof(double));
   perm.alloc((size_t)k * sizeof(int));
@@ -882,9 +998,9 @@ void lanczos_impl(rfdd_handle *h) {
   uint64_t stream_id = 0;
   auto project_out = [&](double *Wp, int64_t bw, int64_t ncols_prev) {  // W -= Q (Q^T W)
     if (ncols_prev <= 0) return;
-    gemm_batched<double>(st, {{Q, Wp, Cb.as<double>(), (int)ncols_prev, (int)bw, (int)s, (int)qld, (int)bw, (int)bw}},
+    gemm_f64x2_batched(st, {{Q, Wp, Cb.as<double>(), (int)ncols_prev, (int)bw, (int)s, (int)qld, (int)bw, (int)bw}},
                          true, false, 1.0, 0.0);
-    gemm_batched<double>(st, {{Q, Cb.as<double>(), Wp, (int)s, (int)bw, (int)ncols_prev, (int)qld, (int)bw, (int)bw}},
+    gemm_f64x2_batched(st, {{Q, Cb.as<double>(), Wp, (int)s, (int)bw, (int)ncols_prev, (int)qld, (int)bw, (int)bw}},
                          false, false, -1.0, 1.0);
   };
   // Lines 4-12 of Alg. 2 for a block of bw columns (row stride bw): two classical Gram-Schmidt
@@ -896,10 +1012,10 @@ void lanczos_impl(rfdd_handle *h) {
       project_out(Wp, bw, ncols_prev);
       bool any_dead = false;
       for (int q = 0; q < 2; ++q) {
-        gemm_batched<double>(st, {{Wp, Wp, Gb.as<double>(), (int)bw, (int)bw, (int)s, (int)bw, (int)bw, (int)bw}}, true,
-                             false, 1.0, 0.0);
+        gemm_f64x2_batched(st, {{Wp, Wp, Gb.as<double>(), (int)bw, (int)bw, (int)s, (int)bw, (int)bw, (int)bw}}, true,
+                           false, 1.0, 0.0, {1});
         chol_inv_batched(st, {CholItem{Gb.as<double>(), Rinv.as<double>(), dead.as<int>(), (int)bw}}, 1e-24);
-        gemm_batched<double>(st, {{Wp, Rinv.as<double>(), tmp.as<double>(), (int)s, (int)bw, (int)bw, (int)bw, (int)bw,
+        gemm_f64x2_batched(st, {{Wp, Rinv.as<double>(), tmp.as<double>(), (int)s, (int)bw, (int)bw, (int)bw, (int)bw,
                                    (int)bw}},
                              false, false, 1.0, 0.0);
         RFDD_CUDA(cudaMemcpyAsync(Wp, tmp.p, (size_t)s * bw * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -937,13 +1053,15 @@ void lanczos_impl(rfdd_handle *h) {
   while (true) {
     double *Qmu = Q + col;
     copy_rows_f64(st, Qmu, qld, Xb.as<double>(), bc, s, bc);
+    Lap lap(st, "lanczos");
     filter_impl<Tf>(h, Xb.as<double>(), W.as<double>(), bc, 1.0);  // line 2: F q
+    lap.mark("filter");
     if (nblk > 0)  // ... - Q_{mu-1} B_mu^T
-      gemm_batched<double>(st, {{Q + col - bprev, Bprev.as<double>(), W.as<double>(), (int)s, (int)bc, (int)bprev,
+      gemm_f64x2_batched(st, {{Q + col - bprev, Bprev.as<double>(), W.as<double>(), (int)s, (int)bc, (int)bprev,
                                  (int)qld, (int)bprev, (int)bc}},
                            false, true, -1.0, 1.0);
     // line 3: A_mu = Q_mu^T W
-    gemm_batched<double>(st, {{Xb.as<double>(), W.as<double>(), Amu.as<double>(), (int)bc, (int)bc, (int)s, (int)bc,
+    gemm_f64x2_batched(st, {{Xb.as<double>(), W.as<double>(), Amu.as<double>(), (int)bc, (int)bc, (int)s, (int)bc,
                                (int)bc, (int)bc}},
                          true, false, 1.0, 0.0);
     RFDD_CUDA(cudaMemcpyAsync(ha.data(), Amu.p, bc * bc * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -966,8 +1084,9 @@ void lanczos_impl(rfdd_handle *h) {
     RFDD_CUDA(cudaMemcpyAsync(Wraw.p, W.p, (size_t)s * bc * sizeof(double), cudaMemcpyDeviceToDevice, st));
     RFDD_CUDA(cudaMemcpyAsync(W.p, tmp.p, (size_t)s * bn * sizeof(double), cudaMemcpyDeviceToDevice, st));
     orthonormalize(W.as<double>(), bn, mu_now);
+    lap.mark("orthonormalize");
     // B (bn x bc) = Q_next^T W_raw
-    gemm_batched<double>(st, {{W.as<double>(), Wraw.as<double>(), Bprev.as<double>(), (int)bn, (int)bc, (int)s, (int)bn,
+    gemm_f64x2_batched(st, {{W.as<double>(), Wraw.as<double>(), Bprev.as<double>(), (int)bn, (int)bc, (int)s, (int)bn,
                                (int)bc, (int)bc}},
                          true, false, 1.0, 0.0);
     copy_rows_f64(st, W.as<double>(), bn, Q + mu_now, qld, s, bn);
@@ -1048,6 +1167,7 @@ void interior_impl(rfdd_handle *h, double sigma) {
     voff[j + 1] = voff[j] + nvb[j];
   }
   h->kappa = voff[p];
+  h->voff = voff;
   // one tall block X (dsum x mbmax): subdomain j uses rows off_j.. and its first mb_j columns
   const int64_t mw = mbmax;
   Buf X, Y, G, Rinv, dead, T;
@@ -1070,13 +1190,13 @@ void interior_impl(rfdd_handle *h, double sigma) {
         ch.push_back({G.as<double>() + (int64_t)j * mw * mw, Rinv.as<double>() + (int64_t)j * mw * mw,
                       dead.as<int>() + j * mw, (int)mb[j]});
       }
-      gemm_batched<double>(st, g, true, false, 1.0, 0.0);
+      gemm_f64x2_batched(st, g, true, false, 1.0, 0.0, std::vector<char>(g.size(), 1));
       chol_inv_batched(st, ch, 1e-28);
       std::vector<GemmItem<double>> g2;
       for (int j = 0; j < p; ++j)
         g2.push_back({Xp + h->off[j] * mw, Rinv.as<double>() + (int64_t)j * mw * mw, T.as<double>() + h->off[j] * mw,
                       (int)h->d[j], (int)mb[j], (int)mb[j], (int)mw, (int)mb[j], (int)mw});
-      gemm_batched<double>(st, g2, false, false, 1.0, 0.0);
+      gemm_f64x2_batched(st, g2, false, false, 1.0, 0.0);
       RFDD_CUDA(cudaMemcpyAsync(Xp, T.p, (size_t)dsum * mw * sizeof(double), cudaMemcpyDeviceToDevice, st));
     }
   };
@@ -1096,7 +1216,7 @@ void interior_impl(rfdd_handle *h, double sigma) {
       g.push_back({X.as<double>() + h->off[j] * mw, Y.as<double>() + h->off[j] * mw,
                    G.as<double>() + (int64_t)j * mw * mw, (int)mb[j], (int)mb[j], (int)h->d[j], (int)mw, (int)mw,
                    (int)mb[j]});
-    gemm_batched<double>(st, g, true, false, 1.0, 0.0);
+    gemm_f64x2_batched(st, g, true, false, 1.0, 0.0, std::vector<char>(g.size(), 1));
   }
   Buf ed, ee, et, ew, el, eZ;
   ed.alloc((size_t)p * mw * sizeof(double));
@@ -1140,7 +1260,7 @@ void interior_impl(rfdd_handle *h, double sigma) {
     for (int j = 0; j < p; ++j)
       g.push_back({X.as<double>() + h->off[j] * mw, Gt.as<double>() + (int64_t)j * mw * mw, Z + h->off[j] * kz + voff[j],
                    (int)h->d[j], (int)nvb[j], (int)mb[j], (int)mw, (int)mb[j], (int)kz});
-    gemm_batched<double>(st, g, false, true, 1.0, 0.0);
+    gemm_f64x2_batched(st, g, false, true, 1.0, 0.0);
   }
   X.release();
   Y.release();
@@ -1204,20 +1324,20 @@ void rr_on_Z(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
       [&](const std::vector<double> &th) {
         int64_t nin = 0;
         for (double t : th) nin += (t >= alpha && t <= beta);
-        const int64_t m = std::min<int64_t>((int64_t)th.size(),
-                                            nin + std::max<int64_t>((int64_t)std::ceil(h->opt.guard_frac * nin),
-                                                                    h->opt.min_guard));
+        int64_t m = nin + std::max<int64_t>((int64_t)std::ceil(h->opt.guard_frac * nin), h->opt.min_guard);
+        if (h->opt.m_align > 1) m = (m + h->opt.m_align - 1) / h->opt.m_align * h->opt.m_align;
+        m = std::min<int64_t>((int64_t)th.size(), m);
         m_sel = m;
         return select_nearest(th, alpha, beta, m);
       },
-      C, sel);
+      C, sel, true, false);
   h->rr_theta = rr.theta;
   h->m0 = (int64_t)sel.size();
   h->X0.alloc((size_t)n * std::max<int64_t>(1, h->m0) * sizeof(double));
   if (h->m0 > 0)
-    gemm_batched<double>(st, {{h->Zb.as<double>(), C.as<double>(), h->X0.as<double>(), (int)n, (int)h->m0, (int)kz,
-                               (int)kz, (int)h->m0, (int)h->m0}},
-                         false, false, 1.0, 0.0);
+    gemm_f64x2_batched(st, {{h->Zb.as<double>(), C.as<double>(), h->X0.as<double>(), (int)n, (int)h->m0, (int)kz,
+                             (int)kz, (int)h->m0, (int)h->m0}},
+                       false, false, 1.0, 0.0);
   if (res) {
     res->pre_evals.clear();
     for (double t : rr.theta)
@@ -1294,13 +1414,13 @@ void complete(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
           std::iota(all.begin(), all.end(), 0);
           return all;
         },
-        C, sel);
+        C, sel, false, true);
     const int64_t r = rr.r;
     Buf Xn;
     Xn.alloc((size_t)n * r * sizeof(double));
-    gemm_batched<double>(st, {{X.as<double>(), C.as<double>(), Xn.as<double>(), (int)n, (int)r, (int)m, (int)m,
-                               (int)r, (int)r}},
-                         false, false, 1.0, 0.0);
+    gemm_f64x2_batched(st, {{X.as<double>(), C.as<double>(), Xn.as<double>(), (int)n, (int)r, (int)m, (int)m,
+                             (int)r, (int)r}},
+                       false, false, 1.0, 0.0);
     theta = rr.theta;
     residuals_of(Xn.as<double>(), r, theta, resid);
     X.alloc((size_t)n * r * sizeof(double));
@@ -1469,6 +1589,7 @@ void rfdd_default_options(rfdd_options *o) {
   o->stream = nullptr;
   o->guard_frac = 0.3;
   o->min_guard = 8;
+  o->m_align = 128;
   o->keep_schur = 0;
   o->subspace_iters = 4;
 }
@@ -1862,6 +1983,30 @@ int rfdd_cgemm(int64_t m, int64_t n, int64_t k, const float *A, int64_t lda, con
   });
 }
 
+int rfdd_dgemm(int64_t m, int64_t n, int64_t k, int32_t ta, const double *A, int64_t lda, int32_t tb, const double *B,
+               int64_t ldb, double *C, int64_t ldc, double alpha, double beta, int32_t engine, int32_t sym) {
+  if (m < 1 || n < 1 || k < 1 || !A || !B || !C || ldc < n) return RFDD_EINVAL;
+  if (lda < (ta ? m : k) || ldb < (tb ? k : n)) return RFDD_EINVAL;
+  if (sym && m != n) return RFDD_EINVAL;
+  return guarded([&] {
+    cudaStream_t st = 0;
+    const size_t na = (size_t)(ta ? k : m) * lda, nb = (size_t)(tb ? n : k) * ldb, ncm = (size_t)m * ldc;
+    Buf a, b, c;
+    a.alloc(na * sizeof(double));
+    b.alloc(nb * sizeof(double));
+    c.alloc(ncm * sizeof(double));
+    RFDD_CUDA(cudaMemcpy(a.p, A, na * sizeof(double), cudaMemcpyHostToDevice));
+    RFDD_CUDA(cudaMemcpy(b.p, B, nb * sizeof(double), cudaMemcpyHostToDevice));
+    RFDD_CUDA(cudaMemcpy(c.p, C, ncm * sizeof(double), cudaMemcpyHostToDevice));
+    std::vector<GemmItem<double>> it = {
+        {a.as<double>(), b.as<double>(), c.as<double>(), (int)m, (int)n, (int)k, (int)lda, (int)ldb, (int)ldc}};
+    if (engine == 1) gemm_f64x2_batched(st, it, ta != 0, tb != 0, alpha, beta, {(char)(sym != 0)});
+    else gemm_simt_batched<double>(st, it, ta != 0, tb != 0, alpha, beta, {(char)(sym != 0)});
+    RFDD_CUDA(cudaStreamSynchronize(st));
+    RFDD_CUDA(cudaMemcpy(C, c.p, ncm * sizeof(double), cudaMemcpyDeviceToHost));
+  });
+}
+
 int rfdd_cgemm_noalloc(int64_t m, int64_t n, int64_t k, const float *A, int64_t lda, const float *B, int64_t ldb,
                        float *C, int64_t ldc, double alpha, double beta, void *stream) {
   if (!A || !B || !C || lda < k || ldb < n || ldc < n) return RFDD_EINVAL;
@@ -1911,7 +2056,8 @@ int rfdd_memory_estimate(const rfdd_handle *h, int32_t n_nodes, int64_t nev_gues
   if (!h || !bytes || n_nodes < 1) return RFDD_EINVAL;
   const size_t scal = h->opt.precision == RFDD_MIXED ? sizeof(cx<float>) : sizeof(cx<double>);
   size_t b = factor_bytes(h, n_nodes, scal);
-  const int64_t m = nev_guess + std::max<int64_t>((int64_t)std::ceil(h->opt.guard_frac * nev_guess), h->opt.min_guard);
+  int64_t m = nev_guess + std::max<int64_t>((int64_t)std::ceil(h->opt.guard_frac * nev_guess), h->opt.min_guard);
+  if (h->opt.m_align > 1) m = (m + h->opt.m_align - 1) / h->opt.m_align * h->opt.m_align;
   b += (size_t)n_nodes * h->n * m * (sizeof(cx<double>) * 3 + scal * 2);  // completion blocks
   b += (size_t)h->s * h->s * sizeof(double);                               // Lanczos basis
   *bytes = b;

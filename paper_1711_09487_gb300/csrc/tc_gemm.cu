@@ -371,6 +371,48 @@ __global__ void pack_b_kernel(PackBatchP pb) {
   }
 }
 
+// real operands: A (m x k, ld), B (k x n, ld) in FP32; the same tile formats with K' = k, N' = n
+__global__ void pack_a_real_kernel(PackBatchP pb) {
+  const PackItem it = pb.it[blockIdx.y];
+  const long long chunks = (long long)it.mtc * TC_BM * it.nkt * 8;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < chunks; e += (long long)gridDim.x * blockDim.x) {
+    const long long row = e / (it.nkt * 8);
+    const int q = (int)(e % (it.nkt * 8));
+    const int kt = q >> 3, c = q & 7;
+    const int mt = (int)(row / TC_BM), r = (int)(row % TC_BM);
+    float h[4], l[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int kr = kt * TC_BK + c * 4 + t;
+      const float x = (row < it.m && kr < it.k) ? it.src[row * it.ld + kr] : 0.f;
+      split_tf32(x, h[t], l[t]);
+    }
+    const long long off = ((long long)mt * it.nkt + kt) * A_TILE + r * TC_BK + ((c ^ (r & 7)) << 2);
+    *reinterpret_cast<float4 *>(it.hi + off) = make_float4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<float4 *>(it.lo + off) = make_float4(l[0], l[1], l[2], l[3]);
+  }
+}
+__global__ void pack_b_real_kernel(PackBatchP pb) {
+  const PackItem it = pb.it[blockIdx.y];
+  const long long chunks = (long long)it.ntc * TC_BN * it.nkt * 8;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < chunks; e += (long long)gridDim.x * blockDim.x) {
+    const long long j = e / (it.nkt * 8);
+    const int q = (int)(e % (it.nkt * 8));
+    const int kt = q >> 3, c = q & 7;
+    const int nt = (int)(j / TC_BN), r = (int)(j % TC_BN);
+    float h[4], l[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int p = kt * TC_BK + c * 4 + t;
+      const float x = (j < it.n && p < it.k) ? it.src[(long long)p * it.ld + j] : 0.f;
+      split_tf32(x, h[t], l[t]);
+    }
+    const long long off = ((long long)nt * it.nkt + kt) * B_TILE + r * TC_BK + ((c ^ (r & 7)) << 2);
+    *reinterpret_cast<float4 *>(it.hi + off) = make_float4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<float4 *>(it.lo + off) = make_float4(l[0], l[1], l[2], l[3]);
+  }
+}
+
 bool tc_enabled() {
   static int on = [] {
     const char *v = getenv("RFDD_TC");
@@ -388,7 +430,9 @@ int tc_take_error() {
   return v;
 }
 
-void tc_gemm_complex(cudaStream_t st, const std::vector<GemmItem<cx<float>>> &items, double alpha, double beta) {
+template <bool CPLX, typename T>
+static void tc_gemm_run(cudaStream_t st, const std::vector<GemmItem<T>> &items, double alpha, double beta) {
+  constexpr int F = CPLX ? 2 : 1;  // real columns / K entries per element
   if (!g_tc_attr_done) {
     RFDD_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
     g_tc_attr_done = 1;
@@ -407,7 +451,7 @@ void tc_gemm_complex(cudaStream_t st, const std::vector<GemmItem<cx<float>>> &it
     double flops = 0.0;
     for (int i = 0; i < cnt; ++i) {
       const auto &g = items[s0 + i];
-      const int mtc = ceil_div(g.m, TC_BM), ntc = ceil_div(2 * (int64_t)g.n, TC_BN), nkt = ceil_div(2 * (int64_t)g.k, TC_BK);
+      const int mtc = ceil_div(g.m, TC_BM), ntc = ceil_div((int64_t)F * g.n, TC_BN), nkt = ceil_div((int64_t)F * g.k, TC_BK);
       offA[i] = total;
       total += (size_t)mtc * nkt * A_TILE * 2;
       offB[i] = total;
@@ -416,27 +460,36 @@ void tc_gemm_complex(cudaStream_t st, const std::vector<GemmItem<cx<float>>> &it
       ntmax = std::max(ntmax, ntc);
       achunks = std::max(achunks, (long long)mtc * TC_BM * nkt * 8);
       bchunks = std::max(bchunks, (long long)ntc * TC_BN * nkt * 8);
-      flops += 8.0 * g.m * (double)g.n * g.k;
+      flops += (CPLX ? 8.0 : 2.0) * g.m * (double)g.n * g.k;
     }
     float *ws = nullptr;
     RFDD_CUDA(cudaMallocAsync((void **)&ws, total * sizeof(float), st));
     int tiles = 0;
     for (int i = 0; i < cnt; ++i) {
       const auto &g = items[s0 + i];
-      const int mtc = ceil_div(g.m, TC_BM), ntc = ceil_div(2 * (int64_t)g.n, TC_BN), nkt = ceil_div(2 * (int64_t)g.k, TC_BK);
+      const int mtc = ceil_div(g.m, TC_BM), ntc = ceil_div((int64_t)F * g.n, TC_BN), nkt = ceil_div((int64_t)F * g.k, TC_BK);
       float *Ah = ws + offA[i], *Al = Ah + (size_t)mtc * nkt * A_TILE;
       float *Bh = ws + offB[i], *Bl = Bh + (size_t)ntc * nkt * B_TILE;
       pa.it[i] = {reinterpret_cast<const float *>(g.A), g.lda, g.m, g.n, g.k, Ah, Al, mtc, ntc, nkt};
       pbb.it[i] = {reinterpret_cast<const float *>(g.B), g.ldb, g.m, g.n, g.k, Bh, Bl, mtc, ntc, nkt};
-      tb.it[i] = {Ah, Al, Bh, Bl, reinterpret_cast<float *>(g.C), 2ll * g.ldc, g.m, 2 * g.n, nkt, mtc, ntc, tiles};
+      tb.it[i] = {Ah, Al, Bh, Bl, reinterpret_cast<float *>(g.C), (long long)F * g.ldc, g.m, F * g.n, nkt, mtc, ntc, tiles};
       tiles += mtc * ntc;
     }
     tb.count = cnt;
     tb.total_tiles = tiles;
-    pack_a_kernel<<<dim3((unsigned)std::min<long long>(ceil_div(achunks, 256), 4096), cnt), 256, 0, st>>>(pa);
-    RFDD_CHECK_LAUNCH();
-    pack_b_kernel<<<dim3((unsigned)std::min<long long>(ceil_div(bchunks, 256), 4096), cnt), 256, 0, st>>>(pbb);
-    RFDD_CHECK_LAUNCH();
+    const dim3 ga((unsigned)std::min<long long>(ceil_div(achunks, 256), 4096), cnt);
+    const dim3 gb((unsigned)std::min<long long>(ceil_div(bchunks, 256), 4096), cnt);
+    if (CPLX) {
+      pack_a_kernel<<<ga, 256, 0, st>>>(pa);
+      RFDD_CHECK_LAUNCH();
+      pack_b_kernel<<<gb, 256, 0, st>>>(pbb);
+      RFDD_CHECK_LAUNCH();
+    } else {
+      pack_a_real_kernel<<<ga, 256, 0, st>>>(pa);
+      RFDD_CHECK_LAUNCH();
+      pack_b_real_kernel<<<gb, 256, 0, st>>>(pbb);
+      RFDD_CHECK_LAUNCH();
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (profiling_enabled()) {
       e0 = profile_event();
@@ -456,6 +509,14 @@ void tc_gemm_complex(cudaStream_t st, const std::vector<GemmItem<cx<float>>> &it
   }
 }
 
+
+void tc_gemm_complex(cudaStream_t st, const std::vector<GemmItem<cx<float>>> &items, double alpha, double beta) {
+  tc_gemm_run<true>(st, items, alpha, beta);
+}
+
+void tc_gemm_real(cudaStream_t st, const std::vector<GemmItem<float>> &items, double alpha, double beta) {
+  tc_gemm_run<false>(st, items, alpha, beta);
+}
 
 // =========================================================================================
 // Allocation-free variant of the tensor-core complex GEMM.
