@@ -174,7 +174,8 @@ void sym_eig_values(cudaStream_t st, const std::vector<SymItem> &items, int *sta
       }
     }
     // e[n-1] = 0 for every item (house_kernel leaves it undefined)
-    bisect_kernel<<<dim3(ceil_div(nmax, 128), cnt), 128, 0, st>>>(b);
+    // FP64-bound and one thread per eigenvalue: warp-sized blocks spread the work over the SMs
+    bisect_kernel<<<dim3(ceil_div(nmax, 32), cnt), 32, 0, st>>>(b);
     RFDD_CHECK_LAUNCH();
   }
 }

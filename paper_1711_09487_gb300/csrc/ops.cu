@@ -124,13 +124,18 @@ __global__ void shifted_residual_kernel(const int64_t *__restrict__ rp, const in
   for (int64_t c0 = 0; c0 < b; c0 += 32) {
     const int64_t c = c0 + lane;
     if (c >= b) break;
-    double sr = 0.0, si = 0.0;
+    // (A x) and (M x) with real coefficients (4 FP64 FMAs per entry), then A x - z M x
+    double ar = 0.0, ai = 0.0, mr = 0.0, mi = 0.0;
     for (int64_t e = e0; e < e1; ++e) {
       const cx<double> x = Xl[(int64_t)col[e] * b + c];
-      const double vr = av[e] - z.re * mv[e], vi = -z.im * mv[e];
-      sr = fma(vr, x.re, fma(-vi, x.im, sr));
-      si = fma(vr, x.im, fma(vi, x.re, si));
+      const double a = av[e], m = mv[e];
+      ar = fma(a, x.re, ar);
+      ai = fma(a, x.im, ai);
+      mr = fma(m, x.re, mr);
+      mi = fma(m, x.im, mi);
     }
+    const double sr = ar - (z.re * mr - z.im * mi);
+    const double si = ai - (z.re * mi + z.im * mr);
     const cx<double> v = V[l * strideV + r * b + c];
     Rr[l * stride + r * b + c] = cx<double>(v.re - sr, v.im - si);
   }

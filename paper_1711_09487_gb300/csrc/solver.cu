@@ -510,7 +510,8 @@ void do_upload(rfdd_handle *h) {
 // ------------------------------------------------------------------------------------
 // precision-dependent parts
 // ------------------------------------------------------------------------------------
-constexpr int NBO = 128;   // outer block of the factorisations and triangular solves
+constexpr int NBO_LU = 128;  // outer block (trailing-update depth) of the factorisations
+constexpr int NBO = 256;     // outer block of the triangular solves
 
 size_t factor_bytes(const rfdd_handle *h, int nc, size_t scal) {
   size_t e = 0;
@@ -562,7 +563,7 @@ void factor_impl(rfdd_handle *h) {
       it.ld = (int)h->D[j];
       items.push_back(it);
     }
-  lu_batched<Tf>(st, items, NBO, h->status.as<int>());
+  lu_batched<Tf>(st, items, NBO_LU, h->status.as<int>());
   // a5: S(z) = C - z M_C + sum_j trailing_j, then LU
   h->Sfac.alloc((size_t)nc * s * s * sizeof(Tf));
   h->pivS.alloc((size_t)nc * s * sizeof(int));
@@ -584,7 +585,7 @@ void factor_impl(rfdd_handle *h) {
     it.dp = it.D = it.ld = (int)s;
     sit.push_back(it);
   }
-  lu_batched<Tf>(st, sit, NBO, h->status.as<int>());
+  lu_batched<Tf>(st, sit, NBO_LU, h->status.as<int>());
   sync_status(h, "factor");
   h->have_factors = true;
 }
@@ -625,6 +626,15 @@ void solve_S(rfdd_handle *h, Tf *G, int64_t ldg, int64_t gs, int64_t m, const st
     it.push_back(x);
   }
   lu_solve_batched<Tf>(h->st, it, NBO);
+}
+
+// Products on the eigenvector bases (Lanczos blocks, interior CholQR, Rayleigh-Ritz Gram
+// matrices, Ritz-vector updates): double-FP32 arithmetic in the mixed-precision solve, FP64 in
+// the plain FP64 solve.
+void basis_gemm(const rfdd_handle *h, const std::vector<GemmItem<double>> &g, bool ta, bool tb, double alpha,
+                double beta, const std::vector<char> &sym = {}) {
+  if (h->opt.precision == RFDD_FP64) gemm_simt_batched<double>(h->st, g, ta, tb, alpha, beta, sym);
+  else gemm_f64x2_batched(h->st, g, ta, tb, alpha, beta, sym);
 }
 
 std::vector<int> all_nodes(const rfdd_handle *h) {
@@ -809,15 +819,11 @@ struct RRout {
 // vstruct: the leading kappa columns of Y are blockdiag(V_j) (subdomain j's rows only, columns
 // voff[j]..voff[j+1]); their Gram blocks are then formed per subdomain (exactly zero between
 // different subdomains), and only the remaining columns need full-length products.
-// fast_gram: form the Gram matrices in double-FP32 arithmetic (near 2^-42 relative) instead of
-// FP64.  Only for bases without near-dependent columns: the pivoted Cholesky's rank test looks
-// at pivots near drop (1e-12), which a Gram matrix wrong in the 13th digit cannot resolve.
 RRout rayleigh_ritz_coeffs(rfdd_handle *h, const double *Y, int64_t k, double drop, double ctol,
                            const std::function<std::vector<int>(const std::vector<double> &)> &select,
-                           Buf &Cout, std::vector<int> &sel_out, bool vstruct, bool fast_gram) {
+                           Buf &Cout, std::vector<int> &sel_out, bool vstruct = false) {
   auto gram = [&](const std::vector<GemmItem<double>> &g, const std::vector<char> &sym) {
-    if (fast_gram) gemm_f64x2_batched(h->st, g, true, false, 1.0, 0.0, sym);
-    else gemm_simt_batched<double>(h->st, g, true, false, 1.0, 0.0, sym);
+    basis_gemm(h, g, true, false, 1.0, 0.0, sym);
   };
   cudaStream_t st = h->st;
   const int64_t n = h->n;
@@ -998,9 +1004,9 @@ void lanczos_impl(rfdd_handle *h) {
   uint64_t stream_id = 0;
   auto project_out = [&](double *Wp, int64_t bw, int64_t ncols_prev) {  // W -= Q (Q^T W)
     if (ncols_prev <= 0) return;
-    gemm_f64x2_batched(st, {{Q, Wp, Cb.as<double>(), (int)ncols_prev, (int)bw, (int)s, (int)qld, (int)bw, (int)bw}},
+    basis_gemm(h, {{Q, Wp, Cb.as<double>(), (int)ncols_prev, (int)bw, (int)s, (int)qld, (int)bw, (int)bw}},
                          true, false, 1.0, 0.0);
-    gemm_f64x2_batched(st, {{Q, Cb.as<double>(), Wp, (int)s, (int)bw, (int)ncols_prev, (int)qld, (int)bw, (int)bw}},
+    basis_gemm(h, {{Q, Cb.as<double>(), Wp, (int)s, (int)bw, (int)ncols_prev, (int)qld, (int)bw, (int)bw}},
                          false, false, -1.0, 1.0);
   };
   // Lines 4-12 of Alg. 2 for a block of bw columns (row stride bw): two classical Gram-Schmidt
@@ -1012,10 +1018,10 @@ void lanczos_impl(rfdd_handle *h) {
       project_out(Wp, bw, ncols_prev);
       bool any_dead = false;
       for (int q = 0; q < 2; ++q) {
-        gemm_f64x2_batched(st, {{Wp, Wp, Gb.as<double>(), (int)bw, (int)bw, (int)s, (int)bw, (int)bw, (int)bw}}, true,
+        basis_gemm(h, {{Wp, Wp, Gb.as<double>(), (int)bw, (int)bw, (int)s, (int)bw, (int)bw, (int)bw}}, true,
                            false, 1.0, 0.0, {1});
         chol_inv_batched(st, {CholItem{Gb.as<double>(), Rinv.as<double>(), dead.as<int>(), (int)bw}}, 1e-24);
-        gemm_f64x2_batched(st, {{Wp, Rinv.as<double>(), tmp.as<double>(), (int)s, (int)bw, (int)bw, (int)bw, (int)bw,
+        basis_gemm(h, {{Wp, Rinv.as<double>(), tmp.as<double>(), (int)s, (int)bw, (int)bw, (int)bw, (int)bw,
                                    (int)bw}},
                              false, false, 1.0, 0.0);
         RFDD_CUDA(cudaMemcpyAsync(Wp, tmp.p, (size_t)s * bw * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -1057,11 +1063,11 @@ void lanczos_impl(rfdd_handle *h) {
     filter_impl<Tf>(h, Xb.as<double>(), W.as<double>(), bc, 1.0);  // line 2: F q
     lap.mark("filter");
     if (nblk > 0)  // ... - Q_{mu-1} B_mu^T
-      gemm_f64x2_batched(st, {{Q + col - bprev, Bprev.as<double>(), W.as<double>(), (int)s, (int)bc, (int)bprev,
+      basis_gemm(h, {{Q + col - bprev, Bprev.as<double>(), W.as<double>(), (int)s, (int)bc, (int)bprev,
                                  (int)qld, (int)bprev, (int)bc}},
                            false, true, -1.0, 1.0);
     // line 3: A_mu = Q_mu^T W
-    gemm_f64x2_batched(st, {{Xb.as<double>(), W.as<double>(), Amu.as<double>(), (int)bc, (int)bc, (int)s, (int)bc,
+    basis_gemm(h, {{Xb.as<double>(), W.as<double>(), Amu.as<double>(), (int)bc, (int)bc, (int)s, (int)bc,
                                (int)bc, (int)bc}},
                          true, false, 1.0, 0.0);
     RFDD_CUDA(cudaMemcpyAsync(ha.data(), Amu.p, bc * bc * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1086,7 +1092,7 @@ void lanczos_impl(rfdd_handle *h) {
     orthonormalize(W.as<double>(), bn, mu_now);
     lap.mark("orthonormalize");
     // B (bn x bc) = Q_next^T W_raw
-    gemm_f64x2_batched(st, {{W.as<double>(), Wraw.as<double>(), Bprev.as<double>(), (int)bn, (int)bc, (int)s, (int)bn,
+    basis_gemm(h, {{W.as<double>(), Wraw.as<double>(), Bprev.as<double>(), (int)bn, (int)bc, (int)s, (int)bn,
                                (int)bc, (int)bc}},
                          true, false, 1.0, 0.0);
     copy_rows_f64(st, W.as<double>(), bn, Q + mu_now, qld, s, bn);
@@ -1135,7 +1141,7 @@ void interior_impl(rfdd_handle *h, double sigma) {
     it.dp = it.D = it.ld = (int)h->d[j];
     items.push_back(it);
   }
-  lu_batched<Tr>(st, items, NBO, h->status.as<int>());
+  lu_batched<Tr>(st, items, NBO_LU, h->status.as<int>());
   sync_status(h, "interior LU");
   auto solve_Bs = [&](double *X, int64_t ldx, int64_t m) {  // X (dsum x m FP64, all subdomains) <- B_sigma^{-1} X
     Buf t;
@@ -1190,13 +1196,13 @@ void interior_impl(rfdd_handle *h, double sigma) {
         ch.push_back({G.as<double>() + (int64_t)j * mw * mw, Rinv.as<double>() + (int64_t)j * mw * mw,
                       dead.as<int>() + j * mw, (int)mb[j]});
       }
-      gemm_f64x2_batched(st, g, true, false, 1.0, 0.0, std::vector<char>(g.size(), 1));
+      basis_gemm(h, g, true, false, 1.0, 0.0, std::vector<char>(g.size(), 1));
       chol_inv_batched(st, ch, 1e-28);
       std::vector<GemmItem<double>> g2;
       for (int j = 0; j < p; ++j)
         g2.push_back({Xp + h->off[j] * mw, Rinv.as<double>() + (int64_t)j * mw * mw, T.as<double>() + h->off[j] * mw,
                       (int)h->d[j], (int)mb[j], (int)mb[j], (int)mw, (int)mb[j], (int)mw});
-      gemm_f64x2_batched(st, g2, false, false, 1.0, 0.0);
+      basis_gemm(h, g2, false, false, 1.0, 0.0);
       RFDD_CUDA(cudaMemcpyAsync(Xp, T.p, (size_t)dsum * mw * sizeof(double), cudaMemcpyDeviceToDevice, st));
     }
   };
@@ -1216,7 +1222,7 @@ void interior_impl(rfdd_handle *h, double sigma) {
       g.push_back({X.as<double>() + h->off[j] * mw, Y.as<double>() + h->off[j] * mw,
                    G.as<double>() + (int64_t)j * mw * mw, (int)mb[j], (int)mb[j], (int)h->d[j], (int)mw, (int)mw,
                    (int)mb[j]});
-    gemm_f64x2_batched(st, g, true, false, 1.0, 0.0, std::vector<char>(g.size(), 1));
+    basis_gemm(h, g, true, false, 1.0, 0.0, std::vector<char>(g.size(), 1));
   }
   Buf ed, ee, et, ew, el, eZ;
   ed.alloc((size_t)p * mw * sizeof(double));
@@ -1260,7 +1266,7 @@ void interior_impl(rfdd_handle *h, double sigma) {
     for (int j = 0; j < p; ++j)
       g.push_back({X.as<double>() + h->off[j] * mw, Gt.as<double>() + (int64_t)j * mw * mw, Z + h->off[j] * kz + voff[j],
                    (int)h->d[j], (int)nvb[j], (int)mb[j], (int)mw, (int)mb[j], (int)kz});
-    gemm_f64x2_batched(st, g, false, true, 1.0, 0.0);
+    basis_gemm(h, g, false, true, 1.0, 0.0);
   }
   X.release();
   Y.release();
@@ -1330,12 +1336,12 @@ void rr_on_Z(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
         m_sel = m;
         return select_nearest(th, alpha, beta, m);
       },
-      C, sel, true, false);
+      C, sel, true);
   h->rr_theta = rr.theta;
   h->m0 = (int64_t)sel.size();
   h->X0.alloc((size_t)n * std::max<int64_t>(1, h->m0) * sizeof(double));
   if (h->m0 > 0)
-    gemm_f64x2_batched(st, {{h->Zb.as<double>(), C.as<double>(), h->X0.as<double>(), (int)n, (int)h->m0, (int)kz,
+    basis_gemm(h, {{h->Zb.as<double>(), C.as<double>(), h->X0.as<double>(), (int)n, (int)h->m0, (int)kz,
                              (int)kz, (int)h->m0, (int)h->m0}},
                        false, false, 1.0, 0.0);
   if (res) {
@@ -1400,8 +1406,9 @@ void complete(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
     spmm_f64(st, h->P, 0, n, 0, n, 0.0, 1.0, X.as<double>(), m, V.as<double>(), m, m, false);
     Xc.ensure((size_t)nc * n * m * sizeof(cx<double>));
     // the filter only has to be as accurate as the subspace it acts on: refine the shifted
-    // solves to a small fraction of the current residual level
-    const double ir_tol = std::max(1e-14, 1e-6 * res_level);
+    // solves to a small fraction of the current residual level, and no further than a small
+    // fraction of the residual target
+    const double ir_tol = std::max(std::max(1e-15, 1e-3 * h->opt.res_tol), 1e-6 * res_level);
     irmax = std::max(irmax, refined_solve<Tf>(h, V.as<double>(), Xc.as<cx<double>>(), m, ir_tol));
     weighted_real_sum<cx<double>>(st, Xc.as<cx<double>>(), n * m, h->w_dev.as<cx<double>>(), nc, 2.0, X.as<double>(),
                                   n * m);
@@ -1414,11 +1421,11 @@ void complete(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
           std::iota(all.begin(), all.end(), 0);
           return all;
         },
-        C, sel, false, true);
+        C, sel);
     const int64_t r = rr.r;
     Buf Xn;
     Xn.alloc((size_t)n * r * sizeof(double));
-    gemm_f64x2_batched(st, {{X.as<double>(), C.as<double>(), Xn.as<double>(), (int)n, (int)r, (int)m, (int)m,
+    basis_gemm(h, {{X.as<double>(), C.as<double>(), Xn.as<double>(), (int)n, (int)r, (int)m, (int)m,
                              (int)r, (int)r}},
                        false, false, 1.0, 0.0);
     theta = rr.theta;
