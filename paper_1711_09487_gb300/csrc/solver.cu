@@ -510,7 +510,7 @@ void do_upload(rfdd_handle *h) {
 // ------------------------------------------------------------------------------------
 // precision-dependent parts
 // ------------------------------------------------------------------------------------
-constexpr int NBO_LU = 128;  // outer block (trailing-update depth) of the factorisations
+constexpr int NBO_LU = 256;  // outer block (trailing-update depth) of the factorisations
 constexpr int NBO = 256;     // outer block of the triangular solves
 
 size_t factor_bytes(const rfdd_handle *h, int nc, size_t scal) {
@@ -1407,8 +1407,8 @@ void complete(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
     Xc.ensure((size_t)nc * n * m * sizeof(cx<double>));
     // the filter only has to be as accurate as the subspace it acts on: refine the shifted
     // solves to a small fraction of the current residual level, and no further than a small
-    // fraction of the residual target
-    const double ir_tol = std::max(std::max(1e-15, 1e-3 * h->opt.res_tol), 1e-6 * res_level);
+    // fraction (1/100) of the residual target
+    const double ir_tol = std::max(std::max(1e-15, 1e-2 * h->opt.res_tol), 1e-6 * res_level);
     irmax = std::max(irmax, refined_solve<Tf>(h, V.as<double>(), Xc.as<cx<double>>(), m, ir_tol));
     weighted_real_sum<cx<double>>(st, Xc.as<cx<double>>(), n * m, h->w_dev.as<cx<double>>(), nc, 2.0, X.as<double>(),
                                   n * m);
