@@ -967,10 +967,148 @@ void apply_pivots(cudaStream_t st, const std::vector<SolveItem<T>> &items) {
   }
 }
 
+// ======================================================================================
+// Triangular solves with inverted diagonal blocks: per nbo-block, X_b <- inv(T_bb) X_b as one
+// product into a scratch slab copied back, then the deep update of the rows still to solve.
+// ======================================================================================
+template <typename T>
+struct CopyItem {
+  const T *src;
+  T *dst;
+  int lds, ldd, rows, cols;
+};
+template <typename T>
+struct CopyBatchP {
+  CopyItem<T> it[MAXB];
+};
+template <typename T>
+__global__ void copy_rows_batched_kernel(CopyBatchP<T> b) {
+  const CopyItem<T> c = b.it[blockIdx.y];
+  const int64_t tot = (int64_t)c.rows * c.cols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / c.cols, q = e % c.cols;
+    c.dst[r * c.ldd + q] = c.src[r * c.lds + q];
+  }
+}
+template <typename T>
+static void copy_rows_batched(cudaStream_t st, const std::vector<CopyItem<T>> &items) {
+  for (size_t s = 0; s < items.size(); s += MAXB) {
+    CopyBatchP<T> b;
+    memset(&b, 0, sizeof(b));
+    const int cnt = (int)std::min<size_t>(MAXB, items.size() - s);
+    int64_t mx = 1;
+    for (int i = 0; i < cnt; ++i) {
+      b.it[i] = items[s + i];
+      mx = std::max<int64_t>(mx, (int64_t)b.it[i].rows * b.it[i].cols);
+    }
+    copy_rows_batched_kernel<T><<<dim3((unsigned)std::min<int64_t>(ceil_div(mx, 256), 1024), cnt), 256, 0, st>>>(b);
+    RFDD_CHECK_LAUNCH();
+  }
+}
+
+template <typename T>
+__global__ void identity_blocks_kernel(T *base, int64_t nblk, int nbi) {
+  const int64_t tot = nblk * nbi * nbi;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t w = e % ((int64_t)nbi * nbi);
+    base[e] = (w / nbi == w % nbi) ? ST<T>::one() : ST<T>::zero();
+  }
+}
+
+template <typename T>
+void trsm_lower_unit(cudaStream_t st, const std::vector<SolveItem<T>> &items, int nbo);
+template <typename T>
+void trsm_upper(cudaStream_t st, const std::vector<SolveItem<T>> &items, int nbo);
+
+template <typename T>
+void lu_block_inverses(cudaStream_t st, const std::vector<SolveItem<T>> &items, int nbi, const std::vector<T *> &Linv,
+                       const std::vector<T *> &Uinv) {
+  for (int which = 0; which < 2; ++which) {
+    const std::vector<T *> &inv = which == 0 ? Linv : Uinv;
+    std::vector<SolveItem<T>> bl;
+    for (size_t i = 0; i < items.size(); ++i) {
+      if (!inv[i] || items[i].n <= 0) continue;
+      const SolveItem<T> &it = items[i];
+      const int64_t nblk = ceil_div(it.n, nbi);
+      identity_blocks_kernel<T><<<(unsigned)std::min<int64_t>(ceil_div(nblk * nbi * nbi, 256), 4096), 256, 0, st>>>(
+          inv[i], nblk, nbi);
+      RFDD_CHECK_LAUNCH();
+      for (int64_t b = 0; b < nblk; ++b) {
+        const int k0 = (int)(b * nbi), w = std::min(nbi, it.n - k0);
+        SolveItem<T> x;
+        x.LU = it.LU + (int64_t)k0 * it.ld + k0;
+        x.piv = nullptr;
+        x.n = w;
+        x.ld = it.ld;
+        x.X = inv[i] + b * nbi * nbi;
+        x.ldx = nbi;
+        x.ncols = w;
+        bl.push_back(x);
+      }
+    }
+    if (bl.empty()) continue;
+    if (which == 0) trsm_lower_unit<T>(st, bl, nbi);
+    else trsm_upper<T>(st, bl, nbi);
+  }
+}
+
+template <typename T>
+static bool has_block_inverses(const std::vector<SolveItem<T>> &items, int nbo, bool upper) {
+  if (items.empty()) return false;
+  for (auto &it : items)
+    if ((upper ? it.Uinv : it.Linv) == nullptr || it.nbi != nbo) return false;
+  return true;
+}
+
+// upper = false: X <- L^{-1} X (blocks top to bottom); true: X <- U^{-1} X (bottom to top)
+template <typename T>
+static void trsm_block_inverse(cudaStream_t st, const std::vector<SolveItem<T>> &items, int nbo, bool upper) {
+  int nmax = 0;
+  size_t tmp_elems = 0;
+  std::vector<size_t> toff(items.size());
+  for (size_t i = 0; i < items.size(); ++i) {
+    nmax = std::max(nmax, items[i].n);
+    toff[i] = tmp_elems;
+    tmp_elems += (size_t)nbo * std::max(items[i].ncols, 0);
+  }
+  if (nmax == 0 || tmp_elems == 0) return;
+  T *tmp = nullptr;
+  RFDD_CUDA(cudaMallocAsync((void **)&tmp, tmp_elems * sizeof(T), st));
+  const int nblk = ceil_div(nmax, nbo);
+  for (int step = 0; step < nblk; ++step) {
+    const int b = upper ? nblk - 1 - step : step;
+    const int K0 = b * nbo;
+    std::vector<GemmItem<T>> g1, g2;
+    std::vector<CopyItem<T>> cp;
+    for (size_t i = 0; i < items.size(); ++i) {
+      const SolveItem<T> &it = items[i];
+      if (K0 >= it.n || it.ncols <= 0) continue;
+      const int w = std::min(nbo, it.n - K0);
+      const T *inv = (upper ? it.Uinv : it.Linv) + (int64_t)b * nbo * nbo;
+      T *xb = it.X + (int64_t)K0 * it.ldx, *t = tmp + toff[i];
+      g1.push_back({inv, xb, t, w, it.ncols, w, nbo, it.ldx, it.ncols});
+      cp.push_back({t, xb, it.ncols, it.ldx, w, it.ncols});
+      if (!upper && it.n - K0 - w > 0)  // rows below: X[K0+w:] -= L[K0+w:, K0:K0+w] X_b
+        g2.push_back({it.LU + (int64_t)(K0 + w) * it.ld + K0, xb, it.X + (int64_t)(K0 + w) * it.ldx, it.n - K0 - w,
+                      it.ncols, w, it.ld, it.ldx, it.ldx});
+      if (upper && K0 > 0)  // rows above: X[0:K0] -= U[0:K0, K0:K0+w] X_b
+        g2.push_back({it.LU + K0, xb, it.X, K0, it.ncols, w, it.ld, it.ldx, it.ldx});
+    }
+    gemm_batched<T>(st, g1, false, false, 1.0, 0.0);
+    copy_rows_batched<T>(st, cp);
+    gemm_batched<T>(st, g2, false, false, -1.0, 1.0);
+  }
+  RFDD_CUDA(cudaFreeAsync(tmp, st));
+}
+
 // X <- L^{-1} X, L unit lower (n x n): 32-row diagonal solves and GEMM updates, two levels
 // (updates inside an nbo-row block, then one deep update of everything below it).
 template <typename T>
 void trsm_lower_unit(cudaStream_t st, const std::vector<SolveItem<T>> &items, int nbo) {
+  if (has_block_inverses(items, nbo, false)) {
+    trsm_block_inverse<T>(st, items, nbo, false);
+    return;
+  }
   constexpr int NB = LU_NB;
   int nmax = 0;
   for (auto &it : items) nmax = std::max(nmax, it.n);
@@ -1008,6 +1146,10 @@ void trsm_lower_unit(cudaStream_t st, const std::vector<SolveItem<T>> &items, in
 // X <- U^{-1} X, U upper (n x n) with its diagonal.
 template <typename T>
 void trsm_upper(cudaStream_t st, const std::vector<SolveItem<T>> &items, int nbo) {
+  if (has_block_inverses(items, nbo, true)) {
+    trsm_block_inverse<T>(st, items, nbo, true);
+    return;
+  }
   constexpr int NB = LU_NB;
   int nmax = 0;
   for (auto &it : items) nmax = std::max(nmax, it.n);
@@ -1056,7 +1198,9 @@ void lu_solve_batched(cudaStream_t st, const std::vector<SolveItem<T>> &items, i
   template void lu_solve_batched<T>(cudaStream_t, const std::vector<SolveItem<T>> &, int);        \
   template void apply_pivots<T>(cudaStream_t, const std::vector<SolveItem<T>> &);                 \
   template void trsm_lower_unit<T>(cudaStream_t, const std::vector<SolveItem<T>> &, int);         \
-  template void trsm_upper<T>(cudaStream_t, const std::vector<SolveItem<T>> &, int);
+  template void trsm_upper<T>(cudaStream_t, const std::vector<SolveItem<T>> &, int);                \
+  template void lu_block_inverses<T>(cudaStream_t, const std::vector<SolveItem<T>> &, int, const std::vector<T *> &, \
+                                     const std::vector<T *> &);
 
 RFDD_INST_DENSE(float)
 RFDD_INST_DENSE(double)

@@ -54,6 +54,11 @@ template <typename T>
 void lu_batched(cudaStream_t st, const std::vector<LuItem<T>> &items, int nbo, int *dev_status);
 
 // Solve with LU factors: X <- U^{-1} L^{-1} P X for the leading dp x dp block of each item.
+// Optional: inverses of the nbi x nbi diagonal blocks of L (unit lower) and U (upper), block b
+// at Linv + b * nbi * nbi (leading dimension nbi; the last block uses its leading w x w part).
+// When every item of a triangular solve carries them and nbi equals the solve's block size, the
+// diagonal blocks are applied as matrix products (tensor cores for complex FP32) instead of by
+// substitution.
 template <typename T>
 struct SolveItem {
   const T *LU;
@@ -61,7 +66,16 @@ struct SolveItem {
   int n, ld;       // order of the factored block and its leading dimension
   T *X;
   int ldx, ncols;
+  const T *Linv = nullptr, *Uinv = nullptr;
+  int nbi = 0;
 };
+// Elements of the inverse-block storage of one n x n factor.
+inline int64_t block_inverse_elems(int64_t n, int nbi) { return (int64_t)((n + nbi - 1) / nbi) * nbi * nbi; }
+// Linv[i] / Uinv[i] <- inverses of the diagonal nbi-blocks of items[i]'s L and U (either may be
+// null to skip it); computed by substitution against identity blocks.
+template <typename T>
+void lu_block_inverses(cudaStream_t st, const std::vector<SolveItem<T>> &items, int nbi, const std::vector<T *> &Linv,
+                       const std::vector<T *> &Uinv);
 template <typename T>
 void lu_solve_batched(cudaStream_t st, const std::vector<SolveItem<T>> &items, int nbo);
 

@@ -200,6 +200,10 @@ struct rfdd_handle {
   int nnodes = 0;
   std::vector<cx<double>> z, w;
   Buf z_dev, w_dev, fac, boff_dev, Doff_dev, pivB, Sfac, pivS, Skeep;
+  // inverses of the NBO-blocks on the diagonals of the B and S factors (triangular solves)
+  Buf BLinv, BUinv, SLinv, SUinv;
+  std::vector<int64_t> binvoff;  // (node, subdomain) -> offset into BLinv / BUinv
+  int64_t sinv_elems = 0;        // per node in SLinv / SUinv
   std::vector<int64_t> boff, pivBoff;
   bool have_factors = false;
   double alpha = 0, beta = 0;
@@ -518,6 +522,9 @@ size_t factor_bytes(const rfdd_handle *h, int nc, size_t scal) {
   for (int j = 0; j < h->p; ++j) e += (size_t)h->D[j] * h->D[j];
   size_t b = (size_t)nc * e * scal;
   b += (size_t)nc * h->s * h->s * scal * (h->opt.keep_schur ? 2 : 1);
+  size_t inv = (size_t)block_inverse_elems(h->s, NBO);  // inverted diagonal blocks of L and U
+  for (int j = 0; j < h->p; ++j) inv += (size_t)block_inverse_elems(h->d[j], NBO);
+  b += 2 * (size_t)nc * inv * scal;
   b += (size_t)nc * (h->dsum + h->s) * sizeof(int);
   return b;
 }
@@ -564,6 +571,33 @@ void factor_impl(rfdd_handle *h) {
       items.push_back(it);
     }
   lu_batched<Tf>(st, items, NBO_LU, h->status.as<int>());
+  {  // inverted diagonal blocks of every B_j(z_l) factor, for the triangular solves
+    h->binvoff.assign((size_t)nc * p, 0);
+    int64_t bt = 0;
+    for (int l = 0; l < nc; ++l)
+      for (int j = 0; j < p; ++j) {
+        h->binvoff[(size_t)l * p + j] = bt;
+        bt += block_inverse_elems(h->d[j], NBO);
+      }
+    h->BLinv.alloc((size_t)bt * sizeof(Tf));
+    h->BUinv.alloc((size_t)bt * sizeof(Tf));
+    std::vector<SolveItem<Tf>> fi;
+    std::vector<Tf *> li, ui;
+    for (int l = 0; l < nc; ++l)
+      for (int j = 0; j < p; ++j) {
+        SolveItem<Tf> x;
+        x.LU = base + h->boff[(size_t)l * p + j];
+        x.piv = nullptr;
+        x.n = (int)h->d[j];
+        x.ld = (int)h->D[j];
+        x.X = nullptr;
+        x.ldx = x.ncols = 0;
+        fi.push_back(x);
+        li.push_back(h->BLinv.as<Tf>() + h->binvoff[(size_t)l * p + j]);
+        ui.push_back(h->BUinv.as<Tf>() + h->binvoff[(size_t)l * p + j]);
+      }
+    lu_block_inverses<Tf>(st, fi, NBO, li, ui);
+  }
   // a5: S(z) = C - z M_C + sum_j trailing_j, then LU
   h->Sfac.alloc((size_t)nc * s * s * sizeof(Tf));
   h->pivS.alloc((size_t)nc * s * sizeof(int));
@@ -586,8 +620,37 @@ void factor_impl(rfdd_handle *h) {
     sit.push_back(it);
   }
   lu_batched<Tf>(st, sit, NBO_LU, h->status.as<int>());
+  {
+    h->sinv_elems = block_inverse_elems(s, NBO);
+    h->SLinv.alloc((size_t)nc * h->sinv_elems * sizeof(Tf));
+    h->SUinv.alloc((size_t)nc * h->sinv_elems * sizeof(Tf));
+    std::vector<SolveItem<Tf>> fi;
+    std::vector<Tf *> li, ui;
+    for (int l = 0; l < nc; ++l) {
+      SolveItem<Tf> x;
+      x.LU = S + (int64_t)l * s * s;
+      x.piv = nullptr;
+      x.n = x.ld = (int)s;
+      x.X = nullptr;
+      x.ldx = x.ncols = 0;
+      fi.push_back(x);
+      li.push_back(h->SLinv.as<Tf>() + (int64_t)l * h->sinv_elems);
+      ui.push_back(h->SUinv.as<Tf>() + (int64_t)l * h->sinv_elems);
+    }
+    lu_block_inverses<Tf>(st, fi, NBO, li, ui);
+  }
   sync_status(h, "factor");
   h->have_factors = true;
+}
+
+// the inverted diagonal blocks of factor (node l, subdomain j), when present
+template <typename Tf>
+void attach_binv(const rfdd_handle *h, SolveItem<Tf> &x, int l, int j) {
+  if (!h->BLinv.p) return;
+  const int64_t o = h->binvoff[(size_t)l * h->p + j];
+  x.Linv = h->BLinv.as<Tf>() + o;
+  x.Uinv = h->BUinv.as<Tf>() + o;
+  x.nbi = NBO;
 }
 
 // B_j(z_l) solves on a tall block F (n x m per node, stride fs): interior rows only
@@ -606,6 +669,7 @@ void solve_B(rfdd_handle *h, Tf *F, int64_t ldf, int64_t fs, int64_t m, const st
       x.X = F + (int64_t)l * fs + (h->off[j] - row_base_shift) * ldf;
       x.ldx = (int)ldf;
       x.ncols = (int)m;
+      attach_binv(h, x, l, j);
       it.push_back(x);
     }
   lu_solve_batched<Tf>(h->st, it, NBO);
@@ -623,6 +687,11 @@ void solve_S(rfdd_handle *h, Tf *G, int64_t ldg, int64_t gs, int64_t m, const st
     x.X = G + (int64_t)l * gs;
     x.ldx = (int)ldg;
     x.ncols = (int)m;
+    if (h->SLinv.p) {
+      x.Linv = h->SLinv.as<Tf>() + (int64_t)l * h->sinv_elems;
+      x.Uinv = h->SUinv.as<Tf>() + (int64_t)l * h->sinv_elems;
+      x.nbi = NBO;
+    }
     it.push_back(x);
   }
   lu_solve_batched<Tf>(h->st, it, NBO);
@@ -690,6 +759,7 @@ void dd_solve(rfdd_handle *h, const cx<double> *R, int64_t strideR, cx<double> *
         x.X = f + (int64_t)l * fs + h->off[j] * m;
         x.ldx = (int)m;
         x.ncols = (int)m;
+        attach_binv(h, x, l, j);
         it.push_back(x);
       }
     apply_pivots<Tf>(st, it);
@@ -740,6 +810,7 @@ void dd_solve(rfdd_handle *h, const cx<double> *R, int64_t strideR, cx<double> *
         x.X = f + (int64_t)l * fs + h->off[j] * m;
         x.ldx = (int)m;
         x.ncols = (int)m;
+        attach_binv(h, x, l, j);
         it.push_back(x);
       }
     gemm_batched<Tf>(st, g, false, false, -1.0, 1.0);
@@ -1142,6 +1213,28 @@ void interior_impl(rfdd_handle *h, double sigma) {
     items.push_back(it);
   }
   lu_batched<Tr>(st, items, NBO_LU, h->status.as<int>());
+  // inverted diagonal blocks for the many solves of the subspace iteration and the chains
+  std::vector<int64_t> rinvoff(p + 1, 0);
+  for (int j = 0; j < p; ++j) rinvoff[j + 1] = rinvoff[j] + block_inverse_elems(h->d[j], NBO);
+  Buf RLinv, RUinv;
+  RLinv.alloc((size_t)rinvoff[p] * sizeof(Tr));
+  RUinv.alloc((size_t)rinvoff[p] * sizeof(Tr));
+  {
+    std::vector<SolveItem<Tr>> fi;
+    std::vector<Tr *> li, ui;
+    for (int j = 0; j < p; ++j) {
+      SolveItem<Tr> x;
+      x.LU = Bs.as<Tr>() + boffr[j];
+      x.piv = nullptr;
+      x.n = x.ld = (int)h->d[j];
+      x.X = nullptr;
+      x.ldx = x.ncols = 0;
+      fi.push_back(x);
+      li.push_back(RLinv.as<Tr>() + rinvoff[j]);
+      ui.push_back(RUinv.as<Tr>() + rinvoff[j]);
+    }
+    lu_block_inverses<Tr>(st, fi, NBO, li, ui);
+  }
   sync_status(h, "interior LU");
   auto solve_Bs = [&](double *X, int64_t ldx, int64_t m) {  // X (dsum x m FP64, all subdomains) <- B_sigma^{-1} X
     Buf t;
@@ -1156,6 +1249,9 @@ void interior_impl(rfdd_handle *h, double sigma) {
       x.X = t.as<Tr>() + h->off[j] * m;
       x.ldx = (int)m;
       x.ncols = (int)m;
+      x.Linv = RLinv.as<Tr>() + rinvoff[j];
+      x.Uinv = RUinv.as<Tr>() + rinvoff[j];
+      x.nbi = NBO;
       si.push_back(x);
     }
     lu_solve_batched<Tr>(st, si, NBO);
@@ -1499,6 +1595,10 @@ void factor(rfdd_handle *h) {
   h->fac.release();
   h->Sfac.release();
   h->Skeep.release();
+  h->BLinv.release();
+  h->BUinv.release();
+  h->SLinv.release();
+  h->SUinv.release();
   if (is_mixed(h)) factor_impl<cx<float>>(h);
   else factor_impl<cx<double>>(h);
 }
@@ -1765,11 +1865,17 @@ int rfdd_shifted_solve(rfdd_handle *h, int32_t node, int32_t which, int32_t j, i
         si[0].piv = h->pivB.as<int>() + h->pivBoff[(size_t)node * h->p + j];
         si[0].n = (int)h->d[j];
         si[0].ld = (int)h->D[j];
+        attach_binv(h, si[0], node, j);
       } else {
         si[0].LU = h->Sfac.as<Tf>() + (int64_t)node * h->s * h->s;
         si[0].piv = h->pivS.as<int>() + (int64_t)node * h->s;
         si[0].n = (int)h->s;
         si[0].ld = (int)h->s;
+        if (h->SLinv.p) {
+          si[0].Linv = h->SLinv.as<Tf>() + (int64_t)node * h->sinv_elems;
+          si[0].Uinv = h->SUinv.as<Tf>() + (int64_t)node * h->sinv_elems;
+          si[0].nbi = NBO;
+        }
       }
       si[0].X = t.as<Tf>();
       si[0].ldx = (int)nrhs;
