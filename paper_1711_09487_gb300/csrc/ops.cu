@@ -149,6 +149,98 @@ void shifted_residual(cudaStream_t st, const DevPencil &P, const cx<double> *z_d
   RFDD_CHECK_LAUNCH();
 }
 
+// Double-FP32 variant.  The residual only has to resolve a scaled backward error a little
+// below the refinement target (1e-12 of (||A|| + |z| ||M||) ||x|| by default); split operands
+// (x = hi + lo, |x - hi - lo| <= 2^-48 |x|), error-free products (FMA) and compensated sums
+// give about 2^-46 of sum |a||x| per product sum at FP32 throughput, instead of the FP64
+// pipes that bound the FP64 kernel above.
+__device__ __forceinline__ void df_mac(float &s, float &c, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  const float e = __fmaf_rn(ah, bh, -p);
+  const float t = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, e));
+  const float s1 = __fadd_rn(s, p);
+  const float bb = __fsub_rn(s1, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(s1, bb)), __fsub_rn(p, bb));
+  s = s1;
+  c = __fadd_rn(c, __fadd_rn(err, t));
+}
+__device__ __forceinline__ void split_d(double v, float &hi, float &lo) {
+  hi = __double2float_rn(v);
+  lo = __double2float_rn(v - (double)hi);
+}
+__global__ void split_pencil_kernel(const double *__restrict__ a, const double *__restrict__ m, int64_t nnz,
+                                    float4 *__restrict__ out) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+    float4 w;
+    split_d(a[e], w.x, w.y);
+    split_d(m[e], w.z, w.w);
+    out[e] = w;
+  }
+}
+void split_pencil(cudaStream_t st, DevPencil &P, float4 *out) {
+  if (P.nnz > 0) {
+    split_pencil_kernel<<<std::min(4096, ceil_div(P.nnz, 256)), 256, 0, st>>>(P.a, P.m, P.nnz, out);
+    RFDD_CHECK_LAUNCH();
+  }
+  P.am_split = out;
+}
+__global__ void split_c64_kernel(const cx<double> *__restrict__ X, float4 *__restrict__ Xs, int64_t count) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+    const cx<double> x = X[e];
+    float4 w;
+    split_d(x.re, w.x, w.y);
+    split_d(x.im, w.z, w.w);
+    Xs[e] = w;
+  }
+}
+void split_c64(cudaStream_t st, const cx<double> *X, float4 *Xs, int64_t count) {
+  if (count <= 0) return;
+  split_c64_kernel<<<(unsigned)std::min<int64_t>(16384, ceil_div(count, 256)), 256, 0, st>>>(X, Xs, count);
+  RFDD_CHECK_LAUNCH();
+}
+__global__ void shifted_residual_df_kernel(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                           const float4 *__restrict__ am, int64_t n, const cx<double> *__restrict__ zz,
+                                           const cx<double> *__restrict__ V, int64_t strideV,
+                                           const float4 *__restrict__ Xs, cx<double> *__restrict__ Rr, int64_t stride,
+                                           int64_t b) {
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const int lane = threadIdx.x & 31;
+  const int l = blockIdx.y;
+  if (r >= n) return;
+  const cx<double> z = zz[l];
+  const float4 *Xl = Xs + l * stride;
+  const int64_t e0 = rp[r], e1 = rp[r + 1];
+  for (int64_t c0 = 0; c0 < b; c0 += 32) {
+    const int64_t c = c0 + lane;
+    if (c >= b) break;
+    // (A x) and (M x), real and imaginary parts, each as an unevaluated pair (s, t)
+    float s0 = 0.f, t0 = 0.f, s1 = 0.f, t1 = 0.f, s2 = 0.f, t2 = 0.f, s3 = 0.f, t3 = 0.f;
+    for (int64_t e = e0; e < e1; ++e) {
+      const float4 x = Xl[(int64_t)col[e] * b + c];
+      const float4 w = am[e];
+      df_mac(s0, t0, w.x, w.y, x.x, x.y);
+      df_mac(s1, t1, w.x, w.y, x.z, x.w);
+      df_mac(s2, t2, w.z, w.w, x.x, x.y);
+      df_mac(s3, t3, w.z, w.w, x.z, x.w);
+    }
+    const double ar = (double)s0 + (double)t0, ai = (double)s1 + (double)t1;
+    const double mr = (double)s2 + (double)t2, mi = (double)s3 + (double)t3;
+    const double sr = ar - (z.re * mr - z.im * mi);
+    const double si = ai - (z.re * mi + z.im * mr);
+    const cx<double> v = V[l * strideV + r * b + c];
+    Rr[l * stride + r * b + c] = cx<double>(v.re - sr, v.im - si);
+  }
+}
+void shifted_residual_df(cudaStream_t st, const DevPencil &P, const cx<double> *z_dev, int nnodes,
+                         const cx<double> *V, int64_t strideV, const float4 *Xs, cx<double> *R, int64_t stride,
+                         int64_t b) {
+  RFDD_REQUIRE(P.am_split != nullptr, RFDD_ESTATE, "split pencil values missing");
+  dim3 grid(ceil_div(P.n * 32, 256), nnodes);
+  shifted_residual_df_kernel<<<grid, 256, 0, st>>>(P.rowptr, P.col, P.am_split, P.n, z_dev, V, strideV, Xs, R, stride,
+                                                   b);
+  RFDD_CHECK_LAUNCH();
+}
+
 // --------------------------------------------------------------------------------------
 // a2: assemble dense (bordered) shifted blocks; warp per row
 // --------------------------------------------------------------------------------------

@@ -12,6 +12,7 @@ struct DevPencil {
   int32_t *col = nullptr;     // nnz
   double *a = nullptr;        // A values
   double *m = nullptr;        // M values
+  float4 *am_split = nullptr; // per entry (hi(a), lo(a), hi(m), lo(m)): double-FP32 copies
 };
 
 // Subdomain geometry on the device.
@@ -38,6 +39,15 @@ void couple(cudaStream_t st, const DevPencil &P, int64_t r0, int64_t r1, int64_t
             int64_t strideY, int64_t b, double sign, bool accumulate);
 
 // R_l = V_l - (A - z_l M) X_l  (complex FP64, all rows, all nodes); V may have stride 0.
+// P.am_split <- the double-FP32 split of the pencil's values (x = hi + lo, hi = fl32(x))
+void split_pencil(cudaStream_t st, DevPencil &P, float4 *out);
+// Xs[i] = (hi(re), lo(re), hi(im), lo(im)) of X[i], count elements
+void split_c64(cudaStream_t st, const cx<double> *X, float4 *Xs, int64_t count);
+// shifted_residual with the products in double-FP32 arithmetic on split operands (P.am_split
+// and Xs); the combination with z_l and the difference with V stay FP64
+void shifted_residual_df(cudaStream_t st, const DevPencil &P, const cx<double> *z_dev, int nnodes,
+                         const cx<double> *V, int64_t strideV, const float4 *Xs, cx<double> *R, int64_t stride,
+                         int64_t b);
 void shifted_residual(cudaStream_t st, const DevPencil &P, const cx<double> *z_dev, int nnodes,
                       const cx<double> *V, int64_t strideV, const cx<double> *X, cx<double> *R, int64_t stride,
                       int64_t b);

@@ -193,6 +193,7 @@ struct rfdd_handle {
   cudaStream_t st = nullptr;
   bool own_stream = false;
   // device copies
+  Buf amsplit;  // double-FP32 split of the pencil values (mixed-precision residuals)
   Buf rowptr, col, aval, mval, off_dev, sidx_dev, sidx_off_dev, posmap, iperm_dev, status;
   DevPencil P;
   DevDD dd;
@@ -495,6 +496,8 @@ void do_upload(rfdd_handle *h) {
   h->P.col = h->col.as<int32_t>();
   h->P.a = h->aval.as<double>();
   h->P.m = h->mval.as<double>();
+  h->amsplit.alloc((size_t)std::max<int64_t>(1, h->nnz) * sizeof(float4));
+  split_pencil(st, h->P, h->amsplit.as<float4>());
   h->dd.p = p;
   h->dd.dsum = dsum;
   h->dd.s = s;
@@ -841,9 +844,18 @@ int refined_solve(rfdd_handle *h, const double *V, cx<double> *X, int64_t m, dou
   nx.alloc((size_t)nc * m * sizeof(double));
   std::vector<double> hr(nc * m), hx(nc * m);
   int steps = 0;
+  Buf Xs;
+  const bool df = std::is_same<Tf, cx<float>>::value;  // mixed solve: double-FP32 residual products
+  if (df) Xs.alloc((size_t)nc * n * m * sizeof(float4));
   for (int it = 0; it <= irmax; ++it) {
-    shifted_residual(st, h->P, h->z_dev.as<cx<double>>(), nc, Vc.as<cx<double>>(), 0, X, Rr.as<cx<double>>(), n * m,
-                     m);
+    if (df) {
+      split_c64(st, X, Xs.as<float4>(), (int64_t)nc * n * m);
+      shifted_residual_df(st, h->P, h->z_dev.as<cx<double>>(), nc, Vc.as<cx<double>>(), 0, Xs.as<float4>(),
+                          Rr.as<cx<double>>(), n * m, m);
+    } else {
+      shifted_residual(st, h->P, h->z_dev.as<cx<double>>(), nc, Vc.as<cx<double>>(), 0, X, Rr.as<cx<double>>(),
+                       n * m, m);
+    }
     col_norms2_c64(st, Rr.as<cx<double>>(), n, m, nc, n * m, nr.as<double>());
     col_norms2_c64(st, X, n, m, nc, n * m, nx.as<double>());
     RFDD_CUDA(cudaMemcpyAsync(hr.data(), nr.p, hr.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -2171,7 +2183,7 @@ int rfdd_memory_estimate(const rfdd_handle *h, int32_t n_nodes, int64_t nev_gues
   size_t b = factor_bytes(h, n_nodes, scal);
   int64_t m = nev_guess + std::max<int64_t>((int64_t)std::ceil(h->opt.guard_frac * nev_guess), h->opt.min_guard);
   if (h->opt.m_align > 1) m = (m + h->opt.m_align - 1) / h->opt.m_align * h->opt.m_align;
-  b += (size_t)n_nodes * h->n * m * (sizeof(cx<double>) * 3 + scal * 2);  // completion blocks
+  b += (size_t)n_nodes * h->n * m * (sizeof(cx<double>) * 4 + scal * 2);  // completion blocks
   b += (size_t)h->s * h->s * sizeof(double);                               // Lanczos basis
   *bytes = b;
   return RFDD_OK;
