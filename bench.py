@@ -165,6 +165,22 @@ def run_reference(args, rank, world):
 
 
 # --------------------------------------------------------------------------------------------
+# multi-rank aggregation (one process per GPU, independent replicas)
+# --------------------------------------------------------------------------------------------
+
+def reduce_over_ranks(ms: float, units: float, dist, device) -> tuple[float, float]:
+    """Whole-job figures of N replicas: the max over ranks of the timed milliseconds and the sum
+    over ranks of the units (eigenpairs) processed.  ``dist`` is torch.distributed with an
+    initialised process group (nccl on the GPU, gloo in the CPU tests)."""
+    import torch
+    mx = torch.tensor([ms], dtype=torch.float64, device=device)
+    sm = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[0])
+
+
+# --------------------------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------------------------
 
@@ -229,12 +245,7 @@ def run_ours(args, rank, world, local_rank):
     R.rfdd_profile(False)
     good = sum(good_per_step)
     if dist:
-        t = torch.tensor([ms_total, good], dtype=torch.float64, device="cuda")
-        mx = t.clone()
-        dist.all_reduce(mx[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        ms_total = float(mx[0])
-        good = float(t[1])
+        ms_total, good = reduce_over_ranks(ms_total, good, dist, "cuda")
     value = good / (ms_total / 1e3)
 
     # end to end through the C ABI with host buffers (rank-local)
@@ -252,7 +263,11 @@ def run_ours(args, rank, world, local_rank):
                w.M.val.nbytes + w.part.nbytes)
         d2h = ev2.nbytes + X2.nbytes + rs2.nbytes
         del r2, h2
-    e2e_value = good2 * world / statistics.median(e2e_times)
+    e2e_s, e2e_good = statistics.median(e2e_times), float(good2)
+    if dist:
+        e2e_ms, e2e_good = reduce_over_ranks(e2e_s * 1e3, e2e_good, dist, "cuda")
+        e2e_s = e2e_ms / 1e3
+    e2e_value = e2e_good / e2e_s
 
     if rank != 0:
         return
