@@ -1079,6 +1079,7 @@ static void trsm_block_inverse(cudaStream_t st, const std::vector<SolveItem<T>> 
     const int b = upper ? nblk - 1 - step : step;
     const int K0 = b * nbo;
     std::vector<GemmItem<T>> g1, g2;
+    std::vector<TcPackedA> p1, p2;
     std::vector<CopyItem<T>> cp;
     for (size_t i = 0; i < items.size(); ++i) {
       const SolveItem<T> &it = items[i];
@@ -1087,16 +1088,33 @@ static void trsm_block_inverse(cudaStream_t st, const std::vector<SolveItem<T>> 
       const T *inv = (upper ? it.Uinv : it.Linv) + (int64_t)b * nbo * nbo;
       T *xb = it.X + (int64_t)K0 * it.ldx, *t = tmp + toff[i];
       g1.push_back({inv, xb, t, w, it.ncols, w, nbo, it.ldx, it.ncols});
+      const float *ih = upper ? it.Uinvp_hi : it.Linvp_hi, *il = upper ? it.Uinvp_lo : it.Linvp_lo;
+      const int64_t bf = tc_packed_a_floats(nbo, nbo);
+      p1.push_back(ih ? TcPackedA{ih + b * bf, il + b * bf, tc_packed_a_ktiles(nbo)} : TcPackedA{});
       cp.push_back({t, xb, it.ncols, it.ldx, w, it.ncols});
-      if (!upper && it.n - K0 - w > 0)  // rows below: X[K0+w:] -= L[K0+w:, K0:K0+w] X_b
+      if (!upper && it.n - K0 - w > 0) {  // rows below: X[K0+w:] -= L[K0+w:, K0:K0+w] X_b
         g2.push_back({it.LU + (int64_t)(K0 + w) * it.ld + K0, xb, it.X + (int64_t)(K0 + w) * it.ldx, it.n - K0 - w,
                       it.ncols, w, it.ld, it.ldx, it.ldx});
-      if (upper && K0 > 0)  // rows above: X[0:K0] -= U[0:K0, K0:K0+w] X_b
+        p2.push_back(it.LUp_hi ? tc_packed_view(it.LUp_hi, it.LUp_lo, it.n, K0 + w, K0) : TcPackedA{});
+      }
+      if (upper && K0 > 0) {  // rows above: X[0:K0] -= U[0:K0, K0:K0+w] X_b
         g2.push_back({it.LU + K0, xb, it.X, K0, it.ncols, w, it.ld, it.ldx, it.ldx});
+        p2.push_back(it.LUp_hi ? tc_packed_view(it.LUp_hi, it.LUp_lo, it.n, 0, K0) : TcPackedA{});
+      }
     }
-    gemm_batched<T>(st, g1, false, false, 1.0, 0.0);
-    copy_rows_batched<T>(st, cp);
-    gemm_batched<T>(st, g2, false, false, -1.0, 1.0);
+    bool use_pa = false;
+    if constexpr (std::is_same<T, cx<float>>::value) use_pa = tc_enabled();
+    if (use_pa) {
+      if constexpr (std::is_same<T, cx<float>>::value) {
+        tc_gemm_complex_pa(st, g1, p1, 1.0, 0.0);
+        copy_rows_batched<T>(st, cp);
+        tc_gemm_complex_pa(st, g2, p2, -1.0, 1.0);
+      }
+    } else {
+      gemm_batched<T>(st, g1, false, false, 1.0, 0.0);
+      copy_rows_batched<T>(st, cp);
+      gemm_batched<T>(st, g2, false, false, -1.0, 1.0);
+    }
   }
   RFDD_CUDA(cudaFreeAsync(tmp, st));
 }

@@ -68,6 +68,12 @@ struct SolveItem {
   int ldx, ncols;
   const T *Linv = nullptr, *Uinv = nullptr;
   int nbi = 0;
+  // Optional tensor-core tile copies (complex FP32 only, see tc_pack_a_batched): of the n x n
+  // factor (LUp, packed as an n x n operand) and of the inverse blocks (one nbi x nbi operand per
+  // block, block b at Linvp/Uinvp + b * tc_packed_a_floats(nbi, nbi)).  Used as the A operands of
+  // the block-inverse solves instead of packing the same factor again on every solve.
+  const float *LUp_hi = nullptr, *LUp_lo = nullptr;
+  const float *Linvp_hi = nullptr, *Linvp_lo = nullptr, *Uinvp_hi = nullptr, *Uinvp_lo = nullptr;
 };
 // Elements of the inverse-block storage of one n x n factor.
 inline int64_t block_inverse_elems(int64_t n, int nbi) { return (int64_t)((n + nbi - 1) / nbi) * nbi * nbi; }

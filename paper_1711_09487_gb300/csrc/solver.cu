@@ -16,6 +16,7 @@
 #include <mutex>
 #include <numeric>
 #include <thread>
+#include <tuple>
 
 #include "dense.cuh"
 #include "eig.cuh"
@@ -205,6 +206,13 @@ struct rfdd_handle {
   Buf BLinv, BUinv, SLinv, SUinv;
   std::vector<int64_t> binvoff;  // (node, subdomain) -> offset into BLinv / BUinv
   int64_t sinv_elems = 0;        // per node in SLinv / SUinv
+  // Mixed solve: tensor-core tile copies (TF32 hi/lo) of the factor operands the solves multiply
+  // by, packed once per factorisation.  Per B factor (node, subdomain) and per S factor (node):
+  // the leading LU, the inverse diagonal blocks of L and of U, and (B only) the border blocks L21
+  // and U12.  Float offsets of each hi array into Pk; its lo array follows it.
+  Buf Pk;
+  struct PkOff { int64_t lu = -1, li = -1, ui = -1, l21 = -1, u12 = -1; };
+  std::vector<PkOff> pkB, pkS;
   std::vector<int64_t> boff, pivBoff;
   bool have_factors = false;
   double alpha = 0, beta = 0;
@@ -528,9 +536,18 @@ size_t factor_bytes(const rfdd_handle *h, int nc, size_t scal) {
   size_t inv = (size_t)block_inverse_elems(h->s, NBO);  // inverted diagonal blocks of L and U
   for (int j = 0; j < h->p; ++j) inv += (size_t)block_inverse_elems(h->d[j], NBO);
   b += 2 * (size_t)nc * inv * scal;
+  if (scal == sizeof(cx<float>)) {  // packed tensor-core copies of the solve operands (hi + lo)
+    size_t pk = (size_t)h->s * h->s + 2 * (size_t)block_inverse_elems(h->s, NBO);
+    for (int j = 0; j < h->p; ++j)
+      pk += (size_t)h->D[j] * h->D[j] - (size_t)(h->D[j] - h->d[j]) * (h->D[j] - h->d[j]) +
+            2 * (size_t)block_inverse_elems(h->d[j], NBO);
+    b += (size_t)nc * pk * 2 * scal;
+  }
   b += (size_t)nc * (h->dsum + h->s) * sizeof(int);
   return b;
 }
+
+void pack_factor_operands(rfdd_handle *h);
 
 template <typename Tf>
 void factor_impl(rfdd_handle *h) {
@@ -642,8 +659,26 @@ void factor_impl(rfdd_handle *h) {
     }
     lu_block_inverses<Tf>(st, fi, NBO, li, ui);
   }
+  if constexpr (std::is_same<Tf, cx<float>>::value) {
+    if (tc_enabled()) pack_factor_operands(h);
+  }
   sync_status(h, "factor");
   h->have_factors = true;
+}
+
+// packed (hi, lo) pointers of one operand in h->Pk; (nullptr, nullptr) when absent
+std::pair<const float *, const float *> pk_ptrs(const rfdd_handle *h, int64_t off, int64_t floats) {
+  if (off < 0 || !h->Pk.p) return {nullptr, nullptr};
+  const float *hi = h->Pk.as<float>() + off;
+  return {hi, hi + floats};
+}
+template <typename Tf>
+void attach_packed(const rfdd_handle *h, SolveItem<Tf> &x, const rfdd_handle::PkOff &o, int64_t n) {
+  if (!h->Pk.p) return;
+  const int64_t nblk = (n + NBO - 1) / NBO, bf = tc_packed_a_floats(NBO, NBO);
+  std::tie(x.LUp_hi, x.LUp_lo) = pk_ptrs(h, o.lu, tc_packed_a_floats(n, n));
+  std::tie(x.Linvp_hi, x.Linvp_lo) = pk_ptrs(h, o.li, nblk * bf);
+  std::tie(x.Uinvp_hi, x.Uinvp_lo) = pk_ptrs(h, o.ui, nblk * bf);
 }
 
 // the inverted diagonal blocks of factor (node l, subdomain j), when present
@@ -654,6 +689,70 @@ void attach_binv(const rfdd_handle *h, SolveItem<Tf> &x, int l, int j) {
   x.Linv = h->BLinv.as<Tf>() + o;
   x.Uinv = h->BUinv.as<Tf>() + o;
   x.nbi = NBO;
+  if (!h->pkB.empty()) attach_packed(h, x, h->pkB[(size_t)l * h->p + j], h->d[j]);
+}
+
+// Mixed solve: pack the factor operands of the later solves once (see rfdd_handle::Pk)
+void pack_factor_operands(rfdd_handle *h) {
+  cudaStream_t st = h->st;
+  const int nc = h->nnodes, p = h->p;
+  const int64_t s = h->s, bf = tc_packed_a_floats(NBO, NBO);
+  h->pkB.assign((size_t)nc * p, {});
+  h->pkS.assign((size_t)nc, {});
+  int64_t tot = 0;
+  auto take = [&](int64_t floats) {
+    const int64_t o = tot;
+    tot += 2 * floats;
+    return o;
+  };
+  for (int l = 0; l < nc; ++l) {
+    for (int j = 0; j < p; ++j) {
+      const int64_t dj = h->d[j], sj = h->D[j] - dj, nblk = (dj + NBO - 1) / NBO;
+      auto &o = h->pkB[(size_t)l * p + j];
+      o.lu = take(tc_packed_a_floats(dj, dj));
+      o.li = take(nblk * bf);
+      o.ui = take(nblk * bf);
+      if (sj > 0) {
+        o.l21 = take(tc_packed_a_floats(sj, dj));
+        o.u12 = take(tc_packed_a_floats(dj, sj));
+      }
+    }
+    auto &o = h->pkS[l];
+    const int64_t nblk = (s + NBO - 1) / NBO;
+    o.lu = take(tc_packed_a_floats(s, s));
+    o.li = take(nblk * bf);
+    o.ui = take(nblk * bf);
+  }
+  h->Pk.alloc((size_t)tot * sizeof(float));
+  float *P = h->Pk.as<float>();
+  std::vector<TcPackJob> jobs;
+  auto job = [&](const cx<float> *A, int64_t lda, int64_t m, int64_t k, int64_t off) {
+    if (off < 0 || m <= 0 || k <= 0) return;
+    jobs.push_back({A, lda, m, k, P + off, P + off + tc_packed_a_floats(m, k)});
+  };
+  auto blocks = [&](const cx<float> *inv, int64_t n, int64_t off) {
+    const int64_t nblk = (n + NBO - 1) / NBO;
+    for (int64_t b = 0; b < nblk; ++b)
+      jobs.push_back({inv + b * NBO * NBO, NBO, NBO, NBO, P + off + b * bf, P + off + nblk * bf + b * bf});
+  };
+  cx<float> *base = h->fac.as<cx<float>>();
+  for (int l = 0; l < nc; ++l) {
+    for (int j = 0; j < p; ++j) {
+      const int64_t dj = h->d[j], Dj = h->D[j], sj = Dj - dj;
+      const auto &o = h->pkB[(size_t)l * p + j];
+      const cx<float> *A = base + h->boff[(size_t)l * p + j];
+      job(A, Dj, dj, dj, o.lu);
+      job(A + dj * Dj, Dj, sj, dj, o.l21);
+      job(A + dj, Dj, dj, sj, o.u12);
+      blocks(h->BLinv.as<cx<float>>() + h->binvoff[(size_t)l * p + j], dj, o.li);
+      blocks(h->BUinv.as<cx<float>>() + h->binvoff[(size_t)l * p + j], dj, o.ui);
+    }
+    const auto &o = h->pkS[l];
+    job(h->Sfac.as<cx<float>>() + (int64_t)l * s * s, s, s, s, o.lu);
+    blocks(h->SLinv.as<cx<float>>() + (int64_t)l * h->sinv_elems, s, o.li);
+    blocks(h->SUinv.as<cx<float>>() + (int64_t)l * h->sinv_elems, s, o.ui);
+  }
+  tc_pack_a_batched(st, jobs);
 }
 
 // B_j(z_l) solves on a tall block F (n x m per node, stride fs): interior rows only
@@ -694,6 +793,7 @@ void solve_S(rfdd_handle *h, Tf *G, int64_t ldg, int64_t gs, int64_t m, const st
       x.Linv = h->SLinv.as<Tf>() + (int64_t)l * h->sinv_elems;
       x.Uinv = h->SUinv.as<Tf>() + (int64_t)l * h->sinv_elems;
       x.nbi = NBO;
+      if (!h->pkS.empty()) attach_packed(h, x, h->pkS[l], h->s);
     }
     it.push_back(x);
   }
@@ -725,6 +825,19 @@ void filter_impl(rfdd_handle *h, const double *X, double *W, int64_t b, double s
   real_to_complex<Tf>(h->st, X, rhs.as<Tf>(), s * b, nc, s * b);
   solve_S<Tf>(h, rhs.as<Tf>(), b, s * b, b, all_nodes(h));
   weighted_real_sum<Tf>(h->st, rhs.as<Tf>(), s * b, h->w_dev.as<cx<double>>(), nc, scale, W, s * b);
+}
+
+// a border product of the DD solve, with the packed border block when there is one
+template <typename Tf>
+void border_gemm(cudaStream_t st, const std::vector<GemmItem<Tf>> &g, const std::vector<TcPackedA> &pa, double alpha,
+                 double beta) {
+  if constexpr (std::is_same<Tf, cx<float>>::value) {
+    if (tc_enabled()) {
+      tc_gemm_complex_pa(st, g, pa, alpha, beta);
+      return;
+    }
+  }
+  gemm_batched<Tf>(st, g, false, false, alpha, beta);
 }
 
 // DD resolvent (Eq. inv_dd2) in the factor precision for all nodes:
@@ -772,6 +885,7 @@ void dd_solve(rfdd_handle *h, const cx<double> *R, int64_t strideR, cx<double> *
   // g -= sum_j L21_j w_j  (s_j x d_j times d_j x m, then an ordered scatter)
   {
     std::vector<GemmItem<Tf>> g;
+    std::vector<TcPackedA> pa;
     for (int l = 0; l < nc; ++l)
       for (int j = 0; j < p; ++j) {
         const int sj = (int)(h->sidx_off[j + 1] - h->sidx_off[j]);
@@ -779,8 +893,11 @@ void dd_solve(rfdd_handle *h, const cx<double> *R, int64_t strideR, cx<double> *
         const int64_t Dj = h->D[j], dj = h->d[j];
         g.push_back({base + h->boff[(size_t)l * p + j] + dj * Dj, f + (int64_t)l * fs + h->off[j] * m,
                      ht + l * hs + (int64_t)j * smax * m, sj, (int)m, (int)dj, (int)Dj, (int)m, (int)m});
+        const auto pp = h->pkB.empty() ? std::pair<const float *, const float *>{nullptr, nullptr}
+                                       : pk_ptrs(h, h->pkB[(size_t)l * p + j].l21, tc_packed_a_floats(sj, dj));
+        pa.push_back(TcPackedA{pp.first, pp.second, tc_packed_a_ktiles(dj)});
       }
-    gemm_batched<Tf>(st, g, false, false, 1.0, 0.0);
+    border_gemm<Tf>(st, g, pa, 1.0, 0.0);
     for (int j = 0; j < p; ++j) {
       const int sj = (int)(h->sidx_off[j + 1] - h->sidx_off[j]);
       scatter_sub_iface<Tf>(st, h->dd.sidx + h->sidx_off[j], sj, m, ht + (int64_t)j * smax * m, hs, f + dsum * m, fs,
@@ -797,14 +914,19 @@ void dd_solve(rfdd_handle *h, const cx<double> *R, int64_t strideR, cx<double> *
       gather_iface<Tf>(st, h->dd.sidx + h->sidx_off[j], sj, m, f + dsum * m, fs, ht + (int64_t)j * smax * m, hs, nc);
     }
     std::vector<GemmItem<Tf>> g;
+    std::vector<TcPackedA> pa;
     std::vector<SolveItem<Tf>> it;
     for (int l = 0; l < nc; ++l)
       for (int j = 0; j < p; ++j) {
         const int sj = (int)(h->sidx_off[j + 1] - h->sidx_off[j]);
         const int64_t Dj = h->D[j], dj = h->d[j];
-        if (sj > 0)
+        if (sj > 0) {
           g.push_back({base + h->boff[(size_t)l * p + j] + dj, ht + l * hs + (int64_t)j * smax * m,
                        f + (int64_t)l * fs + h->off[j] * m, (int)dj, (int)m, sj, (int)Dj, (int)m, (int)m});
+          const auto pp = h->pkB.empty() ? std::pair<const float *, const float *>{nullptr, nullptr}
+                                         : pk_ptrs(h, h->pkB[(size_t)l * p + j].u12, tc_packed_a_floats(dj, sj));
+          pa.push_back(TcPackedA{pp.first, pp.second, tc_packed_a_ktiles(sj)});
+        }
         SolveItem<Tf> x;
         x.LU = base + h->boff[(size_t)l * p + j];
         x.piv = nullptr;
@@ -816,7 +938,7 @@ void dd_solve(rfdd_handle *h, const cx<double> *R, int64_t strideR, cx<double> *
         attach_binv(h, x, l, j);
         it.push_back(x);
       }
-    gemm_batched<Tf>(st, g, false, false, -1.0, 1.0);
+    border_gemm<Tf>(st, g, pa, -1.0, 1.0);
     lap.mark("border U12");
     trsm_upper<Tf>(st, it, NBO);
   }
@@ -1611,6 +1733,9 @@ void factor(rfdd_handle *h) {
   h->BUinv.release();
   h->SLinv.release();
   h->SUinv.release();
+  h->Pk.release();
+  h->pkB.clear();
+  h->pkS.clear();
   if (is_mixed(h)) factor_impl<cx<float>>(h);
   else factor_impl<cx<double>>(h);
 }
@@ -1887,6 +2012,7 @@ int rfdd_shifted_solve(rfdd_handle *h, int32_t node, int32_t which, int32_t j, i
           si[0].Linv = h->SLinv.as<Tf>() + (int64_t)node * h->sinv_elems;
           si[0].Uinv = h->SUinv.as<Tf>() + (int64_t)node * h->sinv_elems;
           si[0].nbi = NBO;
+          if (!h->pkS.empty()) attach_packed(h, si[0], h->pkS[node], h->s);
         }
       }
       si[0].X = t.as<Tf>();

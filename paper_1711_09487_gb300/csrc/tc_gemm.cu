@@ -48,6 +48,7 @@ struct TcItem {
   float *C;
   long long ldc;  // real leading dimension of C
   int m, n2, nkt, mtc, ntc, tile0;  // tile0: first global tile index of this item
+  long long amts;  // A tiles between consecutive 128-row tiles (0: nkt, a packed A of its own)
 };
 constexpr int TC_MAXB = 64;
 struct TcBatchP {
@@ -176,7 +177,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
       for (int tile = blockIdx.x; tile < b.total_tiles && !abort_s; tile += gridDim.x) {
         const TcItem &it = b.it[find_item(b, tile)];
         const int local = tile - it.tile0, mt = local / it.ntc, nt = local % it.ntc;
-        const float *Ahi = it.Ahi + (long long)mt * it.nkt * A_TILE, *Alo = it.Alo + (long long)mt * it.nkt * A_TILE;
+        const long long ams = it.amts ? it.amts : it.nkt;
+        const float *Ahi = it.Ahi + (long long)mt * ams * A_TILE, *Alo = it.Alo + (long long)mt * ams * A_TILE;
         const float *Bhi = it.Bhi + (long long)nt * it.nkt * B_TILE, *Blo = it.Blo + (long long)nt * it.nkt * B_TILE;
         for (int kt = 0; kt < it.nkt; ++kt, ++g) {
           const int s = (int)(g % TC_STAGES);
@@ -431,7 +433,8 @@ int tc_take_error() {
 }
 
 template <bool CPLX, typename T>
-static void tc_gemm_run(cudaStream_t st, const std::vector<GemmItem<T>> &items, double alpha, double beta) {
+static void tc_gemm_run(cudaStream_t st, const std::vector<GemmItem<T>> &items, double alpha, double beta,
+                        const std::vector<TcPackedA> *pre = nullptr) {
   constexpr int F = CPLX ? 2 : 1;  // real columns / K entries per element
   if (!g_tc_attr_done) {
     RFDD_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
@@ -452,8 +455,9 @@ static void tc_gemm_run(cudaStream_t st, const std::vector<GemmItem<T>> &items, 
     for (int i = 0; i < cnt; ++i) {
       const auto &g = items[s0 + i];
       const int mtc = ceil_div(g.m, TC_BM), ntc = ceil_div((int64_t)F * g.n, TC_BN), nkt = ceil_div((int64_t)F * g.k, TC_BK);
+      const bool packed = pre && (*pre)[s0 + i].hi;
       offA[i] = total;
-      total += (size_t)mtc * nkt * A_TILE * 2;
+      if (!packed) total += (size_t)mtc * nkt * A_TILE * 2;
       offB[i] = total;
       total += (size_t)ntc * nkt * B_TILE * 2;
       mtmax = std::max(mtmax, mtc);
@@ -468,20 +472,29 @@ static void tc_gemm_run(cudaStream_t st, const std::vector<GemmItem<T>> &items, 
     for (int i = 0; i < cnt; ++i) {
       const auto &g = items[s0 + i];
       const int mtc = ceil_div(g.m, TC_BM), ntc = ceil_div((int64_t)F * g.n, TC_BN), nkt = ceil_div((int64_t)F * g.k, TC_BK);
-      float *Ah = ws + offA[i], *Al = Ah + (size_t)mtc * nkt * A_TILE;
+      const bool packed = pre && (*pre)[s0 + i].hi;
+      const float *Ah = packed ? (*pre)[s0 + i].hi : ws + offA[i];
+      const float *Al = packed ? (*pre)[s0 + i].lo : ws + offA[i] + (size_t)mtc * nkt * A_TILE;
       float *Bh = ws + offB[i], *Bl = Bh + (size_t)ntc * nkt * B_TILE;
-      pa.it[i] = {reinterpret_cast<const float *>(g.A), g.lda, g.m, g.n, g.k, Ah, Al, mtc, ntc, nkt};
+      // a pre-packed A is not packed again (mtc = 0 gives its pack item no work)
+      pa.it[i] = {reinterpret_cast<const float *>(g.A), g.lda, g.m, g.n, g.k, const_cast<float *>(Ah),
+                  const_cast<float *>(Al), packed ? 0 : mtc, ntc, nkt};
       pbb.it[i] = {reinterpret_cast<const float *>(g.B), g.ldb, g.m, g.n, g.k, Bh, Bl, mtc, ntc, nkt};
-      tb.it[i] = {Ah, Al, Bh, Bl, reinterpret_cast<float *>(g.C), (long long)F * g.ldc, g.m, F * g.n, nkt, mtc, ntc, tiles};
+      tb.it[i] = {Ah, Al, Bh, Bl, reinterpret_cast<float *>(g.C), (long long)F * g.ldc, g.m, F * g.n, nkt, mtc, ntc, tiles,
+                  packed ? (long long)(*pre)[s0 + i].mt_stride : 0ll};
       tiles += mtc * ntc;
     }
     tb.count = cnt;
     tb.total_tiles = tiles;
+    bool any_a = false;
+    for (int i = 0; i < cnt; ++i) any_a |= pa.it[i].mtc > 0;
     const dim3 ga((unsigned)std::min<long long>(ceil_div(achunks, 256), 4096), cnt);
     const dim3 gb((unsigned)std::min<long long>(ceil_div(bchunks, 256), 4096), cnt);
     if (CPLX) {
-      pack_a_kernel<<<ga, 256, 0, st>>>(pa);
-      RFDD_CHECK_LAUNCH();
+      if (any_a) {
+        pack_a_kernel<<<ga, 256, 0, st>>>(pa);
+        RFDD_CHECK_LAUNCH();
+      }
       pack_b_kernel<<<gb, 256, 0, st>>>(pbb);
       RFDD_CHECK_LAUNCH();
     } else {
@@ -512,6 +525,47 @@ static void tc_gemm_run(cudaStream_t st, const std::vector<GemmItem<T>> &items, 
 
 void tc_gemm_complex(cudaStream_t st, const std::vector<GemmItem<cx<float>>> &items, double alpha, double beta) {
   tc_gemm_run<true>(st, items, alpha, beta);
+}
+
+void tc_gemm_complex_pa(cudaStream_t st, const std::vector<GemmItem<cx<float>>> &items,
+                        const std::vector<TcPackedA> &pa, double alpha, double beta) {
+  RFDD_REQUIRE(pa.size() == items.size(), RFDD_EINVAL, "tc_gemm: one packed-A entry per item");
+  std::vector<GemmItem<cx<float>>> live;
+  std::vector<TcPackedA> lpa;
+  for (size_t i = 0; i < items.size(); ++i)
+    if (items[i].m > 0 && items[i].n > 0 && items[i].k > 0) {
+      live.push_back(items[i]);
+      lpa.push_back(pa[i]);
+    }
+  if (!live.empty()) tc_gemm_run<true>(st, live, alpha, beta, &lpa);
+}
+
+int64_t tc_packed_a_ktiles(int64_t k) { return ceil_div(2 * k, TC_BK); }
+int64_t tc_packed_a_floats(int64_t m, int64_t k) { return (int64_t)ceil_div(m, TC_BM) * tc_packed_a_ktiles(k) * A_TILE; }
+
+TcPackedA tc_packed_view(const float *hi, const float *lo, int64_t k_full, int64_t r0, int64_t c0) {
+  RFDD_REQUIRE(r0 % TC_BM == 0 && (2 * c0) % TC_BK == 0, RFDD_EINVAL, "packed view must start on a tile");
+  const int64_t kt = tc_packed_a_ktiles(k_full);
+  const int64_t off = ((r0 / TC_BM) * kt + (2 * c0) / TC_BK) * A_TILE;
+  return TcPackedA{hi + off, lo + off, kt};
+}
+
+void tc_pack_a_batched(cudaStream_t st, const std::vector<TcPackJob> &jobs) {
+  for (size_t s0 = 0; s0 < jobs.size(); s0 += TC_MAXB) {
+    const int cnt = (int)std::min<size_t>(TC_MAXB, jobs.size() - s0);
+    PackBatchP pa;
+    memset(&pa, 0, sizeof(pa));
+    long long achunks = 1;
+    for (int i = 0; i < cnt; ++i) {
+      const TcPackJob &j = jobs[s0 + i];
+      const int mtc = ceil_div(j.m, TC_BM), nkt = (int)tc_packed_a_ktiles(j.k);
+      pa.it[i] = {reinterpret_cast<const float *>(j.A), j.lda, (int)j.m, 0, (int)j.k, j.hi, j.lo,
+                  j.m > 0 && j.k > 0 ? mtc : 0, 0, nkt};
+      achunks = std::max(achunks, (long long)mtc * TC_BM * nkt * 8);
+    }
+    pack_a_kernel<<<dim3((unsigned)std::min<long long>(ceil_div(achunks, 256), 4096), cnt), 256, 0, st>>>(pa);
+    RFDD_CHECK_LAUNCH();
+  }
 }
 
 void tc_gemm_real(cudaStream_t st, const std::vector<GemmItem<float>> &items, double alpha, double beta) {

@@ -8,6 +8,29 @@ bool tc_enabled();  // false when the environment variable RFDD_TC is "0"
 void tc_gemm_complex(cudaStream_t st, const std::vector<GemmItem<cx<float>>> &items, double alpha, double beta);
 // C = beta*C + alpha*A*B for real FP32 items (same kernel, 3xTF32)
 void tc_gemm_real(cudaStream_t st, const std::vector<GemmItem<float>> &items, double alpha, double beta);
+// A operand already split into TF32 hi/lo and laid out in the kernel's tiles (tc_pack_a_batched):
+// tile (mt, kt) of the operand at hi/lo + (mt * mt_stride + kt) * tile size.  Lets a factor that
+// is multiplied many times (triangular-solve updates, border products) be packed once.
+struct TcPackedA {
+  const float *hi = nullptr, *lo = nullptr;
+  int64_t mt_stride = 0;
+};
+// items[i] uses pa[i] as its A operand when pa[i].hi is set (items[i].A is then not read)
+void tc_gemm_complex_pa(cudaStream_t st, const std::vector<GemmItem<cx<float>>> &items,
+                        const std::vector<TcPackedA> &pa, double alpha, double beta);
+// packing of complex m x k matrices (row-major, leading dimension lda) into hi/lo tile arrays
+// of tc_packed_a_floats(m, k) floats each (rows and K padded with zeros to whole tiles)
+struct TcPackJob {
+  const cx<float> *A;
+  int64_t lda, m, k;
+  float *hi, *lo;
+};
+int64_t tc_packed_a_ktiles(int64_t k);
+int64_t tc_packed_a_floats(int64_t m, int64_t k);
+void tc_pack_a_batched(cudaStream_t st, const std::vector<TcPackJob> &jobs);
+// the sub-matrix of a packed m x k_full operand starting at row r0 (a multiple of 128) and complex
+// column c0 (a multiple of 16)
+TcPackedA tc_packed_view(const float *hi, const float *lo, int64_t k_full, int64_t r0, int64_t c0);
 // returns and clears the device-side error flags of the tensor-core kernels (DS_* bits)
 int tc_take_error();
 // allocation-free variant: packed operands in a static device array (m, n <= 1024, k <= 128)
