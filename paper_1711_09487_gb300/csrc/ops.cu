@@ -28,9 +28,9 @@ struct Shift<double> {
 // real SpMM, warp per row, lanes over columns
 // --------------------------------------------------------------------------------------
 __global__ void spmm_f64_kernel(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
-                                const double *__restrict__ av, const double *__restrict__ mv, int64_t r0, int64_t r1,
-                                int64_t qlo, int64_t qhi, double ca, double cm, const double *__restrict__ X,
-                                int64_t ldx, double *__restrict__ Y, int64_t ldy, int64_t b, int acc) {
+                                const double *__restrict__ vals, int64_t r0, int64_t r1, int64_t qlo, int64_t qhi,
+                                const double *__restrict__ X, int64_t ldx, double *__restrict__ Y, int64_t ldy,
+                                int64_t b, int acc) {
   const int64_t r = r0 + ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
   const int lane = threadIdx.x & 31;
   if (r >= r1) return;
@@ -42,8 +42,7 @@ __global__ void spmm_f64_kernel(const int64_t *__restrict__ rp, const int32_t *_
       for (int64_t e = e0; e < e1; ++e) {
         const int64_t q = col[e];
         if (q < qlo || q >= qhi) continue;
-        const double v = ca * av[e] + cm * mv[e];
-        s = fma(v, X[(q - qlo) * ldx + c], s);
+        s = fma(vals[e], X[(q - qlo) * ldx + c], s);
       }
     if (c < b) {
       double *y = Y + (r - r0) * ldy + c;
@@ -51,14 +50,33 @@ __global__ void spmm_f64_kernel(const int64_t *__restrict__ rp, const int32_t *_
     }
   }
 }
-
+__global__ void combine_values_kernel(const double *__restrict__ a, const double *__restrict__ m, double ca, double cm,
+                                      int64_t nnz, double *__restrict__ out) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = ca * a[e] + cm * m[e];
+}
 void spmm_f64(cudaStream_t st, const DevPencil &P, int64_t r0, int64_t r1, int64_t qlo, int64_t qhi, double ca,
               double cm, const double *X, int64_t ldx, double *Y, int64_t ldy, int64_t b, bool accumulate) {
   if (r1 <= r0 || b <= 0) return;
+  // the coefficient ca*a + cm*m of each entry, formed once (FP64 is the bound of this kernel)
+  const double *vals = nullptr;
+  double *comb = nullptr;
+  if (ca == 1.0 && cm == 0.0) {
+    vals = P.a;
+  } else if (ca == 0.0 && cm == 1.0) {
+    vals = P.m;
+  } else {
+    RFDD_CUDA(cudaMallocAsync((void **)&comb, (size_t)std::max<int64_t>(1, P.nnz) * sizeof(double), st));
+    combine_values_kernel<<<std::min(4096, ceil_div(std::max<int64_t>(1, P.nnz), 256)), 256, 0, st>>>(P.a, P.m, ca, cm,
+                                                                                                    P.nnz, comb);
+    RFDD_CHECK_LAUNCH();
+    vals = comb;
+  }
   const int64_t warps = r1 - r0;
-  spmm_f64_kernel<<<ceil_div(warps * 32, 256), 256, 0, st>>>(P.rowptr, P.col, P.a, P.m, r0, r1, qlo, qhi, ca, cm, X,
-                                                               ldx, Y, ldy, b, accumulate ? 1 : 0);
+  spmm_f64_kernel<<<ceil_div(warps * 32, 256), 256, 0, st>>>(P.rowptr, P.col, vals, r0, r1, qlo, qhi, X, ldx, Y, ldy,
+                                                               b, accumulate ? 1 : 0);
   RFDD_CHECK_LAUNCH();
+  if (comb) RFDD_CUDA(cudaFreeAsync(comb, st));
 }
 
 // --------------------------------------------------------------------------------------
