@@ -72,7 +72,9 @@ typedef struct {
   int ir_max;           /* FP64 iterative-refinement steps per shifted solve; default 10 */
   uint64_t seed;        /* counter-based RNG seed for start blocks; default 1 */
   size_t mem_budget;    /* device bytes one solve may hold; 0 = no limit */
-  void *stream;         /* cudaStream_t to run on; NULL = a stream owned by the handle */
+  void *stream;         /* cudaStream_t to run on (must stay valid until rfdd_destroy: the
+                           handle's device buffers are stream-ordered allocations on it);
+                           NULL = a stream owned by the handle */
   double guard_frac;    /* completion block m = n_in + max(ceil(guard_frac n_in), min_guard) */
   int min_guard;        /* (defaults 0.3 and 8) */
   int keep_schur;       /* nonzero: keep an unfactored copy of every S(zeta_l) (for checks) */

@@ -75,26 +75,56 @@ bool log_on() {
 // ------------------------------------------------------------------------------------
 // device buffers
 // ------------------------------------------------------------------------------------
+// Device buffers.  Inside an AllocScope (every entry point that works on a handle's stream)
+// they come from the stream-ordered pool on that stream: allocation and release are ordered
+// with the stream's work and never synchronise the device, as cudaFree would between the many
+// short-lived workspaces of a solve.  Outside a scope, and for buffers that must outlive the
+// handle's stream (results), plain cudaMalloc / cudaFree.
+thread_local cudaStream_t g_alloc_stream = nullptr;
+struct AllocScope {
+  cudaStream_t prev;
+  explicit AllocScope(cudaStream_t s) : prev(g_alloc_stream) { g_alloc_stream = s; }
+  ~AllocScope() { g_alloc_stream = prev; }
+  AllocScope(const AllocScope &) = delete;
+  AllocScope &operator=(const AllocScope &) = delete;
+};
+
 struct Buf {
   void *p = nullptr;
   size_t bytes = 0;
+  cudaStream_t st_ = nullptr;
+  bool async_ = false;
+  bool sync_only = false;
   Buf() = default;
+  explicit Buf(bool sync) : sync_only(sync) {}
   Buf(const Buf &) = delete;
   Buf &operator=(const Buf &) = delete;
   ~Buf() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    if (p) {
+      if (async_) cudaFreeAsync(p, st_);
+      else cudaFree(p);
+    }
     p = nullptr;
     bytes = 0;
+    async_ = false;
   }
   void alloc(size_t b) {
     release();
     if (b == 0) b = 16;
-    cudaError_t e = cudaMalloc(&p, b);
+    cudaError_t e;
+    if (g_alloc_stream && !sync_only) {
+      e = cudaMallocAsync(&p, b, g_alloc_stream);
+      async_ = e == cudaSuccess;
+      st_ = g_alloc_stream;
+    } else {
+      e = cudaMalloc(&p, b);
+    }
     if (e != cudaSuccess) {
       cudaGetLastError();
       p = nullptr;
-      throw Error(RFDD_ENOMEM, "cudaMalloc of " + std::to_string(b) + " bytes failed: " + cudaGetErrorString(e));
+      async_ = false;
+      throw Error(RFDD_ENOMEM, "device allocation of " + std::to_string(b) + " bytes failed: " + cudaGetErrorString(e));
     }
     bytes = b;
   }
@@ -104,6 +134,23 @@ struct Buf {
   template <typename T>
   T *as() const { return reinterpret_cast<T *>(p); }
 };
+
+// Keep freed pool memory for reuse instead of returning it to the driver at every stream
+// synchronisation (once per device; affects this process's default pool only).
+void keep_pool_memory() {
+  static std::mutex mu;
+  static std::vector<int> done;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  std::lock_guard<std::mutex> lk(mu);
+  if (std::find(done.begin(), done.end(), dev) != done.end()) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  done.push_back(dev);
+}
 
 template <typename T>
 void upload(Buf &b, const std::vector<T> &v, cudaStream_t st) {
@@ -170,7 +217,7 @@ struct rfdd_result {
   std::vector<double> evals, resid, pre_evals;
   std::vector<double> evecs_host;  // filled on demand
   bool host_ready = false;
-  Buf evecs, evals_dev, resid_dev;
+  Buf evecs{true}, evals_dev{true}, resid_dev{true};  // outlive the handle's stream
   rfdd_info info{};
   std::atomic<int> ready{1};
   std::thread worker;
@@ -1890,6 +1937,8 @@ int rfdd_setup(const rfdd_csr *A, const rfdd_csr *M, const int32_t *part, int32_
       RFDD_CUDA(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking));
       h->own_stream = true;
     }
+    keep_pool_memory();
+    AllocScope scope(h->st);
     do_upload(h);
   });
   if (rc != RFDD_OK) {
@@ -1921,6 +1970,7 @@ void rfdd_destroy(rfdd_handle *h) {
 int rfdd_factor(rfdd_handle *h, int32_t n_nodes, const double *z, const double *w) {
   if (!h || !z || !w || n_nodes < 1) return RFDD_EINVAL;
   return guarded([&] {
+    AllocScope scope(h->st);
     set_nodes(h, n_nodes, z, w);
     factor(h);
   });
@@ -1929,6 +1979,7 @@ int rfdd_factor(rfdd_handle *h, int32_t n_nodes, const double *z, const double *
 int rfdd_schur_copy(rfdd_handle *h, int32_t node, double *S_out) {
   if (!h || !S_out) return RFDD_EINVAL;
   return guarded([&] {
+    AllocScope scope(h->st);
     RFDD_REQUIRE(h->have_factors && h->opt.keep_schur, RFDD_ESTATE, "schur_copy needs keep_schur and rfdd_factor");
     RFDD_REQUIRE(node >= 0 && node < h->nnodes, RFDD_EINVAL, "node out of range");
     const int64_t s = h->s;
@@ -1950,6 +2001,7 @@ int rfdd_shifted_solve(rfdd_handle *h, int32_t node, int32_t which, int32_t j, i
                        double *X) {
   if (!h || !R || !X || nrhs < 1) return RFDD_EINVAL;
   return guarded([&] {
+    AllocScope scope(h->st);
     RFDD_REQUIRE(h->have_factors, RFDD_ESTATE, "shifted_solve needs rfdd_factor");
     RFDD_REQUIRE(node >= 0 && node < h->nnodes, RFDD_EINVAL, "node out of range");
     cudaStream_t st = h->st;
@@ -2031,6 +2083,7 @@ int rfdd_shifted_solve(rfdd_handle *h, int32_t node, int32_t which, int32_t j, i
 int rfdd_filter_apply(rfdd_handle *h, int64_t b, const double *X, double *W) {
   if (!h || !X || !W || b < 1) return RFDD_EINVAL;
   return guarded([&] {
+    AllocScope scope(h->st);
     RFDD_REQUIRE(h->have_factors, RFDD_ESTATE, "filter_apply needs rfdd_factor");
     const int64_t s = h->s;
     Buf x, wv;
@@ -2047,6 +2100,7 @@ int rfdd_filter_apply(rfdd_handle *h, int64_t b, const double *X, double *W) {
 int rfdd_lanczos(rfdd_handle *h, int64_t cap, double *Q_out, int64_t *mu, double *traces, int32_t *nsteps) {
   if (!h) return RFDD_EINVAL;
   return guarded([&] {
+    AllocScope scope(h->st);
     RFDD_REQUIRE(h->have_factors, RFDD_ESTATE, "lanczos needs rfdd_factor");
     if (is_mixed(h)) lanczos_impl<cx<float>>(h);
     else lanczos_impl<cx<double>>(h);
@@ -2071,6 +2125,7 @@ int rfdd_lanczos(rfdd_handle *h, int64_t cap, double *Q_out, int64_t *mu, double
 int rfdd_interior(rfdd_handle *h, double sigma, int64_t cap, double *Z_out, int64_t *k, int64_t *kappa_out) {
   if (!h) return RFDD_EINVAL;
   return guarded([&] {
+    AllocScope scope(h->st);
     RFDD_REQUIRE(h->mu > 0, RFDD_ESTATE, "interior needs rfdd_lanczos");
     double sg = sigma;
     if (std::isnan(sg)) sg = h->have_interval ? 0.5 * (h->alpha + h->beta) : 0.0;
@@ -2092,6 +2147,7 @@ int rfdd_interior(rfdd_handle *h, double sigma, int64_t cap, double *Z_out, int6
 int rfdd_rayleigh_ritz(rfdd_handle *h, int64_t cap, double *theta_out, int64_t *k) {
   if (!h) return RFDD_EINVAL;
   return guarded([&] {
+    AllocScope scope(h->st);
     RFDD_REQUIRE(h->kz > 0, RFDD_ESTATE, "rayleigh_ritz needs rfdd_interior");
     const double a = h->have_interval ? h->alpha : -INFINITY, b = h->have_interval ? h->beta : INFINITY;
     if (is_mixed(h)) rr_on_Z<cx<float>>(h, a, b, nullptr);
@@ -2107,7 +2163,10 @@ int rfdd_solve(rfdd_handle *h, double alpha, double beta, int32_t n_nodes, rfdd_
   *out = nullptr;
   rfdd_result *r = new (std::nothrow) rfdd_result();
   if (!r) return RFDD_ENOMEM;
-  int rc = guarded([&] { run_solve(h, alpha, beta, n_nodes, r); });
+  int rc = guarded([&] {
+    AllocScope scope(h->st);
+    run_solve(h, alpha, beta, n_nodes, r);
+  });
   if (rc != RFDD_OK) {
     delete r;
     return rc;
@@ -2126,7 +2185,10 @@ int rfdd_solve_async(rfdd_handle *h, double alpha, double beta, int32_t n_nodes,
   r->ready.store(0);
   r->worker = std::thread([h, alpha, beta, n_nodes, r] {
     int device = 0;
-    int rc = guarded([&] { run_solve(h, alpha, beta, n_nodes, r); });
+    int rc = guarded([&] {
+      AllocScope scope(h->st);
+      run_solve(h, alpha, beta, n_nodes, r);
+    });
     (void)device;
     if (rc != RFDD_OK) r->ready.store(-rc);
     else r->ready.store(1);
