@@ -373,6 +373,90 @@ __global__ void pack_b_kernel(PackBatchP pb) {
   }
 }
 
+// The same B tiles, built through shared memory: a block stages a 16 (K) x 64 (N) complex slab
+// of B with reads along B's rows (coalesced), then writes the 128 packed rows x 32 K-values it
+// covers (half a tile) with coalesced 16-byte stores.  Threads of pack_b_kernel above read B down
+// its columns instead (one 8-byte element per row of B per thread).
+__global__ void __launch_bounds__(256) pack_b_t_kernel(PackBatchP pb) {
+  const PackItem it = pb.it[blockIdx.y];
+  const int jblocks = it.ntc * 2;  // 64 complex columns (128 packed rows) per block
+  const int nblk = jblocks * it.nkt;
+  __shared__ float2 sb[16][65];
+  for (int bid = blockIdx.x; bid < nblk; bid += gridDim.x) {
+    const int kt = bid % it.nkt, jb = bid / it.nkt;
+    const long long j0 = (long long)jb * 64;
+    const int p0 = kt * (TC_BK / 2);
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int idx = threadIdx.x + 256 * i;
+      const int pl = idx >> 6, jl = idx & 63;
+      const long long j = j0 + jl;
+      const int pp = p0 + pl;
+      float2 v = make_float2(0.f, 0.f);
+      if (j < it.n && pp < it.k) v = *reinterpret_cast<const float2 *>(it.src + ((long long)pp * it.ld + j) * 2);
+      sb[pl][jl] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int id = threadIdx.x + 256 * i;
+      const int rl = id >> 3, c = id & 7;  // packed row within the half tile, 16-byte chunk
+      const int jl = rl >> 1, tt = rl & 1;
+      float h[4], l[4];
+#pragma unroll
+      for (int t2 = 0; t2 < 2; ++t2) {
+        const float2 b = sb[2 * c + t2][jl];
+        const float x0 = tt == 0 ? b.x : b.y;   // coefficient of Re A
+        const float x1 = tt == 0 ? -b.y : b.x;  // coefficient of Im A
+        split_tf32(x0, h[2 * t2], l[2 * t2]);
+        split_tf32(x1, h[2 * t2 + 1], l[2 * t2 + 1]);
+      }
+      const long long rowp = 2 * j0 + rl;
+      const int nt = (int)(rowp / TC_BN), r = (int)(rowp % TC_BN);
+      const long long off = ((long long)nt * it.nkt + kt) * B_TILE + r * TC_BK + ((c ^ (r & 7)) << 2);
+      *reinterpret_cast<float4 *>(it.hi + off) = make_float4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<float4 *>(it.lo + off) = make_float4(l[0], l[1], l[2], l[3]);
+    }
+  }
+}
+
+// real B, same staging: a 32 (K) x 128 (N) slab, one packed tile half (128 rows x 32 K-values)
+__global__ void __launch_bounds__(256) pack_b_real_t_kernel(PackBatchP pb) {
+  const PackItem it = pb.it[blockIdx.y];
+  const int jblocks = it.ntc * 2;  // 128 columns per block
+  const int nblk = jblocks * it.nkt;
+  __shared__ float sb[32][129];
+  for (int bid = blockIdx.x; bid < nblk; bid += gridDim.x) {
+    const int kt = bid % it.nkt, jb = bid / it.nkt;
+    const long long j0 = (long long)jb * 128;
+    const int p0 = kt * TC_BK;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int idx = threadIdx.x + 256 * i;
+      const int pl = idx >> 7, jl = idx & 127;
+      const long long j = j0 + jl;
+      const int pp = p0 + pl;
+      sb[pl][jl] = (j < it.n && pp < it.k) ? it.src[(long long)pp * it.ld + j] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int id = threadIdx.x + 256 * i;
+      const int rl = id >> 3, c = id & 7;
+      float h[4], l[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) split_tf32(sb[c * 4 + t][rl], h[t], l[t]);
+      const long long row = j0 + rl;
+      const int nt = (int)(row / TC_BN), r = (int)(row % TC_BN);
+      const long long off = ((long long)nt * it.nkt + kt) * B_TILE + r * TC_BK + ((c ^ (r & 7)) << 2);
+      *reinterpret_cast<float4 *>(it.hi + off) = make_float4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<float4 *>(it.lo + off) = make_float4(l[0], l[1], l[2], l[3]);
+    }
+  }
+}
+
 // real operands: A (m x k, ld), B (k x n, ld) in FP32; the same tile formats with K' = k, N' = n
 __global__ void pack_a_real_kernel(PackBatchP pb) {
   const PackItem it = pb.it[blockIdx.y];
@@ -489,18 +573,20 @@ static void tc_gemm_run(cudaStream_t st, const std::vector<GemmItem<T>> &items, 
     bool any_a = false;
     for (int i = 0; i < cnt; ++i) any_a |= pa.it[i].mtc > 0;
     const dim3 ga((unsigned)std::min<long long>(ceil_div(achunks, 256), 4096), cnt);
-    const dim3 gb((unsigned)std::min<long long>(ceil_div(bchunks, 256), 4096), cnt);
+    long long bblocks = 1;  // staged half-tiles of the largest B
+    for (int i = 0; i < cnt; ++i) bblocks = std::max(bblocks, (long long)pbb.it[i].ntc * 2 * pbb.it[i].nkt);
+    const dim3 gbt((unsigned)std::min<long long>(bblocks, 8192), cnt);
     if (CPLX) {
       if (any_a) {
         pack_a_kernel<<<ga, 256, 0, st>>>(pa);
         RFDD_CHECK_LAUNCH();
       }
-      pack_b_kernel<<<gb, 256, 0, st>>>(pbb);
+      pack_b_t_kernel<<<gbt, 256, 0, st>>>(pbb);
       RFDD_CHECK_LAUNCH();
     } else {
       pack_a_real_kernel<<<ga, 256, 0, st>>>(pa);
       RFDD_CHECK_LAUNCH();
-      pack_b_real_kernel<<<gb, 256, 0, st>>>(pbb);
+      pack_b_real_t_kernel<<<gbt, 256, 0, st>>>(pbb);
       RFDD_CHECK_LAUNCH();
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
