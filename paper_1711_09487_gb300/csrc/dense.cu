@@ -536,12 +536,11 @@ __global__ void __launch_bounds__(256) lu_tourn_kernel(LuBatchP<T> lb, int K0, i
     if (nz)
       for (int r = t + 1 + tid; r < nr; r += blockDim.x) Sm[r * NB + t] = S::div(Sm[r * NB + t], pv);
     __syncthreads();
-    const int wc = w - t - 1;
-    if (nz && wc > 0)
-      for (int e = tid; e < (nr - t - 1) * wc; e += blockDim.x) {
-        const int r = t + 1 + e / wc, c = t + 1 + e % wc;
+    // rank-1 update of the remaining rows: lane = column, warps stride over the rows
+    const int c = tid & 31;
+    if (nz && c > t && c < w)
+      for (int r = t + 1 + (tid >> 5); r < nr; r += (int)(blockDim.x >> 5))
         Sm[r * NB + c] = S::fms(Sm[r * NB + t], Sm[t * NB + c], Sm[r * NB + c]);
-      }
     __syncthreads();
   }
   int *o = cout + (int64_t)blockIdx.y * cand_stride + (int64_t)set * NB;
@@ -622,14 +621,14 @@ __global__ void __launch_bounds__(256) lu_finish_kernel(LuBatchP<T> lb, int K0, 
     if (nz)
       for (int r = t + 1 + tid; r < w; r += blockDim.x) U[r][t] = S::div(U[r][t], pv);
     __syncthreads();
-    const int wc = w - t - 1;
-    if (nz && wc > 0)
-      for (int e = tid; e < wc * wc; e += blockDim.x) {
-        const int r = t + 1 + e / wc, c = t + 1 + e % wc;
-        U[r][c] = S::fms(U[r][t], U[t][c], U[r][c]);
-      }
+    const int c = tid & 31;
+    if (nz && c > t && c < w)
+      for (int r = t + 1 + (tid >> 5); r < w; r += (int)(blockDim.x >> 5)) U[r][c] = S::fms(U[r][t], U[t][c], U[r][c]);
     __syncthreads();
   }
+  __shared__ T rdiag[NB];
+  if (tid < w) rdiag[tid] = S::abs1(U[tid][tid]) != (Rl)0 ? S::div(S::one(), U[tid][tid]) : S::one();
+  __syncthreads();
   if (blockIdx.x == 0) {
     T *tp = top + (int64_t)blockIdx.y * NB * NB;
     for (int e = tid; e < w * w; e += blockDim.x) tp[e] = U[e / w][e % w];
@@ -653,7 +652,7 @@ __global__ void __launch_bounds__(256) lu_finish_kernel(LuBatchP<T> lb, int K0, 
 #pragma unroll
       for (int t = 0; t < NB; ++t)
         if (t < c) v = S::fms(x[t], U[t][c], v);
-      x[c] = S::abs1(U[c][c]) != (Rl)0 ? S::div(v, U[c][c]) : v;
+      x[c] = v * rdiag[c];
     }
   }
 #pragma unroll
