@@ -96,6 +96,27 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": reasons, "samples": len(rows)}
 
 
+# DRAM traffic of the dominant kernel (tc_gemm_kernel) per launch, from one ncu capture of
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none -k regex:tc_gemm \
+#       --csv --log-file gpurun_out/tc_traffic.csv python bench.py --mode one-solve
+# (4216 launches, 3828.7 GB; profiles/launches_q1_3d_40.md).  It describes the launch mix of the
+# sources it was taken with, so it is reported only while the CUDA sources hash to the same value.
+TC_TRAFFIC_BYTES_PER_LAUNCH = 908.14e6
+TC_TRAFFIC_SOURCES_SHA256 = "9cf08358818acad78a71b86d7861191b9aac44941fa7af9c39fddf527a16d050"
+
+
+def cuda_sources_sha256() -> str:
+    import glob
+    import hashlib
+    root = os.path.join(ROOT, "paper_1711_09487_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(root, "*.cu")) + glob.glob(os.path.join(root, "*.cuh"))):
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -277,8 +298,10 @@ def run_ours(args, rank, world, local_rank):
     if t_launch > 0:
         ach = t_flops / (t_ms / 1e3) / 1e12
         peak = float(peaks["bf16_tflops_sustained"]) * (1.1 / 2.25) / 3.0
+        traffic = TC_TRAFFIC_BYTES_PER_LAUNCH if cuda_sources_sha256() == TC_TRAFFIC_SOURCES_SHA256 else None
         roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": None, "kernel": "tcgen05 3xTF32 complex GEMM", "launches": t_launch,
+                "traffic": traffic, "traffic_unit": "DRAM bytes per launch, mean over one solve's launches",
+                "kernel": "tcgen05 3xTF32 complex GEMM", "launches": t_launch,
                 "peak_source": f"{src} bf16 sustained x 1.1/2.25 (TF32) / 3 (3xTF32 split)"}
     else:
         ach = g_flops / (g_ms / 1e3) / 1e12 if g_ms > 0 else 0.0
