@@ -934,7 +934,21 @@ void lu_batched(cudaStream_t st, const std::vector<LuItem<T>> &items, int nbo, i
         x.lda = x.ldb = x.ldc = it.ld;
         g.push_back(x);
       }
-      trsm_lower_unit<T>(st, tri, NB);
+      // U12 = L11^{-1} A12 over all trailing columns: invert the strip's unit lower block (small
+      // substitution on identity), then one deep product instead of nbo/32 shallow ones
+      if (!tri.empty()) {
+        T *inv = nullptr;
+        RFDD_CUDA(cudaMallocAsync((void **)&inv, tri.size() * (size_t)nbo * nbo * sizeof(T), st));
+        std::vector<T *> li(tri.size()), ui(tri.size(), nullptr);
+        for (size_t i = 0; i < tri.size(); ++i) li[i] = inv + i * (size_t)nbo * nbo;
+        lu_block_inverses<T>(st, tri, nbo, li, ui);
+        for (size_t i = 0; i < tri.size(); ++i) {
+          tri[i].Linv = li[i];
+          tri[i].nbi = nbo;
+        }
+        trsm_lower_unit<T>(st, tri, nbo);
+        RFDD_CUDA(cudaFreeAsync(inv, st));
+      }
       gemm_batched<T>(st, g, false, false, -1.0, 1.0);
     }
   } catch (...) {
