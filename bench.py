@@ -38,10 +38,14 @@ WORKLOAD = "q1_3d_40"
 
 
 def workload_config(w, precision):
+    grid = tuple(w.grid) if w.grid is not None else (w.n,)
+    splits = tuple(w.meta.get("splits", ())) if isinstance(w.meta, dict) else ()
+    dims = "x".join(str(g) for g in grid)
+    parts = "x".join(str(q) for q in splits) if splits else str(w.p)
     return {
-        "workload": f"3D Q1 Laplacian pencil, 40^3 interior grid (n={w.n}), 2x2x2 geometric partition "
-                    f"(p={w.p}), eigenvalues {w.meta['first']}..{w.meta['last']} (nev={w.expected_nev}), "
-                    f"{w.n_nodes} {w.rule} nodes",
+        "workload": f"{len(grid)}D Q1 Laplacian pencil, {dims} interior grid (n={w.n}), {parts} geometric "
+                    f"partition (p={w.p}), eigenvalues {w.meta['first']}..{w.meta['last']} "
+                    f"(nev={w.expected_nev}), {w.n_nodes} {w.rule.replace('_', '-')} nodes",
         "name": w.name, "n": w.n, "p": w.p, "nev": w.expected_nev, "n_nodes": w.n_nodes,
         "interval": [w.alpha, w.beta], "precision": precision,
         "l2": "no flush: every step streams the bordered factors (tens of GB) through HBM, far above L2",
