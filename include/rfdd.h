@@ -203,7 +203,19 @@ int rfdd_interior(rfdd_handle *h, double sigma, int64_t cap, double *Z_out, int6
  * theta_out: host, all Ritz values ascending (cap entries); *k receives their number. */
 int rfdd_rayleigh_ritz(rfdd_handle *h, int64_t cap, double *theta_out, int64_t *k);
 
-/* a9 building block (Alg. 3 step 7 solves its projected problem with a dense symmetric
+/* Eigenvalue count (the interval problem of Section 1 asks for every eigenvalue in [alpha, beta];
+ * this checks that none is missed): *count = number of eigenvalues of (A, M) strictly below sigma,
+ * by Sylvester's law of inertia.  With the interior-first block form of Eq. (eq1), the inertia of
+ * A - sigma M is that of the blocks B_sigma^(j) plus that of the Schur complement S(sigma)
+ * (Haynsworth additivity).  Everything is FP64: the bordered real blocks are factored as in
+ * rfdd_factor (their trailing blocks give S(sigma)), and each B_sigma^(j) and S(sigma) is reduced
+ * to tridiagonal form by Householder similarity and counted by Sturm sequence.  The number of
+ * eigenvalues in [alpha, beta] is count(beta) - count(alpha) when neither end is an eigenvalue.
+ * Needs only rfdd_setup; uses the handle's stream; O(d_j^3) work per subdomain.
+ * RFDD_ESINGULAR when sigma is an eigenvalue of a block B^(j) (choose another sigma). */
+int rfdd_inertia(rfdd_handle *h, double sigma, int64_t *count);
+
+/* a9 building block (Alg. 3 step 7 solves its projected problem with a dense symmetric/* a9 building block (Alg. 3 step 7 solves its projected problem with a dense symmetric
  * eigensolver): eigen-decomposition of a dense symmetric n x n FP64 matrix H on the GPU by
  * Householder tridiagonalisation, bisection on Sturm counts, inverse iteration (clusters
  * re-orthogonalised) and back-transformation.  H, evals, evecs

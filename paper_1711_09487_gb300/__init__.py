@@ -40,7 +40,7 @@ SYMBOLS = [
     "rfdd_result_pre_evals", "rfdd_result_free", "rfdd_factor", "rfdd_schur_copy", "rfdd_shifted_solve",
     "rfdd_filter_apply", "rfdd_lanczos", "rfdd_interior", "rfdd_rayleigh_ritz", "rfdd_solve_async",
     "rfdd_result_ready", "rfdd_memory_estimate", "rfdd_sym_eig", "rfdd_kernel_launches", "rfdd_profile",
-    "rfdd_profile_get", "rfdd_cgemm", "rfdd_dgemm", "rfdd_cgemm_noalloc",
+    "rfdd_profile_get", "rfdd_cgemm", "rfdd_dgemm", "rfdd_cgemm_noalloc", "rfdd_inertia",
 ]
 
 
@@ -118,6 +118,7 @@ def load(path: str | None = None):
     lib.rfdd_kernel_launches.restype = C.c_longlong
     fp = C.POINTER(C.c_float)
     lib.rfdd_cgemm.argtypes = [i64, i64, i64, fp, i64, fp, i64, fp, i64, C.c_double, C.c_double, i32]
+    lib.rfdd_inertia.argtypes = [vp, C.c_double, C.POINTER(i64)]
     lib.rfdd_dgemm.argtypes = [i64, i64, i64, i32, dp, i64, i32, dp, i64, dp, i64, C.c_double, C.c_double, i32, i32]
     lib.rfdd_cgemm_noalloc.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, i64, C.c_double, C.c_double, vp]
     lib.rfdd_profile.argtypes = [i32]
@@ -378,6 +379,13 @@ def rfdd_cgemm(A: np.ndarray, B: np.ndarray, C: np.ndarray, alpha: float = 1.0, 
 
 C_float_p = C.POINTER(C.c_float)
 C_double_p = C.POINTER(C.c_double)
+
+
+def rfdd_inertia(h: Handle, sigma: float) -> int:
+    """Number of eigenvalues of (A, M) below sigma (Sylvester inertia through the DD blocks)."""
+    c = C.c_int64()
+    _check(load().rfdd_inertia(h.ptr, float(sigma), C.byref(c)))
+    return int(c.value)
 
 
 def rfdd_dgemm(A: np.ndarray, B: np.ndarray, C: np.ndarray, alpha: float = 1.0, beta: float = 0.0,

@@ -152,6 +152,51 @@ __global__ void bisect_kernel(SymBatchP b) {
   it.lam[i] = 0.5 * (lo + hi);
 }
 
+// Householder reduction of every item of the batch to tridiagonal form (d, e)
+static void tridiagonalize(cudaStream_t st, const SymBatchP &b, int cnt, int nmax) {
+  for (int i = 0; i < nmax; ++i) {
+    house_kernel<<<cnt, 256, 0, st>>>(b, i);
+    RFDD_CHECK_LAUNCH();
+    const int len = nmax - i - 1;
+    if (i < nmax - 2) {
+      symv_kernel<<<dim3(ceil_div((int64_t)len * 32, 256), cnt), 256, 0, st>>>(b, i);
+      RFDD_CHECK_LAUNCH();
+      const int blocks = std::max(1, std::min(1024, ceil_div((int64_t)len * len, 256 * 8)));
+      rank2_kernel<<<dim3(blocks, cnt), 256, 0, st>>>(b, i);
+      RFDD_CHECK_LAUNCH();
+    }
+  }
+}
+
+// counts[i] = number of eigenvalues of item i's tridiagonal matrix below shift (Sturm count)
+__global__ void sturm_count_kernel(SymBatchP b, int cnt, double shift, long long *counts) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= cnt) return;
+  const SymItem it = b.it[q];
+  const int n = it.n;
+  if (n <= 0) {
+    counts[q] = 0;
+    return;
+  }
+  double emax2 = 0.0;
+  for (int k = 0; k + 1 < n; ++k) emax2 = fmax(emax2, it.e[k] * it.e[k]);
+  const double pivmin = 2.2250738585072014e-308 * fmax(1.0, emax2);
+  counts[q] = sturm_count(it.d, it.e, n, shift, pivmin);
+}
+
+void sym_negative_counts(cudaStream_t st, const std::vector<SymItem> &items, double shift, long long *counts_dev) {
+  for (size_t s0 = 0; s0 < items.size(); s0 += EIG_MAXB) {
+    SymBatchP b;
+    memset(&b, 0, sizeof(b));
+    const int cnt = (int)std::min<size_t>(EIG_MAXB, items.size() - s0);
+    int nmax = 0;
+    for (int i = 0; i < cnt; ++i) { b.it[i] = items[s0 + i]; nmax = std::max(nmax, b.it[i].n); }
+    if (nmax > 0) tridiagonalize(st, b, cnt, nmax);
+    sturm_count_kernel<<<1, 64, 0, st>>>(b, cnt, shift, counts_dev + s0);
+    RFDD_CHECK_LAUNCH();
+  }
+}
+
 void sym_eig_values(cudaStream_t st, const std::vector<SymItem> &items, int *status) {
   (void)status;
   for (size_t s0 = 0; s0 < items.size(); s0 += EIG_MAXB) {
@@ -161,18 +206,7 @@ void sym_eig_values(cudaStream_t st, const std::vector<SymItem> &items, int *sta
     int nmax = 0;
     for (int i = 0; i < cnt; ++i) { b.it[i] = items[s0 + i]; nmax = std::max(nmax, b.it[i].n); }
     if (nmax == 0) continue;
-    for (int i = 0; i < nmax; ++i) {
-      house_kernel<<<cnt, 256, 0, st>>>(b, i);
-      RFDD_CHECK_LAUNCH();
-      const int len = nmax - i - 1;
-      if (i < nmax - 2) {
-        symv_kernel<<<dim3(ceil_div((int64_t)len * 32, 256), cnt), 256, 0, st>>>(b, i);
-        RFDD_CHECK_LAUNCH();
-        const int blocks = std::max(1, std::min(1024, ceil_div((int64_t)len * len, 256 * 8)));
-        rank2_kernel<<<dim3(blocks, cnt), 256, 0, st>>>(b, i);
-        RFDD_CHECK_LAUNCH();
-      }
-    }
+    tridiagonalize(st, b, cnt, nmax);
     // e[n-1] = 0 for every item (house_kernel leaves it undefined)
     // FP64-bound and one thread per eigenvalue: warp-sized blocks spread the work over the SMs
     bisect_kernel<<<dim3(ceil_div(nmax, 32), cnt), 32, 0, st>>>(b);

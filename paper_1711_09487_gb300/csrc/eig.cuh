@@ -21,6 +21,11 @@ struct SymItem {
 // Tridiagonalise every H and compute all its eigenvalues into lam (ascending).
 void sym_eig_values(cudaStream_t st, const std::vector<SymItem> &items, int *status);
 
+// Number of eigenvalues below shift of every H (Householder tridiagonalisation, which keeps the
+// inertia, then a Sturm count of the tridiagonal matrix); H is overwritten.  counts_dev: device
+// array, one entry per item.
+void sym_negative_counts(cudaStream_t st, const std::vector<SymItem> &items, double shift, long long *counts_dev);
+
 // Eigenvectors for the ascending sorted indices sel of each item: out row r (ld_out) = unit
 // eigenvector of H for lam[sel[r]].  Eigenvalues closer than ctol * ||T|| to a neighbouring
 // selected one form a cluster whose vectors are orthogonalised against each other.

@@ -597,6 +597,11 @@ RFDD_INST_OPS(cx<double>)
                                      int64_t);
 RFDD_INST_OPSC(cx<float>)
 RFDD_INST_OPSC(cx<double>)
+// real shift (inertia counts)
+template void assemble_interface<double>(cudaStream_t, const DevPencil &, const DevDD &, const cx<double> *, int,
+                                         double *);
+template void scatter_schur<double>(cudaStream_t, const DevDD &, int, int, int, int64_t, const int64_t *,
+                                    const double *, int, double *);
 
 
 // ---------------------------------------------------------------------------------------

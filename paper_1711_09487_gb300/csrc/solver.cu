@@ -1749,6 +1749,82 @@ void complete(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
 }
 
 // ------------------------------------------------------------------------------------
+// Eigenvalue count below sigma (Sylvester's law of inertia, in FP64).  With M SPD the number
+// of eigenvalues of (A, M) below sigma is the number of negative eigenvalues of A - sigma M.
+// In the interior-first block form of Eq. (eq1) with B_sigma nonsingular, the inertia of
+// A - sigma M is the sum of the inertias of the blocks B_sigma^(j) and of the Schur
+// complement S(sigma) (Haynsworth).  The bordered real blocks are factored as in the complex
+// path (their trailing blocks give S(sigma)); each B_sigma^(j) and S(sigma) is reduced to
+// tridiagonal form by Householder similarity, which keeps the inertia, and counted by Sturm.
+// ------------------------------------------------------------------------------------
+int64_t inertia_impl(rfdd_handle *h, double sigma) {
+  cudaStream_t st = h->st;
+  const int p = h->p;
+  const int64_t s = h->s;
+  std::vector<int64_t> boff(p, 0), Doff(p + 1, 0), hoff(p + 1, 0);
+  int64_t tot = 0;
+  for (int j = 0; j < p; ++j) {
+    boff[j] = tot;
+    tot += h->D[j] * h->D[j];
+    Doff[j + 1] = Doff[j] + h->D[j];
+    hoff[j + 1] = hoff[j] + h->d[j] * h->d[j];
+  }
+  Buf Bb, boff_dev, Doff_dev, zs, piv, Hs, dbuf, cnt;
+  Bb.alloc((size_t)tot * sizeof(double));
+  upload(boff_dev, boff, st);
+  upload(Doff_dev, Doff, st);
+  std::vector<cx<double>> zv = {cx<double>(sigma, 0.0)};
+  upload(zs, zv, st);
+  assemble_blocks<double>(st, h->P, h->dd, Doff_dev.as<int64_t>(), Doff[p], boff_dev.as<int64_t>(),
+                          zs.as<cx<double>>(), 1, Bb.as<double>(), true);
+  // the B_sigma^(j) blocks are counted from copies (the LU overwrites them); S(sigma) after them
+  Hs.alloc((size_t)(hoff[p] + s * s) * sizeof(double));
+  for (int j = 0; j < p; ++j)
+    copy_rows_f64(st, Bb.as<double>() + boff[j], h->D[j], Hs.as<double>() + hoff[j], h->d[j], h->d[j], h->d[j]);
+  piv.alloc((size_t)std::max<int64_t>(1, h->dsum) * sizeof(int));
+  std::vector<LuItem<double>> items;
+  for (int j = 0; j < p; ++j) {
+    LuItem<double> it;
+    it.A = Bb.as<double>() + boff[j];
+    it.piv = piv.as<int>() + h->off[j];
+    it.dp = (int)h->d[j];
+    it.D = it.ld = (int)h->D[j];
+    items.push_back(it);
+  }
+  lu_batched<double>(st, items, NBO_LU, h->status.as<int>());
+  double *S = Hs.as<double>() + hoff[p];
+  if (s > 0) {
+    assemble_interface<double>(st, h->P, h->dd, zs.as<cx<double>>(), 1, S);
+    for (int j = 0; j < p; ++j) {
+      const int sj = (int)(h->sidx_off[j + 1] - h->sidx_off[j]);
+      scatter_schur<double>(st, h->dd, j, (int)h->d[j], sj, h->sidx_off[j], boff_dev.as<int64_t>(), Bb.as<double>(), 1,
+                            S);
+    }
+  }
+  sync_status(h, "inertia: B_sigma factorisation");
+  Bb.release();
+  int64_t nmax = s;
+  for (int j = 0; j < p; ++j) nmax = std::max(nmax, h->d[j]);
+  const int nitems = p + (s > 0 ? 1 : 0);
+  dbuf.alloc((size_t)nitems * 4 * std::max<int64_t>(1, nmax) * sizeof(double));
+  std::vector<SymItem> si;
+  for (int q = 0; q < nitems; ++q) {
+    const int64_t nq = q < p ? h->d[q] : s;
+    double *w = dbuf.as<double>() + (int64_t)q * 4 * nmax;
+    si.push_back({q < p ? Hs.as<double>() + hoff[q] : S, (int)nq, (int)nq, w, w + nmax, w + 2 * nmax, w + 3 * nmax,
+                  nullptr, nullptr});
+  }
+  cnt.alloc((size_t)nitems * sizeof(long long));
+  sym_negative_counts(st, si, 0.0, cnt.as<long long>());
+  std::vector<long long> hc(nitems);
+  RFDD_CUDA(cudaMemcpyAsync(hc.data(), cnt.p, nitems * sizeof(long long), cudaMemcpyDeviceToHost, st));
+  RFDD_CUDA(cudaStreamSynchronize(st));
+  int64_t total = 0;
+  for (long long c : hc) total += c;
+  return total;
+}
+
+// ------------------------------------------------------------------------------------
 // precision dispatch
 // ------------------------------------------------------------------------------------
 void set_nodes(rfdd_handle *h, int nc, const double *z, const double *w) {
@@ -2155,6 +2231,14 @@ int rfdd_rayleigh_ritz(rfdd_handle *h, int64_t cap, double *theta_out, int64_t *
     if (k) *k = (int64_t)h->rr_theta.size();
     if (theta_out)
       for (int64_t i = 0; i < (int64_t)h->rr_theta.size() && i < cap; ++i) theta_out[i] = h->rr_theta[i];
+  });
+}
+
+int rfdd_inertia(rfdd_handle *h, double sigma, int64_t *count) {
+  if (!h || !count || !std::isfinite(sigma)) return RFDD_EINVAL;
+  return guarded([&] {
+    AllocScope scope(h->st);
+    *count = inertia_impl(h, sigma);
   });
 }
 
