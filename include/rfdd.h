@@ -139,6 +139,10 @@ int rfdd_setup(const rfdd_csr *A, const rfdd_csr *M, const int32_t *part, int32_
 int rfdd_layout(const rfdd_handle *h, int64_t *off, int64_t *perm, int32_t *p_out,
                 int64_t *s_out);
 
+/* Device workspaces of a handle come from the device's default stream-ordered memory pool, on
+ * the handle's stream.  Freed workspaces stay in that pool for reuse by later solves and handles
+ * of the process (its release threshold is raised at the first rfdd_setup on a device); a caller
+ * that needs the memory back can trim the pool (cudaMemPoolTrimTo) after rfdd_destroy. */
 void rfdd_destroy(rfdd_handle *h);
 
 /* ---- full solve: Alg. 3 (RF-DDES) + completion ------------------------------------------

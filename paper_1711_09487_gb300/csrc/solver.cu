@@ -2039,7 +2039,8 @@ void rfdd_destroy(rfdd_handle *h) {
   if (h->st) cudaStreamSynchronize(h->st);
   cudaStream_t st = h->st;
   bool own = h->own_stream;
-  delete h;
+  delete h;                            // enqueues the stream-ordered frees of its buffers on st
+  if (st) cudaStreamSynchronize(st);
   if (own && st) cudaStreamDestroy(st);
 }
 
