@@ -102,7 +102,7 @@ class ClockSampler:
 
 # DRAM traffic of the dominant kernel (tc_gemm_kernel) per launch, from one ncu capture of
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none -k regex:tc_gemm \
-#       --csv --log-file gpurun_out/tc_traffic.csv python bench.py --mode one-solve
+#       --csv --log-file tc_traffic.csv python bench.py --mode one-solve
 # (3736 launches, 3766.2 GB; profiles/launches_q1_3d_40.md).  It describes the launch mix of the
 # sources it was taken with, so it is reported only while the CUDA sources hash to the same value.
 TC_TRAFFIC_BYTES_PER_LAUNCH = 1008.09e6
