@@ -381,8 +381,55 @@ void validate_csr(const rfdd_csr *A, const char *name) {
 }
 
 // symmetric in pattern and value: compare with the transpose built by counting sort
+// Host work over rows split into contiguous chunks, one thread per chunk (results do not depend
+// on the number of threads).
+template <typename F>
+void parallel_rows(int64_t n, F &&f) {
+  const int64_t nt = std::max<int64_t>(1, std::min<int64_t>(std::thread::hardware_concurrency(), (n + 4095) / 4096));
+  if (nt <= 1) {
+    f(0, n, 0);
+    return;
+  }
+  std::vector<std::thread> th;
+  for (int64_t t = 0; t < nt; ++t) th.emplace_back([&, t] { f(n * t / nt, n * (t + 1) / nt, (int)t); });
+  for (auto &x : th) x.join();
+}
+
 void check_symmetric(const rfdd_csr *A, const char *name) {
   const int64_t n = A->n, nnz = A->rowptr[n];
+  // rows with strictly increasing columns: look every entry's mirror up by binary search
+  std::atomic<int> unsorted{0};
+  parallel_rows(n, [&](int64_t r0, int64_t r1, int) {
+    for (int64_t i = r0; i < r1; ++i)
+      for (int64_t e = A->rowptr[i] + 1; e < A->rowptr[i + 1]; ++e)
+        if (A->col[e] <= A->col[e - 1]) {
+          unsorted = 1;
+          return;
+        }
+  });
+  if (!unsorted) {
+    std::atomic<int> bad{0};  // 1: pattern, 2: values
+    parallel_rows(n, [&](int64_t r0, int64_t r1, int) {
+      for (int64_t i = r0; i < r1 && !bad.load(std::memory_order_relaxed); ++i)
+        for (int64_t e = A->rowptr[i]; e < A->rowptr[i + 1]; ++e) {
+          const int64_t j = A->col[e];
+          const int32_t *b = A->col + A->rowptr[j], *en = A->col + A->rowptr[j + 1];
+          const int32_t *f = std::lower_bound(b, en, (int32_t)i);
+          if (f == en || *f != i) {
+            bad = 1;
+            return;
+          }
+          const double a = A->val[e], c = A->val[A->rowptr[j] + (f - b)];
+          if (!(std::fabs(a - c) <= 1e-14 * std::max(std::fabs(a), std::fabs(c)))) {
+            bad = 2;
+            return;
+          }
+        }
+    });
+    RFDD_REQUIRE(bad != 1, RFDD_ENOTSYM, std::string(name) + " is not symmetric (pattern)");
+    RFDD_REQUIRE(bad != 2, RFDD_ENOTSYM, std::string(name) + " is not symmetric (values)");
+    return;
+  }
   std::vector<int64_t> cnt(n + 1, 0);
   for (int64_t e = 0; e < nnz; ++e) cnt[A->col[e] + 1]++;
   for (int64_t i = 0; i < n; ++i) cnt[i + 1] += cnt[i];
@@ -395,25 +442,37 @@ void check_symmetric(const rfdd_csr *A, const char *name) {
       trow[q] = i;
       tval[q] = A->val[e];
     }
-  // row i of A^T: entries (trow, tval) in [cnt[i], cnt[i+1]); compare as sorted sets
-  std::vector<std::pair<int64_t, double>> ra, rt;
-  for (int64_t i = 0; i < n; ++i) {
-    ra.clear();
-    rt.clear();
-    for (int64_t e = A->rowptr[i]; e < A->rowptr[i + 1]; ++e) ra.push_back({A->col[e], A->val[e]});
-    for (int64_t q = cnt[i]; q < cnt[i + 1]; ++q) rt.push_back({trow[q], tval[q]});
-    std::sort(ra.begin(), ra.end());
-    std::sort(rt.begin(), rt.end());
-    RFDD_REQUIRE(ra.size() == rt.size(), RFDD_ENOTSYM, std::string(name) + " is not symmetric (pattern)");
-    for (size_t k = 0; k < ra.size(); ++k) {
-      RFDD_REQUIRE(ra[k].first == rt[k].first, RFDD_ENOTSYM, std::string(name) + " is not symmetric (pattern)");
-      const double a = ra[k].second, b = rt[k].second;
-      RFDD_REQUIRE(std::fabs(a - b) <= 1e-14 * std::max(std::fabs(a), std::fabs(b)), RFDD_ENOTSYM,
-                   std::string(name) + " is not symmetric (values)");
+  // row i of A^T: entries (trow, tval) in [cnt[i], cnt[i+1]), already in increasing row order;
+  // compare with row i of A as sorted sets
+  std::atomic<int> bad{0};  // 1: pattern, 2: values
+  parallel_rows(n, [&](int64_t r0, int64_t r1, int) {
+    std::vector<std::pair<int64_t, double>> ra;
+    for (int64_t i = r0; i < r1 && !bad.load(std::memory_order_relaxed); ++i) {
+      ra.clear();
+      for (int64_t e = A->rowptr[i]; e < A->rowptr[i + 1]; ++e) ra.push_back({A->col[e], A->val[e]});
+      if (!std::is_sorted(ra.begin(), ra.end(), [](auto &x, auto &y) { return x.first < y.first; }))
+        std::sort(ra.begin(), ra.end());
+      if ((int64_t)ra.size() != cnt[i + 1] - cnt[i]) {
+        bad = 1;
+        return;
+      }
+      for (size_t k = 0; k < ra.size(); ++k) {
+        const int64_t q = cnt[i] + (int64_t)k;
+        if (ra[k].first != trow[q]) {
+          bad = 1;
+          return;
+        }
+        const double a = ra[k].second, b = tval[q];
+        if (!(std::fabs(a - b) <= 1e-14 * std::max(std::fabs(a), std::fabs(b)))) {
+          bad = 2;
+          return;
+        }
+      }
     }
-  }
+  });
+  RFDD_REQUIRE(bad != 1, RFDD_ENOTSYM, std::string(name) + " is not symmetric (pattern)");
+  RFDD_REQUIRE(bad != 2, RFDD_ENOTSYM, std::string(name) + " is not symmetric (values)");
 }
-
 void do_setup(rfdd_handle *h, const rfdd_csr *A, const rfdd_csr *M, const int32_t *part, int32_t p) {
   validate_csr(A, "A");
   validate_csr(M, "M");
@@ -464,39 +523,81 @@ void do_setup(rfdd_handle *h, const rfdd_csr *A, const rfdd_csr *M, const int32_
       h->iperm[i] = r;
     }
   }
-  // union CSR in the new ordering
+  // union CSR in the new ordering: rows merged in parallel chunks, then concatenated in order
   std::vector<int64_t> rp(n + 1, 0);
   std::vector<int32_t> cl;
   std::vector<double> av, mv;
-  cl.reserve(A->rowptr[n] + M->rowptr[n]);
-  std::vector<std::pair<int64_t, std::pair<double, double>>> row;
-  h->normA = h->normM = 0.0;
-  for (int64_t r = 0; r < n; ++r) {
-    const int64_t i = h->perm[r];
-    row.clear();
-    double sa = 0, sm = 0;
-    for (int64_t e = A->rowptr[i]; e < A->rowptr[i + 1]; ++e) {
-      row.push_back({h->iperm[A->col[e]], {A->val[e], 0.0}});
-      sa += std::fabs(A->val[e]);
+  const int64_t nt_max = std::max<int64_t>(1, std::thread::hardware_concurrency());
+  std::vector<std::vector<int32_t>> ccl(nt_max);
+  std::vector<std::vector<double>> cav(nt_max), cmv(nt_max);
+  std::vector<double> cna(nt_max, 0.0), cnm(nt_max, 0.0);
+  std::vector<int64_t> cr0(nt_max, -1);
+  std::vector<int64_t> rowlen(n, 0);
+  parallel_rows(n, [&](int64_t r0, int64_t r1, int t) {
+    // thread-local buffers (vector headers of different threads would share cache lines)
+    std::vector<std::pair<int64_t, std::pair<double, double>>> row;
+    std::vector<int32_t> c;
+    std::vector<double> a, m;
+    double na = 0.0, nm = 0.0;
+    int64_t est = 0;
+    for (int64_t r = r0; r < r1; ++r) {
+      const int64_t i = h->perm[r];
+      est += (A->rowptr[i + 1] - A->rowptr[i]) + (M->rowptr[i + 1] - M->rowptr[i]);
     }
-    for (int64_t e = M->rowptr[i]; e < M->rowptr[i + 1]; ++e) {
-      row.push_back({h->iperm[M->col[e]], {0.0, M->val[e]}});
-      sm += std::fabs(M->val[e]);
-    }
-    h->normA = std::max(h->normA, sa);
-    h->normM = std::max(h->normM, sm);
-    std::sort(row.begin(), row.end(), [](auto &x, auto &y) { return x.first < y.first; });
-    for (size_t k = 0; k < row.size(); ++k) {
-      if (!cl.empty() && (int64_t)cl.size() > rp[r] && cl.back() == row[k].first) {
-        av.back() += row[k].second.first;
-        mv.back() += row[k].second.second;
-      } else {
-        cl.push_back((int32_t)row[k].first);
-        av.push_back(row[k].second.first);
-        mv.push_back(row[k].second.second);
+    c.reserve(est);
+    a.reserve(est);
+    m.reserve(est);
+    for (int64_t r = r0; r < r1; ++r) {
+      const int64_t i = h->perm[r];
+      row.clear();
+      double sa = 0, sm = 0;
+      for (int64_t e = A->rowptr[i]; e < A->rowptr[i + 1]; ++e) {
+        row.push_back({h->iperm[A->col[e]], {A->val[e], 0.0}});
+        sa += std::fabs(A->val[e]);
       }
+      for (int64_t e = M->rowptr[i]; e < M->rowptr[i + 1]; ++e) {
+        row.push_back({h->iperm[M->col[e]], {0.0, M->val[e]}});
+        sm += std::fabs(M->val[e]);
+      }
+      na = std::max(na, sa);
+      nm = std::max(nm, sm);
+      // equal columns are summed below; each entry holds only one of (a, m), so their order is free
+      std::sort(row.begin(), row.end(), [](auto &x, auto &y) { return x.first < y.first; });
+      const size_t before = c.size();
+      for (size_t k = 0; k < row.size(); ++k) {
+        if (c.size() > before && c.back() == row[k].first) {
+          a.back() += row[k].second.first;
+          m.back() += row[k].second.second;
+        } else {
+          c.push_back((int32_t)row[k].first);
+          a.push_back(row[k].second.first);
+          m.push_back(row[k].second.second);
+        }
+      }
+      rowlen[r] = (int64_t)(c.size() - before);
     }
-    rp[r + 1] = (int64_t)cl.size();
+    cr0[t] = r0;
+    cna[t] = na;
+    cnm[t] = nm;
+    ccl[t] = std::move(c);
+    cav[t] = std::move(a);
+    cmv[t] = std::move(m);
+  });
+  for (int64_t r = 0; r < n; ++r) rp[r + 1] = rp[r] + rowlen[r];
+  h->normA = h->normM = 0.0;
+  for (int64_t t = 0; t < nt_max; ++t) {
+    h->normA = std::max(h->normA, cna[t]);
+    h->normM = std::max(h->normM, cnm[t]);
+  }
+  cl.resize(rp[n]);
+  av.resize(rp[n]);
+  mv.resize(rp[n]);
+  for (int64_t t = 0; t < nt_max; ++t) {
+    if (cr0[t] < 0) continue;
+    const int64_t o = rp[cr0[t]];
+    std::copy(ccl[t].begin(), ccl[t].end(), cl.begin() + o);
+    std::copy(cav[t].begin(), cav[t].end(), av.begin() + o);
+    std::copy(cmv[t].begin(), cmv[t].end(), mv.begin() + o);
   }
   h->nnz = rp[n];
   // interface coupling sets sidx_j
@@ -2006,7 +2107,10 @@ int rfdd_setup(const rfdd_csr *A, const rfdd_csr *M, const int32_t *part, int32_
     RFDD_REQUIRE(h->opt.precision == RFDD_FP64 || h->opt.precision == RFDD_MIXED, RFDD_EINVAL, "bad precision");
     RFDD_REQUIRE(h->opt.block >= 1 && h->opt.block <= 64, RFDD_EINVAL, "block must be in [1, 64]");
     RFDD_REQUIRE(h->opt.psi >= 1 && h->opt.nev_b >= 1, RFDD_EINVAL, "psi and nev_b must be >= 1");
+    const auto t0 = std::chrono::steady_clock::now();
     do_setup(h, A, M, part, p);  // host-side validation and ordering (no CUDA calls)
+    RFDD_LOGF("setup: host validation and ordering %.1f ms",
+              std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
     if (h->opt.stream) {
       h->st = (cudaStream_t)h->opt.stream;
     } else {
