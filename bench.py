@@ -103,10 +103,10 @@ class ClockSampler:
 # DRAM traffic of the dominant kernel (tc_gemm_kernel) per launch, from one ncu capture of
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none -k regex:tc_gemm \
 #       --csv --log-file tc_traffic.csv python bench.py --mode one-solve
-# (3736 launches, 3766.2 GB; profiles/launches_q1_3d_40.md).  It describes the launch mix of the
+# (3736 launches, 3802.5 GB; profiles/launches_q1_3d_40.md).  It describes the launch mix of the
 # sources it was taken with, so it is reported only while the CUDA sources hash to the same value.
-TC_TRAFFIC_BYTES_PER_LAUNCH = 1008.09e6
-TC_TRAFFIC_SOURCES_SHA256 = "f9f05d2db508fc53ab07e604cf078f9d2caa7ce2d299d4005953762526570e74"
+TC_TRAFFIC_BYTES_PER_LAUNCH = 1017.81e6
+TC_TRAFFIC_SOURCES_SHA256 = "ef8c29a435a0a8f8e9b2a7e0bca98b7b4cc770c9bca11b9fbb6aef91296a122c"
 
 
 def cuda_sources_sha256() -> str:
