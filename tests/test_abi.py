@@ -114,3 +114,42 @@ def test_setup_rejects_indefinite_mass_and_size_mismatch(R):
     with pytest.raises(R.RfddError) as e:
         R.rfdd_setup(A2, M, part, p)
     assert e.value.code == R.RFDD_EINVAL
+
+
+def _reverse_rows(c):
+    """The same matrix with every row's entries stored in decreasing column order."""
+    col, val = c.col.copy(), c.val.copy()
+    for i in range(c.n):
+        a, b = c.rowptr[i], c.rowptr[i + 1]
+        col[a:b] = col[a:b][::-1]
+        val[a:b] = val[a:b][::-1]
+    return I.Csr(c.n, c.rowptr, col, val)
+
+
+def test_setup_accepts_symmetric_matrices_with_unsorted_rows(R):
+    A, M, part, p = _small()
+    try:
+        R.rfdd_setup(_reverse_rows(A), _reverse_rows(M), part, p)  # succeeds where a GPU is present
+    except R.RfddError as e:
+        # without a GPU the call gets past validation and fails at the first CUDA call
+        assert e.code not in (R.RFDD_ENOTSYM, R.RFDD_EPARTITION, R.RFDD_ENOTSPD_M, R.RFDD_EINVAL), e
+
+
+def test_setup_rejects_nonsymmetric_with_unsorted_rows(R):
+    A, M, part, p = _small()
+    Au = _reverse_rows(A)
+    Au.val[Au.rowptr[0]] += 1.0  # row 0's largest column, off the diagonal
+    with pytest.raises(R.RfddError) as e:
+        R.rfdd_setup(Au, M, part, p)
+    assert e.value.code == R.RFDD_ENOTSYM
+
+
+def test_setup_rejects_one_sided_entry(R):
+    A, M, part, p = _small()
+    a = A.to_scipy().tolil()
+    a[0, 2] = 0.5  # no (2, 0) partner in the pattern of q1_2d_24 (not a stencil neighbour)
+    a = sp.csr_matrix(a)
+    assert a[2, 0] == 0
+    with pytest.raises(R.RfddError) as e:
+        R.rfdd_setup(a, M, part, p)
+    assert e.value.code == R.RFDD_ENOTSYM
