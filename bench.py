@@ -372,9 +372,26 @@ def run_gemm(args):
                       "tflops_4m": flops / (ms / 1e3) / 1e12 if ms > 0 else None}), flush=True)
 
 
+def run_dgemm(args):
+    """One Gram-type product C = Y^T Y (Y: k x n FP64, all output tiles formed) in the double-FP32
+    arithmetic of the basis products (the Rayleigh-Ritz Gram shape; profiled alone with ncu)."""
+    import paper_1711_09487_gb300 as R
+    R.load()
+    n, _, k = args.gemm
+    Y = np.random.default_rng(0).standard_normal((k, n))
+    C0 = np.zeros((n, n))
+    R.rfdd_dgemm(Y, Y, C0, 1.0, 0.0, True, False, 1, False)  # warm-up
+    R.rfdd_profile(True)
+    R.rfdd_dgemm(Y, Y, C0, 1.0, 0.0, True, False, 1, False)
+    launches, ms, flops = R.rfdd_profile_get(0)
+    R.rfdd_profile(False)
+    print(json.dumps({"mode": "dgemm", "n": n, "k": k, "kernel_ms": ms,
+                      "fp64_equiv_tflops": flops / (ms / 1e3) / 1e12 if ms > 0 else None}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--mode", default="bench", choices=["bench", "one-solve", "gemm"])
+    ap.add_argument("--mode", default="bench", choices=["bench", "one-solve", "gemm", "dgemm"])
     ap.add_argument("--gemm", type=int, nargs=3, default=[8192, 8192, 128], metavar=("M", "N", "K"))
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
@@ -391,6 +408,9 @@ def main():
         return
     if args.mode == "gemm":
         run_gemm(args)
+        return
+    if args.mode == "dgemm":
+        run_dgemm(args)
         return
     if args.impl == "reference":
         run_reference(args, rank, world)
