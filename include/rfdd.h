@@ -268,10 +268,15 @@ int rfdd_cgemm_noalloc(int64_t m, int64_t n, int64_t k, const float *A, int64_t 
  * rfdd_profile(1): clear the records and time every launch of the dense contraction kernels
  * (kind 0: CUDA-core GEMM, kind 1: tensor-core GEMM) with CUDA events on their stream;
  * rfdd_profile(0) stops recording.  rfdd_profile_get sums, for one kind, the launches, their
- * event-measured milliseconds and their algorithmic flops (a complex multiply-add counts 8). */
+ * event-measured milliseconds and their algorithmic flops (a complex multiply-add counts 8).
+ * rfdd_profile_busy gives, for one kind, the milliseconds during which at least one recorded
+ * launch was running: the union of their [start, end] intervals, so that launches of two
+ * streams that ran at the same time count once (it equals the sum when launches never overlap).
+ * Returns RFDD_ESTATE if launches were recorded without rfdd_profile(1). */
 long long rfdd_kernel_launches(void);
 int rfdd_profile(int32_t enable);
 int rfdd_profile_get(int32_t kind, int64_t *launches, double *ms, double *flops);
+int rfdd_profile_busy(int32_t kind, double *busy_ms);
 
 /* Asynchronous solve for serving: enqueues the solve on `stream` (a cudaStream_t, NULL = the
  * handle's) and returns; rfdd_result_ready() reports completion (1 done, 0 running, <0 error

@@ -40,7 +40,7 @@ SYMBOLS = [
     "rfdd_result_pre_evals", "rfdd_result_free", "rfdd_factor", "rfdd_schur_copy", "rfdd_shifted_solve",
     "rfdd_filter_apply", "rfdd_lanczos", "rfdd_interior", "rfdd_rayleigh_ritz", "rfdd_solve_async",
     "rfdd_result_ready", "rfdd_memory_estimate", "rfdd_sym_eig", "rfdd_kernel_launches", "rfdd_profile",
-    "rfdd_profile_get", "rfdd_cgemm", "rfdd_dgemm", "rfdd_cgemm_noalloc", "rfdd_inertia",
+    "rfdd_profile_get", "rfdd_profile_busy", "rfdd_cgemm", "rfdd_dgemm", "rfdd_cgemm_noalloc", "rfdd_inertia",
 ]
 
 
@@ -123,6 +123,7 @@ def load(path: str | None = None):
     lib.rfdd_cgemm_noalloc.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, i64, C.c_double, C.c_double, vp]
     lib.rfdd_profile.argtypes = [i32]
     lib.rfdd_profile_get.argtypes = [i32, C.POINTER(i64), dp, dp]
+    lib.rfdd_profile_busy.argtypes = [i32, dp]
     _lib = lib
     return lib
 
@@ -423,6 +424,13 @@ def rfdd_profile_get(kind: int):
     n, ms, fl = C.c_int64(), C.c_double(), C.c_double()
     _check(load().rfdd_profile_get(kind, C.byref(n), C.byref(ms), C.byref(fl)))
     return n.value, ms.value, fl.value
+
+
+def rfdd_profile_busy(kind: int) -> float:
+    """Milliseconds during which at least one recorded launch of this kind was running."""
+    ms = C.c_double()
+    _check(load().rfdd_profile_busy(kind, C.byref(ms)))
+    return ms.value
 
 
 def solve(A, M, part, p, alpha, beta, n_nodes, **opts):

@@ -130,12 +130,12 @@ __global__ void __launch_bounds__(256) splitk_reduce_kernel(GemmBatchP<T> batch,
 }
 
 int sm_count() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
+  static const int n = [] {  // initialised once, also when several host threads launch
+    int dev = 0, v = 0;
     cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
-  }
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
+    return v;
+  }();
   return n;
 }
 
@@ -884,12 +884,12 @@ void lu_batched(cudaStream_t st, const std::vector<LuItem<T>> &items, int nbo, i
     dpmax = std::max(dpmax, it.dp);
   }
   if (dpmax == 0) return;
-  static bool attr_set = false;
   const size_t smem = (size_t)R * NB * sizeof(T) + (size_t)R * sizeof(int);
-  if (!attr_set) {
+  static const bool attr_set = [smem] {  // once per T, thread-safe
     RFDD_CUDA(cudaFuncSetAttribute(lu_tourn_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr_set = true;
-  }
+    return true;
+  }();
+  (void)attr_set;
   LuWork wk;
   const int stride = (ceil_div(dpmax, R) + 1) * NB;
   wk.cand_ints = (size_t)2 * MAXB * stride;

@@ -12,6 +12,7 @@
 #include <chrono>
 #include <functional>
 #include <cmath>
+#include <exception>
 #include <memory>
 #include <mutex>
 #include <numeric>
@@ -30,9 +31,10 @@ namespace rfdd {
 std::atomic<long long> g_kernel_launches{0};
 namespace {
 std::mutex g_prof_mu;
-bool g_prof_on = false;
+std::atomic<bool> g_prof_on{false};  // read by every launching host thread
 std::vector<ProfileRec> g_prof;
 std::vector<cudaEvent_t> g_prof_pool;
+cudaEvent_t g_prof_ref = nullptr;  // completed before any recorded launch started
 }  // namespace
 bool profiling_enabled() { return g_prof_on; }
 cudaEvent_t profile_event() {
@@ -260,6 +262,18 @@ struct rfdd_handle {
   Buf Pk;
   struct PkOff { int64_t lu = -1, li = -1, ui = -1, l21 = -1, u12 = -1; };
   std::vector<PkOff> pkB, pkS;
+  // Real factorisation of the B_sigma^(j) (a8), started on a second stream at the beginning of a
+  // solve so that it overlaps the complex factorisations and the Lanczos process; interior_impl
+  // waits for it through ev_join.
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  Buf IBs, Ipiv, IRLinv, IRUinv, I_doff, I_boffr_dev, I_zs, I_status;
+  std::vector<int64_t> I_boffr, I_rinvoff;
+  double I_sigma = 0.0;
+  size_t I_tsize = 0;
+  bool I_ready = false, I_forked = false;
+  std::thread I_thread;       // host thread launching the started factorisation
+  std::exception_ptr I_exc;   // its error, rethrown by interior_join
   std::vector<int64_t> boff, pivBoff;
   bool have_factors = false;
   double alpha = 0, beta = 0;
@@ -283,15 +297,18 @@ namespace {
 
 inline bool is_mixed(const rfdd_handle *h) { return h->opt.precision == RFDD_MIXED; }
 
-void sync_status(rfdd_handle *h, const char *where) {
+// Waits for the handle's stream, then raises what the device recorded in the status word w
+// (h->status unless given) and in the tensor-core error flags; a nonzero word is cleared.
+void sync_status(rfdd_handle *h, const char *where, Buf *w = nullptr) {
   RFDD_CUDA(cudaStreamSynchronize(h->st));
+  if (!w) w = &h->status;
   int s = 0;
-  RFDD_CUDA(cudaMemcpy(&s, h->status.p, sizeof(int), cudaMemcpyDeviceToHost));
+  RFDD_CUDA(cudaMemcpy(&s, w->p, sizeof(int), cudaMemcpyDeviceToHost));
   const int tce = tc_take_error();
   if (tce & DS_WAIT_TIMEOUT)
     throw Error(RFDD_ECUDA, std::string(where) + ": a tensor-core GEMM timed out waiting for its operands");
   if (s != 0) {
-    RFDD_CUDA(cudaMemset(h->status.p, 0, sizeof(int)));
+    RFDD_CUDA(cudaMemset(w->p, 0, sizeof(int)));
     if (s & (DS_ZERO_PIVOT | DS_NONFINITE))
       throw Error(RFDD_ESINGULAR, std::string(where) + ": zero or non-finite pivot (device status " +
                                       std::to_string(s) + ")");
@@ -1460,6 +1477,114 @@ void lanczos_impl(rfdd_handle *h) {
 // ------------------------------------------------------------------------------------
 // a8: interior basis and Z (Eq. trabala, trabala2, z)
 // ------------------------------------------------------------------------------------
+// Waits for an interior factorisation started on the second stream: joins the host thread that
+// launched it (rethrowing its error) and orders the handle's stream after its kernels.
+void interior_join(rfdd_handle *h) {
+  if (h->I_thread.joinable()) h->I_thread.join();
+  if (h->I_forked) {
+    RFDD_CUDA(cudaStreamWaitEvent(h->st, h->ev_join, 0));
+    h->I_forked = false;
+  }
+  if (h->I_exc) {
+    std::exception_ptr e = h->I_exc;
+    h->I_exc = nullptr;
+    h->I_ready = false;
+    std::rethrow_exception(e);
+  }
+}
+
+// B_sigma^(j) dense (real) blocks, their LU and inverted diagonal blocks.  Buffers are allocated
+// and the small tables uploaded on the handle's stream.  With on == h->st the kernels follow
+// there and record into h->status.  Otherwise a host thread launches them on `on` after ev_fork
+// (so that their thousands of small launches do not hold up the launches of the complex
+// factorisations), records the pivot status in I_status and signals ev_join; interior_join
+// waits for it.
+template <typename Tr>
+void interior_factor_start(rfdd_handle *h, double sigma, cudaStream_t on) {
+  cudaStream_t st = h->st;
+  h->I_ready = false;
+  interior_join(h);  // an earlier start that was never consumed (a solve that failed after it)
+  const int p = h->p;
+  const int64_t dsum = h->dsum;
+  std::vector<int64_t> doff(p + 1, 0);
+  h->I_boffr.assign(p, 0);
+  h->I_rinvoff.assign(p + 1, 0);
+  int64_t tot = 0;
+  for (int j = 0; j < p; ++j) {
+    doff[j + 1] = doff[j] + h->d[j];
+    h->I_boffr[j] = tot;
+    tot += h->d[j] * h->d[j];
+    h->I_rinvoff[j + 1] = h->I_rinvoff[j] + block_inverse_elems(h->d[j], NBO);
+  }
+  h->IBs.alloc((size_t)tot * sizeof(Tr));
+  h->Ipiv.alloc((size_t)std::max<int64_t>(1, dsum) * sizeof(int));
+  h->IRLinv.alloc((size_t)h->I_rinvoff[p] * sizeof(Tr));
+  h->IRUinv.alloc((size_t)h->I_rinvoff[p] * sizeof(Tr));
+  upload(h->I_doff, doff, st);
+  upload(h->I_boffr_dev, h->I_boffr, st);
+  std::vector<cx<double>> zsig = {cx<double>(sigma, 0.0)};
+  upload(h->I_zs, zsig, st);
+  int *status = h->status.as<int>();
+  if (on != st) {
+    if (!h->I_status.p) h->I_status.alloc(sizeof(int));
+    RFDD_CUDA(cudaMemsetAsync(h->I_status.p, 0, sizeof(int), st));
+    status = h->I_status.as<int>();
+    RFDD_CUDA(cudaEventRecord(h->ev_fork, st));
+  }
+  Tr *Bs = h->IBs.as<Tr>();
+  std::vector<LuItem<Tr>> items;
+  std::vector<SolveItem<Tr>> fi;
+  std::vector<Tr *> li, ui;
+  for (int j = 0; j < p; ++j) {
+    LuItem<Tr> it;
+    it.A = Bs + h->I_boffr[j];
+    it.piv = h->Ipiv.as<int>() + h->off[j];
+    it.dp = it.D = it.ld = (int)h->d[j];
+    items.push_back(it);
+    SolveItem<Tr> x;
+    x.LU = Bs + h->I_boffr[j];
+    x.piv = nullptr;
+    x.n = x.ld = (int)h->d[j];
+    x.X = nullptr;
+    x.ldx = x.ncols = 0;
+    fi.push_back(x);
+    li.push_back(h->IRLinv.as<Tr>() + h->I_rinvoff[j]);
+    ui.push_back(h->IRUinv.as<Tr>() + h->I_rinvoff[j]);
+  }
+  const DevPencil P = h->P;
+  const DevDD dd = h->dd;
+  const int64_t *doff_dev = h->I_doff.as<int64_t>(), *boffr_dev = h->I_boffr_dev.as<int64_t>();
+  const cx<double> *zs = h->I_zs.as<cx<double>>();
+  auto launch = [=](cudaStream_t s) {
+    // assemble_blocks without border: D_j = d_j, and the same row mapping
+    assemble_blocks<Tr>(s, P, dd, doff_dev, dsum, boffr_dev, zs, 1, Bs, false);
+    lu_batched<Tr>(s, items, NBO_LU, status);
+    // inverted diagonal blocks for the many solves of the subspace iteration and the chains
+    lu_block_inverses<Tr>(s, fi, NBO, li, ui);
+  };
+  if (on == st) {
+    launch(st);
+  } else {
+    int device = 0;
+    RFDD_CUDA(cudaGetDevice(&device));
+    h->I_forked = true;
+    h->I_thread = std::thread([h, on, device, launch] {
+      try {
+        RFDD_CUDA(cudaSetDevice(device));
+        RFDD_CUDA(cudaStreamWaitEvent(on, h->ev_fork, 0));
+        launch(on);
+      } catch (...) {
+        h->I_exc = std::current_exception();
+      }
+      // recorded even after an error, so that interior_join never waits on a stale event
+      cudaEventRecord(h->ev_join, on);
+    });
+  }
+  h->I_sigma = sigma;
+  h->I_tsize = sizeof(Tr);
+  h->I_ready = true;
+}
+
 template <typename Tr>
 void interior_impl(rfdd_handle *h, double sigma) {
   cudaStream_t st = h->st;
@@ -1468,56 +1593,15 @@ void interior_impl(rfdd_handle *h, double sigma) {
   const int psi = std::max(1, h->opt.psi);
   RFDD_REQUIRE(mu > 0, RFDD_ESTATE, "interior: run the Lanczos step first");
   h->sigma_used = sigma;
-  // B_sigma^(j) dense (real) and its LU
-  std::vector<int64_t> doff(p + 1, 0), boffr(p, 0);
-  int64_t tot = 0;
-  for (int j = 0; j < p; ++j) {
-    doff[j + 1] = doff[j] + h->d[j];
-    boffr[j] = tot;
-    tot += h->d[j] * h->d[j];
-  }
-  Buf Bs, doff_dev, boffr_dev, zs, pivs;
-  Bs.alloc((size_t)tot * sizeof(Tr));
-  upload(doff_dev, doff, st);
-  upload(boffr_dev, boffr, st);
-  std::vector<cx<double>> zsig = {cx<double>(sigma, 0.0)};
-  upload(zs, zsig, st);
-  pivs.alloc((size_t)dsum * sizeof(int));
-  // assemble_blocks without border: D_j = d_j, and the same row mapping
-  assemble_blocks<Tr>(st, h->P, h->dd, doff_dev.as<int64_t>(), dsum, boffr_dev.as<int64_t>(), zs.as<cx<double>>(), 1,
-                      Bs.as<Tr>(), false);
-  std::vector<LuItem<Tr>> items;
-  for (int j = 0; j < p; ++j) {
-    LuItem<Tr> it;
-    it.A = Bs.as<Tr>() + boffr[j];
-    it.piv = pivs.as<int>() + h->off[j];
-    it.dp = it.D = it.ld = (int)h->d[j];
-    items.push_back(it);
-  }
-  lu_batched<Tr>(st, items, NBO_LU, h->status.as<int>());
-  // inverted diagonal blocks for the many solves of the subspace iteration and the chains
-  std::vector<int64_t> rinvoff(p + 1, 0);
-  for (int j = 0; j < p; ++j) rinvoff[j + 1] = rinvoff[j] + block_inverse_elems(h->d[j], NBO);
-  Buf RLinv, RUinv;
-  RLinv.alloc((size_t)rinvoff[p] * sizeof(Tr));
-  RUinv.alloc((size_t)rinvoff[p] * sizeof(Tr));
-  {
-    std::vector<SolveItem<Tr>> fi;
-    std::vector<Tr *> li, ui;
-    for (int j = 0; j < p; ++j) {
-      SolveItem<Tr> x;
-      x.LU = Bs.as<Tr>() + boffr[j];
-      x.piv = nullptr;
-      x.n = x.ld = (int)h->d[j];
-      x.X = nullptr;
-      x.ldx = x.ncols = 0;
-      fi.push_back(x);
-      li.push_back(RLinv.as<Tr>() + rinvoff[j]);
-      ui.push_back(RUinv.as<Tr>() + rinvoff[j]);
-    }
-    lu_block_inverses<Tr>(st, fi, NBO, li, ui);
-  }
-  sync_status(h, "interior LU");
+  // B_sigma^(j) dense (real), its LU and inverted diagonal blocks: started at the beginning of
+  // the solve on the second stream, or computed here
+  const bool forked = h->I_forked;
+  interior_join(h);
+  if (!(h->I_ready && h->I_sigma == sigma && h->I_tsize == sizeof(Tr))) interior_factor_start<Tr>(h, sigma, st);
+  h->I_ready = false;  // consumed: the next solve factors again
+  Buf &Bs = h->IBs, &pivs = h->Ipiv, &RLinv = h->IRLinv, &RUinv = h->IRUinv;
+  const std::vector<int64_t> &boffr = h->I_boffr, &rinvoff = h->I_rinvoff;
+  sync_status(h, "interior LU", forked && h->I_status.p ? &h->I_status : nullptr);
   auto solve_Bs = [&](double *X, int64_t ldx, int64_t m) {  // X (dsum x m FP64, all subdomains) <- B_sigma^{-1} X
     Buf t;
     t.alloc((size_t)dsum * m * sizeof(Tr));
@@ -1980,6 +2064,18 @@ void run_solve(rfdd_handle *h, double alpha, double beta, int nc, rfdd_result *r
   h->alpha = alpha;
   h->beta = beta;
   h->have_interval = true;
+  const double sigma = std::isnan(h->opt.sigma) ? 0.5 * (alpha + beta) : h->opt.sigma;
+  {
+    // the real B_sigma factorisation needs neither the complex factors nor the Lanczos basis:
+    // start it on the second stream so that it fills the gaps of the next two steps
+    if (!h->st2) {
+      RFDD_CUDA(cudaStreamCreateWithFlags(&h->st2, cudaStreamNonBlocking));
+      RFDD_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+      RFDD_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    }
+    if (is_mixed(h)) interior_factor_start<float>(h, sigma, h->st2);
+    else interior_factor_start<double>(h, sigma, h->st2);
+  }
   {
     Timer t(h->st);
     factor(h);
@@ -1992,7 +2088,6 @@ void run_solve(rfdd_handle *h, double alpha, double beta, int nc, rfdd_result *r
     res->info.t_lanczos_ms = t.ms();
     res->info.mu = h->mu;
   }
-  const double sigma = std::isnan(h->opt.sigma) ? 0.5 * (alpha + beta) : h->opt.sigma;
   {
     Timer t(h->st);
     if (is_mixed(h)) interior_impl<float>(h, sigma);
@@ -2140,6 +2235,14 @@ int rfdd_layout(const rfdd_handle *h, int64_t *off, int64_t *perm, int32_t *p_ou
 
 void rfdd_destroy(rfdd_handle *h) {
   if (!h) return;
+  if (h->I_thread.joinable()) h->I_thread.join();
+  if (h->st2) {
+    cudaStreamSynchronize(h->st2);
+    cudaStreamDestroy(h->st2);
+    h->st2 = nullptr;
+  }
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   if (h->st) cudaStreamSynchronize(h->st);
   cudaStream_t st = h->st;
   bool own = h->own_stream;
@@ -2372,13 +2475,17 @@ int rfdd_solve_async(rfdd_handle *h, double alpha, double beta, int32_t n_nodes,
   if (!r) return RFDD_ENOMEM;
   if (stream) h->st = (cudaStream_t)stream;
   r->ready.store(0);
-  r->worker = std::thread([h, alpha, beta, n_nodes, r] {
-    int device = 0;
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) {
+    cudaGetLastError();
+    device = 0;
+  }
+  r->worker = std::thread([h, alpha, beta, n_nodes, r, device] {
     int rc = guarded([&] {
+      RFDD_CUDA(cudaSetDevice(device));
       AllocScope scope(h->st);
       run_solve(h, alpha, beta, n_nodes, r);
     });
-    (void)device;
     if (rc != RFDD_OK) r->ready.store(-rc);
     else r->ready.store(1);
   });
@@ -2531,8 +2638,47 @@ int rfdd_profile(int32_t enable) {
     g_prof_pool.push_back(r.b);
   }
   g_prof.clear();
-  g_prof_on = enable != 0;
+  if (enable) {
+    // time origin for rfdd_profile_busy: recorded and completed before any launch that follows
+    return guarded([&] {
+      if (!g_prof_ref) RFDD_CUDA(cudaEventCreate(&g_prof_ref));
+      RFDD_CUDA(cudaEventRecord(g_prof_ref, 0));
+      RFDD_CUDA(cudaEventSynchronize(g_prof_ref));
+      g_prof_on = true;
+    });
+  }
+  g_prof_on = false;
   return RFDD_OK;
+}
+
+int rfdd_profile_busy(int32_t kind, double *busy_ms) {
+  if (!busy_ms) return RFDD_EINVAL;
+  return guarded([&] {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    *busy_ms = 0.0;
+    std::vector<std::pair<double, double>> iv;
+    for (auto &r : g_prof) {
+      if (r.kind != kind) continue;
+      RFDD_REQUIRE(g_prof_ref, RFDD_ESTATE, "profile_busy: no recording started");
+      RFDD_CUDA(cudaEventSynchronize(r.b));
+      float a = 0.f, b = 0.f;
+      RFDD_CUDA(cudaEventElapsedTime(&a, g_prof_ref, r.a));
+      RFDD_CUDA(cudaEventElapsedTime(&b, g_prof_ref, r.b));
+      iv.push_back({(double)a, (double)std::max(a, b)});
+    }
+    std::sort(iv.begin(), iv.end());
+    double lo = 0.0, hi = -1.0;  // the current merged interval
+    for (auto &x : iv) {
+      if (x.first > hi) {
+        if (hi > lo) *busy_ms += hi - lo;
+        lo = x.first;
+        hi = x.second;
+      } else {
+        hi = std::max(hi, x.second);
+      }
+    }
+    if (hi > lo) *busy_ms += hi - lo;
+  });
 }
 
 int rfdd_profile_get(int32_t kind, int64_t *launches, double *ms, double *flops) {

@@ -21,6 +21,7 @@
 #include "tc_gemm.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 #include <mutex>
 
@@ -507,7 +508,7 @@ bool tc_enabled() {
   return on != 0;
 }
 
-static int g_tc_attr_done = 0;
+static std::atomic<int> g_tc_attr_done{0};  // set once; several host threads may launch
 
 int tc_take_error() {
   int v = 0, z = 0;
