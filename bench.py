@@ -103,22 +103,33 @@ class ClockSampler:
 # DRAM traffic of the dominant kernel (tc_gemm_kernel) per launch, from one ncu capture of
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none -k regex:tc_gemm \
 #       --csv --log-file tc_traffic.csv python bench.py --mode one-solve
-# (3736 launches, 3802.5 GB; profiles/launches_q1_3d_40.md).  It describes the launch mix of the
-# sources it was taken with, so it is reported only while the CUDA sources hash to the same value.
+# (3736 launches, 3820.7 GB; profiles/launches_q1_3d_40.md).  The figure depends on the kernel's
+# code and on the launches a solve makes, so it is reported only while both are unchanged: the
+# kernel's sources hash to the value below, and the timed steps make the same number of launches
+# with the same algorithmic flops per solve.
 TC_TRAFFIC_BYTES_PER_LAUNCH = 1022.67e6
-TC_TRAFFIC_SOURCES_SHA256 = "e20768001bcbb33d7d870b0631fb365c83e51b65f5a4a8f1d09d6720c89ffaae"
+TC_TRAFFIC_KERNEL_SOURCES = ("common.cuh", "dense.cuh", "tc_gemm.cuh", "tc_gemm.cu")
+TC_TRAFFIC_SOURCES_SHA256 = "e6fc40d49239c4e3162190abe20cee47361091dd0063d462bd09f41b4624e2ba"
+TC_TRAFFIC_LAUNCHES_PER_SOLVE = 3736
+TC_TRAFFIC_FLOPS_PER_SOLVE = 1.94957959198464e14
 
 
-def cuda_sources_sha256() -> str:
-    import glob
+def kernel_sources_sha256(names=TC_TRAFFIC_KERNEL_SOURCES) -> str:
     import hashlib
     root = os.path.join(ROOT, "paper_1711_09487_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(root, "*.cu")) + glob.glob(os.path.join(root, "*.cuh"))):
-        h.update(os.path.basename(f).encode())
-        with open(f, "rb") as fh:
+    for name in names:
+        h.update(name.encode())
+        with open(os.path.join(root, name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
+
+
+def tc_traffic_valid(launches_per_solve: float, flops_per_solve: float) -> bool:
+    """True while the captured traffic still describes the launches being timed."""
+    return (kernel_sources_sha256() == TC_TRAFFIC_SOURCES_SHA256
+            and launches_per_solve == TC_TRAFFIC_LAUNCHES_PER_SOLVE
+            and abs(flops_per_solve - TC_TRAFFIC_FLOPS_PER_SOLVE) <= 1e-9 * TC_TRAFFIC_FLOPS_PER_SOLVE)
 
 
 def measured_peaks():
@@ -307,7 +318,8 @@ def run_ours(args, rank, world, local_rank):
     if t_launch > 0:
         ach = t_flops / (t_busy / 1e3) / 1e12
         peak = float(peaks["bf16_tflops_sustained"]) * (1.1 / 2.25) / 3.0
-        traffic = TC_TRAFFIC_BYTES_PER_LAUNCH if cuda_sources_sha256() == TC_TRAFFIC_SOURCES_SHA256 else None
+        traffic = (TC_TRAFFIC_BYTES_PER_LAUNCH
+                   if tc_traffic_valid(t_launch / args.steps, t_flops / args.steps) else None)
         roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                 "traffic": traffic, "traffic_unit": "DRAM bytes per launch, mean over one solve's launches",
                 # the same fraction counted in executed TF32 tensor work: the 3xTF32 split issues

@@ -219,6 +219,25 @@ int rfdd_rayleigh_ritz(rfdd_handle *h, int64_t cap, double *theta_out, int64_t *
  * RFDD_ESINGULAR when sigma is an eigenvalue of a block B^(j) (choose another sigma). */
 int rfdd_inertia(rfdd_handle *h, double sigma, int64_t *count);
 
+/* Interior polish of approximate eigenpairs (Section 3, Eqs. (schur_eigvec2) and
+ * (compute_u_parallel): once the interface part y of an eigenvector is known, its interior part
+ * follows from one real solve per subdomain).  For each pair i it keeps the interface rows y of
+ * column i of X and replaces the interior rows of every subdomain j by the solution u_j of
+ *   (B_j - lambda_i M_B^(j)) u_j = -(E_j - lambda_i M_E^(j)) y_j,
+ * each block factored by FP64 dense LU with partial pivoting, all (i, j) batched.  Then it
+ * M-normalises the column, replaces lambda_i by its Rayleigh quotient x^T A x / x^T M x, and
+ * writes resid_i = ||A x - lambda_i M x|| / (|lambda_i| ||M x||).  The result is exact when y is
+ * the interface part of an exact eigenvector; its accuracy otherwise follows that of y.
+ * X: host, n x nev row-major in the original ordering (the layout rfdd_result_get returns),
+ * updated in place; lambda: host, nev, updated; resid: host, nev, written.  Needs only
+ * rfdd_setup; uses the handle's stream.  Device memory: 6 n x nev FP64 arrays plus the dense
+ * blocks of as many pairs at a time as fit in 4 GiB (or in half of opt.mem_budget when set),
+ * at least one pair.
+ * RFDD_ESINGULAR when some B_j - lambda_i M_B^(j) has a zero pivot (lambda_i an eigenvalue of a
+ * subdomain pencil) or a column has a zero vector after the polish; RFDD_EINVAL for nev < 0,
+ * null arrays or a non-finite lambda_i. */
+int rfdd_polish(rfdd_handle *h, int64_t nev, double *lambda, double *X, double *resid);
+
 /* a9 building block (Alg. 3 step 7 solves its projected problem with a dense symmetric/* a9 building block (Alg. 3 step 7 solves its projected problem with a dense symmetric
  * eigensolver): eigen-decomposition of a dense symmetric n x n FP64 matrix H on the GPU by
  * Householder tridiagonalisation, bisection on Sturm counts, inverse iteration (clusters

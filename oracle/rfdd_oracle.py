@@ -14,7 +14,9 @@ are silent or ambiguous are marked "Reading:".
 Pins (see tests/test_oracle_*.py): closed-form Q1 spectra, the Midpoint-filter closed form,
 Gauss-Legendre exactness, the (2,2)-block identity of Eq. (finalizing), the block inverse of
 Eq. (inv_dd2) against a dense inverse, Prop. (lowrank), Theorems (uuhat), (uuhat2), (all) at
-tiny n, Sylvester inertia counts, and brute-force dense generalized eigensolves.
+tiny n, Sylvester inertia counts, the interior polish of Eq. (compute_u_parallel) recovering
+dense-eigensolver eigenvectors from their interface rows, and brute-force dense generalized
+eigensolves.
 """
 from __future__ import annotations
 
@@ -422,6 +424,40 @@ def residuals(A, M, lam, X):
     MX = M @ X
     R = AX - MX * lam
     return np.linalg.norm(R, axis=0) / (np.abs(lam) * np.linalg.norm(MX, axis=0))
+
+
+# ----------------------------------------------------------------------------------------
+# Section 3, Eqs. (schur_eigvec2) and (compute_u_parallel): interior part from interface part
+# ----------------------------------------------------------------------------------------
+
+def polish_interior(blk: Blocks, lam, X):
+    """Interior polish of approximate eigenpairs (lam[i], X[:, i]); X is n x nev in the input
+    ordering.  The interface part y of each column is kept, and the interior part of subdomain j
+    is recomputed from Eq. (compute_u_parallel):
+        (B_j - lam_i M_B^(j)) u_j = -(E_j - lam_i M_E^(j)) y.
+    Reading (the paper stops at u): the new vector is then M-normalised and lam_i becomes its
+    Rayleigh quotient x^T A x / x^T M x, with the residual of ``residuals``.
+    Returns (lam', X' in the input ordering, resid)."""
+    X = np.asarray(X, dtype=float)
+    n, nev = X.shape
+    dsum = int(blk.off[-1])
+    Xp = X[blk.perm]                     # interior-first ordering (new -> old)
+    lam_new = np.empty(nev)
+    Xnew = np.empty((n, nev))
+    for i in range(nev):
+        li = float(lam[i])
+        y = Xp[dsum:, i]
+        x = np.empty(n)
+        x[dsum:] = y
+        for j in range(blk.p):
+            lo, hi = blk.off[j], blk.off[j + 1]
+            rhs = -((blk.E[j] - li * blk.ME[j]) @ y)
+            x[lo:hi] = sla.solve(blk.B[j] - li * blk.MB[j], rhs)
+        xMx = x @ (blk.Mp @ x)
+        lam_new[i] = (x @ (blk.Ap @ x)) / xMx
+        Xnew[:, i] = x / np.sqrt(xMx)
+    resid = residuals(blk.Ap, blk.Mp, lam_new, Xnew)
+    return lam_new, blk.to_original(Xnew), resid
 
 
 # ----------------------------------------------------------------------------------------

@@ -41,6 +41,7 @@ SYMBOLS = [
     "rfdd_filter_apply", "rfdd_lanczos", "rfdd_interior", "rfdd_rayleigh_ritz", "rfdd_solve_async",
     "rfdd_result_ready", "rfdd_memory_estimate", "rfdd_sym_eig", "rfdd_kernel_launches", "rfdd_profile",
     "rfdd_profile_get", "rfdd_profile_busy", "rfdd_cgemm", "rfdd_dgemm", "rfdd_cgemm_noalloc", "rfdd_inertia",
+    "rfdd_polish",
 ]
 
 
@@ -119,6 +120,7 @@ def load(path: str | None = None):
     fp = C.POINTER(C.c_float)
     lib.rfdd_cgemm.argtypes = [i64, i64, i64, fp, i64, fp, i64, fp, i64, C.c_double, C.c_double, i32]
     lib.rfdd_inertia.argtypes = [vp, C.c_double, C.POINTER(i64)]
+    lib.rfdd_polish.argtypes = [vp, i64, dp, dp, dp]
     lib.rfdd_dgemm.argtypes = [i64, i64, i64, i32, dp, i64, i32, dp, i64, dp, i64, C.c_double, C.c_double, i32, i32]
     lib.rfdd_cgemm_noalloc.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, i64, C.c_double, C.c_double, vp]
     lib.rfdd_profile.argtypes = [i32]
@@ -387,6 +389,20 @@ def rfdd_inertia(h: Handle, sigma: float) -> int:
     c = C.c_int64()
     _check(load().rfdd_inertia(h.ptr, float(sigma), C.byref(c)))
     return int(c.value)
+
+
+def rfdd_polish(h: Handle, lam, X):
+    """Interior polish of approximate pairs: (lambda', X', resid) with X (n x nev, original
+    ordering) keeping its interface rows and taking interior rows from the subdomain solves."""
+    lam = np.ascontiguousarray(lam, dtype=np.float64).copy()
+    X = np.ascontiguousarray(X, dtype=np.float64).copy()
+    if X.ndim != 2 or X.shape[0] != h.n or X.shape[1] != lam.shape[0]:
+        raise ValueError("rfdd_polish: X must be n x nev with nev = len(lam)")
+    nev = lam.shape[0]
+    res = np.zeros(nev)
+    fp = lambda a: a.ctypes.data_as(C_double_p)
+    _check(load().rfdd_polish(h.ptr, nev, fp(lam), fp(X), fp(res)))
+    return lam, X, res
 
 
 def rfdd_dgemm(A: np.ndarray, B: np.ndarray, C: np.ndarray, alpha: float = 1.0, beta: float = 0.0,

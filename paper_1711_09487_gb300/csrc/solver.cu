@@ -1478,8 +1478,9 @@ void lanczos_impl(rfdd_handle *h) {
 // a8: interior basis and Z (Eq. trabala, trabala2, z)
 // ------------------------------------------------------------------------------------
 // Waits for an interior factorisation started on the second stream: joins the host thread that
-// launched it (rethrowing its error) and orders the handle's stream after its kernels.
-void interior_join(rfdd_handle *h) {
+// launched it and orders the handle's stream after its kernels.  Its error, if any, is rethrown
+// when the caller is about to use the factors (rethrow), else dropped with the factors.
+void interior_join(rfdd_handle *h, bool rethrow = true) {
   if (h->I_thread.joinable()) h->I_thread.join();
   if (h->I_forked) {
     RFDD_CUDA(cudaStreamWaitEvent(h->st, h->ev_join, 0));
@@ -1489,7 +1490,7 @@ void interior_join(rfdd_handle *h) {
     std::exception_ptr e = h->I_exc;
     h->I_exc = nullptr;
     h->I_ready = false;
-    std::rethrow_exception(e);
+    if (rethrow) std::rethrow_exception(e);
   }
 }
 
@@ -1503,7 +1504,7 @@ template <typename Tr>
 void interior_factor_start(rfdd_handle *h, double sigma, cudaStream_t on) {
   cudaStream_t st = h->st;
   h->I_ready = false;
-  interior_join(h);  // an earlier start that was never consumed (a solve that failed after it)
+  interior_join(h, false);  // an earlier start that was never consumed (a solve that failed after it)
   const int p = h->p;
   const int64_t dsum = h->dsum;
   std::vector<int64_t> doff(p + 1, 0);
@@ -1931,6 +1932,118 @@ void complete(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
   res->info.max_resid = 0.0;
   for (double v : res->resid) res->info.max_resid = std::max(res->info.max_resid, v);
   res->info.status = converged ? RFDD_OK : RFDD_NOT_CONVERGED;
+}
+
+// ------------------------------------------------------------------------------------
+// Interior polish (Section 3, Eqs. (schur_eigvec2) and (compute_u_parallel)): an eigenvector's
+// interior part follows from its interface part y by one real solve per subdomain,
+// (B_j - lambda M_B^(j)) u_j = -(E_j - lambda M_E^(j)) y_j.  Applied to approximate pairs it
+// replaces the interior rows, then M-normalises and takes the Rayleigh quotient.  FP64.
+// ------------------------------------------------------------------------------------
+void polish_impl(rfdd_handle *h, int64_t nev, double *lam, double *Xh, double *resid) {
+  cudaStream_t st = h->st;
+  const int p = h->p;
+  const int64_t n = h->n, dsum = h->dsum;
+  for (int64_t c = 0; c < nev; ++c)
+    RFDD_REQUIRE(std::isfinite(lam[c]), RFDD_EINVAL, "polish: non-finite eigenvalue");
+  // interior-first ordering: Xi[k][c] = X[perm[k]][c]
+  Buf Xo, Xi, permd, lamd, R;
+  Xo.alloc((size_t)n * nev * sizeof(double));
+  Xi.alloc((size_t)n * nev * sizeof(double));
+  RFDD_CUDA(cudaMemcpyAsync(Xo.p, Xh, (size_t)n * nev * sizeof(double), cudaMemcpyHostToDevice, st));
+  upload(permd, h->perm, st);
+  gather_rows_f64(st, Xo.as<double>(), nev, permd.as<int64_t>(), Xi.as<double>(), nev, n, nev);
+  std::vector<double> lv(lam, lam + nev);
+  upload(lamd, lv, st);
+  // right-hand sides of every subdomain at once (interior rows): lambda_c M_E y_c - E y_c
+  R.alloc((size_t)std::max<int64_t>(1, dsum) * nev * sizeof(double));
+  const double *Y = Xi.as<double>() + dsum * nev;
+  spmm_f64(st, h->P, 0, dsum, dsum, n, 0.0, 1.0, Y, nev, R.as<double>(), nev, nev, false);
+  scale_cols_f64(st, R.as<double>(), dsum, nev, nev, lamd.as<double>());
+  spmm_f64(st, h->P, 0, dsum, dsum, n, -1.0, 0.0, Y, nev, R.as<double>(), nev, nev, true);
+  // shifted dense blocks, LU and one solve per (pair, subdomain), in chunks of pairs
+  int64_t per_pair = 0;
+  std::vector<int64_t> doff(p + 1, 0), bo(p, 0);
+  for (int j = 0; j < p; ++j) {
+    doff[j + 1] = doff[j] + h->d[j];
+    bo[j] = per_pair;
+    per_pair += h->d[j] * h->d[j];
+  }
+  size_t cap = (size_t)4 << 30;  // dense-block bytes per chunk
+  if (h->opt.mem_budget > 0) cap = std::min(cap, h->opt.mem_budget / 2);
+  const int64_t chunk =
+      std::max<int64_t>(1, std::min<int64_t>({nev, (int64_t)(cap / ((size_t)per_pair * sizeof(double))), 65535}));
+  Buf doff_dev, boff_dev, zs, Bs, piv;
+  upload(doff_dev, doff, st);
+  std::vector<int64_t> boff((size_t)chunk * p);
+  for (int64_t l = 0; l < chunk; ++l)
+    for (int j = 0; j < p; ++j) boff[l * p + j] = l * per_pair + bo[j];
+  upload(boff_dev, boff, st);
+  Bs.alloc((size_t)chunk * per_pair * sizeof(double));
+  piv.alloc((size_t)chunk * std::max<int64_t>(1, dsum) * sizeof(int));
+  for (int64_t c0 = 0; c0 < nev; c0 += chunk) {
+    const int64_t cnt = std::min(chunk, nev - c0);
+    std::vector<cx<double>> z(cnt);
+    for (int64_t l = 0; l < cnt; ++l) z[l] = cx<double>(lam[c0 + l], 0.0);
+    upload(zs, z, st);
+    assemble_blocks<double>(st, h->P, h->dd, doff_dev.as<int64_t>(), dsum, boff_dev.as<int64_t>(),
+                            zs.as<cx<double>>(), (int)cnt, Bs.as<double>(), false);
+    std::vector<LuItem<double>> items;
+    std::vector<SolveItem<double>> si;
+    for (int64_t l = 0; l < cnt; ++l)
+      for (int j = 0; j < p; ++j) {
+        LuItem<double> it;
+        it.A = Bs.as<double>() + boff[l * p + j];
+        it.piv = piv.as<int>() + l * dsum + h->off[j];
+        it.dp = it.D = it.ld = (int)h->d[j];
+        items.push_back(it);
+        SolveItem<double> x;
+        x.LU = it.A;
+        x.piv = it.piv;
+        x.n = x.ld = (int)h->d[j];
+        x.X = R.as<double>() + h->off[j] * nev + (c0 + l);
+        x.ldx = (int)nev;
+        x.ncols = 1;
+        si.push_back(x);
+      }
+    lu_batched<double>(st, items, NBO_LU, h->status.as<int>());
+    lu_solve_batched<double>(st, si, NBO);
+  }
+  sync_status(h, "polish LU");
+  copy_rows_f64(st, R.as<double>(), nev, Xi.as<double>(), nev, dsum, nev);
+  // M-normalise, Rayleigh quotients and residuals
+  Buf AX, MX, dA, dM, scd, thd, rs;
+  AX.alloc((size_t)n * nev * sizeof(double));
+  MX.alloc((size_t)n * nev * sizeof(double));
+  spmm_f64(st, h->P, 0, n, 0, n, 1.0, 0.0, Xi.as<double>(), nev, AX.as<double>(), nev, nev, false);
+  spmm_f64(st, h->P, 0, n, 0, n, 0.0, 1.0, Xi.as<double>(), nev, MX.as<double>(), nev, nev, false);
+  dA.alloc(nev * sizeof(double));
+  dM.alloc(nev * sizeof(double));
+  col_dots(st, Xi.as<double>(), nev, AX.as<double>(), nev, n, nev, dA.as<double>());
+  col_dots(st, Xi.as<double>(), nev, MX.as<double>(), nev, n, nev, dM.as<double>());
+  std::vector<double> xax(nev), xmx(nev), sc(nev), th(nev);
+  RFDD_CUDA(cudaMemcpyAsync(xax.data(), dA.p, nev * sizeof(double), cudaMemcpyDeviceToHost, st));
+  RFDD_CUDA(cudaMemcpyAsync(xmx.data(), dM.p, nev * sizeof(double), cudaMemcpyDeviceToHost, st));
+  RFDD_CUDA(cudaStreamSynchronize(st));
+  for (int64_t c = 0; c < nev; ++c) {
+    RFDD_REQUIRE(xmx[c] > 0.0 && std::isfinite(xmx[c]), RFDD_ESINGULAR,
+                 "polish: vector " + std::to_string(c) + " has no M-norm (zero interface part?)");
+    sc[c] = 1.0 / std::sqrt(xmx[c]);
+    th[c] = xax[c] / xmx[c];
+  }
+  upload(scd, sc, st);
+  upload(thd, th, st);
+  scale_cols_f64(st, Xi.as<double>(), n, nev, nev, scd.as<double>());
+  scale_cols_f64(st, AX.as<double>(), n, nev, nev, scd.as<double>());
+  scale_cols_f64(st, MX.as<double>(), n, nev, nev, scd.as<double>());
+  rs.alloc(nev * sizeof(double));
+  ritz_residuals(st, AX.as<double>(), MX.as<double>(), thd.as<double>(), n, nev, rs.as<double>());
+  // back to the input ordering: X[o][c] = Xi[iperm[o]][c]
+  gather_rows_f64(st, Xi.as<double>(), nev, h->iperm_dev.as<int64_t>(), Xo.as<double>(), nev, n, nev);
+  RFDD_CUDA(cudaMemcpyAsync(Xh, Xo.p, (size_t)n * nev * sizeof(double), cudaMemcpyDeviceToHost, st));
+  RFDD_CUDA(cudaMemcpyAsync(resid, rs.p, nev * sizeof(double), cudaMemcpyDeviceToHost, st));
+  RFDD_CUDA(cudaStreamSynchronize(st));
+  std::copy(th.begin(), th.end(), lam);
 }
 
 // ------------------------------------------------------------------------------------
@@ -2447,6 +2560,16 @@ int rfdd_inertia(rfdd_handle *h, double sigma, int64_t *count) {
   return guarded([&] {
     AllocScope scope(h->st);
     *count = inertia_impl(h, sigma);
+  });
+}
+
+int rfdd_polish(rfdd_handle *h, int64_t nev, double *lambda, double *X, double *resid) {
+  if (!h || nev < 0 || (nev > 0 && (!lambda || !X || !resid))) return RFDD_EINVAL;
+  if (nev == 0) return RFDD_OK;
+  return guarded([&] {
+    AllocScope scope(h->st);
+    interior_join(h, false);  // nothing of a failed solve may still be running on the second stream
+    polish_impl(h, nev, lambda, X, resid);
   });
 }
 
