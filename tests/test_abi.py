@@ -153,3 +153,29 @@ def test_setup_rejects_one_sided_entry(R):
     with pytest.raises(R.RfddError) as e:
         R.rfdd_setup(a, M, part, p)
     assert e.value.code == R.RFDD_ENOTSYM
+
+
+def test_entry_points_reject_null_arguments_without_touching_the_device(R):
+    lib = ctypes.CDLL(R.LIB_PATH)
+    lib.rfdd_polish.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.rfdd_inertia.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]
+    lib.rfdd_profile_busy.argtypes = [ctypes.c_int32, ctypes.c_void_p]
+    lib.rfdd_profile_get.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.rfdd_polish(None, 1, None, None, None) == R.RFDD_EINVAL
+    assert lib.rfdd_inertia(None, 0.5, None) == R.RFDD_EINVAL
+    assert lib.rfdd_profile_busy(1, None) == R.RFDD_EINVAL
+    assert lib.rfdd_profile_get(1, None, None, None) == R.RFDD_EINVAL
+
+
+def test_profile_busy_is_zero_without_records(R):
+    assert R.rfdd_profile_busy(0) == 0.0 and R.rfdd_profile_busy(1) == 0.0
+
+
+def test_polish_wrapper_checks_shapes_before_the_call(R):
+    class FakeHandle:
+        n = 10
+        ptr = None
+    with pytest.raises(ValueError):
+        R.rfdd_polish(FakeHandle(), np.zeros(3), np.zeros((10, 2)))
+    with pytest.raises(ValueError):
+        R.rfdd_polish(FakeHandle(), np.zeros(2), np.zeros((9, 2)))
