@@ -181,6 +181,28 @@ def schur(blk: Blocks, z):
     return S
 
 
+def schur_columns(A, M, part, p, z, cols):
+    """Columns ``cols`` (interface indices, interior-first ordering) of S_z = C_z - E_z^T B_z^{-1} E_z
+    for pencils too large for the dense ``Blocks``: the same definition as ``schur``, with each
+    B_j(z) factored by a sparse LU (SuperLU, a library primitive) and applied to the columns of
+    E_j(z) that are needed.  Returns an s x len(cols) complex array."""
+    from scipy.sparse.linalg import splu
+    A = sp.csr_matrix(A)
+    M = sp.csr_matrix(M)
+    part = np.asarray(part)
+    groups = [np.flatnonzero(part == j) for j in range(p)]
+    iface = np.flatnonzero(part == -1)
+    cols = np.asarray(cols)
+    Az = (A - z * M).tocsr()
+    S = Az[iface][:, iface[cols]].toarray().astype(np.complex128)
+    for j in range(p):
+        Bz = Az[groups[j]][:, groups[j]].tocsc()
+        Ez = Az[groups[j]][:, iface].tocsc()
+        X = splu(Bz).solve(Ez[:, cols].toarray())
+        S -= (Ez.T @ X)
+    return S
+
+
 class Factors:
     """LU factorisations of every B_j(zeta_l) and S(zeta_l) (Algorithm 3 step 5 needs solves with
     them; the paper uses PARDISO/MUMPS, the oracle uses dense LU with partial pivoting)."""

@@ -294,3 +294,16 @@ def test_end_to_end_random_pencil_brute_force(seed):
     Mx = M @ X[:, 41:61]
     C = r["evecs"].T @ Mx
     np.testing.assert_allclose(np.abs(np.diag(C)), 1.0, atol=1e-8)
+
+
+@pytest.mark.parametrize("name", ["q1_3d_12", "q1_2d_33_p9"])
+def test_sparse_schur_columns_match_the_dense_definition(name):
+    """schur_columns (sparse LUs, for pencils too large for dense blocks) is the same S(zeta)."""
+    w = I.workload(name)
+    blk = O.Blocks(w.A.to_scipy(), w.M.to_scipy(), w.part, w.p)
+    z, _ = O.quadrature(w.alpha, w.beta, w.n_nodes, w.rule)
+    cols = [0, 1, blk.s // 2, blk.s - 1]
+    for l in (0, len(z) - 1):
+        Sd = O.schur(blk, z[l])[:, cols]
+        Ss = O.schur_columns(w.A.to_scipy(), w.M.to_scipy(), w.part, w.p, z[l], cols)
+        assert np.abs(Ss - Sd).max() <= 1e-12 * np.abs(Sd).max()
