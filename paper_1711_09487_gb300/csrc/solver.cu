@@ -16,6 +16,7 @@
 #include <memory>
 #include <mutex>
 #include <numeric>
+#include <system_error>
 #include <thread>
 #include <tuple>
 
@@ -1569,17 +1570,23 @@ void interior_factor_start(rfdd_handle *h, double sigma, cudaStream_t on) {
     int device = 0;
     RFDD_CUDA(cudaGetDevice(&device));
     h->I_forked = true;
-    h->I_thread = std::thread([h, on, device, launch] {
-      try {
-        RFDD_CUDA(cudaSetDevice(device));
-        RFDD_CUDA(cudaStreamWaitEvent(on, h->ev_fork, 0));
-        launch(on);
-      } catch (...) {
-        h->I_exc = std::current_exception();
-      }
-      // recorded even after an error, so that interior_join never waits on a stale event
-      cudaEventRecord(h->ev_join, on);
-    });
+    try {
+      h->I_thread = std::thread([h, on, device, launch] {
+        try {
+          RFDD_CUDA(cudaSetDevice(device));
+          RFDD_CUDA(cudaStreamWaitEvent(on, h->ev_fork, 0));
+          launch(on);
+        } catch (...) {
+          h->I_exc = std::current_exception();
+        }
+        // recorded even after an error, so that interior_join never waits on a stale event
+        cudaEventRecord(h->ev_join, on);
+      });
+    } catch (const std::system_error &) {  // no thread to be had: the same launches from here
+      RFDD_CUDA(cudaStreamWaitEvent(on, h->ev_fork, 0));
+      launch(on);
+      RFDD_CUDA(cudaEventRecord(h->ev_join, on));
+    }
   }
   h->I_sigma = sigma;
   h->I_tsize = sizeof(Tr);
@@ -1602,7 +1609,8 @@ void interior_impl(rfdd_handle *h, double sigma) {
   h->I_ready = false;  // consumed: the next solve factors again
   Buf &Bs = h->IBs, &pivs = h->Ipiv, &RLinv = h->IRLinv, &RUinv = h->IRUinv;
   const std::vector<int64_t> &boffr = h->I_boffr, &rinvoff = h->I_rinvoff;
-  sync_status(h, "interior LU", forked && h->I_status.p ? &h->I_status : nullptr);
+  sync_status(h, "interior LU");
+  if (forked && h->I_status.p) sync_status(h, "interior LU", &h->I_status);
   auto solve_Bs = [&](double *X, int64_t ldx, int64_t m) {  // X (dsum x m FP64, all subdomains) <- B_sigma^{-1} X
     Buf t;
     t.alloc((size_t)dsum * m * sizeof(Tr));
