@@ -516,7 +516,9 @@ def rfdd_solve(A, M, part, p, alpha, beta, n_nodes=4, rule="midpoint", sigma=Non
 
     Readings:
     * sigma defaults to (alpha+beta)/2 (the paper's default is 0; the theory favours sigma
-      near the wanted eigenvalues).
+      near the wanted eigenvalues).  Guard: while sigma lies within 1e-8 max(1, |sigma|) of an
+      eigenvalue of some (B_j, M_B^(j)), B_sigma is (nearly) singular and sigma moves by
+      1e-6 (beta - alpha), at most three times.
     * nev_B^(j) = min(nev_b, d_j).
     * Completion (accuracy contract beyond the paper): X <- 2 Re sum omega (A - zeta M)^{-1} M X
       through Eq. (inv_dd2) with the same factors, then M-orthonormalisation and Rayleigh-Ritz;
@@ -530,6 +532,12 @@ def rfdd_solve(A, M, part, p, alpha, beta, n_nodes=4, rule="midpoint", sigma=Non
     if sigma is None:
         sigma = 0.5 * (alpha + beta)
     blk = Blocks(A, M, part, p)                                   # step 1
+    for _ in range(3):
+        gap = min(np.abs(sla.eigh(blk.B[j] - sigma * blk.MB[j], blk.MB[j], eigvals_only=True)).min()
+                  for j in range(p))
+        if gap >= 1e-8 * max(1.0, abs(sigma)):
+            break
+        sigma += 1e-6 * (beta - alpha)
     z, w = quadrature(alpha, beta, n_nodes, rule)
     fac = Factors(blk, z)
     V = interior_eigvecs(blk, sigma, nev_b)                       # steps 2-4

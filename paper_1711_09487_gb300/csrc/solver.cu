@@ -15,6 +15,7 @@
 #include <exception>
 #include <memory>
 #include <mutex>
+#include <limits>
 #include <numeric>
 #include <system_error>
 #include <thread>
@@ -288,6 +289,7 @@ struct rfdd_handle {
   int64_t kz = 0, kappa = 0;
   std::vector<int64_t> voff;  // V_j occupies Z columns [voff[j], voff[j+1])
   double sigma_used = 0.0;
+  double interior_gap = 0.0;  // min over subdomains of |delta - sigma| seen by the last interior step
   // Rayleigh-Ritz (a9)
   std::vector<double> rr_theta;
   Buf X0;
@@ -1711,6 +1713,10 @@ void interior_impl(rfdd_handle *h, double sigma) {
   std::vector<double> ev((size_t)p * mw);
   RFDD_CUDA(cudaMemcpyAsync(ev.data(), el.p, ev.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
   RFDD_CUDA(cudaStreamSynchronize(st));
+  // Ritz values of (B_sigma, M_B) on span X_j: delta - sigma for the delta nearest sigma
+  h->interior_gap = std::numeric_limits<double>::infinity();
+  for (int j = 0; j < p; ++j)
+    for (int64_t c = 0; c < mb[j]; ++c) h->interior_gap = std::min(h->interior_gap, std::fabs(ev[j * mw + c]));
   Buf Gt;
   Gt.alloc((size_t)p * mw * mw * sizeof(double));
   std::vector<BackItem> bi;
@@ -2211,8 +2217,24 @@ void run_solve(rfdd_handle *h, double alpha, double beta, int nc, rfdd_result *r
   }
   {
     Timer t(h->st);
-    if (is_mixed(h)) interior_impl<float>(h, sigma);
-    else interior_impl<double>(h, sigma);
+    // Guard on the shift: sigma at, or within 1e-8 max(1, |sigma|) of, an eigenvalue of some
+    // pencil (B_j, M_B^(j)) leaves B_sigma (nearly) singular.  The shift then moves by
+    // 1e-6 (beta - alpha) and the interior step is redone, at most three times.
+    double sig = sigma;
+    for (int attempt = 0;; ++attempt) {
+      bool near = false;
+      try {
+        if (is_mixed(h)) interior_impl<float>(h, sig);
+        else interior_impl<double>(h, sig);
+        near = h->interior_gap < 1e-8 * std::max(1.0, std::fabs(sig));
+      } catch (const Error &e) {
+        if (e.code != RFDD_ESINGULAR || attempt >= 3) throw;
+        near = true;
+      }
+      if (!near || attempt >= 3) break;
+      RFDD_LOGF("interior: sigma %.17g within %.3e of a subdomain eigenvalue, moved", sig, h->interior_gap);
+      sig += 1e-6 * (beta - alpha);
+    }
     res->info.t_interior_ms = t.ms();
   }
   {

@@ -296,6 +296,27 @@ def test_end_to_end_random_pencil_brute_force(seed):
     np.testing.assert_allclose(np.abs(np.diag(C)), 1.0, atol=1e-8)
 
 
+def test_sigma_guard_moves_a_shift_on_a_subdomain_eigenvalue():
+    """sigma exactly at an eigenvalue of (B_0, M_B^(0)): the guard moves it by 1e-6 (beta - alpha)
+    and the solve still returns the brute-force eigenpairs; a shift away from the subdomain
+    spectra is kept."""
+    A, M, part, p = random_pencil(N=12, splits=(3, 2), seed=11)
+    lam, _ = dense_eig(A, M)
+    alpha, beta = 0.5 * (lam[40] + lam[41]), 0.5 * (lam[60] + lam[61])
+    blk = O.Blocks(A, M, part, p)
+    d0 = sla.eigh(blk.B[0], blk.MB[0], eigvals_only=True)
+    sig = float(d0[np.argmin(np.abs(d0 - 0.5 * (alpha + beta)))])
+    r = O.rfdd_solve(A, M, part, p, alpha, beta, 6, "midpoint", sigma=sig, nev_b=10, block=2)
+    assert r["sigma"] == sig + 1e-6 * (beta - alpha)
+    assert r["converged"]
+    np.testing.assert_allclose(r["evals"], lam[41:61], rtol=1e-10)
+    sub = np.concatenate([sla.eigh(blk.B[j], blk.MB[j], eigvals_only=True) for j in range(p)])
+    far = 0.5 * (alpha + beta)
+    assert np.abs(sub - far).min() > 1e-6 * abs(far)
+    r2 = O.rfdd_solve(A, M, part, p, alpha, beta, 6, "midpoint", sigma=far, nev_b=10, block=2)
+    assert r2["sigma"] == far
+
+
 @pytest.mark.parametrize("name", ["q1_3d_12", "q1_2d_33_p9"])
 def test_sparse_schur_columns_match_the_dense_definition(name):
     """schur_columns (sparse LUs, for pencils too large for dense blocks) is the same S(zeta)."""
