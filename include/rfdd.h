@@ -11,16 +11,20 @@
  *    owns is modified, except output buffers of the failing call may hold partial data; the
  *    message of the last error on the calling thread is available from rfdd_last_error().
  *  - Sparse inputs are full (both triangles) CSR with int64 row pointers, int32 column indices
- *    (sorted within each row) and float64 values, in HOST memory.  They are copied at setup;
- *    the caller keeps ownership.
+ *    (in any order within a row, no duplicates) and float64 values, in HOST memory.  They are
+ *    copied at setup; the caller keeps ownership.
  *  - Dense host arrays are row-major.  Complex values are interleaved (re, im) float64 pairs.
  *  - "Interior-first ordering" (Eq. dd1): the interior unknowns of subdomain 0, 1, ..., p-1
  *    (each in increasing original index), then the interface unknowns (label -1) in increasing
  *    original index.  Subdomain j occupies rows [off_j, off_j + d_j); the interface occupies the
  *    last s rows.  rfdd_layout() returns off_j, d_j, s and the permutation.
  *  - Every call runs on the handle's CUDA stream and returns after its results are complete,
- *    except rfdd_solve_async().
- *  - A handle is not thread-safe; distinct handles may be used from different threads.
+ *    except rfdd_solve_async().  A solve also runs the real interior factorisation (a8) on a
+ *    second stream that the handle creates and owns, launched from a host thread of its own and
+ *    joined before the call returns or fails.
+ *  - A handle is not thread-safe; distinct handles may be used from different threads.  The
+ *    tensor-core kernels share one device error flag (a wait that ran out of iterations), so
+ *    such an error is reported by whichever handle checks it first.
  */
 #ifndef RFDD_H
 #define RFDD_H

@@ -464,7 +464,7 @@ void check_symmetric(const rfdd_csr *A, const char *name) {
     }
   // row i of A^T: entries (trow, tval) in [cnt[i], cnt[i+1]), already in increasing row order;
   // compare with row i of A as sorted sets
-  std::atomic<int> bad{0};  // 1: pattern, 2: values
+  std::atomic<int> bad{0};  // 1: pattern, 2: values, 3: a column twice in one row
   parallel_rows(n, [&](int64_t r0, int64_t r1, int) {
     std::vector<std::pair<int64_t, double>> ra;
     for (int64_t i = r0; i < r1 && !bad.load(std::memory_order_relaxed); ++i) {
@@ -472,6 +472,11 @@ void check_symmetric(const rfdd_csr *A, const char *name) {
       for (int64_t e = A->rowptr[i]; e < A->rowptr[i + 1]; ++e) ra.push_back({A->col[e], A->val[e]});
       if (!std::is_sorted(ra.begin(), ra.end(), [](auto &x, auto &y) { return x.first < y.first; }))
         std::sort(ra.begin(), ra.end());
+      for (size_t k = 1; k < ra.size(); ++k)
+        if (ra[k].first == ra[k - 1].first) {
+          bad = 3;
+          return;
+        }
       if ((int64_t)ra.size() != cnt[i + 1] - cnt[i]) {
         bad = 1;
         return;
@@ -490,6 +495,7 @@ void check_symmetric(const rfdd_csr *A, const char *name) {
       }
     }
   });
+  RFDD_REQUIRE(bad != 3, RFDD_EINVAL, std::string(name) + ": a column appears twice in one row");
   RFDD_REQUIRE(bad != 1, RFDD_ENOTSYM, std::string(name) + " is not symmetric (pattern)");
   RFDD_REQUIRE(bad != 2, RFDD_ENOTSYM, std::string(name) + " is not symmetric (values)");
 }

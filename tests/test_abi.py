@@ -179,3 +179,19 @@ def test_polish_wrapper_checks_shapes_before_the_call(R):
         R.rfdd_polish(FakeHandle(), np.zeros(3), np.zeros((10, 2)))
     with pytest.raises(ValueError):
         R.rfdd_polish(FakeHandle(), np.zeros(2), np.zeros((9, 2)))
+
+
+def test_setup_rejects_duplicate_entries(R):
+    A, M, part, p = _small()
+    rp, col, val = A.rowptr.copy(), A.col.copy(), A.val.copy()
+    # row 0 stores its diagonal twice (the value split in halves): same matrix, invalid CSR
+    a, b = rp[0], rp[1]
+    k = a + int(np.flatnonzero(col[a:b] == 0)[0])
+    col2 = np.insert(col, k + 1, 0)
+    val2 = np.insert(val, k + 1, 0.5 * val[k])
+    val2[k] *= 0.5
+    rp2 = rp.copy()
+    rp2[1:] += 1
+    with pytest.raises(R.RfddError) as e:
+        R.rfdd_setup(I.Csr(A.n, rp2, col2, val2), M, part, p)
+    assert e.value.code == R.RFDD_EINVAL
