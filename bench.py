@@ -135,7 +135,8 @@ def tc_traffic_valid(launches_per_solve: float, flops_per_solve: float) -> bool:
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
-        return json.load(open(p)), "measured"
+        with open(p) as f:
+            return json.load(f), "measured"
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
         "fallback"
 

@@ -1,0 +1,43 @@
+"""Host-side pieces of bench.py that need no GPU: the workload description of the JSON line, the
+measured-peak lookup, and the rule that reports the captured DRAM traffic only while the
+kernel's sources and the timed launches match the capture."""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+import rfdd_inputs as I  # noqa: E402
+
+
+def test_workload_config_names_the_workload():
+    w = I.workload("q1_3d_40")
+    c = bench.workload_config(w, "mixed")
+    assert c["name"] == "q1_3d_40" and c["n"] == 64000 and c["p"] == 8 and c["nev"] == 202
+    assert c["n_nodes"] == 8 and c["precision"] == "mixed"
+    assert "40x40x40" in c["workload"] and "model" not in c
+
+
+def test_measured_peaks_has_the_denominators():
+    peaks, src = bench.measured_peaks()
+    assert src in ("measured", "fallback")
+    for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained"):
+        assert float(peaks[k]) > 0
+
+
+def test_traffic_reported_only_for_the_captured_kernel_and_launches(monkeypatch):
+    monkeypatch.setattr(bench, "TC_TRAFFIC_SOURCES_SHA256", bench.kernel_sources_sha256())
+    n, f = bench.TC_TRAFFIC_LAUNCHES_PER_SOLVE, bench.TC_TRAFFIC_FLOPS_PER_SOLVE
+    assert bench.tc_traffic_valid(n, f)
+    assert bench.tc_traffic_valid(n, f * (1 + 1e-12))      # summation order of the flop count
+    assert not bench.tc_traffic_valid(n + 1, f)            # a different launch mix
+    assert not bench.tc_traffic_valid(n, f * (1 + 1e-6))   # different shapes
+    monkeypatch.setattr(bench, "TC_TRAFFIC_SOURCES_SHA256", "0" * 64)
+    assert not bench.tc_traffic_valid(n, f)                # the kernel changed
+
+
+def test_kernel_hash_covers_the_kernel_sources():
+    h = bench.kernel_sources_sha256()
+    assert h == bench.kernel_sources_sha256() and len(h) == 64
+    assert bench.kernel_sources_sha256(("tc_gemm.cu",)) != h
