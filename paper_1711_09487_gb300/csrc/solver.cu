@@ -1611,14 +1611,16 @@ void interior_impl(rfdd_handle *h, double sigma) {
   h->sigma_used = sigma;
   // B_sigma^(j) dense (real), its LU and inverted diagonal blocks: started at the beginning of
   // the solve on the second stream, or computed here
-  const bool forked = h->I_forked;
-  interior_join(h);
+  // factors started on the second stream are used when they are for this shift and type; only
+  // then does their launch error or pivot status concern this call
+  const bool use_forked = h->I_forked && h->I_ready && h->I_sigma == sigma && h->I_tsize == sizeof(Tr);
+  interior_join(h, use_forked);
   if (!(h->I_ready && h->I_sigma == sigma && h->I_tsize == sizeof(Tr))) interior_factor_start<Tr>(h, sigma, st);
   h->I_ready = false;  // consumed: the next solve factors again
   Buf &Bs = h->IBs, &pivs = h->Ipiv, &RLinv = h->IRLinv, &RUinv = h->IRUinv;
   const std::vector<int64_t> &boffr = h->I_boffr, &rinvoff = h->I_rinvoff;
   sync_status(h, "interior LU");
-  if (forked && h->I_status.p) sync_status(h, "interior LU", &h->I_status);
+  if (use_forked && h->I_status.p) sync_status(h, "interior LU", &h->I_status);
   auto solve_Bs = [&](double *X, int64_t ldx, int64_t m) {  // X (dsum x m FP64, all subdomains) <- B_sigma^{-1} X
     Buf t;
     t.alloc((size_t)dsum * m * sizeof(Tr));
