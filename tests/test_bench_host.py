@@ -41,3 +41,11 @@ def test_kernel_hash_covers_the_kernel_sources():
     h = bench.kernel_sources_sha256()
     assert h == bench.kernel_sources_sha256() and len(h) == 64
     assert bench.kernel_sources_sha256(("tc_gemm.cu",)) != h
+
+
+def test_reference_arm_other_ranks_exit_without_work():
+    import subprocess
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                        "--steps", "1", "--warmup", "0"], env=env, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == ""
