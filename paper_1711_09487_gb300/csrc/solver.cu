@@ -2275,6 +2275,9 @@ int guarded(F &&f) {
   } catch (const std::exception &e) {
     g_last_error = e.what();
     return RFDD_ECUDA;
+  } catch (...) {  // nothing may unwind through the C ABI
+    g_last_error = "unknown error";
+    return RFDD_ECUDA;
   }
 }
 
