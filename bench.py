@@ -414,7 +414,7 @@ def main():
     ap.add_argument("--mode", default="bench", choices=["bench", "one-solve", "gemm", "dgemm"])
     ap.add_argument("--gemm", type=int, nargs=3, default=[8192, 8192, 128], metavar=("M", "N", "K"))
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
