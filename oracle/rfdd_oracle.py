@@ -282,7 +282,8 @@ def lanczos_interface(apply_F, s, tol=1e-6, block=1, seed=1, check_every=10, max
     * lines 4-6 (one classical Gram-Schmidt pass) are run twice ("CGS2"); no effect in exact
       arithmetic, keeps ||Q^T Q - I|| at rounding level.
     * line 13: every ``check_every`` vectors (ceil(check_every / b) block steps) stop when
-      |tr T_mu - tr T_(mu - check_every)| <= tol * |tr T_mu|; also stop once mu = s.
+      |tr T_mu - tr T_(mu - check_every)| <= tol * |tr T_mu|; also stop once mu = s, the last
+      block keeping only the s - mu columns that still fit.
     * breakdown (line 8): ||w|| <= 1e-14 max|a| -> new random vectors orthogonal to Q.
     """
     b = block
@@ -306,13 +307,18 @@ def lanczos_interface(apply_F, s, tol=1e-6, block=1, seed=1, check_every=10, max
         alphas.append(Amu)
         trace += float(np.trace(Amu))
         traces.append(trace)
-        if mu * b >= s:
+        ncols = sum(q.shape[1] for q in Qs)
+        if ncols >= s:                                          # mu = s: the space is exhausted
             break
+        # Reading: a block that would pass mu = s keeps its leading s - mu columns
+        bn = min(b, s - ncols)
+        Wfull = W
+        W = W[:, :bn]
         Qn, R = np.linalg.qr(W)                                 # lines 7-12
         amax = max(np.max(np.abs(np.diag(A_))) for A_ in alphas)
         dead = np.abs(np.diag(R)) <= 1e-14 * max(amax, 1e-300)
         if np.any(dead):
-            fresh = counter_uniform(seed, extra, s * b).reshape(s, b)
+            fresh = counter_uniform(seed, extra, s * bn).reshape(s, bn)
             extra += 1
             fresh = _orth_against(Qs, fresh)
             Qf, _ = np.linalg.qr(fresh)
@@ -324,7 +330,7 @@ def lanczos_interface(apply_F, s, tol=1e-6, block=1, seed=1, check_every=10, max
         # pass after normalisation restores orthogonality (the "twice is enough" rule)
         Qn = _orth_against(Qs, Qn, passes=1)
         Qn, R2 = np.linalg.qr(Qn)
-        R = R2 @ R
+        R = R2 @ R if bn == Wfull.shape[1] else Qn.T @ Wfull    # B_(mu+1) = Q_(mu+1)^T W
         betas.append(R)
         Bmu = R
         Qprev = Qmu
