@@ -100,18 +100,19 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": reasons, "samples": len(rows)}
 
 
-# DRAM traffic of the dominant kernel (tc_gemm_kernel) per launch, from one ncu capture of
+# DRAM traffic of the dominant kernel (tc_gemm_kernel).  A whole solve is far too large to capture
+# under ncu, so the traffic is measured on one launch of the same kernel on a small case (a deep
+# trailing-update shape: C = 8192 x 8192 complex, k = 256, about 1.1 GB on the device):
+#   python bench.py --mode gemm --gemm 8192 8192 256 && \
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none -k regex:tc_gemm \
-#       --csv --log-file tc_traffic.csv python bench.py --mode one-solve
-# (3736 launches, 3820.7 GB; profiles/launches_q1_3d_40.md).  The figure depends on the kernel's
-# code and on the launches a solve makes, so it is reported only while both are unchanged: the
-# kernel's sources hash to the value below, and the timed steps make the same number of launches
-# with the same algorithmic flops per solve.
-TC_TRAFFIC_BYTES_PER_LAUNCH = 1022.67e6
+#       -s 1 -c 1 --csv --log-file tc_traffic_gemm.csv python bench.py --mode gemm --gemm 8192 8192 256
+# and divided by the launch's compulsory bytes from the kernel's traffic model (C read and written
+# once, packed operand tiles read once; rfdd_profile_bytes).  The full solve's traffic per launch is
+# that ratio times the model bytes of the timed launches.  The ratio holds for the kernel's code as
+# captured, so it is used only while the kernel's sources hash to the value below.
+TC_TRAFFIC_RATIO = None           # measured / model DRAM bytes of the captured launch
 TC_TRAFFIC_KERNEL_SOURCES = ("common.cuh", "dense.cuh", "tc_gemm.cuh", "tc_gemm.cu")
-TC_TRAFFIC_SOURCES_SHA256 = "e6fc40d49239c4e3162190abe20cee47361091dd0063d462bd09f41b4624e2ba"
-TC_TRAFFIC_LAUNCHES_PER_SOLVE = 3736
-TC_TRAFFIC_FLOPS_PER_SOLVE = 1.94957959198464e14
+TC_TRAFFIC_SOURCES_SHA256 = None
 
 
 def kernel_sources_sha256(names=TC_TRAFFIC_KERNEL_SOURCES) -> str:
@@ -125,11 +126,12 @@ def kernel_sources_sha256(names=TC_TRAFFIC_KERNEL_SOURCES) -> str:
     return h.hexdigest()
 
 
-def tc_traffic_valid(launches_per_solve: float, flops_per_solve: float) -> bool:
-    """True while the captured traffic still describes the launches being timed."""
-    return (kernel_sources_sha256() == TC_TRAFFIC_SOURCES_SHA256
-            and launches_per_solve == TC_TRAFFIC_LAUNCHES_PER_SOLVE
-            and abs(flops_per_solve - TC_TRAFFIC_FLOPS_PER_SOLVE) <= 1e-9 * TC_TRAFFIC_FLOPS_PER_SOLVE)
+def tc_traffic_per_launch(model_bytes_per_launch: float):
+    """DRAM bytes per launch of the timed launches, or None while the captured ratio does not
+    describe the kernel being timed."""
+    if TC_TRAFFIC_RATIO is None or kernel_sources_sha256() != TC_TRAFFIC_SOURCES_SHA256:
+        return None
+    return TC_TRAFFIC_RATIO * model_bytes_per_launch
 
 
 def measured_peaks():
@@ -221,6 +223,52 @@ def reduce_over_ranks(ms: float, units: float, dist, device) -> tuple[float, flo
 # our arm
 # --------------------------------------------------------------------------------------------
 
+def run_fp64_plain(R, w, stream, ev_ref=None):
+    """One solve of the workload on the plain FP64 path (FP64 factorisations and solves, no
+    refinement needed), timed with CUDA events on its stream: eigenpairs with residual <= 1e-10
+    per second, and how far its eigenvalues are from the mixed solve's."""
+    import torch
+    opts = R.rfdd_default_options(precision=R.RFDD_FP64, quad_rule=0 if w.rule == "midpoint" else 1,
+                                  stream=stream.cuda_stream)
+    h = R.rfdd_setup(w.A, w.M, w.part, w.p, opts)
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    r = R.rfdd_solve(h, w.alpha, w.beta, w.n_nodes)
+    s1.record(stream)
+    s1.synchronize()
+    ms = s0.elapsed_time(s1)
+    ev, _, rs = R.rfdd_result_get(r, vectors=False)
+    info = R.rfdd_result_info(r)
+    good = int(np.count_nonzero(rs <= 1e-10))
+    out = {"value": good / (ms / 1e3), "unit": UNIT, "ms": ms, "eigenpairs": good,
+           "max_resid": float(rs.max()) if len(rs) else None, "dtype": "c128",
+           "phases_ms": {k: info[k] for k in ("t_factor_ms", "t_lanczos_ms", "t_interior_ms", "t_rr_ms",
+                                               "t_complete_ms")}}
+    if ev_ref is not None and len(ev_ref) == len(ev) and len(ev):
+        out["max_rel_diff_vs_mixed"] = float(np.max(np.abs(ev - ev_ref) / np.abs(ev)))
+    if w.exact is not None and len(ev):
+        ex = w.exact[(w.exact > w.alpha) & (w.exact < w.beta)]
+        if len(ex) == len(ev):
+            out["max_rel_err_vs_closed_form"] = float(np.max(np.abs(ev - ex) / ex))
+    del r, h
+    return out
+
+
+def oracle_model_check():
+    """The flop model behind cpu_baseline, checked on the small 2D Q1 40^2 workload: the oracle's
+    whole solve timed against the model's extrapolated factorisation time for the same workload."""
+    from oracle import rfdd_oracle as O
+    w1 = I.workload("q1_2d_40")
+    t0 = time.perf_counter()
+    O.rfdd_solve(w1.A.to_scipy(), w1.M.to_scipy(), w1.part, w1.p, w1.alpha, w1.beta, w1.n_nodes, w1.rule)
+    full = time.perf_counter() - t0
+    v, _, _, _ = oracle_sample(w1)
+    model = w1.expected_nev / v
+    return {"workload": w1.name, "full_oracle_solve_s": full, "model_factorisation_s": model,
+            "full_over_model": full / model}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_1711_09487_gb300 as R
@@ -266,7 +314,7 @@ def run_ours(args, rank, world, local_rank):
         s1.record(stream)
         s1.synchronize()
         lat.append(s0.elapsed_time(s1))
-        _, _, rs_h = R.rfdd_result_get(r, vectors=False)
+        r_last_evals, _, rs_h = R.rfdd_result_get(r, vectors=False)
         good_per_step.append(int(np.count_nonzero(rs_h <= 1e-10)))
         del r
     e1.record(stream)
@@ -280,6 +328,7 @@ def run_ours(args, rank, world, local_rank):
     g_launch, g_ms, g_flops = R.rfdd_profile_get(0)
     t_launch, t_ms, t_flops = R.rfdd_profile_get(1)
     g_busy, t_busy = R.rfdd_profile_busy(0), R.rfdd_profile_busy(1)
+    t_model_bytes = R.rfdd_profile_bytes(1)
     R.rfdd_profile(False)
     good = sum(good_per_step)
     if dist:
@@ -307,6 +356,11 @@ def run_ours(args, rank, world, local_rank):
         e2e_s = e2e_ms / 1e3
     e2e_value = e2e_good / e2e_s
 
+    # the plain FP64 path on the same workload (the metric's comparison arm): one solve, timed with
+    # CUDA events on its stream, residual bar as for the mixed steps
+    fp64 = None
+    if args.fp64_plain == "on" or (args.fp64_plain == "auto" and world == 1 and precision == R.RFDD_MIXED):
+        fp64 = run_fp64_plain(R, w, stream, ev_ref=r_last_evals)
     if rank != 0:
         return
     peaks, src = measured_peaks()
@@ -317,18 +371,22 @@ def run_ours(args, rank, world, local_rank):
     # launches of the two streams run at the same time; the union counts that time once (with
     # no overlap it is the plain sum of the launch durations, also reported).
     if t_launch > 0:
+        # achieved: the method's algorithmic complex flops (4M count, 8 real flops per complex
+        # multiply-add) per second of busy time; peak: the TF32 tensor peak (measured sustained
+        # bf16 x the nominal TF32/bf16 ratio 1.1/2.25), the rate of the unit the contraction runs on
         ach = t_flops / (t_busy / 1e3) / 1e12
-        peak = float(peaks["bf16_tflops_sustained"]) * (1.1 / 2.25) / 3.0
-        traffic = (TC_TRAFFIC_BYTES_PER_LAUNCH
-                   if tc_traffic_valid(t_launch / args.steps, t_flops / args.steps) else None)
+        peak = float(peaks["bf16_tflops_sustained"]) * (1.1 / 2.25)
+        traffic = tc_traffic_per_launch(t_model_bytes / t_launch)
         roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": traffic, "traffic_unit": "DRAM bytes per launch, mean over one solve's launches",
-                # the same fraction counted in executed TF32 tensor work: the 3xTF32 split issues
-                # three TF32 products per complex-FP32 product
-                "executed_tflops": 3.0 * ach, "executed_peak_tf32": 3.0 * peak,
+                "traffic": traffic,
+                "traffic_unit": "DRAM bytes per launch (model bytes x measured/model ratio of one captured launch)",
+                "model_bytes_per_launch": t_model_bytes / t_launch,
+                # executed tensor work: the realified complex product issues exactly the 4M count
+                # of real multiply-adds, each as three TF32 products (3xTF32 split)
+                "executed_tflops": 3.0 * ach, "executed_frac": 3.0 * ach / peak,
                 "kernel": "tcgen05 3xTF32 complex GEMM", "launches": t_launch,
                 "busy_ms": t_busy, "launch_ms_sum": t_ms,
-                "peak_source": f"{src} bf16 sustained x 1.1/2.25 (TF32) / 3 (3xTF32 split)"}
+                "peak_source": f"{src} bf16 sustained x 1.1/2.25 (TF32 tensor)"}
     else:
         ach = g_flops / (g_busy / 1e3) / 1e12 if g_busy > 0 else 0.0
         peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
@@ -336,7 +394,15 @@ def run_ours(args, rank, world, local_rank):
                 "traffic": None, "kernel": "SIMT complex-FP32 GEMM (gemm_simt_kernel)", "launches": g_launch,
                 "busy_ms": g_busy, "launch_ms_sum": g_ms,
                 "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz ({src} max clock)"}
+    # throughput probes of the units this path is bound by (context for the peaks above)
+    probes = {}
+    for name, which in (("tf32_tensor_tflops", 0), ("fp64_fma_tflops", 1), ("fp32_fma_tflops", 2)):
+        try:
+            probes[name] = R.rfdd_peak_probe(which)
+        except Exception as ex:  # a probe is context, not part of the measurement
+            probes[name] = f"failed: {ex}"
     cpu_value, cpu_t, cpu_desc, cpu_threads = oracle_sample(w)
+    model_check = oracle_model_check()
     lat_sorted = sorted(lat)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -351,9 +417,13 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches,
         "roofline": roof,
         "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": cpu_threads, "kind": "oracle",
-                         "sample": cpu_desc},
+                         "sample": cpu_desc, "model_check": model_check},
+        "probes": probes,
         "clocks": clk,
     }
+    if fp64 is not None:
+        line["fp64_plain"] = fp64
+        line["mixed_over_fp64"] = value / fp64["value"] if fp64["value"] > 0 else None
     print(json.dumps(line), flush=True)
 
 
@@ -387,8 +457,9 @@ def run_gemm(args):
     R.rfdd_profile(True)
     R.rfdd_cgemm(A, B, C, -1.0, 1.0, 1)
     launches, ms, flops = R.rfdd_profile_get(1)
+    model_bytes = R.rfdd_profile_bytes(1)
     R.rfdd_profile(False)
-    print(json.dumps({"mode": "gemm", "m": m, "n": n, "k": k, "kernel_ms": ms,
+    print(json.dumps({"mode": "gemm", "m": m, "n": n, "k": k, "kernel_ms": ms, "model_bytes": model_bytes,
                       "tflops_4m": flops / (ms / 1e3) / 1e12 if ms > 0 else None}), flush=True)
 
 
@@ -419,6 +490,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--fp64-plain", default="auto", choices=["auto", "on", "off"],
+                    help="also time one solve on the plain FP64 path (auto: at N = 1 with --precision mixed)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -22,9 +22,10 @@
  *    except rfdd_solve_async().  A solve also runs the real interior factorisation (a8) on a
  *    second stream that the handle creates and owns, launched from a host thread of its own and
  *    joined before the call returns or fails.
- *  - A handle is not thread-safe; distinct handles may be used from different threads.  The
- *    tensor-core kernels share one device error flag (a wait that ran out of iterations), so
- *    such an error is reported by whichever handle checks it first.
+ *  - A handle is not thread-safe; distinct handles may be used from different threads.  Each
+ *    handle's kernels record device-side failures (a zero pivot, a tensor-core wait that ran out
+ *    of iterations) in a status word of that handle, so a failure is reported by the call that
+ *    met it and by no other handle.
  */
 #ifndef RFDD_H
 #define RFDD_H
@@ -109,6 +110,9 @@ typedef struct {
   double t_complete_ms; /* a10 */
   double t_total_ms;
   int32_t status;       /* RFDD_OK or RFDD_NOT_CONVERGED */
+  double sigma;         /* real shift the interior step used (Eq. prol2): opt.sigma or (alpha+beta)/2,
+                           moved by 1e-6 (beta - alpha) per attempt, at most three times, while it
+                           lies within 1e-8 max(1, |sigma|) of an eigenvalue of some (B_j, M_B^(j)) */
 } rfdd_info;
 
 /* Fill *opt with the defaults listed above. */
@@ -242,7 +246,7 @@ int rfdd_inertia(rfdd_handle *h, double sigma, int64_t *count);
  * null arrays or a non-finite lambda_i. */
 int rfdd_polish(rfdd_handle *h, int64_t nev, double *lambda, double *X, double *resid);
 
-/* a9 building block (Alg. 3 step 7 solves its projected problem with a dense symmetric/* a9 building block (Alg. 3 step 7 solves its projected problem with a dense symmetric
+/* a9 building block (Alg. 3 step 7 solves its projected problem with a dense symmetric
  * eigensolver): eigen-decomposition of a dense symmetric n x n FP64 matrix H on the GPU by
  * Householder tridiagonalisation, bisection on Sturm counts, inverse iteration (clusters
  * re-orthogonalised) and back-transformation.  H, evals, evecs
@@ -253,7 +257,9 @@ int rfdd_sym_eig(int64_t n, const double *H, double *evals, double *evecs);
 /* Building block of a3-a5 (trailing updates of the factorisations), a6 and a10 (triangular-solve
  * updates): C = beta*C + alpha*A*B for complex single-precision A (m x k, leading dimension lda),
  * B (k x n, ldb), C (m x n, ldc), host arrays, row-major, interleaved (re, im) floats.
- * engine 0 = CUDA-core kernel, 1 = tensor-core kernel (tcgen05, 3xTF32 split). */
+ * engine 1 = the tensor-core kernel (tcgen05, 3xTF32 split) that every complex-FP32 contraction
+ * of the solver runs on; engine 0 = a CUDA-core kernel kept as a second engine for tests (the
+ * solver never dispatches to it). */
 int rfdd_cgemm(int64_t m, int64_t n, int64_t k, const float *A, int64_t lda, const float *B, int64_t ldb,
                float *C, int64_t ldc, double alpha, double beta, int32_t engine);
 
@@ -278,10 +284,13 @@ int rfdd_dgemm(int64_t m, int64_t n, int64_t k, int32_t ta, const double *A, int
  * leading dimensions in complex elements) and stages the packed operands in a fixed static
  * device array (6 MiB per device that has loaded the library, held until process exit) instead
  * of a workspace.  Limits: 1 <= m, n <= 1024 and 1 <= k <= 128; larger sizes return RFDD_EINVAL.
- * The first call on a device looks up that array's device address (make that first call before
- * any stream capture).  Work runs on `stream` (a cudaStream_t, NULL = default stream); the call
- * returns after the stream has finished it.  Every call shares the one array: calls that overlap
- * on the GPU (from different host threads or streams) race and must be serialised by the caller.
+ * The first call on a device looks up the device addresses of that array and of its status word
+ * (make that first call before any stream capture).  Work runs on `stream` (a cudaStream_t, NULL =
+ * the legacy default stream): the call clears the status word, packs, multiplies and reads the
+ * status word back on that stream, then waits for that stream alone; it does not synchronise the
+ * device.  Every call shares the one array and status word, which keep the last call's contents:
+ * calls that overlap on the GPU (from different host threads or streams) race and must be
+ * serialised by the caller.  RFDD_ECUDA when the tensor-core kernel's bounded wait ran out.
  * No memory is allocated or freed by this call. */
 int rfdd_cgemm_noalloc(int64_t m, int64_t n, int64_t k, const float *A, int64_t lda, const float *B,
                        int64_t ldb, float *C, int64_t ldc, double alpha, double beta, void *stream);
@@ -297,9 +306,20 @@ int rfdd_cgemm_noalloc(int64_t m, int64_t n, int64_t k, const float *A, int64_t 
  * streams that ran at the same time count once (it equals the sum when launches never overlap).
  * Returns RFDD_ESTATE if launches were recorded without rfdd_profile(1). */
 long long rfdd_kernel_launches(void);
+/* Throughput probe of one arithmetic unit on the current device, in TFLOP/s (best of three timed
+ * launches after a warm-up, CUDA events): which = 0 the plain TF32 tensor path (tcgen05
+ * kind::tf32, one MMA per product; a real 8192^3 GEMM, the MMA kernel alone timed, operand packing
+ * excluded); 1 FP64 fused multiply-add on the CUDA cores; 2 FP32 fused multiply-add on the CUDA
+ * cores.  Allocates about 1.9 GB (which = 0) or a few MB on a stream of its own. */
+int rfdd_peak_probe(int32_t which, double *tflops);
 int rfdd_profile(int32_t enable);
 int rfdd_profile_get(int32_t kind, int64_t *launches, double *ms, double *flops);
 int rfdd_profile_busy(int32_t kind, double *busy_ms);
+/* Sum, over the recorded launches of one kind, of their compulsory DRAM bytes by the traffic model
+ * of the kernel: C read (when beta != 0) and written once, every packed operand tile read once.
+ * (Kind 1 only; kind 0 records 0.)  Scaled by the ratio of ncu-measured to model bytes on one
+ * captured launch, it gives the DRAM traffic of launches too large to capture. */
+int rfdd_profile_bytes(int32_t kind, double *bytes);
 
 /* Asynchronous solve for serving: enqueues the solve on `stream` (a cudaStream_t, NULL = the
  * handle's) and returns; rfdd_result_ready() reports completion (1 done, 0 running, <0 error

@@ -41,7 +41,7 @@ SYMBOLS = [
     "rfdd_filter_apply", "rfdd_lanczos", "rfdd_interior", "rfdd_rayleigh_ritz", "rfdd_solve_async",
     "rfdd_result_ready", "rfdd_memory_estimate", "rfdd_sym_eig", "rfdd_kernel_launches", "rfdd_profile",
     "rfdd_profile_get", "rfdd_profile_busy", "rfdd_cgemm", "rfdd_dgemm", "rfdd_cgemm_noalloc", "rfdd_inertia",
-    "rfdd_polish",
+    "rfdd_polish", "rfdd_peak_probe", "rfdd_profile_bytes",
 ]
 
 
@@ -69,7 +69,8 @@ class rfdd_info(C.Structure):
                 ("passes", C.c_int32), ("ir_steps_max", C.c_int32), ("max_resid", C.c_double),
                 ("pre_max_resid", C.c_double), ("pre_nev", C.c_int64), ("t_factor_ms", C.c_double),
                 ("t_lanczos_ms", C.c_double), ("t_interior_ms", C.c_double), ("t_rr_ms", C.c_double),
-                ("t_complete_ms", C.c_double), ("t_total_ms", C.c_double), ("status", C.c_int32)]
+                ("t_complete_ms", C.c_double), ("t_total_ms", C.c_double), ("status", C.c_int32),
+                ("sigma", C.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -126,6 +127,8 @@ def load(path: str | None = None):
     lib.rfdd_profile.argtypes = [i32]
     lib.rfdd_profile_get.argtypes = [i32, C.POINTER(i64), dp, dp]
     lib.rfdd_profile_busy.argtypes = [i32, dp]
+    lib.rfdd_peak_probe.argtypes = [i32, dp]
+    lib.rfdd_profile_bytes.argtypes = [i32, dp]
     _lib = lib
     return lib
 
@@ -425,6 +428,21 @@ def rfdd_cgemm_noalloc(m: int, n: int, k: int, A_ptr: int, lda: int, B_ptr: int,
     """Allocation-free tensor-core GEMM on device pointers (complex64, row-major); see rfdd.h."""
     _check(load().rfdd_cgemm_noalloc(m, n, k, C.c_void_p(A_ptr), lda, C.c_void_p(B_ptr), ldb, C.c_void_p(C_ptr), ldc,
                                      alpha, beta, C.c_void_p(stream or None)))
+
+
+def rfdd_peak_probe(which: int) -> float:
+    """TFLOP/s of one arithmetic unit on the current device: 0 plain TF32 tensor GEMM, 1 FP64
+    FMA, 2 FP32 FMA (CUDA cores)."""
+    t = C.c_double()
+    _check(load().rfdd_peak_probe(int(which), C.byref(t)))
+    return float(t.value)
+
+
+def rfdd_profile_bytes(kind: int) -> float:
+    """Model (compulsory) DRAM bytes of the recorded launches of one kind."""
+    b = C.c_double()
+    _check(load().rfdd_profile_bytes(int(kind), C.byref(b)))
+    return float(b.value)
 
 
 def rfdd_kernel_launches() -> int:

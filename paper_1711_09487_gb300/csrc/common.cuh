@@ -46,9 +46,10 @@ struct ProfileRec {
   cudaEvent_t a, b;
   double flops;   // algorithmic flops of the launch (complex multiply-add = 8 real flops)
   int kind;       // 0: SIMT GEMM, 1: tensor-core GEMM
+  double bytes;   // compulsory DRAM bytes of the launch (operands read once, C read and/or written)
 };
 bool profiling_enabled();
-void profile_push(cudaEvent_t a, cudaEvent_t b, double flops, int kind);
+void profile_push(cudaEvent_t a, cudaEvent_t b, double flops, int kind, double bytes = 0.0);
 cudaEvent_t profile_event();
 
 #define RFDD_REQUIRE(cond, code, msg)                 \

@@ -6,6 +6,7 @@
 #include "tc_gemm.cuh"
 
 #include <algorithm>
+#include <mutex>
 #include <type_traits>
 
 namespace rfdd {
@@ -129,14 +130,26 @@ __global__ void __launch_bounds__(256) splitk_reduce_kernel(GemmBatchP<T> batch,
   }
 }
 
+// SM count of the current device (looked up once per device; several host threads may launch)
 int sm_count() {
-  static const int n = [] {  // initialised once, also when several host threads launch
-    int dev = 0, v = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
-    return v;
-  }();
-  return n;
+  static std::mutex mu;
+  static std::vector<int> nsm;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    dev = 0;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  if ((int)nsm.size() <= dev) nsm.resize(dev + 1, 0);
+  if (nsm[dev] <= 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+      cudaGetLastError();
+      v = 148;
+    }
+    nsm[dev] = v;
+  }
+  return nsm[dev];
 }
 
 // ======================================================================================
@@ -360,7 +373,7 @@ void gemm_batched(cudaStream_t st, const std::vector<GemmItem<T>> &items, bool t
                   double alpha, double beta) {
   if constexpr (std::is_same<T, cx<float>>::value) {
     // complex FP32 products go to the tensor cores (3xTF32 split, FP32 accumulation)
-    if (!ta && !tb && tc_enabled()) {
+    if (!ta && !tb) {
       std::vector<GemmItem<T>> live;
       for (auto &g : items)
         if (g.m > 0 && g.n > 0 && g.k > 0) live.push_back(g);
@@ -374,7 +387,7 @@ void gemm_batched(cudaStream_t st, const std::vector<GemmItem<T>> &items, bool t
     }
   }
   if constexpr (std::is_same<T, float>::value) {
-    if (!ta && !tb && tc_enabled()) {
+    if (!ta && !tb) {
       std::vector<GemmItem<T>> live, k0;
       for (auto &g : items) {
         if (g.m > 0 && g.n > 0 && g.k > 0) live.push_back(g);
@@ -885,11 +898,18 @@ void lu_batched(cudaStream_t st, const std::vector<LuItem<T>> &items, int nbo, i
   }
   if (dpmax == 0) return;
   const size_t smem = (size_t)R * NB * sizeof(T) + (size_t)R * sizeof(int);
-  static const bool attr_set = [smem] {  // once per T, thread-safe
-    RFDD_CUDA(cudaFuncSetAttribute(lu_tourn_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    return true;
-  }();
-  (void)attr_set;
+  {  // the tournament kernel's shared-memory limit, raised once per device and scalar type
+    static std::mutex mu;
+    static std::vector<char> done;
+    int dev = 0;
+    RFDD_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if ((int)done.size() <= dev) done.resize(dev + 1, 0);
+    if (!done[dev]) {
+      RFDD_CUDA(cudaFuncSetAttribute(lu_tourn_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      done[dev] = 1;
+    }
+  }
   LuWork wk;
   const int stride = (ceil_div(dpmax, R) + 1) * NB;
   wk.cand_ints = (size_t)2 * MAXB * stride;
@@ -1116,7 +1136,7 @@ static void trsm_block_inverse(cudaStream_t st, const std::vector<SolveItem<T>> 
       }
     }
     bool use_pa = false;
-    if constexpr (std::is_same<T, cx<float>>::value) use_pa = tc_enabled();
+    if constexpr (std::is_same<T, cx<float>>::value) use_pa = true;
     if (use_pa) {
       if constexpr (std::is_same<T, cx<float>>::value) {
         tc_gemm_complex_pa(st, g1, p1, 1.0, 0.0);

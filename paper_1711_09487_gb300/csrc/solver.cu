@@ -24,6 +24,7 @@
 #include "dense.cuh"
 #include "eig.cuh"
 #include "ops.cuh"
+#include "probe.cuh"
 #include "small.cuh"
 #include "tc_gemm.cuh"
 
@@ -50,9 +51,9 @@ cudaEvent_t profile_event() {
   cudaEventCreate(&e);
   return e;
 }
-void profile_push(cudaEvent_t a, cudaEvent_t b, double flops, int kind) {
+void profile_push(cudaEvent_t a, cudaEvent_t b, double flops, int kind, double bytes) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
-  g_prof.push_back({a, b, flops, kind});
+  g_prof.push_back({a, b, flops, kind, bytes});
 }
 }  // namespace rfdd
 
@@ -301,17 +302,19 @@ namespace {
 inline bool is_mixed(const rfdd_handle *h) { return h->opt.precision == RFDD_MIXED; }
 
 // Waits for the handle's stream, then raises what the device recorded in the status word w
-// (h->status unless given) and in the tensor-core error flags; a nonzero word is cleared.
+// (h->status unless given; the tensor-core GEMMs of the handle record their wait time-outs in the
+// same word); a nonzero word is cleared.
 void sync_status(rfdd_handle *h, const char *where, Buf *w = nullptr) {
   RFDD_CUDA(cudaStreamSynchronize(h->st));
   if (!w) w = &h->status;
   int s = 0;
-  RFDD_CUDA(cudaMemcpy(&s, w->p, sizeof(int), cudaMemcpyDeviceToHost));
-  const int tce = tc_take_error();
-  if (tce & DS_WAIT_TIMEOUT)
-    throw Error(RFDD_ECUDA, std::string(where) + ": a tensor-core GEMM timed out waiting for its operands");
+  RFDD_CUDA(cudaMemcpyAsync(&s, w->p, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  RFDD_CUDA(cudaStreamSynchronize(h->st));
   if (s != 0) {
-    RFDD_CUDA(cudaMemset(w->p, 0, sizeof(int)));
+    RFDD_CUDA(cudaMemsetAsync(w->p, 0, sizeof(int), h->st));
+    RFDD_CUDA(cudaStreamSynchronize(h->st));
+    if (s & DS_WAIT_TIMEOUT)
+      throw Error(RFDD_ECUDA, std::string(where) + ": a tensor-core GEMM timed out waiting for its operands");
     if (s & (DS_ZERO_PIVOT | DS_NONFINITE))
       throw Error(RFDD_ESINGULAR, std::string(where) + ": zero or non-finite pivot (device status " +
                                       std::to_string(s) + ")");
@@ -833,9 +836,7 @@ void factor_impl(rfdd_handle *h) {
     }
     lu_block_inverses<Tf>(st, fi, NBO, li, ui);
   }
-  if constexpr (std::is_same<Tf, cx<float>>::value) {
-    if (tc_enabled()) pack_factor_operands(h);
-  }
+  if constexpr (std::is_same<Tf, cx<float>>::value) pack_factor_operands(h);
   sync_status(h, "factor");
   h->have_factors = true;
 }
@@ -1006,10 +1007,8 @@ template <typename Tf>
 void border_gemm(cudaStream_t st, const std::vector<GemmItem<Tf>> &g, const std::vector<TcPackedA> &pa, double alpha,
                  double beta) {
   if constexpr (std::is_same<Tf, cx<float>>::value) {
-    if (tc_enabled()) {
-      tc_gemm_complex_pa(st, g, pa, alpha, beta);
-      return;
-    }
+    tc_gemm_complex_pa(st, g, pa, alpha, beta);
+    return;
   }
   gemm_batched<Tf>(st, g, false, false, alpha, beta);
 }
@@ -1566,6 +1565,7 @@ void interior_factor_start(rfdd_handle *h, double sigma, cudaStream_t on) {
   const int64_t *doff_dev = h->I_doff.as<int64_t>(), *boffr_dev = h->I_boffr_dev.as<int64_t>();
   const cx<double> *zs = h->I_zs.as<cx<double>>();
   auto launch = [=](cudaStream_t s) {
+    TcStatusScope ts(status);  // tensor-core time-outs of these launches land in their status word
     // assemble_blocks without border: D_j = d_j, and the same row mapping
     assemble_blocks<Tr>(s, P, dd, doff_dev, dsum, boffr_dev, zs, 1, Bs, false);
     lu_batched<Tr>(s, items, NBO_LU, status);
@@ -2188,6 +2188,12 @@ void run_solve(rfdd_handle *h, double alpha, double beta, int nc, rfdd_result *r
   Timer total(h->st);
   std::vector<cx<double>> z, w;
   quadrature(alpha, beta, nc, h->opt.quad_rule, z, w);
+  if (h->opt.mem_budget > 0) {  // admission before any device work of the solve
+    const size_t need = factor_bytes(h, nc, is_mixed(h) ? sizeof(cx<float>) : sizeof(cx<double>));
+    RFDD_REQUIRE(need <= h->opt.mem_budget, RFDD_EADMIT,
+                 "solve needs " + std::to_string(need) + " bytes of factors, budget " +
+                     std::to_string(h->opt.mem_budget));
+  }
   std::vector<double> zz(2 * nc), ww(2 * nc);
   for (int l = 0; l < nc; ++l) {
     zz[2 * l] = z[l].re;
@@ -2243,6 +2249,7 @@ void run_solve(rfdd_handle *h, double alpha, double beta, int nc, rfdd_result *r
       RFDD_LOGF("interior: sigma %.17g within %.3e of a subdomain eigenvalue, moved", sig, h->interior_gap);
       sig += 1e-6 * (beta - alpha);
     }
+    res->info.sigma = sig;
     res->info.t_interior_ms = t.ms();
   }
   {
@@ -2409,6 +2416,7 @@ int rfdd_factor(rfdd_handle *h, int32_t n_nodes, const double *z, const double *
   if (!h || !z || !w || n_nodes < 1) return RFDD_EINVAL;
   return guarded([&] {
     AllocScope scope(h->st);
+    TcStatusScope tcs(h->status.as<int>());
     set_nodes(h, n_nodes, z, w);
     factor(h);
   });
@@ -2418,6 +2426,7 @@ int rfdd_schur_copy(rfdd_handle *h, int32_t node, double *S_out) {
   if (!h || !S_out) return RFDD_EINVAL;
   return guarded([&] {
     AllocScope scope(h->st);
+    TcStatusScope tcs(h->status.as<int>());
     RFDD_REQUIRE(h->have_factors && h->opt.keep_schur, RFDD_ESTATE, "schur_copy needs keep_schur and rfdd_factor");
     RFDD_REQUIRE(node >= 0 && node < h->nnodes, RFDD_EINVAL, "node out of range");
     const int64_t s = h->s;
@@ -2440,6 +2449,7 @@ int rfdd_shifted_solve(rfdd_handle *h, int32_t node, int32_t which, int32_t j, i
   if (!h || !R || !X || nrhs < 1) return RFDD_EINVAL;
   return guarded([&] {
     AllocScope scope(h->st);
+    TcStatusScope tcs(h->status.as<int>());
     RFDD_REQUIRE(h->have_factors, RFDD_ESTATE, "shifted_solve needs rfdd_factor");
     RFDD_REQUIRE(node >= 0 && node < h->nnodes, RFDD_EINVAL, "node out of range");
     cudaStream_t st = h->st;
@@ -2522,6 +2532,7 @@ int rfdd_filter_apply(rfdd_handle *h, int64_t b, const double *X, double *W) {
   if (!h || !X || !W || b < 1) return RFDD_EINVAL;
   return guarded([&] {
     AllocScope scope(h->st);
+    TcStatusScope tcs(h->status.as<int>());
     RFDD_REQUIRE(h->have_factors, RFDD_ESTATE, "filter_apply needs rfdd_factor");
     const int64_t s = h->s;
     Buf x, wv;
@@ -2539,6 +2550,7 @@ int rfdd_lanczos(rfdd_handle *h, int64_t cap, double *Q_out, int64_t *mu, double
   if (!h) return RFDD_EINVAL;
   return guarded([&] {
     AllocScope scope(h->st);
+    TcStatusScope tcs(h->status.as<int>());
     RFDD_REQUIRE(h->have_factors, RFDD_ESTATE, "lanczos needs rfdd_factor");
     if (is_mixed(h)) lanczos_impl<cx<float>>(h);
     else lanczos_impl<cx<double>>(h);
@@ -2564,6 +2576,7 @@ int rfdd_interior(rfdd_handle *h, double sigma, int64_t cap, double *Z_out, int6
   if (!h) return RFDD_EINVAL;
   return guarded([&] {
     AllocScope scope(h->st);
+    TcStatusScope tcs(h->status.as<int>());
     RFDD_REQUIRE(h->mu > 0, RFDD_ESTATE, "interior needs rfdd_lanczos");
     double sg = sigma;
     if (std::isnan(sg)) sg = h->have_interval ? 0.5 * (h->alpha + h->beta) : 0.0;
@@ -2586,6 +2599,7 @@ int rfdd_rayleigh_ritz(rfdd_handle *h, int64_t cap, double *theta_out, int64_t *
   if (!h) return RFDD_EINVAL;
   return guarded([&] {
     AllocScope scope(h->st);
+    TcStatusScope tcs(h->status.as<int>());
     RFDD_REQUIRE(h->kz > 0, RFDD_ESTATE, "rayleigh_ritz needs rfdd_interior");
     const double a = h->have_interval ? h->alpha : -INFINITY, b = h->have_interval ? h->beta : INFINITY;
     if (is_mixed(h)) rr_on_Z<cx<float>>(h, a, b, nullptr);
@@ -2600,6 +2614,7 @@ int rfdd_inertia(rfdd_handle *h, double sigma, int64_t *count) {
   if (!h || !count || !std::isfinite(sigma)) return RFDD_EINVAL;
   return guarded([&] {
     AllocScope scope(h->st);
+    TcStatusScope tcs(h->status.as<int>());
     *count = inertia_impl(h, sigma);
   });
 }
@@ -2609,6 +2624,7 @@ int rfdd_polish(rfdd_handle *h, int64_t nev, double *lambda, double *X, double *
   if (nev == 0) return RFDD_OK;
   return guarded([&] {
     AllocScope scope(h->st);
+    TcStatusScope tcs(h->status.as<int>());
     interior_join(h, false);  // nothing of a failed solve may still be running on the second stream
     polish_impl(h, nev, lambda, X, resid);
   });
@@ -2621,6 +2637,7 @@ int rfdd_solve(rfdd_handle *h, double alpha, double beta, int32_t n_nodes, rfdd_
   if (!r) return RFDD_ENOMEM;
   int rc = guarded([&] {
     AllocScope scope(h->st);
+    TcStatusScope tcs(h->status.as<int>());
     run_solve(h, alpha, beta, n_nodes, r);
   });
   if (rc != RFDD_OK) {
@@ -2648,6 +2665,7 @@ int rfdd_solve_async(rfdd_handle *h, double alpha, double beta, int32_t n_nodes,
     int rc = guarded([&] {
       RFDD_CUDA(cudaSetDevice(device));
       AllocScope scope(h->st);
+    TcStatusScope tcs(h->status.as<int>());
       run_solve(h, alpha, beta, n_nodes, r);
     });
     if (rc != RFDD_OK) r->ready.store(-rc);
@@ -2748,10 +2766,19 @@ int rfdd_cgemm(int64_t m, int64_t n, int64_t k, const float *A, int64_t lda, con
     RFDD_CUDA(cudaMemcpy(c.p, C, (size_t)m * ldc * sizeof(cx<float>), cudaMemcpyHostToDevice));
     std::vector<GemmItem<cx<float>>> it = {{a.as<cx<float>>(), b.as<cx<float>>(), c.as<cx<float>>(), (int)m, (int)n,
                                             (int)k, (int)lda, (int)ldb, (int)ldc}};
-    if (engine == 1) tc_gemm_complex(st, it, alpha, beta);
-    else gemm_simt_batched<cx<float>>(st, it, false, false, alpha, beta);
+    Buf status;
+    status.alloc(sizeof(int));
+    RFDD_CUDA(cudaMemset(status.p, 0, sizeof(int)));
+    if (engine == 1) {
+      TcStatusScope tcs(status.as<int>());
+      tc_gemm_complex(st, it, alpha, beta);
+    } else {
+      gemm_simt_batched<cx<float>>(st, it, false, false, alpha, beta);
+    }
     RFDD_CUDA(cudaStreamSynchronize(st));
-    RFDD_REQUIRE(tc_take_error() == 0, RFDD_ECUDA, "tensor-core GEMM reported a time-out");
+    int stt = 0;
+    RFDD_CUDA(cudaMemcpy(&stt, status.p, sizeof(int), cudaMemcpyDeviceToHost));
+    RFDD_REQUIRE(stt == 0, RFDD_ECUDA, "tensor-core GEMM reported a time-out");
     RFDD_CUDA(cudaMemcpy(C, c.p, (size_t)m * ldc * sizeof(cx<float>), cudaMemcpyDeviceToHost));
   });
 }
@@ -2785,12 +2812,17 @@ int rfdd_cgemm_noalloc(int64_t m, int64_t n, int64_t k, const float *A, int64_t 
   if (!A || !B || !C || lda < k || ldb < n || ldc < n) return RFDD_EINVAL;
   return guarded([&] {
     cudaStream_t st = (cudaStream_t)stream;
-    tc_gemm_complex_noalloc(st, reinterpret_cast<const cx<float> *>(A), lda, reinterpret_cast<const cx<float> *>(B),
-                            ldb, reinterpret_cast<cx<float> *>(C), ldc, (int)std::min<int64_t>(m, INT32_MAX),
-                            (int)std::min<int64_t>(n, INT32_MAX), (int)std::min<int64_t>(k, INT32_MAX), alpha, beta);
-    RFDD_CUDA(cudaStreamSynchronize(st));
-    RFDD_REQUIRE(tc_take_error() == 0, RFDD_ECUDA, "tensor-core GEMM reported a time-out");
+    const int stt = tc_gemm_complex_noalloc(
+        st, reinterpret_cast<const cx<float> *>(A), lda, reinterpret_cast<const cx<float> *>(B), ldb,
+        reinterpret_cast<cx<float> *>(C), ldc, (int)std::min<int64_t>(m, INT32_MAX),
+        (int)std::min<int64_t>(n, INT32_MAX), (int)std::min<int64_t>(k, INT32_MAX), alpha, beta);
+    RFDD_REQUIRE(stt == 0, RFDD_ECUDA, "tensor-core GEMM reported a time-out");
   });
+}
+
+int rfdd_peak_probe(int32_t which, double *tflops) {
+  if (!tflops) return RFDD_EINVAL;
+  return guarded([&] { *tflops = peak_probe(which); });
 }
 
 long long rfdd_kernel_launches(void) { return g_kernel_launches.load(); }
@@ -2862,6 +2894,15 @@ int rfdd_profile_get(int32_t kind, int64_t *launches, double *ms, double *flops)
       *flops += r.flops;
     }
   });
+}
+
+int rfdd_profile_bytes(int32_t kind, double *bytes) {
+  if (!bytes) return RFDD_EINVAL;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  *bytes = 0.0;
+  for (auto &r : g_prof)
+    if (r.kind == kind) *bytes += r.bytes;
+  return RFDD_OK;
 }
 
 int rfdd_memory_estimate(const rfdd_handle *h, int32_t n_nodes, int64_t nev_guess, size_t *bytes) {

@@ -41,8 +41,18 @@ constexpr int TC_THREADS = 64 + 32 * EPI_WARPS;  // producer warp, MMA warp, epi
 constexpr int TC_SMEM = TC_STAGES * STAGE_BYTES + EPI_BYTES + 1024;
 constexpr long long WAIT_LIMIT = 1ll << 24;
 
-// error flags of the tensor-core kernels (DS_* bits), read and cleared by tc_take_error()
-__device__ int g_tc_error = 0;
+// Status word of the launches issued by the calling host thread (TcStatusScope): a kernel whose
+// bounded wait ran out ORs DS_WAIT_TIMEOUT into it.  Each handle passes its own word, so a
+// failure is reported by the solve that met it and by no other.
+thread_local int *g_tc_status = nullptr;
+
+TcStatusScope::TcStatusScope(int *w) : prev(g_tc_status) { g_tc_status = w; }
+TcStatusScope::~TcStatusScope() { g_tc_status = prev; }
+
+// Events recorded around the tensor-core kernel launches of the calling host thread (probes).
+thread_local const cudaEvent_t *g_tc_events = nullptr;
+TcKernelEvents::TcKernelEvents(const cudaEvent_t *ab) : prev(g_tc_events) { g_tc_events = ab; }
+TcKernelEvents::~TcKernelEvents() { g_tc_events = prev; }
 
 struct TcItem {
   const float *Ahi, *Alo, *Bhi, *Blo;
@@ -55,6 +65,8 @@ constexpr int TC_MAXB = 64;
 struct TcBatchP {
   TcItem it[TC_MAXB];
   int count, total_tiles;
+  int *err;    // status word of the launch (DS_WAIT_TIMEOUT on a wait that ran out)
+  int splits;  // 3: hi*hi + hi*lo + lo*hi (FP32 accuracy); 1: hi*hi only (plain TF32, peak probe)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -135,7 +147,7 @@ __device__ __forceinline__ int find_item(const TcBatchP &b, int tile) {
 // two TMEM accumulators (256 columns each), warps 2..5 drain the other accumulator to C.
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_constant__ TcBatchP b, float alpha,
                                                                 float beta) {
-  int *err = &g_tc_error;
+  int *err = b.err;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   float *epi = reinterpret_cast<float *>(base + TC_STAGES * STAGE_BYTES);
@@ -190,11 +202,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
             break;
           }
           const uint32_t fb = smem_u32(&full_bar[s]);
-          mbar_expect_tx(fb, STAGE_BYTES);
+          mbar_expect_tx(fb, b.splits > 1 ? STAGE_BYTES : (A_TILE + B_TILE) * 4);
           bulk_g2s(stage_addr(s, 0), Ahi + (long long)kt * A_TILE, A_TILE * 4, fb);
-          bulk_g2s(stage_addr(s, 1), Alo + (long long)kt * A_TILE, A_TILE * 4, fb);
           bulk_g2s(stage_addr(s, 2), Bhi + (long long)kt * B_TILE, B_TILE * 4, fb);
-          bulk_g2s(stage_addr(s, 3), Blo + (long long)kt * B_TILE, B_TILE * 4, fb);
+          if (b.splits > 1) {
+            bulk_g2s(stage_addr(s, 1), Alo + (long long)kt * A_TILE, A_TILE * 4, fb);
+            bulk_g2s(stage_addr(s, 3), Blo + (long long)kt * B_TILE, B_TILE * 4, fb);
+          }
         }
       }
       // drain: every issued copy must land before the CTA can exit
@@ -232,8 +246,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
           for (int kk = 0; kk < TC_BK / 8; ++kk) {
             const uint32_t o = kk * 32;  // 8 TF32 values = 32 bytes along K inside the swizzle row
             mma_tf32(dacc, sdesc(ah + o), sdesc(bh + o), idesc, (kt > 0 || kk > 0) ? 1u : 0u);
-            mma_tf32(dacc, sdesc(ah + o), sdesc(bl + o), idesc, 1u);
-            mma_tf32(dacc, sdesc(al + o), sdesc(bh + o), idesc, 1u);
+            if (b.splits > 1) {
+              mma_tf32(dacc, sdesc(ah + o), sdesc(bl + o), idesc, 1u);
+              mma_tf32(dacc, sdesc(al + o), sdesc(bh + o), idesc, 1u);
+            }
           }
           mma_commit(smem_u32(&empty_bar[s]));
         }
@@ -500,31 +516,34 @@ __global__ void pack_b_real_kernel(PackBatchP pb) {
   }
 }
 
-bool tc_enabled() {
-  static int on = [] {
-    const char *v = getenv("RFDD_TC");
-    return (v && v[0] == '0') ? 0 : 1;
-  }();
-  return on != 0;
-}
-
-static std::atomic<int> g_tc_attr_done{0};  // set once; several host threads may launch
-
-int tc_take_error() {
-  int v = 0, z = 0;
-  RFDD_CUDA(cudaMemcpyFromSymbol(&v, g_tc_error, sizeof(int)));
-  if (v) RFDD_CUDA(cudaMemcpyToSymbol(g_tc_error, &z, sizeof(int)));
-  return v;
+// Per-device launch set-up of the tensor-core kernel: its dynamic shared-memory limit is raised
+// once on every device it runs on, and the device's SM count sizes the persistent grid.
+struct TcDevInfo {
+  bool attr = false;
+  int nsm = 0;
+};
+static int tc_device_setup() {
+  static std::mutex mu;
+  static std::vector<TcDevInfo> info;
+  int dev = 0;
+  RFDD_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  if ((int)info.size() <= dev) info.resize(dev + 1);
+  TcDevInfo &d = info[dev];
+  if (!d.attr) {
+    RFDD_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+    RFDD_CUDA(cudaDeviceGetAttribute(&d.nsm, cudaDevAttrMultiProcessorCount, dev));
+    d.attr = true;
+  }
+  return std::max(1, d.nsm);
 }
 
 template <bool CPLX, typename T>
 static void tc_gemm_run(cudaStream_t st, const std::vector<GemmItem<T>> &items, double alpha, double beta,
-                        const std::vector<TcPackedA> *pre = nullptr) {
+                        const std::vector<TcPackedA> *pre = nullptr, int splits = 3) {
   constexpr int F = CPLX ? 2 : 1;  // real columns / K entries per element
-  if (!g_tc_attr_done) {
-    RFDD_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
-    g_tc_attr_done = 1;
-  }
+  RFDD_REQUIRE(g_tc_status != nullptr, RFDD_ESTATE, "tensor-core GEMM launched without a status word");
+  const int nsm = tc_device_setup();
   for (size_t s0 = 0; s0 < items.size(); s0 += TC_MAXB) {
     const int cnt = (int)std::min<size_t>(TC_MAXB, items.size() - s0);
     PackBatchP pa, pbb;
@@ -536,7 +555,7 @@ static void tc_gemm_run(cudaStream_t st, const std::vector<GemmItem<T>> &items, 
     std::vector<size_t> offA(cnt), offB(cnt);
     int mtmax = 1, ntmax = 1;
     long long achunks = 1, bchunks = 1;
-    double flops = 0.0;
+    double flops = 0.0, cbytes = 0.0;
     for (int i = 0; i < cnt; ++i) {
       const auto &g = items[s0 + i];
       const int mtc = ceil_div(g.m, TC_BM), ntc = ceil_div((int64_t)F * g.n, TC_BN), nkt = ceil_div((int64_t)F * g.k, TC_BK);
@@ -550,6 +569,9 @@ static void tc_gemm_run(cudaStream_t st, const std::vector<GemmItem<T>> &items, 
       achunks = std::max(achunks, (long long)mtc * TC_BM * nkt * 8);
       bchunks = std::max(bchunks, (long long)ntc * TC_BN * nkt * 8);
       flops += (CPLX ? 8.0 : 2.0) * g.m * (double)g.n * g.k;
+      // compulsory DRAM bytes: C read (beta != 0) and written, packed hi/lo operands read once
+      cbytes += (beta != 0.0 ? 2.0 : 1.0) * 4.0 * F * g.m * (double)g.n +
+                8.0 * ((double)mtc * nkt * A_TILE + (double)ntc * nkt * B_TILE);
     }
     float *ws = nullptr;
     RFDD_CUDA(cudaMallocAsync((void **)&ws, total * sizeof(float), st));
@@ -571,6 +593,8 @@ static void tc_gemm_run(cudaStream_t st, const std::vector<GemmItem<T>> &items, 
     }
     tb.count = cnt;
     tb.total_tiles = tiles;
+    tb.err = g_tc_status;
+    tb.splits = splits;
     bool any_a = false;
     for (int i = 0; i < cnt; ++i) any_a |= pa.it[i].mtc > 0;
     const dim3 ga((unsigned)std::min<long long>(ceil_div(achunks, 256), 4096), cnt);
@@ -596,14 +620,14 @@ static void tc_gemm_run(cudaStream_t st, const std::vector<GemmItem<T>> &items, 
       e1 = profile_event();
       cudaEventRecord(e0, st);
     }
-    int nsm = 0;
-    RFDD_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, 0));
     const int grid = std::max(1, std::min(tiles, nsm));
+    if (g_tc_events) RFDD_CUDA(cudaEventRecord(g_tc_events[0], st));
     tc_gemm_kernel<<<grid, TC_THREADS, TC_SMEM, st>>>(tb, (float)alpha, (float)beta);
     RFDD_CHECK_LAUNCH();
+    if (g_tc_events) RFDD_CUDA(cudaEventRecord(g_tc_events[1], st));
     if (e0) {
       cudaEventRecord(e1, st);
-      profile_push(e0, e1, flops, 1);
+      profile_push(e0, e1, flops, 1, cbytes);
     }
     RFDD_CUDA(cudaFreeAsync(ws, st));
   }
@@ -659,6 +683,10 @@ void tc_gemm_real(cudaStream_t st, const std::vector<GemmItem<float>> &items, do
   tc_gemm_run<false>(st, items, alpha, beta);
 }
 
+void tc_gemm_real_tf32(cudaStream_t st, const std::vector<GemmItem<float>> &items, double alpha, double beta) {
+  tc_gemm_run<false>(st, items, alpha, beta, nullptr, 1);
+}
+
 // =========================================================================================
 // Allocation-free variant of the tensor-core complex GEMM.
 //
@@ -679,32 +707,40 @@ constexpr size_t NOALLOC_B_FLOATS =
 constexpr size_t NOALLOC_FLOATS = NOALLOC_A_FLOATS + NOALLOC_B_FLOATS;  // 6 MiB of floats in total
 
 static __device__ __align__(256) float g_noalloc_scratch[NOALLOC_FLOATS];
+// status word of the allocation-free launches (DS_WAIT_TIMEOUT), beside the scratch
+static __device__ int g_noalloc_status;
 
-static float *noalloc_scratch_address(int dev) {
+struct NoallocAddr {
+  float *scratch = nullptr;
+  int *status = nullptr;
+};
+// Device addresses of the array and of its status word on the current device, looked up once per
+// device with that device current (the host-side names are only stand-ins).
+static NoallocAddr noalloc_addresses() {
   static std::mutex mu;
-  static std::vector<float *> addr(256, nullptr);
+  static std::vector<NoallocAddr> addr;
+  int dev = 0;
+  RFDD_CUDA(cudaGetDevice(&dev));
   std::lock_guard<std::mutex> lk(mu);
-  RFDD_REQUIRE(dev >= 0 && dev < (int)addr.size(), RFDD_EINVAL, "device index out of range");
-  if (!addr[dev]) {
-    void *p = nullptr;
+  if ((int)addr.size() <= dev) addr.resize(dev + 1);
+  if (!addr[dev].scratch) {
+    void *p = nullptr, *q = nullptr;
     RFDD_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-    addr[dev] = reinterpret_cast<float *>(p);
+    RFDD_CUDA(cudaGetSymbolAddress(&q, g_noalloc_status));
+    addr[dev].scratch = reinterpret_cast<float *>(p);
+    addr[dev].status = reinterpret_cast<int *>(q);
   }
   return addr[dev];
 }
 
-void tc_gemm_complex_noalloc(cudaStream_t st, const cx<float> *A, int64_t lda, const cx<float> *B, int64_t ldb,
-                             cx<float> *C, int64_t ldc, int m, int n, int k, double alpha, double beta) {
+int tc_gemm_complex_noalloc(cudaStream_t st, const cx<float> *A, int64_t lda, const cx<float> *B, int64_t ldb,
+                            cx<float> *C, int64_t ldc, int m, int n, int k, double alpha, double beta) {
   RFDD_REQUIRE(m >= 1 && n >= 1 && k >= 1, RFDD_EINVAL, "cgemm_noalloc: sizes must be positive");
   RFDD_REQUIRE(m <= NOALLOC_MAX_M && n <= NOALLOC_MAX_N && k <= NOALLOC_MAX_K, RFDD_EINVAL,
                "cgemm_noalloc: m, n must be <= 1024 and k <= 128 (size of the static scratch)");
-  int dev = 0;
-  RFDD_CUDA(cudaGetDevice(&dev));
-  float *ws = noalloc_scratch_address(dev);
-  if (!g_tc_attr_done) {
-    RFDD_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
-    g_tc_attr_done = 1;
-  }
+  const NoallocAddr na = noalloc_addresses();
+  const int nsm = tc_device_setup();
+  float *ws = na.scratch;
   const int mtc = ceil_div(m, TC_BM), ntc = ceil_div(2 * (int64_t)n, TC_BN), nkt = ceil_div(2 * (int64_t)k, TC_BK);
   float *Ah = ws, *Al = Ah + (size_t)mtc * nkt * A_TILE;
   float *Bh = ws + NOALLOC_A_FLOATS, *Bl = Bh + (size_t)ntc * nkt * B_TILE;
@@ -718,16 +754,24 @@ void tc_gemm_complex_noalloc(cudaStream_t st, const cx<float> *A, int64_t lda, c
   tb.it[0] = {Ah, Al, Bh, Bl, reinterpret_cast<float *>(C), 2ll * ldc, m, 2 * n, nkt, mtc, ntc, 0};
   tb.count = 1;
   tb.total_tiles = mtc * ntc;
-  const long long achunks = (long long)mtc * TC_BM * nkt * 8, bchunks = (long long)ntc * TC_BN * nkt * 8;
+  tb.err = na.status;
+  tb.splits = 3;
+  // the word keeps the last call's value: cleared on the caller's stream before this call's work
+  RFDD_CUDA(cudaMemsetAsync(na.status, 0, sizeof(int), st));
+  const long long achunks = (long long)mtc * TC_BM * nkt * 8;
   pack_a_kernel<<<dim3((unsigned)std::min<long long>(ceil_div(achunks, 256), 4096), 1), 256, 0, st>>>(pa);
   RFDD_CHECK_LAUNCH();
-  pack_b_kernel<<<dim3((unsigned)std::min<long long>(ceil_div(bchunks, 256), 4096), 1), 256, 0, st>>>(pbb);
+  // B staged through shared memory (rows of B read along their length): ntc * 2 half-tile column
+  // blocks per K tile, every one inside the ntc x nkt tiles reserved for B above
+  pack_b_t_kernel<<<dim3((unsigned)(ntc * 2 * nkt), 1), 256, 0, st>>>(pbb);
   RFDD_CHECK_LAUNCH();
-  int nsm = 0;
-  RFDD_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   tc_gemm_kernel<<<std::max(1, std::min(tb.total_tiles, nsm)), TC_THREADS, TC_SMEM, st>>>(tb, (float)alpha,
                                                                                       (float)beta);
   RFDD_CHECK_LAUNCH();
+  int status = 0;
+  RFDD_CUDA(cudaMemcpyAsync(&status, na.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  RFDD_CUDA(cudaStreamSynchronize(st));
+  return status;
 }
 
 }  // namespace rfdd

@@ -3,11 +3,32 @@
 #include "dense.cuh"
 
 namespace rfdd {
-bool tc_enabled();  // false when the environment variable RFDD_TC is "0"
+// Status word (device int) that the tensor-core launches issued by the calling host thread record
+// a failed wait in (DS_WAIT_TIMEOUT), for the lifetime of the scope.  A launch outside any scope is
+// refused with RFDD_ESTATE.
+struct TcStatusScope {
+  int *prev;
+  explicit TcStatusScope(int *word);
+  ~TcStatusScope();
+  TcStatusScope(const TcStatusScope &) = delete;
+  TcStatusScope &operator=(const TcStatusScope &) = delete;
+};
+// While alive, the tensor-core kernel launches of the calling host thread record ab[0] just before
+// and ab[1] just after the kernel (not the operand packing): the probes time the MMA kernel alone.
+struct TcKernelEvents {
+  const cudaEvent_t *prev;
+  explicit TcKernelEvents(const cudaEvent_t *ab);
+  ~TcKernelEvents();
+  TcKernelEvents(const TcKernelEvents &) = delete;
+  TcKernelEvents &operator=(const TcKernelEvents &) = delete;
+};
 // C = beta*C + alpha*A*B for every item (complex, row-major, no transposes)
 void tc_gemm_complex(cudaStream_t st, const std::vector<GemmItem<cx<float>>> &items, double alpha, double beta);
 // C = beta*C + alpha*A*B for real FP32 items (same kernel, 3xTF32)
 void tc_gemm_real(cudaStream_t st, const std::vector<GemmItem<float>> &items, double alpha, double beta);
+// the same with one TF32 product per multiply (operands rounded to TF32): the throughput probe of
+// the plain TF32 tensor path, not used by the solver
+void tc_gemm_real_tf32(cudaStream_t st, const std::vector<GemmItem<float>> &items, double alpha, double beta);
 // A operand already split into TF32 hi/lo and laid out in the kernel's tiles (tc_pack_a_batched):
 // tile (mt, kt) of the operand at hi/lo + (mt * mt_stride + kt) * tile size.  Lets a factor that
 // is multiplied many times (triangular-solve updates, border products) be packed once.
@@ -31,9 +52,8 @@ void tc_pack_a_batched(cudaStream_t st, const std::vector<TcPackJob> &jobs);
 // the sub-matrix of a packed m x k_full operand starting at row r0 (a multiple of 128) and complex
 // column c0 (a multiple of 16)
 TcPackedA tc_packed_view(const float *hi, const float *lo, int64_t k_full, int64_t r0, int64_t c0);
-// returns and clears the device-side error flags of the tensor-core kernels (DS_* bits)
-int tc_take_error();
-// allocation-free variant: packed operands in a static device array (m, n <= 1024, k <= 128)
-void tc_gemm_complex_noalloc(cudaStream_t st, const cx<float> *A, int64_t lda, const cx<float> *B, int64_t ldb,
+// allocation-free variant: packed operands in a static device array (m, n <= 1024, k <= 128);
+// waits for `st` and returns the launch's DS_* status bits (0 = ok)
+int tc_gemm_complex_noalloc(cudaStream_t st, const cx<float> *A, int64_t lda, const cx<float> *B, int64_t ldb,
                              cx<float> *C, int64_t ldc, int m, int n, int k, double alpha, double beta);
 }  // namespace rfdd

@@ -116,6 +116,27 @@ def test_setup_rejects_indefinite_mass_and_size_mismatch(R):
     assert e.value.code == R.RFDD_EINVAL
 
 
+@pytest.mark.parametrize("which", ["A", "M"])
+@pytest.mark.parametrize("bad", [np.nan, np.inf, -np.inf])
+def test_setup_rejects_non_finite_values_before_device_work(R, which, bad):
+    """A NaN or infinite CSR value is refused by the host validation (RFDD_EINVAL) before any
+    kernel launch or device allocation."""
+    A, M, part, p = _small()
+    c = A if which == "A" else M
+    val = c.val.copy()
+    val[c.rowptr[5]] = bad          # first stored entry of row 5 (its mirror keeps symmetry out of play)
+    bad_csr = I.Csr(c.n, c.rowptr, c.col, val)
+    launches = R.rfdd_kernel_launches()
+    with pytest.raises(R.RfddError) as e:
+        if which == "A":
+            R.rfdd_setup(bad_csr, M, part, p)
+        else:
+            R.rfdd_setup(A, bad_csr, part, p)
+    assert e.value.code == R.RFDD_EINVAL
+    assert "non-finite" in str(e.value)
+    assert R.rfdd_kernel_launches() == launches
+
+
 def _reverse_rows(c):
     """The same matrix with every row's entries stored in decreasing column order."""
     col, val = c.col.copy(), c.val.copy()

@@ -1,6 +1,6 @@
 """Host-side pieces of bench.py that need no GPU: the workload description of the JSON line, the
-measured-peak lookup, and the rule that reports the captured DRAM traffic only while the
-kernel's sources and the timed launches match the capture."""
+measured-peak lookup, and the rule that scales the DRAM traffic of one captured launch to the
+timed launches only while the kernel's sources match the capture."""
 import os
 import sys
 
@@ -26,15 +26,15 @@ def test_measured_peaks_has_the_denominators():
         assert float(peaks[k]) > 0
 
 
-def test_traffic_reported_only_for_the_captured_kernel_and_launches(monkeypatch):
+def test_traffic_scaled_from_the_captured_ratio_only_for_the_captured_kernel(monkeypatch):
+    monkeypatch.setattr(bench, "TC_TRAFFIC_RATIO", 1.25)
     monkeypatch.setattr(bench, "TC_TRAFFIC_SOURCES_SHA256", bench.kernel_sources_sha256())
-    n, f = bench.TC_TRAFFIC_LAUNCHES_PER_SOLVE, bench.TC_TRAFFIC_FLOPS_PER_SOLVE
-    assert bench.tc_traffic_valid(n, f)
-    assert bench.tc_traffic_valid(n, f * (1 + 1e-12))      # summation order of the flop count
-    assert not bench.tc_traffic_valid(n + 1, f)            # a different launch mix
-    assert not bench.tc_traffic_valid(n, f * (1 + 1e-6))   # different shapes
+    assert bench.tc_traffic_per_launch(1.0e9) == 1.25e9     # measured/model ratio x model bytes
     monkeypatch.setattr(bench, "TC_TRAFFIC_SOURCES_SHA256", "0" * 64)
-    assert not bench.tc_traffic_valid(n, f)                # the kernel changed
+    assert bench.tc_traffic_per_launch(1.0e9) is None       # the kernel changed since the capture
+    monkeypatch.setattr(bench, "TC_TRAFFIC_RATIO", None)
+    monkeypatch.setattr(bench, "TC_TRAFFIC_SOURCES_SHA256", bench.kernel_sources_sha256())
+    assert bench.tc_traffic_per_launch(1.0e9) is None       # nothing captured
 
 
 def test_kernel_hash_covers_the_kernel_sources():

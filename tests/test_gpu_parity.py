@@ -208,6 +208,30 @@ def test_interior_chains_and_rr(R, name, prec):
         assert err_g <= 3.0 * err_o + 1e-9, (err_g, err_o)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("name", ["q1_2d_24", "q1_3d_12"])
+def test_rayleigh_ritz_on_a_well_conditioned_basis(R, name, prec):
+    """a9 to rounding: with psi = 1 and nev_b = 4 the basis Z is far from rank deficient (the
+    unit-diagonal Gram matrix Z^T M Z has its smallest eigenvalue near 1e-4..1e-2, far above the
+    1e-12 pruning threshold), so both pruning rules keep every column and the Rayleigh-Ritz values
+    of range(Z) are unique: the GPU's must equal the oracle's on the same Z to 1e-10 (FP64) /
+    1e-9 (mixed, whose Gram matrix is formed in double-FP32 arithmetic)."""
+    w, blk, z, wt, fac = oracle_case(name)
+    h = handle(R, w, prec, nev_b=4, psi=1, block=4)
+    R.rfdd_factor(h, z, wt)
+    R.rfdd_lanczos(h)
+    sigma = 0.5 * (w.alpha + w.beta)
+    Z, k, kappa = R.rfdd_interior(h, sigma)
+    G = Z.T @ (blk.Mp @ Z)
+    dg = 1.0 / np.sqrt(np.diag(G))
+    assert np.linalg.eigvalsh(G * dg[:, None] * dg[None, :])[0] >= 1e-8
+    th_g = R.rfdd_rayleigh_ritz(h)
+    th_o, _ = O.rayleigh_ritz(blk.Ap, blk.Mp, Z)
+    assert len(th_g) == len(th_o) == k
+    rel = np.abs(th_g - th_o) / np.abs(th_o)
+    assert rel.max() <= (1e-10 if prec == 0 else 1e-9), rel.max()
+
+
 def check_result(R, w, ev, X, rs, info, prec):
     ex = w.exact[(w.exact > w.alpha) & (w.exact < w.beta)] if w.exact is not None else None
     assert info["status"] == 0, info
