@@ -396,7 +396,8 @@ def run_ours(args, rank, world, local_rank):
                 "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz ({src} max clock)"}
     # throughput probes of the units this path is bound by (context for the peaks above)
     probes = {}
-    for name, which in (("tf32_tensor_tflops", 0), ("fp64_fma_tflops", 1), ("fp32_fma_tflops", 2)):
+    for name, which in (("tf32_mma_tflops", 0), ("fp64_fma_tflops", 1), ("fp32_fma_tflops", 2),
+                        ("tf32_gemm_8192_tflops", 3)):
         try:
             probes[name] = R.rfdd_peak_probe(which)
         except Exception as ex:  # a probe is context, not part of the measurement
@@ -480,9 +481,93 @@ def run_dgemm(args):
                       "fp64_equiv_tflops": flops / (ms / 1e3) / 1e12 if ms > 0 else None}), flush=True)
 
 
+def run_serve(args):
+    """The serving pattern: a seeded Poisson stream of requests of mixed size and kind (2-D Q1 and
+    3-D variable-coefficient pencils, 20..400 eigenvalues each, p in {4, 8, 16}, 8 nodes), each
+    bringing its pencil, served by the library's continuous-batching server under a 150 GiB memory
+    budget.  The arrival rate is `--load` times the single-stream capacity, measured first on the
+    stream's first requests run one at a time.  Reports eigenpairs/s (residual <= 1e-10) over the
+    stream and the p50/p99 latency from arrival to result."""
+    import torch
+    import paper_1711_09487_gb300 as R
+    torch.cuda.set_device(0)
+    R.load()
+    reqs = I.serving_stream(args.requests, seed=7)
+    pencils = [I.serving_pencil(q) for q in reqs]          # built before any clock starts
+    opts = R.rfdd_default_options(precision=R.RFDD_MIXED)
+    budget = 150 << 30
+
+    def submit(srv, q, pc):
+        A, M, part, p = pc
+        return srv.submit_pencil(A, M, part, p, q["alpha"], q["beta"], q["n_nodes"], nev_hint=q["nev"], opts=opts)
+
+    # single-stream capacity: the first requests one at a time (after one warm-up request)
+    k = min(args.capacity_sample, len(reqs))
+    srv1 = R.Server(max_inflight=1, mem_budget=budget)
+    r = srv1.wait(submit(srv1, reqs[0], pencils[0]))
+    del r
+    run_ms = []
+    for q, pc in zip(reqs[:k], pencils[:k]):
+        rid = submit(srv1, q, pc)
+        r = srv1.wait(rid)
+        run_ms.append(srv1.request_info(rid)["latency_ms"])
+        del r
+    srv1.close()
+    capacity = 1000.0 / statistics.mean(run_ms)            # requests per second, one at a time
+    rate = args.load * capacity
+    gaps = np.random.default_rng(7).exponential(1.0 / rate, len(reqs))
+    arrival = np.cumsum(gaps) - gaps[0]
+
+    srv = R.Server(max_inflight=args.inflight, mem_budget=budget)
+    ids, t_sub = [None] * len(reqs), [0.0] * len(reqs)
+    t0 = time.perf_counter()
+    for i, (q, pc) in enumerate(zip(reqs, pencils)):
+        dt = t0 + arrival[i] - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        ids[i] = submit(srv, q, pc)
+        t_sub[i] = time.perf_counter()
+    good, wrong_count, lat, done_at = 0, 0, [], []
+    per_kind = {}
+    for i, q in enumerate(reqs):
+        r = srv.wait(ids[i])
+        ev, _, rs = R.rfdd_result_get(r, vectors=False)
+        info = srv.request_info(ids[i])
+        del r
+        g = int(np.count_nonzero(rs <= 1e-10))
+        good += g
+        wrong_count += int(len(ev) != q["nev"])
+        t_done = t_sub[i] - t0 + info["latency_ms"] / 1e3      # seconds after the first arrival
+        done_at.append(t_done)
+        lat.append((t_done - arrival[i]) * 1e3)
+        k_ = per_kind.setdefault(q["kind"], {"requests": 0, "eigenpairs": 0})
+        k_["requests"] += 1
+        k_["eigenpairs"] += g
+    st = srv.stats()
+    srv.close()
+    wall = max(done_at)
+    lat_s = sorted(lat)
+    line = {"mode": "serve", "metric": METRIC, "value": good / wall, "unit": UNIT, "requests": len(reqs),
+            "eigenpairs": good, "wall_s": wall, "latency_ms": {
+                "p50": lat_s[len(lat_s) // 2],
+                "p99": lat_s[min(len(lat_s) - 1, int(math.ceil(0.99 * len(lat_s))) - 1)],
+                "max": lat_s[-1]},
+            "arrival_rate_per_s": rate, "load": args.load, "single_stream_capacity_per_s": capacity,
+            "capacity_sample_requests": k, "max_inflight": args.inflight, "mem_budget_bytes": budget,
+            "requests_with_wrong_count": wrong_count, "per_kind": per_kind, "server": st,
+            "config": {"workload": "serving stream: seeded Poisson arrivals, 50% 2D Q1 N in 64..256, 50% 3D "
+                                   "variable-kappa 7-point N in 24..48, 20..400 eigenvalues, p in {4,8,16}, 8 nodes",
+                       "seed": 7, "precision": "mixed"}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--mode", default="bench", choices=["bench", "one-solve", "gemm", "dgemm"])
+    ap.add_argument("--mode", default="bench", choices=["bench", "one-solve", "gemm", "dgemm", "serve"])
+    ap.add_argument("--requests", type=int, default=256, help="serve mode: requests in the stream")
+    ap.add_argument("--load", type=float, default=0.7, help="serve mode: arrival rate / single-stream capacity")
+    ap.add_argument("--inflight", type=int, default=4, help="serve mode: requests running at once")
+    ap.add_argument("--capacity-sample", type=int, default=8, help="serve mode: requests timed one at a time")
     ap.add_argument("--gemm", type=int, nargs=3, default=[8192, 8192, 128], metavar=("M", "N", "K"))
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -504,6 +589,9 @@ def main():
         return
     if args.mode == "dgemm":
         run_dgemm(args)
+        return
+    if args.mode == "serve":
+        run_serve(args)
         return
     if args.impl == "reference":
         run_reference(args, rank, world)

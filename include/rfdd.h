@@ -111,8 +111,10 @@ typedef struct {
   double t_total_ms;
   int32_t status;       /* RFDD_OK or RFDD_NOT_CONVERGED */
   double sigma;         /* real shift the interior step used (Eq. prol2): opt.sigma or (alpha+beta)/2,
-                           moved by 1e-6 (beta - alpha) per attempt, at most three times, while it
-                           lies within 1e-8 max(1, |sigma|) of an eigenvalue of some (B_j, M_B^(j)) */
+                           moved, at most three times, while it lies within tau max(1, |sigma|) of
+                           an eigenvalue of some (B_j, M_B^(j)): FP64 tau = 1e-8, move
+                           1e-6 (beta - alpha); mixed (FP32 factors) tau = 1e-5, move
+                           max(1e-3 (beta - alpha), 2 tau max(1, |sigma|)) */
 } rfdd_info;
 
 /* Fill *opt with the defaults listed above. */
@@ -152,6 +154,13 @@ int rfdd_layout(const rfdd_handle *h, int64_t *off, int64_t *perm, int32_t *p_ou
  * of the process (its release threshold is raised at the first rfdd_setup on a device); a caller
  * that needs the memory back can trim the pool (cudaMemPoolTrimTo) after rfdd_destroy. */
 void rfdd_destroy(rfdd_handle *h);
+
+/* Frees the device memory of the last solve on the handle -- the factors of every B_j(zeta_l) and
+ * S(zeta_l), their inverted diagonal blocks and packed copies, the interior factors, the Lanczos
+ * basis, Z and the completion block -- and keeps the set-up (pencil, partition, maps), so that a
+ * resident pencil holds only its set-up between solves.  Step-level calls that need factors then
+ * return RFDD_ESTATE until the next rfdd_factor or rfdd_solve.  Waits for the handle's streams. */
+int rfdd_release(rfdd_handle *h);
 
 /* ---- full solve: Alg. 3 (RF-DDES) + completion ------------------------------------------
  * Runs a0-a10 for [alpha, beta] with n_nodes quadrature poles.  Factors of the previous solve
@@ -307,10 +316,12 @@ int rfdd_cgemm_noalloc(int64_t m, int64_t n, int64_t k, const float *A, int64_t 
  * Returns RFDD_ESTATE if launches were recorded without rfdd_profile(1). */
 long long rfdd_kernel_launches(void);
 /* Throughput probe of one arithmetic unit on the current device, in TFLOP/s (best of three timed
- * launches after a warm-up, CUDA events): which = 0 the plain TF32 tensor path (tcgen05
- * kind::tf32, one MMA per product; a real 8192^3 GEMM, the MMA kernel alone timed, operand packing
- * excluded); 1 FP64 fused multiply-add on the CUDA cores; 2 FP32 fused multiply-add on the CUDA
- * cores.  Allocates about 1.9 GB (which = 0) or a few MB on a stream of its own. */
+ * launches after a warm-up, CUDA events): which = 0 the tensor pipe's TF32 rate (tcgen05
+ * kind::tf32 MMAs of 128 x 256 x 8 issued back to back from operand tiles held in shared memory,
+ * one CTA per SM); 1 FP64 fused multiply-add on the CUDA cores; 2 FP32 fused multiply-add on the
+ * CUDA cores; 3 a plain TF32 GEMM through the solver's tensor-core kernel (one MMA per product,
+ * operands fed from memory; a real 8192^3 GEMM, the MMA kernel alone timed, operand packing
+ * excluded).  Allocates about 1.9 GB (which = 3) or a few MB, on a stream of its own. */
 int rfdd_peak_probe(int32_t which, double *tflops);
 int rfdd_profile(int32_t enable);
 int rfdd_profile_get(int32_t kind, int64_t *launches, double *ms, double *flops);
@@ -331,6 +342,77 @@ int rfdd_result_ready(const rfdd_result *r);
 /* Device bytes a solve with these parameters needs (factors, Schur complements, workspaces);
  * used for admission against a memory budget. */
 int rfdd_memory_estimate(const rfdd_handle *h, int32_t n_nodes, int64_t nev_guess, size_t *bytes);
+
+/* ---- serving: continuous batching of interval requests (no counterpart in the paper) --------
+ * Many clients asking the interval problem of Section 1 on one GPU.  A pencil is set up once
+ * (rfdd_server_add_pencil runs rfdd_setup on the calling thread and returns its errors) and stays
+ * resident; a request names a resident pencil and an interval.  max_inflight worker threads take
+ * waiting requests in arrival order, each solving on the stream of its pencil's handle, so the
+ * work of different requests overlaps on the device.  A request starts when a worker is free, no
+ * other request of its pencil runs (a handle serves one solve at a time) and its device-memory
+ * estimate (rfdd_memory_estimate with nev_hint, or 100 when 0) fits in what mem_budget has left;
+ * the first waiting request that satisfies these starts, and the oldest waiting request is passed
+ * over at most max_bypass times.  After each solve the handle's factors are released
+ * (rfdd_release).  Results are those of rfdd_solve on the same pencil and interval; they do not
+ * depend on what else runs. */
+typedef struct rfdd_server rfdd_server;
+typedef struct {
+  size_t mem_budget;     /* device bytes the running requests may hold by estimate (default 150 GiB) */
+  int32_t max_inflight;  /* requests running at once, one worker thread each (default 4, max 64) */
+  int32_t max_bypass;    /* times the oldest waiting request may be passed over (default 8) */
+  int32_t device;        /* CUDA device; -1 = the device current at rfdd_server_create (default) */
+} rfdd_server_options;
+
+typedef struct {
+  int32_t status;        /* -1 waiting, -2 running, else the solve's return code (RFDD_OK,
+                            RFDD_NOT_CONVERGED or an error; RFDD_ESTATE if dropped at destroy) */
+  int64_t pencil;
+  int64_t nev;           /* eigenpairs returned */
+  size_t bytes;          /* device-memory estimate it was admitted with */
+  double queue_ms;       /* submit -> start (host steady clock) */
+  double run_ms;         /* start -> done */
+  double latency_ms;     /* submit -> done */
+} rfdd_request_info;
+
+typedef struct {
+  int64_t completed, failed, waiting;
+  int32_t running, peak_running;
+  size_t in_use, peak_in_use;   /* estimated device bytes of the running requests */
+  int64_t pencils;              /* resident pencils */
+} rfdd_server_stats;
+
+void rfdd_server_default_options(rfdd_server_options *o);
+/* RFDD_EINVAL for max_inflight outside [1, 64], a zero budget or a negative max_bypass. */
+int rfdd_server_create(const rfdd_server_options *o, rfdd_server **out);
+/* Set up a pencil (same inputs and errors as rfdd_setup; opt.stream is ignored: each resident
+ * pencil gets a stream of its own).  *pencil_id identifies it in later calls. */
+int rfdd_server_add_pencil(rfdd_server *s, const rfdd_csr *A, const rfdd_csr *M, const int32_t *part, int32_t p,
+                           const rfdd_options *opt, int64_t *pencil_id);
+/* Queue a request; returns at once.  RFDD_EADMIT when its estimate exceeds the whole budget (it
+ * could never start), RFDD_EINVAL for an unknown pencil, alpha >= beta or n_nodes < 1. */
+int rfdd_server_submit(rfdd_server *s, int64_t pencil_id, double alpha, double beta, int32_t n_nodes,
+                       int64_t nev_hint, int64_t *request_id);
+/* Queue a request that brings its own pencil (host CSR copied by this call; no device work here):
+ * the worker that runs it sets the pencil up, solves and frees it, so its latency includes the
+ * set-up.  It is admitted by the estimate of rfdd_memory_estimate plus the set-up, from the block
+ * sizes that a host scan of the pattern and labels gives.  Returns at once; RFDD_EADMIT and
+ * RFDD_EINVAL as for rfdd_server_submit, RFDD_EINVAL also for labels or columns out of range
+ * (the other rfdd_setup errors come back as the request's status). */
+int rfdd_server_submit_pencil(rfdd_server *s, const rfdd_csr *A, const rfdd_csr *M, const int32_t *part, int32_t p,
+                              const rfdd_options *opt, double alpha, double beta, int32_t n_nodes,
+                              int64_t nev_hint, int64_t *request_id);
+/* Wait up to timeout_ms (< 0: no limit; 0: poll) for a request.  *done = 1 when it finished; then
+ * *out receives its result (NULL if the solve failed; see rfdd_server_request_info for the code),
+ * which the caller owns and frees with rfdd_result_free.  A result is handed out once (RFDD_ESTATE
+ * on a second wait). */
+int rfdd_server_wait(rfdd_server *s, int64_t request_id, double timeout_ms, int32_t *done, rfdd_result **out);
+int rfdd_server_request_info(rfdd_server *s, int64_t request_id, rfdd_request_info *info);
+int rfdd_server_get_stats(rfdd_server *s, rfdd_server_stats *out);
+/* Frees a resident pencil; RFDD_ESTATE while requests of it wait or run (and for the pencil of a
+ * rfdd_server_submit_pencil request, which the server frees itself). */
+int rfdd_server_remove_pencil(rfdd_server *s, int64_t pencil_id);
+/* Drops waiting requests, waits for running ones, frees every pencil and unclaimed result. */
+void rfdd_server_destroy(rfdd_server *s);
 
 #ifdef __cplusplus
 }

@@ -41,7 +41,10 @@ SYMBOLS = [
     "rfdd_filter_apply", "rfdd_lanczos", "rfdd_interior", "rfdd_rayleigh_ritz", "rfdd_solve_async",
     "rfdd_result_ready", "rfdd_memory_estimate", "rfdd_sym_eig", "rfdd_kernel_launches", "rfdd_profile",
     "rfdd_profile_get", "rfdd_profile_busy", "rfdd_cgemm", "rfdd_dgemm", "rfdd_cgemm_noalloc", "rfdd_inertia",
-    "rfdd_polish", "rfdd_peak_probe", "rfdd_profile_bytes",
+    "rfdd_polish", "rfdd_peak_probe", "rfdd_profile_bytes", "rfdd_release",
+    "rfdd_server_default_options", "rfdd_server_create", "rfdd_server_add_pencil", "rfdd_server_submit",
+    "rfdd_server_wait", "rfdd_server_submit_pencil", "rfdd_server_request_info", "rfdd_server_get_stats", "rfdd_server_remove_pencil",
+    "rfdd_server_destroy",
 ]
 
 
@@ -71,6 +74,28 @@ class rfdd_info(C.Structure):
                 ("t_lanczos_ms", C.c_double), ("t_interior_ms", C.c_double), ("t_rr_ms", C.c_double),
                 ("t_complete_ms", C.c_double), ("t_total_ms", C.c_double), ("status", C.c_int32),
                 ("sigma", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class rfdd_server_options(C.Structure):
+    _fields_ = [("mem_budget", C.c_size_t), ("max_inflight", C.c_int32), ("max_bypass", C.c_int32),
+                ("device", C.c_int32)]
+
+
+class rfdd_request_info(C.Structure):
+    _fields_ = [("status", C.c_int32), ("pencil", C.c_int64), ("nev", C.c_int64), ("bytes", C.c_size_t),
+                ("queue_ms", C.c_double), ("run_ms", C.c_double), ("latency_ms", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class rfdd_server_stats(C.Structure):
+    _fields_ = [("completed", C.c_int64), ("failed", C.c_int64), ("waiting", C.c_int64),
+                ("running", C.c_int32), ("peak_running", C.c_int32), ("in_use", C.c_size_t),
+                ("peak_in_use", C.c_size_t), ("pencils", C.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -129,6 +154,20 @@ def load(path: str | None = None):
     lib.rfdd_profile_busy.argtypes = [i32, dp]
     lib.rfdd_peak_probe.argtypes = [i32, dp]
     lib.rfdd_profile_bytes.argtypes = [i32, dp]
+    lib.rfdd_release.argtypes = [vp]
+    lib.rfdd_server_default_options.argtypes = [vp]
+    lib.rfdd_server_default_options.restype = None
+    lib.rfdd_server_create.argtypes = [vp, C.POINTER(vp)]
+    lib.rfdd_server_add_pencil.argtypes = [vp, vp, vp, C.POINTER(i32), i32, vp, C.POINTER(i64)]
+    lib.rfdd_server_submit.argtypes = [vp, i64, C.c_double, C.c_double, i32, i64, C.POINTER(i64)]
+    lib.rfdd_server_wait.argtypes = [vp, i64, C.c_double, C.POINTER(i32), C.POINTER(vp)]
+    lib.rfdd_server_submit_pencil.argtypes = [vp, vp, vp, C.POINTER(i32), i32, vp, C.c_double, C.c_double, i32,
+                                              i64, C.POINTER(i64)]
+    lib.rfdd_server_request_info.argtypes = [vp, i64, vp]
+    lib.rfdd_server_get_stats.argtypes = [vp, vp]
+    lib.rfdd_server_remove_pencil.argtypes = [vp, i64]
+    lib.rfdd_server_destroy.argtypes = [vp]
+    lib.rfdd_server_destroy.restype = None
     _lib = lib
     return lib
 
@@ -443,6 +482,95 @@ def rfdd_profile_bytes(kind: int) -> float:
     b = C.c_double()
     _check(load().rfdd_profile_bytes(int(kind), C.byref(b)))
     return float(b.value)
+
+
+def rfdd_release(h: Handle):
+    """Free the factors and solve buffers of the handle's last solve (its set-up stays)."""
+    _check(load().rfdd_release(h.ptr))
+
+
+def rfdd_server_default_options(**overrides) -> rfdd_server_options:
+    o = rfdd_server_options()
+    load().rfdd_server_default_options(C.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+class Server:
+    """Owns an rfdd_server* (continuous batching of interval requests on one GPU)."""
+
+    def __init__(self, **opts):
+        lib = load()
+        self.opts = rfdd_server_default_options(**opts)
+        out = C.c_void_p()
+        _check(lib.rfdd_server_create(C.byref(self.opts), C.byref(out)))
+        self.ptr = out
+        self.n_of = {}    # pencil id -> n
+        self.n_req = {}   # request id -> n, for requests that brought their own pencil
+
+    def add_pencil(self, A, M, part, p: int, opts: rfdd_options | None = None) -> int:
+        a, m = _Csr(_as_csr(A)), _Csr(_as_csr(M))
+        pt = np.ascontiguousarray(part, dtype=np.int32)
+        o = opts if opts is not None else rfdd_default_options()
+        pid = C.c_int64()
+        _check(load().rfdd_server_add_pencil(self.ptr, C.byref(a.s), C.byref(m.s),
+                                             pt.ctypes.data_as(C.POINTER(C.c_int32)), int(p), C.byref(o),
+                                             C.byref(pid)))
+        self.n_of[pid.value] = a.s.n
+        return pid.value
+
+    def submit(self, pencil: int, alpha: float, beta: float, n_nodes: int, nev_hint: int = 0) -> int:
+        rid = C.c_int64()
+        _check(load().rfdd_server_submit(self.ptr, int(pencil), float(alpha), float(beta), int(n_nodes),
+                                         int(nev_hint), C.byref(rid)))
+        return rid.value
+
+    def submit_pencil(self, A, M, part, p: int, alpha: float, beta: float, n_nodes: int, nev_hint: int = 0,
+                      opts: rfdd_options | None = None) -> int:
+        """Queue a request that brings its own pencil (set up, solved and freed by the server)."""
+        a, m = _Csr(_as_csr(A)), _Csr(_as_csr(M))
+        pt = np.ascontiguousarray(part, dtype=np.int32)
+        o = opts if opts is not None else rfdd_default_options()
+        rid = C.c_int64()
+        _check(load().rfdd_server_submit_pencil(self.ptr, C.byref(a.s), C.byref(m.s),
+                                                pt.ctypes.data_as(C.POINTER(C.c_int32)), int(p), C.byref(o),
+                                                float(alpha), float(beta), int(n_nodes), int(nev_hint),
+                                                C.byref(rid)))
+        self.n_req[rid.value] = a.s.n
+        return rid.value
+
+    def wait(self, request: int, timeout_ms: float = -1.0):
+        """Result of a finished request (None while it runs); raises if its solve failed."""
+        done, out = C.c_int32(), C.c_void_p()
+        _check(load().rfdd_server_wait(self.ptr, int(request), float(timeout_ms), C.byref(done), C.byref(out)))
+        if not done.value:
+            return None
+        info = self.request_info(request)
+        if out.value is None:
+            raise RfddError(info["status"], f"request {request} failed: {rfdd_status_string(info['status'])}")
+        n = self.n_req.pop(request, None) or self.n_of[info["pencil"]]
+        return Result(out.value, info["status"], n)
+
+    def request_info(self, request: int) -> dict:
+        inf = rfdd_request_info()
+        _check(load().rfdd_server_request_info(self.ptr, int(request), C.byref(inf)))
+        return inf.as_dict()
+
+    def stats(self) -> dict:
+        st = rfdd_server_stats()
+        _check(load().rfdd_server_get_stats(self.ptr, C.byref(st)))
+        return st.as_dict()
+
+    def remove_pencil(self, pencil: int):
+        _check(load().rfdd_server_remove_pencil(self.ptr, int(pencil)))
+
+    def close(self):
+        if getattr(self, "ptr", None) is not None and self.ptr.value and _lib is not None:
+            _lib.rfdd_server_destroy(self.ptr)
+            self.ptr = C.c_void_p(None)
+
+    __del__ = close
 
 
 def rfdd_kernel_launches() -> int:

@@ -153,4 +153,16 @@ enum DevStatus : int {
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
+// Sizes that set the device memory of a solve (admission estimates).
+struct SolveShape {
+  int64_t n = 0, s = 0, nnz = 0;
+  int p = 0;
+  const int64_t *d = nullptr;  // interior sizes d_j
+  const int64_t *D = nullptr;  // bordered sizes D_j = d_j + s_j
+  int precision = RFDD_MIXED, keep_schur = 0, min_guard = 8, m_align = 128;
+  double guard_frac = 0.3;
+};
+size_t factor_bytes_of(const SolveShape &g, int nc);
+size_t solve_bytes_of(const SolveShape &g, int nc, int64_t nev_guess, bool with_setup);
+
 }  // namespace rfdd

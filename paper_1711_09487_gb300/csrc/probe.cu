@@ -1,6 +1,7 @@
 // Throughput probes of the arithmetic units the solver's kernels are bound by (measurement hooks,
-// no counterpart in the paper): the plain TF32 tensor path (tcgen05 kind::tf32, one MMA per
-// product), and fused multiply-adds on the CUDA cores in FP64 and FP32.  Each probe is timed with
+// no counterpart in the paper): the tensor pipe's TF32 MMA rate (operands resident in shared
+// memory), a plain TF32 GEMM through the solver's tensor-core kernel (one MMA per product,
+// operands fed from memory), and fused multiply-adds on the CUDA cores in FP64 and FP32.  Each probe is timed with
 // CUDA events on its own stream after a warm-up launch; the best of a few launches is returned.
 #include <algorithm>
 #include <vector>
@@ -118,6 +119,25 @@ double tf32_probe(cudaStream_t st) {
   return best;
 }
 
+double mma_probe(cudaStream_t st) {
+  int *status = nullptr;
+  RFDD_CUDA(cudaMallocAsync((void **)&status, sizeof(int), st));
+  RFDD_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
+  double r = 0.0;
+  try {
+    r = tc_mma_probe_tflops(st, status);
+  } catch (...) {
+    cudaFreeAsync(status, st);
+    throw;
+  }
+  int stt = 0;
+  RFDD_CUDA(cudaMemcpyAsync(&stt, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  RFDD_CUDA(cudaFreeAsync(status, st));
+  RFDD_CUDA(cudaStreamSynchronize(st));
+  RFDD_REQUIRE(stt == 0, RFDD_ECUDA, "MMA probe: a wait timed out");
+  return r;
+}
+
 }  // namespace
 
 double peak_probe(int which) {
@@ -125,10 +145,11 @@ double peak_probe(int which) {
   RFDD_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
   double r = 0.0;
   try {
-    if (which == 0) r = tf32_probe(st);
+    if (which == 0) r = mma_probe(st);
     else if (which == 1) r = fma_probe<double>(st);
     else if (which == 2) r = fma_probe<float>(st);
-    else throw Error(RFDD_EINVAL, "peak probe: which must be 0 (TF32 tensor), 1 (FP64 FMA) or 2 (FP32 FMA)");
+    else if (which == 3) r = tf32_probe(st);
+    else throw Error(RFDD_EINVAL, "peak probe: which must be 0..3");
   } catch (...) {
     cudaStreamSynchronize(st);
     cudaStreamDestroy(st);

@@ -705,24 +705,66 @@ void do_upload(rfdd_handle *h) {
 constexpr int NBO_LU = 256;  // outer block (trailing-update depth) of the factorisations
 constexpr int NBO = 256;     // outer block of the triangular solves
 
-size_t factor_bytes(const rfdd_handle *h, int nc, size_t scal) {
+}  // namespace
+
+// Device bytes of the factors of one solve (a2-a5 storage, inverted diagonal blocks, packed
+// tensor-core copies in the mixed solve, pivots).
+size_t rfdd::factor_bytes_of(const SolveShape &g, int nc) {
+  const bool mixed = g.precision == RFDD_MIXED;
+  const size_t scal = mixed ? sizeof(cx<float>) : sizeof(cx<double>);
   size_t e = 0;
-  for (int j = 0; j < h->p; ++j) e += (size_t)h->D[j] * h->D[j];
+  for (int j = 0; j < g.p; ++j) e += (size_t)g.D[j] * g.D[j];
   size_t b = (size_t)nc * e * scal;
-  b += (size_t)nc * h->s * h->s * scal * (h->opt.keep_schur ? 2 : 1);
-  size_t inv = (size_t)block_inverse_elems(h->s, NBO);  // inverted diagonal blocks of L and U
-  for (int j = 0; j < h->p; ++j) inv += (size_t)block_inverse_elems(h->d[j], NBO);
+  b += (size_t)nc * g.s * g.s * scal * (g.keep_schur ? 2 : 1);
+  size_t inv = (size_t)block_inverse_elems(g.s, 256);  // inverted diagonal blocks of L and U
+  for (int j = 0; j < g.p; ++j) inv += (size_t)block_inverse_elems(g.d[j], 256);
   b += 2 * (size_t)nc * inv * scal;
-  if (scal == sizeof(cx<float>)) {  // packed tensor-core copies of the solve operands (hi + lo)
-    size_t pk = (size_t)h->s * h->s + 2 * (size_t)block_inverse_elems(h->s, NBO);
-    for (int j = 0; j < h->p; ++j)
-      pk += (size_t)h->D[j] * h->D[j] - (size_t)(h->D[j] - h->d[j]) * (h->D[j] - h->d[j]) +
-            2 * (size_t)block_inverse_elems(h->d[j], NBO);
+  if (mixed) {  // packed tensor-core copies of the solve operands (hi + lo)
+    size_t pk = (size_t)g.s * g.s + 2 * (size_t)block_inverse_elems(g.s, 256);
+    for (int j = 0; j < g.p; ++j)
+      pk += (size_t)g.D[j] * g.D[j] - (size_t)(g.D[j] - g.d[j]) * (g.D[j] - g.d[j]) +
+            2 * (size_t)block_inverse_elems(g.d[j], 256);
     b += (size_t)nc * pk * 2 * scal;
   }
-  b += (size_t)nc * (h->dsum + h->s) * sizeof(int);
+  int64_t dsum = 0;
+  for (int j = 0; j < g.p; ++j) dsum += g.d[j];
+  b += (size_t)nc * (dsum + g.s) * sizeof(int);
   return b;
 }
+
+// Device bytes a solve holds at its peak: the factors, the completion blocks for about nev_guess
+// pairs, the Lanczos basis; plus, when with_setup, the resident set-up (union CSR with both
+// values, its double-FP32 split, maps).
+size_t rfdd::solve_bytes_of(const SolveShape &g, int nc, int64_t nev_guess, bool with_setup) {
+  const size_t scal = g.precision == RFDD_MIXED ? sizeof(cx<float>) : sizeof(cx<double>);
+  size_t b = factor_bytes_of(g, nc);
+  int64_t m = nev_guess + std::max<int64_t>((int64_t)std::ceil(g.guard_frac * nev_guess), g.min_guard);
+  if (g.m_align > 1) m = (m + g.m_align - 1) / g.m_align * g.m_align;
+  b += (size_t)nc * g.n * m * (sizeof(cx<double>) * 4 + scal * 2);  // completion blocks
+  b += (size_t)g.s * g.s * sizeof(double);                           // Lanczos basis
+  if (with_setup) b += (size_t)g.nnz * (4 + 8 + 8 + 16) + (size_t)g.n * 64;
+  return b;
+}
+
+namespace {
+
+rfdd::SolveShape shape_of(const rfdd_handle *h) {
+  rfdd::SolveShape g;
+  g.n = h->n;
+  g.s = h->s;
+  g.p = h->p;
+  g.nnz = h->nnz;
+  g.d = h->d.data();
+  g.D = h->D.data();
+  g.precision = h->opt.precision;
+  g.keep_schur = h->opt.keep_schur;
+  g.guard_frac = h->opt.guard_frac;
+  g.min_guard = h->opt.min_guard;
+  g.m_align = h->opt.m_align;
+  return g;
+}
+
+size_t factor_bytes(const rfdd_handle *h, int nc) { return rfdd::factor_bytes_of(shape_of(h), nc); }
 
 void pack_factor_operands(rfdd_handle *h);
 
@@ -2162,9 +2204,8 @@ void set_nodes(rfdd_handle *h, int nc, const double *z, const double *w) {
 }
 
 void factor(rfdd_handle *h) {
-  const size_t scal = is_mixed(h) ? sizeof(cx<float>) : sizeof(cx<double>);
   if (h->opt.mem_budget > 0) {
-    const size_t need = factor_bytes(h, h->nnodes, scal);
+    const size_t need = factor_bytes(h, h->nnodes);
     RFDD_REQUIRE(need <= h->opt.mem_budget, RFDD_EADMIT,
                  "factorisation needs " + std::to_string(need) + " bytes, budget " + std::to_string(h->opt.mem_budget));
   }
@@ -2189,7 +2230,7 @@ void run_solve(rfdd_handle *h, double alpha, double beta, int nc, rfdd_result *r
   std::vector<cx<double>> z, w;
   quadrature(alpha, beta, nc, h->opt.quad_rule, z, w);
   if (h->opt.mem_budget > 0) {  // admission before any device work of the solve
-    const size_t need = factor_bytes(h, nc, is_mixed(h) ? sizeof(cx<float>) : sizeof(cx<double>));
+    const size_t need = factor_bytes(h, nc);
     RFDD_REQUIRE(need <= h->opt.mem_budget, RFDD_EADMIT,
                  "solve needs " + std::to_string(need) + " bytes of factors, budget " +
                      std::to_string(h->opt.mem_budget));
@@ -2231,23 +2272,27 @@ void run_solve(rfdd_handle *h, double alpha, double beta, int nc, rfdd_result *r
   }
   {
     Timer t(h->st);
-    // Guard on the shift: sigma at, or within 1e-8 max(1, |sigma|) of, an eigenvalue of some
-    // pencil (B_j, M_B^(j)) leaves B_sigma (nearly) singular.  The shift then moves by
-    // 1e-6 (beta - alpha) and the interior step is redone, at most three times.
+    // Guard on the shift: sigma at, or within tau max(1, |sigma|) of, an eigenvalue of some
+    // pencil (B_j, M_B^(j)) leaves B_sigma (nearly) singular.  The shift then moves and the
+    // interior step is redone, at most three times.  FP64 factors: tau = 1e-8, move
+    // 1e-6 (beta - alpha).  FP32 factors (mixed) resolve B_sigma only to about 1e-7 relative, so
+    // there tau = 1e-5 and the move is max(1e-3 (beta - alpha), 2 tau max(1, |sigma|)).
+    const double tau = is_mixed(h) ? 1e-5 : 1e-8;
     double sig = sigma;
     for (int attempt = 0;; ++attempt) {
       bool near = false;
       try {
         if (is_mixed(h)) interior_impl<float>(h, sig);
         else interior_impl<double>(h, sig);
-        near = h->interior_gap < 1e-8 * std::max(1.0, std::fabs(sig));
+        near = h->interior_gap < tau * std::max(1.0, std::fabs(sig));
       } catch (const Error &e) {
         if (e.code != RFDD_ESINGULAR || attempt >= 3) throw;
         near = true;
       }
       if (!near || attempt >= 3) break;
       RFDD_LOGF("interior: sigma %.17g within %.3e of a subdomain eigenvalue, moved", sig, h->interior_gap);
-      sig += 1e-6 * (beta - alpha);
+      sig += is_mixed(h) ? std::max(1e-3 * (beta - alpha), 2.0 * tau * std::max(1.0, std::fabs(sig)))
+                         : 1e-6 * (beta - alpha);
     }
     res->info.sigma = sig;
     res->info.t_interior_ms = t.ms();
@@ -2410,6 +2455,24 @@ void rfdd_destroy(rfdd_handle *h) {
   delete h;                            // enqueues the stream-ordered frees of its buffers on st
   if (st) cudaStreamSynchronize(st);
   if (own && st) cudaStreamDestroy(st);
+}
+
+int rfdd_release(rfdd_handle *h) {
+  if (!h) return RFDD_EINVAL;
+  return guarded([&] {
+    interior_join(h, false);  // a started interior factorisation finishes before its buffers go
+    RFDD_CUDA(cudaStreamSynchronize(h->st));
+    if (h->st2) RFDD_CUDA(cudaStreamSynchronize(h->st2));
+    for (Buf *b : {&h->fac, &h->boff_dev, &h->Doff_dev, &h->pivB, &h->Sfac, &h->pivS, &h->Skeep, &h->BLinv,
+                   &h->BUinv, &h->SLinv, &h->SUinv, &h->Pk, &h->IBs, &h->Ipiv, &h->IRLinv, &h->IRUinv, &h->I_doff,
+                   &h->I_boffr_dev, &h->I_zs, &h->Q, &h->Zb, &h->X0})
+      b->release();
+    h->have_factors = false;
+    h->I_ready = false;
+    h->mu = h->kz = h->kappa = h->m0 = 0;
+    h->rr_theta.clear();
+    RFDD_CUDA(cudaStreamSynchronize(h->st));
+  });
 }
 
 int rfdd_factor(rfdd_handle *h, int32_t n_nodes, const double *z, const double *w) {
@@ -2906,14 +2969,8 @@ int rfdd_profile_bytes(int32_t kind, double *bytes) {
 }
 
 int rfdd_memory_estimate(const rfdd_handle *h, int32_t n_nodes, int64_t nev_guess, size_t *bytes) {
-  if (!h || !bytes || n_nodes < 1) return RFDD_EINVAL;
-  const size_t scal = h->opt.precision == RFDD_MIXED ? sizeof(cx<float>) : sizeof(cx<double>);
-  size_t b = factor_bytes(h, n_nodes, scal);
-  int64_t m = nev_guess + std::max<int64_t>((int64_t)std::ceil(h->opt.guard_frac * nev_guess), h->opt.min_guard);
-  if (h->opt.m_align > 1) m = (m + h->opt.m_align - 1) / h->opt.m_align * h->opt.m_align;
-  b += (size_t)n_nodes * h->n * m * (sizeof(cx<double>) * 4 + scal * 2);  // completion blocks
-  b += (size_t)h->s * h->s * sizeof(double);                               // Lanczos basis
-  *bytes = b;
+  if (!h || !bytes || n_nodes < 1 || nev_guess < 0) return RFDD_EINVAL;
+  *bytes = rfdd::solve_bytes_of(shape_of(h), n_nodes, nev_guess, false);
   return RFDD_OK;
 }
 

@@ -60,7 +60,22 @@ struct TcItem {
   long long ldc;  // real leading dimension of C
   int m, n2, nkt, mtc, ntc, tile0;  // tile0: first global tile index of this item
   long long amts;  // A tiles between consecutive 128-row tiles (0: nkt, a packed A of its own)
+  int colmajor;    // 1: tiles walk down the columns (mt fastest), 0: along the rows (nt fastest)
 };
+
+// Position of tile `local` of an item.  Along the rows, the CTAs running at once share one row of
+// A tiles and sweep all of B; down the columns they share one column of B tiles and sweep all of A.
+// Down the columns is chosen when the item's packed A fits comfortably in L2 and B is wide, so that
+// A stays cached while each B column is read once (tc_tile_order).
+__device__ __forceinline__ void tile_pos(const TcItem &it, int local, int &mt, int &nt) {
+  if (it.colmajor) {
+    mt = local % it.mtc;
+    nt = local / it.mtc;
+  } else {
+    mt = local / it.ntc;
+    nt = local % it.ntc;
+  }
+}
 constexpr int TC_MAXB = 64;
 struct TcBatchP {
   TcItem it[TC_MAXB];
@@ -189,7 +204,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
       long long g = 0;  // global k-tile counter (stage ring position)
       for (int tile = blockIdx.x; tile < b.total_tiles && !abort_s; tile += gridDim.x) {
         const TcItem &it = b.it[find_item(b, tile)];
-        const int local = tile - it.tile0, mt = local / it.ntc, nt = local % it.ntc;
+        const int local = tile - it.tile0;
+        int mt, nt;
+        tile_pos(it, local, mt, nt);
         const long long ams = it.amts ? it.amts : it.nkt;
         const float *Ahi = it.Ahi + (long long)mt * ams * A_TILE, *Alo = it.Alo + (long long)mt * ams * A_TILE;
         const float *Bhi = it.Bhi + (long long)nt * it.nkt * B_TILE, *Blo = it.Blo + (long long)nt * it.nkt * B_TILE;
@@ -266,7 +283,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
     int lt = 0;
     for (int tile = blockIdx.x; tile < b.total_tiles; tile += gridDim.x, ++lt) {
       const TcItem &it = b.it[find_item(b, tile)];
-      const int local = tile - it.tile0, mt = local / it.ntc, nt = local % it.ntc;
+      const int local = tile - it.tile0;
+      int mt, nt;
+      tile_pos(it, local, mt, nt);
       const int acc = lt & 1;
       const bool ready = mbar_wait(smem_u32(&tfull_bar[acc]), (uint32_t)((lt >> 1) & 1), &abort_s);
       // the whole warp takes the same branch (tcgen05.ld below is a warp-collective)
@@ -310,6 +329,84 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_BN) : "memory");
   }
+}
+
+// ---------------------------------------------------------------------------------------
+// Tensor-pipe throughput probe: one CTA per SM issues `iters` x 4 kind::tf32 MMAs of
+// 128 x 256 x 8 from operand tiles that stay in shared memory (no loads), into one TMEM
+// accumulator, then waits for their completion on an mbarrier (bounded; DS_WAIT_TIMEOUT into *err
+// on time-out).  Measures the MMA issue rate alone, not the operand feed.
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(128, 1) tf32_mma_probe_kernel(int iters, int *err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t done_bar;
+  __shared__ uint32_t tmem_s;
+  __shared__ volatile int abort_s;
+  const int warp = threadIdx.x >> 5;
+  // operand tiles: zeros (the rate does not depend on the values)
+  for (int i = threadIdx.x; i < (A_TILE + B_TILE); i += blockDim.x) reinterpret_cast<float *>(base)[i] = 0.f;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&done_bar), 1);
+    abort_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_s)),
+                 "r"(TC_BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = tmem_s;
+  if (threadIdx.x == 0) {
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
+                           ((uint32_t)(TC_BM >> 4) << 24);
+    const uint32_t a = smem_u32(base), b = smem_u32(base + A_TILE * 4);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+      for (int kk = 0; kk < TC_BK / 8; ++kk)
+        mma_tf32(tmem, sdesc(a + kk * 32), sdesc(b + kk * 32), idesc, (it > 0 || kk > 0) ? 1u : 0u);
+    }
+    mma_commit(smem_u32(&done_bar));
+    if (!mbar_wait(smem_u32(&done_bar), 0, &abort_s)) atomicOr(err, DS_WAIT_TIMEOUT);
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_BN) : "memory");
+  }
+}
+
+double tc_mma_probe_tflops(cudaStream_t st, int *dev_status) {
+  int dev = 0, nsm = 0;
+  RFDD_CUDA(cudaGetDevice(&dev));
+  RFDD_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int smem = (A_TILE + B_TILE) * 4 + 1024;
+  RFDD_CUDA(cudaFuncSetAttribute(tf32_mma_probe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  cudaEvent_t e0, e1;
+  RFDD_CUDA(cudaEventCreate(&e0));
+  RFDD_CUDA(cudaEventCreate(&e1));
+  const int iters = 4096;
+  double best = 0.0;
+  for (int rep = 0; rep < 4; ++rep) {  // the first launch is a warm-up
+    RFDD_CUDA(cudaEventRecord(e0, st));
+    tf32_mma_probe_kernel<<<nsm, 128, smem, st>>>(iters, dev_status);
+    RFDD_CHECK_LAUNCH();
+    RFDD_CUDA(cudaEventRecord(e1, st));
+    RFDD_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    RFDD_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    const double fl = 2.0 * TC_BM * TC_BN * 8.0 * (TC_BK / 8) * (double)iters * nsm;
+    if (rep > 0 && ms > 0.f) best = std::max(best, fl / (ms * 1e-3) / 1e12);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -538,6 +635,13 @@ static int tc_device_setup() {
   return std::max(1, d.nsm);
 }
 
+// Tile walk of one item: down the columns when B spans at least 8 tile columns and the item's
+// packed A (hi + lo) takes at most 48 MB of the 129 MB L2, else along the rows.
+int tc_tile_order(int mtc, int ntc, int nkt) {
+  const double a_bytes = (double)mtc * nkt * A_TILE * 8.0;
+  return (ntc >= 8 && mtc >= 2 && a_bytes <= 48e6) ? 1 : 0;
+}
+
 template <bool CPLX, typename T>
 static void tc_gemm_run(cudaStream_t st, const std::vector<GemmItem<T>> &items, double alpha, double beta,
                         const std::vector<TcPackedA> *pre = nullptr, int splits = 3) {
@@ -588,7 +692,7 @@ static void tc_gemm_run(cudaStream_t st, const std::vector<GemmItem<T>> &items, 
                   const_cast<float *>(Al), packed ? 0 : mtc, ntc, nkt};
       pbb.it[i] = {reinterpret_cast<const float *>(g.B), g.ldb, g.m, g.n, g.k, Bh, Bl, mtc, ntc, nkt};
       tb.it[i] = {Ah, Al, Bh, Bl, reinterpret_cast<float *>(g.C), (long long)F * g.ldc, g.m, F * g.n, nkt, mtc, ntc, tiles,
-                  packed ? (long long)(*pre)[s0 + i].mt_stride : 0ll};
+                  packed ? (long long)(*pre)[s0 + i].mt_stride : 0ll, tc_tile_order(mtc, ntc, nkt)};
       tiles += mtc * ntc;
     }
     tb.count = cnt;
@@ -751,7 +855,8 @@ int tc_gemm_complex_noalloc(cudaStream_t st, const cx<float> *A, int64_t lda, co
   memset(&tb, 0, sizeof(tb));
   pa.it[0] = {reinterpret_cast<const float *>(A), lda, m, n, k, Ah, Al, mtc, ntc, nkt};
   pbb.it[0] = {reinterpret_cast<const float *>(B), ldb, m, n, k, Bh, Bl, mtc, ntc, nkt};
-  tb.it[0] = {Ah, Al, Bh, Bl, reinterpret_cast<float *>(C), 2ll * ldc, m, 2 * n, nkt, mtc, ntc, 0};
+  tb.it[0] = {Ah, Al, Bh, Bl, reinterpret_cast<float *>(C), 2ll * ldc, m, 2 * n, nkt, mtc, ntc, 0, 0ll,
+              tc_tile_order(mtc, ntc, nkt)};
   tb.count = 1;
   tb.total_tiles = mtc * ntc;
   tb.err = na.status;

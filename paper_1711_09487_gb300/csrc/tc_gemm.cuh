@@ -52,6 +52,12 @@ void tc_pack_a_batched(cudaStream_t st, const std::vector<TcPackJob> &jobs);
 // the sub-matrix of a packed m x k_full operand starting at row r0 (a multiple of 128) and complex
 // column c0 (a multiple of 16)
 TcPackedA tc_packed_view(const float *hi, const float *lo, int64_t k_full, int64_t r0, int64_t c0);
+// TFLOP/s of kind::tf32 MMAs issued back to back from operand tiles resident in shared memory
+// (one CTA per SM, no operand loads): the tensor pipe's own TF32 rate.  Time-outs go to *dev_status.
+double tc_mma_probe_tflops(cudaStream_t st, int *dev_status);
+// tile walk of a GEMM item with mtc x ntc output tiles and nkt K tiles: 1 down the columns, 0
+// along the rows (see tc_gemm.cu)
+int tc_tile_order(int mtc, int ntc, int nkt);
 // allocation-free variant: packed operands in a static device array (m, n <= 1024, k <= 128);
 // waits for `st` and returns the launch's DS_* status bits (0 = ok)
 int tc_gemm_complex_noalloc(cudaStream_t st, const cx<float> *A, int64_t lda, const cx<float> *B, int64_t ldb,

@@ -34,7 +34,8 @@ import scipy.sparse as sp
 __all__ = [
     "Csr", "Pencil", "q1_1d", "q1_pencil", "q1_eigenvalues", "varkappa7_pencil",
     "separator_planes", "geometric_partition", "interval_from_sorted", "workload",
-    "WORKLOADS", "random_rhs", "snap_to_gaps",
+    "WORKLOADS", "random_rhs", "snap_to_gaps", "sym_inertia_count", "VARKAPPA_POOL", "serving_stream",
+    "serving_pencil",
 ]
 
 
@@ -171,6 +172,29 @@ def varkappa7_pencil(N: int, seed: int) -> tuple[Csr, Csr]:
     return Csr.from_scipy(A), Csr.from_scipy(M)
 
 
+def sym_inertia_count(A: Csr, M: Csr, beta: float) -> int:
+    """Number of eigenvalues of the pencil (A, M) below ``beta`` (M SPD), by Sylvester's law of
+    inertia: P (A - beta M) P^T = L D L^T with a fill-reducing symmetric permutation P and no
+    off-diagonal pivoting (SuperLU in symmetric mode, diagonal pivots only), so the count is the
+    number of negative entries of D = diag(U).  Used to place the intervals of generated
+    requests; it is not the solver's eigenvalue count (that one works through the domain
+    decomposition on the GPU)."""
+    import scipy.sparse.linalg as sla
+    K = (A.to_scipy() - beta * M.to_scipy()).tocsc()
+    lu = sla.splu(K, permc_spec="MMD_AT_PLUS_A", diag_pivot_thresh=0.0, options=dict(SymmetricMode=True))
+    if not np.array_equal(lu.perm_r, lu.perm_c):
+        raise RuntimeError("sym_inertia_count: the factorisation pivoted off the diagonal")
+    d = lu.U.diagonal()
+    if not np.all(np.isfinite(d)) or np.any(d == 0):
+        raise RuntimeError(f"sym_inertia_count: singular or unstable at beta={beta}")
+    return int(np.count_nonzero(d < 0))
+
+
+# the 3-D variable-coefficient pencils of the serving stream: (N, seed); the exact eigenvalue
+# counts on a grid of shifts are stored in varkappa_counts.json (make_varkappa_counts.py)
+VARKAPPA_POOL = [(24, 1), (24, 2), (32, 1), (32, 2), (40, 1), (40, 2), (48, 1), (48, 2)]
+
+
 # ----------------------------------------------------------------------------------------
 # Geometric vertex-separator partitions
 # ----------------------------------------------------------------------------------------
@@ -281,3 +305,66 @@ WORKLOADS = {
 def random_rhs(n: int, b: int, seed: int) -> np.ndarray:
     """Seeded dense test block (n x b, float64, row-major) for solve/filter parity cases."""
     return np.random.default_rng(seed).standard_normal((n, b))
+
+
+# ----------------------------------------------------------------------------------------
+# Serving stream: requests of mixed size and kind
+# ----------------------------------------------------------------------------------------
+
+def _varkappa_counts():
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "varkappa_counts.json")
+    with open(path) as f:
+        return {(e["N"], e["seed"]): (np.array(e["beta"]), np.array(e["count"])) for e in json.load(f)["pencils"]}
+
+
+def serving_stream(count: int = 256, seed: int = 7) -> list[dict]:
+    """Seeded request descriptions of the serving stream (arrival times are drawn by the caller).
+
+    Half the requests are 2-D Q1 Laplacian pencils on an N^2 grid, N ~ U{64..256}, with a window of
+    nev ~ U[20, 400] consecutive eigenvalues starting at index U{1..200}, widened to whole clusters
+    and bounded at gap midpoints (closed form).  The other half are 3-D variable-coefficient
+    7-point pencils drawn from ``VARKAPPA_POOL`` (N = 24..48), with a window between two shifts of
+    the stored count grid that holds 20..400 eigenvalues (exact counts by inertia).  Partitions:
+    2x2, 4x2 or 4x4 (2-D) and 2x2x1, 2x2x2 or 4x2x2 (3-D), i.e. p in {4, 8, 16}; 8 midpoint nodes.
+    """
+    rng = np.random.default_rng(seed)
+    counts = None
+    out = []
+    for i in range(count):
+        if rng.random() < 0.5:
+            N = int(rng.integers(64, 257))
+            splits = [(2, 2), (4, 2), (4, 4)][int(rng.integers(0, 3))]
+            ev = q1_eigenvalues(N, 2)
+            nev = int(rng.integers(20, 401))
+            first = int(rng.integers(1, 201))
+            first, last = snap_to_gaps(ev, first, first + nev - 1)
+            alpha, beta = interval_from_sorted(ev, first, last)
+            out.append(dict(index=i, kind="q1_2d", N=N, seed=0, splits=splits, alpha=alpha, beta=beta,
+                            nev=last - first + 1, n_nodes=8, n=N * N))
+        else:
+            if counts is None:
+                counts = _varkappa_counts()
+            N, pseed = VARKAPPA_POOL[int(rng.integers(0, len(VARKAPPA_POOL)))]
+            splits = [(2, 2, 1), (2, 2, 2), (4, 2, 2)][int(rng.integers(0, 3))]
+            betas, cnt = counts[(N, pseed)]
+            pairs = [(a, b) for a in range(len(cnt)) for b in range(a + 1, len(cnt))
+                     if 20 <= cnt[b] - cnt[a] <= 400]
+            a, b = pairs[int(rng.integers(0, len(pairs)))]
+            out.append(dict(index=i, kind="varkappa7_3d", N=N, seed=pseed, splits=splits,
+                            alpha=float(betas[a]), beta=float(betas[b]), nev=int(cnt[b] - cnt[a]), n_nodes=8,
+                            n=N ** 3))
+    return out
+
+
+def serving_pencil(req: dict) -> tuple[Csr, Csr, np.ndarray, int]:
+    """(A, M, part, p) of one request of ``serving_stream``."""
+    N, splits = req["N"], tuple(req["splits"])
+    if req["kind"] == "q1_2d":
+        A, M = q1_pencil(N, 2)
+        part, p = geometric_partition(N, 2, splits)
+    else:
+        A, M = varkappa7_pencil(N, req["seed"])
+        part, p = geometric_partition(N, 3, splits)
+    return A, M, part, p
