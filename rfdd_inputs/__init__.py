@@ -319,6 +319,16 @@ def _varkappa_counts():
         return {(e["N"], e["seed"]): (np.array(e["beta"]), np.array(e["count"])) for e in json.load(f)["pencils"]}
 
 
+MAX_BLOCK = 8192  # largest nominal subdomain interior (unknowns) a generated request may have
+
+
+def _pick_splits(rng, n: int, options: list) -> tuple:
+    """A partition drawn uniformly among the options whose nominal subdomain size n / p is at most
+    MAX_BLOCK (the dense blocks of a larger one would hold most of the device on their own)."""
+    ok = [sp_ for sp_ in options if n / math.prod(sp_) <= MAX_BLOCK]
+    return ok[int(rng.integers(0, len(ok)))]
+
+
 def serving_stream(count: int = 256, seed: int = 7) -> list[dict]:
     """Seeded request descriptions of the serving stream (arrival times are drawn by the caller).
 
@@ -327,7 +337,8 @@ def serving_stream(count: int = 256, seed: int = 7) -> list[dict]:
     and bounded at gap midpoints (closed form).  The other half are 3-D variable-coefficient
     7-point pencils drawn from ``VARKAPPA_POOL`` (N = 24..48), with a window between two shifts of
     the stored count grid that holds 20..400 eigenvalues (exact counts by inertia).  Partitions:
-    2x2, 4x2 or 4x4 (2-D) and 2x2x1, 2x2x2 or 4x2x2 (3-D), i.e. p in {4, 8, 16}; 8 midpoint nodes.
+    2x2, 4x2 or 4x4 (2-D) and 2x2x1, 2x2x2 or 4x2x2 (3-D), i.e. p in {4, 8, 16}, drawn among those
+    whose nominal subdomain holds at most MAX_BLOCK = 8192 unknowns; 8 midpoint nodes.
     """
     rng = np.random.default_rng(seed)
     counts = None
@@ -335,7 +346,7 @@ def serving_stream(count: int = 256, seed: int = 7) -> list[dict]:
     for i in range(count):
         if rng.random() < 0.5:
             N = int(rng.integers(64, 257))
-            splits = [(2, 2), (4, 2), (4, 4)][int(rng.integers(0, 3))]
+            splits = _pick_splits(rng, N ** 2, [(2, 2), (4, 2), (4, 4)])
             ev = q1_eigenvalues(N, 2)
             nev = int(rng.integers(20, 401))
             first = int(rng.integers(1, 201))
@@ -347,7 +358,7 @@ def serving_stream(count: int = 256, seed: int = 7) -> list[dict]:
             if counts is None:
                 counts = _varkappa_counts()
             N, pseed = VARKAPPA_POOL[int(rng.integers(0, len(VARKAPPA_POOL)))]
-            splits = [(2, 2, 1), (2, 2, 2), (4, 2, 2)][int(rng.integers(0, 3))]
+            splits = _pick_splits(rng, N ** 3, [(2, 2, 1), (2, 2, 2), (4, 2, 2)])
             betas, cnt = counts[(N, pseed)]
             pairs = [(a, b) for a in range(len(cnt)) for b in range(a + 1, len(cnt))
                      if 20 <= cnt[b] - cnt[a] <= 400]
