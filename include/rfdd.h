@@ -87,6 +87,12 @@ typedef struct {
   int m_align;          /* completion block m rounded up to a multiple of this (default 128, the
                            complex column width of one tensor-core tile: the extra guard vectors
                            ride in tile columns that would otherwise be padding); <= 1: none */
+  int pack_factors;     /* mixed solve: form of the complex factors kept for the solves.  1: the
+                           tensor-core tile copies only (TF32 hi/lo, 16 bytes per complex entry,
+                           packed once after the factorisation; the complex64 factors are freed
+                           then, so the peak holds both); 0: the complex64 factors only (8 bytes
+                           per entry; every solve product packs its factor block on the fly);
+                           -1 (default): 1 unless mem_budget is set and the peak of 1 exceeds it */
 } rfdd_options;
 
 typedef struct rfdd_handle rfdd_handle;
@@ -110,6 +116,7 @@ typedef struct {
   double t_complete_ms; /* a10 */
   double t_total_ms;
   int32_t status;       /* RFDD_OK or RFDD_NOT_CONVERGED */
+  int32_t packed;       /* 1 if the solves used tile copies of the factors (opt.pack_factors) */
   double sigma;         /* real shift the interior step used (Eq. prol2): opt.sigma or (alpha+beta)/2,
                            moved, at most three times, while it lies within tau max(1, |sigma|) of
                            an eigenvalue of some (B_j, M_B^(j)): FP64 tau = 1e-8, move
@@ -353,8 +360,9 @@ int rfdd_memory_estimate(const rfdd_handle *h, int32_t n_nodes, int64_t nev_gues
  * estimate (rfdd_memory_estimate with nev_hint, or 100 when 0) fits in what mem_budget has left;
  * the first waiting request that satisfies these starts, and the oldest waiting request is passed
  * over at most max_bypass times.  After each solve the handle's factors are released
- * (rfdd_release).  Results are those of rfdd_solve on the same pencil and interval; they do not
- * depend on what else runs. */
+ * (rfdd_release).  A request's own mem_budget is capped at the server's (so the form of its factors,
+ * rfdd_options.pack_factors, fits the server's budget).  Results are those of rfdd_solve on the same
+ * pencil and interval with those options; they do not depend on what else runs. */
 typedef struct rfdd_server rfdd_server;
 typedef struct {
   size_t mem_budget;     /* device bytes the running requests may hold by estimate (default 150 GiB) */

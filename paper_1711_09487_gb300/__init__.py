@@ -64,7 +64,8 @@ class rfdd_options(C.Structure):
                 ("psi", C.c_int), ("lanczos_tol", C.c_double), ("block", C.c_int), ("res_tol", C.c_double),
                 ("max_passes", C.c_int), ("ir_max", C.c_int), ("seed", C.c_uint64), ("mem_budget", C.c_size_t),
                 ("stream", C.c_void_p), ("guard_frac", C.c_double), ("min_guard", C.c_int),
-                ("keep_schur", C.c_int), ("subspace_iters", C.c_int), ("m_align", C.c_int)]
+                ("keep_schur", C.c_int), ("subspace_iters", C.c_int), ("m_align", C.c_int),
+                ("pack_factors", C.c_int)]
 
 
 class rfdd_info(C.Structure):
@@ -73,7 +74,7 @@ class rfdd_info(C.Structure):
                 ("pre_max_resid", C.c_double), ("pre_nev", C.c_int64), ("t_factor_ms", C.c_double),
                 ("t_lanczos_ms", C.c_double), ("t_interior_ms", C.c_double), ("t_rr_ms", C.c_double),
                 ("t_complete_ms", C.c_double), ("t_total_ms", C.c_double), ("status", C.c_int32),
-                ("sigma", C.c_double)]
+                ("packed", C.c_int32), ("sigma", C.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

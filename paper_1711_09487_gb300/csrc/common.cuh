@@ -161,7 +161,11 @@ struct SolveShape {
   const int64_t *D = nullptr;  // bordered sizes D_j = d_j + s_j
   int precision = RFDD_MIXED, keep_schur = 0, min_guard = 8, m_align = 128;
   double guard_frac = 0.3;
+  int pack_factors = -1;  // rfdd_options.pack_factors
+  size_t mem_budget = 0;
 };
+// whether the mixed solve keeps tile copies of its factors (rfdd_options.pack_factors)
+bool packed_factors(const SolveShape &g, int nc);
 size_t factor_bytes_of(const SolveShape &g, int nc);
 size_t solve_bytes_of(const SolveShape &g, int nc, int64_t nev_guess, bool with_setup);
 

@@ -109,8 +109,8 @@ __global__ void rank2_kernel(SymBatchP b, int i) {
 }
 
 // --------------------------------------------------------------------------------------
-// Eigenvalues of the tridiagonal matrix by bisection: thread per eigenvalue index.  The Sturm
-// count of x is the number of negative pivots of the LDL^T factorisation of T - x I.
+// Eigenvalues of the tridiagonal matrix by multisection on Sturm counts.  The Sturm count of x is
+// the number of negative pivots of the LDL^T factorisation of T - x I (Sylvester's law).
 // --------------------------------------------------------------------------------------
 __device__ inline int sturm_count(const double *d, const double *e, int n, double x, double pivmin) {
   int cnt = 0;
@@ -125,11 +125,43 @@ __device__ inline int sturm_count(const double *d, const double *e, int n, doubl
   return cnt;
 }
 
-__global__ void bisect_kernel(SymBatchP b) {
+// 1/q by the hardware's approximate reciprocal refined with one Newton-Raphson step
+// (r <- r + r (1 - q r)), which doubles the number of correct bits: relative error about 2^-44,
+// far below what a Sturm count needs (it is a tiny backward perturbation of e_k^2).  |q| >= pivmin
+// keeps q a normal number.
+__device__ inline double recip_nr(double q) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(q));
+  return fma(r, fma(-q, r, 1.0), r);
+}
+
+__device__ inline int sturm_count_nr(const double *__restrict__ d, const double *__restrict__ e, int n, double x,
+                                     double pivmin) {
+  int cnt = 0;
+  double q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  cnt += q < 0.0;
+  for (int k = 1; k < n; ++k) {
+    const double ek = e[k - 1];
+    q = fma(-ek * ek, recip_nr(q), d[k] - x);
+    if (fabs(q) < pivmin) q = -pivmin;
+    cnt += q < 0.0;
+  }
+  return cnt;
+}
+
+// BIS_G lanes per eigenvalue: each round the lanes take the Sturm counts at BIS_G points that cut
+// [lo, hi] into BIS_G + 1 equal parts, and the part holding eigenvalue i becomes the new interval
+// (log2(BIS_G + 1) bits per round instead of one, at BIS_G times the counting work).
+constexpr int BIS_G = 8;
+
+__global__ void __launch_bounds__(256) bisect_kernel(SymBatchP b) {
   const SymItem it = b.it[blockIdx.y];
   const int n = it.n;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  const int g = threadIdx.x % BIS_G;                                   // lane within the group
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) / BIS_G;       // eigenvalue index
+  const unsigned gmask = ((1u << BIS_G) - 1u) << ((threadIdx.x & 31) & ~(BIS_G - 1));
+  if (i >= n) return;  // the lanes of a group share i, so a group leaves together
   const double *d = it.d, *e = it.e;
   double gl = d[0], gu = d[0], emax2 = 0.0;
   for (int k = 0; k < n; ++k) {
@@ -142,14 +174,22 @@ __global__ void bisect_kernel(SymBatchP b) {
   const double pivmin = 2.2250738585072014e-308 * fmax(1.0, emax2);
   const double span = fmax(fabs(gl), fabs(gu));
   double lo = gl - 2.0 * eps * span * n - pivmin, hi = gu + 2.0 * eps * span * n + pivmin;
-  for (int iter = 0; iter < 200; ++iter) {
+  for (int round = 0; round < 100; ++round) {
     if (hi - lo <= 2.0 * eps * fmax(fabs(lo), fabs(hi)) + 4.0 * pivmin) break;
-    const double mid = 0.5 * (lo + hi);
-    if (mid <= lo || mid >= hi) break;
-    if (sturm_count(d, e, n, mid, pivmin) > i) hi = mid;
-    else lo = mid;
+    const double step = (hi - lo) / (BIS_G + 1);
+    const double x = lo + step * (g + 1);
+    const bool above = (x > lo && x < hi) ? sturm_count_nr(d, e, n, x, pivmin) > i : (x >= hi);
+    // the first cut point whose count exceeds i bounds the eigenvalue from above
+    const unsigned m = __ballot_sync(gmask, above) & gmask;
+    const int base = (threadIdx.x & 31) & ~(BIS_G - 1);
+    const int first = m ? (__ffs(m) - 1 - base) : BIS_G;
+    const double nlo = first > 0 ? lo + step * first : lo;
+    const double nhi = first < BIS_G ? lo + step * (first + 1) : hi;
+    if (!(nlo > lo || nhi < hi)) break;  // no progress in floating point
+    lo = nlo;
+    hi = nhi;
   }
-  it.lam[i] = 0.5 * (lo + hi);
+  if (g == 0) it.lam[i] = 0.5 * (lo + hi);
 }
 
 // Householder reduction of every item of the batch to tridiagonal form (d, e)
@@ -208,8 +248,8 @@ void sym_eig_values(cudaStream_t st, const std::vector<SymItem> &items, int *sta
     if (nmax == 0) continue;
     tridiagonalize(st, b, cnt, nmax);
     // e[n-1] = 0 for every item (house_kernel leaves it undefined)
-    // FP64-bound and one thread per eigenvalue: warp-sized blocks spread the work over the SMs
-    bisect_kernel<<<dim3(ceil_div(nmax, 32), cnt), 32, 0, st>>>(b);
+    // BIS_G lanes per eigenvalue, 256 / BIS_G eigenvalues per block
+    bisect_kernel<<<dim3(ceil_div((int64_t)nmax * BIS_G, 256), cnt), 256, 0, st>>>(b);
     RFDD_CHECK_LAUNCH();
   }
 }
@@ -238,7 +278,7 @@ __global__ void __launch_bounds__(256) inviter_kernel(InvIterP p, const Cluster 
   const int n = it.n;
   const double *d = it.d, *e = it.e;
   double *u1 = scratch + (int64_t)blockIdx.x * scratch_per_cta;
-  double *u2 = u1 + n, *u3 = u2 + n, *ml = u3 + n, *pv = ml + n, *x = pv + n;
+  double *u2 = u1 + n, *u3 = u2 + n, *ml = u3 + n, *pv = ml + n, *x = pv + n, *ru = x + n;
   __shared__ double red[32];
   __shared__ double tnorm_s;
   if (threadIdx.x == 0) {
@@ -292,8 +332,12 @@ __global__ void __launch_bounds__(256) inviter_kernel(InvIterP p, const Cluster 
         }
       }
       u1[n - 1] = (fabs(cd) < delta) ? (cd < 0 ? -delta : delta) : cd;
-      for (int k = 0; k < n - 1; ++k)
-        if (fabs(u1[k]) < delta) u1[k] = u1[k] < 0 ? -delta : delta;
+    }
+    __syncthreads();
+    // reciprocals of the pivots, once, by all threads: the solves below then multiply
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      const double u = (k < n - 1 && fabs(u1[k]) < delta) ? (u1[k] < 0 ? -delta : delta) : u1[k];
+      ru[k] = 1.0 / u;
     }
     __syncthreads();
     for (int iter = 0; iter < 3; ++iter) {
@@ -306,9 +350,9 @@ __global__ void __launch_bounds__(256) inviter_kernel(InvIterP p, const Cluster 
           }
           x[k + 1] -= ml[k] * x[k];
         }
-        x[n - 1] /= u1[n - 1];
-        if (n > 1) x[n - 2] = (x[n - 2] - u2[n - 2] * x[n - 1]) / u1[n - 2];
-        for (int k = n - 3; k >= 0; --k) x[k] = (x[k] - u2[k] * x[k + 1] - u3[k] * x[k + 2]) / u1[k];
+        x[n - 1] *= ru[n - 1];
+        if (n > 1) x[n - 2] = (x[n - 2] - u2[n - 2] * x[n - 1]) * ru[n - 2];
+        for (int k = n - 3; k >= 0; --k) x[k] = (x[k] - u2[k] * x[k + 1] - u3[k] * x[k + 2]) * ru[k];
       }
       __syncthreads();
       // scale to unit max-norm first so that the dot products below cannot overflow
@@ -427,7 +471,7 @@ void sym_eig_vectors(cudaStream_t st, const std::vector<BackItem> &items, double
     int *sel_dev = nullptr;
     Cluster *cl_dev = nullptr;
     double *scratch = nullptr;
-    const int64_t per = (int64_t)6 * nmax;
+    const int64_t per = (int64_t)7 * nmax;
     RFDD_CUDA(cudaMallocAsync((void **)&sel_dev, allsel.size() * sizeof(int), st));
     RFDD_CUDA(cudaMallocAsync((void **)&cl_dev, clusters.size() * sizeof(Cluster), st));
     RFDD_CUDA(cudaMallocAsync((void **)&scratch, (size_t)clusters.size() * per * sizeof(double), st));

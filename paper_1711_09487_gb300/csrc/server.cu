@@ -240,6 +240,8 @@ int rfdd_server_add_pencil(rfdd_server *s, const rfdd_csr *A, const rfdd_csr *M,
   if (opt) o = *opt;
   else rfdd_default_options(&o);
   o.stream = nullptr;  // every resident pencil solves on a stream of its own handle
+  // a request may hold at most the server's budget: its factor form follows from that (pack_factors)
+  if (o.mem_budget == 0 || o.mem_budget > s->opt.mem_budget) o.mem_budget = s->opt.mem_budget;
   if (cudaSetDevice(s->device) != cudaSuccess) {
     cudaGetLastError();
     return RFDD_ECUDA;
@@ -288,6 +290,7 @@ int rfdd_server_submit_pencil(rfdd_server *s, const rfdd_csr *A, const rfdd_csr 
   if (opt) o = *opt;
   else rfdd_default_options(&o);
   o.stream = nullptr;
+  if (o.mem_budget == 0 || o.mem_budget > s->opt.mem_budget) o.mem_budget = s->opt.mem_budget;
   std::vector<int64_t> d, D;
   int64_t sz = 0, nnz = 0;
   int rc = shape_from_csr(*A, *M, part, p, d, D, sz, nnz);
@@ -304,6 +307,8 @@ int rfdd_server_submit_pencil(rfdd_server *s, const rfdd_csr *A, const rfdd_csr 
   g.guard_frac = o.guard_frac;
   g.min_guard = o.min_guard;
   g.m_align = o.m_align;
+  g.pack_factors = o.pack_factors;
+  g.mem_budget = o.mem_budget;
   const size_t bytes = rfdd::solve_bytes_of(g, n_nodes, nev_hint > 0 ? nev_hint : 100, true);
   if (bytes > s->opt.mem_budget) return RFDD_EADMIT;  // could never start
   SPencil pc;

@@ -707,9 +707,10 @@ constexpr int NBO = 256;     // outer block of the triangular solves
 
 }  // namespace
 
-// Device bytes of the factors of one solve (a2-a5 storage, inverted diagonal blocks, packed
-// tensor-core copies in the mixed solve, pivots).
-size_t rfdd::factor_bytes_of(const SolveShape &g, int nc) {
+// Device bytes of the factors of one solve at their peak (a2-a5 storage, inverted diagonal
+// blocks, pivots; with tile copies, the copies too: the complex64 factors are freed only after
+// they have been packed).
+static size_t factor_bytes_impl(const SolveShape &g, int nc, bool packed) {
   const bool mixed = g.precision == RFDD_MIXED;
   const size_t scal = mixed ? sizeof(cx<float>) : sizeof(cx<double>);
   size_t e = 0;
@@ -719,7 +720,7 @@ size_t rfdd::factor_bytes_of(const SolveShape &g, int nc) {
   size_t inv = (size_t)block_inverse_elems(g.s, 256);  // inverted diagonal blocks of L and U
   for (int j = 0; j < g.p; ++j) inv += (size_t)block_inverse_elems(g.d[j], 256);
   b += 2 * (size_t)nc * inv * scal;
-  if (mixed) {  // packed tensor-core copies of the solve operands (hi + lo)
+  if (mixed && packed) {  // packed tensor-core copies of the solve operands (hi + lo)
     size_t pk = (size_t)g.s * g.s + 2 * (size_t)block_inverse_elems(g.s, 256);
     for (int j = 0; j < g.p; ++j)
       pk += (size_t)g.D[j] * g.D[j] - (size_t)(g.D[j] - g.d[j]) * (g.D[j] - g.d[j]) +
@@ -731,6 +732,14 @@ size_t rfdd::factor_bytes_of(const SolveShape &g, int nc) {
   b += (size_t)nc * (dsum + g.s) * sizeof(int);
   return b;
 }
+
+bool rfdd::packed_factors(const SolveShape &g, int nc) {
+  if (g.precision != RFDD_MIXED || g.pack_factors == 0) return false;
+  if (g.pack_factors == 1 || g.mem_budget == 0) return true;
+  return factor_bytes_impl(g, nc, true) <= g.mem_budget;
+}
+
+size_t rfdd::factor_bytes_of(const SolveShape &g, int nc) { return factor_bytes_impl(g, nc, packed_factors(g, nc)); }
 
 // Device bytes a solve holds at its peak: the factors, the completion blocks for about nev_guess
 // pairs, the Lanczos basis; plus, when with_setup, the resident set-up (union CSR with both
@@ -761,6 +770,8 @@ rfdd::SolveShape shape_of(const rfdd_handle *h) {
   g.guard_frac = h->opt.guard_frac;
   g.min_guard = h->opt.min_guard;
   g.m_align = h->opt.m_align;
+  g.pack_factors = h->opt.pack_factors;
+  g.mem_budget = h->opt.mem_budget;
   return g;
 }
 
@@ -878,7 +889,15 @@ void factor_impl(rfdd_handle *h) {
     }
     lu_block_inverses<Tf>(st, fi, NBO, li, ui);
   }
-  if constexpr (std::is_same<Tf, cx<float>>::value) pack_factor_operands(h);
+  if constexpr (std::is_same<Tf, cx<float>>::value) {
+    if (rfdd::packed_factors(shape_of(h), h->nnodes)) {
+      // the solves read only the tile copies (and the inverted diagonal blocks): one copy of each
+      // factor stays
+      pack_factor_operands(h);
+      h->fac.release();  // stream-ordered: after the packing kernels
+      h->Sfac.release();
+    }
+  }
   sync_status(h, "factor");
   h->have_factors = true;
 }
@@ -2262,6 +2281,7 @@ void run_solve(rfdd_handle *h, double alpha, double beta, int nc, rfdd_result *r
     Timer t(h->st);
     factor(h);
     res->info.t_factor_ms = t.ms();
+    res->info.packed = h->pkB.empty() ? 0 : 1;
   }
   {
     Timer t(h->st);
@@ -2359,6 +2379,7 @@ void rfdd_default_options(rfdd_options *o) {
   o->guard_frac = 0.3;
   o->min_guard = 8;
   o->m_align = 128;
+  o->pack_factors = -1;
   o->keep_schur = 0;
   o->subspace_iters = 4;
 }

@@ -261,6 +261,21 @@ def test_end_to_end(R, name, prec):
         np.testing.assert_allclose(ev, ro["evals"], rtol=TOL[prec]["ev"])
 
 
+@pytest.mark.parametrize("name", ["q1_2d_24", "q1_3d_12"])
+def test_factor_forms_give_the_same_pairs(R, name):
+    """Mixed solve with the complex64 factors only (every solve product packs its factor block on
+    the fly) and with their tile copies only (packed once, complex64 freed): the same pairs."""
+    w = I.workload(name)
+    out = {}
+    for pk in (0, 1):
+        ev, X, rs, info = R.solve(w.A, w.M, w.part, w.p, w.alpha, w.beta, w.n_nodes, precision=1,
+                                  quad_rule=RULES[w.rule], pack_factors=pk)
+        assert info["packed"] == pk
+        check_result(R, w, ev, X, rs, info, 1)
+        out[pk] = ev
+    np.testing.assert_allclose(out[0], out[1], rtol=1e-10)
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_edge_cases_one_node_block_one(R, prec):
     """Nc = 1, Lanczos block 1 (the printed Algorithm 2), psi = 1."""
