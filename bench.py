@@ -460,13 +460,14 @@ def run_gemm(args):
     A = (g.standard_normal((m, k)) + 1j * g.standard_normal((m, k))).astype(np.complex64)
     B = (g.standard_normal((k, n)) + 1j * g.standard_normal((k, n))).astype(np.complex64)
     C = np.zeros((m, n), dtype=np.complex64)
-    R.rfdd_cgemm(A, B, C, -1.0, 1.0, 1)  # warm-up
+    R.rfdd_cgemm(A, B, C, -1.0, 1.0, args.engine)  # warm-up
     R.rfdd_profile(True)
-    R.rfdd_cgemm(A, B, C, -1.0, 1.0, 1)
+    R.rfdd_cgemm(A, B, C, -1.0, 1.0, args.engine)
     launches, ms, flops = R.rfdd_profile_get(1)
     model_bytes = R.rfdd_profile_bytes(1)
     R.rfdd_profile(False)
-    print(json.dumps({"mode": "gemm", "m": m, "n": n, "k": k, "kernel_ms": ms, "model_bytes": model_bytes,
+    print(json.dumps({"mode": "gemm", "m": m, "n": n, "k": k, "engine": args.engine, "kernel_ms": ms,
+                      "model_bytes": model_bytes,
                       "tflops_4m": flops / (ms / 1e3) / 1e12 if ms > 0 else None}), flush=True)
 
 
@@ -575,6 +576,8 @@ def main():
     ap.add_argument("--inflight", type=int, default=4, help="serve mode: requests running at once")
     ap.add_argument("--capacity-sample", type=int, default=8, help="serve mode: requests timed one at a time")
     ap.add_argument("--gemm", type=int, nargs=3, default=[8192, 8192, 128], metavar=("M", "N", "K"))
+    ap.add_argument("--engine", type=int, default=1, choices=[1, 2, 3],
+                    help="gemm mode: 1 automatic kernel choice, 2 one-CTA kernel, 3 two-CTA kernel")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)

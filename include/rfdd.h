@@ -11,8 +11,10 @@
  *    owns is modified, except output buffers of the failing call may hold partial data; the
  *    message of the last error on the calling thread is available from rfdd_last_error().
  *  - Sparse inputs are full (both triangles) CSR with int64 row pointers, int32 column indices
- *    (in any order within a row, no duplicates) and float64 values, in HOST memory.  They are
- *    copied at setup; the caller keeps ownership.
+ *    (in any order within a row, no duplicates) and float64 values, in host memory or, with
+ *    rfdd_csr.location = 1, in device memory.  They are copied at setup; the caller keeps
+ *    ownership.  (A device-resident CSR is copied to the host for the validation and the
+ *    interior-first ordering, which run on the host, then uploaded in that order.)
  *  - Dense host arrays are row-major.  Complex values are interleaved (re, im) float64 pairs.
  *  - "Interior-first ordering" (Eq. dd1): the interior unknowns of subdomain 0, 1, ..., p-1
  *    (each in increasing original index), then the interface unknowns (label -1) in increasing
@@ -61,6 +63,8 @@ typedef struct {
   const int64_t *rowptr; /* n+1 */
   const int32_t *col;    /* rowptr[n] */
   const double *val;     /* rowptr[n] */
+  int32_t location;      /* where rowptr, col and val live: 0 host memory (the default of a
+                            zero-initialised struct), 1 device memory of the current device */
 } rfdd_csr;
 
 typedef struct {
@@ -142,7 +146,9 @@ int rfdd_quadrature(double alpha, double beta, int32_t n_nodes, int32_t rule, do
 
 /* ---- a1: setup (Alg. 3 step 1; Section 2.3, Eq. dd1) -----------------------------------
  * Validates (A, M, part), computes the interior-first ordering, splits the pencil into the
- * blocks B_j, M_B^(j), E_j, M_E^(j), C, M_C and uploads them.  part: host int32[n], label -1
+ * blocks B_j, M_B^(j), E_j, M_E^(j), C, M_C and uploads them.  A and M may each be host- or
+ * device-resident (rfdd_csr.location; RFDD_EINVAL for another value, RFDD_ECUDA if a device
+ * copy fails).  part: host int32[n], label -1
  * for interface unknowns and 0..p-1 for subdomain interiors; the labels must form a vertex
  * separator (no A or M entry couples two different subdomains) and every subdomain and the
  * interface must be non-empty.  opt may be NULL (defaults).  On success *out owns device
@@ -273,9 +279,12 @@ int rfdd_sym_eig(int64_t n, const double *H, double *evals, double *evecs);
 /* Building block of a3-a5 (trailing updates of the factorisations), a6 and a10 (triangular-solve
  * updates): C = beta*C + alpha*A*B for complex single-precision A (m x k, leading dimension lda),
  * B (k x n, ldb), C (m x n, ldc), host arrays, row-major, interleaved (re, im) floats.
- * engine 1 = the tensor-core kernel (tcgen05, 3xTF32 split) that every complex-FP32 contraction
- * of the solver runs on; engine 0 = a CUDA-core kernel kept as a second engine for tests (the
- * solver never dispatches to it). */
+ * engine 1 = the tensor-core GEMM (tcgen05, 3xTF32 split) that every complex-FP32 contraction of
+ * the solver runs on, with its automatic choice between a one-CTA kernel (128 x 256 tiles of the
+ * realified product) and a two-CTA kernel (cta_group::2, 256 x 256 tiles on a pair of SMs);
+ * engines 2 and 3 force the one-CTA and the two-CTA kernel; engine 0 = a CUDA-core kernel kept
+ * as another engine for tests (the solver never dispatches to it).  RFDD_EINVAL for other
+ * engines. */
 int rfdd_cgemm(int64_t m, int64_t n, int64_t k, const float *A, int64_t lda, const float *B, int64_t ldb,
                float *C, int64_t ldc, double alpha, double beta, int32_t engine);
 
@@ -400,7 +409,8 @@ int rfdd_server_add_pencil(rfdd_server *s, const rfdd_csr *A, const rfdd_csr *M,
  * could never start), RFDD_EINVAL for an unknown pencil, alpha >= beta or n_nodes < 1. */
 int rfdd_server_submit(rfdd_server *s, int64_t pencil_id, double alpha, double beta, int32_t n_nodes,
                        int64_t nev_hint, int64_t *request_id);
-/* Queue a request that brings its own pencil (host CSR copied by this call; no device work here):
+/* Queue a request that brings its own pencil (host CSR, location 0, copied by this call; no device
+ * work here):
  * the worker that runs it sets the pencil up, solves and frees it, so its latency includes the
  * set-up.  It is admitted by the estimate of rfdd_memory_estimate plus the set-up, from the block
  * sizes that a host scan of the pattern and labels gives.  Returns at once; RFDD_EADMIT and

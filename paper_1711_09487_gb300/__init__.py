@@ -56,7 +56,7 @@ class RfddError(RuntimeError):
 
 class rfdd_csr(C.Structure):
     _fields_ = [("n", C.c_int64), ("rowptr", C.POINTER(C.c_int64)), ("col", C.POINTER(C.c_int32)),
-                ("val", C.POINTER(C.c_double))]
+                ("val", C.POINTER(C.c_double)), ("location", C.c_int32)]
 
 
 class rfdd_options(C.Structure):
@@ -204,14 +204,24 @@ def rfdd_quadrature(alpha: float, beta: float, n_nodes: int, rule: int = RFDD_MI
 
 
 class _Csr:
-    """Keeps the numpy arrays behind an rfdd_csr alive."""
+    """Keeps the arrays behind an rfdd_csr alive: numpy arrays (host), or CUDA torch tensors
+    (int64 rowptr, int32 col, float64 val; the struct then says location = 1)."""
 
     def __init__(self, csr):
+        if all(hasattr(getattr(csr, f), "data_ptr") and getattr(csr, f).is_cuda for f in ("rowptr", "col", "val")):
+            import torch
+            self.rowptr = csr.rowptr.contiguous().to(torch.int64)
+            self.col = csr.col.contiguous().to(torch.int32)
+            self.val = csr.val.contiguous().to(torch.float64)
+            vp = lambda t, ty: C.cast(C.c_void_p(t.data_ptr()), C.POINTER(ty))
+            self.s = rfdd_csr(int(self.rowptr.numel() - 1), vp(self.rowptr, C.c_int64), vp(self.col, C.c_int32),
+                              vp(self.val, C.c_double), 1)
+            return
         self.rowptr = np.ascontiguousarray(csr.rowptr, dtype=np.int64)
         self.col = np.ascontiguousarray(csr.col, dtype=np.int32)
         self.val = np.ascontiguousarray(csr.val, dtype=np.float64)
         self.s = rfdd_csr(int(len(self.rowptr) - 1), self.rowptr.ctypes.data_as(C.POINTER(C.c_int64)),
-                          self.col.ctypes.data_as(C.POINTER(C.c_int32)), _dp(self.val))
+                          self.col.ctypes.data_as(C.POINTER(C.c_int32)), _dp(self.val), 0)
 
 
 def _as_csr(x):

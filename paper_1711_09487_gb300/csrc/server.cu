@@ -33,7 +33,7 @@ struct HostCsr {
     col.assign(a.col, a.col + rowptr.back());
     val.assign(a.val, a.val + rowptr.back());
   }
-  rfdd_csr view() const { return rfdd_csr{(int64_t)rowptr.size() - 1, rowptr.data(), col.data(), val.data()}; }
+  rfdd_csr view() const { return rfdd_csr{(int64_t)rowptr.size() - 1, rowptr.data(), col.data(), val.data(), 0}; }
 };
 
 struct SPencil {
@@ -286,6 +286,7 @@ int rfdd_server_submit_pencil(rfdd_server *s, const rfdd_csr *A, const rfdd_csr 
                               const rfdd_options *opt, double alpha, double beta, int32_t n_nodes, int64_t nev_hint,
                               int64_t *request_id) {
   if (!s || !A || !M || !request_id || !(beta > alpha) || n_nodes < 1 || nev_hint < 0) return RFDD_EINVAL;
+  if (A->location != 0 || M->location != 0) return RFDD_EINVAL;  // requests bring host copies
   rfdd_options o;
   if (opt) o = *opt;
   else rfdd_default_options(&o);

@@ -403,6 +403,32 @@ void validate_csr(const rfdd_csr *A, const char *name) {
   }
 }
 
+// A CSR given in device memory (rfdd_csr.location = 1) copied to host vectors; a host CSR is
+// returned as it is.
+struct HostCsrCopy {
+  std::vector<int64_t> rowptr;
+  std::vector<int32_t> col;
+  std::vector<double> val;
+  rfdd_csr view{};
+};
+const rfdd_csr *on_host(const rfdd_csr *X, HostCsrCopy &c, const char *name) {
+  if (!X || X->location == 0) return X;
+  RFDD_REQUIRE(X->location == 1, RFDD_EINVAL, std::string(name) + ": location must be 0 (host) or 1 (device)");
+  RFDD_REQUIRE(X->rowptr && X->col && X->val && X->n > 0, RFDD_EINVAL, std::string(name) + ": NULL or empty");
+  c.rowptr.resize(X->n + 1);
+  RFDD_CUDA(cudaMemcpy(c.rowptr.data(), X->rowptr, (X->n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+  const int64_t nnz = c.rowptr[X->n];
+  RFDD_REQUIRE(c.rowptr[0] == 0 && nnz >= 0, RFDD_EINVAL, std::string(name) + ": bad row pointers");
+  c.col.resize(nnz);
+  c.val.resize(nnz);
+  if (nnz > 0) {
+    RFDD_CUDA(cudaMemcpy(c.col.data(), X->col, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    RFDD_CUDA(cudaMemcpy(c.val.data(), X->val, nnz * sizeof(double), cudaMemcpyDeviceToHost));
+  }
+  c.view = rfdd_csr{X->n, c.rowptr.data(), c.col.data(), c.val.data(), 0};
+  return &c.view;
+}
+
 // symmetric in pattern and value: compare with the transpose built by counting sort
 // Host work over rows split into contiguous chunks, one thread per chunk (results do not depend
 // on the number of threads).
@@ -2423,7 +2449,10 @@ int rfdd_setup(const rfdd_csr *A, const rfdd_csr *M, const int32_t *part, int32_
   *out = nullptr;
   rfdd_handle *h = new (std::nothrow) rfdd_handle();
   if (!h) return RFDD_ENOMEM;
+  HostCsrCopy hostA, hostM;
   int rc = guarded([&] {
+    A = on_host(A, hostA, "A");
+    M = on_host(M, hostM, "M");
     if (opt) h->opt = *opt;
     else rfdd_default_options(&h->opt);
     RFDD_REQUIRE(h->opt.precision == RFDD_FP64 || h->opt.precision == RFDD_MIXED, RFDD_EINVAL, "bad precision");
@@ -2839,6 +2868,7 @@ int rfdd_sym_eig(int64_t n, const double *H, double *evals, double *evecs) {
 int rfdd_cgemm(int64_t m, int64_t n, int64_t k, const float *A, int64_t lda, const float *B, int64_t ldb, float *C,
                int64_t ldc, double alpha, double beta, int32_t engine) {
   if (m < 1 || n < 1 || k < 1 || !A || !B || !C || lda < k || ldb < n || ldc < n) return RFDD_EINVAL;
+  if (engine < 0 || engine > 3) return RFDD_EINVAL;
   return guarded([&] {
     cudaStream_t st = 0;
     Buf a, b, c;
@@ -2853,8 +2883,9 @@ int rfdd_cgemm(int64_t m, int64_t n, int64_t k, const float *A, int64_t lda, con
     Buf status;
     status.alloc(sizeof(int));
     RFDD_CUDA(cudaMemset(status.p, 0, sizeof(int)));
-    if (engine == 1) {
+    if (engine >= 1 && engine <= 3) {
       TcStatusScope tcs(status.as<int>());
+      TcEngineScope eng(engine == 2 ? 1 : engine == 3 ? 2 : 0);
       tc_gemm_complex(st, it, alpha, beta);
     } else {
       gemm_simt_batched<cx<float>>(st, it, false, false, alpha, beta);

@@ -158,6 +158,37 @@ __device__ __forceinline__ int find_item(const TcBatchP &b, int tile) {
   return lo;
 }
 
+// Epilogue of one output tile by one warp: TMEM lanes 32q..32q+31 (rows mt*128 + 32q ..), column
+// chunks of 32 accumulator columns [half*4, half*4 + 4), staged through shared memory so that C
+// is read and written along its rows; C = alpha * acc + beta * C, rows and columns masked.
+__device__ __forceinline__ void drain_tile(const TcItem &it, uint32_t tacc, int mt, int nt, int q, int half, int lane,
+                                           float *stg, float alpha, float beta) {
+  const int row0 = mt * TC_BM + q * 32;
+  const int nrows = min(32, it.m - row0);
+  float *__restrict__ Cb = it.C;
+#pragma unroll 1
+  for (int c = half * (TC_BN / 64); c < (half + 1) * (TC_BN / 64); ++c) {
+    uint32_t v[32];
+    TC_LD32(tacc + ((uint32_t)(q * 32) << 16) + (uint32_t)(c * 32), v);
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 32; ++j) stg[lane * EPI_PITCH + j] = __uint_as_float(v[j]);
+    __syncwarp();
+    const int col = nt * TC_BN + c * 32 + lane;
+    if (col < it.n2 && nrows > 0) {
+      // all loads of C first (independent, in flight together), then the stores
+      float cv[32];
+#pragma unroll
+      for (int r = 0; r < 32; ++r)
+        cv[r] = (beta != 0.f && r < nrows) ? Cb[(long long)(row0 + r) * it.ldc + col] : 0.f;
+#pragma unroll
+      for (int r = 0; r < 32; ++r)
+        if (r < nrows) Cb[(long long)(row0 + r) * it.ldc + col] = fmaf(alpha, stg[r * EPI_PITCH + lane], beta * cv[r]);
+    }
+    __syncwarp();
+  }
+}
+
 // Persistent, warp-specialised: warp 0 streams operand tiles, warp 1 issues the MMAs into one of
 // two TMEM accumulators (256 columns each), warps 2..5 drain the other accumulator to C.
 __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_constant__ TcBatchP b, float alpha,
@@ -295,30 +326,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
         break;
       }
       fence_after();
-      const int row0 = mt * TC_BM + q * 32;
-      const int nrows = min(32, it.m - row0);
-      float *__restrict__ Cb = it.C;
-#pragma unroll 1
-      for (int c = half * (TC_BN / 64); c < (half + 1) * (TC_BN / 64); ++c) {
-        uint32_t v[32];
-        TC_LD32(tmem + (uint32_t)(acc * TC_BN) + ((uint32_t)(q * 32) << 16) + (uint32_t)(c * 32), v);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int j = 0; j < 32; ++j) stg[lane * EPI_PITCH + j] = __uint_as_float(v[j]);
-        __syncwarp();
-        const int col = nt * TC_BN + c * 32 + lane;
-        if (col < it.n2 && nrows > 0) {
-          // all loads of C first (independent, in flight together), then the stores
-          float cv[32];
-#pragma unroll
-          for (int r = 0; r < 32; ++r)
-            cv[r] = (beta != 0.f && r < nrows) ? Cb[(long long)(row0 + r) * it.ldc + col] : 0.f;
-#pragma unroll
-          for (int r = 0; r < 32; ++r)
-            if (r < nrows) Cb[(long long)(row0 + r) * it.ldc + col] = fmaf(alpha, stg[r * EPI_PITCH + lane], beta * cv[r]);
-        }
-        __syncwarp();
-      }
+      drain_tile(it, tmem + (uint32_t)(acc * TC_BN), mt, nt, q, half, lane, stg, alpha, beta);
       fence_before();
       mbar_arrive(smem_u32(&tempty_bar[acc]));
     }
@@ -328,6 +336,257 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm_kernel(const __grid_con
   fence_after();
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_BN) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Two-CTA variant (cta_group::2): a cluster of two CTAs on two SMs computes a 256 x 256 tile of
+// Cr with one MMA stream.  Each CTA holds its own 128 rows of A and its half (128 packed rows) of
+// the B tile in shared memory; the MMAs, issued by the leader CTA (rank 0), read A and B from both
+// CTAs and leave rows 0..127 of the accumulator in the leader's TMEM and rows 128..255 in the
+// peer's.  Per 32-deep K tile an SM so takes in 64 KB instead of the 96 KB of the one-CTA kernel
+// (whose 128 x 256 tile needs all of B), which is what limits that kernel (operand feed, not the
+// tensor pipe).
+//
+// Synchronisation (all waits bounded; DS_WAIT_TIMEOUT into *err on time-out):
+//  - each CTA's producer loads its halves into its own stage and completes its own full_bar;
+//  - the peer's warp 1 forwards: it waits on its own full_bar and arrives on the leader's pfull_bar;
+//  - the leader waits on full_bar and pfull_bar, issues the MMAs, and commits to empty_bar of both
+//    CTAs (stage reusable) and, per tile, to tfull_bar of both CTAs (accumulator ready);
+//  - every epilogue warp of both CTAs drains its TMEM lanes and arrives on the leader's tempty_bar.
+// ---------------------------------------------------------------------------------------
+constexpr int T2_STAGES = 3;
+constexpr int T2_BHALF = (TC_BN / 2) * TC_BK;                       // floats of one CTA's B half
+constexpr int T2_STAGE_BYTES = (2 * A_TILE + 2 * T2_BHALF) * 4;     // 64 KB
+constexpr int T2_SMEM = T2_STAGES * T2_STAGE_BYTES + EPI_BYTES + 1024;
+
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t map_to_rank(uint32_t saddr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+// bounded wait with cluster-scope acquire (the barrier may be completed from the peer CTA)
+__device__ __forceinline__ bool mbar_wait_cl(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+  for (long long i = 0; i < WAIT_LIMIT; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((i & 1023) == 1023 && *abort_flag) return false;
+  }
+  return false;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void mma2_tf32(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(da), "l"(db), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma2_commit_both(uint32_t bar) {
+  const uint16_t mask = 0x3;
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+      "h"(mask)
+      : "memory");
+}
+
+// pair tile `local` of an item -> (pair row mp, tile column nt); two CTAs take rows 2 mp, 2 mp + 1
+__device__ __forceinline__ void pair_pos(const TcItem &it, int local, int &mp, int &nt) {
+  const int mpc = (it.mtc + 1) >> 1;
+  if (it.colmajor) {
+    mp = local % mpc;
+    nt = local / mpc;
+  } else {
+    mp = local / it.ntc;
+    nt = local % it.ntc;
+  }
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) tc_gemm2_kernel(const __grid_constant__ TcBatchP b, float alpha,
+                                                                 float beta) {
+  int *err = b.err;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *base = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  float *epi = reinterpret_cast<float *>(base + T2_STAGES * T2_STAGE_BYTES);
+  __shared__ __align__(8) uint64_t full_bar[T2_STAGES], pfull_bar[T2_STAGES], empty_bar[T2_STAGES], tfull_bar[2],
+      tempty_bar[2];
+  __shared__ uint32_t tmem_s;
+  __shared__ volatile int abort_s;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_ctarank();
+  const int cl = (int)(blockIdx.x >> 1), ncl = (int)(gridDim.x >> 1);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < T2_STAGES; ++s) {
+      mbar_init(smem_u32(&full_bar[s]), 1);
+      mbar_init(smem_u32(&pfull_bar[s]), 1);
+      mbar_init(smem_u32(&empty_bar[s]), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(smem_u32(&tfull_bar[a]), 1);
+      mbar_init(smem_u32(&tempty_bar[a]), 2 * EPI_WARPS);  // one arrival per epilogue warp of each CTA
+    }
+    abort_s = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {  // both CTAs of the pair allocate together
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_s)),
+                 "r"(2 * TC_BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  cluster_sync_all();  // both CTAs' barriers initialised and TMEM allocated before any remote use
+  fence_after();
+  const uint32_t tmem = tmem_s;
+  auto stage_addr = [&](int s, int which) -> uint32_t {  // which: 0 Ahi, 1 Alo, 2 Bhi half, 3 Blo half
+    const uint32_t off = (uint32_t)s * T2_STAGE_BYTES +
+                         (which == 0 ? 0u : which == 1 ? A_TILE * 4u : which == 2 ? 2u * A_TILE * 4u
+                                                                                  : 2u * A_TILE * 4u + T2_BHALF * 4u);
+    return smem_u32(base + off);
+  };
+  if (warp == 0) {
+    if (lane == 0) {  // producer (both CTAs): this CTA's A rows and B half
+      long long g = 0;
+      for (int pt = cl; pt < b.total_tiles && !abort_s; pt += ncl) {
+        const TcItem &it = b.it[find_item(b, pt)];
+        int mp, nt;
+        pair_pos(it, pt - it.tile0, mp, nt);
+        const int mt = min(2 * mp + (int)rank, it.mtc - 1);  // a missing second row re-reads the last one
+        const long long ams = it.amts ? it.amts : it.nkt;
+        const float *Ahi = it.Ahi + (long long)mt * ams * A_TILE, *Alo = it.Alo + (long long)mt * ams * A_TILE;
+        const long long boff = (long long)nt * it.nkt * B_TILE + (long long)rank * T2_BHALF;
+        const float *Bhi = it.Bhi + boff, *Blo = it.Blo + boff;
+        for (int kt = 0; kt < it.nkt; ++kt, ++g) {
+          const int s = (int)(g % T2_STAGES);
+          const long long u = g / T2_STAGES;
+          if (u >= 1 && !mbar_wait_cl(smem_u32(&empty_bar[s]), (uint32_t)((u - 1) & 1), &abort_s)) {
+            atomicOr(err, DS_WAIT_TIMEOUT);
+            abort_s = 1;
+            break;
+          }
+          const uint32_t fb = smem_u32(&full_bar[s]);
+          mbar_expect_tx(fb, T2_STAGE_BYTES);
+          bulk_g2s(stage_addr(s, 0), Ahi + (long long)kt * A_TILE, A_TILE * 4, fb);
+          bulk_g2s(stage_addr(s, 1), Alo + (long long)kt * A_TILE, A_TILE * 4, fb);
+          bulk_g2s(stage_addr(s, 2), Bhi + (long long)kt * B_TILE, T2_BHALF * 4, fb);
+          bulk_g2s(stage_addr(s, 3), Blo + (long long)kt * B_TILE, T2_BHALF * 4, fb);
+        }
+      }
+      // every issued copy lands, and every stage's last consumption is signalled here (the leader's
+      // commits arrive on this CTA's empty barriers), before the CTA leaves
+      for (long long q = (g > T2_STAGES ? g - T2_STAGES : 0); q < g; ++q) {
+        mbar_wait_cl(smem_u32(&full_bar[q % T2_STAGES]), (uint32_t)((q / T2_STAGES) & 1), &abort_s);
+        mbar_wait_cl(smem_u32(&empty_bar[q % T2_STAGES]), (uint32_t)((q / T2_STAGES) & 1), &abort_s);
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0 && rank == 1) {  // peer: forward "my halves of stage s are in" to the leader
+      long long g = 0;
+      for (int pt = cl; pt < b.total_tiles && !abort_s; pt += ncl) {
+        const TcItem &it = b.it[find_item(b, pt)];
+        bool ok = true;
+        for (int kt = 0; kt < it.nkt; ++kt, ++g) {
+          const int s = (int)(g % T2_STAGES);
+          if (!mbar_wait_cl(smem_u32(&full_bar[s]), (uint32_t)((g / T2_STAGES) & 1), &abort_s)) {
+            atomicOr(err, DS_WAIT_TIMEOUT);
+            abort_s = 1;
+            ok = false;
+            break;
+          }
+          mbar_arrive_cluster(map_to_rank(smem_u32(&pfull_bar[s]), 0));
+        }
+        if (!ok) break;
+      }
+    } else if (lane == 0 && rank == 0) {  // leader: MMA issuer for the pair
+      const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_BN >> 3) << 17) |
+                             ((uint32_t)((2 * TC_BM) >> 4) << 24);
+      long long g = 0;
+      int lt = 0;
+      for (int pt = cl; pt < b.total_tiles && !abort_s; pt += ncl, ++lt) {
+        const TcItem &it = b.it[find_item(b, pt)];
+        const int acc = lt & 1;
+        if (lt >= 2 && !mbar_wait_cl(smem_u32(&tempty_bar[acc]), (uint32_t)(((lt >> 1) - 1) & 1), &abort_s)) {
+          atomicOr(err, DS_WAIT_TIMEOUT);
+          abort_s = 1;
+          break;
+        }
+        fence_after();
+        const uint32_t dacc = tmem + (uint32_t)(acc * TC_BN);
+        bool ok = true;
+        for (int kt = 0; kt < it.nkt; ++kt, ++g) {
+          const int s = (int)(g % T2_STAGES);
+          const uint32_t par = (uint32_t)((g / T2_STAGES) & 1);
+          if (!mbar_wait_cl(smem_u32(&full_bar[s]), par, &abort_s) ||
+              !mbar_wait_cl(smem_u32(&pfull_bar[s]), par, &abort_s)) {
+            atomicOr(err, DS_WAIT_TIMEOUT);
+            abort_s = 1;
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t ah = stage_addr(s, 0), al = stage_addr(s, 1), bh = stage_addr(s, 2), bl = stage_addr(s, 3);
+#pragma unroll
+          for (int kk = 0; kk < TC_BK / 8; ++kk) {
+            const uint32_t o = kk * 32;
+            mma2_tf32(dacc, sdesc(ah + o), sdesc(bh + o), idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+            mma2_tf32(dacc, sdesc(ah + o), sdesc(bl + o), idesc, 1u);
+            mma2_tf32(dacc, sdesc(al + o), sdesc(bh + o), idesc, 1u);
+          }
+          mma2_commit_both(smem_u32(&empty_bar[s]));
+        }
+        if (!ok) break;
+        mma2_commit_both(smem_u32(&tfull_bar[acc]));
+      }
+    }
+  } else {
+    // epilogue warps of both CTAs: this CTA's 128 accumulator rows of the pair tile
+    const int q = warp & 3;
+    const int half = (warp - 2) >> 2;
+    float *stg = epi + (warp - 2) * 32 * EPI_PITCH;
+    const uint32_t tempty_leader0 = map_to_rank(smem_u32(&tempty_bar[0]), 0);
+    const uint32_t tempty_leader1 = map_to_rank(smem_u32(&tempty_bar[1]), 0);
+    int lt = 0;
+    for (int pt = cl; pt < b.total_tiles; pt += ncl, ++lt) {
+      const TcItem &it = b.it[find_item(b, pt)];
+      int mp, nt;
+      pair_pos(it, pt - it.tile0, mp, nt);
+      const int mt = 2 * mp + (int)rank;  // rows beyond m (a missing second row) are masked
+      const int acc = lt & 1;
+      const bool ready = mbar_wait_cl(smem_u32(&tfull_bar[acc]), (uint32_t)((lt >> 1) & 1), &abort_s);
+      if (!__all_sync(0xffffffffu, ready && !abort_s)) {
+        if (lane == 0) atomicOr(err, DS_WAIT_TIMEOUT);
+        abort_s = 1;
+        break;
+      }
+      fence_after();
+      drain_tile(it, tmem + (uint32_t)(acc * TC_BN), mt, nt, q, half, lane, stg, alpha, beta);
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cluster(acc ? tempty_leader1 : tempty_leader0);
+    }
+  }
+  fence_before();
+  cluster_sync_all();  // no CTA leaves while its peer may still signal it or read its shared memory
+  fence_after();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_BN) : "memory");
   }
 }
 
@@ -618,8 +877,9 @@ __global__ void pack_b_real_kernel(PackBatchP pb) {
 struct TcDevInfo {
   bool attr = false;
   int nsm = 0;
+  int clusters2 = 0;  // two-CTA clusters of tc_gemm2_kernel that can be resident at once
 };
-static int tc_device_setup() {
+static TcDevInfo tc_device_info() {
   static std::mutex mu;
   static std::vector<TcDevInfo> info;
   int dev = 0;
@@ -629,11 +889,37 @@ static int tc_device_setup() {
   TcDevInfo &d = info[dev];
   if (!d.attr) {
     RFDD_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+    RFDD_CUDA(cudaFuncSetAttribute(tc_gemm2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, T2_SMEM));
     RFDD_CUDA(cudaDeviceGetAttribute(&d.nsm, cudaDevAttrMultiProcessorCount, dev));
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = 2;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2, 1, 1);
+    cfg.blockDim = dim3(TC_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = T2_SMEM;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, (void *)tc_gemm2_kernel, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      nc = 0;
+    }
+    d.clusters2 = nc;
     d.attr = true;
   }
-  return std::max(1, d.nsm);
+  return d;
 }
+static int tc_device_setup() { return std::max(1, tc_device_info().nsm); }
+
+// Kernel choice for a launch (g_tc_engine_override lets rfdd_cgemm force one for tests):
+// the two-CTA kernel when it has work for every resident cluster and few of its pair tiles are
+// half empty (an odd number of row tiles leaves the second CTA of the last pair without rows).
+thread_local int g_tc_engine_override = 0;  // 0 automatic, 1 one-CTA kernel, 2 two-CTA kernel
+TcEngineScope::TcEngineScope(int e) : prev(g_tc_engine_override) { g_tc_engine_override = e; }
+TcEngineScope::~TcEngineScope() { g_tc_engine_override = prev; }
 
 // Tile walk of one item: down the columns when B spans at least 8 tile columns and the item's
 // packed A (hi + lo) takes at most 48 MB of the 129 MB L2, else along the rows.
@@ -724,10 +1010,45 @@ static void tc_gemm_run(cudaStream_t st, const std::vector<GemmItem<T>> &items, 
       e1 = profile_event();
       cudaEventRecord(e0, st);
     }
-    const int grid = std::max(1, std::min(tiles, nsm));
+    // pair tiles of the two-CTA kernel
+    long long pairs = 0, ghosts = 0;
+    for (int i = 0; i < cnt; ++i) {
+      pairs += (long long)((tb.it[i].mtc + 1) / 2) * tb.it[i].ntc;
+      ghosts += (long long)(tb.it[i].mtc & 1) * tb.it[i].ntc;
+    }
+    const TcDevInfo dinfo = tc_device_info();
+    bool two = splits == 3 && dinfo.clusters2 > 0 && pairs >= dinfo.clusters2 && 8 * ghosts <= pairs;
+    if (g_tc_engine_override == 1) two = false;
+    if (g_tc_engine_override == 2) two = splits == 3 && dinfo.clusters2 > 0;
     if (g_tc_events) RFDD_CUDA(cudaEventRecord(g_tc_events[0], st));
-    tc_gemm_kernel<<<grid, TC_THREADS, TC_SMEM, st>>>(tb, (float)alpha, (float)beta);
-    RFDD_CHECK_LAUNCH();
+    if (two) {
+      TcBatchP t2 = tb;
+      int p0 = 0;
+      for (int i = 0; i < cnt; ++i) {
+        t2.it[i].tile0 = p0;
+        p0 += ((t2.it[i].mtc + 1) / 2) * t2.it[i].ntc;
+      }
+      t2.total_tiles = p0;
+      const int ncl = std::max(1, std::min(p0, dinfo.clusters2));
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute attr;
+      attr.id = cudaLaunchAttributeClusterDimension;
+      attr.val.clusterDim.x = 2;
+      attr.val.clusterDim.y = 1;
+      attr.val.clusterDim.z = 1;
+      cfg.gridDim = dim3(2 * ncl, 1, 1);
+      cfg.blockDim = dim3(TC_THREADS, 1, 1);
+      cfg.dynamicSmemBytes = T2_SMEM;
+      cfg.stream = st;
+      cfg.attrs = &attr;
+      cfg.numAttrs = 1;
+      RFDD_CUDA(cudaLaunchKernelEx(&cfg, tc_gemm2_kernel, t2, (float)alpha, (float)beta));
+      RFDD_CHECK_LAUNCH();
+    } else {
+      const int grid = std::max(1, std::min(tiles, nsm));
+      tc_gemm_kernel<<<grid, TC_THREADS, TC_SMEM, st>>>(tb, (float)alpha, (float)beta);
+      RFDD_CHECK_LAUNCH();
+    }
     if (g_tc_events) RFDD_CUDA(cudaEventRecord(g_tc_events[1], st));
     if (e0) {
       cudaEventRecord(e1, st);

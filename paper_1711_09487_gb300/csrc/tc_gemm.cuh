@@ -22,6 +22,16 @@ struct TcKernelEvents {
   TcKernelEvents(const TcKernelEvents &) = delete;
   TcKernelEvents &operator=(const TcKernelEvents &) = delete;
 };
+// While alive, the tensor-core launches of the calling host thread use one kernel: 1 the one-CTA
+// kernel (128 x 256 tiles), 2 the two-CTA kernel (256 x 256 tiles on SM pairs), 0 the automatic
+// choice.  For tests that check both kernels.
+struct TcEngineScope {
+  int prev;
+  explicit TcEngineScope(int engine);
+  ~TcEngineScope();
+  TcEngineScope(const TcEngineScope &) = delete;
+  TcEngineScope &operator=(const TcEngineScope &) = delete;
+};
 // C = beta*C + alpha*A*B for every item (complex, row-major, no transposes)
 void tc_gemm_complex(cudaStream_t st, const std::vector<GemmItem<cx<float>>> &items, double alpha, double beta);
 // C = beta*C + alpha*A*B for real FP32 items (same kernel, 3xTF32)

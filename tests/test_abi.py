@@ -137,6 +137,19 @@ def test_setup_rejects_non_finite_values_before_device_work(R, which, bad):
     assert R.rfdd_kernel_launches() == launches
 
 
+def test_setup_rejects_an_unknown_csr_location_before_device_work(R):
+    A, M, part, p = _small()
+    a, m = R._Csr(A), R._Csr(M)
+    a.s.location = 7
+    out = R.C.c_void_p()
+    pt = np.ascontiguousarray(part, dtype=np.int32)
+    launches = R.rfdd_kernel_launches()
+    rc = R.load().rfdd_setup(R.C.byref(a.s), R.C.byref(m.s), pt.ctypes.data_as(R.C.POINTER(R.C.c_int32)), p,
+                             None, R.C.byref(out))
+    assert rc == R.RFDD_EINVAL and "location" in R.load().rfdd_last_error().decode()
+    assert R.rfdd_kernel_launches() == launches and not out.value
+
+
 def _reverse_rows(c):
     """The same matrix with every row's entries stored in decreasing column order."""
     col, val = c.col.copy(), c.val.copy()

@@ -1,5 +1,7 @@
-"""The complex-FP32 GEMM of the factorisations and solves: tensor-core kernel (tcgen05, 3xTF32)
-and CUDA-core kernel against an FP64 product, on ragged shapes that span several tiles."""
+"""The complex-FP32 GEMM of the factorisations and solves: the tensor-core GEMM (tcgen05, 3xTF32)
+with its automatic kernel choice, its one-CTA and two-CTA kernels forced, and the CUDA-core
+kernel, against an FP64 product on ragged shapes that span several tiles (odd and even numbers of
+128-row tiles, so the two-CTA kernel meets pairs with a missing second row)."""
 import numpy as np
 import pytest
 
@@ -20,9 +22,10 @@ def rnd(shape, seed):
     return (g.standard_normal(shape) + 1j * g.standard_normal(shape)).astype(np.complex64)
 
 
-@pytest.mark.parametrize("engine", [1, 0])
+@pytest.mark.parametrize("engine", [1, 0, 2, 3])
 @pytest.mark.parametrize("m,n,k", [(1, 1, 1), (5, 3, 7), (128, 128, 16), (130, 129, 33), (300, 257, 64),
-                                   (1000, 70, 128), (77, 640, 256), (513, 515, 100)])
+                                   (1000, 70, 128), (77, 640, 256), (513, 515, 100), (2000, 900, 256),
+                                   (1100, 1300, 96)])
 def test_cgemm(R, engine, m, n, k):
     A, B, C0 = rnd((m, k), 1), rnd((k, n), 2), rnd((m, n), 3)
     for alpha, beta in ((1.0, 0.0), (-1.0, 1.0)):

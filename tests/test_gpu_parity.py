@@ -276,6 +276,32 @@ def test_factor_forms_give_the_same_pairs(R, name):
     np.testing.assert_allclose(out[0], out[1], rtol=1e-10)
 
 
+def test_device_resident_csr_gives_the_same_pairs(R):
+    """rfdd_setup with A and M in device memory (rfdd_csr.location = 1) solves the same problem as
+    with host arrays; an unknown location is refused."""
+    import torch
+
+    class DevCsr:
+        def __init__(self, c):
+            self.rowptr = torch.from_numpy(c.rowptr.astype(np.int64)).cuda()
+            self.col = torch.from_numpy(c.col.astype(np.int32)).cuda()
+            self.val = torch.from_numpy(c.val.astype(np.float64)).cuda()
+
+    w = I.workload("q1_2d_24")
+    ev0, X0, rs0, _ = R.solve(w.A, w.M, w.part, w.p, w.alpha, w.beta, w.n_nodes)
+    ev1, X1, rs1, info = R.solve(DevCsr(w.A), DevCsr(w.M), w.part, w.p, w.alpha, w.beta, w.n_nodes)
+    np.testing.assert_array_equal(ev0, ev1)
+    assert info["status"] == 0 and rs1.max() <= 1e-10
+    a = R._Csr(w.A)
+    a.s.location = 7
+    m = R._Csr(w.M)
+    out = R.C.c_void_p()
+    pt = np.ascontiguousarray(w.part, dtype=np.int32)
+    rc = R.load().rfdd_setup(R.C.byref(a.s), R.C.byref(m.s), pt.ctypes.data_as(R.C.POINTER(R.C.c_int32)), w.p,
+                             None, R.C.byref(out))
+    assert rc == R.RFDD_EINVAL
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_edge_cases_one_node_block_one(R, prec):
     """Nc = 1, Lanczos block 1 (the printed Algorithm 2), psi = 1."""
