@@ -535,15 +535,22 @@ def run_serve(args):
         ids[i] = submit(srv, q, pc)
         t_sub[i] = time.perf_counter()
     good, wrong_count, lat, done_at = 0, 0, [], []
-    per_kind = {}
+    per_kind, statuses, wrong = {}, {}, []
     for i, q in enumerate(reqs):
         r = srv.wait(ids[i])
         ev, _, rs = R.rfdd_result_get(r, vectors=False)
         info = srv.request_info(ids[i])
+        rinfo = R.rfdd_result_info(r)
         del r
         g = int(np.count_nonzero(rs <= 1e-10))
         good += g
-        wrong_count += int(len(ev) != q["nev"])
+        statuses[str(info["status"])] = statuses.get(str(info["status"]), 0) + 1
+        if len(ev) != q["nev"]:
+            wrong_count += 1
+            if len(wrong) < 24:
+                wrong.append({"i": i, "kind": q["kind"], "N": q["N"], "splits": list(q["splits"]), "expected": q["nev"],
+                              "got": len(ev), "good": g, "status": info["status"], "passes": rinfo["passes"],
+                              "pre_nev": rinfo["pre_nev"], "max_resid": rinfo["max_resid"]})
         t_done = t_sub[i] - t0 + info["latency_ms"] / 1e3      # seconds after the first arrival
         done_at.append(t_done)
         lat.append((t_done - arrival[i]) * 1e3)
@@ -561,7 +568,8 @@ def run_serve(args):
                 "max": lat_s[-1]},
             "arrival_rate_per_s": rate, "load": args.load, "single_stream_capacity_per_s": capacity,
             "capacity_sample_requests": k, "max_inflight": args.inflight, "mem_budget_bytes": budget,
-            "requests_with_wrong_count": wrong_count, "per_kind": per_kind, "server": st,
+            "requests_with_wrong_count": wrong_count, "wrong_count_sample": wrong, "statuses": statuses,
+            "per_kind": per_kind, "server": st,
             "config": {"workload": "serving stream: seeded Poisson arrivals, 50% 2D Q1 N in 64..256, 50% 3D "
                                    "variable-kappa 7-point N in 24..48, 20..400 eigenvalues, p in {4,8,16}, 8 nodes",
                        "seed": 7, "precision": "mixed"}}

@@ -107,7 +107,8 @@ typedef struct {
   int64_t nev;          /* eigenpairs returned (inside [alpha, beta]) */
   int64_t mu;           /* Alg. 2 basis size (columns of Q) */
   int64_t k;            /* columns of Z (Eq. z) kept after M-orthonormalisation */
-  int64_t m;            /* completion block size */
+  int64_t m;            /* completion block size at the last pass (it grows when the Ritz values
+                           inside [alpha, beta] fill it; see rfdd_solve) */
   int32_t passes;       /* completion passes run */
   int32_t ir_steps_max; /* largest number of refinement steps any shifted solve needed */
   double max_resid;     /* largest residual among the returned pairs */
@@ -176,8 +177,12 @@ void rfdd_destroy(rfdd_handle *h);
 int rfdd_release(rfdd_handle *h);
 
 /* ---- full solve: Alg. 3 (RF-DDES) + completion ------------------------------------------
- * Runs a0-a10 for [alpha, beta] with n_nodes quadrature poles.  Factors of the previous solve
- * are replaced.  *out receives a result (also on RFDD_NOT_CONVERGED, whose pairs carry their
+ * Runs a0-a10 for [alpha, beta] with n_nodes quadrature poles.  The completion block starts at
+ * m = n_in + max(ceil(guard_frac n_in), min_guard) columns (n_in: RF-DDES Ritz values inside,
+ * rounded up to m_align); when the Ritz values inside leave fewer than that many guard columns, the
+ * block doubles with fresh counter-based vectors (at most four times, two more passes each), so
+ * that an interval holding more eigenvalues than RF-DDES found is still completed.  Factors of the
+ * previous solve are replaced.  *out receives a result (also on RFDD_NOT_CONVERGED, whose pairs carry their
  * residuals); free it with rfdd_result_free(). */
 int rfdd_solve(rfdd_handle *h, double alpha, double beta, int32_t n_nodes, rfdd_result **out);
 

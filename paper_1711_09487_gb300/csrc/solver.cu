@@ -1969,10 +1969,10 @@ void complete(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
   double res_level = std::max(res->info.pre_max_resid, 1e-300);
   Buf V, Xc, C;
   std::vector<double> theta, resid;
-  int passes = 0, irmax = 0;
+  int passes = 0, irmax = 0, grown = 0, pass_limit = h->opt.max_passes;
   bool converged = false;
   int64_t c0 = 0, nin = 0;
-  for (passes = 1; passes <= h->opt.max_passes; ++passes) {
+  for (passes = 1; passes <= pass_limit; ++passes) {
     // X <- 2 Re sum w_l (A - z_l M)^{-1} M X   (Eq. rhoAM through Eq. inv_dd2)
     V.ensure((size_t)n * m * sizeof(double));
     spmm_f64(st, h->P, 0, n, 0, n, 0.0, 1.0, X.as<double>(), m, V.as<double>(), m, m, false);
@@ -2017,13 +2017,41 @@ void complete(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
     RFDD_LOGF("pass %d: m=%lld r=%lld inside=%lld (prev %lld) max_res_inside=%.3e ir_steps=%d", passes,
               (long long)m, (long long)r, (long long)nin, (long long)count_prev, mx, irmax);
     res_level = nin > 0 ? mx : 1.0;
+    // The block must hold every eigenvalue inside plus guard vectors.  When the Ritz values inside
+    // leave fewer than the guard count of columns outside, the interval may hold more eigenvalues
+    // than the block (the RF-DDES count it was sized from was short), and subspace iteration
+    // cannot converge there: the filter is nearly flat inside the interval.  The block then grows
+    // to twice its size with fresh counter-based vectors, and the passes continue.
+    const int64_t guard = std::max<int64_t>((int64_t)std::ceil(h->opt.guard_frac * nin), h->opt.min_guard);
+    if (nin > 0 && r - nin < guard && grown < 4 && r < n) {
+      int64_t mn = std::max<int64_t>(2 * r, nin + 2 * guard);
+      if (h->opt.m_align > 1) mn = (mn + h->opt.m_align - 1) / h->opt.m_align * h->opt.m_align;
+      mn = std::min<int64_t>(mn, n);
+      if (mn > r) {
+        Buf Xg, T;
+        Xg.alloc((size_t)n * mn * sizeof(double));
+        T.alloc((size_t)n * (mn - r) * sizeof(double));
+        copy_rows_f64(st, X.as<double>(), r, Xg.as<double>(), mn, n, r);
+        counter_uniform_dev(st, h->opt.seed, 5000 + (uint64_t)grown, T.as<double>(), n * (mn - r));
+        copy_rows_f64(st, T.as<double>(), mn - r, Xg.as<double>() + r, mn, n, mn - r);
+        X.alloc((size_t)n * mn * sizeof(double));
+        RFDD_CUDA(cudaMemcpyAsync(X.p, Xg.p, (size_t)n * mn * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        RFDD_LOGF("pass %d: %lld Ritz values inside a block of %lld: block grown to %lld", passes, (long long)nin,
+                  (long long)r, (long long)mn);
+        m = mn;
+        ++grown;
+        pass_limit += 2;  // the grown block gets passes of its own
+        count_prev = -1;
+        continue;
+      }
+    }
     if (nin == count_prev && (nin == 0 || mx <= h->opt.res_tol)) {
       converged = true;
       break;
     }
     count_prev = nin;
   }
-  if (passes > h->opt.max_passes) passes = h->opt.max_passes;
+  if (passes > pass_limit) passes = pass_limit;
   // results in the original ordering: evecs[i_orig][c] = X[iperm[i_orig]][c0 + c]
   res->n = n;
   res->nev = nin;
@@ -2035,7 +2063,7 @@ void complete(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
   upload(res->resid_dev, res->resid, st);
   RFDD_CUDA(cudaStreamSynchronize(st));
   res->info.nev = nin;
-  res->info.m = h->m0;
+  res->info.m = m;
   res->info.passes = passes;
   res->info.ir_steps_max = irmax;
   res->info.max_resid = 0.0;

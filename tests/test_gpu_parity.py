@@ -303,6 +303,23 @@ def test_device_resident_csr_gives_the_same_pairs(R):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
+def test_completion_block_grows_when_rfddes_finds_too_few(R, prec):
+    """A poor RF-DDES basis (one eigenvector per subdomain, psi = 1, a loose Krylov tolerance) finds
+    far fewer Ritz values inside a wide interval than it holds; the completion block, sized from
+    that count without tile rounding, fills up and must grow until every eigenvalue is found."""
+    w = I.workload("q1_2d_24")
+    ev = w.exact
+    first, last = I.snap_to_gaps(ev, 11, 90)
+    a, b = I.interval_from_sorted(ev, first, last)
+    got, X, rs, info = R.solve(w.A, w.M, w.part, w.p, a, b, 8, precision=prec, nev_b=1, psi=1, block=2,
+                               lanczos_tol=0.5, m_align=1)
+    assert info["pre_nev"] < last - first + 1          # RF-DDES alone is short here
+    assert info["status"] == 0 and len(got) == last - first + 1
+    assert info["m"] >= len(got) and rs.max() <= 1e-10
+    np.testing.assert_allclose(got, ev[first - 1:last], rtol=TOL[prec]["ev"])
+
+
+@pytest.mark.parametrize("prec", [0, 1])
 def test_edge_cases_one_node_block_one(R, prec):
     """Nc = 1, Lanczos block 1 (the printed Algorithm 2), psi = 1."""
     w = I.workload("q1_2d_24")
