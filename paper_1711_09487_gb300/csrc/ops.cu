@@ -579,6 +579,22 @@ void gather_rows_f64(cudaStream_t st, const double *src, int64_t lds, const int6
   RFDD_CHECK_LAUNCH();
 }
 
+__global__ void gather_rows_cols_kernel(const double *__restrict__ src, int64_t lds, const int64_t *__restrict__ ridx,
+                                        const int64_t *__restrict__ cidx, double *__restrict__ dst, int64_t ldd,
+                                        int64_t nrows, int64_t ncols) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nrows * ncols;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / ncols, c = e % ncols;
+    dst[i * ldd + c] = src[ridx[i] * lds + cidx[c]];
+  }
+}
+void gather_rows_cols_f64(cudaStream_t st, const double *src, int64_t lds, const int64_t *ridx, const int64_t *cidx,
+                          double *dst, int64_t ldd, int64_t nrows, int64_t ncols) {
+  if (nrows * ncols <= 0) return;
+  gather_rows_cols_kernel<<<grid_for(nrows * ncols), 256, 0, st>>>(src, lds, ridx, cidx, dst, ldd, nrows, ncols);
+  RFDD_CHECK_LAUNCH();
+}
+
 #define RFDD_INST_OPS(T)                                                                                     \
   template void assemble_blocks<T>(cudaStream_t, const DevPencil &, const DevDD &, const int64_t *, int64_t, \
                                    const int64_t *, const cx<double> *, int, T *, bool);

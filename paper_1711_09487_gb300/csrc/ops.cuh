@@ -96,6 +96,9 @@ void copy_rows_f64(cudaStream_t st, const double *src, int64_t lds, double *dst,
 // X[i][c] -> X[perm[i]][c] style row permutation: dst[i] = src[idx[i]]
 void gather_rows_f64(cudaStream_t st, const double *src, int64_t lds, const int64_t *idx, double *dst,
                      int64_t ldd, int64_t nrows, int64_t ncols);
+// dst[i][c] = src[ridx[i]][cidx[c]]  (nrows x ncols)
+void gather_rows_cols_f64(cudaStream_t st, const double *src, int64_t lds, const int64_t *ridx, const int64_t *cidx,
+                          double *dst, int64_t ldd, int64_t nrows, int64_t ncols);
 
 // Y_l (s_j x m) = rows sidx_j of G_l ; G_l rows sidx_j -= R_l (ordered, call for j = 0..p-1)
 template <typename T>

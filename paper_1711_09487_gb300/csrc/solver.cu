@@ -239,6 +239,8 @@ struct rfdd_handle {
   std::vector<int64_t> off, perm, iperm, d, sidx_off, D;
   std::vector<int32_t> sidx;
   double normA = 0.0, normM = 0.0;  // max absolute row sums
+  double gershM = 0.0;              // min over rows of M_ii - sum_{j != i} |M_ij| (a lower bound of M's
+                                    // spectrum when positive)
   bool has_me = false;              // M_E != 0 (the Gamma block of Z is needed)
   std::vector<int64_t> host_rp;
   std::vector<int32_t> host_cl, host_posmap;
@@ -585,7 +587,7 @@ void do_setup(rfdd_handle *h, const rfdd_csr *A, const rfdd_csr *M, const int32_
   const int64_t nt_max = std::max<int64_t>(1, std::thread::hardware_concurrency());
   std::vector<std::vector<int32_t>> ccl(nt_max);
   std::vector<std::vector<double>> cav(nt_max), cmv(nt_max);
-  std::vector<double> cna(nt_max, 0.0), cnm(nt_max, 0.0);
+  std::vector<double> cna(nt_max, 0.0), cnm(nt_max, 0.0), cgm(nt_max, std::numeric_limits<double>::infinity());
   std::vector<int64_t> cr0(nt_max, -1);
   std::vector<int64_t> rowlen(n, 0);
   parallel_rows(n, [&](int64_t r0, int64_t r1, int t) {
@@ -593,7 +595,7 @@ void do_setup(rfdd_handle *h, const rfdd_csr *A, const rfdd_csr *M, const int32_
     std::vector<std::pair<int64_t, std::pair<double, double>>> row;
     std::vector<int32_t> c;
     std::vector<double> a, m;
-    double na = 0.0, nm = 0.0;
+    double na = 0.0, nm = 0.0, gm = std::numeric_limits<double>::infinity();
     int64_t est = 0;
     for (int64_t r = r0; r < r1; ++r) {
       const int64_t i = h->perm[r];
@@ -610,12 +612,15 @@ void do_setup(rfdd_handle *h, const rfdd_csr *A, const rfdd_csr *M, const int32_
         row.push_back({h->iperm[A->col[e]], {A->val[e], 0.0}});
         sa += std::fabs(A->val[e]);
       }
+      double mdiag = 0.0;
       for (int64_t e = M->rowptr[i]; e < M->rowptr[i + 1]; ++e) {
         row.push_back({h->iperm[M->col[e]], {0.0, M->val[e]}});
         sm += std::fabs(M->val[e]);
+        if (M->col[e] == i) mdiag += M->val[e];
       }
       na = std::max(na, sa);
       nm = std::max(nm, sm);
+      gm = std::min(gm, 2.0 * mdiag - sm);
       // equal columns are summed below; each entry holds only one of (a, m), so their order is free
       std::sort(row.begin(), row.end(), [](auto &x, auto &y) { return x.first < y.first; });
       const size_t before = c.size();
@@ -634,15 +639,18 @@ void do_setup(rfdd_handle *h, const rfdd_csr *A, const rfdd_csr *M, const int32_
     cr0[t] = r0;
     cna[t] = na;
     cnm[t] = nm;
+    cgm[t] = gm;
     ccl[t] = std::move(c);
     cav[t] = std::move(a);
     cmv[t] = std::move(m);
   });
   for (int64_t r = 0; r < n; ++r) rp[r + 1] = rp[r] + rowlen[r];
   h->normA = h->normM = 0.0;
+  h->gershM = std::numeric_limits<double>::infinity();
   for (int64_t t = 0; t < nt_max; ++t) {
     h->normA = std::max(h->normA, cna[t]);
     h->normM = std::max(h->normM, cnm[t]);
+    h->gershM = std::min(h->gershM, cgm[t]);
   }
   cl.resize(rp[n]);
   av.resize(rp[n]);
@@ -1967,11 +1975,22 @@ void complete(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
   }
   int64_t count_prev = res->info.pre_nev;
   double res_level = std::max(res->info.pre_max_resid, 1e-300);
+  // Condition bound of the shifted systems when M's Gershgorin bound is positive:
+  // ||(A - z M)^{-1}|| <= 1 / (|Im z| lambda_min(M)), so kappa(A - z M) <= (||A|| + |z| ||M||) /
+  // (|Im z| gershM).  A solve refined to scaled backward error eta has forward error up to kappa eta.
+  double kappa = 0.0;
+  if (h->gershM > 0.0 && std::isfinite(h->gershM))
+    for (const auto &zl : h->z) {
+      const double zn = std::hypot(zl.re, zl.im);
+      kappa = std::max(kappa, (h->normA + zn * h->normM) / (std::fabs(zl.im) * h->gershM));
+    }
   Buf V, Xc, C;
   std::vector<double> theta, resid;
+  std::vector<int64_t> keep;  // Ritz pairs returned: inside [alpha, beta] and not spurious
   int passes = 0, irmax = 0, grown = 0, pass_limit = h->opt.max_passes;
   bool converged = false;
-  int64_t c0 = 0, nin = 0;
+  bool gamma_ok = true;  // X holds M-orthonormal Ritz vectors (filter gains can be measured)
+  int64_t nin = 0;
   for (passes = 1; passes <= pass_limit; ++passes) {
     // X <- 2 Re sum w_l (A - z_l M)^{-1} M X   (Eq. rhoAM through Eq. inv_dd2)
     V.ensure((size_t)n * m * sizeof(double));
@@ -1979,11 +1998,22 @@ void complete(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
     Xc.ensure((size_t)nc * n * m * sizeof(cx<double>));
     // the filter only has to be as accurate as the subspace it acts on: refine the shifted
     // solves to a small fraction of the current residual level, and no further than a small
-    // fraction (1/100) of the residual target
-    const double ir_tol = std::max(std::max(1e-15, 1e-2 * h->opt.res_tol), 1e-6 * res_level);
+    // fraction (1/100) of the residual target; where the condition bound is known, kappa times
+    // the backward error stays below those fractions
+    double ir_tol = 1e-6 * res_level;
+    if (kappa > 0.0) ir_tol = std::min(ir_tol, 1e-2 * res_level / kappa);
+    ir_tol = std::max(std::max(1e-15, 1e-2 * h->opt.res_tol / std::max(1.0, kappa)), ir_tol);
     irmax = std::max(irmax, refined_solve<Tf>(h, V.as<double>(), Xc.as<cx<double>>(), m, ir_tol));
     weighted_real_sum<cx<double>>(st, Xc.as<cx<double>>(), n * m, h->w_dev.as<cx<double>>(), nc, 2.0, X.as<double>(),
                                   n * m);
+    // filter gains: with X_in the M-orthonormal block before filtering (V = M X_in) and Y the
+    // filtered block, G = X_in^T M Y is the filter projected on range(X_in)
+    Buf G;
+    if (gamma_ok) {
+      G.alloc((size_t)m * m * sizeof(double));
+      basis_gemm(h, {{V.as<double>(), X.as<double>(), G.as<double>(), (int)m, (int)m, (int)n, (int)m, (int)m, (int)m}},
+                 true, false, 1.0, 0.0, {1});
+    }
     // Rayleigh-Ritz on range(X), all Ritz pairs kept
     std::vector<int> sel;
     RRout rr = rayleigh_ritz_coeffs(
@@ -1995,6 +2025,27 @@ void complete(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
         },
         C, sel);
     const int64_t r = rr.r;
+    // gain of Ritz vector j = Y c_j: the filter's Rayleigh quotient at its preimage X_in c_j,
+    // c_j^T G c_j / c_j^T c_j (rho(lambda) for an eigenvector; rho >= 1/2 on [alpha, beta])
+    std::vector<double> gain;
+    if (gamma_ok) {
+      Buf T;
+      T.alloc((size_t)m * r * sizeof(double));
+      basis_gemm(h, {{G.as<double>(), C.as<double>(), T.as<double>(), (int)m, (int)r, (int)m, (int)m, (int)r, (int)r}},
+                 false, false, 1.0, 0.0);
+      std::vector<double> hc((size_t)m * r), ht((size_t)m * r);
+      RFDD_CUDA(cudaMemcpyAsync(hc.data(), C.p, hc.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+      RFDD_CUDA(cudaMemcpyAsync(ht.data(), T.p, ht.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+      RFDD_CUDA(cudaStreamSynchronize(st));
+      gain.assign(r, 0.0);
+      std::vector<double> nrm(r, 0.0);
+      for (int64_t i = 0; i < m; ++i)
+        for (int64_t j = 0; j < r; ++j) {
+          gain[j] += hc[i * r + j] * ht[i * r + j];
+          nrm[j] += hc[i * r + j] * hc[i * r + j];
+        }
+      for (int64_t j = 0; j < r; ++j) gain[j] = nrm[j] > 0.0 ? gain[j] / nrm[j] : 0.0;
+    }
     Buf Xn;
     Xn.alloc((size_t)n * r * sizeof(double));
     basis_gemm(h, {{X.as<double>(), C.as<double>(), Xn.as<double>(), (int)n, (int)r, (int)m, (int)m,
@@ -2005,43 +2056,54 @@ void complete(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
     X.alloc((size_t)n * r * sizeof(double));
     RFDD_CUDA(cudaMemcpyAsync(X.p, Xn.p, (size_t)n * r * sizeof(double), cudaMemcpyDeviceToDevice, st));
     m = r;
-    c0 = 0;
-    nin = 0;
+    gamma_ok = true;
+    // A Ritz value inside [alpha, beta] whose vector the filter damps below 1/4 is spurious: a
+    // mixture of eigenvectors from both sides of the interval with nearly equal, small filter
+    // values (the midpoint filter is symmetric about the centre), whose Rayleigh quotient falls
+    // inside.  It is neither counted nor returned.
+    keep.clear();
+    int64_t inside = 0, spurious = 0;
     double mx = 0.0;
     for (int64_t c = 0; c < r; ++c)
       if (theta[c] >= alpha && theta[c] <= beta) {
-        if (nin == 0) c0 = c;
-        ++nin;
+        ++inside;
+        if (!gain.empty() && gain[c] < 0.25) {
+          ++spurious;
+          continue;
+        }
+        keep.push_back(c);
         mx = std::max(mx, resid[c]);
       }
-    RFDD_LOGF("pass %d: m=%lld r=%lld inside=%lld (prev %lld) max_res_inside=%.3e ir_steps=%d", passes,
-              (long long)m, (long long)r, (long long)nin, (long long)count_prev, mx, irmax);
+    nin = (int64_t)keep.size();
+    RFDD_LOGF("pass %d: m=%lld inside=%lld (spurious %lld, prev %lld) max_res_inside=%.3e ir_steps=%d", passes,
+              (long long)m, (long long)nin, (long long)spurious, (long long)count_prev, mx, irmax);
     res_level = nin > 0 ? mx : 1.0;
     // The block must hold every eigenvalue inside plus guard vectors.  When the Ritz values inside
     // leave fewer than the guard count of columns outside, the interval may hold more eigenvalues
     // than the block (the RF-DDES count it was sized from was short), and subspace iteration
     // cannot converge there: the filter is nearly flat inside the interval.  The block then grows
     // to twice its size with fresh counter-based vectors, and the passes continue.
-    const int64_t guard = std::max<int64_t>((int64_t)std::ceil(h->opt.guard_frac * nin), h->opt.min_guard);
-    if (nin > 0 && r - nin < guard && grown < 4 && r < n) {
-      int64_t mn = std::max<int64_t>(2 * r, nin + 2 * guard);
+    const int64_t guard = std::max<int64_t>((int64_t)std::ceil(h->opt.guard_frac * inside), h->opt.min_guard);
+    if (inside > 0 && r - inside < guard && grown < 4 && r < n) {
+      int64_t mn = std::max<int64_t>(2 * r, inside + 2 * guard);
       if (h->opt.m_align > 1) mn = (mn + h->opt.m_align - 1) / h->opt.m_align * h->opt.m_align;
       mn = std::min<int64_t>(mn, n);
       if (mn > r) {
-        Buf Xg, T;
+        Buf Xg, Tr;
         Xg.alloc((size_t)n * mn * sizeof(double));
-        T.alloc((size_t)n * (mn - r) * sizeof(double));
+        Tr.alloc((size_t)n * (mn - r) * sizeof(double));
         copy_rows_f64(st, X.as<double>(), r, Xg.as<double>(), mn, n, r);
-        counter_uniform_dev(st, h->opt.seed, 5000 + (uint64_t)grown, T.as<double>(), n * (mn - r));
-        copy_rows_f64(st, T.as<double>(), mn - r, Xg.as<double>() + r, mn, n, mn - r);
+        counter_uniform_dev(st, h->opt.seed, 5000 + (uint64_t)grown, Tr.as<double>(), n * (mn - r));
+        copy_rows_f64(st, Tr.as<double>(), mn - r, Xg.as<double>() + r, mn, n, mn - r);
         X.alloc((size_t)n * mn * sizeof(double));
         RFDD_CUDA(cudaMemcpyAsync(X.p, Xg.p, (size_t)n * mn * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        RFDD_LOGF("pass %d: %lld Ritz values inside a block of %lld: block grown to %lld", passes, (long long)nin,
+        RFDD_LOGF("pass %d: %lld Ritz values inside a block of %lld: block grown to %lld", passes, (long long)inside,
                   (long long)r, (long long)mn);
         m = mn;
         ++grown;
         pass_limit += 2;  // the grown block gets passes of its own
         count_prev = -1;
+        gamma_ok = false;  // the new columns are not Ritz vectors yet
         continue;
       }
     }
@@ -2052,13 +2114,23 @@ void complete(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
     count_prev = nin;
   }
   if (passes > pass_limit) passes = pass_limit;
-  // results in the original ordering: evecs[i_orig][c] = X[iperm[i_orig]][c0 + c]
+  // results in the original ordering: evecs[i_orig][c] = X[iperm[i_orig]][keep[c]]
   res->n = n;
   res->nev = nin;
-  res->evals.assign(theta.begin() + c0, theta.begin() + c0 + nin);
-  res->resid.assign(resid.begin() + c0, resid.begin() + c0 + nin);
+  res->evals.clear();
+  res->resid.clear();
+  for (int64_t c : keep) {
+    res->evals.push_back(theta[c]);
+    res->resid.push_back(resid[c]);
+  }
   res->evecs.alloc((size_t)n * std::max<int64_t>(1, nin) * sizeof(double));
-  if (nin > 0) gather_rows_f64(st, X.as<double>() + c0, m, h->iperm_dev.as<int64_t>(), res->evecs.as<double>(), nin, n, nin);
+  if (nin > 0) {
+    Buf keep_dev;
+    upload(keep_dev, keep, st);
+    gather_rows_cols_f64(st, X.as<double>(), m, h->iperm_dev.as<int64_t>(), keep_dev.as<int64_t>(),
+                         res->evecs.as<double>(), nin, n, nin);
+    RFDD_CUDA(cudaStreamSynchronize(st));
+  }
   upload(res->evals_dev, res->evals, st);
   upload(res->resid_dev, res->resid, st);
   RFDD_CUDA(cudaStreamSynchronize(st));

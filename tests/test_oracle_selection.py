@@ -145,3 +145,38 @@ def test_stop_pin_catches_an_absolute_tolerance_and_a_wrong_check_period():
                              "steps_per_check = check_every")
     F, _ = diag_F(1.0)
     assert per_block_step(F, S_DIM, tol=1e-6, block=3, seed=5)["mu"] != expected_mu(3)
+
+
+# ----------------------------------------------------------------------------------------
+# Completion (reading A17): filter gain of Ritz vectors, spurious Ritz values
+# ----------------------------------------------------------------------------------------
+
+def test_filter_gain_is_rho_on_eigenvectors_and_small_on_mirror_mixtures():
+    """For exact eigenvectors the gain equals the closed-form filter value rho(lambda); a mixture
+    of two eigenvectors on opposite sides of the interval (equal small rho) has a Rayleigh
+    quotient inside the interval but a gain far below 1/4, so the completion discards it."""
+    import rfdd_inputs as I
+    w = I.workload("q1_2d_24")
+    blk = O.Blocks(w.A.to_scipy(), w.M.to_scipy(), w.part, w.p)
+    lam, Xe = sla.eigh(blk.Ap.toarray(), blk.Mp.toarray())
+    z, wt = O.quadrature(w.alpha, w.beta, w.n_nodes, w.rule)
+    fac = O.Factors(blk, z)
+    pick = [5, 12, 25, 40, 60]
+    Xp = Xe[:, pick]
+    Y = O.filter_full(fac, wt, blk.Mp @ Xp)
+    th, Xn = O.rayleigh_ritz(blk.Ap, blk.Mp, Y)
+    g = O.filter_gain(blk.Mp, Xp, Y, Xn)
+    rho = O.filter_value(lam[pick], z, wt)
+    np.testing.assert_allclose(np.sort(g), np.sort(rho), rtol=1e-8, atol=1e-12)
+    # mirror pair: eigenvalues below alpha and above beta with nearly equal filter values
+    c = 0.5 * (w.alpha + w.beta)
+    lo = np.flatnonzero(lam < w.alpha)[-3]
+    hi = np.flatnonzero(lam > w.beta)[np.argmin(np.abs(lam[lam > w.beta] - (2 * c - lam[lo])))]
+    v = (Xe[:, lo] + Xe[:, hi]) / np.sqrt(2.0)
+    theta = (v @ (blk.Ap @ v)) / (v @ (blk.Mp @ v))
+    assert w.alpha < theta < w.beta
+    Xp = np.column_stack([v, Xe[:, 15]])
+    Y = O.filter_full(fac, wt, blk.Mp @ Xp)
+    Xn = Y / np.sqrt(np.einsum("ij,ij->j", Y, blk.Mp @ Y))
+    g = O.filter_gain(blk.Mp, Xp, Y, Xn)
+    assert g[0] < 0.25 and g[1] > 0.5
