@@ -530,11 +530,13 @@ def rfdd_solve(A, M, part, p, alpha, beta, n_nodes=4, rule="midpoint", sigma=Non
       through Eq. (inv_dd2) with the same factors, then M-orthonormalisation and Rayleigh-Ritz;
       X starts from the m RF-DDES Ritz vectors nearest the interval, m = n_in + max(ceil(0.3 n_in),
       8); stop when every Ritz pair inside [alpha, beta] has residual <= res_tol and the count
-      inside is unchanged from the previous pass.  A Ritz value inside whose filter gain
-      (filter_gain) is below 1/4 is spurious and neither counted nor returned.  When the Ritz
-      values inside leave fewer than max(ceil(0.3 count), 8) columns of the block, the block
-      doubles with counter-based vectors (stream 5000 + growth index), at most four times, two
-      more passes each.
+      inside is unchanged from the previous pass.  When some inside pairs keep large residuals
+      while the number of converged ones stays the same over two passes, the next filter
+      application measures the filter gain (filter_gain) of those suspects; if every suspect's
+      gain is below 1/4 they are spurious and the converged pairs of that pass are the result.
+      When the Ritz values inside leave fewer than max(ceil(0.3 count), 8) columns of the block,
+      the block doubles with counter-based vectors (stream 5000 + growth index), at most four
+      times, two more passes each; at most max_passes + 10 passes in all.
     Returns a dict with eigenvalues, eigenvectors (original ordering), residuals and diagnostics.
     """
     A = sp.csr_matrix(A)
@@ -569,43 +571,56 @@ def rfdd_solve(A, M, part, p, alpha, beta, n_nodes=4, rule="midpoint", sigma=Non
     res_in = pre["res"]
     th_in = pre["theta"]
     X_in = X
-    gain_ok, grown, limit = True, 0, max_passes
+    grown, limit, good_prev, suspect = 0, max_passes, -1, None
     while passes < limit:
         passes += 1
         Y = filter_full(fac, w, Mp @ X)                           # completion pass
-        theta, X_new = rayleigh_ritz(Ap, Mp, Y)
-        raw = (theta >= alpha) & (theta <= beta)
-        inside = raw & (filter_gain(Mp, X, Y, X_new) >= 0.25) if gain_ok else raw
-        X, gain_ok = X_new, True
+        if suspect is not None:
+            # the last pass's inside pairs with large residuals: spurious when the filter damps
+            # them below 1/4 (mixtures of eigenvectors from both sides of the interval)
+            th_s, res_s, X_s = suspect
+            g = filter_gain(Mp, X_s, Y)
+            bad = (th_s >= alpha) & (th_s <= beta) & (res_s > res_tol)
+            if np.all(g[bad] < 0.25):
+                ok = (th_s >= alpha) & (th_s <= beta) & (res_s <= res_tol)
+                th_in, X_in, res_in = th_s[ok], X_s[:, ok], res_s[ok]
+                converged = True
+                break
+        theta, X = rayleigh_ritz(Ap, Mp, Y)
+        inside = (theta >= alpha) & (theta <= beta)
         th_in = theta[inside]
         X_in = X[:, inside]
         res_in = residuals(Ap, Mp, th_in, X_in)
         cnt = int(np.count_nonzero(inside))
-        n_raw = int(np.count_nonzero(raw))
-        guard = max(int(math.ceil(guard_frac * n_raw)), min_guard)
-        if n_raw > 0 and X.shape[1] - n_raw < guard and grown < 4 and X.shape[1] < X.shape[0]:
-            mn = min(max(2 * X.shape[1], n_raw + 2 * guard), X.shape[0])
+        good = int(np.count_nonzero(res_in <= res_tol))
+        guard = max(int(math.ceil(guard_frac * cnt)), min_guard)
+        if cnt > 0 and X.shape[1] - cnt < guard and grown < 4 and X.shape[1] < X.shape[0]:
+            mn = min(max(2 * X.shape[1], cnt + 2 * guard), X.shape[0])
             extra = counter_uniform(seed, 5000 + grown, X.shape[0] * (mn - X.shape[1]))
             X = np.hstack([X, extra.reshape(X.shape[0], mn - X.shape[1])])
-            grown, limit, count_prev, gain_ok = grown + 1, limit + 2, -1, False
+            grown, limit = grown + 1, min(max_passes + 10, limit + 2)
+            count_prev, good_prev, suspect = -1, -1, None
             continue
         if cnt == count_prev and (cnt == 0 or res_in.max() <= res_tol):
             converged = True
             break
-        count_prev = cnt
+        suspect = None
+        if 0 < good < cnt and good == good_prev:
+            res_all = np.full(len(theta), np.inf)
+            res_all[inside] = res_in
+            suspect = (theta.copy(), res_all, X.copy())
+            limit = min(max_passes + 10, max(limit, passes + 1))
+        count_prev, good_prev = cnt, good
     return dict(evals=th_in, evecs=blk.to_original(X_in), resid=res_in, passes=passes,
                 converged=converged, mu=lz["mu"], k=Z.shape[1], pre=pre, blocks=blk,
                 z=z, w=w, sigma=sigma, lanczos=lz)
 
 
-def filter_gain(Mp, X_prev, Y, X_new):
-    """Filter gain of each new Ritz vector x = Y c (Y = rho(A) X_prev, X_prev M-orthonormal): the
-    Rayleigh quotient of the filter at the preimage X_prev c, c^T (X_prev^T M Y) c / c^T c.  It is
-    rho(lambda) when x is an eigenvector (rho >= 1/2 on [alpha, beta], Section 2.1)."""
-    C = np.linalg.lstsq(Y, X_new, rcond=None)[0]
-    G = X_prev.T @ (Mp @ Y)
-    G = 0.5 * (G + G.T)
-    return np.einsum("ij,ij->j", C, G @ C) / np.einsum("ij,ij->j", C, C)
+def filter_gain(Mp, X, Y):
+    """Filter gain of each column x of an M-orthonormal block X with Y = rho(A) X: the Rayleigh
+    quotient x^T M rho(A) x, which is rho(lambda) when x is an eigenvector (rho >= 1/2 on
+    [alpha, beta], Section 2.1)."""
+    return np.einsum("ij,ij->j", Mp @ X, Y)
 
 
 def brute_force(A, M, alpha=None, beta=None):

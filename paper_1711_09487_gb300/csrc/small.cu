@@ -156,6 +156,27 @@ void ritz_residuals(cudaStream_t st, const double *AX, const double *MX, const d
   RFDD_CHECK_LAUNCH();
 }
 
+// out[c] = sum_i X[i][c] Y[i][c]  (n x b row-major blocks; fixed-order block reduction)
+__global__ void col_dots_kernel(const double *__restrict__ X, const double *__restrict__ Y, int64_t n, int64_t b,
+                                double *out) {
+  const int64_t c = blockIdx.x;
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s = fma(X[i * b + c], Y[i * b + c], s);
+  __shared__ double r1[256];
+  r1[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) r1[threadIdx.x] += r1[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[c] = r1[0];
+}
+void col_dots(cudaStream_t st, const double *X, const double *Y, int64_t n, int64_t b, double *out) {
+  if (b <= 0) return;
+  col_dots_kernel<<<(unsigned)b, 256, 0, st>>>(X, Y, n, b, out);
+  RFDD_CHECK_LAUNCH();
+}
+
 template <typename T>
 __global__ void sub_inplace_kernel(const T *__restrict__ x, T *__restrict__ y, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)

@@ -25,6 +25,8 @@ void inv_sqrt_vec(cudaStream_t st, const double *lam, int64_t r, double *f);
 // residual norms: res[c] = ||AX_c - theta_c MX_c|| / (|theta_c| ||MX_c||)
 void ritz_residuals(cudaStream_t st, const double *AX, const double *MX, const double *theta, int64_t n, int64_t b,
                     double *res);
+// out[c] = sum_i X[i][c] Y[i][c] for n x b row-major blocks
+void col_dots(cudaStream_t st, const double *X, const double *Y, int64_t n, int64_t b, double *out);
 // y[i] -= x[i] for generic element type
 template <typename T>
 void sub_inplace(cudaStream_t st, const T *x, T *y, int64_t n);

@@ -1984,17 +1984,28 @@ void complete(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
       const double zn = std::hypot(zl.re, zl.im);
       kappa = std::max(kappa, (h->normA + zn * h->normM) / (std::fabs(zl.im) * h->gershM));
     }
-  Buf V, Xc, C;
-  std::vector<double> theta, resid;
-  std::vector<int64_t> keep;  // Ritz pairs returned: inside [alpha, beta] and not spurious
+  Buf V, Xc, C, Xprev;
+  std::vector<double> theta, resid, theta_prev, resid_prev;
+  std::vector<int64_t> keep;  // Ritz pairs returned: inside [alpha, beta], converged, not spurious
   int passes = 0, irmax = 0, grown = 0, pass_limit = h->opt.max_passes;
-  bool converged = false;
-  bool gamma_ok = true;  // X holds M-orthonormal Ritz vectors (filter gains can be measured)
-  int64_t nin = 0;
+  bool converged = false, from_prev = false;
+  // A pass whose inside Ritz pairs have all converged except some with large residuals, while
+  // the number of converged ones did not change, leaves those pairs "suspect": the next filter
+  // application measures the filter's Rayleigh quotient at each of them (gain, rho(lambda) for an
+  // eigenvector and >= 1/2 on [alpha, beta]).  Suspects with gain below 1/4 are spurious: mixtures
+  // of eigenvectors from both sides of the interval with equal small filter values (the midpoint
+  // filter is symmetric about the centre), whose Rayleigh quotient falls inside.  They are
+  // dropped and the converged pairs of that pass are the result.
+  bool suspect = false;
+  int64_t nin = 0, good_prev = -1;
   for (passes = 1; passes <= pass_limit; ++passes) {
     // X <- 2 Re sum w_l (A - z_l M)^{-1} M X   (Eq. rhoAM through Eq. inv_dd2)
     V.ensure((size_t)n * m * sizeof(double));
     spmm_f64(st, h->P, 0, n, 0, n, 0.0, 1.0, X.as<double>(), m, V.as<double>(), m, m, false);
+    if (suspect) {
+      Xprev.alloc((size_t)n * m * sizeof(double));
+      RFDD_CUDA(cudaMemcpyAsync(Xprev.p, X.p, (size_t)n * m * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
     Xc.ensure((size_t)nc * n * m * sizeof(cx<double>));
     // the filter only has to be as accurate as the subspace it acts on: refine the shifted
     // solves to a small fraction of the current residual level, and no further than a small
@@ -2006,13 +2017,34 @@ void complete(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
     irmax = std::max(irmax, refined_solve<Tf>(h, V.as<double>(), Xc.as<cx<double>>(), m, ir_tol));
     weighted_real_sum<cx<double>>(st, Xc.as<cx<double>>(), n * m, h->w_dev.as<cx<double>>(), nc, 2.0, X.as<double>(),
                                   n * m);
-    // filter gains: with X_in the M-orthonormal block before filtering (V = M X_in) and Y the
-    // filtered block, G = X_in^T M Y is the filter projected on range(X_in)
-    Buf G;
-    if (gamma_ok) {
-      G.alloc((size_t)m * m * sizeof(double));
-      basis_gemm(h, {{V.as<double>(), X.as<double>(), G.as<double>(), (int)m, (int)m, (int)n, (int)m, (int)m, (int)m}},
-                 true, false, 1.0, 0.0, {1});
+    if (suspect) {
+      // gains of the last pass's Ritz vectors x (M-orthonormal): x^T M rho(A) x
+      Buf g;
+      g.alloc((size_t)m * sizeof(double));
+      col_dots(st, V.as<double>(), X.as<double>(), n, m, g.as<double>());
+      std::vector<double> gain(m);
+      RFDD_CUDA(cudaMemcpyAsync(gain.data(), g.p, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+      RFDD_CUDA(cudaStreamSynchronize(st));
+      bool all_spurious = true;
+      int64_t spurious = 0;
+      for (int64_t c = 0; c < m; ++c)
+        if (theta_prev[c] >= alpha && theta_prev[c] <= beta && resid_prev[c] > h->opt.res_tol) {
+          if (gain[c] < 0.25) ++spurious;
+          else all_spurious = false;
+        }
+      RFDD_LOGF("pass %d: %lld suspect Ritz pairs of the last pass are spurious (all: %d)", passes,
+                (long long)spurious, (int)all_spurious);
+      if (all_spurious) {
+        keep.clear();
+        for (int64_t c = 0; c < m; ++c)
+          if (theta_prev[c] >= alpha && theta_prev[c] <= beta && resid_prev[c] <= h->opt.res_tol) keep.push_back(c);
+        theta = theta_prev;
+        resid = resid_prev;
+        nin = (int64_t)keep.size();
+        converged = true;
+        from_prev = true;
+        break;
+      }
     }
     // Rayleigh-Ritz on range(X), all Ritz pairs kept
     std::vector<int> sel;
@@ -2025,27 +2057,6 @@ void complete(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
         },
         C, sel);
     const int64_t r = rr.r;
-    // gain of Ritz vector j = Y c_j: the filter's Rayleigh quotient at its preimage X_in c_j,
-    // c_j^T G c_j / c_j^T c_j (rho(lambda) for an eigenvector; rho >= 1/2 on [alpha, beta])
-    std::vector<double> gain;
-    if (gamma_ok) {
-      Buf T;
-      T.alloc((size_t)m * r * sizeof(double));
-      basis_gemm(h, {{G.as<double>(), C.as<double>(), T.as<double>(), (int)m, (int)r, (int)m, (int)m, (int)r, (int)r}},
-                 false, false, 1.0, 0.0);
-      std::vector<double> hc((size_t)m * r), ht((size_t)m * r);
-      RFDD_CUDA(cudaMemcpyAsync(hc.data(), C.p, hc.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-      RFDD_CUDA(cudaMemcpyAsync(ht.data(), T.p, ht.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-      RFDD_CUDA(cudaStreamSynchronize(st));
-      gain.assign(r, 0.0);
-      std::vector<double> nrm(r, 0.0);
-      for (int64_t i = 0; i < m; ++i)
-        for (int64_t j = 0; j < r; ++j) {
-          gain[j] += hc[i * r + j] * ht[i * r + j];
-          nrm[j] += hc[i * r + j] * hc[i * r + j];
-        }
-      for (int64_t j = 0; j < r; ++j) gain[j] = nrm[j] > 0.0 ? gain[j] / nrm[j] : 0.0;
-    }
     Buf Xn;
     Xn.alloc((size_t)n * r * sizeof(double));
     basis_gemm(h, {{X.as<double>(), C.as<double>(), Xn.as<double>(), (int)n, (int)r, (int)m, (int)m,
@@ -2056,28 +2067,26 @@ void complete(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
     X.alloc((size_t)n * r * sizeof(double));
     RFDD_CUDA(cudaMemcpyAsync(X.p, Xn.p, (size_t)n * r * sizeof(double), cudaMemcpyDeviceToDevice, st));
     m = r;
-    gamma_ok = true;
-    // A Ritz value inside [alpha, beta] whose vector the filter damps below 1/4 is spurious: a
-    // mixture of eigenvectors from both sides of the interval with nearly equal, small filter
-    // values (the midpoint filter is symmetric about the centre), whose Rayleigh quotient falls
-    // inside.  It is neither counted nor returned.
     keep.clear();
-    int64_t inside = 0, spurious = 0;
+    int64_t inside = 0, good = 0;
     double mx = 0.0;
     for (int64_t c = 0; c < r; ++c)
       if (theta[c] >= alpha && theta[c] <= beta) {
         ++inside;
-        if (!gain.empty() && gain[c] < 0.25) {
-          ++spurious;
-          continue;
-        }
         keep.push_back(c);
         mx = std::max(mx, resid[c]);
+        good += resid[c] <= h->opt.res_tol;
       }
-    nin = (int64_t)keep.size();
-    RFDD_LOGF("pass %d: m=%lld inside=%lld (spurious %lld, prev %lld) max_res_inside=%.3e ir_steps=%d", passes,
-              (long long)m, (long long)nin, (long long)spurious, (long long)count_prev, mx, irmax);
-    res_level = nin > 0 ? mx : 1.0;
+    nin = inside;
+    RFDD_LOGF("pass %d: m=%lld inside=%lld converged=%lld (prev inside %lld, prev converged %lld) max_res_inside=%.3e "
+              "ir_steps=%d", passes, (long long)m, (long long)inside, (long long)good, (long long)count_prev,
+              (long long)good_prev, mx, irmax);
+    // the residual level the next refinement targets: that of the converged pairs when only
+    // suspects remain above it
+    double mx_good = 0.0;
+    for (int64_t c : keep)
+      if (resid[c] <= h->opt.res_tol) mx_good = std::max(mx_good, resid[c]);
+    res_level = inside > 0 ? mx : 1.0;
     // The block must hold every eigenvalue inside plus guard vectors.  When the Ritz values inside
     // leave fewer than the guard count of columns outside, the interval may hold more eigenvalues
     // than the block (the RF-DDES count it was sized from was short), and subspace iteration
@@ -2101,17 +2110,27 @@ void complete(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
                   (long long)r, (long long)mn);
         m = mn;
         ++grown;
-        pass_limit += 2;  // the grown block gets passes of its own
+        pass_limit = std::min(h->opt.max_passes + 10, pass_limit + 2);  // passes for the grown block
         count_prev = -1;
-        gamma_ok = false;  // the new columns are not Ritz vectors yet
+        good_prev = -1;
+        suspect = false;
         continue;
       }
     }
-    if (nin == count_prev && (nin == 0 || mx <= h->opt.res_tol)) {
+    if (inside == count_prev && (inside == 0 || mx <= h->opt.res_tol)) {
       converged = true;
       break;
     }
-    count_prev = nin;
+    suspect = good > 0 && good < inside && good == good_prev;
+    if (suspect) {
+      theta_prev = theta;
+      resid_prev = resid;
+      res_level = mx_good;
+      // the test needs one more filter application (the passes stay bounded: max_passes + 10)
+      pass_limit = std::min(h->opt.max_passes + 10, std::max(pass_limit, passes + 1));
+    }
+    count_prev = inside;
+    good_prev = good;
   }
   if (passes > pass_limit) passes = pass_limit;
   // results in the original ordering: evecs[i_orig][c] = X[iperm[i_orig]][keep[c]]
@@ -2127,8 +2146,8 @@ void complete(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
   if (nin > 0) {
     Buf keep_dev;
     upload(keep_dev, keep, st);
-    gather_rows_cols_f64(st, X.as<double>(), m, h->iperm_dev.as<int64_t>(), keep_dev.as<int64_t>(),
-                         res->evecs.as<double>(), nin, n, nin);
+    gather_rows_cols_f64(st, (from_prev ? Xprev : X).as<double>(), m, h->iperm_dev.as<int64_t>(),
+                         keep_dev.as<int64_t>(), res->evecs.as<double>(), nin, n, nin);
     RFDD_CUDA(cudaStreamSynchronize(st));
   }
   upload(res->evals_dev, res->evals, st);
