@@ -2081,12 +2081,21 @@ void complete(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
     RFDD_LOGF("pass %d: m=%lld inside=%lld converged=%lld (prev inside %lld, prev converged %lld) max_res_inside=%.3e "
               "ir_steps=%d", passes, (long long)m, (long long)inside, (long long)good, (long long)count_prev,
               (long long)good_prev, mx, irmax);
-    // the residual level the next refinement targets: that of the converged pairs when only
-    // suspects remain above it
+    // the residual level the next refinement targets: the median over the inside pairs (spurious
+    // pairs never converge and would hold the level of the others up), and that of the converged
+    // pairs when only suspects remain above it
     double mx_good = 0.0;
-    for (int64_t c : keep)
+    std::vector<double> rin;
+    for (int64_t c : keep) {
+      rin.push_back(resid[c]);
       if (resid[c] <= h->opt.res_tol) mx_good = std::max(mx_good, resid[c]);
-    res_level = inside > 0 ? mx : 1.0;
+    }
+    if (!rin.empty()) {
+      std::nth_element(rin.begin(), rin.begin() + rin.size() / 2, rin.end());
+      res_level = rin[rin.size() / 2];
+    } else {
+      res_level = 1.0;
+    }
     // The block must hold every eigenvalue inside plus guard vectors.  When the Ritz values inside
     // leave fewer than the guard count of columns outside, the interval may hold more eigenvalues
     // than the block (the RF-DDES count it was sized from was short), and subspace iteration
