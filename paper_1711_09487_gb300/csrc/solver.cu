@@ -1219,7 +1219,7 @@ void dd_solve(rfdd_handle *h, const cx<double> *R, int64_t strideR, cx<double> *
 // Refinement stops once every shifted residual satisfies
 //   ||r|| <= tol * (||A|| + |z| ||M||) ||x||   (tol >= 1e-14), or after ir_max steps.
 template <typename Tf>
-int refined_solve(rfdd_handle *h, const double *V, cx<double> *X, int64_t m, double tol) {
+int refined_solve(rfdd_handle *h, const double *V, cx<double> *X, int64_t m, double tol, bool fp64_residual = false) {
   cudaStream_t st = h->st;
   const int nc = h->nnodes;
   const int64_t n = h->n;
@@ -1235,7 +1235,8 @@ int refined_solve(rfdd_handle *h, const double *V, cx<double> *X, int64_t m, dou
   std::vector<double> hr(nc * m), hx(nc * m);
   int steps = 0;
   Buf Xs;
-  const bool df = std::is_same<Tf, cx<float>>::value;  // mixed solve: double-FP32 residual products
+  // mixed solve: double-FP32 residual products unless the caller needs FP64 ones
+  const bool df = std::is_same<Tf, cx<float>>::value && !fp64_residual;
   if (df) Xs.alloc((size_t)nc * n * m * sizeof(float4));
   for (int it = 0; it <= irmax; ++it) {
     if (df) {
@@ -1984,6 +1985,9 @@ void complete(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
       const double zn = std::hypot(zl.re, zl.im);
       kappa = std::max(kappa, (h->normA + zn * h->normM) / (std::fabs(zl.im) * h->gershM));
     }
+  // The double-FP32 refinement residual is accurate to about 2^-46 of sum |a||x|; when kappa times
+  // that exceeds 1/100 of the residual target, the residual is formed with FP64 products.
+  const bool fp64_res = kappa * 0x1p-46 > 1e-2 * h->opt.res_tol;
   Buf V, Xc, C, Xprev;
   std::vector<double> theta, resid, theta_prev, resid_prev;
   std::vector<int64_t> keep;  // Ritz pairs returned: inside [alpha, beta], converged, not spurious
@@ -2014,7 +2018,7 @@ void complete(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
     double ir_tol = 1e-6 * res_level;
     if (kappa > 0.0) ir_tol = std::min(ir_tol, 1e-2 * res_level / kappa);
     ir_tol = std::max(std::max(1e-15, 1e-2 * h->opt.res_tol / std::max(1.0, kappa)), ir_tol);
-    irmax = std::max(irmax, refined_solve<Tf>(h, V.as<double>(), Xc.as<cx<double>>(), m, ir_tol));
+    irmax = std::max(irmax, refined_solve<Tf>(h, V.as<double>(), Xc.as<cx<double>>(), m, ir_tol, fp64_res));
     weighted_real_sum<cx<double>>(st, Xc.as<cx<double>>(), n * m, h->w_dev.as<cx<double>>(), nc, 2.0, X.as<double>(),
                                   n * m);
     if (suspect) {
