@@ -1017,7 +1017,13 @@ static void tc_gemm_run(cudaStream_t st, const std::vector<GemmItem<T>> &items, 
       ghosts += (long long)(tb.it[i].mtc & 1) * tb.it[i].ntc;
     }
     const TcDevInfo dinfo = tc_device_info();
-    bool two = splits == 3 && dinfo.clusters2 > 0 && pairs >= dinfo.clusters2 && 8 * ghosts <= pairs;
+    // measured on 8192 x 8192 products: the two-CTA kernel gains from K = 256 (complex) on (4 %
+    // there, 1.5 % at K = 1024) and loses at K = 128, where the epilogue, not the operand feed,
+    // bounds both kernels
+    int nkt_min = 1 << 30;
+    for (int i = 0; i < cnt; ++i) nkt_min = std::min(nkt_min, tb.it[i].nkt);
+    bool two = splits == 3 && dinfo.clusters2 > 0 && pairs >= dinfo.clusters2 && 8 * ghosts <= pairs &&
+               (CPLX ? nkt_min >= 16 : nkt_min >= 8);
     if (g_tc_engine_override == 1) two = false;
     if (g_tc_engine_override == 2) two = splits == 3 && dinfo.clusters2 > 0;
     if (g_tc_events) RFDD_CUDA(cudaEventRecord(g_tc_events[0], st));
