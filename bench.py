@@ -361,6 +361,11 @@ def run_ours(args, rank, world, local_rank):
     fp64 = None
     if args.fp64_plain == "on" or (args.fp64_plain == "auto" and world == 1 and precision == R.RFDD_MIXED):
         fp64 = run_fp64_plain(R, w, stream, ev_ref=r_last_evals)
+    # the serving pattern on a short stream (the full 256-request stream: --mode serve)
+    serving = None
+    if args.serve_requests > 0 and world == 1:
+        serving = serve_stream(R, args.serve_requests, args.load, args.inflight, min(4, args.capacity_sample))
+        serving.pop("metric", None)
     if rank != 0:
         return
     peaks, src = measured_peaks()
@@ -431,6 +436,8 @@ def run_ours(args, rank, world, local_rank):
     if fp64 is not None:
         line["fp64_plain"] = fp64
         line["mixed_over_fp64"] = value / fp64["value"] if fp64["value"] > 0 else None
+    if serving is not None:
+        line["serving"] = serving
     print(json.dumps(line), flush=True)
 
 
@@ -489,17 +496,22 @@ def run_dgemm(args):
 
 
 def run_serve(args):
-    """The serving pattern: a seeded Poisson stream of requests of mixed size and kind (2-D Q1 and
-    3-D variable-coefficient pencils, 20..400 eigenvalues each, p in {4, 8, 16}, 8 nodes), each
-    bringing its pencil, served by the library's continuous-batching server under a 150 GiB memory
-    budget.  The arrival rate is `--load` times the single-stream capacity, measured first on the
-    stream's first requests run one at a time.  Reports eigenpairs/s (residual <= 1e-10) over the
-    stream and the p50/p99 latency from arrival to result."""
+    """The serving pattern on its own (bench.py --mode serve): prints the serve_stream() line."""
     import torch
     import paper_1711_09487_gb300 as R
     torch.cuda.set_device(0)
     R.load()
-    reqs = I.serving_stream(args.requests, seed=7)
+    print(json.dumps(serve_stream(R, args.requests, args.load, args.inflight, args.capacity_sample)), flush=True)
+
+
+def serve_stream(R, requests, load, inflight, capacity_sample):
+    """The serving pattern: a seeded Poisson stream of requests of mixed size and kind (2-D Q1 and
+    3-D variable-coefficient pencils, 20..400 eigenvalues each, p in {4, 8, 16}, 8 nodes), each
+    bringing its pencil, served by the library's continuous-batching server under a 150 GiB memory
+    budget.  The arrival rate is `load` times the single-stream capacity, measured first on the
+    stream's first requests run one at a time.  Returns eigenpairs/s (residual <= 1e-10) over the
+    stream and the p50/p99 latency from arrival to result."""
+    reqs = I.serving_stream(requests, seed=7)
     pencils = [I.serving_pencil(q) for q in reqs]          # built before any clock starts
     opts = R.rfdd_default_options(precision=R.RFDD_MIXED)
     budget = 150 << 30
@@ -509,7 +521,7 @@ def run_serve(args):
         return srv.submit_pencil(A, M, part, p, q["alpha"], q["beta"], q["n_nodes"], nev_hint=q["nev"], opts=opts)
 
     # single-stream capacity: the first requests one at a time (after one warm-up request)
-    k = min(args.capacity_sample, len(reqs))
+    k = min(capacity_sample, len(reqs))
     srv1 = R.Server(max_inflight=1, mem_budget=budget)
     r = srv1.wait(submit(srv1, reqs[0], pencils[0]))
     del r
@@ -521,11 +533,11 @@ def run_serve(args):
         del r
     srv1.close()
     capacity = 1000.0 / statistics.mean(run_ms)            # requests per second, one at a time
-    rate = args.load * capacity
+    rate = load * capacity
     gaps = np.random.default_rng(7).exponential(1.0 / rate, len(reqs))
     arrival = np.cumsum(gaps) - gaps[0]
 
-    srv = R.Server(max_inflight=args.inflight, mem_budget=budget)
+    srv = R.Server(max_inflight=inflight, mem_budget=budget)
     ids, t_sub = [None] * len(reqs), [0.0] * len(reqs)
     t0 = time.perf_counter()
     for i, (q, pc) in enumerate(zip(reqs, pencils)):
@@ -566,14 +578,14 @@ def run_serve(args):
                 "p50": lat_s[len(lat_s) // 2],
                 "p99": lat_s[min(len(lat_s) - 1, int(math.ceil(0.99 * len(lat_s))) - 1)],
                 "max": lat_s[-1]},
-            "arrival_rate_per_s": rate, "load": args.load, "single_stream_capacity_per_s": capacity,
-            "capacity_sample_requests": k, "max_inflight": args.inflight, "mem_budget_bytes": budget,
+            "arrival_rate_per_s": rate, "load": load, "single_stream_capacity_per_s": capacity,
+            "capacity_sample_requests": k, "max_inflight": inflight, "mem_budget_bytes": budget,
             "requests_with_wrong_count": wrong_count, "wrong_count_sample": wrong, "statuses": statuses,
             "per_kind": per_kind, "server": st,
             "config": {"workload": "serving stream: seeded Poisson arrivals, 50% 2D Q1 N in 64..256, 50% 3D "
                                    "variable-kappa 7-point N in 24..48, 20..400 eigenvalues, p in {4,8,16}, 8 nodes",
                        "seed": 7, "precision": "mixed"}}
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def main():
@@ -583,6 +595,8 @@ def main():
     ap.add_argument("--load", type=float, default=0.7, help="serve mode: arrival rate / single-stream capacity")
     ap.add_argument("--inflight", type=int, default=4, help="serve mode: requests running at once")
     ap.add_argument("--capacity-sample", type=int, default=8, help="serve mode: requests timed one at a time")
+    ap.add_argument("--serve-requests", type=int, default=24,
+                    help="bench mode: requests of a short serving stream reported beside the solve line (0: none)")
     ap.add_argument("--gemm", type=int, nargs=3, default=[8192, 8192, 128], metavar=("M", "N", "K"))
     ap.add_argument("--engine", type=int, default=1, choices=[1, 2, 3],
                     help="gemm mode: 1 automatic kernel choice, 2 one-CTA kernel, 3 two-CTA kernel")
