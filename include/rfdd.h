@@ -127,6 +127,10 @@ typedef struct {
                            an eigenvalue of some (B_j, M_B^(j)): FP64 tau = 1e-8, move
                            1e-6 (beta - alpha); mixed (FP32 factors) tau = 1e-5, move
                            max(1e-3 (beta - alpha), 2 tau max(1, |sigma|)) */
+  double t_factor_enqueue_ms; /* host wall time to issue the a2-a5 launches (they run
+                                 asynchronously: the host limits the phase only if this
+                                 approaches t_factor_ms) */
+  int64_t factor_launches;    /* kernels launched for a2-a5 */
 } rfdd_info;
 
 /* Fill *opt with the defaults listed above. */
@@ -305,6 +309,24 @@ int rfdd_cgemm(int64_t m, int64_t n, int64_t k, const float *A, int64_t lda, con
 int rfdd_dgemm(int64_t m, int64_t n, int64_t k, int32_t ta, const double *A, int64_t lda, int32_t tb,
                const double *B, int64_t ldb, double *C, int64_t ldc, double alpha, double beta,
                int32_t engine, int32_t sym);
+
+/* Tile-shape autotuner of the tensor-core GEMMs (no counterpart in the paper).  Where both the
+ * one-CTA kernel (128 x 256 output tiles) and the two-CTA kernel (256 x 256 tiles per SM pair)
+ * can run a launch, the library times both on real launches of the same class -- device,
+ * complex or real, the K depth bucket floor(log2(K/32 tiles)) and the launch's tile count against
+ * the SM count; never what else runs -- three timings each, with CUDA events on the launch's
+ * stream and without blocking, then keeps the faster for every later launch of that class in this
+ * process.  Until a class is decided, and whenever tuning is off, a fixed rule chooses (the
+ * two-CTA kernel from complex K = 256 on).  Launches inside a stream capture are never timed;
+ * they take a decided class's choice, else the rule.
+ * rfdd_autotune: mode 0 turns tuning off, 1 on (the default), 2 forgets every class.  Returns 1
+ * if tuning was on before the call, 0 if off, -RFDD_EINVAL for another mode.
+ * rfdd_autotune_table: writes the table as text, one line per class, "device complex splits
+ * kbucket tbucket winner n0 ms_per_gflop0 n1 ms_per_gflop1" (winner -1 while undecided;
+ * candidate 0 = one-CTA, 1 = two-CTA), NUL-terminated and truncated to cap bytes; *len = its
+ * full length.  Pass cap = 0 to query the length. */
+int rfdd_autotune(int32_t mode);
+int rfdd_autotune_table(char *buf, int64_t cap, int64_t *len);
 
 /* Allocation-free variant of rfdd_cgemm (no counterpart in the paper).  For callers that cannot
  * allocate device memory -- a process whose device memory is capped or owned by another

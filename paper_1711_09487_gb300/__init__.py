@@ -44,7 +44,7 @@ SYMBOLS = [
     "rfdd_polish", "rfdd_peak_probe", "rfdd_profile_bytes", "rfdd_release",
     "rfdd_server_default_options", "rfdd_server_create", "rfdd_server_add_pencil", "rfdd_server_submit",
     "rfdd_server_wait", "rfdd_server_submit_pencil", "rfdd_server_request_info", "rfdd_server_get_stats", "rfdd_server_remove_pencil",
-    "rfdd_server_destroy",
+    "rfdd_server_destroy", "rfdd_autotune", "rfdd_autotune_table",
 ]
 
 
@@ -74,7 +74,8 @@ class rfdd_info(C.Structure):
                 ("pre_max_resid", C.c_double), ("pre_nev", C.c_int64), ("t_factor_ms", C.c_double),
                 ("t_lanczos_ms", C.c_double), ("t_interior_ms", C.c_double), ("t_rr_ms", C.c_double),
                 ("t_complete_ms", C.c_double), ("t_total_ms", C.c_double), ("status", C.c_int32),
-                ("packed", C.c_int32), ("sigma", C.c_double)]
+                ("packed", C.c_int32), ("sigma", C.c_double), ("t_factor_enqueue_ms", C.c_double),
+                ("factor_launches", C.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -156,6 +157,8 @@ def load(path: str | None = None):
     lib.rfdd_peak_probe.argtypes = [i32, dp]
     lib.rfdd_profile_bytes.argtypes = [i32, dp]
     lib.rfdd_release.argtypes = [vp]
+    lib.rfdd_autotune.argtypes = [i32]
+    lib.rfdd_autotune_table.argtypes = [C.c_char_p, i64, C.POINTER(i64)]
     lib.rfdd_server_default_options.argtypes = [vp]
     lib.rfdd_server_default_options.restype = None
     lib.rfdd_server_create.argtypes = [vp, C.POINTER(vp)]
@@ -481,11 +484,37 @@ def rfdd_cgemm_noalloc(m: int, n: int, k: int, A_ptr: int, lda: int, B_ptr: int,
 
 
 def rfdd_peak_probe(which: int) -> float:
-    """TFLOP/s of one arithmetic unit on the current device: 0 plain TF32 tensor GEMM, 1 FP64
-    FMA, 2 FP32 FMA (CUDA cores)."""
+    """TFLOP/s of one arithmetic unit on the current device: 0 the tensor pipe's TF32 MMA rate,
+    1 FP64 FMA, 2 FP32 FMA (CUDA cores), 3 a plain TF32 8192^3 GEMM through the tensor-core kernel."""
     t = C.c_double()
     _check(load().rfdd_peak_probe(int(which), C.byref(t)))
     return float(t.value)
+
+
+def rfdd_autotune(mode: int) -> int:
+    """Tile-shape autotuner: 0 off (fixed rule), 1 on, 2 forget every class.  Returns whether it
+    was on."""
+    r = load().rfdd_autotune(int(mode))
+    if r < 0:
+        _check(-r)
+    return r
+
+
+def rfdd_autotune_table() -> list[dict]:
+    """The autotuner's classes: key, winner (-1 undecided; 0 one-CTA, 1 two-CTA) and the mean
+    milliseconds per GFLOP each candidate measured."""
+    lib = load()
+    n = C.c_int64()
+    _check(lib.rfdd_autotune_table(None, 0, C.byref(n)))
+    buf = C.create_string_buffer(n.value + 1)
+    _check(lib.rfdd_autotune_table(buf, n.value + 1, C.byref(n)))
+    out = []
+    for line in buf.value.decode().splitlines():
+        f = line.split()
+        out.append({"device": int(f[0]), "complex": int(f[1]), "splits": int(f[2]), "kbucket": int(f[3]),
+                    "tbucket": int(f[4]), "winner": int(f[5]), "n": [int(f[6]), int(f[8])],
+                    "ms_per_gflop": [float(f[7]), float(f[9])]})
+    return out
 
 
 def rfdd_profile_bytes(kind: int) -> float:

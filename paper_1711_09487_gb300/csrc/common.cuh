@@ -34,9 +34,12 @@ struct Error : public std::runtime_error {
 
 // Every kernel launch of the library goes through RFDD_CHECK_LAUNCH, which also counts it.
 extern std::atomic<long long> g_kernel_launches;
+// launches issued by the calling host thread (phases that run on two threads count their own)
+extern thread_local long long g_thread_launches;
 #define RFDD_CHECK_LAUNCH()                                           \
   do {                                                                \
     ::rfdd::g_kernel_launches.fetch_add(1, std::memory_order_relaxed); \
+    ++::rfdd::g_thread_launches;                                      \
     RFDD_CUDA(cudaGetLastError());                                    \
   } while (0)
 

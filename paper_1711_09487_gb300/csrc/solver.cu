@@ -32,6 +32,7 @@ using namespace rfdd;
 
 namespace rfdd {
 std::atomic<long long> g_kernel_launches{0};
+thread_local long long g_thread_launches = 0;
 namespace {
 std::mutex g_prof_mu;
 std::atomic<bool> g_prof_on{false};  // read by every launching host thread
@@ -281,6 +282,8 @@ struct rfdd_handle {
   std::exception_ptr I_exc;   // its error, rethrown by interior_join
   std::vector<int64_t> boff, pivBoff;
   bool have_factors = false;
+  double factor_enqueue_ms = 0.0;  // host time to issue the last factorisation's launches
+  long long factor_launches = 0;   // kernels it launched
   double alpha = 0, beta = 0;
   bool have_interval = false;
   // Lanczos (a7)
@@ -815,6 +818,8 @@ void pack_factor_operands(rfdd_handle *h);
 
 template <typename Tf>
 void factor_impl(rfdd_handle *h) {
+  const auto host0 = std::chrono::steady_clock::now();
+  const long long launches0 = g_thread_launches;
   cudaStream_t st = h->st;
   const int nc = h->nnodes, p = h->p;
   const int64_t s = h->s;
@@ -932,6 +937,11 @@ void factor_impl(rfdd_handle *h) {
       h->Sfac.release();
     }
   }
+  // how long the host took to issue the phase, against its device time (t_factor_ms): the
+  // launches are asynchronous, so the host only limits the phase if it takes as long
+  h->factor_enqueue_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - host0).count();
+  h->factor_launches = g_thread_launches - launches0;
   sync_status(h, "factor");
   h->have_factors = true;
 }
@@ -2439,6 +2449,8 @@ void run_solve(rfdd_handle *h, double alpha, double beta, int nc, rfdd_result *r
     Timer t(h->st);
     factor(h);
     res->info.t_factor_ms = t.ms();
+    res->info.t_factor_enqueue_ms = h->factor_enqueue_ms;
+    res->info.factor_launches = h->factor_launches;
     res->info.packed = h->pkB.empty() ? 0 : 1;
   }
   {
@@ -3051,6 +3063,24 @@ int rfdd_dgemm(int64_t m, int64_t n, int64_t k, int32_t ta, const double *A, int
     else gemm_simt_batched<double>(st, it, ta != 0, tb != 0, alpha, beta, {(char)(sym != 0)});
     RFDD_CUDA(cudaStreamSynchronize(st));
     RFDD_CUDA(cudaMemcpy(C, c.p, ncm * sizeof(double), cudaMemcpyDeviceToHost));
+  });
+}
+
+int rfdd_autotune(int32_t mode) {
+  if (mode < 0 || mode > 2) return -RFDD_EINVAL;
+  return tc_autotune(mode);
+}
+
+int rfdd_autotune_table(char *buf, int64_t cap, int64_t *len) {
+  if (!len || cap < 0 || (cap > 0 && !buf)) return RFDD_EINVAL;
+  return guarded([&] {
+    const std::string t = tc_autotune_table();
+    *len = (int64_t)t.size();
+    if (cap > 0) {
+      const size_t c = std::min<size_t>((size_t)cap - 1, t.size());
+      memcpy(buf, t.data(), c);
+      buf[c] = 0;
+    }
   });
 }
 

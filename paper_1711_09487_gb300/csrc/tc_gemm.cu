@@ -19,6 +19,7 @@
 // accumulators so that draining tile i overlaps the MMAs of tile i+1.
 #include "dense.cuh"
 #include "tc_gemm.cuh"
+#include "tc_tune.h"
 
 #include <algorithm>
 #include <atomic>
@@ -921,6 +922,59 @@ thread_local int g_tc_engine_override = 0;  // 0 automatic, 1 one-CTA kernel, 2 
 TcEngineScope::TcEngineScope(int e) : prev(g_tc_engine_override) { g_tc_engine_override = e; }
 TcEngineScope::~TcEngineScope() { g_tc_engine_override = prev; }
 
+// The tile-shape autotuner (tc_tune.h) and the timings it is waiting for.  Launches it asks to
+// measure are bracketed by events on their own stream; the events are polled without blocking at
+// the next launch and when the table is read.
+namespace {
+struct TunePending {
+  tune::Key key;
+  int cand;
+  double gflop;
+  cudaEvent_t e0, e1;
+};
+std::mutex g_tune_mu;
+tune::Tuner g_tuner;
+std::vector<TunePending> g_tune_pending;
+
+void tune_poll_locked() {
+  for (size_t i = 0; i < g_tune_pending.size();) {
+    TunePending &q = g_tune_pending[i];
+    const cudaError_t r = cudaEventQuery(q.e1);
+    if (r == cudaErrorNotReady) {
+      ++i;
+      continue;
+    }
+    float ms = 0.0f;
+    if (r == cudaSuccess && cudaEventElapsedTime(&ms, q.e0, q.e1) == cudaSuccess && q.gflop > 0.0)
+      g_tuner.record(q.key, q.cand, ms / q.gflop);
+    else
+      g_tuner.forget(q.key, q.cand);
+    if (r != cudaSuccess) cudaGetLastError();
+    cudaEventDestroy(q.e0);
+    cudaEventDestroy(q.e1);
+    g_tune_pending.erase(g_tune_pending.begin() + i);
+  }
+}
+}  // namespace
+
+int tc_autotune(int mode) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  const int prev = g_tuner.enabled ? 1 : 0;
+  if (mode == 2) {
+    tune_poll_locked();
+    g_tuner.clear();
+  } else {
+    g_tuner.enabled = mode != 0;
+  }
+  return prev;
+}
+
+std::string tc_autotune_table() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  tune_poll_locked();
+  return g_tuner.dump();
+}
+
 // Tile walk of one item: down the columns when B spans at least 8 tile columns and the item's
 // packed A (hi + lo) takes at most 48 MB of the 129 MB L2, else along the rows.
 int tc_tile_order(int mtc, int ntc, int nkt) {
@@ -1022,10 +1076,45 @@ static void tc_gemm_run(cudaStream_t st, const std::vector<GemmItem<T>> &items, 
     // bounds both kernels
     int nkt_min = 1 << 30;
     for (int i = 0; i < cnt; ++i) nkt_min = std::min(nkt_min, tb.it[i].nkt);
-    bool two = splits == 3 && dinfo.clusters2 > 0 && pairs >= dinfo.clusters2 && 8 * ghosts <= pairs &&
-               (CPLX ? nkt_min >= 16 : nkt_min >= 8);
+    const bool two_ok = splits == 3 && dinfo.clusters2 > 0 && pairs >= dinfo.clusters2 && 8 * ghosts <= pairs;
+    bool two = two_ok && (CPLX ? nkt_min >= 16 : nkt_min >= 8);
+    // the autotuner decides where both kernels can run, outside stream capture
+    tune::Key tkey;
+    bool tmeasure = false;
+    if (two_ok && g_tc_engine_override == 0) {
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      RFDD_CUDA(cudaStreamIsCapturing(st, &cs));
+      RFDD_CUDA(cudaGetDevice(&tkey.device));
+      tkey.cplx = CPLX ? 1 : 0;
+      tkey.splits = splits;
+      tkey.kbucket = tune::k_bucket(nkt_min);
+      tkey.tbucket = tune::t_bucket(tiles, nsm);
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      tune_poll_locked();
+      if (cs == cudaStreamCaptureStatusNone) {
+        const tune::Choice ch = g_tuner.choose(tkey, two ? 1 : 0);
+        two = ch.cand == 1;
+        tmeasure = ch.measure;
+      } else {
+        const auto &t = g_tuner.table();
+        const auto it = t.find(tkey);
+        if (it != t.end() && it->second.winner >= 0) two = it->second.winner == 1;
+      }
+    }
     if (g_tc_engine_override == 1) two = false;
     if (g_tc_engine_override == 2) two = splits == 3 && dinfo.clusters2 > 0;
+    cudaEvent_t te0 = nullptr, te1 = nullptr;
+    if (tmeasure) {
+      if (cudaEventCreate(&te0) != cudaSuccess || cudaEventCreate(&te1) != cudaSuccess) {
+        cudaGetLastError();
+        if (te0) cudaEventDestroy(te0);
+        te0 = te1 = nullptr;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuner.forget(tkey, two ? 1 : 0);
+      } else {
+        RFDD_CUDA(cudaEventRecord(te0, st));
+      }
+    }
     if (g_tc_events) RFDD_CUDA(cudaEventRecord(g_tc_events[0], st));
     if (two) {
       TcBatchP t2 = tb;
@@ -1056,6 +1145,11 @@ static void tc_gemm_run(cudaStream_t st, const std::vector<GemmItem<T>> &items, 
       RFDD_CHECK_LAUNCH();
     }
     if (g_tc_events) RFDD_CUDA(cudaEventRecord(g_tc_events[1], st));
+    if (te1) {
+      RFDD_CUDA(cudaEventRecord(te1, st));
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tune_pending.push_back({tkey, two ? 1 : 0, flops * 1e-9, te0, te1});
+    }
     if (e0) {
       cudaEventRecord(e1, st);
       profile_push(e0, e1, flops, 1, cbytes);

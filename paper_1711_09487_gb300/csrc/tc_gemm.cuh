@@ -2,6 +2,8 @@
 #pragma once
 #include "dense.cuh"
 
+#include <string>
+
 namespace rfdd {
 // Status word (device int) that the tensor-core launches issued by the calling host thread record
 // a failed wait in (DS_WAIT_TIMEOUT), for the lifetime of the scope.  A launch outside any scope is
@@ -39,6 +41,11 @@ void tc_gemm_real(cudaStream_t st, const std::vector<GemmItem<float>> &items, do
 // the same with one TF32 product per multiply (operands rounded to TF32): the throughput probe of
 // the plain TF32 tensor path, not used by the solver
 void tc_gemm_real_tf32(cudaStream_t st, const std::vector<GemmItem<float>> &items, double alpha, double beta);
+
+// The tile-shape autotuner: mode 0 off (fixed rule), 1 on, 2 forget every class (re-tune);
+// returns whether it was on.  tc_autotune_table: one line per class (tc_tune.h, Tuner::dump).
+int tc_autotune(int mode);
+std::string tc_autotune_table();
 // A operand already split into TF32 hi/lo and laid out in the kernel's tiles (tc_pack_a_batched):
 // tile (mt, kt) of the operand at hi/lo + (mt * mt_stride + kt) * tile size.  Lets a factor that
 // is multiplied many times (triangular-solve updates, border products) be packed once.
