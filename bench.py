@@ -432,6 +432,10 @@ def run_ours(args, rank, world, local_rank):
         "cpu_baseline": {"value": cpu_value, "unit": UNIT, "cores": cpu_threads, "kind": "oracle",
                          "sample": cpu_desc, "model_check": model_check},
         "probes": probes,
+        # the tile-shape autotuner's classes after the run: complex/real, K-depth and size buckets,
+        # the kept kernel (0 one-CTA, 1 two-CTA) and each kernel's mean ms per GFLOP
+        "autotune": [[e["complex"], e["kbucket"], e["tbucket"], e["winner"]] + e["ms_per_gflop"]
+                     for e in R.rfdd_autotune_table()],
         "clocks": clk,
     }
     if fp64 is not None:

@@ -16,6 +16,11 @@ Laplacians, ``M = I`` or a mass matrix) and the synthetic workloads named for th
 * ``varkappa7_pencil(N, seed)``: 3-D 7-point diffusion with a per-edge coefficient
   kappa_e = exp(g_e), g_e ~ N(0, 1) i.i.d., boundary edges included, and a diagonal lumped mass
   with entries uniform in [0.5, 1.5].
+* ``fd5_pencil(N)``: the 2-D 5-point finite-difference Laplacian stencil (4 on the diagonal,
+  -1 to each grid neighbour, Dirichlet boundary, no 1/h^2 scaling) on an N x N grid with M = I,
+  the pencils the paper's distributed comparison calls FDmesh (FDmesh2: N = 500,
+  n = 250,000; FDmesh3: N = 1000).  Eigenvalues 4 - 2 cos(a pi/(N+1)) - 2 cos(b pi/(N+1))
+  (``fd5_eigenvalues``).
 * ``geometric_partition``: axis-aligned vertex separators (planes of width one node) that split
   the grid into a product of blocks; label -1 marks the interface (the ordering of Eq. dd1 puts
   those variables last).
@@ -35,7 +40,7 @@ __all__ = [
     "Csr", "Pencil", "q1_1d", "q1_pencil", "q1_eigenvalues", "varkappa7_pencil",
     "separator_planes", "geometric_partition", "interval_from_sorted", "workload",
     "WORKLOADS", "random_rhs", "snap_to_gaps", "sym_inertia_count", "VARKAPPA_POOL", "serving_stream",
-    "serving_pencil",
+    "serving_pencil", "fd5_pencil", "fd5_eigenvalues",
 ]
 
 
@@ -122,6 +127,25 @@ def q1_eigenvalues(N: int, dim: int) -> np.ndarray:
     else:
         ev = lam[:, None, None] + lam[None, :, None] + lam[None, None, :]
     return np.sort(ev.ravel())
+
+
+# ----------------------------------------------------------------------------------------
+# 5-point finite-difference Laplacian with M = I (the FDmesh pencils)
+# ----------------------------------------------------------------------------------------
+
+def fd5_pencil(N: int) -> tuple[Csr, Csr]:
+    """tridiag(-1, 2, -1) Kronecker-summed over two axes (row-major grid), and M = I."""
+    e = np.ones(N)
+    T = sp.diags([-e[:-1], 2 * e, -e[:-1]], [-1, 0, 1])
+    I1 = sp.identity(N)
+    A = sp.kron(T, I1) + sp.kron(I1, T)
+    return Csr.from_scipy(A), Csr.from_scipy(sp.identity(N * N))
+
+
+def fd5_eigenvalues(N: int) -> np.ndarray:
+    """Sorted closed-form eigenvalues of ``fd5_pencil(N)``."""
+    lam = 2.0 - 2.0 * np.cos(np.arange(1, N + 1) * np.pi / (N + 1))
+    return np.sort((lam[:, None] + lam[None, :]).ravel())
 
 
 # ----------------------------------------------------------------------------------------
@@ -279,6 +303,19 @@ def _q1_workload(name, N, dim, splits, first, last, n_nodes, rule):
                   grid=(N,) * dim, meta=dict(first=first, last=last, splits=splits))
 
 
+def _fd5_workload(name, N, splits, first, last, n_nodes, rule):
+    A, M = fd5_pencil(N)
+    part, p = geometric_partition(N, 2, splits)
+    ev = fd5_eigenvalues(N)
+    first, last = snap_to_gaps(ev, first, last)
+    alpha, beta = interval_from_sorted(ev, first, last)
+    if first == 1:
+        alpha = 0.0   # the smallest eigenvalues: [0, beta], as the paper's FDmesh windows
+    nev = int(np.count_nonzero((ev > alpha) & (ev < beta)))
+    return Pencil(name, A, M, part, p, alpha, beta, n_nodes, rule, ev, nev,
+                  grid=(N, N), meta=dict(first=first, last=last, splits=splits))
+
+
 def workload(name: str) -> Pencil:
     """Build one named seeded workload (see ``WORKLOADS``)."""
     if name not in WORKLOADS:
@@ -299,6 +336,14 @@ WORKLOADS = {
     "q1_3d_12": lambda: _q1_workload("q1_3d_12", 12, 3, (2, 2, 2), 8, 27, 6, "midpoint"),
     "q1_3d_16": lambda: _q1_workload("q1_3d_16", 16, 3, (2, 2, 2), 20, 60, 8, "midpoint"),
     "q1_2d_64": lambda: _q1_workload("q1_2d_64", 64, 2, (2, 2), 40, 120, 8, "midpoint"),
+    # FDmesh2 of the paper's RF-KRYLOV / RF-DDES comparison: 5-point FD Laplacian, M = I, 500^2
+    # grid (n = 250,000), the 100 algebraically smallest eigenvalues, Nc = 2 midpoint nodes; an
+    # 8 x 8 separator grid (64 subdomains of about 62^2, s = 6,951) so that the dense
+    # subdomain blocks stay small.
+    "fdmesh2": lambda: _fd5_workload("fdmesh2", 500, (8, 8), 1, 100, 2, "midpoint"),
+    # small FD cases for parity tests
+    "fd5_32": lambda: _fd5_workload("fd5_32", 32, (2, 2), 1, 20, 4, "midpoint"),
+    "fd5_40_p16": lambda: _fd5_workload("fd5_40_p16", 40, (4, 4), 1, 30, 2, "midpoint"),
 }
 
 
