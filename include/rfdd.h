@@ -375,6 +375,23 @@ int rfdd_profile_busy(int32_t kind, double *busy_ms);
  * captured launch, it gives the DRAM traffic of launches too large to capture. */
 int rfdd_profile_bytes(int32_t kind, double *bytes);
 
+/* RF-KRYLOV, Algorithm 1 (Section 2.2): the paper's comparison method, on the same factors.
+ * Computes the quadrature (n_nodes, opt.quad_rule), factors every B_j(zeta_l) and S(zeta_l) as
+ * rfdd_solve does, then runs Krylov on rho(M^{-1}A) in the whole space: each step applies
+ * w = 2 Re sum_l omega_l (A - zeta_l M)^{-1} M q (line 2) to a block of opt.block vectors through
+ * Eq. (inv_dd2) with FP64 refinement, orthogonalises in the M inner product (rho(M^{-1}A) is
+ * self-adjoint there, so H_mu is symmetric; with M = I it is the printed Euclidean process), and
+ * every ceil(10/opt.block) steps stops when the sum of the eigenvalues of H_mu that are >= 1/2
+ * changed by at most opt.lanczos_tol of its magnitude (line 13), or when mu reaches max_dim
+ * (0 = min(n, 4096)).  Lines 15-16: Rayleigh-Ritz of (A, M) on the Krylov basis, then the
+ * completion passes of rfdd_solve to the residual target.  The result is read like rfdd_solve's;
+ * info.mu is the Krylov dimension, info.k the Rayleigh-Ritz rank, info.t_lanczos_ms the Krylov
+ * phase, rfdd_result_pre_evals the Ritz values inside [alpha, beta] before completion.  Device
+ * memory beyond the factors: n x min(max_dim, n) doubles for the basis and about
+ * (3 + 2 n_nodes) n x block doubles of workspace.  Errors as rfdd_solve; RFDD_EINVAL also for
+ * max_dim < 0 or 0 < max_dim < opt.block. */
+int rfdd_rfkrylov(rfdd_handle *h, double alpha, double beta, int32_t n_nodes, int64_t max_dim, rfdd_result **out);
+
 /* Asynchronous solve for serving: enqueues the solve on `stream` (a cudaStream_t, NULL = the
  * handle's) and returns; rfdd_result_ready() reports completion (1 done, 0 running, <0 error
  * code negated).  The handle must not be used until the result is ready. */

@@ -616,6 +616,133 @@ def rfdd_solve(A, M, part, p, alpha, beta, n_nodes=4, rule="midpoint", sigma=Non
                 z=z, w=w, sigma=sigma, lanczos=lz)
 
 
+# ----------------------------------------------------------------------------------------
+# Algorithm 1 (RF-KRYLOV): Krylov on rho(M^{-1} A) in the whole space, Section 2.2
+# ----------------------------------------------------------------------------------------
+
+def _m_orth_against(Mp, Qs, W, passes=2):
+    """W minus its M-projection onto the columns of the blocks in Qs (classical Gram-Schmidt,
+    repeated ``passes`` times); also returns the accumulated coefficients Q^T M W per block."""
+    coef = [np.zeros((Qk.shape[1], W.shape[1])) for Qk in Qs]
+    for _ in range(passes):
+        MW = Mp @ W
+        for i, Qk in enumerate(Qs):
+            c = Qk.T @ MW
+            W = W - Qk @ c
+            coef[i] += c
+    return W, coef
+
+
+def _m_cholqr(Mp, W):
+    """W = Q R with Q^T M Q = I, R upper triangular (Cholesky of the Gram matrix W^T M W)."""
+    G = W.T @ (Mp @ W)
+    R = np.linalg.cholesky(0.5 * (G + G.T)).T
+    return sla.solve_triangular(R, W.T, trans="T", lower=False).T, R
+
+
+def rf_krylov(Ap, Mp, apply_rho, alpha, beta, tol=1e-6, block=1, seed=1, check_every=10, max_dim=None):
+    """Algorithm 1 (RF-KRYLOV) on rho(M^{-1}A), with ``apply_rho(Q)`` = 2 Re sum_l omega_l
+    (A - zeta_l M)^{-1} M Q (line 2).  Returns dict(Q (n x mu), H (mu x mu), mu, sums, theta,
+    X, inside): the Krylov basis, the projected matrix, the sums that line 13 compares, and the
+    Ritz pairs of (A, M) from lines 15-16 (X M-orthonormal, theta ascending; ``inside`` marks
+    theta in [alpha, beta]).
+
+    Readings:
+    * the inner product is M's.  rho(M^{-1}A) is self-adjoint in it, so H_mu = Q^T M rho Q is
+      symmetric and the Arnoldi process of lines 3-12 is a Lanczos process with full
+      orthogonalisation; with M = I (the paper's RF-KRYLOV experiments) it is the printed
+      Euclidean one.
+    * q^(1): ``block`` counter-based uniform vectors (stream 7000), M-orthonormalised; b = 1 is
+      the printed algorithm.
+    * lines 3-6 are run twice (CGS2); h_{k,mu} accumulates both passes.
+    * lines 7-12: the columns of the new block are M-normalised one after another, each first
+      projected (twice) off Q and the block's earlier columns; a column whose M norm is then at
+      most 1e-14 max|H| (breakdown, h_{mu+1,mu} = 0) is replaced by fresh counter-based vectors
+      (streams 7001, ...) projected the same way.
+    * line 13: every ceil(check_every / b) block steps, stop when the sum of the eigenvalues of
+      (the symmetric part of) H_mu that are >= 1/2 changed by at most tol times its magnitude
+      since the previous check; also stop when mu reaches n or ``max_dim``.
+    * lines 15-16: the Ritz vectors of (A, M) are those of the Rayleigh-Ritz problem on
+      range(Q_mu); each one's Rayleigh quotient x^T A x / x^T M x is its Ritz value.  (The
+      eigenvectors of H_mu alone are not enough where rho takes nearly equal values on several
+      eigenvalues -- rho is symmetric about the centre of [alpha, beta] -- since any mixture of
+      their eigenvectors is then an eigenvector of H_mu.)
+    """
+    n = Ap.shape[0]
+    b = block
+    max_dim = min(max_dim or n, n)
+    Q1, _ = _m_cholqr(Mp, counter_uniform(seed, 7000, n * b).reshape(n, b))
+    Qs = [Q1]
+    cols = []               # H columns, one block of b columns per step
+    sums = []
+    steps_per_check = max(1, -(-check_every // b))
+    last = None
+    extra = 1
+    mu = b
+    while True:
+        W = apply_rho(Qs[-1])                                               # line 2
+        W, coef = _m_orth_against(Mp, Qs, W)                                # lines 3-6 (twice)
+        cols.append(np.vstack(coef))
+        t = len(cols)
+        if t % steps_per_check == 0 or mu >= max_dim:                       # line 13
+            H = _assemble_h(cols, Qs, b)
+            ev = np.linalg.eigvalsh(H)
+            cur = float(ev[ev >= 0.5].sum())
+            sums.append(cur)
+            if last is not None and abs(cur - last) <= tol * abs(cur):
+                break
+            last = cur
+        if mu >= max_dim:
+            break
+        bn = min(b, max_dim - mu)
+        # lines 7-12, column by column: normalise in the M norm what is left after the
+        # projections; a column left with norm <= 1e-14 max|H| (h_{mu+1,mu} = 0) is replaced by
+        # a fresh counter-based vector orthogonal to everything so far
+        hmax = max(np.abs(c).max() for c in cols)
+        new_cols = []
+        for j in range(bn):
+            v = W[:, j:j + 1]
+            for attempt in range(2):
+                prev = Qs + ([np.hstack(new_cols)] if new_cols else [])
+                v, _ = _m_orth_against(Mp, prev, v)
+                nrm = math.sqrt(max(float(v[:, 0] @ (Mp @ v[:, 0])), 0.0))
+                if nrm > 1e-14 * max(hmax, 1e-300):
+                    break
+                v = counter_uniform(seed, 7000 + extra, n).reshape(n, 1)
+                extra += 1
+            new_cols.append(v / nrm)
+        Qs.append(np.hstack(new_cols))
+        mu += bn
+    Q = np.hstack(Qs[:len(cols)])
+    H = _assemble_h(cols, Qs, b)
+    theta, X = rayleigh_ritz(Ap, Mp, Q)                                      # lines 15-16
+    inside = (theta >= alpha) & (theta <= beta)
+    return dict(Q=Q, H=H, mu=Q.shape[1], sums=sums, theta=theta, X=X, inside=inside)
+
+
+def _assemble_h(cols, Qs, b):
+    """H_mu = Q_mu^T M rho(M^{-1}A) Q_mu.  The block column of step t holds the coefficients of
+    rho(M^{-1}A) Q_t on blocks 1..t, i.e. the blocks of H on and above the diagonal; H is
+    symmetric, so the blocks below it are their transposes (the diagonal blocks are
+    symmetrised)."""
+    widths = [q.shape[1] for q in Qs[:len(cols)]]
+    mu = sum(widths)
+    U = np.zeros((mu, mu))
+    c0 = 0
+    for t, c in enumerate(cols):
+        w = widths[t]
+        U[:c.shape[0], c0:c0 + w] = c[:, :w]
+        c0 += w
+    D = np.zeros((mu, mu))
+    c0 = 0
+    for w in widths:
+        blk = U[c0:c0 + w, c0:c0 + w]
+        D[c0:c0 + w, c0:c0 + w] = 0.5 * (blk + blk.T)
+        U[c0:c0 + w, c0:c0 + w] = 0.0
+        c0 += w
+    return U + U.T + D
+
+
 def filter_gain(Mp, X, Y):
     """Filter gain of each column x of an M-orthonormal block X with Y = rho(A) X: the Rayleigh
     quotient x^T M rho(A) x, which is rho(lambda) when x is an eigenvector (rho >= 1/2 on

@@ -45,6 +45,7 @@ SYMBOLS = [
     "rfdd_server_default_options", "rfdd_server_create", "rfdd_server_add_pencil", "rfdd_server_submit",
     "rfdd_server_wait", "rfdd_server_submit_pencil", "rfdd_server_request_info", "rfdd_server_get_stats", "rfdd_server_remove_pencil",
     "rfdd_server_destroy", "rfdd_autotune", "rfdd_autotune_table",
+    "rfdd_rfkrylov",
 ]
 
 
@@ -129,6 +130,7 @@ def load(path: str | None = None):
     lib.rfdd_destroy.restype = None
     lib.rfdd_solve.argtypes = [vp, C.c_double, C.c_double, i32, C.POINTER(vp)]
     lib.rfdd_solve_async.argtypes = [vp, C.c_double, C.c_double, i32, vp, C.POINTER(vp)]
+    lib.rfdd_rfkrylov.argtypes = [vp, C.c_double, C.c_double, i32, i64, C.POINTER(vp)]
     lib.rfdd_result_ready.argtypes = [vp]
     lib.rfdd_result_get.argtypes = [vp, C.POINTER(i64), C.POINTER(dp), C.POINTER(dp), C.POINTER(dp), i32]
     lib.rfdd_result_info.argtypes = [vp, C.POINTER(rfdd_info)]
@@ -293,6 +295,14 @@ class Result:
 def rfdd_solve(h: Handle, alpha: float, beta: float, n_nodes: int) -> Result:
     out = C.c_void_p()
     rc = load().rfdd_solve(h.ptr, alpha, beta, n_nodes, C.byref(out))
+    _check(rc, ok=(RFDD_OK, RFDD_NOT_CONVERGED))
+    return Result(out.value, rc, h.n)
+
+
+def rfdd_rfkrylov(h: Handle, alpha: float, beta: float, n_nodes: int, max_dim: int = 0) -> Result:
+    """RF-KRYLOV (Algorithm 1) on the handle's pencil, then the completion passes."""
+    out = C.c_void_p()
+    rc = load().rfdd_rfkrylov(h.ptr, alpha, beta, n_nodes, int(max_dim), C.byref(out))
     _check(rc, ok=(RFDD_OK, RFDD_NOT_CONVERGED))
     return Result(out.value, rc, h.n)
 

@@ -1944,6 +1944,20 @@ void rr_on_Z(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
   RFDD_CUDA(cudaStreamSynchronize(st));
 }
 
+// Condition bound of the shifted systems when M's Gershgorin bound is positive:
+// ||(A - z M)^{-1}|| <= 1 / (|Im z| lambda_min(M)), so kappa(A - z M) <= (||A|| + |z| ||M||) /
+// (|Im z| gershM).  A solve refined to scaled backward error eta has forward error up to kappa eta.
+// 0 when no bound is known.
+double shifted_kappa_bound(const rfdd_handle *h) {
+  double kappa = 0.0;
+  if (h->gershM > 0.0 && std::isfinite(h->gershM))
+    for (const auto &zl : h->z) {
+      const double zn = std::hypot(zl.re, zl.im);
+      kappa = std::max(kappa, (h->normA + zn * h->normM) / (std::fabs(zl.im) * h->gershM));
+    }
+  return kappa;
+}
+
 template <typename Tf>
 void complete(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
   cudaStream_t st = h->st;
@@ -1986,15 +2000,7 @@ void complete(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
   }
   int64_t count_prev = res->info.pre_nev;
   double res_level = std::max(res->info.pre_max_resid, 1e-300);
-  // Condition bound of the shifted systems when M's Gershgorin bound is positive:
-  // ||(A - z M)^{-1}|| <= 1 / (|Im z| lambda_min(M)), so kappa(A - z M) <= (||A|| + |z| ||M||) /
-  // (|Im z| gershM).  A solve refined to scaled backward error eta has forward error up to kappa eta.
-  double kappa = 0.0;
-  if (h->gershM > 0.0 && std::isfinite(h->gershM))
-    for (const auto &zl : h->z) {
-      const double zn = std::hypot(zl.re, zl.im);
-      kappa = std::max(kappa, (h->normA + zn * h->normM) / (std::fabs(zl.im) * h->gershM));
-    }
+  const double kappa = shifted_kappa_bound(h);
   // The double-FP32 refinement residual is accurate to about 2^-46 of sum |a||x|; when kappa times
   // that exceeds 1/100 of the residual target, the residual is formed with FP64 products.
   const bool fp64_res = kappa * 0x1p-46 > 1e-2 * h->opt.res_tol;
@@ -2409,6 +2415,266 @@ void factor(rfdd_handle *h) {
   h->pkS.clear();
   if (is_mixed(h)) factor_impl<cx<float>>(h);
   else factor_impl<cx<double>>(h);
+}
+
+// ------------------------------------------------------------------------------------
+// Algorithm 1 (RF-KRYLOV, Section 2.2): Krylov on rho(M^{-1}A) in the whole space
+// ------------------------------------------------------------------------------------
+// Block Krylov with full orthogonalisation in the M inner product (rho(M^{-1}A) is self-adjoint
+// there, so H_mu = Q^T M rho Q is symmetric; with M = I this is the printed Euclidean process):
+//   line 2:     W = 2 Re sum_l w_l (A - z_l M)^{-1} M Q_t through Eq. (inv_dd2) with the same
+//               factors as the RF-DDES solve and FP64 refinement;
+//   lines 3-6:  two classical Gram-Schmidt passes in the M inner product against Q; their
+//               coefficients are the block column t of H;
+//   lines 7-12: M-Cholesky-QR of the new block (twice, with one more projection between);
+//               columns that vanish are replaced by counter-based vectors (streams 7001, ...);
+//   line 13:    every ceil(10/b) block steps, stop when the sum of the eigenvalues >= 1/2 of H_mu
+//               changed by at most lanczos_tol of its magnitude since the previous check, or
+//               when mu reaches the column cap;
+//   lines 15-16: Rayleigh-Ritz of (A, M) on range(Q_mu); then the completion passes as in
+//               rfdd_solve.
+// The start block is counter-based (stream 7000).
+template <typename Tf>
+void rfkrylov_impl(rfdd_handle *h, double alpha, double beta, int64_t max_dim, rfdd_result *res) {
+  cudaStream_t st = h->st;
+  const int64_t n = h->n;
+  const int nc = h->nnodes;
+  const int64_t b = std::max<int64_t>(1, std::min<int64_t>(h->opt.block, n));
+  const int64_t cap = std::min<int64_t>(n, max_dim > 0 ? max_dim : 4096);
+  RFDD_REQUIRE(cap >= b, RFDD_EINVAL, "rf-krylov: max_dim below the block size");
+  Buf Qb, W, MW, Xb, V, Xc, Cb, Gb, Rinv, dead, tmp;
+  Qb.alloc((size_t)n * cap * sizeof(double));
+  double *Q = Qb.as<double>();
+  W.alloc((size_t)n * b * sizeof(double));
+  MW.alloc((size_t)n * b * sizeof(double));
+  Xb.alloc((size_t)n * b * sizeof(double));
+  V.alloc((size_t)n * b * sizeof(double));
+  Xc.alloc((size_t)nc * n * b * sizeof(cx<double>));
+  Cb.alloc((size_t)cap * b * sizeof(double));
+  Gb.alloc((size_t)b * b * sizeof(double));
+  Rinv.alloc((size_t)b * b * sizeof(double));
+  dead.alloc((size_t)b * sizeof(int));
+  tmp.alloc((size_t)n * b * sizeof(double));
+  const double kappa = shifted_kappa_bound(h);
+  const bool fp64_res = kappa * 0x1p-46 > 1e-2 * h->opt.res_tol;
+  // the filter is applied as accurately as the completion passes finish: 1/100 of the residual
+  // target, divided by the condition bound where it is known
+  const double ir_tol = std::max(1e-15, 1e-2 * h->opt.res_tol / std::max(1.0, kappa));
+  std::vector<double> U((size_t)cap * cap, 0.0);  // blocks of H on and above the diagonal
+  std::vector<double> hc((size_t)cap * b), hdiag(b);
+  std::vector<int> hdead(b);
+  double hmax = 0.0;
+  // W -= Q C, C = Q[:, :ncols]^T M W (twice); with `acc` the coefficients are added to H's
+  // block column starting at column c0
+  auto mproj = [&](double *Wp, int64_t bw, int64_t ncols, bool acc, int64_t c0) {
+    if (ncols <= 0) return;
+    for (int pass = 0; pass < 2; ++pass) {
+      spmm_f64(st, h->P, 0, n, 0, n, 0.0, 1.0, Wp, bw, MW.as<double>(), bw, bw, false);
+      basis_gemm(h, {{Q, MW.as<double>(), Cb.as<double>(), (int)ncols, (int)bw, (int)n, (int)cap, (int)bw, (int)bw}},
+                 true, false, 1.0, 0.0);
+      basis_gemm(h, {{Q, Cb.as<double>(), Wp, (int)n, (int)bw, (int)ncols, (int)cap, (int)bw, (int)bw}}, false,
+                 false, -1.0, 1.0);
+      if (acc) {
+        RFDD_CUDA(cudaMemcpyAsync(hc.data(), Cb.p, (size_t)ncols * bw * sizeof(double), cudaMemcpyDeviceToHost, st));
+        RFDD_CUDA(cudaStreamSynchronize(st));
+        for (int64_t r = 0; r < ncols; ++r)
+          for (int64_t c = 0; c < bw; ++c) {
+            U[(size_t)r * cap + c0 + c] += hc[(size_t)r * bw + c];
+            hmax = std::max(hmax, std::fabs(U[(size_t)r * cap + c0 + c]));
+          }
+      }
+    }
+  };
+  uint64_t extra = 0;
+  // M-Cholesky-QR of Wp (n x bw) against Q[:, :ncols]; dead columns replaced and redone
+  auto morth = [&](double *Wp, int64_t bw, int64_t ncols) {
+    for (int attempt = 0; attempt < 4; ++attempt) {
+      bool any_dead = false;
+      for (int q = 0; q < 2 && !any_dead; ++q) {
+        spmm_f64(st, h->P, 0, n, 0, n, 0.0, 1.0, Wp, bw, MW.as<double>(), bw, bw, false);
+        basis_gemm(h, {{Wp, MW.as<double>(), Gb.as<double>(), (int)bw, (int)bw, (int)n, (int)bw, (int)bw, (int)bw}},
+                   true, false, 1.0, 0.0, {1});
+        std::vector<double> g((size_t)bw * bw);
+        RFDD_CUDA(cudaMemcpyAsync(g.data(), Gb.p, g.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        chol_inv_batched(st, {CholItem{Gb.as<double>(), Rinv.as<double>(), dead.as<int>(), (int)bw}}, 1e-24);
+        RFDD_CUDA(cudaMemcpyAsync(hdead.data(), dead.p, bw * sizeof(int), cudaMemcpyDeviceToHost, st));
+        RFDD_CUDA(cudaStreamSynchronize(st));
+        // a column whose M norm is at most 1e-14 max|H| is dead even when all are that small
+        const double floor2 = (1e-14 * hmax) * (1e-14 * hmax);
+        for (int64_t c = 0; c < bw; ++c) {
+          if (!(g[(size_t)c * bw + c] > floor2)) hdead[c] = 1;
+          any_dead |= hdead[c] != 0;
+        }
+        if (any_dead) break;
+        basis_gemm(h, {{Wp, Rinv.as<double>(), tmp.as<double>(), (int)n, (int)bw, (int)bw, (int)bw, (int)bw, (int)bw}},
+                   false, false, 1.0, 0.0);
+        RFDD_CUDA(cudaMemcpyAsync(Wp, tmp.p, (size_t)n * bw * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        if (q == 0 && ncols > 0) mproj(Wp, bw, ncols, false, 0);  // one more pass after normalising
+      }
+      if (!any_dead) return;
+      Buf fresh;
+      fresh.alloc((size_t)n * sizeof(double));
+      for (int64_t c = 0; c < bw; ++c)
+        if (hdead[c]) {
+          counter_uniform_dev(st, h->opt.seed, 7001 + extra++, fresh.as<double>(), n);
+          copy_rows_f64(st, fresh.as<double>(), 1, Wp + c, bw, n, 1);
+        }
+      mproj(Wp, bw, ncols, false, 0);
+    }
+    throw Error(RFDD_ESINGULAR, "rf-krylov: could not extend the basis");
+  };
+  // eigenvalues of the symmetric H_mu (mu x mu) on the GPU
+  auto h_eigs = [&](int64_t mu) {
+    std::vector<double> H((size_t)mu * mu);
+    for (int64_t r = 0; r < mu; ++r)
+      for (int64_t c = 0; c < mu; ++c) {
+        const double up = r <= c ? U[(size_t)r * cap + c] : U[(size_t)c * cap + r];
+        H[(size_t)r * mu + c] = up;
+      }
+    // diagonal blocks: symmetric part (the coefficients of a block on itself)
+    for (int64_t r = 0; r < mu; ++r)
+      for (int64_t c = r + 1; c < mu; ++c)
+        if (r / b == c / b) {
+          const double v = 0.5 * (U[(size_t)r * cap + c] + U[(size_t)c * cap + r]);
+          H[(size_t)r * mu + c] = H[(size_t)c * mu + r] = v;
+        }
+    Buf Hd, d, e, t, wk, lam;
+    upload(Hd, H, st);
+    d.alloc(mu * sizeof(double));
+    e.alloc(mu * sizeof(double));
+    t.alloc(mu * sizeof(double));
+    wk.alloc(mu * sizeof(double));
+    lam.alloc(mu * sizeof(double));
+    SymItem si{Hd.as<double>(), (int)mu, (int)mu, d.as<double>(), e.as<double>(), t.as<double>(), wk.as<double>(),
+               lam.as<double>(), nullptr};
+    sym_eig_values(st, {si}, h->status.as<int>());
+    std::vector<double> ev(mu);
+    RFDD_CUDA(cudaMemcpyAsync(ev.data(), lam.p, mu * sizeof(double), cudaMemcpyDeviceToHost, st));
+    RFDD_CUDA(cudaStreamSynchronize(st));
+    return ev;
+  };
+  // line 0
+  counter_uniform_dev(st, h->opt.seed, 7000, W.as<double>(), n * b);
+  hmax = 1.0;
+  morth(W.as<double>(), b, 0);
+  hmax = 0.0;
+  copy_rows_f64(st, W.as<double>(), b, Q, cap, n, b);
+  int64_t col = 0, bc = b, steps = 0;
+  const int64_t per_check = std::max<int64_t>(1, (10 + b - 1) / b);
+  double last = NAN;
+  std::vector<double> sums;
+  int irmax = 0;
+  while (true) {
+    copy_rows_f64(st, Q + col, cap, Xb.as<double>(), bc, n, bc);
+    spmm_f64(st, h->P, 0, n, 0, n, 0.0, 1.0, Xb.as<double>(), bc, V.as<double>(), bc, bc, false);
+    irmax = std::max(irmax, refined_solve<Tf>(h, V.as<double>(), Xc.as<cx<double>>(), bc, ir_tol, fp64_res));
+    weighted_real_sum<cx<double>>(st, Xc.as<cx<double>>(), n * bc, h->w_dev.as<cx<double>>(), nc, 2.0,
+                                  W.as<double>(), n * bc);                                      // line 2
+    const int64_t mu = col + bc;
+    mproj(W.as<double>(), bc, mu, true, col);                                                   // lines 3-6
+    ++steps;
+    if (steps % per_check == 0 || mu >= cap) {                                                  // line 13
+      const std::vector<double> ev = h_eigs(mu);
+      double cur = 0.0;
+      for (double x : ev)
+        if (x >= 0.5) cur += x;
+      sums.push_back(cur);
+      RFDD_LOGF("rf-krylov: mu=%lld sum of eigenvalues >= 1/2 of H: %.12g", (long long)mu, cur);
+      if (!std::isnan(last) && std::fabs(cur - last) <= h->opt.lanczos_tol * std::fabs(cur)) break;
+      last = cur;
+    }
+    if (mu >= cap) break;
+    const int64_t bn = std::min<int64_t>(b, cap - mu);                                          // lines 7-12
+    if (bn < bc) {
+      copy_rows_f64(st, W.as<double>(), bc, tmp.as<double>(), bn, n, bn);
+      RFDD_CUDA(cudaMemcpyAsync(W.p, tmp.p, (size_t)n * bn * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
+    morth(W.as<double>(), bn, mu);
+    copy_rows_f64(st, W.as<double>(), bn, Q + mu, cap, n, bn);
+    col = mu;
+    bc = bn;
+  }
+  const int64_t mu = col + bc;
+  h->mu = mu;
+  res->info.mu = mu;
+  res->info.ir_steps_max = std::max(res->info.ir_steps_max, irmax);
+  h->traces = sums;
+  // lines 15-16: Rayleigh-Ritz of (A, M) on range(Q_mu)
+  Buf Y, C;
+  Y.alloc((size_t)n * mu * sizeof(double));
+  copy_rows_f64(st, Q, cap, Y.as<double>(), mu, n, mu);
+  Qb.release();
+  std::vector<int> sel;
+  RRout rr = rayleigh_ritz_coeffs(
+      h, Y.as<double>(), mu, 1e-12, 1e-9,
+      [&](const std::vector<double> &th) {
+        int64_t nin = 0;
+        for (double x : th) nin += (x >= alpha && x <= beta);
+        int64_t m = nin + std::max<int64_t>((int64_t)std::ceil(h->opt.guard_frac * nin), h->opt.min_guard);
+        if (h->opt.m_align > 1) m = (m + h->opt.m_align - 1) / h->opt.m_align * h->opt.m_align;
+        m = std::min<int64_t>((int64_t)th.size(), m);
+        return select_nearest(th, alpha, beta, m);
+      },
+      C, sel);
+  h->rr_theta = rr.theta;
+  h->m0 = (int64_t)sel.size();
+  h->X0.alloc((size_t)n * std::max<int64_t>(1, h->m0) * sizeof(double));
+  if (h->m0 > 0)
+    basis_gemm(h, {{Y.as<double>(), C.as<double>(), h->X0.as<double>(), (int)n, (int)h->m0, (int)mu, (int)mu,
+                    (int)h->m0, (int)h->m0}},
+               false, false, 1.0, 0.0);
+  res->pre_evals.clear();
+  for (double t : rr.theta)
+    if (t >= alpha && t <= beta) res->pre_evals.push_back(t);
+  res->info.k = rr.r;
+  RFDD_CUDA(cudaStreamSynchronize(st));
+}
+
+void run_rfkrylov(rfdd_handle *h, double alpha, double beta, int nc, int64_t max_dim, rfdd_result *res) {
+  RFDD_REQUIRE(beta > alpha && nc >= 1, RFDD_EINVAL, "rf-krylov: need alpha < beta and n_nodes >= 1");
+  RFDD_REQUIRE(max_dim >= 0, RFDD_EINVAL, "rf-krylov: max_dim must be >= 0");
+  Timer total(h->st);
+  std::vector<cx<double>> z, w;
+  quadrature(alpha, beta, nc, h->opt.quad_rule, z, w);
+  if (h->opt.mem_budget > 0) {
+    const size_t need = factor_bytes(h, nc);
+    RFDD_REQUIRE(need <= h->opt.mem_budget, RFDD_EADMIT,
+                 "rf-krylov needs " + std::to_string(need) + " bytes of factors, budget " +
+                     std::to_string(h->opt.mem_budget));
+  }
+  std::vector<double> zz(2 * nc), ww(2 * nc);
+  for (int l = 0; l < nc; ++l) {
+    zz[2 * l] = z[l].re;
+    zz[2 * l + 1] = z[l].im;
+    ww[2 * l] = w[l].re;
+    ww[2 * l + 1] = w[l].im;
+  }
+  set_nodes(h, nc, zz.data(), ww.data());
+  h->alpha = alpha;
+  h->beta = beta;
+  h->have_interval = true;
+  {
+    Timer t(h->st);
+    factor(h);
+    res->info.t_factor_ms = t.ms();
+    res->info.t_factor_enqueue_ms = h->factor_enqueue_ms;
+    res->info.factor_launches = h->factor_launches;
+    res->info.packed = h->pkB.empty() ? 0 : 1;
+  }
+  {
+    Timer t(h->st);
+    if (is_mixed(h)) rfkrylov_impl<cx<float>>(h, alpha, beta, max_dim, res);
+    else rfkrylov_impl<cx<double>>(h, alpha, beta, max_dim, res);
+    res->info.t_lanczos_ms = t.ms();
+  }
+  {
+    Timer t(h->st);
+    if (is_mixed(h)) complete<cx<float>>(h, alpha, beta, res);
+    else complete<cx<double>>(h, alpha, beta, res);
+    res->info.t_complete_ms = t.ms();
+  }
+  res->info.sigma = NAN;
+  res->info.t_total_ms = total.ms();
 }
 
 void run_solve(rfdd_handle *h, double alpha, double beta, int nc, rfdd_result *res) {
@@ -2896,6 +3162,24 @@ int rfdd_solve(rfdd_handle *h, double alpha, double beta, int32_t n_nodes, rfdd_
     AllocScope scope(h->st);
     TcStatusScope tcs(h->status.as<int>());
     run_solve(h, alpha, beta, n_nodes, r);
+  });
+  if (rc != RFDD_OK) {
+    delete r;
+    return rc;
+  }
+  *out = r;
+  return r->info.status;
+}
+
+int rfdd_rfkrylov(rfdd_handle *h, double alpha, double beta, int32_t n_nodes, int64_t max_dim, rfdd_result **out) {
+  if (!h || !out) return RFDD_EINVAL;
+  *out = nullptr;
+  rfdd_result *r = new (std::nothrow) rfdd_result();
+  if (!r) return RFDD_ENOMEM;
+  int rc = guarded([&] {
+    AllocScope scope(h->st);
+    TcStatusScope tcs(h->status.as<int>());
+    run_rfkrylov(h, alpha, beta, n_nodes, max_dim, r);
   });
   if (rc != RFDD_OK) {
     delete r;
