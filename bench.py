@@ -462,6 +462,60 @@ def run_one_solve(args):
                       "eigenpairs_per_s": info["nev"] / (info["t_total_ms"] * 1e-3), "solve_info": info}), flush=True)
 
 
+def run_compare(args):
+    """RF-DDES (Algorithm 3 + completion) against RF-KRYLOV (Algorithm 1 + the same completion) on
+    one workload, both on the same factorisation code and precision: the paper's comparison
+    (Section 6.3: Krylov dimensions, accuracy before completion, time), here on one GPU."""
+    import torch
+    import paper_1711_09487_gb300 as R
+    torch.cuda.set_device(0)
+    R.load()
+    w = I.workload(args.workload)
+    precision = R.RFDD_MIXED if args.precision == "mixed" else R.RFDD_FP64
+    stream = torch.cuda.Stream()
+    extra = {} if args.nev_b is None else {"nev_b": args.nev_b}
+    opts = R.rfdd_default_options(precision=precision, quad_rule=0 if w.rule == "midpoint" else 1,
+                                  stream=stream.cuda_stream, **extra)
+    h = R.rfdd_setup(w.A, w.M, w.part, w.p, opts)
+    ex = w.exact[(w.exact > w.alpha) & (w.exact < w.beta)] if w.exact is not None else None
+    out = {"mode": "compare", "workload": w.name, "n": w.n, "p": w.p, "n_nodes": w.n_nodes,
+           "nev": w.expected_nev, "nev_b": opts.nev_b, "precision": args.precision, "steps": args.steps,
+           "warmup": args.warmup}
+    for name, call in (("rf_ddes", lambda: R.rfdd_solve(h, w.alpha, w.beta, w.n_nodes)),
+                       ("rf_krylov", lambda: R.rfdd_rfkrylov(h, w.alpha, w.beta, w.n_nodes))):
+        for _ in range(args.warmup):
+            call()
+        times, info, pre, good = [], None, None, 0
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = call()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            info = R.rfdd_result_info(r)
+            pre = np.sort(R.rfdd_result_pre_evals(r))
+            ev, _, rs = R.rfdd_result_get(r, vectors=False)
+            good = int(np.count_nonzero(rs <= 1e-10))
+            del r
+        ms = statistics.median(times)
+        d = {"eigenpairs_per_s": good / (ms / 1e3), "ms_median": ms, "eigenpairs": good,
+             "krylov_dim": info["mu"], "rr_rank": info["k"], "passes": info["passes"],
+             "max_resid": info["max_resid"], "status": info["status"], "fp64_basis": info["fp64_basis"],
+             "phases_ms": {k: info[k] for k in ("t_factor_ms", "t_lanczos_ms", "t_interior_ms", "t_rr_ms",
+                                                 "t_complete_ms")}}
+        if ex is not None and len(pre) == len(ex) and len(ex):
+            d["pre_completion_max_rel_err"] = float(np.max(np.abs(pre - ex) / np.abs(ex)))
+        else:
+            d["pre_completion_count"] = int(len(pre))
+        if ex is not None and len(ev) == len(ex) and len(ex):
+            d["final_max_rel_err"] = float(np.max(np.abs(np.sort(ev) - ex) / np.abs(ex)))
+        out[name] = d
+    out["ddes_over_krylov"] = out["rf_ddes"]["eigenpairs_per_s"] / max(out["rf_krylov"]["eigenpairs_per_s"], 1e-300)
+    print(json.dumps(out), flush=True)
+
+
 def run_gemm(args):
     """One large complex GEMM C -= A B (m x k times k x n) on the tensor cores: the shape of the
     deep trailing updates of the factorisations (profiled alone with ncu)."""
@@ -595,7 +649,7 @@ def serve_stream(R, requests, load, inflight, capacity_sample):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--mode", default="bench", choices=["bench", "one-solve", "gemm", "dgemm", "serve"])
+    ap.add_argument("--mode", default="bench", choices=["bench", "one-solve", "gemm", "dgemm", "serve", "compare"])
     ap.add_argument("--requests", type=int, default=256, help="serve mode: requests in the stream")
     ap.add_argument("--load", type=float, default=0.7, help="serve mode: arrival rate / single-stream capacity")
     ap.add_argument("--inflight", type=int, default=4, help="serve mode: requests running at once")
@@ -611,6 +665,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--nev-b", type=int, default=None,
+                    help="compare mode: eigenvectors per subdomain in the RF-DDES basis (default 100)")
     ap.add_argument("--fp64-plain", default="auto", choices=["auto", "on", "off"],
                     help="also time one solve on the plain FP64 path (auto: at N = 1 with --precision mixed)")
     args = ap.parse_args()
@@ -628,6 +684,9 @@ def main():
         return
     if args.mode == "serve":
         run_serve(args)
+        return
+    if args.mode == "compare":
+        run_compare(args)
         return
     if args.impl == "reference":
         run_reference(args, rank, world)

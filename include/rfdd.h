@@ -131,6 +131,11 @@ typedef struct {
                                  asynchronously: the host limits the phase only if this
                                  approaches t_factor_ms) */
   int64_t factor_launches;    /* kernels launched for a2-a5 */
+  int32_t fp64_basis;         /* 1 if the completion passes switched their basis products (Gram
+                                 matrices, Ritz vectors) and refinement residuals from
+                                 double-FP32 to FP64 because the residuals stopped falling
+                                 (mixed precision only) */
+  int32_t reserved0;
 } rfdd_info;
 
 /* Fill *opt with the defaults listed above. */

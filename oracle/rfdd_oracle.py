@@ -15,8 +15,10 @@ Pins (see tests/test_oracle_*.py): closed-form Q1 spectra, the Midpoint-filter c
 Gauss-Legendre exactness, the (2,2)-block identity of Eq. (finalizing), the block inverse of
 Eq. (inv_dd2) against a dense inverse, Prop. (lowrank), Theorems (uuhat), (uuhat2), (all) at
 tiny n, Sylvester inertia counts, the interior polish of Eq. (compute_u_parallel) recovering
-dense-eigensolver eigenvectors from their interface rows, and brute-force dense generalized
-eigensolves.
+dense-eigensolver eigenvectors from their interface rows, brute-force dense generalized
+eigensolves, and for RF-KRYLOV (Algorithm 1) the closed-form spectra of the 5-point Laplacian
+with M = I and of the Q1 pencil, the projected filter H_mu formed directly, and the stopping
+step on filters whose Krylov space is exhausted at a known step.
 """
 from __future__ import annotations
 

@@ -76,7 +76,7 @@ class rfdd_info(C.Structure):
                 ("t_lanczos_ms", C.c_double), ("t_interior_ms", C.c_double), ("t_rr_ms", C.c_double),
                 ("t_complete_ms", C.c_double), ("t_total_ms", C.c_double), ("status", C.c_int32),
                 ("packed", C.c_int32), ("sigma", C.c_double), ("t_factor_enqueue_ms", C.c_double),
-                ("factor_launches", C.c_int64)]
+                ("factor_launches", C.c_int64), ("fp64_basis", C.c_int32), ("reserved0", C.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -282,6 +282,7 @@ struct rfdd_handle {
   std::exception_ptr I_exc;   // its error, rethrown by interior_join
   std::vector<int64_t> boff, pivBoff;
   bool have_factors = false;
+  bool basis_fp64 = false;         // the completion's basis products in FP64 (see complete)
   double factor_enqueue_ms = 0.0;  // host time to issue the last factorisation's launches
   long long factor_launches = 0;   // kernels it launched
   double alpha = 0, beta = 0;
@@ -1085,7 +1086,7 @@ void solve_S(rfdd_handle *h, Tf *G, int64_t ldg, int64_t gs, int64_t m, const st
 // the plain FP64 solve.
 void basis_gemm(const rfdd_handle *h, const std::vector<GemmItem<double>> &g, bool ta, bool tb, double alpha,
                 double beta, const std::vector<char> &sym = {}) {
-  if (h->opt.precision == RFDD_FP64) gemm_simt_batched<double>(h->st, g, ta, tb, alpha, beta, sym);
+  if (h->opt.precision == RFDD_FP64 || h->basis_fp64) gemm_simt_batched<double>(h->st, g, ta, tb, alpha, beta, sym);
   else gemm_f64x2_batched(h->st, g, ta, tb, alpha, beta, sym);
 }
 
@@ -2003,7 +2004,18 @@ void complete(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
   const double kappa = shifted_kappa_bound(h);
   // The double-FP32 refinement residual is accurate to about 2^-46 of sum |a||x|; when kappa times
   // that exceeds 1/100 of the residual target, the residual is formed with FP64 products.
-  const bool fp64_res = kappa * 0x1p-46 > 1e-2 * h->opt.res_tol;
+  bool fp64_res = kappa * 0x1p-46 > 1e-2 * h->opt.res_tol;
+  // The double-FP32 basis products (Gram matrices, Ritz vectors) leave an error of about 2^-46
+  // relative in each Ritz vector; a residual relative to |lambda| then cannot fall below about
+  // 2^-46 ||A|| / |lambda|, which is above the target for eigenvalues far smaller than ||A||.
+  // When the largest residual of the unconverged inside pairs shrinks by less than 10x over a
+  // pass, the remaining passes form those products, and the refinement residuals, in FP64.
+  struct BasisPrecision {
+    rfdd_handle *h;
+    ~BasisPrecision() { h->basis_fp64 = false; }
+  } basis_precision{h};
+  h->basis_fp64 = false;
+  double unconv_prev = -1.0;
   Buf V, Xc, C, Xprev;
   std::vector<double> theta, resid, theta_prev, resid_prev;
   std::vector<int64_t> keep;  // Ritz pairs returned: inside [alpha, beta], converged, not spurious
@@ -2149,6 +2161,19 @@ void complete(rfdd_handle *h, double alpha, double beta, rfdd_result *res) {
     if (inside == count_prev && (inside == 0 || mx <= h->opt.res_tol)) {
       converged = true;
       break;
+    }
+    {
+      double unconv = 0.0;
+      for (int64_t c : keep)
+        if (resid[c] > h->opt.res_tol) unconv = std::max(unconv, resid[c]);
+      if (is_mixed(h) && !h->basis_fp64 && unconv > 0.0 && unconv_prev > 0.0 && unconv > 0.1 * unconv_prev) {
+        h->basis_fp64 = true;
+        fp64_res = true;
+        res->info.fp64_basis = 1;
+        RFDD_LOGF("pass %d: unconverged residuals %.3e after %.3e: basis products in FP64 from here on", passes,
+                  unconv, unconv_prev);
+      }
+      unconv_prev = unconv;
     }
     suspect = good > 0 && good < inside && good == good_prev;
     if (suspect) {
