@@ -209,9 +209,12 @@ class Factors:
     """LU factorisations of every B_j(zeta_l) and S(zeta_l) (Algorithm 3 step 5 needs solves with
     them; the paper uses PARDISO/MUMPS, the oracle uses dense LU with partial pivoting)."""
 
-    def __init__(self, blk: Blocks, z):
+    def __init__(self, blk: Blocks, z, groups=None):
+        """``groups`` (optional, one label in 0..G-1 per subdomain): factor each S(zeta_l) in two
+        levels (``TwoLevelSchur``) instead of one dense LU."""
         self.blk = blk
         self.z = np.atleast_1d(np.asarray(z, dtype=np.complex128))
+        self.levels = None if groups is None else interface_levels(blk, groups)
         self.Blu, self.Slu, self.Ez = [], [], []
         for zl in self.z:
             Bz, Ez, Cz = shifted(blk, zl)
@@ -221,9 +224,14 @@ class Factors:
                 S -= Ez[j].T @ sla.lu_solve(lus[j], Ez[j])
             self.Blu.append(lus)
             self.Ez.append(Ez)
-            self.Slu.append(sla.lu_factor(S))
+            if self.levels is None:
+                self.Slu.append(sla.lu_factor(S))
+            else:
+                self.Slu.append(TwoLevelSchur(S, self.levels))
 
     def solve_S(self, l, G):
+        if self.levels is not None:
+            return self.Slu[l].solve(G)
         return sla.lu_solve(self.Slu[l], G.astype(np.complex128))
 
     def solve_B(self, l, F):
@@ -246,6 +254,109 @@ class Factors:
         y = self.solve_S(l, g - Et.T @ t)
         u = t - self.solve_B(l, Et @ y)
         return np.vstack([u, y])
+
+
+# ----------------------------------------------------------------------------------------
+# Two-level interface factorisation: the block inverse of Eq. (inv_dd2) applied once more, to
+# S(zeta) itself, with groups of subdomains in the role of the subdomains (the recursive use of
+# RF-DDES's decomposition that Section 7 suggests; Section 6.3 names the S solves as what limits
+# RF-DDES when p grows)
+# ----------------------------------------------------------------------------------------
+
+class InterfaceLevels:
+    """Split of the interface for a grouping of the subdomains.
+
+    ``I1[g]``: level-1 nodes of group g; ``I2``: level-2 nodes; ``I2g[g]``: the level-2 nodes
+    that S(zeta) can couple to ``I1[g]`` (all index arrays ascending, interface numbering)."""
+
+    def __init__(self, I1, I2, I2g, cls):
+        self.I1, self.I2, self.I2g, self.cls = I1, I2, I2g, cls
+
+
+def interface_levels(blk: Blocks, groups):
+    """Reading (the paper gives no recursion of the interface): S(zeta)[a, b] can be nonzero
+    only when interface nodes a and b touch a common subdomain (a term of E^T B^{-1} E) or are
+    coupled in C or M_C.  An interface node is level 1 of group g when every subdomain it touches
+    is in group g (at least one) and no node it is coupled to in C or M_C is such a level-1
+    candidate of another group; every other interface node is level 2.  S(zeta) restricted to
+    the level-1 nodes is then block diagonal over the groups."""
+    groups = np.asarray(groups, dtype=np.int64)
+    s, p = blk.s, blk.p
+    G = int(groups.max()) + 1 if p else 0
+    touch = [set() for _ in range(s)]
+    for j in range(p):
+        for a in blk.sidx[j]:
+            touch[a].add(int(groups[j]))
+    cand = np.full(s, -1, dtype=np.int64)
+    for a in range(s):
+        if len(touch[a]) == 1:
+            cand[a] = next(iter(touch[a]))
+    pattern = (blk.C != 0) | (blk.MC != 0)
+    cls = cand.copy()
+    for a in range(s):
+        if cand[a] < 0:
+            continue
+        nb = np.flatnonzero(pattern[a])
+        if np.any((cand[nb] >= 0) & (cand[nb] != cand[a])):
+            cls[a] = -1
+    I1 = [np.flatnonzero(cls == g) for g in range(G)]
+    I2 = np.flatnonzero(cls < 0)
+    I2g = []
+    for g in range(G):
+        near = np.zeros(s, dtype=bool)
+        for j in np.flatnonzero(groups == g):
+            near[blk.sidx[j]] = True
+        if len(I1[g]):
+            near |= pattern[I1[g]].any(axis=0)
+        near &= cls < 0
+        I2g.append(np.flatnonzero(near))
+    return InterfaceLevels(I1, I2, I2g, cls)
+
+
+class TwoLevelSchur:
+    """S = [[S11, S12], [S21, S22]] with S11 = blockdiag_g S(I1_g, I1_g) (``interface_levels``),
+    factored by Eq. (inv_dd2) one level down:
+        S22' = S22 - sum_g S(I2g_g, I1_g) S(I1_g, I1_g)^{-1} S(I1_g, I2g_g),
+    and solved as t_g = S11_g^{-1} g1_g,  S22' y2 = g2 - sum_g S21_g t_g,
+    y1_g = S11_g^{-1} (g1_g - S12_g y2[I2g_g])."""
+
+    def __init__(self, S, lv: InterfaceLevels):
+        self.lv = lv
+        self.s = S.shape[0]
+        pos2 = np.full(self.s, -1, dtype=np.int64)
+        pos2[lv.I2] = np.arange(len(lv.I2))
+        self.pos2 = pos2
+        S22 = S[np.ix_(lv.I2, lv.I2)].astype(np.complex128).copy()
+        self.lu11, self.S12, self.S21 = [], [], []
+        for g in range(len(lv.I1)):
+            I1, J = lv.I1[g], lv.I2g[g]
+            lu = sla.lu_factor(S[np.ix_(I1, I1)]) if len(I1) else None
+            S12 = S[np.ix_(I1, J)]
+            S21 = S[np.ix_(J, I1)]
+            if len(I1) and len(J):
+                S22[np.ix_(pos2[J], pos2[J])] -= S21 @ sla.lu_solve(lu, S12)
+            self.lu11.append(lu)
+            self.S12.append(S12)
+            self.S21.append(S21)
+        self.S22p = S22
+        self.lu22 = sla.lu_factor(S22) if len(lv.I2) else None
+
+    def solve(self, G):
+        lv = self.lv
+        G = G.astype(np.complex128)
+        Y = np.zeros(G.shape, dtype=np.complex128)
+        g2 = G[lv.I2].copy()
+        for g in range(len(lv.I1)):
+            I1, J = lv.I1[g], lv.I2g[g]
+            if len(I1) and len(J):
+                g2[self.pos2[J]] -= self.S21[g] @ sla.lu_solve(self.lu11[g], G[I1])
+        y2 = sla.lu_solve(self.lu22, g2) if len(lv.I2) else g2
+        Y[lv.I2] = y2
+        for g in range(len(lv.I1)):
+            I1, J = lv.I1[g], lv.I2g[g]
+            if len(I1):
+                Y[I1] = sla.lu_solve(self.lu11[g], G[I1] - self.S12[g] @ y2[self.pos2[J]])
+        return Y
 
 
 def filter_interface(fac: Factors, w, X):
@@ -519,7 +630,7 @@ def select_nearest(theta, alpha, beta, m):
 
 def rfdd_solve(A, M, part, p, alpha, beta, n_nodes=4, rule="midpoint", sigma=None, nev_b=100,
                psi=3, lanczos_tol=1e-6, block=1, seed=1, res_tol=1e-10, max_passes=8,
-               guard_frac=0.3, min_guard=8):
+               guard_frac=0.3, min_guard=8, groups=None):
     """RF-DDES (Algorithm 3) followed by completion passes.
 
     Readings:
@@ -539,6 +650,8 @@ def rfdd_solve(A, M, part, p, alpha, beta, n_nodes=4, rule="midpoint", sigma=Non
       When the Ritz values inside leave fewer than max(ceil(0.3 count), 8) columns of the block,
       the block doubles with counter-based vectors (stream 5000 + growth index), at most four
       times, two more passes each; at most max_passes + 10 passes in all.
+    * groups: subdomain group labels for the two-level interface factorisation (TwoLevelSchur);
+      None factors each S(zeta_l) densely.
     Returns a dict with eigenvalues, eigenvectors (original ordering), residuals and diagnostics.
     """
     A = sp.csr_matrix(A)
@@ -553,7 +666,7 @@ def rfdd_solve(A, M, part, p, alpha, beta, n_nodes=4, rule="midpoint", sigma=Non
             break
         sigma += 1e-6 * (beta - alpha)
     z, w = quadrature(alpha, beta, n_nodes, rule)
-    fac = Factors(blk, z)
+    fac = Factors(blk, z, groups)
     V = interior_eigvecs(blk, sigma, nev_b)                       # steps 2-4
     lz = lanczos_interface(lambda X: filter_interface(fac, w, X), blk.s, lanczos_tol, block, seed)
     Q = lz["Q"]                                                   # step 5

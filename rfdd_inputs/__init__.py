@@ -270,6 +270,20 @@ def geometric_partition(N: int, dim: int, splits: tuple[int, ...], shift_frac: f
     return lab.ravel().astype(np.int32), p
 
 
+def subdomain_groups(splits: tuple[int, ...], group_splits: tuple[int, ...]) -> np.ndarray:
+    """Group label of every subdomain of ``geometric_partition(N, dim, splits)`` when the blocks
+    along each axis are gathered into ``group_splits[ax]`` contiguous runs (row-major over the
+    group grid, like the subdomain ids).  Input to the two-level interface factorisation."""
+    assert len(splits) == len(group_splits)
+    for k, g in zip(splits, group_splits):
+        assert 1 <= g <= k
+    idx = np.meshgrid(*[np.arange(k) for k in splits], indexing="ij")
+    lab = np.zeros(splits, dtype=np.int64)
+    for ax, (k, g) in enumerate(zip(splits, group_splits)):
+        lab = lab * g + (idx[ax] * g) // k
+    return lab.ravel().astype(np.int32)
+
+
 def interval_from_sorted(ev: np.ndarray, first: int, last: int) -> tuple[float, float]:
     """[alpha, beta] holding sorted eigenvalues first..last (1-based, inclusive), with both
     endpoints at the midpoints of the neighbouring spectral gaps."""

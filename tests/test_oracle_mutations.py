@@ -81,3 +81,35 @@ def test_pin_catches_wrong_interval_count():
                 for j in range(blk.p))
     assert neg_b != int(np.count_nonzero(w.exact < w.beta))
     assert O.inertia_count(blk, w.beta) == int(np.count_nonzero(w.exact < w.beta))
+
+
+def test_pins_catch_two_level_interface_mistakes():
+    from tests.test_oracle_levels import _thick_separator_pencil
+    # (1) level 1 without the demotion of C-coupled candidates of different groups: the thick
+    # separator's two columns become level 1 of groups 0 and 1 while S couples them
+    A, M, part, p, xs, ny = _thick_separator_pencil()
+    blk = O.Blocks(A, M, part, p)
+    good = O.interface_levels(blk, [0, 0, 1, 1])
+    orig = np.flatnonzero
+    groups = np.array([0, 0, 1, 1])
+    touch = [set() for _ in range(blk.s)]
+    for j in range(p):
+        for a in blk.sidx[j]:
+            touch[a].add(int(groups[j]))
+    cls = np.array([next(iter(t)) if len(t) == 1 else -1 for t in touch])
+    I1 = [orig(cls == g) for g in range(2)]
+    S = O.schur(blk, 1.5 + 0.5j)
+    assert np.all(S[np.ix_(good.I1[0], good.I1[1])] == 0)
+    assert np.any(S[np.ix_(I1[0], I1[1])] != 0)
+    # (2) S22' without the group updates S21 S11^{-1} S12: the Schur identity and the solve fail
+    A, M, part, p = random_pencil(N=14, splits=(3, 3), seed=5)
+    blk = O.Blocks(A, M, part, p)
+    lv = O.interface_levels(blk, I.subdomain_groups((3, 3), (2, 2)))
+    S = O.schur(blk, -0.2 + 0.9j)
+    G = np.random.default_rng(5).standard_normal((blk.s, 3))
+    ref = np.linalg.solve(S, G)
+    bad = O.TwoLevelSchur(S, lv)
+    bad.S22p = S[np.ix_(lv.I2, lv.I2)].copy()
+    bad.lu22 = sla.lu_factor(bad.S22p)
+    assert np.abs(O.TwoLevelSchur(S, lv).solve(G) - ref).max() <= 1e-11 * np.abs(ref).max()
+    assert np.abs(bad.solve(G) - ref).max() > 1e-3 * np.abs(ref).max()
