@@ -516,6 +516,65 @@ def run_compare(args):
     print(json.dumps(out), flush=True)
 
 
+def run_levels(args):
+    """Dense against two-level interface factorisation (rfdd_set_interface_groups) on one
+    workload: factor-phase time, the device bytes of the factors, and whole solves, both
+    completed to residual <= 1e-10 (median of --steps after --warmup)."""
+    import torch
+    import paper_1711_09487_gb300 as R
+    torch.cuda.set_device(0)
+    R.load()
+    w = I.workload(args.workload)
+    precision = R.RFDD_MIXED if args.precision == "mixed" else R.RFDD_FP64
+    splits = w.meta["splits"]
+    gs = tuple(int(x) for x in args.group_splits.split(",")) if args.group_splits else \
+        tuple(max(1, k // 2) for k in splits)
+    groups = I.subdomain_groups(splits, gs)
+    stream = torch.cuda.Stream()
+    extra = {} if args.nev_b is None else {"nev_b": args.nev_b}
+    opts = R.rfdd_default_options(precision=precision, quad_rule=0 if w.rule == "midpoint" else 1,
+                                  stream=stream.cuda_stream, **extra)
+    h = R.rfdd_setup(w.A, w.M, w.part, w.p, opts)
+    ex = w.exact[(w.exact > w.alpha) & (w.exact < w.beta)] if w.exact is not None else None
+    _, _, s = R.rfdd_layout(h)
+    out = {"mode": "levels", "workload": w.name, "n": w.n, "p": w.p, "s": s, "n_nodes": w.n_nodes,
+           "nev": w.expected_nev, "nev_b": opts.nev_b, "precision": args.precision, "group_splits": list(gs),
+           "steps": args.steps, "warmup": args.warmup}
+    for name, grp in (("dense", None), ("two_level", groups)):
+        R.rfdd_set_interface_groups(h, grp)
+        cls, s2 = R.rfdd_interface_levels(h)
+        mem = R.rfdd_memory_estimate(h, w.n_nodes, int(w.expected_nev or 100))
+        for _ in range(args.warmup):
+            R.rfdd_solve(h, w.alpha, w.beta, w.n_nodes)
+        times, infos, good, err = [], [], 0, None
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = R.rfdd_solve(h, w.alpha, w.beta, w.n_nodes)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            infos.append(R.rfdd_result_info(r))
+            ev, _, rs = R.rfdd_result_get(r, vectors=False)
+            good = int(np.count_nonzero(rs <= 1e-10))
+            if ex is not None and len(ev) == len(ex) and len(ex):
+                err = float(np.max(np.abs(np.sort(ev) - ex) / np.abs(ex)))
+            del r
+        ms = statistics.median(times)
+        tf = statistics.median(i["t_factor_ms"] for i in infos)
+        d = {"eigenpairs_per_s": good / (ms / 1e3), "ms_median": ms, "eigenpairs": good, "t_factor_ms": tf,
+             "memory_estimate_bytes": mem, "s2": s2, "level1": int(np.count_nonzero(cls >= 0)),
+             "krylov_dim": infos[-1]["mu"], "passes": infos[-1]["passes"], "max_resid": infos[-1]["max_resid"],
+             "status": infos[-1]["status"], "final_max_rel_err": err,
+             "phases_ms": {k: infos[-1][k] for k in ("t_factor_ms", "t_lanczos_ms", "t_interior_ms", "t_rr_ms",
+                                                      "t_complete_ms")}}
+        out[name] = d
+    out["two_level_over_dense"] = out["two_level"]["eigenpairs_per_s"] / max(out["dense"]["eigenpairs_per_s"], 1e-300)
+    out["factor_speedup"] = out["dense"]["t_factor_ms"] / max(out["two_level"]["t_factor_ms"], 1e-300)
+    print(json.dumps(out), flush=True)
+
+
 def run_gemm(args):
     """One large complex GEMM C -= A B (m x k times k x n) on the tensor cores: the shape of the
     deep trailing updates of the factorisations (profiled alone with ncu)."""
@@ -649,7 +708,7 @@ def serve_stream(R, requests, load, inflight, capacity_sample):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--mode", default="bench", choices=["bench", "one-solve", "gemm", "dgemm", "serve", "compare"])
+    ap.add_argument("--mode", default="bench", choices=["bench", "one-solve", "gemm", "dgemm", "serve", "compare", "levels"])
     ap.add_argument("--requests", type=int, default=256, help="serve mode: requests in the stream")
     ap.add_argument("--load", type=float, default=0.7, help="serve mode: arrival rate / single-stream capacity")
     ap.add_argument("--inflight", type=int, default=4, help="serve mode: requests running at once")
@@ -665,6 +724,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--group-splits", default=None,
+                    help="levels mode: subdomain blocks per group along each axis, e.g. 2,2,2 "
+                         "(default: half the subdomain splits)")
     ap.add_argument("--nev-b", type=int, default=None,
                     help="compare mode: eigenvectors per subdomain in the RF-DDES basis (default 100)")
     ap.add_argument("--fp64-plain", default="auto", choices=["auto", "on", "off"],
@@ -687,6 +749,9 @@ def main():
         return
     if args.mode == "compare":
         run_compare(args)
+        return
+    if args.mode == "levels":
+        run_levels(args)
         return
     if args.impl == "reference":
         run_reference(args, rank, world)

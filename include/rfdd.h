@@ -172,6 +172,31 @@ int rfdd_setup(const rfdd_csr *A, const rfdd_csr *M, const int32_t *part, int32_
 int rfdd_layout(const rfdd_handle *h, int64_t *off, int64_t *perm, int32_t *p_out,
                 int64_t *s_out);
 
+/* Two-level interface factorisation (a5 and the S solves of a6 and a10): the block inverse of
+ * Eq. (inv_dd2) applied a second time, to S(zeta_l), with groups of subdomains in the role of the
+ * subdomains.  This is the recursive use of the decomposition that Section 7 proposes; Section
+ * 6.3 names the S(zeta) solves as what limits RF-DDES as p grows.
+ *   group: p labels in 0..n_groups-1 (host memory, read during the call).  n_groups = 0 (group
+ *   may be NULL) restores the one dense LU of S(zeta_l) per node.
+ * Reading (the paper gives no recursion of the interface): an interface node is level 1 of group
+ * g when every subdomain it touches (has a coupling to) is in g and no interface node it is
+ * coupled to in C or M_C is such a candidate of another group; all other interface nodes are
+ * level 2.  S restricted to the level-1 nodes is then block diagonal over the groups.  Each node's
+ * factors are, per group, the LU of the bordered block [[S(I1_g,I1_g), S(I1_g,I2_g)],
+ * [S(I2_g,I1_g), 0]] (I2_g: the level-2 nodes S couples to I1_g) and the dense LU of
+ * S2' = S(I2,I2) - sum_g S(I2_g,I1_g) S(I1_g,I1_g)^{-1} S(I1_g,I2_g).  The results of a solve are
+ * those of the dense factorisation up to rounding; the memory and the flops of a5 fall from s^2
+ * and s^3 per node to about s2^2 + sum_g (|I1_g| + |I2_g|)^2 and their cubes.
+ * Drops the handle's factors (the next rfdd_solve or rfdd_factor refactors).  RFDD_EINVAL: a
+ * label out of range, n_groups < 0, or keep_schur set (the dense S is never formed). */
+int rfdd_set_interface_groups(rfdd_handle *h, int32_t n_groups, const int32_t *group);
+
+/* The split made by rfdd_set_interface_groups: cls (s int32, may be NULL) receives, per
+ * interface unknown in interior-first order, its group when it is level 1 and -1 when it is
+ * level 2 (all -1 with the dense factorisation); *s2 (may be NULL) the level-2 count (s with the
+ * dense factorisation). */
+int rfdd_interface_levels(const rfdd_handle *h, int32_t *cls, int64_t *s2);
+
 /* Device workspaces of a handle come from the device's default stream-ordered memory pool, on
  * the handle's stream.  Freed workspaces stay in that pool for reuse by later solves and handles
  * of the process (its release threshold is raised at the first rfdd_setup on a device); a caller

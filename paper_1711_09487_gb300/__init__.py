@@ -45,7 +45,7 @@ SYMBOLS = [
     "rfdd_server_default_options", "rfdd_server_create", "rfdd_server_add_pencil", "rfdd_server_submit",
     "rfdd_server_wait", "rfdd_server_submit_pencil", "rfdd_server_request_info", "rfdd_server_get_stats", "rfdd_server_remove_pencil",
     "rfdd_server_destroy", "rfdd_autotune", "rfdd_autotune_table",
-    "rfdd_rfkrylov",
+    "rfdd_rfkrylov", "rfdd_set_interface_groups", "rfdd_interface_levels",
 ]
 
 
@@ -126,6 +126,8 @@ def load(path: str | None = None):
     lib.rfdd_setup.argtypes = [C.POINTER(rfdd_csr), C.POINTER(rfdd_csr), C.POINTER(C.c_int32), i32,
                                C.POINTER(rfdd_options), C.POINTER(vp)]
     lib.rfdd_layout.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i32), C.POINTER(i64)]
+    lib.rfdd_set_interface_groups.argtypes = [vp, i32, C.POINTER(i32)]
+    lib.rfdd_interface_levels.argtypes = [vp, C.POINTER(i32), C.POINTER(i64)]
     lib.rfdd_destroy.argtypes = [vp]
     lib.rfdd_destroy.restype = None
     lib.rfdd_solve.argtypes = [vp, C.c_double, C.c_double, i32, C.POINTER(vp)]
@@ -278,6 +280,26 @@ def rfdd_layout(h: Handle):
     _check(lib.rfdd_layout(h.ptr, off.ctypes.data_as(C.POINTER(C.c_int64)),
                            perm.ctypes.data_as(C.POINTER(C.c_int64)), None, None))
     return off, perm, int(ss.value)
+
+
+def rfdd_set_interface_groups(h: Handle, group) -> None:
+    """Two-level interface factorisation for these subdomain group labels (None: dense S)."""
+    if group is None:
+        _check(load().rfdd_set_interface_groups(h.ptr, 0, None))
+        return
+    g = np.ascontiguousarray(group, dtype=np.int32)
+    ng = int(g.max()) + 1 if g.size else 0
+    _check(load().rfdd_set_interface_groups(h.ptr, ng, g.ctypes.data_as(C.POINTER(C.c_int32))))
+
+
+def rfdd_interface_levels(h: Handle):
+    """(cls, s2): per interface unknown its level-1 group or -1, and the level-2 count."""
+    lib = load()
+    _, _, s = rfdd_layout(h)
+    cls = np.zeros(s, dtype=np.int32)
+    s2 = C.c_int64()
+    _check(lib.rfdd_interface_levels(h.ptr, cls.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(s2)))
+    return cls, int(s2.value)
 
 
 class Result:
@@ -645,9 +667,12 @@ def rfdd_profile_busy(kind: int) -> float:
     return ms.value
 
 
-def solve(A, M, part, p, alpha, beta, n_nodes, **opts):
-    """Convenience: setup + solve + host results (evals, evecs in original order, resid, info)."""
+def solve(A, M, part, p, alpha, beta, n_nodes, groups=None, **opts):
+    """Convenience: setup + solve + host results (evals, evecs in original order, resid, info).
+    ``groups``: subdomain group labels for the two-level interface factorisation."""
     h = rfdd_setup(A, M, part, p, rfdd_default_options(**opts))
+    if groups is not None:
+        rfdd_set_interface_groups(h, groups)
     r = rfdd_solve(h, alpha, beta, n_nodes)
     ev, X, rs = rfdd_result_get(r)
     return ev, X, rs, rfdd_result_info(r)

@@ -166,6 +166,11 @@ struct SolveShape {
   double guard_frac = 0.3;
   int pack_factors = -1;  // rfdd_options.pack_factors
   size_t mem_budget = 0;
+  // two-level interface factorisation: groups (0 = one dense S per node), level-2 size, and per
+  // group the level-1 size n1 and the level-2 border n2
+  int lv_groups = 0;
+  int64_t lv_s2 = 0;
+  const int64_t *lv_n1 = nullptr, *lv_n2 = nullptr;
 };
 // whether the mixed solve keeps tile copies of its factors (rfdd_options.pack_factors)
 bool packed_factors(const SolveShape &g, int nc);

@@ -669,4 +669,90 @@ template void scatter_sub_iface<cx<float>>(cudaStream_t, const int32_t *, int, i
 template void scatter_sub_iface<cx<double>>(cudaStream_t, const int32_t *, int, int64_t, const cx<double> *, int64_t,
                                             cx<double> *, int64_t, int);
 
+
+// ---------------------------------------------------------------------------------------
+// Two-level interface factorisation: assembly of the level storage of each node
+// (S2 = level-2 block s2 x s2 at offset 0, then one bordered block per group)
+// ---------------------------------------------------------------------------------------
+// L_l[edst[e]] = (a - z_l m) of interface CSR entry e0 + e, for entries with edst[e] >= 0
+template <typename T>
+__global__ void assemble_iface_levels_kernel(const double *__restrict__ av, const double *__restrict__ mv, int64_t e0,
+                                             int64_t ne, const int64_t *__restrict__ edst,
+                                             const cx<double> *__restrict__ zz, T *__restrict__ L, int64_t tsz) {
+  const int l = blockIdx.y;
+  const cx<double> z = zz[l];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t d = edst[e];
+    if (d >= 0) L[(int64_t)l * tsz + d] = Shift<T>::make(av[e0 + e], mv[e0 + e], z);
+  }
+}
+template <typename T>
+void assemble_iface_levels(cudaStream_t st, const DevPencil &P, int64_t e0, int64_t ne, const int64_t *edst,
+                           const cx<double> *z_dev, int nnodes, T *L, int64_t tsz) {
+  if (ne <= 0) return;
+  assemble_iface_levels_kernel<T><<<dim3(std::min<int64_t>(4096, ceil_div(ne, 256)), nnodes), 256, 0, st>>>(
+      P.a, P.m, e0, ne, edst, z_dev, L, tsz);
+  RFDD_CHECK_LAUNCH();
+}
+
+// Trailing block of subdomain j's bordered factor into the level storage: entry (t, u) goes to
+// S2[r[t]][r[u]] when both are level 2, else to the group block at (q[t], q[u]).
+template <typename T>
+__global__ void scatter_schur_levels_kernel(int p, int j, int dj, int sj, const int32_t *__restrict__ q,
+                                            const int32_t *__restrict__ r, int64_t s2, int64_t gbase, int64_t Dg,
+                                            const int64_t *__restrict__ boff, const T *__restrict__ base,
+                                            T *__restrict__ L, int64_t tsz) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int l = blockIdx.y;
+  if (e >= (int64_t)sj * sj) return;
+  const int t = (int)(e / sj), u = (int)(e % sj);
+  const int64_t Dj = (int64_t)dj + sj;
+  const T v = base[boff[(int64_t)l * p + j] + (int64_t)dj * Dj + dj + (int64_t)t * Dj + u];
+  const int rt = r[t], ru = r[u];
+  T *dst = L + (int64_t)l * tsz + ((rt >= 0 && ru >= 0) ? (int64_t)rt * s2 + ru : gbase + (int64_t)q[t] * Dg + q[u]);
+  *dst = *dst + v;
+}
+template <typename T>
+void scatter_schur_levels(cudaStream_t st, int p, int j, int dj, int sj, const int32_t *q_j, const int32_t *r_j,
+                          int64_t s2, int64_t gbase, int64_t Dg, const int64_t *dev_boff, const T *base, int nnodes,
+                          T *L, int64_t tsz) {
+  if (sj <= 0) return;
+  scatter_schur_levels_kernel<T><<<dim3(ceil_div((int64_t)sj * sj, 256), nnodes), 256, 0, st>>>(
+      p, j, dj, sj, q_j, r_j, s2, gbase, Dg, dev_boff, base, L, tsz);
+  RFDD_CHECK_LAUNCH();
+}
+
+// Trailing block of group g's bordered factor (n2 x n2 at gbase + n1 (Dg + 1), ld Dg) added to
+// S2 at the level-2 positions i2g[0..n2)
+template <typename T>
+__global__ void scatter_trail_levels_kernel(const int32_t *__restrict__ i2g, int n1, int n2, int64_t gbase,
+                                            int64_t s2, T *__restrict__ L, int64_t tsz) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int l = blockIdx.y;
+  if (e >= (int64_t)n2 * n2) return;
+  const int t = (int)(e / n2), u = (int)(e % n2);
+  const int64_t Dg = (int64_t)n1 + n2;
+  T *Ll = L + (int64_t)l * tsz;
+  const T v = Ll[gbase + (int64_t)n1 * Dg + n1 + (int64_t)t * Dg + u];
+  T *dst = Ll + (int64_t)i2g[t] * s2 + i2g[u];
+  *dst = *dst + v;
+}
+template <typename T>
+void scatter_trail_levels(cudaStream_t st, const int32_t *i2g, int n1, int n2, int64_t gbase, int64_t s2, int nnodes,
+                          T *L, int64_t tsz) {
+  if (n2 <= 0) return;
+  scatter_trail_levels_kernel<T><<<dim3(ceil_div((int64_t)n2 * n2, 256), nnodes), 256, 0, st>>>(i2g, n1, n2, gbase,
+                                                                                                  s2, L, tsz);
+  RFDD_CHECK_LAUNCH();
+}
+
+#define RFDD_INST_LEVELS(T)                                                                                      \
+  template void assemble_iface_levels<T>(cudaStream_t, const DevPencil &, int64_t, int64_t, const int64_t *,    \
+                                         const cx<double> *, int, T *, int64_t);                                \
+  template void scatter_schur_levels<T>(cudaStream_t, int, int, int, int, const int32_t *, const int32_t *,     \
+                                        int64_t, int64_t, int64_t, const int64_t *, const T *, int, T *, int64_t); \
+  template void scatter_trail_levels<T>(cudaStream_t, const int32_t *, int, int, int64_t, int64_t, int, T *, int64_t);
+RFDD_INST_LEVELS(cx<float>)
+RFDD_INST_LEVELS(cx<double>)
+
 }  // namespace rfdd

@@ -71,6 +71,24 @@ template <typename T>
 void scatter_schur(cudaStream_t st, const DevDD &dd, int j, int dj, int sj, int64_t sidx_start,
                    const int64_t *dev_boff, const T *base, int nnodes, T *S);
 
+// Two-level interface factorisation (storage per node: S2 (s2 x s2) at 0, then the bordered
+// block of each group; tsz elements per node, node l at L + l*tsz).
+// L_l[edst[e]] = a - z_l m for the interface CSR entries e0 + e, e < ne, with edst[e] >= 0.
+template <typename T>
+void assemble_iface_levels(cudaStream_t st, const DevPencil &P, int64_t e0, int64_t ne, const int64_t *edst,
+                           const cx<double> *z_dev, int nnodes, T *L, int64_t tsz);
+// Adds the trailing s_j x s_j block of subdomain j's bordered factor: entry (t, u) to
+// S2[r_j[t]][r_j[u]] if both are >= 0, else to the group block at gbase (ld Dg), (q_j[t], q_j[u]).
+// Called for j = 0..p-1 in order (reproducible sums).
+template <typename T>
+void scatter_schur_levels(cudaStream_t st, int p, int j, int dj, int sj, const int32_t *q_j, const int32_t *r_j,
+                          int64_t s2, int64_t gbase, int64_t Dg, const int64_t *dev_boff, const T *base, int nnodes,
+                          T *L, int64_t tsz);
+// S2[i2g[t]][i2g[u]] += trailing n2 x n2 block of the group block at gbase (n1 + n2 square).
+template <typename T>
+void scatter_trail_levels(cudaStream_t st, const int32_t *i2g, int n1, int n2, int64_t gbase, int64_t s2, int nnodes,
+                          T *L, int64_t tsz);
+
 template <typename TO, typename TI>
 void convert(cudaStream_t st, const TI *x, TO *y, int64_t n);
 // copy a real block into complex (imag 0), possibly replicated for several nodes

@@ -301,6 +301,40 @@ struct rfdd_handle {
   std::vector<double> rr_theta;
   Buf X0;
   int64_t m0 = 0;
+  // Interface rows of the union CSR, kept for the two-level split: per interface row a, entries
+  // [if_rp[a], if_rp[a+1]) (relative to the first interface row's first entry), their column in
+  // interface numbering (-1: an interior column) and whether A or M is nonzero there.
+  int64_t if_e0 = 0;  // union-CSR index of the first interface row's first entry
+  std::vector<int64_t> if_rp;
+  std::vector<int32_t> if_cl;
+  std::vector<char> if_nz;
+  // Two-level interface factorisation (rfdd_set_interface_groups): the block inverse of
+  // Eq. (inv_dd2) applied to S(z) with groups of subdomains as its subdomains.
+  struct Levels {
+    int G = 0;                           // groups; 0 = one dense S per node
+    std::vector<int32_t> group;          // group of each subdomain
+    std::vector<int32_t> cls;            // per interface node: its group if level 1, else -1
+    int64_t s1 = 0, s2 = 0;              // level-1 and level-2 node counts
+    std::vector<int64_t> n1, n2, g1off;  // per group |I1_g|, |I2_g|, first level-order row of I1_g
+    std::vector<int64_t> goff;           // per group: element offset of its block in a node's storage
+    std::vector<int64_t> poff, ioff;     // per group: pivot and inverse-block offsets within a node
+    int64_t tsz = 0, psz = 0, isz = 0;   // per node: storage, pivot and inverse-block elements
+    std::vector<int32_t> lorder, lpos;   // level order -> interface index, and its inverse
+    std::vector<int32_t> i2g;            // I2_g as level-2 positions, concatenated over groups
+    std::vector<int64_t> i2g_off;        // G + 1 offsets into i2g
+    std::vector<int64_t> edst;           // per interface CSR entry: offset in a node's storage or -1
+    std::vector<int32_t> q, r;           // per sidx entry: position in the group block / level-2 position
+    Buf lorder_dev, lpos_dev, i2g_dev, edst_dev, q_dev, r_dev;
+    void clear() {
+      G = 0;
+      s1 = s2 = tsz = psz = isz = 0;
+      for (auto *v : {&group, &cls, &lorder, &lpos, &i2g, &q, &r}) v->clear();
+      for (auto *v : {&n1, &n2, &g1off, &goff, &poff, &ioff, &i2g_off, &edst}) v->clear();
+      for (Buf *b : {&lorder_dev, &lpos_dev, &i2g_dev, &edst_dev, &q_dev, &r_dev}) b->release();
+    }
+  } lv;
+  Buf Lfac, pivL, LLinv, LUinv;          // two-level factors, nc nodes x (tsz, psz, isz)
+  std::vector<PkOff> pkG;                // packed operands of the group blocks (node, group)
 };
 
 namespace {
@@ -728,6 +762,18 @@ void do_upload(rfdd_handle *h) {
   h->dd.sidx = h->sidx_dev.as<int32_t>();
   h->dd.sidx_off = h->sidx_off_dev.as<int64_t>();
   h->dd.posmap = h->posmap.as<int32_t>();
+  // interface rows, for the two-level split of the interface
+  h->if_e0 = rp[dsum];
+  h->if_rp.assign(s + 1, 0);
+  h->if_cl.clear();
+  h->if_nz.clear();
+  for (int64_t a = 0; a < s; ++a) {
+    for (int64_t e = rp[dsum + a]; e < rp[dsum + a + 1]; ++e) {
+      h->if_cl.push_back(cl[e] >= dsum ? (int32_t)(cl[e] - dsum) : -1);
+      h->if_nz.push_back(av[e] != 0.0 || mv[e] != 0.0);
+    }
+    h->if_rp[a + 1] = (int64_t)h->if_cl.size();
+  }
   // M_E != 0 iff some interior row has a nonzero M entry in an interface column
   h->has_me = false;
   for (int64_t r = 0; r < dsum && !h->has_me; ++r)
@@ -737,11 +783,145 @@ void do_upload(rfdd_handle *h) {
   rp.shrink_to_fit(); cl.shrink_to_fit(); av.shrink_to_fit(); mv.shrink_to_fit(); posmap.shrink_to_fit();
 }
 
+constexpr int NBO_LU = 256;  // outer block (trailing-update depth) of the factorisations
+constexpr int NBO = 256;     // outer block of the triangular solves
+
+// Two-level split of the interface for a grouping of the subdomains (rfdd_set_interface_groups).
+// S(z)[a][b] can be nonzero only when interface nodes a and b touch a common subdomain (a term
+// of E^T B^{-1} E) or are coupled in C or M_C.  Node a is level 1 of group g when every
+// subdomain it touches is in g (at least one) and no node it is coupled to in C or M_C is such a
+// candidate of another group; all other nodes are level 2.  S restricted to the level-1 nodes is
+// then block diagonal over the groups, and I2_g (the level-2 nodes S can couple to I1_g) are the
+// level-2 nodes touched by a subdomain of g or coupled in C / M_C to a node of I1_g.
+void build_levels(rfdd_handle *h, int G, const int32_t *group) {
+  auto &L = h->lv;
+  L.clear();
+  if (G <= 0) return;
+  const int p = h->p;
+  const int64_t s = h->s;
+  L.G = G;
+  L.group.assign(group, group + p);
+  std::vector<int32_t> touch(s, -2);  // -2 none, -1 several groups, else the one group
+  for (int j = 0; j < p; ++j)
+    for (int64_t t = h->sidx_off[j]; t < h->sidx_off[j + 1]; ++t) {
+      const int32_t a = h->sidx[t];
+      touch[a] = touch[a] == -2 ? group[j] : (touch[a] == group[j] ? touch[a] : -1);
+    }
+  L.cls.assign(s, -1);
+  for (int64_t a = 0; a < s; ++a) {
+    if (touch[a] < 0) continue;
+    bool ok = true;
+    for (int64_t e = h->if_rp[a]; e < h->if_rp[a + 1] && ok; ++e) {
+      const int32_t b = h->if_cl[e];
+      if (b >= 0 && h->if_nz[e] && touch[b] >= 0 && touch[b] != touch[a]) ok = false;
+    }
+    if (ok) L.cls[a] = touch[a];
+  }
+  // level order: I1_0, I1_1, ..., I2 (each ascending)
+  L.n1.assign(G, 0);
+  L.n2.assign(G, 0);
+  L.g1off.assign(G + 1, 0);
+  std::vector<int32_t> pos1(s, -1), pos2(s, -1);  // index in I1_g, index in I2
+  for (int64_t a = 0; a < s; ++a)
+    if (L.cls[a] >= 0) pos1[a] = (int32_t)L.n1[L.cls[a]]++;
+    else pos2[a] = (int32_t)L.s2++;
+  for (int g = 0; g < G; ++g) L.g1off[g + 1] = L.g1off[g] + L.n1[g];
+  L.s1 = L.g1off[G];
+  L.lorder.assign(s, 0);
+  L.lpos.assign(s, 0);
+  for (int64_t a = 0; a < s; ++a) {
+    const int64_t q = L.cls[a] >= 0 ? L.g1off[L.cls[a]] + pos1[a] : L.s1 + pos2[a];
+    L.lorder[q] = (int32_t)a;
+    L.lpos[a] = (int32_t)q;
+  }
+  // I2_g, and each group block's position of its level-2 nodes
+  std::vector<std::vector<int32_t>> i1(G);
+  for (int64_t a = 0; a < s; ++a)
+    if (L.cls[a] >= 0) i1[L.cls[a]].push_back((int32_t)a);
+  L.i2g_off.assign(G + 1, 0);
+  std::vector<int32_t> gpos2(s, -1);  // index of a level-2 node in I2_g of the group at hand
+  L.edst.assign(h->if_cl.size(), -1);
+  L.q.assign(h->sidx.size(), -1);
+  L.r.assign(h->sidx.size(), -1);
+  L.goff.assign(G, 0);
+  L.poff.assign(G, 0);
+  L.ioff.assign(G, 0);
+  int64_t tot = L.s2 * L.s2, ptot = L.s2, itot = block_inverse_elems(L.s2, NBO);
+  for (int g = 0; g < G; ++g) {
+    std::vector<char> near(s, 0);
+    for (int j = 0; j < p; ++j)
+      if (group[j] == g)
+        for (int64_t t = h->sidx_off[j]; t < h->sidx_off[j + 1]; ++t) near[h->sidx[t]] = 1;
+    for (int32_t a : i1[g])
+      for (int64_t e = h->if_rp[a]; e < h->if_rp[a + 1]; ++e)
+        if (h->if_cl[e] >= 0 && h->if_nz[e]) near[h->if_cl[e]] = 1;
+    std::vector<int32_t> j2;
+    for (int64_t b = 0; b < s; ++b)
+      if (near[b] && L.cls[b] < 0) j2.push_back((int32_t)b);
+    L.n2[g] = (int64_t)j2.size();
+    for (size_t k = 0; k < j2.size(); ++k) {
+      gpos2[j2[k]] = (int32_t)k;
+      L.i2g.push_back(pos2[j2[k]]);
+    }
+    L.i2g_off[g + 1] = (int64_t)L.i2g.size();
+    const int64_t n1 = L.n1[g], Dg = n1 + L.n2[g];
+    L.goff[g] = tot;
+    L.poff[g] = ptot;
+    L.ioff[g] = itot;
+    tot += Dg * Dg;
+    ptot += n1;
+    itot += block_inverse_elems(n1, NBO);
+    // position of node x in group g's bordered block (-1: not in it)
+    auto gp = [&](int32_t x) -> int64_t {
+      if (L.cls[x] == g) return pos1[x];
+      if (L.cls[x] < 0 && gpos2[x] >= 0) return n1 + gpos2[x];
+      return -1;
+    };
+    // C - z M_C entries in the group block: rows of I1_g, and rows of I2_g at columns of I1_g
+    for (int32_t a : i1[g])
+      for (int64_t e = h->if_rp[a]; e < h->if_rp[a + 1]; ++e) {
+        const int32_t b = h->if_cl[e];
+        if (b < 0) continue;
+        const int64_t cb = gp(b);
+        if (cb >= 0) L.edst[e] = L.goff[g] + (int64_t)pos1[a] * Dg + cb;
+      }
+    for (int32_t a : j2)
+      for (int64_t e = h->if_rp[a]; e < h->if_rp[a + 1]; ++e) {
+        const int32_t b = h->if_cl[e];
+        if (b >= 0 && L.cls[b] == g) L.edst[e] = L.goff[g] + (n1 + gpos2[a]) * Dg + pos1[b];
+      }
+    for (int j = 0; j < p; ++j)
+      if (group[j] == g)
+        for (int64_t t = h->sidx_off[j]; t < h->sidx_off[j + 1]; ++t) {
+          const int32_t a = h->sidx[t];
+          L.q[t] = (int32_t)gp(a);
+          L.r[t] = L.cls[a] < 0 ? pos2[a] : -1;
+        }
+    for (int32_t b : j2) gpos2[b] = -1;
+  }
+  // level-2 rows at level-2 columns go to S2
+  for (int64_t a = 0; a < s; ++a)
+    if (L.cls[a] < 0)
+      for (int64_t e = h->if_rp[a]; e < h->if_rp[a + 1]; ++e) {
+        const int32_t b = h->if_cl[e];
+        if (b >= 0 && L.cls[b] < 0) L.edst[e] = (int64_t)pos2[a] * L.s2 + pos2[b];
+      }
+  L.tsz = tot;
+  L.psz = ptot;
+  L.isz = itot;
+  cudaStream_t st = h->st;
+  upload(L.lorder_dev, L.lorder, st);
+  upload(L.lpos_dev, L.lpos, st);
+  if (!L.i2g.empty()) upload(L.i2g_dev, L.i2g, st);
+  if (!L.edst.empty()) upload(L.edst_dev, L.edst, st);
+  upload(L.q_dev, L.q, st);
+  upload(L.r_dev, L.r, st);
+  RFDD_CUDA(cudaStreamSynchronize(st));
+}
+
 // ------------------------------------------------------------------------------------
 // precision-dependent parts
 // ------------------------------------------------------------------------------------
-constexpr int NBO_LU = 256;  // outer block (trailing-update depth) of the factorisations
-constexpr int NBO = 256;     // outer block of the triangular solves
 
 }  // namespace
 
@@ -754,12 +934,25 @@ static size_t factor_bytes_impl(const SolveShape &g, int nc, bool packed) {
   size_t e = 0;
   for (int j = 0; j < g.p; ++j) e += (size_t)g.D[j] * g.D[j];
   size_t b = (size_t)nc * e * scal;
-  b += (size_t)nc * g.s * g.s * scal * (g.keep_schur ? 2 : 1);
-  size_t inv = (size_t)block_inverse_elems(g.s, 256);  // inverted diagonal blocks of L and U
+  // interface factors: one dense S, or S2' and the bordered group blocks
+  size_t se = (size_t)g.s * g.s, sinv = (size_t)block_inverse_elems(g.s, 256), spk = se + 2 * sinv;
+  if (g.lv_groups > 0) {
+    se = (size_t)g.lv_s2 * g.lv_s2;
+    sinv = (size_t)block_inverse_elems(g.lv_s2, 256);
+    spk = se + 2 * sinv;
+    for (int k = 0; k < g.lv_groups; ++k) {
+      const size_t n1 = (size_t)g.lv_n1[k], n2 = (size_t)g.lv_n2[k], bi = (size_t)block_inverse_elems(n1, 256);
+      se += (n1 + n2) * (n1 + n2);
+      sinv += bi;
+      spk += n1 * n1 + 2 * n1 * n2 + 2 * bi;
+    }
+  }
+  b += (size_t)nc * se * scal * (g.keep_schur ? 2 : 1);
+  size_t inv = sinv;  // inverted diagonal blocks of L and U
   for (int j = 0; j < g.p; ++j) inv += (size_t)block_inverse_elems(g.d[j], 256);
   b += 2 * (size_t)nc * inv * scal;
   if (mixed && packed) {  // packed tensor-core copies of the solve operands (hi + lo)
-    size_t pk = (size_t)g.s * g.s + 2 * (size_t)block_inverse_elems(g.s, 256);
+    size_t pk = spk;
     for (int j = 0; j < g.p; ++j)
       pk += (size_t)g.D[j] * g.D[j] - (size_t)(g.D[j] - g.d[j]) * (g.D[j] - g.d[j]) +
             2 * (size_t)block_inverse_elems(g.d[j], 256);
@@ -810,12 +1003,18 @@ rfdd::SolveShape shape_of(const rfdd_handle *h) {
   g.m_align = h->opt.m_align;
   g.pack_factors = h->opt.pack_factors;
   g.mem_budget = h->opt.mem_budget;
+  g.lv_groups = h->lv.G;
+  g.lv_s2 = h->lv.s2;
+  g.lv_n1 = h->lv.n1.data();
+  g.lv_n2 = h->lv.n2.data();
   return g;
 }
 
 size_t factor_bytes(const rfdd_handle *h, int nc) { return rfdd::factor_bytes_of(shape_of(h), nc); }
 
 void pack_factor_operands(rfdd_handle *h);
+template <typename Tf>
+void factor_levels(rfdd_handle *h, const Tf *base);
 
 template <typename Tf>
 void factor_impl(rfdd_handle *h) {
@@ -888,7 +1087,9 @@ void factor_impl(rfdd_handle *h) {
       }
     lu_block_inverses<Tf>(st, fi, NBO, li, ui);
   }
-  // a5: S(z) = C - z M_C + sum_j trailing_j, then LU
+  // a5: S(z) = C - z M_C + sum_j trailing_j, then LU (two levels when the subdomains are grouped)
+  if (h->lv.G > 0) factor_levels<Tf>(h, base);
+  else {
   h->Sfac.alloc((size_t)nc * s * s * sizeof(Tf));
   h->pivS.alloc((size_t)nc * s * sizeof(int));
   Tf *S = h->Sfac.as<Tf>();
@@ -929,6 +1130,7 @@ void factor_impl(rfdd_handle *h) {
     }
     lu_block_inverses<Tf>(st, fi, NBO, li, ui);
   }
+  }
   if constexpr (std::is_same<Tf, cx<float>>::value) {
     if (rfdd::packed_factors(shape_of(h), h->nnodes)) {
       // the solves read only the tile copies (and the inverted diagonal blocks): one copy of each
@@ -936,6 +1138,7 @@ void factor_impl(rfdd_handle *h) {
       pack_factor_operands(h);
       h->fac.release();  // stream-ordered: after the packing kernels
       h->Sfac.release();
+      h->Lfac.release();
     }
   }
   // how long the host took to issue the phase, against its device time (t_factor_ms): the
@@ -980,6 +1183,7 @@ void pack_factor_operands(rfdd_handle *h) {
   const int64_t s = h->s, bf = tc_packed_a_floats(NBO, NBO);
   h->pkB.assign((size_t)nc * p, {});
   h->pkS.assign((size_t)nc, {});
+  h->pkG.assign((size_t)nc * h->lv.G, {});
   int64_t tot = 0;
   auto take = [&](int64_t floats) {
     const int64_t o = tot;
@@ -999,10 +1203,25 @@ void pack_factor_operands(rfdd_handle *h) {
       }
     }
     auto &o = h->pkS[l];
-    const int64_t nblk = (s + NBO - 1) / NBO;
-    o.lu = take(tc_packed_a_floats(s, s));
-    o.li = take(nblk * bf);
-    o.ui = take(nblk * bf);
+    const int64_t sS = h->lv.G > 0 ? h->lv.s2 : s;  // two levels: S2' takes the place of S
+    const int64_t nblk = (sS + NBO - 1) / NBO;
+    if (sS > 0) {
+      o.lu = take(tc_packed_a_floats(sS, sS));
+      o.li = take(nblk * bf);
+      o.ui = take(nblk * bf);
+    }
+    for (int g = 0; g < h->lv.G; ++g) {
+      const int64_t n1 = h->lv.n1[g], n2 = h->lv.n2[g], nb1 = (n1 + NBO - 1) / NBO;
+      auto &og = h->pkG[(size_t)l * h->lv.G + g];
+      if (n1 == 0) continue;
+      og.lu = take(tc_packed_a_floats(n1, n1));
+      og.li = take(nb1 * bf);
+      og.ui = take(nb1 * bf);
+      if (n2 > 0) {
+        og.l21 = take(tc_packed_a_floats(n2, n1));
+        og.u12 = take(tc_packed_a_floats(n1, n2));
+      }
+    }
   }
   h->Pk.alloc((size_t)tot * sizeof(float));
   float *P = h->Pk.as<float>();
@@ -1029,9 +1248,31 @@ void pack_factor_operands(rfdd_handle *h) {
       blocks(h->BUinv.as<cx<float>>() + h->binvoff[(size_t)l * p + j], dj, o.ui);
     }
     const auto &o = h->pkS[l];
-    job(h->Sfac.as<cx<float>>() + (int64_t)l * s * s, s, s, s, o.lu);
-    blocks(h->SLinv.as<cx<float>>() + (int64_t)l * h->sinv_elems, s, o.li);
-    blocks(h->SUinv.as<cx<float>>() + (int64_t)l * h->sinv_elems, s, o.ui);
+    if (h->lv.G == 0) {
+      job(h->Sfac.as<cx<float>>() + (int64_t)l * s * s, s, s, s, o.lu);
+      blocks(h->SLinv.as<cx<float>>() + (int64_t)l * h->sinv_elems, s, o.li);
+      blocks(h->SUinv.as<cx<float>>() + (int64_t)l * h->sinv_elems, s, o.ui);
+      continue;
+    }
+    const auto &L = h->lv;
+    const cx<float> *T = h->Lfac.as<cx<float>>() + (int64_t)l * L.tsz;
+    const cx<float> *Li = h->LLinv.as<cx<float>>() + (int64_t)l * L.isz, *Ui = h->LUinv.as<cx<float>>() + (int64_t)l * L.isz;
+    if (L.s2 > 0) {
+      job(T, L.s2, L.s2, L.s2, o.lu);
+      blocks(Li, L.s2, o.li);
+      blocks(Ui, L.s2, o.ui);
+    }
+    for (int g = 0; g < L.G; ++g) {
+      const int64_t n1 = L.n1[g], n2 = L.n2[g], Dg = n1 + n2;
+      if (n1 == 0) continue;
+      const auto &og = h->pkG[(size_t)l * L.G + g];
+      const cx<float> *Bg = T + L.goff[g];
+      job(Bg, Dg, n1, n1, og.lu);
+      job(Bg + n1 * Dg, Dg, n2, n1, og.l21);
+      job(Bg + n1, Dg, n1, n2, og.u12);
+      blocks(Li + L.ioff[g], n1, og.li);
+      blocks(Ui + L.ioff[g], n1, og.ui);
+    }
   }
   tc_pack_a_batched(st, jobs);
 }
@@ -1059,7 +1300,15 @@ void solve_B(rfdd_handle *h, Tf *F, int64_t ldf, int64_t fs, int64_t m, const st
 }
 
 template <typename Tf>
+void solve_S_levels(rfdd_handle *h, Tf *G, int64_t gs, int64_t m, const std::vector<int> &nodes);
+
+template <typename Tf>
 void solve_S(rfdd_handle *h, Tf *G, int64_t ldg, int64_t gs, int64_t m, const std::vector<int> &nodes) {
+  if (h->lv.G > 0) {
+    RFDD_REQUIRE(ldg == m, RFDD_EINVAL, "two-level interface solve needs ldg == m");
+    solve_S_levels<Tf>(h, G, gs, m, nodes);
+    return;
+  }
   std::vector<SolveItem<Tf>> it;
   for (int l : nodes) {
     SolveItem<Tf> x;
@@ -1079,6 +1328,191 @@ void solve_S(rfdd_handle *h, Tf *G, int64_t ldg, int64_t gs, int64_t m, const st
     it.push_back(x);
   }
   lu_solve_batched<Tf>(h->st, it, NBO);
+}
+
+template <typename Tf>
+void border_gemm(cudaStream_t st, const std::vector<GemmItem<Tf>> &g, const std::vector<TcPackedA> &pa, double alpha,
+                 double beta);
+
+// ------------------------------------------------------------------------------------
+// Two-level interface factorisation (rfdd_set_interface_groups): Eq. (inv_dd2) applied to S(z)
+// with the subdomain groups as its subdomains.  Per node the level storage holds S2 (level-2
+// block, s2 x s2) and, per group g, the bordered block [[S(I1_g, I1_g), S(I1_g, I2_g)],
+// [S(I2_g, I1_g), 0]].  The bordered LU of each group block leaves -S21 S11^{-1} S12 in its
+// trailing block; their ordered sum into S2 gives S2' = S22 - sum_g S21 S11^{-1} S12, which is
+// factored densely.
+// ------------------------------------------------------------------------------------
+template <typename Tf>
+void factor_levels(rfdd_handle *h, const Tf *base) {
+  auto &L = h->lv;
+  cudaStream_t st = h->st;
+  const int nc = h->nnodes, p = h->p, G = L.G;
+  h->Lfac.alloc((size_t)nc * L.tsz * sizeof(Tf));
+  h->pivL.alloc((size_t)nc * std::max<int64_t>(L.psz, 1) * sizeof(int));
+  Tf *T = h->Lfac.as<Tf>();
+  RFDD_CUDA(cudaMemsetAsync(T, 0, (size_t)nc * L.tsz * sizeof(Tf), st));
+  assemble_iface_levels<Tf>(st, h->P, h->if_e0, (int64_t)L.edst.size(), L.edst_dev.as<int64_t>(),
+                            h->z_dev.as<cx<double>>(), nc, T, L.tsz);
+  for (int j = 0; j < p; ++j) {
+    const int g = L.group[j];
+    const int sj = (int)(h->sidx_off[j + 1] - h->sidx_off[j]);
+    scatter_schur_levels<Tf>(st, p, j, (int)h->d[j], sj, L.q_dev.as<int32_t>() + h->sidx_off[j],
+                             L.r_dev.as<int32_t>() + h->sidx_off[j], L.s2, L.goff[g], L.n1[g] + L.n2[g],
+                             h->boff_dev.as<int64_t>(), base, nc, T, L.tsz);
+  }
+  int *piv = h->pivL.as<int>();
+  std::vector<LuItem<Tf>> items;
+  for (int l = 0; l < nc; ++l)
+    for (int g = 0; g < G; ++g) {
+      if (L.n1[g] == 0) continue;
+      LuItem<Tf> it;
+      it.A = T + (int64_t)l * L.tsz + L.goff[g];
+      it.piv = piv + (int64_t)l * L.psz + L.poff[g];
+      it.dp = (int)L.n1[g];
+      it.D = it.ld = (int)(L.n1[g] + L.n2[g]);
+      items.push_back(it);
+    }
+  if (!items.empty()) lu_batched<Tf>(st, items, NBO_LU, h->status.as<int>());
+  for (int g = 0; g < G; ++g)
+    if (L.n1[g] > 0)
+      scatter_trail_levels<Tf>(st, L.i2g_dev.as<int32_t>() + L.i2g_off[g], (int)L.n1[g], (int)L.n2[g], L.goff[g],
+                               L.s2, nc, T, L.tsz);
+  if (L.s2 > 0) {
+    items.clear();
+    for (int l = 0; l < nc; ++l) {
+      LuItem<Tf> it;
+      it.A = T + (int64_t)l * L.tsz;
+      it.piv = piv + (int64_t)l * L.psz;
+      it.dp = it.D = it.ld = (int)L.s2;
+      items.push_back(it);
+    }
+    lu_batched<Tf>(st, items, NBO_LU, h->status.as<int>());
+  }
+  // inverted diagonal blocks of every level factor, for the triangular solves
+  h->LLinv.alloc((size_t)nc * L.isz * sizeof(Tf));
+  h->LUinv.alloc((size_t)nc * L.isz * sizeof(Tf));
+  std::vector<SolveItem<Tf>> fi;
+  std::vector<Tf *> li, ui;
+  for (int l = 0; l < nc; ++l)
+    for (int g = -1; g < G; ++g) {
+      const int64_t n = g < 0 ? L.s2 : L.n1[g];
+      if (n == 0) continue;
+      SolveItem<Tf> x;
+      x.LU = T + (int64_t)l * L.tsz + (g < 0 ? 0 : L.goff[g]);
+      x.piv = nullptr;
+      x.n = (int)n;
+      x.ld = (int)(g < 0 ? L.s2 : L.n1[g] + L.n2[g]);
+      x.X = nullptr;
+      x.ldx = x.ncols = 0;
+      fi.push_back(x);
+      const int64_t o = (int64_t)l * L.isz + (g < 0 ? 0 : L.ioff[g]);
+      li.push_back(h->LLinv.as<Tf>() + o);
+      ui.push_back(h->LUinv.as<Tf>() + o);
+    }
+  if (!fi.empty()) lu_block_inverses<Tf>(st, fi, NBO, li, ui);
+}
+
+// factor of level block g (-1: S2) of node l as a solve item on X (ld m)
+template <typename Tf>
+SolveItem<Tf> level_item(const rfdd_handle *h, int l, int g, Tf *X, int64_t m) {
+  const auto &L = h->lv;
+  SolveItem<Tf> x;
+  x.LU = h->Lfac.as<Tf>() + (int64_t)l * L.tsz + (g < 0 ? 0 : L.goff[g]);
+  x.piv = h->pivL.as<int>() + (int64_t)l * L.psz + (g < 0 ? 0 : L.poff[g]);
+  x.n = (int)(g < 0 ? L.s2 : L.n1[g]);
+  x.ld = (int)(g < 0 ? L.s2 : L.n1[g] + L.n2[g]);
+  x.X = X;
+  x.ldx = (int)m;
+  x.ncols = (int)m;
+  if (h->LLinv.p) {
+    const int64_t o = (int64_t)l * L.isz + (g < 0 ? 0 : L.ioff[g]);
+    x.Linv = h->LLinv.as<Tf>() + o;
+    x.Uinv = h->LUinv.as<Tf>() + o;
+    x.nbi = NBO;
+    if (g < 0 && !h->pkS.empty()) attach_packed(h, x, h->pkS[l], L.s2);
+    if (g >= 0 && !h->pkG.empty()) attach_packed(h, x, h->pkG[(size_t)l * L.G + g], L.n1[g]);
+  }
+  return x;
+}
+
+// Y = S(z_l)^{-1} Y through the level factors: with the rows in level order (u),
+//   w_g = L11_g^{-1} P_g u[I1_g];  u[I2] -= sum_g scatter(L21_g w_g);  u[I2] = S2'^{-1} u[I2];
+//   w_g -= U12_g u[I2_g];  u[I1_g] = U11_g^{-1} w_g.
+// G rows are interface-ordered, ld m; node list position i reads G + i * gs.
+template <typename Tf>
+void solve_S_levels_run(rfdd_handle *h, Tf *G, int64_t gs, int64_t m, const std::vector<int> &nl) {
+  const auto &L = h->lv;
+  cudaStream_t st = h->st;
+  const int64_t s = h->s, s1 = L.s1;
+  const int nn = (int)nl.size(), NG = L.G;
+  int64_t n2max = 1;
+  for (int g = 0; g < NG; ++g) n2max = std::max(n2max, L.n2[g]);
+  const int64_t us = s * m, hs = (int64_t)NG * n2max * m;
+  Buf U, Ht;
+  U.alloc((size_t)nn * us * sizeof(Tf));
+  Ht.alloc((size_t)nn * hs * sizeof(Tf));
+  Tf *u = U.as<Tf>(), *ht = Ht.as<Tf>();
+  gather_iface<Tf>(st, L.lorder_dev.as<int32_t>(), (int)s, m, G, gs, u, us, nn);
+  std::vector<SolveItem<Tf>> it;
+  for (int i = 0; i < nn; ++i)
+    for (int g = 0; g < NG; ++g)
+      if (L.n1[g] > 0) it.push_back(level_item<Tf>(h, nl[i], g, u + i * us + L.g1off[g] * m, m));
+  if (!it.empty()) {
+    apply_pivots<Tf>(st, it);
+    trsm_lower_unit<Tf>(st, it, NBO);
+  }
+  auto border = [&](bool lower) {
+    std::vector<GemmItem<Tf>> gi;
+    std::vector<TcPackedA> pa;
+    for (int i = 0; i < nn; ++i)
+      for (int g = 0; g < NG; ++g) {
+        const int64_t n1 = L.n1[g], n2 = L.n2[g], Dg = n1 + n2;
+        if (n1 == 0 || n2 == 0) continue;
+        const Tf *blk = h->Lfac.as<Tf>() + (int64_t)nl[i] * L.tsz + L.goff[g];
+        Tf *w = u + i * us + L.g1off[g] * m, *hh = ht + i * hs + (int64_t)g * n2max * m;
+        const auto *pk = h->pkG.empty() ? nullptr : &h->pkG[(size_t)nl[i] * NG + g];
+        if (lower) {
+          gi.push_back({blk + n1 * Dg, w, hh, (int)n2, (int)m, (int)n1, (int)Dg, (int)m, (int)m});
+          const auto pp = pk ? pk_ptrs(h, pk->l21, tc_packed_a_floats(n2, n1))
+                             : std::pair<const float *, const float *>{nullptr, nullptr};
+          pa.push_back(TcPackedA{pp.first, pp.second, tc_packed_a_ktiles(n1)});
+        } else {
+          gi.push_back({blk + n1, hh, w, (int)n1, (int)m, (int)n2, (int)Dg, (int)m, (int)m});
+          const auto pp = pk ? pk_ptrs(h, pk->u12, tc_packed_a_floats(n1, n2))
+                             : std::pair<const float *, const float *>{nullptr, nullptr};
+          pa.push_back(TcPackedA{pp.first, pp.second, tc_packed_a_ktiles(n2)});
+        }
+      }
+    if (!gi.empty()) border_gemm<Tf>(st, gi, pa, lower ? 1.0 : -1.0, lower ? 0.0 : 1.0);
+  };
+  border(true);
+  for (int g = 0; g < NG; ++g)
+    if (L.n1[g] > 0 && L.n2[g] > 0)
+      scatter_sub_iface<Tf>(st, L.i2g_dev.as<int32_t>() + L.i2g_off[g], (int)L.n2[g], m, ht + (int64_t)g * n2max * m,
+                            hs, u + s1 * m, us, nn);
+  if (L.s2 > 0) {
+    std::vector<SolveItem<Tf>> si;
+    for (int i = 0; i < nn; ++i) si.push_back(level_item<Tf>(h, nl[i], -1, u + i * us + s1 * m, m));
+    lu_solve_batched<Tf>(st, si, NBO);
+  }
+  for (int g = 0; g < NG; ++g)
+    if (L.n1[g] > 0 && L.n2[g] > 0)
+      gather_iface<Tf>(st, L.i2g_dev.as<int32_t>() + L.i2g_off[g], (int)L.n2[g], m, u + s1 * m, us,
+                       ht + (int64_t)g * n2max * m, hs, nn);
+  border(false);
+  if (!it.empty()) trsm_upper<Tf>(st, it, NBO);
+  gather_iface<Tf>(st, L.lpos_dev.as<int32_t>(), (int)s, m, u, us, G, gs, nn);
+}
+
+template <typename Tf>
+void solve_S_levels(rfdd_handle *h, Tf *G, int64_t gs, int64_t m, const std::vector<int> &nodes) {
+  bool all = (int)nodes.size() == h->nnodes;
+  for (size_t i = 0; i < nodes.size() && all; ++i) all = nodes[i] == (int)i;
+  if (all) {
+    solve_S_levels_run<Tf>(h, G, gs, m, nodes);
+    return;
+  }
+  for (int l : nodes) solve_S_levels_run<Tf>(h, G + (int64_t)l * gs, 0, m, std::vector<int>{l});
 }
 
 // Products on the eigenvector bases (Lanczos blocks, interior CholQR, Rayleigh-Ritz Gram
@@ -2438,6 +2872,11 @@ void factor(rfdd_handle *h) {
   h->Pk.release();
   h->pkB.clear();
   h->pkS.clear();
+  h->pkG.clear();
+  h->Lfac.release();
+  h->pivL.release();
+  h->LLinv.release();
+  h->LUinv.release();
   if (is_mixed(h)) factor_impl<cx<float>>(h);
   else factor_impl<cx<double>>(h);
 }
@@ -2924,6 +3363,39 @@ int rfdd_layout(const rfdd_handle *h, int64_t *off, int64_t *perm, int32_t *p_ou
   return RFDD_OK;
 }
 
+int rfdd_set_interface_groups(rfdd_handle *h, int32_t n_groups, const int32_t *group) {
+  if (!h || n_groups < 0 || (n_groups > 0 && !group)) return RFDD_EINVAL;
+  return guarded([&] {
+    AllocScope scope(h->st);
+    if (n_groups > 0) {
+      RFDD_REQUIRE(!h->opt.keep_schur, RFDD_EINVAL, "keep_schur needs the dense interface factorisation");
+      for (int j = 0; j < h->p; ++j)
+        RFDD_REQUIRE(group[j] >= 0 && group[j] < n_groups, RFDD_EINVAL, "group label out of range");
+    }
+    interior_join(h, false);
+    RFDD_CUDA(cudaStreamSynchronize(h->st));
+    // the factors of the previous split are no longer valid
+    for (Buf *b : {&h->fac, &h->pivB, &h->Sfac, &h->pivS, &h->Skeep, &h->BLinv, &h->BUinv, &h->SLinv, &h->SUinv,
+                   &h->Pk, &h->Lfac, &h->pivL, &h->LLinv, &h->LUinv})
+      b->release();
+    h->pkB.clear();
+    h->pkS.clear();
+    h->pkG.clear();
+    h->have_factors = false;
+    build_levels(h, n_groups, group);
+  });
+}
+
+int rfdd_interface_levels(const rfdd_handle *h, int32_t *cls, int64_t *s2) {
+  if (!h) return RFDD_EINVAL;
+  if (cls) {
+    if (h->lv.G > 0) std::copy(h->lv.cls.begin(), h->lv.cls.end(), cls);
+    else std::fill(cls, cls + h->s, -1);
+  }
+  if (s2) *s2 = h->lv.G > 0 ? h->lv.s2 : h->s;
+  return RFDD_OK;
+}
+
 void rfdd_destroy(rfdd_handle *h) {
   if (!h) return;
   if (h->I_thread.joinable()) h->I_thread.join();
@@ -2949,7 +3421,7 @@ int rfdd_release(rfdd_handle *h) {
     RFDD_CUDA(cudaStreamSynchronize(h->st));
     if (h->st2) RFDD_CUDA(cudaStreamSynchronize(h->st2));
     for (Buf *b : {&h->fac, &h->boff_dev, &h->Doff_dev, &h->pivB, &h->Sfac, &h->pivS, &h->Skeep, &h->BLinv,
-                   &h->BUinv, &h->SLinv, &h->SUinv, &h->Pk, &h->IBs, &h->Ipiv, &h->IRLinv, &h->IRUinv, &h->I_doff,
+                   &h->BUinv, &h->SLinv, &h->SUinv, &h->Pk, &h->Lfac, &h->pivL, &h->LLinv, &h->LUinv, &h->IBs, &h->Ipiv, &h->IRLinv, &h->IRUinv, &h->I_doff,
                    &h->I_boffr_dev, &h->I_zs, &h->Q, &h->Zb, &h->X0})
       b->release();
     h->have_factors = false;
@@ -3051,22 +3523,13 @@ int rfdd_shifted_solve(rfdd_handle *h, int32_t node, int32_t which, int32_t j, i
         si[0].n = (int)h->d[j];
         si[0].ld = (int)h->D[j];
         attach_binv(h, si[0], node, j);
+        si[0].X = t.as<Tf>();
+        si[0].ldx = (int)nrhs;
+        si[0].ncols = (int)nrhs;
+        lu_solve_batched<Tf>(st, si, NBO);
       } else {
-        si[0].LU = h->Sfac.as<Tf>() + (int64_t)node * h->s * h->s;
-        si[0].piv = h->pivS.as<int>() + (int64_t)node * h->s;
-        si[0].n = (int)h->s;
-        si[0].ld = (int)h->s;
-        if (h->SLinv.p) {
-          si[0].Linv = h->SLinv.as<Tf>() + (int64_t)node * h->sinv_elems;
-          si[0].Uinv = h->SUinv.as<Tf>() + (int64_t)node * h->sinv_elems;
-          si[0].nbi = NBO;
-          if (!h->pkS.empty()) attach_packed(h, si[0], h->pkS[node], h->s);
-        }
+        solve_S<Tf>(h, t.as<Tf>(), nrhs, 0, nrhs, std::vector<int>{(int)node});
       }
-      si[0].X = t.as<Tf>();
-      si[0].ldx = (int)nrhs;
-      si[0].ncols = (int)nrhs;
-      lu_solve_batched<Tf>(st, si, NBO);
       convert<cx<double>, Tf>(st, t.as<Tf>(), r64.as<cx<double>>(), rows * nrhs);
       RFDD_CUDA(cudaMemcpyAsync(X, r64.p, (size_t)rows * nrhs * sizeof(cx<double>), cudaMemcpyDeviceToHost, st));
       RFDD_CUDA(cudaStreamSynchronize(st));

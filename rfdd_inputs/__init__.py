@@ -350,6 +350,12 @@ WORKLOADS = {
     "q1_3d_12": lambda: _q1_workload("q1_3d_12", 12, 3, (2, 2, 2), 8, 27, 6, "midpoint"),
     "q1_3d_16": lambda: _q1_workload("q1_3d_16", 16, 3, (2, 2, 2), 20, 60, 8, "midpoint"),
     "q1_2d_64": lambda: _q1_workload("q1_2d_64", 64, 2, (2, 2), 40, 120, 8, "midpoint"),
+    # many subdomains, for the two-level interface factorisation (groups of subdomains)
+    "q1_2d_49_p16": lambda: _q1_workload("q1_2d_49_p16", 49, 2, (4, 4), 21, 60, 6, "midpoint"),
+    "q1_3d_24_p64": lambda: _q1_workload("q1_3d_24_p64", 24, 3, (4, 4, 4), 30, 80, 8, "midpoint"),
+    # 3-D Q1, 48^3, 4 x 4 x 4 subdomains (s = 19,467 against d_j of 1,331-1,728): the dense S(zeta)
+    # dominates the factorisation; eigenvalues 100..200, 8 midpoint nodes
+    "q1_3d_48_p64": lambda: _q1_workload("q1_3d_48_p64", 48, 3, (4, 4, 4), 100, 200, 8, "midpoint"),
     # FDmesh2 of the paper's RF-KRYLOV / RF-DDES comparison: 5-point FD Laplacian, M = I, 500^2
     # grid (n = 250,000), the 100 algebraically smallest eigenvalues, Nc = 2 midpoint nodes; an
     # 8 x 8 separator grid (64 subdomains of about 62^2, s = 6,951) so that the dense
