@@ -6,6 +6,9 @@
 
 namespace rfdd {
 
+// SM count of the current device (cached per device)
+int sm_count();
+
 constexpr int MAXB = 64;      // matrices per launch (descriptors travel as kernel parameters)
 constexpr int LU_NB = 32;     // tournament panel width (pivot columns per inner step)
 

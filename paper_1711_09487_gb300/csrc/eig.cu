@@ -16,25 +16,55 @@ struct SymBatchP {
   SymItem it[EIG_MAXB];
 };
 
+// Block-wide sum, the same value in every thread.  One thread adds the warp partials (FP64
+// arithmetic is scarce on this GPU: every thread adding them would cost nw FP64 adds each).
 __device__ double block_sum(double v, double *red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   __syncthreads();
   if ((threadIdx.x & 31) == 0) red[w] = v;
   __syncthreads();
-  double s = 0.0;
-  for (int q = 0; q < nw; ++q) s += red[q];
-  return s;
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int q = 0; q < nw; ++q) s += red[q];
+    red[32] = s;
+  }
+  __syncthreads();
+  return red[32];
 }
 
-// Step i, part 1: Householder vector for row i (columns i+1..n-1), LAPACK convention
-// H_i = I - tau v v^T with v[0] = 1, H_i x = beta e_1.
-__global__ void house_kernel(SymBatchP b, int i) {
+// Householder tridiagonalisation, one pass over the trailing block per step.  Step i reflects row
+// i (columns i+1..n-1) with H_i = I - tau v v^T, v[0] = 1, H_i x = beta e_1 (LAPACK convention;
+// v is kept in row i for the back-transformation); the trailing block then takes the rank-2
+// update -v q^T - q v^T with p = tau H_t v, q = p - (tau/2)(p^T v) v.  The update of step i-1 is
+// applied lazily: house_kernel(i) forms q_{i-1} and applies it to row i only (O(n) work: on this
+// GPU one SM's FP64 rate is far too low for more), and update_symv_kernel(i) applies it to rows
+// and columns i+1..n-1 while forming p_i from the updated entries, so each step reads and writes
+// the trailing block once.
+
+// Step i, part 1 (one CTA per item): q_{i-1} into qbuf, row i updated by step i-1, then the
+// Householder vector of row i.
+__global__ void __launch_bounds__(512) house_kernel(SymBatchP b, int i, double *qbuf, int64_t qstride) {
   SymItem it = b.it[blockIdx.x];
   const int n = it.n;
   if (i >= n) return;
+  double *q = qbuf + (int64_t)blockIdx.x * qstride;
   double *row = it.H + (int64_t)i * it.ld;
-  __shared__ double red[32];
+  __shared__ double red[33];
+  const int ip = i - 1;
+  if (ip >= 0 && ip < n - 2) {
+    // p_{i-1} covers rows i..n-1 (work[0..len)); v_{i-1} is row i-1 from column i on
+    const int len = n - i;
+    const double *v = it.H + (int64_t)ip * it.ld + i;
+    double ss = 0.0;
+    for (int k = threadIdx.x; k < len; k += blockDim.x) ss = fma(it.work[k], v[k], ss);
+    const double K = 0.5 * it.tau[ip] * block_sum(ss, red);
+    for (int k = threadIdx.x; k < len; k += blockDim.x) q[i + k] = it.work[k] - K * v[k];
+    __syncthreads();
+    const double vi = v[0], qi = q[i];
+    for (int k = threadIdx.x; k < len; k += blockDim.x) row[i + k] = fma(-qi, v[k], fma(-vi, q[i + k], row[i + k]));
+    __syncthreads();
+  }
   if (i >= n - 1) {
     if (threadIdx.x == 0) { it.d[i] = row[i]; it.tau[i] = 0.0; }
     return;
@@ -68,43 +98,47 @@ __global__ void house_kernel(SymBatchP b, int i) {
   if (threadIdx.x == 0) x[0] = 1.0;
 }
 
-// Step i, part 2: p = tau * H_t v (H_t = trailing block), warp per row.
-__global__ void symv_kernel(SymBatchP b, int i) {
+// Step i, part 2 (TRD_WPR warps per row r of the trailing block i+1..n-1): apply step i-1's rank-2
+// update as two FMAs (the FP64 pipes bound this kernel; the block stays symmetric to rounding, a
+// backward perturbation of the order of the update's rounding), then p_i[r] = tau_i (H_t v_i)[r]
+// into work.  Runs for i <= n-2 (at i = n-2 only the pending update is left).
+constexpr int TRD_WPR = 2;
+__global__ void __launch_bounds__(256) update_symv_kernel(SymBatchP b, int i, const double *qbuf, int64_t qstride) {
   SymItem it = b.it[blockIdx.y];
   const int n = it.n;
-  if (i >= n - 2) return;
+  if (i > n - 2) return;
   const int len = n - i - 1;
-  const int r = (blockIdx.x * blockDim.x + threadIdx.x) / 32;
-  const int lane = threadIdx.x & 31;
-  if (r >= len) return;
-  const double *v = it.H + (int64_t)i * it.ld + i + 1;
-  const double *h = it.H + (int64_t)(i + 1 + r) * it.ld + i + 1;
+  constexpr int TPR = 32 * TRD_WPR;                 // threads per row
+  const int rloc = threadIdx.x / TPR, tr = threadIdx.x % TPR;
+  const int r = blockIdx.x * (256 / TPR) + rloc;
+  __shared__ double part[256 / 32];
+  const int c0 = i + 1;
+  const bool upd = i >= 1 && i - 1 < n - 2;
+  const bool sym = i < n - 2;
   double s = 0.0;
-  for (int c = lane; c < len; c += 32) s = fma(h[c], v[c], s);
+  if (r < len) {
+    double *h = it.H + (int64_t)(c0 + r) * it.ld + c0;
+    const double *v = it.H + (int64_t)i * it.ld + c0;         // v_i (row i)
+    const double *vp = it.H + (int64_t)(i - 1) * it.ld + c0;  // v_{i-1} from column i+1 on
+    const double *q = qbuf + (int64_t)blockIdx.y * qstride + c0;
+    const double vr = upd ? vp[r] : 0.0, qr = upd ? q[r] : 0.0;
+    for (int c = tr; c < len; c += TPR) {
+      double h0 = h[c];
+      if (upd) {
+        h0 = fma(-qr, vp[c], fma(-vr, q[c], h0));
+        h[c] = h0;
+      }
+      s = fma(h0, v[c], s);
+    }
+  }
+  if (!sym) return;  // uniform over the block
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if (lane == 0) it.work[r] = it.tau[i] * s;
-}
-
-// Step i, part 3: H_t -= v q^T + q v^T, q = p - (tau/2)(p^T v) v.  Each CTA recomputes p^T v.
-// Products are rounded separately so that H_t stays exactly symmetric.
-__global__ void rank2_kernel(SymBatchP b, int i) {
-  SymItem it = b.it[blockIdx.y];
-  const int n = it.n;
-  if (i >= n - 2) return;
-  const int len = n - i - 1;
-  const double *v = it.H + (int64_t)i * it.ld + i + 1;
-  __shared__ double red[32];
-  double s = 0.0;
-  for (int c = threadIdx.x; c < len; c += blockDim.x) s = fma(it.work[c], v[c], s);
-  const double K = 0.5 * it.tau[i] * block_sum(s, red);
-  const int64_t total = (int64_t)len * len;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int r = (int)(e / len), c = (int)(e % len);
-    const double qr = it.work[r] - K * v[r];
-    const double qc = it.work[c] - K * v[c];
-    const double t = __dadd_rn(__dmul_rn(v[r], qc), __dmul_rn(qr, v[c]));
-    double *h = it.H + (int64_t)(i + 1 + r) * it.ld + i + 1 + c;
-    *h = *h - t;
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (tr == 0 && r < len) {
+    double t = 0.0;
+    for (int w = 0; w < TRD_WPR; ++w) t += part[rloc * TRD_WPR + w];
+    it.work[r] = it.tau[i] * t;
   }
 }
 
@@ -194,18 +228,18 @@ __global__ void __launch_bounds__(256) bisect_kernel(SymBatchP b) {
 
 // Householder reduction of every item of the batch to tridiagonal form (d, e)
 static void tridiagonalize(cudaStream_t st, const SymBatchP &b, int cnt, int nmax) {
+  double *qbuf = nullptr;
+  RFDD_CUDA(cudaMallocAsync((void **)&qbuf, (size_t)cnt * std::max(nmax, 1) * sizeof(double), st));
   for (int i = 0; i < nmax; ++i) {
-    house_kernel<<<cnt, 256, 0, st>>>(b, i);
+    house_kernel<<<cnt, 512, 0, st>>>(b, i, qbuf, nmax);
     RFDD_CHECK_LAUNCH();
-    const int len = nmax - i - 1;
-    if (i < nmax - 2) {
-      symv_kernel<<<dim3(ceil_div((int64_t)len * 32, 256), cnt), 256, 0, st>>>(b, i);
-      RFDD_CHECK_LAUNCH();
-      const int blocks = std::max(1, std::min(1024, ceil_div((int64_t)len * len, 256 * 8)));
-      rank2_kernel<<<dim3(blocks, cnt), 256, 0, st>>>(b, i);
+    if (i <= nmax - 2) {
+      const int len = nmax - i - 1;
+      update_symv_kernel<<<dim3(ceil_div((int64_t)len * 32 * TRD_WPR, 256), cnt), 256, 0, st>>>(b, i, qbuf, nmax);
       RFDD_CHECK_LAUNCH();
     }
   }
+  RFDD_CUDA(cudaFreeAsync(qbuf, st));
 }
 
 // counts[i] = number of eigenvalues of item i's tridiagonal matrix below shift (Sturm count)
@@ -279,7 +313,7 @@ __global__ void __launch_bounds__(256) inviter_kernel(InvIterP p, const Cluster 
   const double *d = it.d, *e = it.e;
   double *u1 = scratch + (int64_t)blockIdx.x * scratch_per_cta;
   double *u2 = u1 + n, *u3 = u2 + n, *ml = u3 + n, *pv = ml + n, *x = pv + n, *ru = x + n;
-  __shared__ double red[32];
+  __shared__ double red[33];
   __shared__ double tnorm_s;
   if (threadIdx.x == 0) {
     double t = 0.0;
@@ -407,7 +441,7 @@ __global__ void back_kernel(BackBatchP b) {
   const SymItem it = b.s[bi];
   const int n = it.n;
   extern __shared__ double x[];
-  __shared__ double red[32];
+  __shared__ double red[33];
   for (int k = threadIdx.x; k < n; k += blockDim.x) x[k] = it.Zt[(int64_t)r * n + k];
   __syncthreads();
   for (int i = n - 3; i >= 0; --i) {

@@ -249,6 +249,47 @@ __global__ void shifted_residual_df_kernel(const int64_t *__restrict__ rp, const
     Rr[l * stride + r * b + c] = cx<double>(v.re - sr, v.im - si);
   }
 }
+// (A X, M X) for a real FP64 block X (n x b, ld b): products in double-FP32 on split operands
+__global__ void split_f64_kernel(const double *__restrict__ X, float2 *__restrict__ Xs, int64_t count) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+    float2 w;
+    split_d(X[e], w.x, w.y);
+    Xs[e] = w;
+  }
+}
+__global__ void spmm_am_df_kernel(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                  const float4 *__restrict__ am, int64_t n, const float2 *__restrict__ Xs,
+                                  double *__restrict__ YA, double *__restrict__ YM, int64_t b) {
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const int lane = threadIdx.x & 31;
+  if (r >= n) return;
+  const int64_t e0 = rp[r], e1 = rp[r + 1];
+  for (int64_t c0 = 0; c0 < b; c0 += 32) {
+    const int64_t c = c0 + lane;
+    if (c >= b) break;
+    float sa = 0.f, ta = 0.f, sm = 0.f, tm = 0.f;
+    for (int64_t e = e0; e < e1; ++e) {
+      const float2 x = Xs[(int64_t)col[e] * b + c];
+      const float4 w = am[e];
+      df_mac(sa, ta, w.x, w.y, x.x, x.y);
+      df_mac(sm, tm, w.z, w.w, x.x, x.y);
+    }
+    YA[r * b + c] = (double)sa + (double)ta;
+    YM[r * b + c] = (double)sm + (double)tm;
+  }
+}
+void spmm_am_df(cudaStream_t st, const DevPencil &P, const double *X, double *YA, double *YM, int64_t b) {
+  RFDD_REQUIRE(P.am_split != nullptr, RFDD_ESTATE, "split pencil values missing");
+  if (P.n <= 0 || b <= 0) return;
+  float2 *Xs = nullptr;
+  const int64_t count = P.n * b;
+  RFDD_CUDA(cudaMallocAsync((void **)&Xs, (size_t)count * sizeof(float2), st));
+  split_f64_kernel<<<(unsigned)std::min<int64_t>(16384, ceil_div(count, 256)), 256, 0, st>>>(X, Xs, count);
+  RFDD_CHECK_LAUNCH();
+  spmm_am_df_kernel<<<ceil_div(P.n * 32, 256), 256, 0, st>>>(P.rowptr, P.col, P.am_split, P.n, Xs, YA, YM, b);
+  RFDD_CHECK_LAUNCH();
+  RFDD_CUDA(cudaFreeAsync(Xs, st));
+}
 void shifted_residual_df(cudaStream_t st, const DevPencil &P, const cx<double> *z_dev, int nnodes,
                          const cx<double> *V, int64_t strideV, const float4 *Xs, cx<double> *R, int64_t stride,
                          int64_t b) {

@@ -48,6 +48,9 @@ void split_c64(cudaStream_t st, const cx<double> *X, float4 *Xs, int64_t count);
 void shifted_residual_df(cudaStream_t st, const DevPencil &P, const cx<double> *z_dev, int nnodes,
                          const cx<double> *V, int64_t strideV, const float4 *Xs, cx<double> *R, int64_t stride,
                          int64_t b);
+// YA = A X and YM = M X for a real FP64 block X (n x b, row-major, ld b), all rows, with the
+// products in double-FP32 arithmetic (about 2^-46 of sum |a||x|) on P.am_split and a split of X
+void spmm_am_df(cudaStream_t st, const DevPencil &P, const double *X, double *YA, double *YM, int64_t b);
 void shifted_residual(cudaStream_t st, const DevPencil &P, const cx<double> *z_dev, int nnodes,
                       const cx<double> *V, int64_t strideV, const cx<double> *X, cx<double> *R, int64_t stride,
                       int64_t b);

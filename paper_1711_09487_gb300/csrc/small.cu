@@ -1,7 +1,9 @@
 // Small dense FP64 kernels for block orthonormalisation and Rayleigh-Ritz bookkeeping.
 #include "small.cuh"
+#include "dense.cuh"
 
 #include <algorithm>
+#include <climits>
 
 namespace rfdd {
 
@@ -197,75 +199,117 @@ template void sub_inplace<double>(cudaStream_t, const double *, double *, int64_
 namespace rfdd {
 
 // ---------------------------------------------------------------------------------------
-// Pivoted Cholesky (right-looking, full symmetric storage), one step per launch pair.
-// Step t: choose the largest remaining diagonal entry, stop (rank = t) when it is <= tol,
-// interchange rows and columns t and p (whole matrix, including the factored rows' trailing
-// part), scale row t; then update the trailing block.  On exit the leading rank x rank upper
-// triangle holds R with P^T G P = R^T R on the kept directions.
+// Pivoted Cholesky P^T G P = R^T R, right-looking, on the upper triangle only (the lower
+// triangle is not read), one step per launch pair.
+// Step t: choose the largest remaining diagonal entry (a contiguous copy dg of the diagonal is
+// kept; its argmax compares the IEEE bit patterns as integers, which orders the non-negative
+// values like the doubles and costs no FP64 instruction; smallest index on ties), stop
+// (rank = t) when it is <= tol or not finite, interchange t and p symmetrically within the upper
+// triangle (the factored rows' trailing parts included); then update the trailing upper triangle
+// with the unscaled row g = G[t][t+1..]: G_ij -= (g_i g_j) / G_tt.  Rows of R are scaled by
+// 1/sqrt(G_tt) once at the end (pchol_scale_kernel).  FP64 arithmetic is scarce on this GPU, so
+// each step does one division and two FP64 operations per trailing upper entry.  On exit the
+// leading rank x rank upper triangle holds R on the kept directions.
 // ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) pchol_pivot_kernel(double *G, int k, int *perm, int t, double tol, int *rank) {
+__global__ void __launch_bounds__(1024) pchol_pivot_kernel(double *G, int k, int *perm, int t, double tol, int *rank,
+                                                           double *dg, double *dinv) {
   if (*rank >= 0) return;
-  __shared__ double bv[32];
+  __shared__ long long bv[32];
   __shared__ int bi[32];
   __shared__ int piv_s;
-  double v = -1.0;
+  long long v = LLONG_MIN;
   int idx = k;
   for (int i = t + threadIdx.x; i < k; i += blockDim.x) {
-    const double g = G[(int64_t)i * k + i];
-    if (g > v || (g == v && i < idx)) { v = g; idx = i; }
+    const long long g = __double_as_longlong(dg[i]);
+    if (g > v) { v = g; idx = i; }  // i increases within a thread: the first maximum is kept
   }
   for (int o = 16; o > 0; o >>= 1) {
-    const double v2 = __shfl_down_sync(0xffffffffu, v, o);
+    const long long v2 = __shfl_down_sync(0xffffffffu, v, o);
     const int i2 = __shfl_down_sync(0xffffffffu, idx, o);
     if (v2 > v || (v2 == v && i2 < idx)) { v = v2; idx = i2; }
   }
   if ((threadIdx.x & 31) == 0) { bv[threadIdx.x >> 5] = v; bi[threadIdx.x >> 5] = idx; }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double bvv = bv[0];
+    long long bvv = bv[0];
     int bii = bi[0];
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
       if (bv[w] > bvv || (bv[w] == bvv && bi[w] < bii)) { bvv = bv[w]; bii = bi[w]; }
-    piv_s = (bvv > tol && isfinite(bvv)) ? bii : -1;
+    const double d = bii < k ? dg[bii] : -1.0;
+    piv_s = (d > tol && isfinite(d)) ? bii : -1;
     if (piv_s < 0) *rank = t;
+    else *dinv = 1.0 / d;
   }
   __syncthreads();
   const int p = piv_s;
-  if (p < 0) return;
-  if (p != t) {
-    for (int c = threadIdx.x; c < k; c += blockDim.x) {
-      const double a = G[(int64_t)t * k + c];
-      G[(int64_t)t * k + c] = G[(int64_t)p * k + c];
-      G[(int64_t)p * k + c] = a;
+  if (p < 0 || p == t) return;
+  // symmetric interchange of t < p in upper storage:
+  //   r < t: G[r][t] <-> G[r][p];  t < r < p: G[t][r] <-> G[r][p];  r > p: G[t][r] <-> G[p][r];
+  //   diagonal G[t][t] <-> G[p][p];  G[t][p] stays
+  for (int r = threadIdx.x; r < k; r += blockDim.x) {
+    double *a, *b;
+    if (r < t) {
+      a = G + (int64_t)r * k + t;
+      b = G + (int64_t)r * k + p;
+    } else if (r == t) {
+      a = G + (int64_t)t * k + t;
+      b = G + (int64_t)p * k + p;
+    } else if (r < p) {
+      a = G + (int64_t)t * k + r;
+      b = G + (int64_t)r * k + p;
+    } else if (r == p) {
+      continue;
+    } else {
+      a = G + (int64_t)t * k + r;
+      b = G + (int64_t)p * k + r;
     }
-    __syncthreads();
-    for (int r = threadIdx.x; r < k; r += blockDim.x) {
-      const double a = G[(int64_t)r * k + t];
-      G[(int64_t)r * k + t] = G[(int64_t)r * k + p];
-      G[(int64_t)r * k + p] = a;
-    }
-    if (threadIdx.x == 0) {
-      const int a = perm[t];
-      perm[t] = perm[p];
-      perm[p] = a;
-    }
-    __syncthreads();
+    const double x = *a;
+    *a = *b;
+    *b = x;
   }
-  const double r = sqrt(G[(int64_t)t * k + t]);
-  __syncthreads();
-  if (threadIdx.x == 0) G[(int64_t)t * k + t] = r;
-  for (int c = t + 1 + threadIdx.x; c < k; c += blockDim.x) G[(int64_t)t * k + c] /= r;
+  if (threadIdx.x == 0) {
+    const int a = perm[t];
+    perm[t] = perm[p];
+    perm[p] = a;
+    const double d = dg[t];
+    dg[t] = dg[p];
+    dg[p] = d;
+  }
 }
 
-__global__ void pchol_update_kernel(double *G, int k, int t, const int *rank) {
+// trailing upper triangle: row t+1+i (grid-stride over rows), columns j >= i by the block's threads
+__global__ void pchol_update_kernel(double *G, int k, int t, const int *rank, double *dg, const double *dinv_p) {
   if (*rank >= 0) return;
   const int len = k - t - 1;
-  const int64_t total = (int64_t)len * len;
-  const double *rt = G + (int64_t)t * k + t + 1;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(e / len), j = (int)(e % len);
-    G[(int64_t)(t + 1 + i) * k + t + 1 + j] -= rt[i] * rt[j];
+  const double *g = G + (int64_t)t * k + t + 1;
+  const double dinv = *dinv_p;
+  for (int i = blockIdx.x; i < len; i += gridDim.x) {
+    const double gi = g[i];
+    double *row = G + (int64_t)(t + 1 + i) * k + t + 1;
+    for (int j = i + threadIdx.x; j < len; j += blockDim.x) {
+      const double nv = fma(-(gi * g[j]), dinv, row[j]);
+      row[j] = nv;
+      if (j == i) dg[t + 1 + i] = nv;
+    }
   }
+}
+
+// R rows: G[t][c] /= sqrt(G_tt) for c > t, G[t][t] = sqrt(G_tt), t < rank (rows in parallel)
+__global__ void pchol_scale_kernel(double *G, int k, const int *rank) {
+  const int r = *rank < 0 ? k : *rank;
+  for (int t = blockIdx.x; t < r; t += gridDim.x) {
+    double *row = G + (int64_t)t * k;
+    const double rt = sqrt(row[t]);
+    const double inv = 1.0 / rt;
+    __syncthreads();
+    for (int c = t + 1 + threadIdx.x; c < k; c += blockDim.x) row[c] *= inv;
+    __syncthreads();
+    if (threadIdx.x == 0) row[t] = rt;
+  }
+}
+
+__global__ void pchol_diag_kernel(const double *G, int k, double *dg) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) dg[i] = G[(int64_t)i * k + i];
 }
 
 __global__ void iota_kernel(int *p, int k) {
@@ -278,16 +322,23 @@ int pivoted_cholesky(cudaStream_t st, double *G, int k, int *perm, double tol, i
   RFDD_CHECK_LAUNCH();
   set_int_kernel<<<1, 1, 0, st>>>(rank_dev, -1);
   RFDD_CHECK_LAUNCH();
+  double *dg = nullptr;  // k diagonal entries, then 1 / (the current pivot)
+  RFDD_CUDA(cudaMallocAsync((void **)&dg, (size_t)(k + 1) * sizeof(double), st));
+  double *dinv = dg + k;
+  pchol_diag_kernel<<<ceil_div(k, 256), 256, 0, st>>>(G, k, dg);
+  RFDD_CHECK_LAUNCH();
   for (int t = 0; t < k; ++t) {
-    pchol_pivot_kernel<<<1, 1024, 0, st>>>(G, k, perm, t, tol, rank_dev);
+    pchol_pivot_kernel<<<1, 1024, 0, st>>>(G, k, perm, t, tol, rank_dev, dg, dinv);
     RFDD_CHECK_LAUNCH();
     const int len = k - t - 1;
     if (len > 0) {
-      const int blocks = std::max(1, std::min(1024, ceil_div((int64_t)len * len, 256 * 8)));
-      pchol_update_kernel<<<blocks, 256, 0, st>>>(G, k, t, rank_dev);
+      pchol_update_kernel<<<std::min(len, 8 * sm_count()), 256, 0, st>>>(G, k, t, rank_dev, dg, dinv);
       RFDD_CHECK_LAUNCH();
     }
   }
+  pchol_scale_kernel<<<std::min(k, 1024), 256, 0, st>>>(G, k, rank_dev);
+  RFDD_CHECK_LAUNCH();
+  RFDD_CUDA(cudaFreeAsync(dg, st));
   int rank = -1;
   RFDD_CUDA(cudaMemcpyAsync(&rank, rank_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
   RFDD_CUDA(cudaStreamSynchronize(st));

@@ -1750,8 +1750,12 @@ RRout rayleigh_ritz_coeffs(rfdd_handle *h, const double *Y, int64_t k, double dr
   Buf MY, AY, G, K;
   MY.alloc((size_t)n * k * sizeof(double));
   AY.alloc((size_t)n * k * sizeof(double));
-  spmm_f64(st, h->P, 0, n, 0, n, 0.0, 1.0, Y, k, MY.as<double>(), k, k, false);
-  spmm_f64(st, h->P, 0, n, 0, n, 1.0, 0.0, Y, k, AY.as<double>(), k, k, false);
+  if (is_mixed(h) && !h->basis_fp64) {  // the basis products' precision (basis_gemm)
+    spmm_am_df(st, h->P, Y, AY.as<double>(), MY.as<double>(), k);
+  } else {
+    spmm_f64(st, h->P, 0, n, 0, n, 0.0, 1.0, Y, k, MY.as<double>(), k, k, false);
+    spmm_f64(st, h->P, 0, n, 0, n, 1.0, 0.0, Y, k, AY.as<double>(), k, k, false);
+  }
   lap.mark("spmm");
   G.alloc((size_t)k * k * sizeof(double));
   K.alloc((size_t)k * k * sizeof(double));
