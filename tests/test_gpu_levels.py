@@ -141,3 +141,31 @@ def test_set_interface_groups_rejects_bad_labels(R):
     with pytest.raises(R.RfddError) as e:
         R.rfdd_set_interface_groups(hk, I.subdomain_groups((3, 3), (2, 2)))
     assert e.value.code == R.RFDD_EINVAL
+
+
+def test_two_level_with_complex64_factors_only(R):
+    """pack_factors = 0: the level factors stay complex64 and every solve product packs its
+    block on the fly (the border products of the group blocks included)."""
+    name, splits, gs = CASES[1]
+    w = I.workload(name)
+    groups = I.subdomain_groups(splits, gs)
+    ev, X, rs, info = R.solve(w.A, w.M, w.part, w.p, w.alpha, w.beta, w.n_nodes, groups=groups,
+                              precision=1, quad_rule=RULES[w.rule], pack_factors=0)
+    ex = w.exact[(w.exact > w.alpha) & (w.exact < w.beta)]
+    assert info["packed"] == 0
+    assert len(ev) == len(ex) and np.max(np.abs(ev - ex) / np.abs(ex)) <= TOL[1]["ev"]
+    assert rs.max() <= 1e-10
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_rfkrylov_through_the_two_level_factors(R, prec):
+    """RF-KRYLOV's full-space filter goes through Eq. (inv_dd2) and so through the level solves."""
+    name, splits, gs = CASES[1]
+    w = I.workload(name)
+    h = _handle(R, w, prec)
+    R.rfdd_set_interface_groups(h, I.subdomain_groups(splits, gs))
+    r = R.rfdd_rfkrylov(h, w.alpha, w.beta, w.n_nodes)
+    ev, X, rs = R.rfdd_result_get(r)
+    ex = w.exact[(w.exact > w.alpha) & (w.exact < w.beta)]
+    assert len(ev) == len(ex) and np.max(np.abs(ev - ex) / np.abs(ex)) <= TOL[prec]["ev"]
+    assert rs.max() <= 1e-10
