@@ -2160,6 +2160,7 @@ void interior_impl(rfdd_handle *h, double sigma) {
   // then does their launch error or pivot status concern this call
   const bool use_forked = h->I_forked && h->I_ready && h->I_sigma == sigma && h->I_tsize == sizeof(Tr);
   interior_join(h, use_forked);
+  Lap lap(st, "interior");
   if (!(h->I_ready && h->I_sigma == sigma && h->I_tsize == sizeof(Tr))) interior_factor_start<Tr>(h, sigma, st);
   h->I_ready = false;  // consumed: the next solve factors again
   Buf &Bs = h->IBs, &pivs = h->Ipiv, &RLinv = h->IRLinv, &RUinv = h->IRUinv;
@@ -2232,6 +2233,7 @@ void interior_impl(rfdd_handle *h, double sigma) {
       RFDD_CUDA(cudaMemcpyAsync(Xp, T.p, (size_t)dsum * mw * sizeof(double), cudaMemcpyDeviceToDevice, st));
     }
   };
+  lap.mark("join");
   m_orth(X.as<double>());
   const int iters = std::max(1, h->opt.subspace_iters);
   for (int it = 0; it < iters; ++it) {
@@ -2240,6 +2242,7 @@ void interior_impl(rfdd_handle *h, double sigma) {
     RFDD_CUDA(cudaMemcpyAsync(X.p, Y.p, (size_t)dsum * mw * sizeof(double), cudaMemcpyDeviceToDevice, st));
     m_orth(X.as<double>());
   }
+  lap.mark("subspace iteration");
   // Rayleigh-Ritz for (B_sigma, M_B) on span(X_j): H_j = X_j^T B_sigma X_j (X_j is M_B-orthonormal)
   spmm_f64(st, h->P, 0, dsum, 0, dsum, 1.0, -sigma, X.as<double>(), mw, Y.as<double>(), mw, mw, false);
   {
@@ -2301,41 +2304,35 @@ void interior_impl(rfdd_handle *h, double sigma) {
   X.release();
   Y.release();
   T.release();
-  // Phi = (E - sigma M_E) Q, Psi = M_E Q  (all interior rows, d x mu)
-  Buf Phi, Psi;
-  Phi.alloc((size_t)dsum * mu * sizeof(double));
-  spmm_f64(st, h->P, 0, dsum, dsum, n, 1.0, -sigma, h->Q.as<double>(), h->qcap, Phi.as<double>(), mu, mu, false);
-  if (with_gamma) {
-    Psi.alloc((size_t)dsum * mu * sizeof(double));
-    spmm_f64(st, h->P, 0, dsum, dsum, n, 0.0, 1.0, h->Q.as<double>(), h->qcap, Psi.as<double>(), mu, mu, false);
-  }
-  Buf tmp;
-  tmp.alloc((size_t)dsum * mu * sizeof(double));
-  for (int chain = 0; chain < (with_gamma ? 2 : 1); ++chain) {
-    double *Xc = chain == 0 ? Phi.as<double>() : Psi.as<double>();
-    const double sign = chain == 0 ? -1.0 : 1.0;
-    const int64_t col0 = h->kappa + (chain == 0 ? 0 : (int64_t)psi * mu);
-    for (int t = 0; t < psi; ++t) {
-      if (t > 0) {
-        spmm_f64(st, h->P, 0, dsum, 0, dsum, 0.0, 1.0, Xc, mu, tmp.as<double>(), mu, mu, false);  // M_B X
-        RFDD_CUDA(cudaMemcpyAsync(Xc, tmp.p, (size_t)dsum * mu * sizeof(double), cudaMemcpyDeviceToDevice, st));
-      }
-      solve_Bs(Xc, mu, mu);
-      // Z[0:dsum, col0 + t*mu : +mu] = sign * Xc
-      RFDD_CUDA(cudaMemcpyAsync(tmp.p, Xc, (size_t)dsum * mu * sizeof(double), cudaMemcpyDeviceToDevice, st));
-      if (sign < 0) {
-        Buf zero;
-        zero.alloc((size_t)dsum * mu * sizeof(double));
-        RFDD_CUDA(cudaMemsetAsync(zero.p, 0, (size_t)dsum * mu * sizeof(double), st));
-        sub_inplace<double>(st, Xc, zero.as<double>(), dsum * mu);
-        copy_rows_f64(st, zero.as<double>(), mu, Z + col0 + t * mu, kz, dsum, mu);
-      } else {
-        copy_rows_f64(st, Xc, mu, Z + col0 + t * mu, kz, dsum, mu);
-      }
+  lap.mark("V_j");
+  // Phi = (E - sigma M_E) Q, Psi = M_E Q  (all interior rows, d x mu), side by side in one block
+  // [Phi | Psi]: both chains apply the same B_sigma^{-1} M_B, so each step is one product and one
+  // solve on nch * mu columns (Eq. trabala, trabala2)
+  const int nch = with_gamma ? 2 : 1;
+  const int64_t wc = (int64_t)nch * mu;
+  Buf PP, tmp, neg;
+  PP.alloc((size_t)dsum * wc * sizeof(double));
+  tmp.alloc((size_t)dsum * wc * sizeof(double));
+  spmm_f64(st, h->P, 0, dsum, dsum, n, 1.0, -sigma, h->Q.as<double>(), h->qcap, PP.as<double>(), wc, mu, false);
+  if (with_gamma)
+    spmm_f64(st, h->P, 0, dsum, dsum, n, 0.0, 1.0, h->Q.as<double>(), h->qcap, PP.as<double>() + mu, wc, mu, false);
+  const std::vector<double> negv((size_t)mu, -1.0);
+  upload(neg, negv, st);
+  for (int t = 0; t < psi; ++t) {
+    if (t > 0) {
+      spmm_f64(st, h->P, 0, dsum, 0, dsum, 0.0, 1.0, PP.as<double>(), wc, tmp.as<double>(), wc, wc, false);  // M_B X
+      RFDD_CUDA(cudaMemcpyAsync(PP.p, tmp.p, (size_t)dsum * wc * sizeof(double), cudaMemcpyDeviceToDevice, st));
     }
+    solve_Bs(PP.as<double>(), wc, wc);
+    // Z[0:dsum, kappa + t*mu : +mu] = -Sigma step t;  Z[0:dsum, kappa + psi*mu + t*mu : +mu] = Gamma step t
+    const int64_t cs = h->kappa + (int64_t)t * mu;
+    copy_rows_f64(st, PP.as<double>(), wc, Z + cs, kz, dsum, mu);
+    scale_cols_f64(st, Z + cs, dsum, mu, kz, neg.as<double>());
+    if (with_gamma) copy_rows_f64(st, PP.as<double>() + mu, wc, Z + h->kappa + (int64_t)psi * mu + t * mu, kz, dsum, mu);
   }
   // interface rows: Q under the first mu columns of the Sigma block
   copy_rows_f64(st, h->Q.as<double>(), h->qcap, Z + dsum * kz + h->kappa, kz, s, mu);
+  lap.mark("chains");
   sync_status(h, "interior");
 }
 
