@@ -274,6 +274,13 @@ struct rfdd_handle {
   cudaStream_t st2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   Buf IBs, Ipiv, IRLinv, IRUinv, I_doff, I_boffr_dev, I_zs, I_status;
+  // V_j of the same shift (Alg. 3 step 3), computed right after the B_sigma factorisation on the
+  // same stream: the M_B-orthonormal subspace basis X (dsum x I_mw), the selected eigenvectors of
+  // its Rayleigh-Ritz problem (rows of I_Gt, p blocks of I_mw x I_mw) and the smallest
+  // |delta - sigma| seen (the shift guard's test)
+  Buf IVX, IVGt;
+  int64_t I_mw = 0;
+  double I_gap = 0.0;
   std::vector<int64_t> I_boffr, I_rinvoff;
   double I_sigma = 0.0;
   size_t I_tsize = 0;
@@ -1518,10 +1525,14 @@ void solve_S_levels(rfdd_handle *h, Tf *G, int64_t gs, int64_t m, const std::vec
 // Products on the eigenvector bases (Lanczos blocks, interior CholQR, Rayleigh-Ritz Gram
 // matrices, Ritz-vector updates): double-FP32 arithmetic in the mixed-precision solve, FP64 in
 // the plain FP64 solve.
+void basis_gemm_on(const rfdd_handle *h, cudaStream_t st, const std::vector<GemmItem<double>> &g, bool ta, bool tb,
+                   double alpha, double beta, const std::vector<char> &sym = {}) {
+  if (h->opt.precision == RFDD_FP64 || h->basis_fp64) gemm_simt_batched<double>(st, g, ta, tb, alpha, beta, sym);
+  else gemm_f64x2_batched(st, g, ta, tb, alpha, beta, sym);
+}
 void basis_gemm(const rfdd_handle *h, const std::vector<GemmItem<double>> &g, bool ta, bool tb, double alpha,
                 double beta, const std::vector<char> &sym = {}) {
-  if (h->opt.precision == RFDD_FP64 || h->basis_fp64) gemm_simt_batched<double>(h->st, g, ta, tb, alpha, beta, sym);
-  else gemm_f64x2_batched(h->st, g, ta, tb, alpha, beta, sym);
+  basis_gemm_on(h, h->st, g, ta, tb, alpha, beta, sym);
 }
 
 std::vector<int> all_nodes(const rfdd_handle *h) {
@@ -2047,6 +2058,140 @@ void interior_join(rfdd_handle *h, bool rethrow = true) {
   }
 }
 
+// X (dsum x m FP64, all subdomains, row-major) <- B_sigma^{-1} X on stream st, through the real
+// factors of the interior step (LU and inverted diagonal blocks)
+template <typename Tr>
+void bsig_solve(const rfdd_handle *h, cudaStream_t st, double *X, int64_t m) {
+  const int p = h->p;
+  const int64_t dsum = h->dsum;
+  Buf t;
+  t.alloc((size_t)dsum * m * sizeof(Tr));
+  convert<Tr, double>(st, X, t.as<Tr>(), dsum * m);
+  std::vector<SolveItem<Tr>> si;
+  for (int j = 0; j < p; ++j) {
+    SolveItem<Tr> x;
+    x.LU = h->IBs.as<Tr>() + h->I_boffr[j];
+    x.piv = h->Ipiv.as<int>() + h->off[j];
+    x.n = x.ld = (int)h->d[j];
+    x.X = t.as<Tr>() + h->off[j] * m;
+    x.ldx = (int)m;
+    x.ncols = (int)m;
+    x.Linv = h->IRLinv.as<Tr>() + h->I_rinvoff[j];
+    x.Uinv = h->IRUinv.as<Tr>() + h->I_rinvoff[j];
+    x.nbi = NBO;
+    si.push_back(x);
+  }
+  lu_solve_batched<Tr>(st, si, NBO);
+  convert<double, Tr>(st, t.as<Tr>(), X, dsum * m);
+}
+
+// nev_B^(j) = min(nev_b, d_j) eigenvectors per subdomain, from a subspace of mb_j columns
+void vj_sizes(const rfdd_handle *h, std::vector<int64_t> &nvb, std::vector<int64_t> &mb, int64_t &mw) {
+  const int p = h->p;
+  nvb.assign(p, 0);
+  mb.assign(p, 0);
+  mw = 0;
+  for (int j = 0; j < p; ++j) {
+    nvb[j] = std::min<int64_t>(h->opt.nev_b, h->d[j]);
+    mb[j] = std::min<int64_t>(h->d[j], nvb[j] + std::max<int64_t>(8, nvb[j] / 5));
+    mw = std::max(mw, mb[j]);
+  }
+}
+
+// V_j (Alg. 3 step 3): block shift-invert subspace iteration on B_sigma^{-1} M_B with
+// M_B-orthonormalisation (Cholesky-QR twice), then a Rayleigh-Ritz step for (B_sigma, M_B) on each
+// span(X_j) that keeps the nev_B eigenvectors with the smallest |delta - sigma|.  Runs on stream
+// st after the B_sigma factors; leaves X in h->IVX, the selected eigenvectors of the projected
+// problems in h->IVGt and the smallest |delta - sigma| in h->I_gap.  The two buffers are
+// allocated by the caller's thread on the handle's stream.
+template <typename Tr>
+void interior_vj(rfdd_handle *h, cudaStream_t st, int *status, double sigma) {
+  const int p = h->p;
+  const int64_t dsum = h->dsum;
+  std::vector<int64_t> nvb, mb;
+  int64_t mw = 0;
+  vj_sizes(h, nvb, mb, mw);
+  double *X = h->IVX.as<double>();
+  Buf Y, G, Rinv, dead, T;
+  Y.alloc((size_t)dsum * mw * sizeof(double));
+  T.alloc((size_t)dsum * mw * sizeof(double));
+  G.alloc((size_t)p * mw * mw * sizeof(double));
+  Rinv.alloc((size_t)p * mw * mw * sizeof(double));
+  dead.alloc((size_t)p * mw * sizeof(int));
+  RFDD_CUDA(cudaMemsetAsync(T.p, 0, (size_t)dsum * mw * sizeof(double), st));
+  counter_uniform_dev(st, h->opt.seed, 500, X, dsum * mw);
+  auto m_orth = [&](double *Xp) {  // M_B-orthonormalise each subdomain block (CholQR, twice)
+    for (int pass = 0; pass < 2; ++pass) {
+      spmm_f64(st, h->P, 0, dsum, 0, dsum, 0.0, 1.0, Xp, mw, Y.as<double>(), mw, mw, false);
+      std::vector<GemmItem<double>> g;
+      std::vector<CholItem> ch;
+      for (int j = 0; j < p; ++j) {
+        g.push_back({Xp + h->off[j] * mw, Y.as<double>() + h->off[j] * mw, G.as<double>() + (int64_t)j * mw * mw,
+                     (int)mb[j], (int)mb[j], (int)h->d[j], (int)mw, (int)mw, (int)mb[j]});
+        ch.push_back({G.as<double>() + (int64_t)j * mw * mw, Rinv.as<double>() + (int64_t)j * mw * mw,
+                      dead.as<int>() + j * mw, (int)mb[j]});
+      }
+      basis_gemm_on(h, st, g, true, false, 1.0, 0.0, std::vector<char>(g.size(), 1));
+      chol_inv_batched(st, ch, 1e-28);
+      std::vector<GemmItem<double>> g2;
+      for (int j = 0; j < p; ++j)
+        g2.push_back({Xp + h->off[j] * mw, Rinv.as<double>() + (int64_t)j * mw * mw, T.as<double>() + h->off[j] * mw,
+                      (int)h->d[j], (int)mb[j], (int)mb[j], (int)mw, (int)mb[j], (int)mw});
+      basis_gemm_on(h, st, g2, false, false, 1.0, 0.0);
+      RFDD_CUDA(cudaMemcpyAsync(Xp, T.p, (size_t)dsum * mw * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
+  };
+  m_orth(X);
+  const int iters = std::max(1, h->opt.subspace_iters);
+  for (int it = 0; it < iters; ++it) {
+    spmm_f64(st, h->P, 0, dsum, 0, dsum, 0.0, 1.0, X, mw, Y.as<double>(), mw, mw, false);  // M_B X
+    bsig_solve<Tr>(h, st, Y.as<double>(), mw);
+    RFDD_CUDA(cudaMemcpyAsync(X, Y.p, (size_t)dsum * mw * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    m_orth(X);
+  }
+  // Rayleigh-Ritz for (B_sigma, M_B) on span(X_j): H_j = X_j^T B_sigma X_j (X_j is M_B-orthonormal)
+  spmm_f64(st, h->P, 0, dsum, 0, dsum, 1.0, -sigma, X, mw, Y.as<double>(), mw, mw, false);
+  {
+    std::vector<GemmItem<double>> g;
+    for (int j = 0; j < p; ++j)
+      g.push_back({X + h->off[j] * mw, Y.as<double>() + h->off[j] * mw, G.as<double>() + (int64_t)j * mw * mw,
+                   (int)mb[j], (int)mb[j], (int)h->d[j], (int)mw, (int)mw, (int)mb[j]});
+    basis_gemm_on(h, st, g, true, false, 1.0, 0.0, std::vector<char>(g.size(), 1));
+  }
+  Buf ed, ee, et, ew, el, eZ;
+  ed.alloc((size_t)p * mw * sizeof(double));
+  ee.alloc((size_t)p * mw * sizeof(double));
+  et.alloc((size_t)p * mw * sizeof(double));
+  ew.alloc((size_t)p * mw * sizeof(double));
+  el.alloc((size_t)p * mw * sizeof(double));
+  eZ.alloc((size_t)p * mw * mw * sizeof(double));
+  std::vector<SymItem> si;
+  for (int j = 0; j < p; ++j)
+    si.push_back({G.as<double>() + (int64_t)j * mw * mw, (int)mb[j], (int)mb[j], ed.as<double>() + j * mw,
+                  ee.as<double>() + j * mw, et.as<double>() + j * mw, ew.as<double>() + j * mw,
+                  el.as<double>() + j * mw, eZ.as<double>() + (int64_t)j * mw * mw});
+  sym_eig_values(st, si, status);
+  std::vector<double> ev((size_t)p * mw);
+  RFDD_CUDA(cudaMemcpyAsync(ev.data(), el.p, ev.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  RFDD_CUDA(cudaStreamSynchronize(st));
+  // Ritz values of (B_sigma, M_B) on span X_j: delta - sigma for the delta nearest sigma
+  double gap = std::numeric_limits<double>::infinity();
+  for (int j = 0; j < p; ++j)
+    for (int64_t c = 0; c < mb[j]; ++c) gap = std::min(gap, std::fabs(ev[j * mw + c]));
+  std::vector<BackItem> bi;
+  for (int j = 0; j < p; ++j) {
+    std::vector<int> idx(mb[j]);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(),
+                     [&](int a, int b) { return std::fabs(ev[j * mw + a]) < std::fabs(ev[j * mw + b]); });
+    idx.resize(nvb[j]);
+    std::sort(idx.begin(), idx.end());
+    bi.push_back({&si[j], idx, h->IVGt.as<double>() + (int64_t)j * mw * mw, (int)mb[j]});
+  }
+  sym_eig_vectors(st, bi, 1e-6);
+  h->I_gap = gap;
+}
+
 // B_sigma^(j) dense (real) blocks, their LU and inverted diagonal blocks.  Buffers are allocated
 // and the small tables uploaded on the handle's stream.  With on == h->st the kernels follow
 // there and record into h->status.  Otherwise a host thread launches them on `on` after ev_fork
@@ -2078,6 +2223,12 @@ void interior_factor_start(rfdd_handle *h, double sigma, cudaStream_t on) {
   upload(h->I_boffr_dev, h->I_boffr, st);
   std::vector<cx<double>> zsig = {cx<double>(sigma, 0.0)};
   upload(h->I_zs, zsig, st);
+  {
+    std::vector<int64_t> nvb, mb;
+    vj_sizes(h, nvb, mb, h->I_mw);
+    h->IVX.alloc((size_t)std::max<int64_t>(1, dsum * h->I_mw) * sizeof(double));
+    h->IVGt.alloc((size_t)std::max<int64_t>(1, (int64_t)p * h->I_mw * h->I_mw) * sizeof(double));
+  }
   int *status = h->status.as<int>();
   if (on != st) {
     if (!h->I_status.p) h->I_status.alloc(sizeof(int));
@@ -2116,6 +2267,9 @@ void interior_factor_start(rfdd_handle *h, double sigma, cudaStream_t on) {
     lu_batched<Tr>(s, items, NBO_LU, status);
     // inverted diagonal blocks for the many solves of the subspace iteration and the chains
     lu_block_inverses<Tr>(s, fi, NBO, li, ui);
+    // V_j needs only these factors: on the second stream it overlaps the complex factorisations
+    // and the Lanczos process too
+    interior_vj<Tr>(h, s, status, sigma);
   };
   if (on == st) {
     launch(st);
@@ -2127,6 +2281,7 @@ void interior_factor_start(rfdd_handle *h, double sigma, cudaStream_t on) {
       h->I_thread = std::thread([h, on, device, launch] {
         try {
           RFDD_CUDA(cudaSetDevice(device));
+          AllocScope scope(on);  // this thread's workspaces are stream-ordered on its stream
           RFDD_CUDA(cudaStreamWaitEvent(on, h->ev_fork, 0));
           launch(on);
         } catch (...) {
@@ -2136,6 +2291,7 @@ void interior_factor_start(rfdd_handle *h, double sigma, cudaStream_t on) {
         cudaEventRecord(h->ev_join, on);
       });
     } catch (const std::system_error &) {  // no thread to be had: the same launches from here
+      AllocScope scope(on);
       RFDD_CUDA(cudaStreamWaitEvent(on, h->ev_fork, 0));
       launch(on);
       RFDD_CUDA(cudaEventRecord(h->ev_join, on));
@@ -2163,129 +2319,18 @@ void interior_impl(rfdd_handle *h, double sigma) {
   Lap lap(st, "interior");
   if (!(h->I_ready && h->I_sigma == sigma && h->I_tsize == sizeof(Tr))) interior_factor_start<Tr>(h, sigma, st);
   h->I_ready = false;  // consumed: the next solve factors again
-  Buf &Bs = h->IBs, &pivs = h->Ipiv, &RLinv = h->IRLinv, &RUinv = h->IRUinv;
-  const std::vector<int64_t> &boffr = h->I_boffr, &rinvoff = h->I_rinvoff;
   sync_status(h, "interior LU");
   if (use_forked && h->I_status.p) sync_status(h, "interior LU", &h->I_status);
-  auto solve_Bs = [&](double *X, int64_t ldx, int64_t m) {  // X (dsum x m FP64, all subdomains) <- B_sigma^{-1} X
-    Buf t;
-    t.alloc((size_t)dsum * m * sizeof(Tr));
-    convert<Tr, double>(st, X, t.as<Tr>(), dsum * m);
-    std::vector<SolveItem<Tr>> si;
-    for (int j = 0; j < p; ++j) {
-      SolveItem<Tr> x;
-      x.LU = Bs.as<Tr>() + boffr[j];
-      x.piv = pivs.as<int>() + h->off[j];
-      x.n = x.ld = (int)h->d[j];
-      x.X = t.as<Tr>() + h->off[j] * m;
-      x.ldx = (int)m;
-      x.ncols = (int)m;
-      x.Linv = RLinv.as<Tr>() + rinvoff[j];
-      x.Uinv = RUinv.as<Tr>() + rinvoff[j];
-      x.nbi = NBO;
-      si.push_back(x);
-    }
-    lu_solve_batched<Tr>(st, si, NBO);
-    convert<double, Tr>(st, t.as<Tr>(), X, dsum * m);
-    (void)ldx;
-  };
-  // V_j: block shift-invert subspace iteration on B_sigma^{-1} M_B with M_B-orthonormalisation,
-  // then a Rayleigh-Ritz step that keeps the nev_B eigenvectors with the smallest |delta - sigma|
-  std::vector<int64_t> nvb(p), mb(p), voff(p + 1, 0);
-  int64_t mbmax = 0;
-  for (int j = 0; j < p; ++j) {
-    nvb[j] = std::min<int64_t>(h->opt.nev_b, h->d[j]);
-    mb[j] = std::min<int64_t>(h->d[j], nvb[j] + std::max<int64_t>(8, nvb[j] / 5));
-    mbmax = std::max(mbmax, mb[j]);
-    voff[j + 1] = voff[j] + nvb[j];
-  }
+  lap.mark("join");
+  // V_j (computed with the factors, see interior_vj): sizes and column offsets in Z
+  std::vector<int64_t> nvb, mb, voff(p + 1, 0);
+  int64_t mw = 0;
+  vj_sizes(h, nvb, mb, mw);
+  for (int j = 0; j < p; ++j) voff[j + 1] = voff[j] + nvb[j];
+  RFDD_REQUIRE(mw == h->I_mw, RFDD_ESTATE, "interior: V_j buffers of another size");
   h->kappa = voff[p];
   h->voff = voff;
-  // one tall block X (dsum x mbmax): subdomain j uses rows off_j.. and its first mb_j columns
-  const int64_t mw = mbmax;
-  Buf X, Y, G, Rinv, dead, T;
-  X.alloc((size_t)dsum * mw * sizeof(double));
-  Y.alloc((size_t)dsum * mw * sizeof(double));
-  T.alloc((size_t)dsum * mw * sizeof(double));
-  G.alloc((size_t)p * mw * mw * sizeof(double));
-  Rinv.alloc((size_t)p * mw * mw * sizeof(double));
-  dead.alloc((size_t)p * mw * sizeof(int));
-  RFDD_CUDA(cudaMemsetAsync(T.p, 0, (size_t)dsum * mw * sizeof(double), st));
-  counter_uniform_dev(st, h->opt.seed, 500, X.as<double>(), dsum * mw);
-  auto m_orth = [&](double *Xp) {  // M_B-orthonormalise each subdomain block (CholQR, twice)
-    for (int pass = 0; pass < 2; ++pass) {
-      spmm_f64(st, h->P, 0, dsum, 0, dsum, 0.0, 1.0, Xp, mw, Y.as<double>(), mw, mw, false);
-      std::vector<GemmItem<double>> g;
-      std::vector<CholItem> ch;
-      for (int j = 0; j < p; ++j) {
-        g.push_back({Xp + h->off[j] * mw, Y.as<double>() + h->off[j] * mw, G.as<double>() + (int64_t)j * mw * mw,
-                     (int)mb[j], (int)mb[j], (int)h->d[j], (int)mw, (int)mw, (int)mb[j]});
-        ch.push_back({G.as<double>() + (int64_t)j * mw * mw, Rinv.as<double>() + (int64_t)j * mw * mw,
-                      dead.as<int>() + j * mw, (int)mb[j]});
-      }
-      basis_gemm(h, g, true, false, 1.0, 0.0, std::vector<char>(g.size(), 1));
-      chol_inv_batched(st, ch, 1e-28);
-      std::vector<GemmItem<double>> g2;
-      for (int j = 0; j < p; ++j)
-        g2.push_back({Xp + h->off[j] * mw, Rinv.as<double>() + (int64_t)j * mw * mw, T.as<double>() + h->off[j] * mw,
-                      (int)h->d[j], (int)mb[j], (int)mb[j], (int)mw, (int)mb[j], (int)mw});
-      basis_gemm(h, g2, false, false, 1.0, 0.0);
-      RFDD_CUDA(cudaMemcpyAsync(Xp, T.p, (size_t)dsum * mw * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    }
-  };
-  lap.mark("join");
-  m_orth(X.as<double>());
-  const int iters = std::max(1, h->opt.subspace_iters);
-  for (int it = 0; it < iters; ++it) {
-    spmm_f64(st, h->P, 0, dsum, 0, dsum, 0.0, 1.0, X.as<double>(), mw, Y.as<double>(), mw, mw, false);  // M_B X
-    solve_Bs(Y.as<double>(), mw, mw);
-    RFDD_CUDA(cudaMemcpyAsync(X.p, Y.p, (size_t)dsum * mw * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    m_orth(X.as<double>());
-  }
-  lap.mark("subspace iteration");
-  // Rayleigh-Ritz for (B_sigma, M_B) on span(X_j): H_j = X_j^T B_sigma X_j (X_j is M_B-orthonormal)
-  spmm_f64(st, h->P, 0, dsum, 0, dsum, 1.0, -sigma, X.as<double>(), mw, Y.as<double>(), mw, mw, false);
-  {
-    std::vector<GemmItem<double>> g;
-    for (int j = 0; j < p; ++j)
-      g.push_back({X.as<double>() + h->off[j] * mw, Y.as<double>() + h->off[j] * mw,
-                   G.as<double>() + (int64_t)j * mw * mw, (int)mb[j], (int)mb[j], (int)h->d[j], (int)mw, (int)mw,
-                   (int)mb[j]});
-    basis_gemm(h, g, true, false, 1.0, 0.0, std::vector<char>(g.size(), 1));
-  }
-  Buf ed, ee, et, ew, el, eZ;
-  ed.alloc((size_t)p * mw * sizeof(double));
-  ee.alloc((size_t)p * mw * sizeof(double));
-  et.alloc((size_t)p * mw * sizeof(double));
-  ew.alloc((size_t)p * mw * sizeof(double));
-  el.alloc((size_t)p * mw * sizeof(double));
-  eZ.alloc((size_t)p * mw * mw * sizeof(double));
-  std::vector<SymItem> si;
-  for (int j = 0; j < p; ++j)
-    si.push_back({G.as<double>() + (int64_t)j * mw * mw, (int)mb[j], (int)mb[j], ed.as<double>() + j * mw,
-                  ee.as<double>() + j * mw, et.as<double>() + j * mw, ew.as<double>() + j * mw,
-                  el.as<double>() + j * mw, eZ.as<double>() + (int64_t)j * mw * mw});
-  sym_eig_values(st, si, h->status.as<int>());
-  std::vector<double> ev((size_t)p * mw);
-  RFDD_CUDA(cudaMemcpyAsync(ev.data(), el.p, ev.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
-  RFDD_CUDA(cudaStreamSynchronize(st));
-  // Ritz values of (B_sigma, M_B) on span X_j: delta - sigma for the delta nearest sigma
-  h->interior_gap = std::numeric_limits<double>::infinity();
-  for (int j = 0; j < p; ++j)
-    for (int64_t c = 0; c < mb[j]; ++c) h->interior_gap = std::min(h->interior_gap, std::fabs(ev[j * mw + c]));
-  Buf Gt;
-  Gt.alloc((size_t)p * mw * mw * sizeof(double));
-  std::vector<BackItem> bi;
-  for (int j = 0; j < p; ++j) {
-    std::vector<int> idx(mb[j]);
-    std::iota(idx.begin(), idx.end(), 0);
-    std::stable_sort(idx.begin(), idx.end(),
-                     [&](int a, int b) { return std::fabs(ev[j * mw + a]) < std::fabs(ev[j * mw + b]); });
-    idx.resize(nvb[j]);
-    std::sort(idx.begin(), idx.end());
-    bi.push_back({&si[j], idx, Gt.as<double>() + (int64_t)j * mw * mw, (int)mb[j]});
-  }
-  sym_eig_vectors(st, bi, 1e-6);
+  h->interior_gap = h->I_gap;
   // Z = [blockdiag(V_j) | -Sigma^(psi) | Gamma^(psi)] (n x k), interface rows [0 | Q 0 | 0]
   const bool with_gamma = h->has_me;
   const int64_t kz = h->kappa + (int64_t)psi * mu * (with_gamma ? 2 : 1);
@@ -2297,13 +2342,12 @@ void interior_impl(rfdd_handle *h, double sigma) {
     // V_j = X_j * Gt_j^T  (d_j x nvb_j) into Z rows off_j, columns voff_j
     std::vector<GemmItem<double>> g;
     for (int j = 0; j < p; ++j)
-      g.push_back({X.as<double>() + h->off[j] * mw, Gt.as<double>() + (int64_t)j * mw * mw, Z + h->off[j] * kz + voff[j],
-                   (int)h->d[j], (int)nvb[j], (int)mb[j], (int)mw, (int)mb[j], (int)kz});
+      g.push_back({h->IVX.as<double>() + h->off[j] * mw, h->IVGt.as<double>() + (int64_t)j * mw * mw,
+                   Z + h->off[j] * kz + voff[j], (int)h->d[j], (int)nvb[j], (int)mb[j], (int)mw, (int)mb[j], (int)kz});
     basis_gemm(h, g, false, true, 1.0, 0.0);
   }
-  X.release();
-  Y.release();
-  T.release();
+  h->IVX.release();
+  h->IVGt.release();
   lap.mark("V_j");
   // Phi = (E - sigma M_E) Q, Psi = M_E Q  (all interior rows, d x mu), side by side in one block
   // [Phi | Psi]: both chains apply the same B_sigma^{-1} M_B, so each step is one product and one
@@ -2323,7 +2367,7 @@ void interior_impl(rfdd_handle *h, double sigma) {
       spmm_f64(st, h->P, 0, dsum, 0, dsum, 0.0, 1.0, PP.as<double>(), wc, tmp.as<double>(), wc, wc, false);  // M_B X
       RFDD_CUDA(cudaMemcpyAsync(PP.p, tmp.p, (size_t)dsum * wc * sizeof(double), cudaMemcpyDeviceToDevice, st));
     }
-    solve_Bs(PP.as<double>(), wc, wc);
+    bsig_solve<Tr>(h, st, PP.as<double>(), wc);
     // Z[0:dsum, kappa + t*mu : +mu] = -Sigma step t;  Z[0:dsum, kappa + psi*mu + t*mu : +mu] = Gamma step t
     const int64_t cs = h->kappa + (int64_t)t * mu;
     copy_rows_f64(st, PP.as<double>(), wc, Z + cs, kz, dsum, mu);
@@ -3423,7 +3467,7 @@ int rfdd_release(rfdd_handle *h) {
     if (h->st2) RFDD_CUDA(cudaStreamSynchronize(h->st2));
     for (Buf *b : {&h->fac, &h->boff_dev, &h->Doff_dev, &h->pivB, &h->Sfac, &h->pivS, &h->Skeep, &h->BLinv,
                    &h->BUinv, &h->SLinv, &h->SUinv, &h->Pk, &h->Lfac, &h->pivL, &h->LLinv, &h->LUinv, &h->IBs, &h->Ipiv, &h->IRLinv, &h->IRUinv, &h->I_doff,
-                   &h->I_boffr_dev, &h->I_zs, &h->Q, &h->Zb, &h->X0})
+                   &h->I_boffr_dev, &h->I_zs, &h->IVX, &h->IVGt, &h->Q, &h->Zb, &h->X0})
       b->release();
     h->have_factors = false;
     h->I_ready = false;
