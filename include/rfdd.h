@@ -21,9 +21,9 @@
  *    original index.  Subdomain j occupies rows [off_j, off_j + d_j); the interface occupies the
  *    last s rows.  rfdd_layout() returns off_j, d_j, s and the permutation.
  *  - Every call runs on the handle's CUDA stream and returns after its results are complete,
- *    except rfdd_solve_async().  A solve also runs the real interior factorisation (a8) on a
- *    second stream that the handle creates and owns, launched from a host thread of its own and
- *    joined before the call returns or fails.
+ *    except rfdd_solve_async().  A solve also runs the real interior factorisation and the V_j
+ *    subspace iteration (a8) on a second stream that the handle creates and owns, launched from
+ *    a host thread of its own and joined before the call returns or fails.
  *  - A handle is not thread-safe; distinct handles may be used from different threads.  Each
  *    handle's kernels record device-side failures (a zero pivot, a tensor-core wait that ran out
  *    of iterations) in a status word of that handle, so a failure is reported by the call that
