@@ -231,9 +231,30 @@ __global__ void shifted_residual_df_kernel(const int64_t *__restrict__ rp, const
   for (int64_t c0 = 0; c0 < b; c0 += 32) {
     const int64_t c = c0 + lane;
     if (c >= b) break;
-    // (A x) and (M x), real and imaginary parts, each as an unevaluated pair (s, t)
+    // (A x) and (M x), real and imaginary parts, each as an unevaluated pair (s, t); the loads of
+    // four entries are issued before their products (the column index, then the operand, is a
+    // chain of two dependent loads per entry), the products are formed in entry order
     float s0 = 0.f, t0 = 0.f, s1 = 0.f, t1 = 0.f, s2 = 0.f, t2 = 0.f, s3 = 0.f, t3 = 0.f;
-    for (int64_t e = e0; e < e1; ++e) {
+    int64_t e = e0;
+    for (; e + 4 <= e1; e += 4) {
+      int32_t q[4];
+      float4 x[4], w[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) q[u] = col[e + u];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        x[u] = Xl[(int64_t)q[u] * b + c];
+        w[u] = am[e + u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        df_mac(s0, t0, w[u].x, w[u].y, x[u].x, x[u].y);
+        df_mac(s1, t1, w[u].x, w[u].y, x[u].z, x[u].w);
+        df_mac(s2, t2, w[u].z, w[u].w, x[u].x, x[u].y);
+        df_mac(s3, t3, w[u].z, w[u].w, x[u].z, x[u].w);
+      }
+    }
+    for (; e < e1; ++e) {
       const float4 x = Xl[(int64_t)col[e] * b + c];
       const float4 w = am[e];
       df_mac(s0, t0, w.x, w.y, x.x, x.y);
