@@ -611,9 +611,12 @@ __global__ void __launch_bounds__(256) lu_swap_kernel(LuBatchP<T> lb, int K0, in
   }
 }
 
+// LU without pivoting of the w x w diagonal block of the panel (its rows are the tournament's
+// pivots, already in place), once per item: the combined L\U block into top (NB x NB, leading
+// dimension w) and the reciprocals of U's diagonal after it (NB entries); zero or non-finite
+// pivots are recorded in status.
 template <typename T>
-__global__ void __launch_bounds__(256) lu_finish_kernel(LuBatchP<T> lb, int K0, int nbo, int k0, T *top,
-                                                        int *status) {
+__global__ void __launch_bounds__(256) lu_diag_kernel(LuBatchP<T> lb, int K0, int nbo, int k0, T *top, int *status) {
   using S = ST<T>;
   using Rl = typename S::real;
   constexpr int NB = LU_NB;
@@ -639,28 +642,49 @@ __global__ void __launch_bounds__(256) lu_finish_kernel(LuBatchP<T> lb, int K0, 
       for (int r = t + 1 + (tid >> 5); r < w; r += (int)(blockDim.x >> 5)) U[r][c] = S::fms(U[r][t], U[t][c], U[r][c]);
     __syncthreads();
   }
-  __shared__ T rdiag[NB];
-  if (tid < w) rdiag[tid] = S::abs1(U[tid][tid]) != (Rl)0 ? S::div(S::one(), U[tid][tid]) : S::one();
-  __syncthreads();
-  if (blockIdx.x == 0) {
-    T *tp = top + (int64_t)blockIdx.y * NB * NB;
-    for (int e = tid; e < w * w; e += blockDim.x) tp[e] = U[e / w][e % w];
-    if (tid < w) {
-      const T d = U[tid][tid];
-      if (!S::finite(d)) atomicOr(status, DS_NONFINITE);
-      else if (S::abs1(d) == (Rl)0) atomicOr(status, DS_ZERO_PIVOT);
-    }
+  T *tp = top + (int64_t)blockIdx.y * (NB * NB + NB);
+  for (int e = tid; e < w * w; e += blockDim.x) tp[e] = U[e / w][e % w];
+  if (tid < w) {
+    const T d = U[tid][tid];
+    tp[NB * NB + tid] = S::abs1(d) != (Rl)0 ? S::div(S::one(), d) : S::one();
+    if (!S::finite(d)) atomicOr(status, DS_NONFINITE);
+    else if (S::abs1(d) == (Rl)0) atomicOr(status, DS_ZERO_PIVOT);
   }
-  const int r = k0 + w + blockIdx.x * blockDim.x + tid;
-  if (r >= it.D) return;
-  T *row = it.A + (int64_t)r * it.ld + k0;
+}
+
+// L21 = A21 U11^{-1} for the rows below the panel's diagonal block, one thread per row, with the
+// diagonal block's factors from lu_diag_kernel.  Each warp moves its 32 rows' panel columns
+// through shared memory so that global loads and stores run along the rows (coalesced).
+constexpr int FIN_THREADS = 128;
+template <typename T>
+__global__ void __launch_bounds__(FIN_THREADS) lu_finish_kernel(LuBatchP<T> lb, int K0, int nbo, int k0,
+                                                                const T *top) {
+  using S = ST<T>;
+  constexpr int NB = LU_NB;
+  const LuItem<T> it = lb.it[blockIdx.y];
+  const int wend = strip_end(K0, nbo, it.dp);
+  const int w = min(NB, wend - k0);
+  if (w <= 0) return;
+  __shared__ T U[NB][NB + 1];
+  __shared__ T rdiag[NB];
+  __shared__ T stage[FIN_THREADS / 32][32][NB + 1];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const T *tp = top + (int64_t)blockIdx.y * (NB * NB + NB);
+  for (int e = tid; e < w * w; e += blockDim.x) U[e / w][e % w] = tp[e];
+  if (tid < w) rdiag[tid] = tp[NB * NB + tid];
+  const int rbase = k0 + w + blockIdx.x * blockDim.x + wid * 32;  // first row of this warp
+  T(*st)[NB + 1] = stage[wid];
+  for (int rr = 0; rr < 32; ++rr)
+    if (rbase + rr < it.D && lane < w) st[rr][lane] = it.A[(int64_t)(rbase + rr) * it.ld + k0 + lane];
+  __syncthreads();  // U, rdiag and every warp's rows
+  const bool mine = rbase + lane < it.D;
   T x[NB];
 #pragma unroll
   for (int c = 0; c < NB; ++c)
-    if (c < w) x[c] = row[c];
+    if (c < w && mine) x[c] = st[lane][c];
 #pragma unroll
   for (int c = 0; c < NB; ++c) {
-    if (c < w) {
+    if (c < w && mine) {
       T v = x[c];
 #pragma unroll
       for (int t = 0; t < NB; ++t)
@@ -670,7 +694,10 @@ __global__ void __launch_bounds__(256) lu_finish_kernel(LuBatchP<T> lb, int K0, 
   }
 #pragma unroll
   for (int c = 0; c < NB; ++c)
-    if (c < w) row[c] = x[c];
+    if (c < w && mine) st[lane][c] = x[c];
+  __syncwarp();
+  for (int rr = 0; rr < 32; ++rr)
+    if (rbase + rr < it.D && lane < w) it.A[(int64_t)(rbase + rr) * it.ld + k0 + lane] = st[rr][lane];
 }
 
 template <typename T>
@@ -683,7 +710,7 @@ __global__ void __launch_bounds__(256) lu_u12_kernel(LuBatchP<T> lb, int K0, int
   const int w = min(NB, wend - k0);
   if (w <= 0) return;
   __shared__ T L[NB][NB + 1];
-  const T *tp = top + (int64_t)blockIdx.y * NB * NB;
+  const T *tp = top + (int64_t)blockIdx.y * (NB * NB + NB);
   for (int e = threadIdx.x; e < w * w; e += blockDim.x) L[e / w][e % w] = tp[e];
   __syncthreads();
   if (blockIdx.x == 0)
@@ -857,9 +884,11 @@ static void launch_lu_common(cudaStream_t st, const std::vector<LuItem<T>> &item
     // (2) interchanges on whole rows
     lu_swap_kernel<T><<<dim3(ceil_div(dmax, 256), cnt), 256, 0, st>>>(b, K0, nbo, k0, ca, stride);
     RFDD_CHECK_LAUNCH();
-    // (3) U11/L11 and L21
-    lu_finish_kernel<T><<<dim3(std::max(1, ceil_div(dmax - k0 - 1, 256)), cnt), 256, 0, st>>>(
-        b, K0, nbo, k0, (T *)wk.top, status);
+    // (3) U11/L11 once per item, then L21
+    lu_diag_kernel<T><<<dim3(1, cnt), 256, 0, st>>>(b, K0, nbo, k0, (T *)wk.top, status);
+    RFDD_CHECK_LAUNCH();
+    lu_finish_kernel<T><<<dim3(std::max(1, ceil_div(dmax - k0 - 1, FIN_THREADS)), cnt), FIN_THREADS, 0, st>>>(
+        b, K0, nbo, k0, (const T *)wk.top);
     RFDD_CHECK_LAUNCH();
     // (4) U12 inside the strip (also stores L11/U11 into the matrix)
     lu_u12_kernel<T><<<dim3(std::max(1, ceil_div(nbo, 256)), cnt), 256, 0, st>>>(b, K0, nbo, k0,
@@ -913,7 +942,7 @@ void lu_batched(cudaStream_t st, const std::vector<LuItem<T>> &items, int nbo, i
   LuWork wk;
   const int stride = (ceil_div(dpmax, R) + 1) * NB;
   wk.cand_ints = (size_t)2 * MAXB * stride;
-  wk.top_bytes = (size_t)MAXB * NB * NB * sizeof(T);
+  wk.top_bytes = (size_t)MAXB * (NB * NB + NB) * sizeof(T);
   RFDD_CUDA(cudaMallocAsync((void **)&wk.cand, wk.cand_ints * sizeof(int), st));
   RFDD_CUDA(cudaMallocAsync(&wk.top, wk.top_bytes, st));
   try {
