@@ -560,47 +560,98 @@ __global__ void __launch_bounds__(256) lu_tourn_kernel(LuBatchP<T> lb, int K0, i
   for (int t = tid; t < NB; t += blockDim.x) o[t] = (t < steps) ? rid[t] : -1;
 }
 
+// The panel's interchanges, once per item: LAPACK-style pivots into it.piv, and their composition
+// as a permutation of the touched rows, perm = [n, key[0..2NB), val[0..2NB)]: row position
+// key[i] receives original row val[i].
+template <typename T>
+__global__ void __launch_bounds__(32) lu_perm_kernel(LuBatchP<T> lb, int K0, int nbo, int k0,
+                                                     const int *__restrict__ cfinal, int cand_stride,
+                                                     int *__restrict__ perm) {
+  constexpr int NB = LU_NB;
+  const LuItem<T> it = lb.it[blockIdx.x];
+  const int wend = strip_end(K0, nbo, it.dp);
+  const int w = min(NB, wend - k0);
+  if (w <= 0) return;
+  // one warp: the map (key -> val) lives in shared memory, entry i with lanes i and i - 32
+  __shared__ int key[2 * NB], val[2 * NB];
+  const int lane = threadIdx.x;
+  const unsigned full = 0xffffffffu;
+  const int *pr = cfinal + (int64_t)blockIdx.x * cand_stride;
+  int nk = 0;
+  // the entry whose field equals v (keys and values are each distinct), or -1
+  auto find = [&](const int *f, int v) {
+    int at = -1;
+    for (int i0 = 0; i0 < nk; i0 += 32) {
+      const int i = i0 + lane;
+      const unsigned m = __ballot_sync(full, i < nk && f[i] == v);
+      if (m) { at = i0 + __ffs(m) - 1; break; }
+    }
+    return at;
+  };
+  for (int t = 0; t < w; ++t) {
+    const int target = pr[t];
+    const int iq = find(val, target);
+    const int q = iq >= 0 ? key[iq] : target;
+    if (lane == 0) it.piv[k0 + t] = q;
+    const int pa = k0 + t;
+    const int ia = find(key, pa), ib = find(key, q);
+    const int ra = ia >= 0 ? val[ia] : pa, rb = ib >= 0 ? val[ib] : q;
+    __syncwarp();
+    if (lane == 0) {
+      if (ia >= 0) val[ia] = rb;
+      if (ib >= 0 && ib != ia) val[ib] = ra;
+      int n = nk;
+      if (ia < 0) { key[n] = pa; val[n] = rb; ++n; }
+      if (ib < 0 && q != pa) { key[n] = q; val[n] = ra; ++n; }
+    }
+    nk += (ia < 0 ? 1 : 0) + (ib < 0 && q != pa ? 1 : 0);
+    __syncwarp();
+  }
+  int *pm = perm + (int64_t)blockIdx.x * (1 + 4 * NB);
+  if (lane == 0) pm[0] = nk;
+  for (int i = lane; i < nk; i += 32) {
+    pm[1 + i] = key[i];
+    pm[1 + 2 * NB + i] = val[i];
+  }
+}
+
+// Interchanges on whole rows: each thread moves one column of the touched rows, all of its
+// source values first (independent loads), then all of its destinations.
 template <typename T>
 __global__ void __launch_bounds__(256) lu_swap_kernel(LuBatchP<T> lb, int K0, int nbo, int k0,
-                                                      const int *__restrict__ cfinal, int cand_stride) {
+                                                      const int *__restrict__ perm) {
   constexpr int NB = LU_NB;
   const LuItem<T> it = lb.it[blockIdx.y];
   const int wend = strip_end(K0, nbo, it.dp);
   const int w = min(NB, wend - k0);
   if (w <= 0) return;
-  __shared__ int ipiv[NB];
-  if (threadIdx.x == 0) {
-    const int *pr = cfinal + (int64_t)blockIdx.y * cand_stride;
-    int key[2 * NB], val[2 * NB];
-    int nk = 0;
-    for (int t = 0; t < w; ++t) {
-      const int target = pr[t];
-      int q = target;
-      for (int i = 0; i < nk; ++i)
-        if (val[i] == target) { q = key[i]; break; }
-      ipiv[t] = q;
-      const int pa = k0 + t;
-      int ra = pa, rb = q;
-      for (int i = 0; i < nk; ++i) {
-        if (key[i] == pa) ra = val[i];
-        if (key[i] == q) rb = val[i];
-      }
-      bool fa = false, fb = false;
-      for (int i = 0; i < nk; ++i) {
-        if (key[i] == pa) { val[i] = rb; fa = true; }
-        else if (key[i] == q) { val[i] = ra; fb = true; }
-      }
-      if (!fa) { key[nk] = pa; val[nk] = rb; ++nk; }
-      if (!fb && q != pa) { key[nk] = q; val[nk] = ra; ++nk; }
-    }
-    if (blockIdx.x == 0)
-      for (int t = 0; t < w; ++t) it.piv[k0 + t] = ipiv[t];
+  __shared__ int pkey[2 * NB], pval[2 * NB];
+  __shared__ int pn;
+  const int *pm = perm + (int64_t)blockIdx.y * (1 + 4 * NB);
+  if (threadIdx.x == 0) pn = pm[0];
+  for (int i = threadIdx.x; i < 2 * NB; i += blockDim.x) {
+    pkey[i] = pm[1 + i];
+    pval[i] = pm[1 + 2 * NB + i];
   }
   __syncthreads();
+  const int n = pn;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= it.D) return;
+  if (c >= it.D || n == 0) return;
+  constexpr int CH = sizeof(T) <= 8 ? 2 * NB : 16;  // values held in registers at once
+  if (n <= CH) {
+    T x[CH];
+#pragma unroll
+    for (int i = 0; i < CH; ++i)
+      if (i < n) x[i] = it.A[(int64_t)pval[i] * it.ld + c];
+#pragma unroll
+    for (int i = 0; i < CH; ++i)
+      if (i < n) it.A[(int64_t)pkey[i] * it.ld + c] = x[i];
+    return;
+  }
+  // more touched rows than registers (complex FP64): the interchanges one after another, in the
+  // order of the LAPACK-style pivots that lu_perm_kernel stored
   for (int t = 0; t < w; ++t) {
-    const int q = ipiv[t];
+    const int q = it.piv[k0 + t];
     if (q != k0 + t) {
       T *a = it.A + (int64_t)(k0 + t) * it.ld + c;
       T *b = it.A + (int64_t)q * it.ld + c;
@@ -851,7 +902,7 @@ __global__ void __launch_bounds__(256) apply_piv_kernel(PivBatchP<T> pb) {
 // ======================================================================================
 template <typename T>
 static void launch_lu_common(cudaStream_t st, const std::vector<LuItem<T>> &items, int K0, int nbo,
-                             int k0, LuWork &wk, int *status) {
+                             int k0, LuWork &wk, int *perm, int *status) {
   constexpr int NB = LU_NB;
   constexpr int R = TournRows<T>::R;
   const size_t smem = (size_t)R * NB * sizeof(T) + (size_t)R * sizeof(int);
@@ -882,7 +933,9 @@ static void launch_lu_common(cudaStream_t st, const std::vector<LuItem<T>> &item
       std::swap(ca, cb);
     }
     // (2) interchanges on whole rows
-    lu_swap_kernel<T><<<dim3(ceil_div(dmax, 256), cnt), 256, 0, st>>>(b, K0, nbo, k0, ca, stride);
+    lu_perm_kernel<T><<<cnt, 32, 0, st>>>(b, K0, nbo, k0, ca, stride, perm);
+    RFDD_CHECK_LAUNCH();
+    lu_swap_kernel<T><<<dim3(ceil_div(dmax, 256), cnt), 256, 0, st>>>(b, K0, nbo, k0, perm);
     RFDD_CHECK_LAUNCH();
     // (3) U11/L11 once per item, then L21
     lu_diag_kernel<T><<<dim3(1, cnt), 256, 0, st>>>(b, K0, nbo, k0, (T *)wk.top, status);
@@ -945,6 +998,8 @@ void lu_batched(cudaStream_t st, const std::vector<LuItem<T>> &items, int nbo, i
   wk.top_bytes = (size_t)MAXB * (NB * NB + NB) * sizeof(T);
   RFDD_CUDA(cudaMallocAsync((void **)&wk.cand, wk.cand_ints * sizeof(int), st));
   RFDD_CUDA(cudaMallocAsync(&wk.top, wk.top_bytes, st));
+  int *perm = nullptr;  // composed interchanges of each item's panel (lu_perm_kernel)
+  RFDD_CUDA(cudaMallocAsync((void **)&perm, (size_t)MAXB * (1 + 4 * NB) * sizeof(int), st));
   try {
     for (int K0 = 0; K0 < dpmax; K0 += nbo) {
       std::vector<LuItem<T>> act;
@@ -954,7 +1009,7 @@ void lu_batched(cudaStream_t st, const std::vector<LuItem<T>> &items, int nbo, i
         std::vector<LuItem<T>> in;
         for (auto &it : act)
           if (std::min(K0 + nbo, it.dp) > k0) in.push_back(it);
-        if (!in.empty()) launch_lu_common<T>(st, in, K0, nbo, k0, wk, dev_status);
+        if (!in.empty()) launch_lu_common<T>(st, in, K0, nbo, k0, wk, perm, dev_status);
       }
       // outer strip: U12 over all trailing columns, then the deep trailing update
       std::vector<SolveItem<T>> tri;
@@ -1003,10 +1058,12 @@ void lu_batched(cudaStream_t st, const std::vector<LuItem<T>> &items, int nbo, i
   } catch (...) {
     cudaFreeAsync(wk.cand, st);
     cudaFreeAsync(wk.top, st);
+    cudaFreeAsync(perm, st);
     throw;
   }
   RFDD_CUDA(cudaFreeAsync(wk.cand, st));
   RFDD_CUDA(cudaFreeAsync(wk.top, st));
+  RFDD_CUDA(cudaFreeAsync(perm, st));
 }
 
 template <typename T>
