@@ -1182,13 +1182,15 @@ static bool has_block_inverses(const std::vector<SolveItem<T>> &items, int nbo, 
 // upper = false: X <- L^{-1} X (blocks top to bottom); true: X <- U^{-1} X (bottom to top)
 template <typename T>
 static void trsm_block_inverse(cudaStream_t st, const std::vector<SolveItem<T>> &items, int nbo, bool upper) {
+  // Each block step forms t_b = inv_b x_b into a full-height copy t of X and updates the other
+  // rows from t_b; X takes t in one copy at the end (instead of one small copy per block step).
   int nmax = 0;
   size_t tmp_elems = 0;
   std::vector<size_t> toff(items.size());
   for (size_t i = 0; i < items.size(); ++i) {
     nmax = std::max(nmax, items[i].n);
     toff[i] = tmp_elems;
-    tmp_elems += (size_t)nbo * std::max(items[i].ncols, 0);
+    tmp_elems += (size_t)std::max(items[i].n, 0) * std::max(items[i].ncols, 0);
   }
   if (nmax == 0 || tmp_elems == 0) return;
   T *tmp = nullptr;
@@ -1199,25 +1201,23 @@ static void trsm_block_inverse(cudaStream_t st, const std::vector<SolveItem<T>> 
     const int K0 = b * nbo;
     std::vector<GemmItem<T>> g1, g2;
     std::vector<TcPackedA> p1, p2;
-    std::vector<CopyItem<T>> cp;
     for (size_t i = 0; i < items.size(); ++i) {
       const SolveItem<T> &it = items[i];
       if (K0 >= it.n || it.ncols <= 0) continue;
       const int w = std::min(nbo, it.n - K0);
       const T *inv = (upper ? it.Uinv : it.Linv) + (int64_t)b * nbo * nbo;
-      T *xb = it.X + (int64_t)K0 * it.ldx, *t = tmp + toff[i];
+      T *xb = it.X + (int64_t)K0 * it.ldx, *t = tmp + toff[i] + (int64_t)K0 * it.ncols;
       g1.push_back({inv, xb, t, w, it.ncols, w, nbo, it.ldx, it.ncols});
       const float *ih = upper ? it.Uinvp_hi : it.Linvp_hi, *il = upper ? it.Uinvp_lo : it.Linvp_lo;
       const int64_t bf = tc_packed_a_floats(nbo, nbo);
       p1.push_back(ih ? TcPackedA{ih + b * bf, il + b * bf, tc_packed_a_ktiles(nbo)} : TcPackedA{});
-      cp.push_back({t, xb, it.ncols, it.ldx, w, it.ncols});
-      if (!upper && it.n - K0 - w > 0) {  // rows below: X[K0+w:] -= L[K0+w:, K0:K0+w] X_b
-        g2.push_back({it.LU + (int64_t)(K0 + w) * it.ld + K0, xb, it.X + (int64_t)(K0 + w) * it.ldx, it.n - K0 - w,
-                      it.ncols, w, it.ld, it.ldx, it.ldx});
+      if (!upper && it.n - K0 - w > 0) {  // rows below: X[K0+w:] -= L[K0+w:, K0:K0+w] t_b
+        g2.push_back({it.LU + (int64_t)(K0 + w) * it.ld + K0, t, it.X + (int64_t)(K0 + w) * it.ldx, it.n - K0 - w,
+                      it.ncols, w, it.ld, it.ncols, it.ldx});
         p2.push_back(it.LUp_hi ? tc_packed_view(it.LUp_hi, it.LUp_lo, it.n, K0 + w, K0) : TcPackedA{});
       }
-      if (upper && K0 > 0) {  // rows above: X[0:K0] -= U[0:K0, K0:K0+w] X_b
-        g2.push_back({it.LU + K0, xb, it.X, K0, it.ncols, w, it.ld, it.ldx, it.ldx});
+      if (upper && K0 > 0) {  // rows above: X[0:K0] -= U[0:K0, K0:K0+w] t_b
+        g2.push_back({it.LU + K0, t, it.X, K0, it.ncols, w, it.ld, it.ncols, it.ldx});
         p2.push_back(it.LUp_hi ? tc_packed_view(it.LUp_hi, it.LUp_lo, it.n, 0, K0) : TcPackedA{});
       }
     }
@@ -1226,15 +1226,19 @@ static void trsm_block_inverse(cudaStream_t st, const std::vector<SolveItem<T>> 
     if (use_pa) {
       if constexpr (std::is_same<T, cx<float>>::value) {
         tc_gemm_complex_pa(st, g1, p1, 1.0, 0.0);
-        copy_rows_batched<T>(st, cp);
         tc_gemm_complex_pa(st, g2, p2, -1.0, 1.0);
       }
     } else {
       gemm_batched<T>(st, g1, false, false, 1.0, 0.0);
-      copy_rows_batched<T>(st, cp);
       gemm_batched<T>(st, g2, false, false, -1.0, 1.0);
     }
   }
+  std::vector<CopyItem<T>> cp;
+  for (size_t i = 0; i < items.size(); ++i) {
+    const SolveItem<T> &it = items[i];
+    if (it.n > 0 && it.ncols > 0) cp.push_back({tmp + toff[i], it.X, it.ncols, it.ldx, it.n, it.ncols});
+  }
+  copy_rows_batched<T>(st, cp);
   RFDD_CUDA(cudaFreeAsync(tmp, st));
 }
 
