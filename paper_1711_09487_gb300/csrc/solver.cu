@@ -988,6 +988,7 @@ size_t rfdd::solve_bytes_of(const SolveShape &g, int nc, int64_t nev_guess, bool
   int64_t m = nev_guess + std::max<int64_t>((int64_t)std::ceil(g.guard_frac * nev_guess), g.min_guard);
   if (g.m_align > 1) m = (m + g.m_align - 1) / g.m_align * g.m_align;
   b += (size_t)nc * g.n * m * (sizeof(cx<double>) * 4 + scal * 2);  // completion blocks
+  b += (size_t)nc * g.n * m * scal;  // triangular solves: full-height block products
   b += (size_t)g.s * g.s * sizeof(double);                           // Lanczos basis
   if (with_setup) b += (size_t)g.nnz * (4 + 8 + 8 + 16) + (size_t)g.n * 64;
   return b;
