@@ -6,6 +6,7 @@
 #include "tc_gemm.cuh"
 
 #include <algorithm>
+#include <climits>
 #include <mutex>
 #include <type_traits>
 
@@ -446,7 +447,7 @@ struct LuBatchP {
 constexpr int TOURN_G = 8;   // candidate sets merged per CTA
 
 template <typename T>
-struct TournRows {           // rows per tournament CTA (R = G * NB), sized for <= 128 KB smem
+struct TournRows {           // rows per tournament CTA (R = G * NB): one per thread
   static constexpr int R = TOURN_G * LU_NB;
 };
 
@@ -459,16 +460,24 @@ __device__ inline int tourn_sets(int rows, int R, int level) {
   return n;
 }
 
-template <typename T>
-__device__ inline void warp_argmax(typename ST<T>::real &v, int &row, int &idx) {
-  for (int o = 16; o > 0; o >>= 1) {
-    auto v2 = __shfl_down_sync(0xffffffffu, v, o);
-    int r2 = __shfl_down_sync(0xffffffffu, row, o);
-    int i2 = __shfl_down_sync(0xffffffffu, idx, o);
-    if (v2 > v || (v2 == v && r2 < row)) { v = v2; row = r2; idx = i2; }
+// Calls f(std::integral_constant<int, i>) for i = I .. N-1 in order.
+template <int I, int N, typename F>
+__device__ __forceinline__ void static_for(F &f) {
+  if constexpr (I < N) {
+    f(std::integral_constant<int, I>{});
+    static_for<I + 1, N>(f);
   }
 }
 
+// One tournament round of the panel's pivot search.  A CTA takes up to R = G * NB candidate rows of
+// the panel's w columns (level 0: a slice of consecutive rows; above it: the winners of G sets of
+// the level below), runs LU with partial pivoting on them and emits the pivot rows in the order
+// chosen.  Thread i keeps candidate row i in registers for the whole elimination: each step is a
+// block-wide argmax of |a_it| over the rows not yet chosen (ties go to the lower row index, so
+// the winner does not depend on where a row sits), the winner publishes its row through shared
+// memory, and every other row forms its multiplier and rank-1 update in its own registers.  The
+// multipliers and updates are the same operations, in the same order, as LU on the gathered
+// rows.  Only the row indices leave the CTA.
 template <typename T>
 __global__ void __launch_bounds__(256) lu_tourn_kernel(LuBatchP<T> lb, int K0, int nbo, int k0, int level,
                                                        const int *__restrict__ cin, int *__restrict__ cout,
@@ -477,6 +486,7 @@ __global__ void __launch_bounds__(256) lu_tourn_kernel(LuBatchP<T> lb, int K0, i
   using Rl = typename S::real;
   constexpr int NB = LU_NB;
   constexpr int R = TournRows<T>::R;
+  static_assert(R == 256, "one candidate row per thread of a 256-thread CTA");
   const LuItem<T> it = lb.it[blockIdx.y];
   const int wend = strip_end(K0, nbo, it.dp);
   const int w = min(NB, wend - k0);
@@ -484,80 +494,73 @@ __global__ void __launch_bounds__(256) lu_tourn_kernel(LuBatchP<T> lb, int K0, i
   const int rows_total = it.dp - k0;
   const int set = blockIdx.x;
   if (set >= tourn_sets(rows_total, R, level)) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *Sm = reinterpret_cast<T *>(smem_raw);          // R x NB
-  int *rid = reinterpret_cast<int *>(Sm + R * NB);  // R
-  __shared__ int nr_s;
-  __shared__ Rl red_v[8];
-  __shared__ int red_r[8], red_i[8];
-  __shared__ int piv_s;
+  __shared__ T prow[NB];
+  __shared__ Rl red_v[R / 32];
+  __shared__ int red_r[R / 32];
   const int tid = threadIdx.x;
+  int my = -1;  // global index of this thread's candidate row; -1 when it has none (or it was chosen)
   if (level == 0) {
-    const int r0 = k0 + set * R;
-    const int nr = min(R, it.dp - r0);
-    for (int r = tid; r < nr; r += blockDim.x) rid[r] = r0 + r;
-    if (tid == 0) nr_s = nr;
+    const int r = k0 + set * R + tid;
+    if (r < it.dp) my = r;
   } else {
     const int *c = cin + (int64_t)blockIdx.y * cand_stride + (int64_t)set * TOURN_G * NB;
     const int nsets_in = tourn_sets(rows_total, R, level - 1);
     const int nin = min(TOURN_G, nsets_in - set * TOURN_G) * NB;
-    if (tid == 0) {
-      int nr = 0;
-      for (int e = 0; e < nin; ++e)
-        if (c[e] >= 0) rid[nr++] = c[e];
-      nr_s = nr;
-    }
+    if (tid < nin) my = c[tid];  // empty slots hold -1
   }
-  __syncthreads();
-  const int nr = nr_s;
-  for (int e = tid; e < nr * w; e += blockDim.x) {
-    const int r = e / w, c = e - r * w;
-    Sm[r * NB + c] = it.A[(int64_t)rid[r] * it.ld + k0 + c];
-  }
-  __syncthreads();
-  const int steps = min(nr, w);
-  for (int t = 0; t < steps; ++t) {
-    Rl bv = (Rl)-1;
-    int br = 0x7fffffff, bi = -1;
-    for (int r = t + tid; r < nr; r += blockDim.x) {
-      const Rl v = S::abs1(Sm[r * NB + t]);
-      if (v > bv || (v == bv && rid[r] < br)) { bv = v; br = rid[r]; bi = r; }
-    }
-    warp_argmax<T>(bv, br, bi);
-    if ((tid & 31) == 0) { red_v[tid >> 5] = bv; red_r[tid >> 5] = br; red_i[tid >> 5] = bi; }
-    __syncthreads();
-    if (tid == 0) {
-      Rl v = red_v[0];
-      int r = red_r[0], i = red_i[0];
-      for (int q = 1; q < (int)(blockDim.x >> 5); ++q)
-        if (red_v[q] > v || (red_v[q] == v && red_r[q] < r)) { v = red_v[q]; r = red_r[q]; i = red_i[q]; }
-      piv_s = i;
-    }
-    __syncthreads();
-    const int pi = piv_s;
-    if (pi != t) {
-      for (int c = tid; c < w; c += blockDim.x) {
-        T a = Sm[t * NB + c];
-        Sm[t * NB + c] = Sm[pi * NB + c];
-        Sm[pi * NB + c] = a;
-      }
-      if (tid == 0) { int a = rid[t]; rid[t] = rid[pi]; rid[pi] = a; }
-    }
-    __syncthreads();
-    const T pv = Sm[t * NB + t];
-    const bool nz = S::abs1(pv) != (Rl)0;
-    if (nz)
-      for (int r = t + 1 + tid; r < nr; r += blockDim.x) Sm[r * NB + t] = S::div(Sm[r * NB + t], pv);
-    __syncthreads();
-    // rank-1 update of the remaining rows: lane = column, warps stride over the rows
-    const int c = tid & 31;
-    if (nz && c > t && c < w)
-      for (int r = t + 1 + (tid >> 5); r < nr; r += (int)(blockDim.x >> 5))
-        Sm[r * NB + c] = S::fms(Sm[r * NB + t], Sm[t * NB + c], Sm[r * NB + c]);
-    __syncthreads();
+  T row[NB];
+  {
+    const T *src = it.A + (int64_t)(my >= 0 ? my : 0) * it.ld + k0;
+#pragma unroll
+    for (int c = 0; c < NB; ++c) row[c] = (my >= 0 && c < w) ? src[c] : S::zero();
   }
   int *o = cout + (int64_t)blockIdx.y * cand_stride + (int64_t)set * NB;
-  for (int t = tid; t < NB; t += blockDim.x) o[t] = (t < steps) ? rid[t] : -1;
+  int steps = 0;
+  bool live = true;  // false once the panel's w columns or the candidate rows are used up
+  // step t of the elimination, t a compile-time constant so that row[] stays in registers
+  auto step = [&](auto tc) {
+    constexpr int t = decltype(tc)::value;
+    if (!live || t >= w) { live = false; return; }
+    Rl v = (Rl)-1;
+    int r = INT_MAX;
+    if (my >= 0) {
+      v = S::abs1(row[t]);
+      if (v != v) v = (Rl)INFINITY;  // a NaN row still counts as a candidate
+      r = my;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      const Rl v2 = __shfl_xor_sync(0xffffffffu, v, off);
+      const int r2 = __shfl_xor_sync(0xffffffffu, r, off);
+      if (v2 > v || (v2 == v && r2 < r)) { v = v2; r = r2; }
+    }
+    if ((tid & 31) == 0) { red_v[tid >> 5] = v; red_r[tid >> 5] = r; }
+    __syncthreads();
+    v = red_v[0];
+    r = red_r[0];
+#pragma unroll
+    for (int q = 1; q < R / 32; ++q)
+      if (red_v[q] > v || (red_v[q] == v && red_r[q] < r)) { v = red_v[q]; r = red_r[q]; }
+    if (v < (Rl)0) { live = false; return; }  // no row left: the same decision in every thread
+    if (my == r) {
+#pragma unroll
+      for (int c = t; c < NB; ++c) prow[c] = row[c];
+      o[t] = my;
+      my = -1;
+    }
+    ++steps;
+    __syncthreads();
+    if (my >= 0) {
+      const T pv = prow[t];
+      if (S::abs1(pv) != (Rl)0) {
+        const T l = S::div(row[t], pv);
+#pragma unroll
+        for (int c = t + 1; c < NB; ++c)
+          if (c < w) row[c] = S::fms(l, prow[c], row[c]);
+      }
+    }
+  };
+  static_for<0, NB>(step);
+  for (int t = steps + tid; t < NB; t += blockDim.x) o[t] = -1;
 }
 
 // The panel's interchanges, once per item: LAPACK-style pivots into it.piv, and their composition
@@ -905,7 +908,6 @@ static void launch_lu_common(cudaStream_t st, const std::vector<LuItem<T>> &item
                              int k0, LuWork &wk, int *perm, int *status) {
   constexpr int NB = LU_NB;
   constexpr int R = TournRows<T>::R;
-  const size_t smem = (size_t)R * NB * sizeof(T) + (size_t)R * sizeof(int);
   for (size_t s = 0; s < items.size(); s += MAXB) {
     LuBatchP<T> b;
     memset(&b, 0, sizeof(b));
@@ -922,13 +924,13 @@ static void launch_lu_common(cudaStream_t st, const std::vector<LuItem<T>> &item
     int *ca = wk.cand, *cb = wk.cand + (size_t)MAXB * stride;
     // (1) tournament
     int nsets = ceil_div(rows_max, R);
-    lu_tourn_kernel<T><<<dim3(nsets, cnt), 256, smem, st>>>(b, K0, nbo, k0, 0, nullptr, ca, stride);
+    lu_tourn_kernel<T><<<dim3(nsets, cnt), R, 0, st>>>(b, K0, nbo, k0, 0, nullptr, ca, stride);
     RFDD_CHECK_LAUNCH();
     int level = 0;
     while (nsets > 1) {
       ++level;
       nsets = ceil_div(nsets, TOURN_G);
-      lu_tourn_kernel<T><<<dim3(nsets, cnt), 256, smem, st>>>(b, K0, nbo, k0, level, ca, cb, stride);
+      lu_tourn_kernel<T><<<dim3(nsets, cnt), R, 0, st>>>(b, K0, nbo, k0, level, ca, cb, stride);
       RFDD_CHECK_LAUNCH();
       std::swap(ca, cb);
     }
@@ -979,19 +981,6 @@ void lu_batched(cudaStream_t st, const std::vector<LuItem<T>> &items, int nbo, i
     dpmax = std::max(dpmax, it.dp);
   }
   if (dpmax == 0) return;
-  const size_t smem = (size_t)R * NB * sizeof(T) + (size_t)R * sizeof(int);
-  {  // the tournament kernel's shared-memory limit, raised once per device and scalar type
-    static std::mutex mu;
-    static std::vector<char> done;
-    int dev = 0;
-    RFDD_CUDA(cudaGetDevice(&dev));
-    std::lock_guard<std::mutex> lk(mu);
-    if ((int)done.size() <= dev) done.resize(dev + 1, 0);
-    if (!done[dev]) {
-      RFDD_CUDA(cudaFuncSetAttribute(lu_tourn_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      done[dev] = 1;
-    }
-  }
   LuWork wk;
   const int stride = (ceil_div(dpmax, R) + 1) * NB;
   wk.cand_ints = (size_t)2 * MAXB * stride;
